@@ -1,0 +1,265 @@
+/*
+ * sbr.h - C ABI of the GB300 (sm_103a) SBR channel-modelling library.
+ *
+ * Implements the data-parallel hot path of "An SBR Based Ray Tracing Channel
+ * Modeling Method for THz and Massive MIMO Communications" (arXiv
+ * 2208.10006): geodesic ray launching (Sec. II-A.1), shoot-and-bounce tracing
+ * with reception spheres (Sec. II-A.2, II-A.3), duplicate-path removal,
+ * image-method refinement, path gains with Fresnel x Kirchhoff roughness and
+ * atmospheric absorption (Eq. 1, 3, 6-10), near-field MIMO H(f) synthesis
+ * (Eq. 11-14), PDP / delay spread / angles (Eq. 2, 4, 5) and capacity
+ * (Eq. 15-17).
+ *
+ * Conventions (all entry points):
+ *  - Plain C types only. Pointers marked "dev" are CUDA device pointers owned
+ *    by the caller; "host" pointers are read before the call returns.
+ *    Handles (sbr_bvh, sbr_trace_result, sbr_path_list) are owned by the
+ *    library and released with their *_free function (NULL is accepted).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Calls enqueue work on it and return without waiting unless
+ *    marked "synchronous".
+ *  - Units: metres, hertz, siemens per metre; angles out in degrees.
+ *  - Inputs are validated on the host before any launch; a failed check
+ *    returns SBR_ERR_INVALID_ARG and launches nothing. No call traps or
+ *    asserts on the device: device-side failures (a full dedup table, a
+ *    traversal stack overflow, a bounded wait that ran out) are recorded in a
+ *    status word and returned by the next synchronous call.
+ *  - sbr_last_error() returns a thread-local message for the last failure.
+ *  - Every call works on the current CUDA device; handles must be used on the
+ *    device they were created on.
+ */
+#ifndef SBR_H
+#define SBR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SBR_OK = 0,
+    SBR_ERR_INVALID_ARG = 1,    /* bad pointer, size or parameter               */
+    SBR_ERR_CUDA = 2,           /* a CUDA runtime call failed                   */
+    SBR_ERR_CAPACITY = 3,       /* dedup table full: retry with larger table_log2 */
+    SBR_ERR_STACK_OVERFLOW = 4, /* BVH deeper than the traversal stack          */
+    SBR_ERR_TIMEOUT = 5,        /* a bounded device wait gave up                */
+    SBR_ERR_NUMERIC = 6,        /* non-finite input or result                   */
+    SBR_ERR_UNSUPPORTED = 7,    /* valid request this build cannot serve        */
+    SBR_ERR_ALLOC = 8           /* device allocation failed                      */
+} sbr_status;
+
+#define SBR_KMAX 8          /* maximum reflections per path                      */
+#define SBR_POL_V 0         /* theta-hat polarisation at both ends               */
+#define SBR_POL_H 1         /* phi-hat polarisation at both ends                 */
+
+/* precision of sbr_synthesize_H */
+#define SBR_SYNTH_FP64 0    /* FP64 CUDA-core summation                          */
+#define SBR_SYNTH_FP32 1    /* FP32 CUDA-core summation, FP64 delay phase        */
+#define SBR_SYNTH_BF16X3 2  /* tcgen05 BF16 hi/lo split (3 products), FP32 TMEM  */
+
+/* number of stats columns written by sbr_pdp_angles */
+#define SBR_NSTATS 7
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* sbr_last_error(void);
+
+/* Library version string. */
+const char* sbr_version(void);
+
+typedef struct sbr_bvh sbr_bvh;
+typedef struct sbr_trace_result sbr_trace_result;
+typedef struct sbr_path_list sbr_path_list;
+
+/* Per-surface material: relative permittivity, conductivity (S/m) and the
+ * Kirchhoff roughness standard deviation (m) of Eq. 7. */
+typedef struct {
+    double eps_r;
+    double sigma_s_per_m;
+    double rough_m;
+} sbr_material;
+
+/*
+ * sbr_launch_dirs - geodesic launch directions (Sec. II-A.1, Fig. 1).
+ * Class-I frequency-N subdivision of the icosahedron, projected to the unit
+ * sphere; R = 10 N^2 + 2 directions in the order: 12 vertices, then the N-1
+ * interior points of each of the 30 edges (sorted vertex pairs), then the
+ * interior points of each of the 20 faces (sorted vertex triples, row i
+ * outer). dirs: dev double [R*3] (x,y,z per ray). alpha: dev double [1] or
+ * NULL; receives the largest angle (rad) between directions joined by a
+ * sub-triangle edge, the ray spacing that sizes the reception sphere.
+ * N in [1, 20000].
+ */
+sbr_status sbr_launch_dirs(int32_t N, double* dirs, double* alpha, void* stream);
+
+/*
+ * sbr_build_bvh - acceleration structure over the scene triangles (the paper
+ * gives none; Sec. III-C only says the intersection search is parallelised).
+ * tri_xyz: dev float [T*9], vertices v0,v1,v2 (x,y,z) per triangle, face id =
+ * index. surface_id: dev int32 [T] in [0, S): coplanar faces that form one
+ * reflecting surface share an id. T may be 0 (an empty scene). The handle
+ * keeps its own copies; the inputs may be freed once the stream has run.
+ * *out receives the handle (library-owned; sbr_bvh_free).
+ */
+sbr_status sbr_build_bvh(const float* tri_xyz, const int32_t* surface_id, int64_t T, int32_t S,
+                         sbr_bvh** out, void* stream);
+void sbr_bvh_free(sbr_bvh* bvh);
+
+typedef struct {
+    int64_t T;
+    int32_t S;
+    int32_t n_nodes;   /* internal nodes */
+    int32_t depth;     /* maximum leaf depth */
+    int32_t reserved;
+} sbr_bvh_info;
+
+/* Synchronous: waits for the build and reports its shape. */
+sbr_status sbr_bvh_query(const sbr_bvh* bvh, sbr_bvh_info* out);
+
+/*
+ * sbr_trace - shoot and bounce (Sec. II-A.2, II-A.3).
+ * Rays start at tx (the Tx reference point) along the sbr_launch_dirs set.
+ * Each segment finds the nearest face (smallest t > 0, ties to the lower
+ * face id), ignoring every face of the surface reflected last. For bounce
+ * b = 0..max_bounces the segment [0, t_hit] is tested against every
+ * receiver: t* = (Rx - o).d, received when 0 <= t* <= t_hit and
+ * |o + t* d - Rx| <= alpha (L + t*) / sqrt(3), L the unfolded length before
+ * the segment. Then the ray reflects specularly, d' = d - 2 (d.n) n, until
+ * max_bounces reflections or escape. Received (rx, surface sequence) keys
+ * are deduplicated on the device, keeping the minimum distance (ties to the
+ * lower ray id).
+ * rx_xyz: dev double [n_rx*3] (copied; may be freed after the stream runs).
+ * alpha: 0 = computed as in sbr_launch_dirs. table_log2: 0 = automatic.
+ * max_bounces in [0, 8]; n_rx in [0, 2^20]; 10 N^2 + 2 < 2^32.
+ */
+typedef struct {
+    double tx[3];
+    const double* rx_xyz;
+    int32_t n_rx;
+    int32_t subdiv_N;
+    int32_t max_bounces;
+    int32_t table_log2;
+    double alpha;
+    uint32_t flags;
+    int32_t reserved;
+} sbr_trace_params;
+
+typedef struct {
+    int64_t rays;
+    int64_t ray_bounces;        /* segments traced: a ray with k reflections adds k+1 */
+    int64_t candidates;         /* receptions before dedup                          */
+    int64_t keys;               /* distinct (rx, surface sequence) keys             */
+    int64_t fp64_segments;      /* segments re-decided by the FP64 traversal        */
+    int64_t queue[SBR_KMAX + 2];/* rays alive at the start of each bounce           */
+    double alpha;
+    int32_t status;             /* sbr_status of the device-side checks             */
+    int32_t table_log2;
+} sbr_trace_counters;
+
+sbr_status sbr_trace(const sbr_bvh* bvh, const sbr_trace_params* params, sbr_trace_result** out,
+                     void* stream);
+/* Synchronous: waits for the trace and returns its counters and status. */
+sbr_status sbr_trace_stats(const sbr_trace_result* tr, sbr_trace_counters* out);
+void sbr_trace_free(sbr_trace_result* tr);
+
+/*
+ * sbr_paths - effective paths (Sec. II-A.2 "pick out effective paths",
+ * image method of Sec. I). Synchronous. The dedup table is compacted and
+ * sorted by (rx, n_bounce, surface sequence); each key is refined in FP64:
+ * the Tx is mirrored through the surface planes in order, the path is
+ * back-traced from the Rx, and it is kept when every intersection parameter
+ * lies in (0, 1) and every point lies inside one of its surface's triangles
+ * (barycentric tolerance 1e-9). The reported face of each point is the
+ * lowest-id such triangle; L = |image - Rx|. Invalid keys are dropped and
+ * counted. *n_paths_out receives the number of valid paths P.
+ */
+sbr_status sbr_paths(const sbr_trace_result* tr, const sbr_bvh* bvh, sbr_path_list** out,
+                     int64_t* n_paths_out, void* stream);
+
+typedef struct {
+    int64_t n_paths;
+    int64_t n_keys;       /* before refinement */
+    int64_t n_invalid;    /* dropped by refinement */
+    int32_t n_rx;
+    int32_t max_bounces;
+} sbr_path_info;
+
+sbr_status sbr_path_query(const sbr_path_list* pl, sbr_path_info* out);
+
+/*
+ * sbr_path_export - copy the path list into caller buffers (dev, any may be
+ * NULL). Layouts for P paths: rx, n_bounce int32 [P]; surf_seq, face_seq
+ * int32 [P*8] (-1 padded); pts double [P*8*3] interaction points; length
+ * double [P] (m); aod, aoa double [P*2] (azimuth, elevation from the
+ * horizontal, degrees; AoD towards the first interaction point, AoA towards
+ * the last); ray_id uint32 [P] (kept candidate); dist float [P] (its
+ * distance to the Rx at reception).
+ */
+sbr_status sbr_path_export(const sbr_path_list* pl, int32_t* rx, int32_t* n_bounce,
+                           int32_t* surf_seq, int32_t* face_seq, double* pts, double* length,
+                           double* aod, double* aoa, uint32_t* ray_id, float* dist, void* stream);
+void sbr_path_list_free(sbr_path_list* pl);
+
+/*
+ * sbr_path_gains - complex path gain g_n(f) (Eq. 1, 3, 6-10).
+ * Per reflection: lossy Fresnel TE/TM with eta = eps_r - j sigma/(2 pi f eps0)
+ * times the roughness factor rho = exp(-g/2), g = (4 pi sigma_h cos(theta_i) f / c)^2
+ * (Eq. 6-8), tracked polarimetrically (E <- rho [G_TE (E.s) s + G_TM (E.p_in) p_out]);
+ * free-space amplitude c / (4 pi f L) (Eq. 3 with unit power and beta = 1),
+ * absorption 10^(-gamma(f) L / 20000) (Eq. 9, gamma in dB/km) and dispersion
+ * phase -phi(f) (pi/180) L / 1000 (Eq. 10, phi in deg/km); projected on the
+ * Rx polarisation. The delay phasor exp(-j 2 pi f L / c) is not included.
+ * mats: dev sbr_material [S] indexed by surface id. freqs_hz: dev double [F].
+ * gamma_db_km, disp_deg_km: dev float [F] or NULL (zero). pol: SBR_POL_V/H.
+ * gains: dev complex64 [P*F] (re, im interleaved), path-major.
+ */
+sbr_status sbr_path_gains(const sbr_path_list* pl, const sbr_material* mats, int32_t S,
+                          const double* freqs_hz, int32_t F, const float* gamma_db_km,
+                          const float* disp_deg_km, int32_t pol, void* gains, void* stream);
+
+/*
+ * sbr_synthesize_H - MIMO channel matrix per frequency (Eq. 11-14) with the
+ * near-field spherical wavefront (Sec. I). For the paths of receiver
+ * rx_index, with first/last interaction points P1/Pm:
+ *   H[f,q,p] = sum_n g_n(f) exp(-j 2 pi f (L_n + dt_pn + dr_qn) / c),
+ *   dt_pn = |T_p - P1| - |T_0 - P1|,  dr_qn = |R_q - Pm| - |R_0 - Pm|,
+ * T_0 = the trace's tx, R_0 = rx_xyz[rx_index]; a LoS path uses the exact
+ * |T_p - R_q| in its phase. gains: dev complex64 [P*F] from sbr_path_gains.
+ * tx_elem: dev double [Nt*3]; rx_elem: dev double [Nr*3].
+ * precision: SBR_SYNTH_FP64 / FP32 (CUDA cores) or SBR_SYNTH_BF16X3
+ * (tcgen05 tensor cores, U diag(w) V^T contraction, FP32 accumulation).
+ * H: dev complex64 [F*Nr*Nt], element (f, q, p) at (f*Nr + q)*Nt + p.
+ */
+sbr_status sbr_synthesize_H(const sbr_path_list* pl, const void* gains, const double* freqs_hz,
+                            int32_t F, const double* tx_elem, int32_t Nt, const double* rx_elem,
+                            int32_t Nr, int32_t rx_index, int32_t precision, void* H, void* stream);
+
+/*
+ * sbr_pdp_angles - PDP and channel statistics per receiver (Eq. 2, 4, 5).
+ * Uses column f_index of gains (F columns) at frequency fc_hz. PDP: absolute
+ * delay tau = L / c in bins [k, k+1) * bin_s, tap = sum |g|^2 in dB (empty
+ * bins -inf). stats per receiver: PL_coh = -10 log10 |sum g exp(-j 2 pi fc tau)|^2,
+ * PL_inc = -10 log10 sum |g|^2, tau_rms (Eq. 5, s), power-weighted mean AoD
+ * azimuth/elevation and AoA azimuth/elevation (deg). A receiver without
+ * paths gets +inf path loss and NaN for the rest.
+ * pdp_db: dev float [n_rx*n_bins]; stats: dev double [n_rx*SBR_NSTATS].
+ */
+sbr_status sbr_pdp_angles(const sbr_path_list* pl, const void* gains, int32_t F, int32_t f_index,
+                          double fc_hz, double bin_s, int32_t n_bins, float* pdp_db,
+                          double* stats, void* stream);
+
+/*
+ * sbr_capacity - MIMO capacity (Eq. 15-17). Eq. 16's factor Q = sum |h|^2 is
+ * read as a Frobenius normalisation: W_f = (Nr Nt / Qbar) H_f H_f^H
+ * (H_f^H H_f when Nt < Nr), Qbar = mean over f of ||H_f||_F^2; SNR linear
+ * 10^(dB/10); C = mean_f log2 det(I + SNR/Nt W_f) by an FP64 Cholesky.
+ * H: dev complex64 [F*Nr*Nt]; snr_db: host double [n_snr];
+ * C: dev double [n_snr] (bit/s/Hz). min(Nr, Nt) <= 128.
+ */
+sbr_status sbr_capacity(const void* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,
+                        int32_t n_snr, double* C, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBR_H */

@@ -1,0 +1,311 @@
+"""GB300-native SBR channel modelling (arXiv 2208.10006): Python binding.
+
+Every call marshals arguments to the C ABI of libsbr.so (include/sbr.h);
+every step of the path runs in the library's CUDA kernels. PyTorch provides
+device memory and the current stream only. There is no CPU fallback: the
+functions raise if the library is missing or no CUDA device is present.
+
+Pipeline (paper section / equation):
+    build_bvh                       scene acceleration structure (Sec. III-C)
+    trace                           Sec. II-A.1 launch, II-A.2 trace, II-A.3 reception, dedup
+    paths                           effective paths, image-method refinement (Sec. I)
+    path_gains                      Eq. 1, 3, 6-10
+    synthesize_H                    Eq. 11-14, near-field wavefront
+    pdp_angles                      Eq. 2, 4, 5
+    capacity                        Eq. 15-17
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (KMAX, NSTATS, POL_H, POL_V, SYNTH_BF16X3, SYNTH_FP32, SYNTH_FP64,
+                   STATUS_NAMES)
+
+__all__ = ["SbrError", "BVH", "TraceResult", "PathList", "launch_dirs", "build_bvh", "trace",
+           "paths", "path_gains", "synthesize_H", "pdp_angles", "capacity", "version",
+           "POL_V", "POL_H", "SYNTH_FP64", "SYNTH_FP32", "SYNTH_BF16X3", "KMAX", "NSTATS",
+           "scene_to_device", "run_scene"]
+
+
+class SbrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), msg))
+        self.status = status
+
+
+def _L():
+    return _lib.load()
+
+
+def _check(st: int):
+    if st != 0:
+        raise SbrError(st, _L().sbr_last_error().decode(errors="replace"))
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the SBR library has no CPU path")
+    return torch.device("cuda", torch.cuda.current_device())
+
+
+def version() -> str:
+    return _L().sbr_version().decode()
+
+
+def launch_dirs(N: int, with_alpha: bool = True, stream=None):
+    """Geodesic launch directions [R, 3] (float64) and alpha (Sec. II-A.1)."""
+    dev = _dev()
+    R = 10 * N * N + 2
+    d = torch.empty((R, 3), dtype=torch.float64, device=dev)
+    a = torch.empty(1, dtype=torch.float64, device=dev) if with_alpha else None
+    _check(_L().sbr_launch_dirs(N, _ptr(d), _ptr(a), _stream(stream)))
+    return d, a
+
+
+class BVH:
+    def __init__(self, handle, T, S):
+        self._h = handle
+        self.T, self.S = T, S
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        i = _lib.BvhInfo()
+        _check(_L().sbr_bvh_query(self._h, C.byref(i)))
+        return dict(T=i.T, S=i.S, n_nodes=i.n_nodes, depth=i.depth)
+
+    def free(self):
+        if self._h is not None:
+            _L().sbr_bvh_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_bvh(tri: torch.Tensor, surface_id: torch.Tensor, S: int, stream=None) -> BVH:
+    """tri: float32 [T,3,3] (or [T,9]); surface_id: int32 [T]; both CUDA."""
+    T = int(surface_id.numel())
+    tri = tri.reshape(T, 9) if T else tri
+    if T:
+        assert tri.dtype == torch.float32 and surface_id.dtype == torch.int32
+    h = C.c_void_p()
+    _check(_L().sbr_build_bvh(_ptr(tri) if T else None, _ptr(surface_id) if T else None, T, int(S),
+                              C.byref(h), _stream(stream)))
+    return BVH(h, T, int(S))
+
+
+class TraceResult:
+    def __init__(self, handle, params):
+        self._h = handle
+        self.params = params
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self, check: bool = True) -> dict:
+        c = _lib.TraceCounters()
+        st = _L().sbr_trace_stats(self._h, C.byref(c))
+        if check:
+            _check(st)
+        return dict(rays=c.rays, ray_bounces=c.ray_bounces, candidates=c.candidates, keys=c.keys,
+                    fp64_segments=c.fp64_segments, queue=list(c.queue), alpha=c.alpha,
+                    status=c.status, table_log2=c.table_log2)
+
+    def free(self):
+        if self._h is not None:
+            _L().sbr_trace_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def trace(bvh: BVH, tx, rx: torch.Tensor, N: int, K: int, alpha: float = 0.0, table_log2: int = 0,
+          stream=None) -> TraceResult:
+    """Shoot and bounce. tx: 3 floats; rx: float64 [n_rx, 3] CUDA."""
+    p = _lib.TraceParams()
+    for k in range(3):
+        p.tx[k] = float(tx[k])
+    n_rx = int(rx.shape[0]) if rx is not None else 0
+    p.rx_xyz = rx.data_ptr() if n_rx else None
+    if n_rx:
+        assert rx.dtype == torch.float64 and rx.is_cuda and rx.is_contiguous()
+    p.n_rx = n_rx
+    p.subdiv_N = int(N)
+    p.max_bounces = int(K)
+    p.table_log2 = int(table_log2)
+    p.alpha = float(alpha)
+    h = C.c_void_p()
+    _check(_L().sbr_trace(bvh.handle, C.byref(p), C.byref(h), _stream(stream)))
+    return TraceResult(h, p)
+
+
+class PathList:
+    def __init__(self, handle, n):
+        self._h = handle
+        self.n = n
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        i = _lib.PathInfo()
+        _check(_L().sbr_path_query(self._h, C.byref(i)))
+        return dict(n_paths=i.n_paths, n_keys=i.n_keys, n_invalid=i.n_invalid, n_rx=i.n_rx,
+                    max_bounces=i.max_bounces)
+
+    def export(self, stream=None) -> dict:
+        dev = _dev()
+        P = self.n
+        out = dict(
+            rx=torch.empty(P, dtype=torch.int32, device=dev),
+            nb=torch.empty(P, dtype=torch.int32, device=dev),
+            seq=torch.empty((P, KMAX), dtype=torch.int32, device=dev),
+            face=torch.empty((P, KMAX), dtype=torch.int32, device=dev),
+            pts=torch.empty((P, KMAX, 3), dtype=torch.float64, device=dev),
+            L=torch.empty(P, dtype=torch.float64, device=dev),
+            aod=torch.empty((P, 2), dtype=torch.float64, device=dev),
+            aoa=torch.empty((P, 2), dtype=torch.float64, device=dev),
+            ray=torch.empty(P, dtype=torch.int32, device=dev),
+            dist=torch.empty(P, dtype=torch.float32, device=dev),
+        )
+        o = out
+        _check(_L().sbr_path_export(self._h, _ptr(o["rx"]), _ptr(o["nb"]), _ptr(o["seq"]),
+                                    _ptr(o["face"]), _ptr(o["pts"]), _ptr(o["L"]), _ptr(o["aod"]),
+                                    _ptr(o["aoa"]), _ptr(o["ray"]), _ptr(o["dist"]),
+                                    _stream(stream)))
+        return out
+
+    def free(self):
+        if self._h is not None:
+            _L().sbr_path_list_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def paths(tr: TraceResult, bvh: BVH, stream=None) -> PathList:
+    h = C.c_void_p()
+    n = C.c_int64()
+    _check(_L().sbr_paths(tr.handle, bvh.handle, C.byref(h), C.byref(n), _stream(stream)))
+    return PathList(h, int(n.value))
+
+
+def path_gains(pl: PathList, mats: torch.Tensor, freqs: torch.Tensor, gamma_db_km=None,
+               disp_deg_km=None, pol: int = POL_V, out=None, stream=None) -> torch.Tensor:
+    """Complex path gains [P, F] (complex64). mats: float64 [S, 3] CUDA."""
+    F = int(freqs.numel())
+    g = out if out is not None else torch.empty((pl.n, F), dtype=torch.complex64, device=_dev())
+    _check(_L().sbr_path_gains(pl.handle, _ptr(mats), int(mats.shape[0]), _ptr(freqs), F,
+                               _ptr(gamma_db_km), _ptr(disp_deg_km), int(pol), _ptr(g),
+                               _stream(stream)))
+    return g
+
+
+def synthesize_H(pl: PathList, gains: torch.Tensor, freqs: torch.Tensor, tx_elem: torch.Tensor,
+                 rx_elem: torch.Tensor, rx_index: int = 0, precision: int = SYNTH_FP32, out=None,
+                 stream=None) -> torch.Tensor:
+    """H(f) [F, Nr, Nt] complex64 for receiver rx_index (Eq. 13-14)."""
+    F, Nt, Nr = int(freqs.numel()), int(tx_elem.shape[0]), int(rx_elem.shape[0])
+    H = out if out is not None else torch.empty((F, Nr, Nt), dtype=torch.complex64, device=_dev())
+    g = gains if gains.numel() else torch.empty(1, dtype=torch.complex64, device=_dev())
+    _check(_L().sbr_synthesize_H(pl.handle, _ptr(g), _ptr(freqs), F, _ptr(tx_elem), Nt,
+                                 _ptr(rx_elem), Nr, int(rx_index), int(precision), _ptr(H),
+                                 _stream(stream)))
+    return H
+
+
+def pdp_angles(pl: PathList, gains: torch.Tensor, f_index: int, fc_hz: float, bin_s: float = 1e-9,
+               n_bins: int = 1024, stream=None):
+    """PDP in dB [n_rx, n_bins] (float32) and stats [n_rx, 7] (float64)."""
+    info = pl.info()
+    n_rx = info["n_rx"]
+    F = int(gains.shape[1]) if gains.dim() == 2 else 1
+    pdp = torch.empty((max(n_rx, 1), n_bins), dtype=torch.float32, device=_dev())
+    stats = torch.empty((max(n_rx, 1), NSTATS), dtype=torch.float64, device=_dev())
+    g = gains if gains.numel() else torch.empty(1, dtype=torch.complex64, device=_dev())
+    _check(_L().sbr_pdp_angles(pl.handle, _ptr(g), F, int(f_index), float(fc_hz), float(bin_s),
+                               int(n_bins), _ptr(pdp), _ptr(stats), _stream(stream)))
+    return pdp[:n_rx], stats[:n_rx]
+
+
+def capacity(H: torch.Tensor, snr_db, stream=None) -> torch.Tensor:
+    """Mean capacity over frequency (bit/s/Hz) per SNR (Eq. 15-17)."""
+    F, Nr, Nt = H.shape
+    snr = np.ascontiguousarray(np.asarray(snr_db, dtype=np.float64))
+    C_out = torch.empty(len(snr), dtype=torch.float64, device=_dev())
+    _check(_L().sbr_capacity(_ptr(H), F, Nr, Nt, snr.ctypes.data_as(C.c_void_p), len(snr),
+                             _ptr(C_out), _stream(stream)))
+    return C_out
+
+
+# ---------------------------------------------------------------- convenience
+def scene_to_device(sc: dict) -> dict:
+    """Move a scene dict of numpy arrays (see the `scenes` module) to the GPU."""
+    dev = _dev()
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    return dict(
+        tri=t(sc["tri"].reshape(-1, 9), torch.float32),
+        surface_id=t(sc["surface_id"], torch.int32),
+        S=int(len(sc["materials"])),
+        mats=t(sc["materials"].reshape(-1, 3), torch.float64),
+        rx=t(sc["rx"].reshape(-1, 3), torch.float64),
+        freqs=t(sc["freqs"], torch.float64),
+        gamma=t(sc["gamma_db_km"], torch.float32),
+        disp=t(sc["disp_deg_km"], torch.float32),
+        tx_elem=t(sc["tx_elem"].reshape(-1, 3), torch.float64),
+        rx_elem=t(sc["rx_elem"].reshape(-1, 3), torch.float64),
+        tx=[float(x) for x in sc["tx"]], N=int(sc["N"]), K=int(sc["K"]),
+        pol=POL_V if sc.get("pol", "V") == "V" else POL_H,
+    )
+
+
+def run_scene(sc: dict, alpha: float = 0.0, table_log2: int = 0, stream=None):
+    """build_bvh + trace + paths + gains for a scene dict. Returns a dict."""
+    d = scene_to_device(sc)
+    bvh = build_bvh(d["tri"], d["surface_id"], d["S"], stream=stream)
+    lg = table_log2
+    for _ in range(3):
+        tr = trace(bvh, d["tx"], d["rx"], d["N"], d["K"], alpha=alpha, table_log2=lg, stream=stream)
+        st = tr.stats(check=False)
+        if st["status"] != 3:  # SBR_ERR_CAPACITY: retry with a larger table
+            break
+        lg = st["table_log2"] + 2
+    _check(st["status"])
+    pl = paths(tr, bvh, stream=stream)
+    g = path_gains(pl, d["mats"], d["freqs"], d["gamma"], d["disp"], d["pol"], stream=stream)
+    return dict(dev=d, bvh=bvh, trace=tr, stats=st, paths=pl, export=pl.export(stream=stream), g=g)

@@ -1,0 +1,98 @@
+"""ctypes declarations of the C ABI in include/sbr.h (libsbr.so, in-tree)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsbr.so")
+
+SBR_OK = 0
+STATUS_NAMES = {0: "SBR_OK", 1: "SBR_ERR_INVALID_ARG", 2: "SBR_ERR_CUDA", 3: "SBR_ERR_CAPACITY",
+                4: "SBR_ERR_STACK_OVERFLOW", 5: "SBR_ERR_TIMEOUT", 6: "SBR_ERR_NUMERIC",
+                7: "SBR_ERR_UNSUPPORTED", 8: "SBR_ERR_ALLOC"}
+KMAX = 8
+NSTATS = 7
+POL_V, POL_H = 0, 1
+SYNTH_FP64, SYNTH_FP32, SYNTH_BF16X3 = 0, 1, 2
+
+EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_dirs", "sbr_build_bvh", "sbr_bvh_free",
+           "sbr_bvh_query", "sbr_trace", "sbr_trace_stats", "sbr_trace_free", "sbr_paths",
+           "sbr_path_query", "sbr_path_export", "sbr_path_list_free", "sbr_path_gains",
+           "sbr_synthesize_H", "sbr_pdp_angles", "sbr_capacity"]
+
+
+class TraceParams(C.Structure):
+    _fields_ = [("tx", C.c_double * 3), ("rx_xyz", C.c_void_p), ("n_rx", C.c_int32),
+                ("subdiv_N", C.c_int32), ("max_bounces", C.c_int32), ("table_log2", C.c_int32),
+                ("alpha", C.c_double), ("flags", C.c_uint32), ("reserved", C.c_int32)]
+
+
+class TraceCounters(C.Structure):
+    _fields_ = [("rays", C.c_int64), ("ray_bounces", C.c_int64), ("candidates", C.c_int64),
+                ("keys", C.c_int64), ("fp64_segments", C.c_int64), ("queue", C.c_int64 * (KMAX + 2)),
+                ("alpha", C.c_double), ("status", C.c_int32), ("table_log2", C.c_int32)]
+
+
+class BvhInfo(C.Structure):
+    _fields_ = [("T", C.c_int64), ("S", C.c_int32), ("n_nodes", C.c_int32), ("depth", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class PathInfo(C.Structure):
+    _fields_ = [("n_paths", C.c_int64), ("n_keys", C.c_int64), ("n_invalid", C.c_int64),
+                ("n_rx", C.c_int32), ("max_bounces", C.c_int32)]
+
+
+assert C.sizeof(TraceParams) == 64
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libsbr.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libsbr.so is not built: run __graft_entry__.build() or "
+                          "python paper_2208_10006_gb300/build.py")
+    L = C.CDLL(LIB_PATH)
+    p, i32, i64, f64, st = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_int
+    pp = C.POINTER(C.c_void_p)
+    L.sbr_last_error.restype = C.c_char_p
+    L.sbr_last_error.argtypes = []
+    L.sbr_version.restype = C.c_char_p
+    L.sbr_version.argtypes = []
+    L.sbr_launch_dirs.restype = st
+    L.sbr_launch_dirs.argtypes = [i32, p, p, p]
+    L.sbr_build_bvh.restype = st
+    L.sbr_build_bvh.argtypes = [p, p, i64, i32, pp, p]
+    L.sbr_bvh_free.restype = None
+    L.sbr_bvh_free.argtypes = [p]
+    L.sbr_bvh_query.restype = st
+    L.sbr_bvh_query.argtypes = [p, C.POINTER(BvhInfo)]
+    L.sbr_trace.restype = st
+    L.sbr_trace.argtypes = [p, C.POINTER(TraceParams), pp, p]
+    L.sbr_trace_stats.restype = st
+    L.sbr_trace_stats.argtypes = [p, C.POINTER(TraceCounters)]
+    L.sbr_trace_free.restype = None
+    L.sbr_trace_free.argtypes = [p]
+    L.sbr_paths.restype = st
+    L.sbr_paths.argtypes = [p, p, pp, C.POINTER(C.c_int64), p]
+    L.sbr_path_query.restype = st
+    L.sbr_path_query.argtypes = [p, C.POINTER(PathInfo)]
+    L.sbr_path_export.restype = st
+    L.sbr_path_export.argtypes = [p] + [p] * 10 + [p]
+    L.sbr_path_list_free.restype = None
+    L.sbr_path_list_free.argtypes = [p]
+    L.sbr_path_gains.restype = st
+    L.sbr_path_gains.argtypes = [p, p, i32, p, i32, p, p, i32, p, p]
+    L.sbr_synthesize_H.restype = st
+    L.sbr_synthesize_H.argtypes = [p, p, p, i32, p, i32, p, i32, i32, i32, p, p]
+    L.sbr_pdp_angles.restype = st
+    L.sbr_pdp_angles.argtypes = [p, p, i32, i32, f64, f64, i32, p, p, p]
+    L.sbr_capacity.restype = st
+    L.sbr_capacity.argtypes = [p, i32, i32, i32, p, i32, p, p]
+    _lib = L
+    return L

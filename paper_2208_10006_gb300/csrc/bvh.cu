@@ -1,0 +1,378 @@
+// Acceleration structure for the intersection search (the paper parallelises
+// this step on the GPU, Sec. III-C, without describing a structure).
+//
+// Linear BVH built entirely on the device: Morton codes of primitive
+// centroids, stable radix sort, Karras radix tree (one thread per internal
+// node), bottom-up box refit with atomic arrival flags, then emission into
+// 64-byte nodes that hold both child boxes, so a traversal step reads one
+// node and tests two boxes. Boxes are padded outward by a relative margin so
+// that FP32 traversal never culls a box that the exact ray touches.
+#include <algorithm>
+
+#include "sbr_internal.cuh"
+
+namespace sbr {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(int64_t n, int t = kThreads) {
+    return (unsigned)std::max<int64_t>(1, (n + t - 1) / t);
+}
+
+// out[0..5] centroid lo/hi, out[6..11] box lo/hi (one block)
+__global__ void k_bounds(const float* __restrict__ box, int64_t n, float* __restrict__ out) {
+    __shared__ float red[12][1024 / 32];
+    float v[12];
+    for (int a = 0; a < 3; ++a) {
+        v[a] = INFINITY; v[3 + a] = -INFINITY; v[6 + a] = INFINITY; v[9 + a] = -INFINITY;
+    }
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int a = 0; a < 3; ++a) {
+            float lo = box[6 * i + a], hi = box[6 * i + 3 + a];
+            float c = 0.5f * (lo + hi);
+            v[a] = fminf(v[a], c); v[3 + a] = fmaxf(v[3 + a], c);
+            v[6 + a] = fminf(v[6 + a], lo); v[9 + a] = fmaxf(v[9 + a], hi);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < 12; ++k) {
+        float x = v[k];
+        bool mx = (k / 3) & 1;
+        for (int o = 16; o; o >>= 1) {
+            float y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = mx ? fmaxf(x, y) : fminf(x, y);
+        }
+        if (lane == 0) red[k][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        int k = threadIdx.x;
+        bool mx = (k / 3) & 1;
+        float x = red[k][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) x = mx ? fmaxf(x, red[k][w]) : fminf(x, red[k][w]);
+        out[k] = x;
+    }
+}
+
+__device__ __forceinline__ uint32_t expand_bits(uint32_t x) {
+    x = (x * 0x00010001u) & 0xFF0000FFu;
+    x = (x * 0x00000101u) & 0x0F00F00Fu;
+    x = (x * 0x00000011u) & 0xC30C30C3u;
+    x = (x * 0x00000005u) & 0x49249249u;
+    return x;
+}
+
+__global__ void k_morton(const float* __restrict__ box, int64_t n, const float* __restrict__ bnd,
+                         uint32_t* __restrict__ code, uint32_t* __restrict__ idx) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t q[3];
+    for (int a = 0; a < 3; ++a) {
+        float c = 0.5f * (box[6 * i + a] + box[6 * i + 3 + a]);
+        float ext = bnd[3 + a] - bnd[a];
+        float u = ext > 0.f ? (c - bnd[a]) / ext : 0.f;
+        u = fminf(fmaxf(u * 1024.f, 0.f), 1023.f);
+        q[a] = (uint32_t)u;
+    }
+    code[i] = (expand_bits(q[0]) << 2) | (expand_bits(q[1]) << 1) | expand_bits(q[2]);
+    idx[i] = (uint32_t)i;
+}
+
+// longest common prefix of the (code, index) keys of sorted positions i and j
+__device__ __forceinline__ int delta(const uint32_t* __restrict__ code, int64_t n, int64_t i,
+                                     int64_t j) {
+    if (j < 0 || j >= n) return -1;
+    uint64_t a = ((uint64_t)code[i] << 32) | (uint64_t)(uint32_t)i;
+    uint64_t b = ((uint64_t)code[j] << 32) | (uint64_t)(uint32_t)j;
+    return __clzll((long long)(a ^ b));
+}
+
+__global__ void k_karras(const uint32_t* __restrict__ code, int64_t n, int32_t* __restrict__ left,
+                         int32_t* __restrict__ right, int32_t* __restrict__ parent_int,
+                         int32_t* __restrict__ parent_leaf) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (delta(code, n, i, i + 1) - delta(code, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = delta(code, n, i, i - d);
+    int64_t lmax = 2;
+    while (delta(code, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int64_t l = 0;
+    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(code, n, i, i + (l + t) * d) > dmin) l += t;
+    int64_t j = i + l * d;
+    int dnode = delta(code, n, i, j);
+    int64_t s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(code, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+    int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    if (lo == gamma) {
+        left[i] = ~(int32_t)gamma;
+        parent_leaf[gamma] = (int32_t)i;
+    } else {
+        left[i] = (int32_t)gamma;
+        parent_int[gamma] = (int32_t)i;
+    }
+    if (hi == gamma + 1) {
+        right[i] = ~(int32_t)(gamma + 1);
+        parent_leaf[gamma + 1] = (int32_t)i;
+    } else {
+        right[i] = (int32_t)(gamma + 1);
+        parent_int[gamma + 1] = (int32_t)i;
+    }
+    if (i == 0) parent_int[0] = -1;
+}
+
+__device__ __forceinline__ void ld_box(const float* p, float b[6]) {
+    const volatile float* q = p;
+    for (int k = 0; k < 6; ++k) b[k] = q[k];
+}
+
+__global__ void k_refit(const float* __restrict__ prim_box, const int32_t* __restrict__ order,
+                        int64_t n, const int32_t* __restrict__ left,
+                        const int32_t* __restrict__ right, const int32_t* __restrict__ parent_int,
+                        const int32_t* __restrict__ parent_leaf, int32_t* __restrict__ flag,
+                        float* lbox, float* ibox, int32_t* __restrict__ depth) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float* src = prim_box + 6 * (int64_t)order[j];
+    for (int k = 0; k < 6; ++k) lbox[6 * j + k] = src[k];
+    // depth of this leaf
+    {
+        int dd = 1;
+        int32_t node = n > 1 ? parent_leaf[j] : -1;
+        while (node >= 0) { ++dd; node = parent_int[node]; }
+        atomicMax(depth, dd);
+    }
+    __threadfence();
+    if (n < 2) return;
+    int32_t node = parent_leaf[j];
+    while (node >= 0) {
+        if (atomicAdd(&flag[node], 1) == 0) return;  // the sibling subtree is not done yet
+        __threadfence();
+        float a[6], b[6];
+        int32_t l = left[node], r = right[node];
+        ld_box(l < 0 ? lbox + 6 * (int64_t)(~l) : ibox + 6 * (int64_t)l, a);
+        ld_box(r < 0 ? lbox + 6 * (int64_t)(~r) : ibox + 6 * (int64_t)r, b);
+        volatile float* o = ibox + 6 * (int64_t)node;
+        for (int k = 0; k < 3; ++k) {
+            o[k] = fminf(a[k], b[k]);
+            o[3 + k] = fmaxf(a[3 + k], b[3 + k]);
+        }
+        __threadfence();
+        node = parent_int[node];
+    }
+}
+
+__device__ __forceinline__ float pad_lo(float x, float pad) { return x - pad * (fabsf(x) + 1.f); }
+__device__ __forceinline__ float pad_hi(float x, float pad) { return x + pad * (fabsf(x) + 1.f); }
+
+__global__ void k_emit(int64_t n, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                       const float* __restrict__ lbox, const float* __restrict__ ibox, float pad,
+                       float4* __restrict__ nodes, float* __restrict__ root) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nn = n > 1 ? n - 1 : 1;
+    if (i >= nn) return;
+    float b0[6], b1[6];
+    int32_t r0, r1;
+    if (n == 1) {
+        // single primitive: both children name leaf 0; traversals skip r1 == r0
+        for (int k = 0; k < 6; ++k) b0[k] = b1[k] = lbox[k];
+        r0 = ~0; r1 = ~0;
+    } else {
+        r0 = left[i]; r1 = right[i];
+        const float* p0 = r0 < 0 ? lbox + 6 * (int64_t)(~r0) : ibox + 6 * (int64_t)r0;
+        const float* p1 = r1 < 0 ? lbox + 6 * (int64_t)(~r1) : ibox + 6 * (int64_t)r1;
+        for (int k = 0; k < 6; ++k) { b0[k] = p0[k]; b1[k] = p1[k]; }
+    }
+    for (int k = 0; k < 3; ++k) {
+        b0[k] = pad_lo(b0[k], pad); b0[3 + k] = pad_hi(b0[3 + k], pad);
+        b1[k] = pad_lo(b1[k], pad); b1[3 + k] = pad_hi(b1[3 + k], pad);
+    }
+    float4* o = nodes + 4 * i;
+    o[0] = make_float4(b0[0], b0[1], b0[2], b0[3]);
+    o[1] = make_float4(b0[4], b0[5], b1[0], b1[1]);
+    o[2] = make_float4(b1[2], b1[3], b1[4], b1[5]);
+    o[3] = make_float4(__int_as_float(r0), __int_as_float(r1), 0.f, 0.f);
+    if (i == 0) {
+        const float* rb = n > 1 ? ibox : lbox;
+        for (int k = 0; k < 3; ++k) { root[k] = pad_lo(rb[k], pad); root[3 + k] = pad_hi(rb[3 + k], pad); }
+    }
+}
+
+// ---------------------------------------------------------------- triangles
+__global__ void k_tri_boxes(const float* __restrict__ tri, int64_t T, float* __restrict__ box) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    for (int a = 0; a < 3; ++a) {
+        float x0 = tri[9 * t + a], x1 = tri[9 * t + 3 + a], x2 = tri[9 * t + 6 + a];
+        box[6 * t + a] = fminf(x0, fminf(x1, x2));
+        box[6 * t + 3 + a] = fmaxf(x0, fmaxf(x1, x2));
+    }
+}
+
+__global__ void k_tri_normals(const float* __restrict__ tri, int64_t T, double* __restrict__ nrm,
+                              unsigned int* __restrict__ status) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    d3 v0 = mk3(tri[9 * t], tri[9 * t + 1], tri[9 * t + 2]);
+    d3 v1 = mk3(tri[9 * t + 3], tri[9 * t + 4], tri[9 * t + 5]);
+    d3 v2 = mk3(tri[9 * t + 6], tri[9 * t + 7], tri[9 * t + 8]);
+    d3 c = cross(v1 - v0, v2 - v0);
+    double l = norm(c);
+    if (!(l > 0.0) || !isfinite(l)) atomicOr(status, (unsigned)ST_NUMERIC);
+    st3(nrm + 3 * t, c * (1.0 / l));
+}
+
+__global__ void k_tri_pack(const float* __restrict__ tri, const int32_t* __restrict__ surf,
+                           const double* __restrict__ nrm, const int32_t* __restrict__ order,
+                           int64_t T, float4* __restrict__ out, double* __restrict__ nrm_sorted) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= T) return;
+    int64_t t = order[j];
+    const float* v = tri + 9 * t;
+    out[3 * j + 0] = make_float4(v[0], v[1], v[2], __int_as_float(surf[t]));
+    out[3 * j + 1] = make_float4(v[3], v[4], v[5], __int_as_float((int)t));
+    out[3 * j + 2] = make_float4(v[6], v[7], v[8], 0.f);
+    for (int k = 0; k < 3; ++k) nrm_sorted[3 * j + k] = nrm[3 * t + k];
+}
+
+__global__ void k_copy_surf(const int32_t* __restrict__ surf, int64_t T, int32_t S,
+                            uint32_t* __restrict__ key, uint32_t* __restrict__ val,
+                            unsigned int* __restrict__ status) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    int32_t s = surf[t];
+    if (s < 0 || s >= S) atomicOr(status, (unsigned)ST_NUMERIC);
+    key[t] = (uint32_t)min(max(s, 0), S - 1);
+    val[t] = (uint32_t)t;
+}
+
+__global__ void k_surface_offsets(const uint32_t* __restrict__ key, int64_t T, int32_t S,
+                                  int32_t* __restrict__ s_off) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s > S) return;
+    int64_t lo = 0, hi = T;  // first position with key >= s
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (key[mid] < (uint32_t)s) lo = mid + 1; else hi = mid;
+    }
+    s_off[s] = (int32_t)lo;
+}
+
+}  // namespace
+
+sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, BvhNodes* out,
+                      int32_t* d_depth, cudaStream_t s) {
+    *out = BvhNodes{};
+    if (n <= 0) return SBR_OK;
+    if (n >= (int64_t)1 << 31) {
+        set_error("too many primitives for the BVH");
+        return SBR_ERR_UNSUPPORTED;
+    }
+    int64_t nn = n > 1 ? n - 1 : 1;
+    float* bnd;
+    uint32_t *code, *idx;
+    int32_t *left, *right, *pint, *pleaf, *flag;
+    float *lbox, *ibox;
+    SBR_TRY(dalloc_n(&bnd, 12, s));
+    SBR_TRY(dalloc_n(&code, n, s));
+    SBR_TRY(dalloc_n(&idx, n, s));
+    SBR_TRY(dalloc_n(&left, nn, s));
+    SBR_TRY(dalloc_n(&right, nn, s));
+    SBR_TRY(dalloc_n(&pint, nn, s));
+    SBR_TRY(dalloc_n(&pleaf, n, s));
+    SBR_TRY(dalloc_n(&flag, nn, s));
+    SBR_TRY(dalloc_n(&lbox, 6 * n, s));
+    SBR_TRY(dalloc_n(&ibox, 6 * nn, s));
+    SBR_TRY(dalloc_n(&out->nodes, 4 * nn, s));
+    SBR_TRY(dalloc_n(&out->d_root, 6, s));
+    SBR_TRY_CUDA(cudaMemsetAsync(flag, 0, nn * sizeof(int32_t), s));
+    SBR_TRY_CUDA(cudaMemsetAsync(d_depth, 0, sizeof(int32_t), s));
+    k_bounds<<<1, 1024, 0, s>>>(prim_box, n, bnd);
+    k_morton<<<blocks_for(n), kThreads, 0, s>>>(prim_box, n, bnd, code, idx);
+    SBR_TRY_CUDA(cudaGetLastError());
+    SBR_TRY(radix_sort_pairs(code, idx, n, 30, s));
+    if (n > 1) k_karras<<<blocks_for(n - 1), kThreads, 0, s>>>(code, n, left, right, pint, pleaf);
+    k_refit<<<blocks_for(n), kThreads, 0, s>>>(prim_box, (const int32_t*)idx, n, left, right, pint,
+                                               pleaf, flag, lbox, ibox, d_depth);
+    k_emit<<<blocks_for(nn), kThreads, 0, s>>>(n, left, right, lbox, ibox, pad_rel, out->nodes,
+                                               out->d_root);
+    SBR_TRY_CUDA(cudaGetLastError());
+    out->order = reinterpret_cast<int32_t*>(idx);
+    out->n_nodes = (int32_t)nn;
+    dfree(bnd, s); dfree(code, s); dfree(left, s); dfree(right, s); dfree(pint, s);
+    dfree(pleaf, s); dfree(flag, s); dfree(lbox, s); dfree(ibox, s);
+    return SBR_OK;
+}
+
+void free_lbvh(BvhNodes* b, cudaStream_t s) {
+    if (b->nodes) dfree(b->nodes, s);
+    if (b->order) dfree(b->order, s);
+    if (b->d_root) dfree(b->d_root, s);
+    *b = BvhNodes{};
+}
+
+sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S, sbr_bvh* b,
+                     cudaStream_t s) {
+    b->T = T;
+    b->S = S;
+    SBR_TRY(dalloc_n(&b->d_depth, 1, s));
+    SBR_TRY_CUDA(cudaMemsetAsync(b->d_depth, 0, sizeof(int32_t), s));
+    SBR_TRY(dalloc_n(&b->s_off, (size_t)S + 1, s));
+    if (T == 0) {
+        SBR_TRY_CUDA(cudaMemsetAsync(b->s_off, 0, sizeof(int32_t) * ((size_t)S + 1), s));
+        return SBR_OK;
+    }
+    unsigned int* status;
+    SBR_TRY(dalloc_n(&status, 1, s));
+    SBR_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
+    SBR_TRY(dalloc_n(&b->tri, 9 * T, s));
+    SBR_TRY(dalloc_n(&b->surf, T, s));
+    SBR_TRY(dalloc_n(&b->nrm, 3 * T, s));
+    SBR_TRY(dalloc_n(&b->tri_sorted, 3 * T, s));
+    SBR_TRY(dalloc_n(&b->nrm_sorted, 3 * T, s));
+    SBR_TRY(dalloc_n(&b->s_tri, T, s));
+    SBR_TRY_CUDA(cudaMemcpyAsync(b->tri, tri, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, s));
+    SBR_TRY_CUDA(cudaMemcpyAsync(b->surf, surf, sizeof(int32_t) * T, cudaMemcpyDeviceToDevice, s));
+    float* box;
+    SBR_TRY(dalloc_n(&box, 6 * T, s));
+    k_tri_boxes<<<blocks_for(T), kThreads, 0, s>>>(b->tri, T, box);
+    k_tri_normals<<<blocks_for(T), kThreads, 0, s>>>(b->tri, T, b->nrm, status);
+    SBR_TRY_CUDA(cudaGetLastError());
+    // relative box padding: 2^-20 of (|x| + 1) covers FP32 ray/box rounding
+    SBR_TRY(build_lbvh(box, T, 1.0f / (1 << 20), &b->tree, b->d_depth, s));
+    k_tri_pack<<<blocks_for(T), kThreads, 0, s>>>(b->tri, b->surf, b->nrm, b->tree.order, T,
+                                                  b->tri_sorted, b->nrm_sorted);
+    // faces per surface, ascending face id (stable sort on the surface id)
+    uint32_t *key, *val;
+    SBR_TRY(dalloc_n(&key, T, s));
+    val = reinterpret_cast<uint32_t*>(b->s_tri);
+    k_copy_surf<<<blocks_for(T), kThreads, 0, s>>>(b->surf, T, S, key, val, status);
+    SBR_TRY_CUDA(cudaGetLastError());
+    int bits = 1;
+    while (bits < 31 && ((int64_t)1 << bits) < (int64_t)S) ++bits;
+    SBR_TRY(radix_sort_pairs(key, val, T, bits, s));
+    k_surface_offsets<<<blocks_for((int64_t)S + 1), kThreads, 0, s>>>(key, T, S, b->s_off);
+    SBR_TRY_CUDA(cudaGetLastError());
+    uint32_t h_status = 0;
+    SBR_TRY_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    SBR_TRY_CUDA(cudaMemcpyAsync(b->tree.lo, b->tree.d_root, 3 * sizeof(float),
+                                 cudaMemcpyDeviceToHost, s));
+    SBR_TRY_CUDA(cudaMemcpyAsync(b->tree.hi, b->tree.d_root + 3, 3 * sizeof(float),
+                                 cudaMemcpyDeviceToHost, s));
+    SBR_TRY_CUDA(cudaStreamSynchronize(s));
+    dfree(box, s);
+    dfree(key, s);
+    dfree(status, s);
+    if (h_status) {
+        set_error("sbr_build_bvh: degenerate triangle or surface id out of range");
+        return SBR_ERR_INVALID_ARG;
+    }
+    return SBR_OK;
+}
+
+}  // namespace sbr

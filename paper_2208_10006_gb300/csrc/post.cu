@@ -1,0 +1,236 @@
+// Channel statistics (Eq. 2, 4, 5; the Table I quantities) and MIMO capacity
+// (Eq. 15-17).
+//
+// PDP / stats: one block per receiver. tau = L / c, bin floor(tau / bin_s),
+// tap = sum |g|^2 (FP64 accumulation), PL_coh from the coherent sum with the
+// FP64-reduced delay phase, tau_rms from the power-weighted moments (Eq. 5),
+// power-weighted mean AoD/AoA.
+//
+// Capacity: Eq. 16 multiplies W by Q = sum |h|^2, which read literally drives
+// C to zero at realistic path loss; the reading used is the Frobenius
+// normalisation W_f = (Nr Nt / Qbar) H_f H_f^H (H_f^H H_f when Nt < Nr),
+// Qbar = mean_f ||H_f||_F^2. W_f is formed in FP32 on CUDA cores, then
+// log2 det(I + SNR/Nt W_f) by an FP64 complex Cholesky in shared memory, one
+// block per frequency; the per-(f, SNR) log-determinants are averaged over f
+// in a fixed order.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "sbr_internal.cuh"
+
+namespace sbr {
+namespace {
+
+constexpr int kPdpThreads = 256;
+
+__device__ double block_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        sh[32] = t;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+__global__ void __launch_bounds__(kPdpThreads)
+k_pdp(const int32_t* __restrict__ rx_off, const double* __restrict__ L, const double* __restrict__ aod,
+      const double* __restrict__ aoa, const float2* __restrict__ g, int32_t F, int32_t f_index,
+      double fc, double bin_s, int32_t n_bins, float* __restrict__ pdp, double* __restrict__ stats) {
+    extern __shared__ double acc[];  // [n_bins]
+    __shared__ double sh[33];
+    const int r = blockIdx.x;
+    const int32_t o0 = rx_off[r], o1 = rx_off[r + 1];
+    for (int k = threadIdx.x; k < n_bins; k += blockDim.x) acc[k] = 0.0;
+    __syncthreads();
+    double sp = 0, st = 0, st2 = 0, cr = 0, ci = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    for (int32_t n = o0 + threadIdx.x; n < o1; n += blockDim.x) {
+        float2 gg = g[(int64_t)n * F + f_index];
+        double gr = gg.x, gi = gg.y;
+        double pw = gr * gr + gi * gi;
+        double tau = L[n] / kC0;
+        double kb = floor(tau / bin_s);
+        if (kb >= 0.0 && kb < (double)n_bins) atomicAdd(&acc[(int)kb], pw);
+        sp += pw; st += pw * tau; st2 += pw * tau * tau;
+        double cyc = fc * L[n] / kC0;
+        double s, c;
+        sincospi(-2.0 * (cyc - floor(cyc)), &s, &c);
+        cr += gr * c - gi * s;
+        ci += gr * s + gi * c;
+        a1 += pw * aod[2 * n]; a2 += pw * aod[2 * n + 1];
+        a3 += pw * aoa[2 * n]; a4 += pw * aoa[2 * n + 1];
+    }
+    sp = block_sum(sp, sh); st = block_sum(st, sh); st2 = block_sum(st2, sh);
+    cr = block_sum(cr, sh); ci = block_sum(ci, sh);
+    a1 = block_sum(a1, sh); a2 = block_sum(a2, sh); a3 = block_sum(a3, sh); a4 = block_sum(a4, sh);
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_bins; k += blockDim.x)
+        pdp[(int64_t)r * n_bins + k] = acc[k] > 0.0 ? (float)(10.0 * log10(acc[k])) : -INFINITY;
+    if (threadIdx.x == 0) {
+        double* o = stats + (int64_t)r * SBR_NSTATS;
+        if (o1 == o0 || !(sp > 0.0)) {
+            o[0] = INFINITY; o[1] = INFINITY;
+            for (int k = 2; k < SBR_NSTATS; ++k) o[k] = NAN;
+        } else {
+            o[0] = -10.0 * log10(cr * cr + ci * ci);
+            o[1] = -10.0 * log10(sp);
+            double m1 = st / sp, m2 = st2 / sp, var = m2 - m1 * m1;
+            o[2] = sqrt(var > 0.0 ? var : 0.0);
+            o[3] = a1 / sp; o[4] = a2 / sp; o[5] = a3 / sp; o[6] = a4 / sp;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- capacity
+constexpr int kCapThreads = 256;
+
+__global__ void k_frob(const float2* __restrict__ H, int64_t per_f, double* __restrict__ qf) {
+    __shared__ double sh[33];
+    const float2* h = H + (int64_t)blockIdx.x * per_f;
+    double v = 0.0;
+    for (int64_t i = threadIdx.x; i < per_f; i += blockDim.x) {
+        float2 x = h[i];
+        v += (double)x.x * x.x + (double)x.y * x.y;
+    }
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) qf[blockIdx.x] = v;
+}
+
+__global__ void k_qbar(const double* __restrict__ qf, int32_t F, double* __restrict__ qbar) {
+    double s = 0.0;
+    for (int32_t f = 0; f < F; ++f) s += qf[f];
+    *qbar = s / F;
+}
+
+// one block per frequency; n = min(Nr, Nt) <= 64
+__global__ void __launch_bounds__(kCapThreads)
+k_capacity(const float2* __restrict__ H, int32_t Nr, int32_t Nt, const double* __restrict__ snr_lin,
+           int32_t n_snr, const double* __restrict__ qbar, double* __restrict__ ld) {
+    extern __shared__ unsigned char smem[];
+    const int n = Nr < Nt ? Nr : Nt;
+    float2* W = reinterpret_cast<float2*>(smem);                           // [n*n]
+    double2* A = reinterpret_cast<double2*>(smem + sizeof(float2) * ((n * n + 1) & ~1));  // [n*n]
+    __shared__ double s_ld;
+    __shared__ int s_bad;
+    const int f = blockIdx.x;
+    const float2* h = H + (int64_t)f * Nr * Nt;
+    // W[a][b] = sum_p H[a][p] conj(H[b][p])  (Nt >= Nr)  or  sum_q conj(H[q][a]) H[q][b]
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int a = e / n, b = e - a * n;
+        float re = 0.f, im = 0.f;
+        if (Nt >= Nr) {
+            for (int p = 0; p < Nt; ++p) {
+                float2 x = h[(int64_t)a * Nt + p], y = h[(int64_t)b * Nt + p];
+                re += x.x * y.x + x.y * y.y;
+                im += x.y * y.x - x.x * y.y;
+            }
+        } else {
+            for (int q = 0; q < Nr; ++q) {
+                float2 x = h[(int64_t)q * Nt + a], y = h[(int64_t)q * Nt + b];
+                re += x.x * y.x + x.y * y.y;
+                im += x.x * y.y - x.y * y.x;
+            }
+        }
+        W[e] = make_float2(re, im);
+    }
+    __syncthreads();
+    const double scale = (double)Nr * Nt / *qbar;
+    for (int si = 0; si < n_snr; ++si) {
+        const double c = snr_lin[si] / Nt * scale;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            int a = e / n, b = e - a * n;
+            A[e] = make_double2((a == b ? 1.0 : 0.0) + c * W[e].x, c * W[e].y);
+        }
+        if (threadIdx.x == 0) { s_ld = 0.0; s_bad = 0; }
+        __syncthreads();
+        for (int j = 0; j < n; ++j) {
+            if (threadIdx.x == 0) {
+                double d = A[j * n + j].x;
+                if (!(d > 0.0)) { s_bad = 1; d = 1.0; }
+                double l = sqrt(d);
+                A[j * n + j] = make_double2(l, 0.0);
+                s_ld += 2.0 * log(l);
+            }
+            __syncthreads();
+            const double inv = 1.0 / A[j * n + j].x;
+            for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+                double2 v = A[i * n + j];
+                A[i * n + j] = make_double2(v.x * inv, v.y * inv);
+            }
+            __syncthreads();
+            const int m = n - j - 1;
+            for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+                int i = j + 1 + e / m, k = j + 1 + e % m;
+                if (k > i) continue;
+                double2 lij = A[i * n + j], lkj = A[k * n + j];
+                double2 v = A[i * n + k];
+                // A[i][k] -= L[i][j] conj(L[k][j])
+                v.x -= lij.x * lkj.x + lij.y * lkj.y;
+                v.y -= lij.y * lkj.x - lij.x * lkj.y;
+                A[i * n + k] = v;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) ld[(int64_t)f * n_snr + si] = s_bad ? NAN : s_ld;
+        __syncthreads();
+    }
+}
+
+__global__ void k_cap_reduce(const double* __restrict__ ld, int32_t F, int32_t n_snr,
+                             double* __restrict__ C) {
+    int si = threadIdx.x;
+    if (si >= n_snr) return;
+    double s = 0.0;
+    for (int32_t f = 0; f < F; ++f) s += ld[(int64_t)f * n_snr + si];
+    C[si] = s / F / log(2.0);
+}
+
+}  // namespace
+
+sbr_status pdp_run(const sbr_path_list* pl, const float2* g, int32_t F, int32_t f_index, double fc,
+                   double bin_s, int32_t n_bins, float* pdp, double* stats, cudaStream_t s) {
+    if (pl->n_rx == 0) return SBR_OK;
+    size_t smem = sizeof(double) * (size_t)n_bins;
+    if (smem > 48 * 1024)
+        SBR_TRY_CUDA(cudaFuncSetAttribute(k_pdp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_pdp<<<pl->n_rx, kPdpThreads, smem, s>>>(pl->rx_off, pl->L, pl->aod, pl->aoa, g, F, f_index, fc,
+                                               bin_s, n_bins, pdp, stats);
+    SBR_TRY_CUDA(cudaGetLastError());
+    return SBR_OK;
+}
+
+size_t capacity_smem(int32_t Nr, int32_t Nt) {
+    int n = std::min(Nr, Nt);
+    return sizeof(float2) * (size_t)((n * n + 1) & ~1) + sizeof(double2) * (size_t)n * n;
+}
+
+sbr_status capacity_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,
+                        int32_t n_snr, double* C, cudaStream_t s) {
+    std::vector<double> lin(n_snr);
+    for (int i = 0; i < n_snr; ++i) lin[i] = std::pow(10.0, snr_db[i] / 10.0);
+    double *d_lin, *qf, *qbar, *ld;
+    SBR_TRY(dalloc_n(&d_lin, n_snr, s));
+    SBR_TRY(dalloc_n(&qf, F, s));
+    SBR_TRY(dalloc_n(&qbar, 1, s));
+    SBR_TRY(dalloc_n(&ld, (size_t)F * n_snr, s));
+    SBR_TRY_CUDA(cudaMemcpyAsync(d_lin, lin.data(), sizeof(double) * n_snr, cudaMemcpyHostToDevice, s));
+    k_frob<<<F, kCapThreads, 0, s>>>(H, (int64_t)Nr * Nt, qf);
+    k_qbar<<<1, 1, 0, s>>>(qf, F, qbar);
+    size_t smem = capacity_smem(Nr, Nt);
+    SBR_TRY_CUDA(cudaFuncSetAttribute(k_capacity, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_capacity<<<F, kCapThreads, smem, s>>>(H, Nr, Nt, d_lin, n_snr, qbar, ld);
+    k_cap_reduce<<<1, 32, 0, s>>>(ld, F, n_snr, C);
+    SBR_TRY_CUDA(cudaGetLastError());
+    // the host SNR table must outlive the copy
+    SBR_TRY_CUDA(cudaStreamSynchronize(s));
+    dfree(d_lin, s); dfree(qf, s); dfree(qbar, s); dfree(ld, s);
+    return SBR_OK;
+}
+
+}  // namespace sbr

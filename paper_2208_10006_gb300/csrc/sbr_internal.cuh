@@ -1,0 +1,217 @@
+// Internal declarations shared by the CUDA translation units of libsbr.
+// Not part of the public ABI (include/sbr.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sbr.h"
+
+namespace sbr {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define SBR_TRY_CUDA(expr)                                                             \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            ::sbr::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),   \
+                             __FILE__, __LINE__);                                      \
+            return SBR_ERR_CUDA;                                                       \
+        }                                                                              \
+    } while (0)
+
+#define SBR_TRY(expr)                      \
+    do {                                   \
+        sbr_status s_ = (expr);            \
+        if (s_ != SBR_OK) return s_;       \
+    } while (0)
+
+#define SBR_CHECK_ARG(cond, msg)                                          \
+    do {                                                                  \
+        if (!(cond)) {                                                    \
+            ::sbr::set_error("invalid argument: %s (%s)", msg, #cond);    \
+            return SBR_ERR_INVALID_ARG;                                   \
+        }                                                             \
+    } while (0)
+
+// device status word bits (written with atomicOr, read by synchronous calls)
+enum : uint32_t {
+    ST_CAPACITY = 1u,
+    ST_STACK = 2u,
+    ST_TIMEOUT = 4u,
+    ST_NUMERIC = 8u,
+};
+sbr_status status_from_bits(uint32_t bits);
+
+constexpr double kC0 = 299792458.0;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kKmax = SBR_KMAX;
+constexpr int kKeyWords = 2 + kKmax;  // rx, n_bounce, surface sequence
+
+// stream-ordered allocation helpers
+sbr_status dalloc(void** p, size_t bytes, cudaStream_t s);
+void dfree(void* p, cudaStream_t s);
+template <class T>
+sbr_status dalloc_n(T** p, size_t n, cudaStream_t s) {
+    return dalloc(reinterpret_cast<void**>(p), n * sizeof(T) + (n == 0 ? 16 : 0), s);
+}
+int sm_count();
+// enqueue a device-side store of a value (no host buffer outlives the call)
+sbr_status set_u64(unsigned long long* dst, unsigned long long v, cudaStream_t s);
+sbr_status set_f64(double* dst, double v, cudaStream_t s);
+
+// ---------------------------------------------------------------- icosahedron
+struct Ico {
+    double v[12][3];
+    int8_t e[30][2];
+    int8_t f[20][3];
+};
+Ico make_ico();
+
+// ---------------------------------------------------------------- sort / scan
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
+// keys/vals are sorted in place; tmp buffers are allocated on the stream.
+sbr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t s);
+// Exclusive prefix sum of n uint32 values, in place; *total (device, may be
+// NULL) receives the sum.
+sbr_status exclusive_scan_u32(uint32_t* data, int64_t n, uint32_t* total, cudaStream_t s);
+
+// ---------------------------------------------------------------- BVH
+// Node: 4 x float4 = child 0 box, child 1 box, refs. ref >= 0 internal node,
+// ref < 0 leaf holding sorted primitive ~ref.
+struct BvhNodes {
+    float4* nodes = nullptr;   // [n_nodes * 4]
+    int32_t* order = nullptr;  // [n] sorted position -> primitive index
+    int32_t n_nodes = 0;       // internal nodes (>= 1 when n >= 1)
+    float lo[3], hi[3];        // root bounds (host copy, valid after sync)
+    float* d_root = nullptr;   // [6] root bounds on the device
+};
+// Build over n primitives given by boxes [n*6] (lo xyz, hi xyz) on the device.
+// pad: absolute padding added to every child box (covers FP32 rounding).
+sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, BvhNodes* out,
+                      int32_t* d_depth, cudaStream_t s);
+void free_lbvh(BvhNodes* b, cudaStream_t s);
+
+}  // namespace sbr
+
+// ---------------------------------------------------------------- handles
+struct sbr_bvh {
+    int device = 0;
+    int64_t T = 0;
+    int32_t S = 0;
+    sbr::BvhNodes tree;
+    float4* tri_sorted = nullptr;   // [T*3]: v0 (w = surface id bits), v1 (w = face id bits), v2
+    double* nrm_sorted = nullptr;   // [T*3] unit normal (FP64), BVH order
+    float* tri = nullptr;           // [T*9] face-id order copy
+    int32_t* surf = nullptr;        // [T]
+    double* nrm = nullptr;          // [T*3] unit normal (FP64), face order
+    int32_t* s_off = nullptr;       // [S+1] CSR of faces per surface
+    int32_t* s_tri = nullptr;       // [T]   faces of each surface, ascending id
+    int32_t* d_depth = nullptr;     // [1]
+    cudaStream_t stream = nullptr;
+};
+
+struct TraceCountersDev {
+    unsigned long long queue[SBR_KMAX + 2];  // rays entering bounce b
+    unsigned long long work[SBR_KMAX + 2];   // work counters of the persistent grid
+    unsigned long long candidates;
+    unsigned long long keys;
+    unsigned long long fp64_segments;
+    unsigned int status;
+    unsigned int pad;
+};
+
+struct sbr_trace_result {
+    int device = 0;
+    sbr_trace_params params{};
+    int64_t R = 0;
+    int32_t n_rx = 0;
+    double* rx = nullptr;                   // [n_rx*3] own copy
+    double* d_alpha = nullptr;              // [1]
+    int32_t table_log2 = 0;
+    uint32_t* ht_state = nullptr;           // [cap]
+    uint32_t* ht_key = nullptr;             // [cap * kKeyWords]
+    unsigned long long* ht_val = nullptr;   // [cap]
+    TraceCountersDev* cnt = nullptr;
+    cudaStream_t stream = nullptr;
+};
+
+struct sbr_path_list {
+    int device = 0;
+    int64_t P = 0, n_keys = 0, n_invalid = 0;
+    int32_t n_rx = 0, K = 0, S = 0;
+    double tx[3];
+    double* rx_xyz = nullptr;   // [n_rx*3]
+    int32_t* rx = nullptr;      // [P]
+    int32_t* nb = nullptr;      // [P]
+    int32_t* surf = nullptr;    // [P*8]
+    int32_t* face = nullptr;    // [P*8]
+    double* pts = nullptr;      // [P*8*3]
+    double* L = nullptr;        // [P]
+    double* aod = nullptr;      // [P*2]
+    double* aoa = nullptr;      // [P*2]
+    uint32_t* ray = nullptr;    // [P]
+    float* dist = nullptr;      // [P]
+    float* jones = nullptr;     // [P*kJones] polarimetric transfer data (gains)
+    int32_t* rx_off = nullptr;  // [n_rx+1] paths of receiver r: [rx_off[r], rx_off[r+1])
+    int32_t* h_rx_off = nullptr;  // host copy
+    cudaStream_t stream = nullptr;
+};
+
+namespace sbr {
+// per-path polarimetric record for the gains kernel (FP32, from FP64 geometry):
+//   [0..1]   a1 (V): Tx theta-hat in the (s_1, p_in_1) basis      (LoS: [1, 0])
+//   [2..3]   a1 (H): Tx phi-hat in the same basis                  (LoS: [1, 0])
+//   [4..31]  M_k (k=1..7): 2x2 basis change (s_k, p_out_k) -> (s_k+1, p_in_k+1), row-major
+//   [32..33] c (V): Rx theta-hat . (s_m, p_out_m)                  (LoS: [1, 0])
+//   [34..35] c (H): Rx phi-hat . (s_m, p_out_m)                    (LoS: [1, 0])
+//   [36..43] cos(theta_i) per reflection
+constexpr int kJones = 48;
+
+// launchers implemented in the .cu files
+sbr_status launch_dirs(int32_t N, double* dirs, cudaStream_t s);
+sbr_status launch_alpha(int32_t N, double* alpha, cudaStream_t s);
+sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S, sbr_bvh* b,
+                     cudaStream_t s);
+sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s);
+sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list* pl,
+                     cudaStream_t s);
+sbr_status gains_run(const sbr_path_list* pl, const sbr_material* mats, int32_t S,
+                     const double* freqs, int32_t F, const float* gamma, const float* disp,
+                     int32_t pol, float2* g, cudaStream_t s);
+sbr_status synth_simt_run(const sbr_path_list* pl, const float2* g, const double* freqs, int32_t F,
+                          const double* tx_elem, int32_t Nt, const double* rx_elem, int32_t Nr,
+                          int32_t rx_index, bool fp64, float2* H, cudaStream_t s);
+sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* freqs, int32_t F,
+                        const double* tx_elem, int32_t Nt, const double* rx_elem, int32_t Nr,
+                        int32_t rx_index, float2* H, cudaStream_t s);
+sbr_status pdp_run(const sbr_path_list* pl, const float2* g, int32_t F, int32_t f_index, double fc,
+                   double bin_s, int32_t n_bins, float* pdp, double* stats, cudaStream_t s);
+sbr_status capacity_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,
+                        int32_t n_snr, double* C, cudaStream_t s);
+}  // namespace sbr
+
+// ---------------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+namespace sbr {
+struct d3 {
+    double x, y, z;
+};
+__host__ __device__ __forceinline__ d3 mk3(double x, double y, double z) { return d3{x, y, z}; }
+__device__ __forceinline__ d3 operator+(d3 a, d3 b) { return d3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ d3 operator-(d3 a, d3 b) { return d3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ d3 operator*(d3 a, double s) { return d3{a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ d3 cross(d3 a, d3 b) {
+    return d3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ double norm(d3 a) { return sqrt(dot(a, a)); }
+__device__ __forceinline__ d3 unit(d3 a) { return a * (1.0 / norm(a)); }
+__device__ __forceinline__ d3 ld3(const double* p) { return d3{p[0], p[1], p[2]}; }
+__device__ __forceinline__ void st3(double* p, d3 a) { p[0] = a.x; p[1] = a.y; p[2] = a.z; }
+}  // namespace sbr
+#endif

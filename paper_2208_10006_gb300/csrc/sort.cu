@@ -1,0 +1,200 @@
+// Device sort and scan primitives used by the BVH build (Morton order,
+// surface CSR) and by path compaction (key order, valid-path compaction).
+//
+// radix_sort_pairs: stable LSD radix sort, 8-bit digits. Each pass: a tile
+// histogram per block, an exclusive scan of the digit-major histogram, and a
+// stable scatter that ranks equal digits by (round, warp, lane) order.
+#include "sbr_internal.cuh"
+
+namespace sbr {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 8;
+constexpr int kSortTile = kSortThreads * kSortRounds;  // 2048 elements per block
+constexpr int kScanBlock = 1024;
+
+__global__ void k_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                       uint32_t* __restrict__ hist, int nblocks) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortRounds; ++r) {
+        int64_t i = base + r * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                          int shift, const uint32_t* __restrict__ hist, int nblocks) {
+    __shared__ uint32_t s_run[256];
+    __shared__ uint32_t s_warp[kSortThreads / 32][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    s_run[tid] = hist[(int64_t)tid * nblocks + blockIdx.x];
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < kSortRounds; ++r) {
+        for (int w = 0; w < kSortThreads / 32; ++w) s_warp[w][tid] = 0;
+        __syncthreads();
+        int64_t i = base + r * kSortThreads + tid;
+        bool valid = i < n;
+        uint32_t k = valid ? kin[i] : 0u, v = valid ? vin[i] : 0u;
+        uint32_t d = valid ? ((k >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & lt);
+        if (valid && rank == 0) s_warp[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t run = s_run[tid];
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                uint32_t c = s_warp[w][tid];
+                s_warp[w][tid] = run;
+                run += c;
+            }
+            s_run[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = s_warp[warp][d] + rank;
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// block-level exclusive scan of up to kScanBlock values
+__device__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* total) {
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t s_total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        uint32_t s = lane < nw ? warp_sums[lane] : 0u;
+        uint32_t si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += y;
+        }
+        if (lane < nw) warp_sums[lane] = si - s;
+        if (lane == nw - 1) s_total = si;
+    }
+    __syncthreads();
+    uint32_t res = warp_sums[warp] + incl - x;
+    if (total) *total = s_total;
+    __syncthreads();
+    return res;
+}
+
+__global__ void k_scan_blocks(uint32_t* data, int64_t n, uint32_t* block_sums) {
+    int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    uint32_t x = i < n ? data[i] : 0u;
+    uint32_t tot;
+    uint32_t ex = block_exclusive_scan(x, &tot);
+    if (i < n) data[i] = ex;
+    if (threadIdx.x == 0 && block_sums) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_add_offsets(uint32_t* data, int64_t n, const uint32_t* offs) {
+    int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    if (i < n) data[i] += offs[blockIdx.x];
+}
+
+__global__ void k_total(const uint32_t* scanned, const uint32_t* last_in, int64_t n,
+                        uint32_t* total) {
+    *total = n > 0 ? scanned[n - 1] + *last_in : 0u;
+}
+
+sbr_status scan_rec(uint32_t* data, int64_t n, cudaStream_t s) {
+    if (n <= 0) return SBR_OK;
+    int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    if (nb == 1) {
+        k_scan_blocks<<<1, kScanBlock, 0, s>>>(data, n, nullptr);
+        SBR_TRY_CUDA(cudaGetLastError());
+        return SBR_OK;
+    }
+    uint32_t* sums;
+    SBR_TRY(dalloc_n(&sums, nb, s));
+    k_scan_blocks<<<(unsigned)nb, kScanBlock, 0, s>>>(data, n, sums);
+    SBR_TRY_CUDA(cudaGetLastError());
+    sbr_status st = scan_rec(sums, nb, s);
+    if (st == SBR_OK) {
+        k_add_offsets<<<(unsigned)nb, kScanBlock, 0, s>>>(data, n, sums);
+        if (cudaGetLastError() != cudaSuccess) st = SBR_ERR_CUDA;
+    }
+    dfree(sums, s);
+    return st;
+}
+
+}  // namespace
+
+sbr_status exclusive_scan_u32(uint32_t* data, int64_t n, uint32_t* total, cudaStream_t s) {
+    if (n <= 0) {
+        if (total) SBR_TRY_CUDA(cudaMemsetAsync(total, 0, sizeof(uint32_t), s));
+        return SBR_OK;
+    }
+    uint32_t* last = nullptr;
+    if (total) {
+        SBR_TRY(dalloc_n(&last, 1, s));
+        SBR_TRY_CUDA(cudaMemcpyAsync(last, data + n - 1, sizeof(uint32_t),
+                                     cudaMemcpyDeviceToDevice, s));
+    }
+    sbr_status st = scan_rec(data, n, s);
+    if (st == SBR_OK && total) {
+        k_total<<<1, 1, 0, s>>>(data, last, n, total);
+        if (cudaGetLastError() != cudaSuccess) st = SBR_ERR_CUDA;
+    }
+    if (last) dfree(last, s);
+    return st;
+}
+
+sbr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t s) {
+    if (n <= 1 || bits <= 0) return SBR_OK;
+    if (n > 0x7fffffffLL) {
+        set_error("radix_sort_pairs: n too large");
+        return SBR_ERR_UNSUPPORTED;
+    }
+    int nblocks = (int)((n + kSortTile - 1) / kSortTile);
+    uint32_t *k2, *v2, *hist;
+    SBR_TRY(dalloc_n(&k2, n, s));
+    SBR_TRY(dalloc_n(&v2, n, s));
+    SBR_TRY(dalloc_n(&hist, (size_t)256 * nblocks, s));
+    uint32_t *ka = keys, *va = vals, *kb = k2, *vb = v2;
+    int passes = (bits + 7) / 8;
+    sbr_status st = SBR_OK;
+    for (int p = 0; p < passes && st == SBR_OK; ++p) {
+        k_hist<<<nblocks, kSortThreads, 0, s>>>(ka, n, 8 * p, hist, nblocks);
+        st = scan_rec(hist, (int64_t)256 * nblocks, s);
+        if (st != SBR_OK) break;
+        k_scatter<<<nblocks, kSortThreads, 0, s>>>(ka, va, kb, vb, n, 8 * p, hist, nblocks);
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("radix scatter launch failed");
+            st = SBR_ERR_CUDA;
+        }
+        uint32_t* t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+    }
+    if (st == SBR_OK && ka != keys) {
+        cudaMemcpyAsync(keys, ka, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    }
+    dfree(k2, s);
+    dfree(v2, s);
+    dfree(hist, s);
+    return st;
+}
+
+}  // namespace sbr

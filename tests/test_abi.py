@@ -1,0 +1,54 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/sbr.h (no GPU needed; no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sbr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sbr_[A-Za-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2208_10006_gb300 import build as b
+    b.build()
+    from paper_2208_10006_gb300 import _lib
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2208_10006_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == names
+
+
+def test_version_and_error_string_without_gpu(lib):
+    assert b"sm_103a" in lib.sbr_version()
+    assert lib.sbr_last_error() == b""
+
+
+def test_host_validation_rejects_bad_arguments_before_any_launch(lib):
+    from paper_2208_10006_gb300 import _lib
+    # N out of range: rejected on the host, no CUDA call made
+    assert lib.sbr_launch_dirs(0, None, None, None) == 1
+    assert b"N in" in lib.sbr_last_error()
+    out = ctypes.c_void_p()
+    assert lib.sbr_build_bvh(None, None, -1, 1, ctypes.byref(out), None) == 1
+    assert lib.sbr_trace(None, None, ctypes.byref(out), None) == 1
+    assert lib.sbr_capacity(None, 1, 1, 1, None, 1, None, None) == 1
+
+
+def test_library_is_built_for_sm103a_only():
+    from paper_2208_10006_gb300 import build as b
+    assert b.ARCH == "-gencode=arch=compute_103a,code=sm_103a"
+    assert all("-gencode" not in f or f == b.ARCH for f in b.flags())

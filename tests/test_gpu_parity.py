@@ -1,0 +1,203 @@
+"""CUDA path vs FP64 oracle, element by element, through the C ABI.
+
+Sizes are chosen so the oracle finishes in seconds while the scenes span
+many BVH levels, several bounces and ragged tails (ray counts that are not
+multiples of the warp or block size). Tolerances: path sets exact (edge-
+ambiguous exemptions counted), faces exact, L 1e-9 relative, gains 1e-4
+relative, PDP taps 0.01 dB.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from parity import assert_parity, compare_paths, to_numpy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+C0 = 299792458.0
+
+
+@pytest.fixture(scope="module")
+def sbr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_10006_gb300 import build as b
+    b.build()
+    import paper_2208_10006_gb300 as m
+    return m
+
+
+SCENES = {
+    "config1": lambda: scenes.config1(),
+    "config1_N37_K3": lambda: scenes.config1(N=37, K=3),
+    "corner": lambda: scenes.corner_reflector(),
+    "two_ray_H": lambda: scenes.two_ray(pol="H", N=97),
+    "shoebox": lambda: scenes.shoebox(),
+    "shoebox_K5": lambda: scenes.shoebox(N=61, K=5, sub=3),
+    "urban_small": lambda: scenes.config2(N=60, K=3, nx=2, ny=2, sub=3, ground_sub=6, rx_grid=6),
+    "urban_med": lambda: scenes.config2(N=150, K=4, nx=3, ny=3, sub=4, ground_sub=8, rx_grid=8),
+    "indoor_small": lambda: scenes.config3(N=40, K=3, F=8),
+}
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 50, 101])
+def test_launch_dirs_and_alpha(sbr, N):
+    d, a = sbr.launch_dirs(N)
+    ref = oracle.geodesic_dirs(N)
+    dd = d.cpu().numpy()
+    assert dd.shape == ref.shape
+    assert np.abs(dd - ref).max() < 4e-16
+    assert abs(float(a.cpu()[0]) - oracle.alpha(N)) <= 1e-14 * oracle.alpha(N)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_paths_and_gains_match_oracle(sbr, name):
+    sc = SCENES[name]()
+    r = sbr.run_scene(sc)
+    ex = to_numpy(r["export"])
+    g = r["g"].cpu().numpy()
+    orc = oracle.run(sc)
+    rep = compare_paths(ex, g, orc)
+    print(name, {k: v for k, v in rep.items() if k not in ("only_gpu", "only_orc")},
+          "gpu stats", r["stats"])
+    assert_parity(rep)
+    assert rep["n_common"] >= 1
+    # exemptions are rare: at most a few percent of the keys
+    assert rep["exempt"] <= max(2, 0.05 * rep["n_orc"]), rep
+    st = r["stats"]
+    assert st["ray_bounces"] == orc["counters"]["segments"]
+    assert st["rays"] == 10 * sc["N"] ** 2 + 2
+    info = r["paths"].info()
+    assert info["n_paths"] == len(ex["rx"])
+
+
+@pytest.mark.parametrize("name", ["config1", "urban_med", "indoor_small"])
+def test_pdp_and_stats_match_oracle(sbr, name):
+    sc = SCENES[name]()
+    r = sbr.run_scene(sc)
+    ex = to_numpy(r["export"])
+    orc = oracle.run(sc)
+    rep = compare_paths(ex, r["g"].cpu().numpy(), orc)
+    assert_parity(rep)
+    if rep["only_gpu"] or rep["only_orc"]:
+        pytest.skip("edge-ambiguous keys present; per-receiver sums differ by construction")
+    fc = float(sc["freqs"][len(sc["freqs"]) // 2])
+    fi = len(sc["freqs"]) // 2
+    n_bins = 2048
+    pdp, st = sbr.pdp_angles(r["paths"], r["g"], fi, fc, 1e-9, n_bins)
+    pdp, st = pdp.cpu().numpy(), st.cpu().numpy()
+    opdp, ost = oracle.pdp_stats(orc["paths"], orc["g"], fi, fc, 1e-9, n_bins, len(sc["rx"]))
+    empty = np.isneginf(opdp)
+    assert np.array_equal(empty, np.isneginf(pdp))
+    assert np.abs(pdp[~empty] - opdp[~empty]).max(initial=0) < 0.01
+    has = np.isfinite(ost[:, 1])
+    assert np.array_equal(has, np.isfinite(st[:, 1]))
+    assert np.abs(st[has, :2] - ost[has, :2]).max(initial=0) < 0.01          # dB
+    assert np.abs(st[has, 2] - ost[has, 2]).max(initial=0) < 1e-4 * max(ost[has, 2].max(initial=0), 1e-12)
+    assert np.abs(st[has, 3:] - ost[has, 3:]).max(initial=0) < 1e-4          # degrees
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 2e-5)])
+def test_synthesis_matches_oracle(sbr, precision, tol):
+    sc = scenes.config3(N=40, K=3, F=12)
+    r = sbr.run_scene(sc)
+    ex = to_numpy(r["export"])
+    d = r["dev"]
+    H = sbr.synthesize_H(r["paths"], r["g"], d["freqs"], d["tx_elem"], d["rx_elem"], 0,
+                         precision).cpu().numpy()
+    # the oracle synthesises from the GPU's own path list, so this isolates Eq. 13-14
+    paths = dict(rx=ex["rx"], nb=ex["nb"], pts=ex["pts"], L=ex["L"])
+    g_ref = oracle.gains(sc, dict(rx=ex["rx"], nb=ex["nb"], seq=ex["seq"], pts=ex["pts"], L=ex["L"]))
+    Ho = oracle.synth_H(paths, g_ref, sc["freqs"], sc["tx"], sc["rx"][0], sc["tx_elem"], sc["rx_elem"])
+    err = np.abs(H - Ho).max() / np.abs(Ho).max()
+    print("synthesis precision", precision, "max|dH|/max|H| =", err)
+    # gains are FP32 on the GPU (1e-6 relative), which bounds the FP64 form too
+    assert err < max(tol, 5e-6 if precision == 0 else tol)
+
+
+def test_synthesis_los_and_empty_receivers(sbr):
+    # free space: a single LoS path, spherical-wave response across the arrays
+    sc = dict(name="free", tri=np.zeros((0, 3, 3), np.float32), surface_id=np.zeros(0, np.int32),
+              materials=np.zeros((0, 3)), tx=np.array([0.0, 0.0, 1.0]),
+              rx=np.array([[3.0, 0.5, 1.2], [50.0, 0.0, 0.0]]), rx_valid=np.ones(2, bool),
+              freqs=np.array([27e9, 28e9, 29e9]), gamma_db_km=np.zeros(3, np.float32),
+              disp_deg_km=np.zeros(3, np.float32), N=30, K=1, pol="V",
+              tx_elem=scenes.upa_yz([0.0, 0.0, 1.0], 4, 4, 0.05),
+              rx_elem=scenes.ula_y([3.0, 0.5, 1.2], 6, 0.05))
+    r = sbr.run_scene(sc)
+    ex = to_numpy(r["export"])
+    assert ex["nb"].tolist() == [0, 0]
+    d = r["dev"]
+    for prec, tol in ((0, 1e-6), (1, 1e-5)):
+        H = sbr.synthesize_H(r["paths"], r["g"], d["freqs"], d["tx_elem"], d["rx_elem"], 0, prec)
+        H = H.cpu().numpy()
+        d0 = np.linalg.norm(sc["tx"] - sc["rx"][0])
+        dist = np.linalg.norm(sc["rx_elem"][:, None, :] - sc["tx_elem"][None, :, :], axis=2)
+        f = sc["freqs"]
+        ref = (C0 / (4 * np.pi * f * d0))[:, None, None] * np.exp(-2j * np.pi * f[:, None, None] * dist / C0)
+        assert np.abs(H - ref).max() < tol * np.abs(ref).max()
+
+
+def test_capacity_matches_oracle(sbr):
+    rng = np.random.default_rng(0)
+    for (F, Nr, Nt) in ((5, 4, 7), (3, 9, 5), (4, 64, 256), (2, 64, 64)):
+        H = (rng.normal(size=(F, Nr, Nt)) + 1j * rng.normal(size=(F, Nr, Nt))).astype(np.complex64)
+        Ht = torch.as_tensor(H, device="cuda")
+        snr = np.arange(0.0, 31.0, 5.0)
+        C = sbr.capacity(Ht, snr).cpu().numpy()
+        Co = oracle.capacity(H.astype(np.complex128), snr)
+        assert np.abs(C - Co).max() < 1e-5 * np.abs(Co).max(), (F, Nr, Nt, C, Co)
+
+
+def test_edge_cases(sbr):
+    # K = 0: only the LoS path survives dedup and refinement
+    r = sbr.run_scene(scenes.config1(N=23, K=0))
+    assert to_numpy(r["export"])["nb"].tolist() == [0]
+    # empty scene: LoS to every receiver, no reflections
+    sc = scenes.config1(N=11, K=3)
+    sc["tri"] = np.zeros((0, 3, 3), np.float32)
+    sc["surface_id"] = np.zeros(0, np.int32)
+    r = sbr.run_scene(sc)
+    assert to_numpy(r["export"])["nb"].tolist() == [0]
+    # single-triangle scene (one-leaf BVH)
+    sc = scenes.two_ray(N=64)
+    sc["tri"], sc["surface_id"] = sc["tri"][:1], sc["surface_id"][:1]
+    r = sbr.run_scene(sc)
+    orc = oracle.run(sc)
+    assert_parity(compare_paths(to_numpy(r["export"]), r["g"].cpu().numpy(), orc))
+    # receivers: none
+    d = sbr.scene_to_device(scenes.config1(N=9, K=2))
+    bvh = sbr.build_bvh(d["tri"], d["surface_id"], d["S"])
+    tr = sbr.trace(bvh, d["tx"], None, 9, 2)
+    pl = sbr.paths(tr, bvh)
+    assert pl.n == 0
+    # vanishing reception sphere
+    tr = sbr.trace(bvh, d["tx"], d["rx"], 9, 2, alpha=1e-12)
+    assert sbr.paths(tr, bvh).n == 0
+    # invalid arguments are rejected on the host
+    with pytest.raises(sbr.SbrError) as e:
+        sbr.trace(bvh, d["tx"], d["rx"], 9, 9)
+    assert e.value.status == 1
+    with pytest.raises(sbr.SbrError):
+        sbr.trace(bvh, [float("nan"), 0, 0], d["rx"], 9, 2)
+    # a dedup table too small reports SBR_ERR_CAPACITY instead of corrupting memory
+    sc = scenes.shoebox(N=40, K=3, n_rx=8)
+    d = sbr.scene_to_device(sc)
+    bvh = sbr.build_bvh(d["tri"], d["surface_id"], d["S"])
+    tr = sbr.trace(bvh, d["tx"], d["rx"], 40, 3, table_log2=4)
+    st = tr.stats(check=False)
+    assert st["status"] == 3
+    with pytest.raises(sbr.SbrError) as e:
+        sbr.paths(tr, bvh)
+    assert e.value.status == 3
+
+
+def test_bvh_shape(sbr):
+    for sc in (scenes.config1(), scenes.config2(N=10, K=1), scenes.config3(N=10, K=1, F=2)):
+        d = sbr.scene_to_device(sc)
+        info = sbr.build_bvh(d["tri"], d["surface_id"], d["S"]).info()
+        T = len(sc["tri"])
+        assert info["T"] == T and info["n_nodes"] == T - 1
+        assert 1 <= info["depth"] <= 64
