@@ -1,0 +1,431 @@
+#!/usr/bin/env python3
+"""Throughput of the SBR hot path on GB300 (one JSON line on stdout).
+
+Headline metric: Mray-bounces/s of one full pass of the hot path over the
+synthetic urban workload at 300 GHz (40 box buildings on an 8 x 5 grid,
+51,600 triangles, 10,000,002 geodesic rays, 6 reflections, 1024 receivers):
+BVH build, launch + trace + reception + dedup, effective paths with FP64
+image-method refinement, path gains and per-receiver PDP / statistics. A
+ray-bounce is one closest-hit query plus the reception test of one segment.
+
+The same line carries the H(f) synthesis throughput (H tensors/s) of the
+indoor MIMO workload (16x16 UPA to 64-ULA, 1024 subcarriers, H [1024, 64,
+256]) in each precision form, the live roofline of the dominant kernel
+(the bounce kernel), the oracle's CPU throughput on a bounded sample, an
+end-to-end number through host buffers, clocks sampled during the timed
+region and the number of library kernels launched.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun: every rank traces an independent Tx position of the
+same city (weak scaling, no collective on the data path); rank 0 prints.
+--impl reference times the FP64 CPU oracle on bounded samples of the same
+workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "Mray-bounces/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+RAY_REC_BYTES = 64      # one queued ray record (origin, direction, L, id, last surface)
+SEQ_BYTES = 4           # surface id appended per reflection
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- oracle baseline
+def oracle_sample(sc, n_rays: int, n_chunks: int = 16):
+    """Trace n_rays spread over the geodesic id range with the FP64 oracle."""
+    import oracle
+    R = 10 * sc["N"] ** 2 + 2
+    per = max(1, n_rays // n_chunks)
+    segs, t_total, cands = 0, 0.0, 0
+    for c in range(n_chunks):
+        b = (R * c) // n_chunks
+        t0 = time.perf_counter()
+        cc, fl, cnt = oracle.trace(sc, ray_begin=b, ray_end=min(R, b + per))
+        keys, nprod, allf = oracle.dedup(cc)
+        ref = oracle.refine(sc, keys)
+        paths = oracle.paths_of(sc, keys, ref)
+        oracle.gains(sc, paths)
+        t_total += time.perf_counter() - t0
+        segs += cnt["segments"]
+        cands += len(cc)
+    return segs, t_total, per * n_chunks
+
+
+def cpu_baseline(sc, budget_s: float = 15.0):
+    import oracle
+    oracle.build()
+    segs, t, rays = oracle_sample(sc, 64, 16)          # calibration
+    rate = segs / max(t, 1e-9)
+    n = int(min(200000, max(256, 64 * budget_s / max(t, 1e-3))))
+    segs, t, rays = oracle_sample(sc, n, 16)
+    return {"value": segs / t / 1e6, "unit": METRIC, "cores": oracle.nthreads_default(),
+            "kind": "oracle",
+            "sample": "%d rays in 16 evenly spaced id ranges of the %d-ray urban workload, "
+                      "trace + dedup + refine + gains (%.1f s, %d ray-bounces)" % (
+                          rays, 10 * sc["N"] ** 2 + 2, t, segs)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    sc = scenes.config2()
+    cfg = {"workload": "urban_300GHz_8x5_51600tri_N1000_R10000002_K6_1024rx",
+           "sample_per_step": "2048 rays in 16 spread id ranges, trace + dedup + refine + gains"}
+    for _ in range(args.warmup):
+        oracle_sample(sc, 2048, 16)
+    segs, t = 0, 0.0
+    for _ in range(args.steps):
+        s, tt, _ = oracle_sample(sc, 2048, 16)
+        segs += s
+        t += tt
+    value = segs / t / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.nthreads_default(),
+                             "kind": "oracle", "sample": cfg["sample_per_step"]},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def count_launches(fn):
+    """Kernels launched by one call of fn, from the CUDA profiler (kineto/CUPTI)."""
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+    try:
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        names = [e.name for e in prof.events() if e.device_type.name == "CUDA"]
+        ours = [n for n in names if "sbr" in n]
+        return len(ours), sorted(set(ours))
+    except Exception as e:  # profiler unavailable: no claim
+        return None, [repr(e)]
+
+
+def run_gpu(args):
+    import torch
+    import paper_2208_10006_gb300 as sbr
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2208_10006_gb300 import build as b
+    if rank == 0:
+        b.build()
+    if world > 1:
+        torch.distributed.barrier()
+    sbr._lib.load()
+    peaks, peak_src = load_peaks()
+
+    crossings = [(4, 2), (3, 2), (5, 2), (4, 1), (4, 3), (2, 2), (6, 2), (3, 1)]
+    N_w = {"urban": 1000, "urban_n400": 400}[args.workload]
+    sc = scenes.config2(N=N_w, crossing=crossings[rank % len(crossings)])
+    d = sbr.scene_to_device(sc)
+    N, K = sc["N"], sc["K"]
+    _, a = sbr.launch_dirs(N, with_dirs=False)
+    alpha = float(a.cpu()[0])
+    fc = float(sc["freqs"][0])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step(dd):
+        bvh = sbr.build_bvh(dd["tri"], dd["surface_id"], dd["S"])
+        tr = sbr.trace(bvh, dd["tx"], dd["rx"], N, K, alpha=alpha, timing=True)
+        pl = sbr.paths(tr, bvh)
+        g = sbr.path_gains(pl, dd["mats"], dd["freqs"], dd["gamma"], dd["disp"], dd["pol"])
+        pdp, st = sbr.pdp_angles(pl, g, 0, fc, 1e-9, 2048)
+        stats = tr.stats()
+        return bvh, tr, pl, g, pdp, st, stats
+
+    for _ in range(args.warmup):
+        step(d)
+    torch.cuda.synchronize()
+    n_launch, kernel_names = count_launches(lambda: step(d))
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times, rb, bounce_ms, bounce_bytes = [], 0, 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = step(d)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stats = out[-1]
+        rb += stats["ray_bounces"]
+        q = stats["queue"]
+        for bb in range(K + 1):
+            bounce_ms += stats["bounce_ms"][bb]
+            reads = q[bb] * RAY_REC_BYTES if bb > 0 else 0
+            writes = q[bb + 1] * (RAY_REC_BYTES + SEQ_BYTES) if bb < K else 0
+            bounce_bytes += reads + writes
+        del out
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_total = sum(times) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_total, float(rb)], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+        t_total, rb_all = float(mx[0]), float(tt[1])
+    else:
+        rb_all = float(rb)
+    value = rb_all / t_total / 1e6
+
+    # e2e: the same step through the public API from pinned host buffers, with the
+    # inputs copied in and the path list, gains, PDP and statistics copied out
+    host = {k: v.cpu().pin_memory() for k, v in d.items() if isinstance(v, torch.Tensor)}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    e2e_t, e2e_rb, d2h = 0.0, 0, 0
+    for _ in range(0 if args.no_e2e else max(1, args.steps // 2)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dd = dict(d)
+        for k, v in host.items():
+            dd[k] = v.to(dev, non_blocking=True)
+        bvh, tr, pl, g, pdp, st, stats = step(dd)
+        ex = pl.export()
+        outs = [v.to("cpu", non_blocking=True) for v in ex.values()]
+        outs += [g.to("cpu", non_blocking=True), pdp.to("cpu", non_blocking=True),
+                 st.to("cpu", non_blocking=True)]
+        e1.record()
+        e1.synchronize()
+        e2e_t += e0.elapsed_time(e1) / 1e3
+        e2e_rb += stats["ray_bounces"]
+        d2h = sum(v.numel() * v.element_size() for v in outs)
+    e2e_value = e2e_rb / e2e_t / 1e6 * world if e2e_t > 0 else None
+
+    synth = None
+    if not args.no_synth and rank == 0:
+        synth = bench_synthesis(sbr, torch, flush, peaks, peak_src, args)
+
+    if rank != 0:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(scenes.config2(), budget_s=args.cpu_budget)
+
+    achieved = bounce_bytes / (bounce_ms / 1e3) / 1e9
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
+    roof = {"kernel": "k_trace_bounce", "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+            "peak_source": peak_src,
+            "algorithmic_bytes": "64 B ray record read (bounces >= 1) + 68 B record and surface "
+                                 "id written per surviving ray, per launch",
+            "avg_launch_ms": bounce_ms / (args.steps * (K + 1)),
+            "kernel_share_of_step": bounce_ms / sum(times)}
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "urban_300GHz_8x5_51600tri_N%d_R%d_K6_1024rx" % (N, 10 * N * N + 2),
+                   "rays": 10 * N * N + 2, "max_bounces": K, "triangles": int(len(sc["tri"])),
+                   "receivers": int(len(sc["rx"])), "ray_bounces_per_step": rb // args.steps,
+                   "step": "build_bvh+trace+paths+gains+pdp", "l2": "flushed (256 MB write) "
+                   "between timed steps; ray queues (640 MB) exceed L2",
+                   "parallelism": "dp%d (independent Tx per rank)" % world},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": None if n_launch is None else n_launch * args.steps,
+        "launches_per_step": n_launch,
+        "clocks": clk,
+        "synthesis": synth,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def bench_synthesis(sbr, torch, flush, peaks, peak_src, args):
+    """H(f) tensors/s on the indoor MIMO workload for each precision form."""
+    sc = scenes.config3()
+    d = sbr.scene_to_device(sc)
+    bvh = sbr.build_bvh(d["tri"], d["surface_id"], d["S"])
+    tr = sbr.trace(bvh, d["tx"], d["rx"], sc["N"], sc["K"])
+    pl = sbr.paths(tr, bvh)
+    g = sbr.path_gains(pl, d["mats"], d["freqs"], d["gamma"], d["disp"], d["pol"])
+    F, Nr, Nt = len(sc["freqs"]), len(sc["rx_elem"]), len(sc["tx_elem"])
+    P = pl.n
+    out = {"metric": "H(f) tensors/s", "workload":
+           "indoor_100GHz_5736tri_N632_K4_UPA16x16_ULA64_F1024", "paths": P,
+           "H_shape": [F, Nr, Nt], "forms": {}}
+    H = torch.empty((F, Nr, Nt), dtype=torch.complex64, device=d["freqs"].device)
+    reps = {sbr.SYNTH_BF16X3: max(5, args.steps), sbr.SYNTH_FP32: 3, sbr.SYNTH_FP64: 1}
+    names = {sbr.SYNTH_BF16X3: "bf16x3_tcgen05", sbr.SYNTH_FP32: "fp32_simt", sbr.SYNTH_FP64: "fp64_simt"}
+    Href = None
+    for prec in (sbr.SYNTH_FP64, sbr.SYNTH_FP32, sbr.SYNTH_BF16X3):
+        try:
+            sbr.synthesize_H(pl, g, d["freqs"], d["tx_elem"], d["rx_elem"], 0, prec, out=H)
+        except sbr.SbrError as e:
+            out["forms"][names[prec]] = {"unavailable": str(e)}
+            continue
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps[prec]):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sbr.synthesize_H(pl, g, d["freqs"], d["tx_elem"], d["rx_elem"], 0, prec, out=H)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        t = statistics.median(ts)
+        Hc = H.clone()
+        if prec == sbr.SYNTH_FP64:
+            Href = Hc
+        err = None
+        if Href is not None:
+            err = float((Hc - Href).abs().max() / Href.abs().max())
+        bytes_ = 8.0 * F * Nr * Nt
+        flops = 8.0 * F * Nr * Nt * P
+        entry = {"value": 1.0 / t, "unit": "H tensors/s", "ms": t * 1e3,
+                 "achieved_GBps": bytes_ / t / 1e9, "achieved_TFLOPs": flops / t / 1e12,
+                 "max_abs_err_vs_fp64_over_max": err}
+        if prec == sbr.SYNTH_BF16X3:
+            hbm = float(peaks.get("hbm_gbs", 6800.0))
+            tc = float(peaks.get("bf16_tflops", 1900.0))
+            t_roof = max(bytes_ / (hbm * 1e9), 3 * flops / (tc * 1e12))
+            entry["roofline"] = {"bound": "hbm" if bytes_ / (hbm * 1e9) >= 3 * flops / (tc * 1e12)
+                                 else "tensor", "frac": t_roof / t, "peak_source": peak_src}
+        out["forms"][names[prec]] = entry
+    best = [v for v in out["forms"].values() if "value" in v]
+    out["value"] = max(v["value"] for v in best) if best else None
+    out["unit"] = "H tensors/s"
+    C = sbr.capacity(H, sc["snr_db"])
+    out["capacity_bits_per_s_per_hz"] = [float(x) for x in C.cpu()]
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__,
+                                 formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-synth", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="urban", choices=["urban", "urban_n400"],
+                    help="urban: the headline workload; urban_n400: 1.6M rays (profiling case)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

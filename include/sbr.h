@@ -144,16 +144,22 @@ typedef struct {
     int32_t reserved;
 } sbr_trace_params;
 
+/* sbr_trace_params.flags */
+#define SBR_TRACE_TIMING 1u  /* record CUDA events around each bounce launch (bounce_ms) */
+
 typedef struct {
     int64_t rays;
     int64_t ray_bounces;        /* segments traced: a ray with k reflections adds k+1 */
     int64_t candidates;         /* receptions before dedup                          */
     int64_t keys;               /* distinct (rx, surface sequence) keys             */
-    int64_t fp64_segments;      /* segments re-decided by the FP64 traversal        */
+    int64_t fp64_segments;      /* segments re-traversed entirely in FP64           */
+    int64_t fp64_tests;         /* faces re-decided by an exact FP64 test           */
     int64_t queue[SBR_KMAX + 2];/* rays alive at the start of each bounce           */
     double alpha;
     int32_t status;             /* sbr_status of the device-side checks             */
     int32_t table_log2;
+    float bounce_ms[SBR_KMAX + 1]; /* device time of each bounce launch (SBR_TRACE_TIMING) */
+    int32_t reserved;
 } sbr_trace_counters;
 
 sbr_status sbr_trace(const sbr_bvh* bvh, const sbr_trace_params* params, sbr_trace_result** out,

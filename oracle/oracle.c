@@ -104,26 +104,32 @@ static void ico_topology(double V[12][3], int edges[30][2], int faces[20][3]) {
 
 int64_t orc_geodesic_count(int32_t N) { return 10 * (int64_t)N * N + 2; }
 
-/* out[R*3]; returns R, or -1 if N < 1 */
-int64_t orc_geodesic_dirs(int32_t N, double* out) {
+/* Directions of rays [r0, r1) in enumeration order into out[(r1-r0)*3].
+ * Returns the total count R, or -1 if N < 1. */
+static int64_t geodesic_range(int32_t N, int64_t r0, int64_t r1, double* out) {
     if (N < 1) return -1;
     double V[12][3]; int E[30][2], Fc[20][3];
     ico_vertices(V); ico_topology(V, E, Fc);
     int64_t r = 0;
-    for (int k = 0; k < 12; ++k) st3(out + 3 * r++, unit(ld3(V[k])));
+#define ORC_EMIT(expr) do { if (r >= r0 && r < r1) st3(out + 3 * (r - r0), unit(expr)); ++r; } while (0)
+    for (int k = 0; k < 12; ++k) ORC_EMIT(ld3(V[k]));
     for (int e = 0; e < 30; ++e) {
         v3 a = ld3(V[E[e][0]]), b = ld3(V[E[e][1]]);
-        for (int k = 1; k <= N - 1; ++k)
-            st3(out + 3 * r++, unit(add(a, scl(sub(b, a), (double)k / N))));
+        for (int k = 1; k <= N - 1; ++k) ORC_EMIT(add(a, scl(sub(b, a), (double)k / N)));
     }
     for (int f = 0; f < 20; ++f) {
         v3 a = ld3(V[Fc[f][0]]), b = ld3(V[Fc[f][1]]), c = ld3(V[Fc[f][2]]);
         for (int i = 1; i <= N - 2; ++i)
             for (int j = 1; i + j <= N - 1; ++j)
-                st3(out + 3 * r++, unit(add(a, add(scl(sub(b, a), (double)i / N),
-                                                   scl(sub(c, a), (double)j / N)))));
+                ORC_EMIT(add(a, add(scl(sub(b, a), (double)i / N), scl(sub(c, a), (double)j / N))));
     }
+#undef ORC_EMIT
     return r;
+}
+
+/* out[R*3]; returns R, or -1 if N < 1 */
+int64_t orc_geodesic_dirs(int32_t N, double* out) {
+    return geodesic_range(N, 0, orc_geodesic_count(N), out);
 }
 
 static double angle_between(v3 a, v3 b) { return atan2(norm(cross(a, b)), dot(a, b)); }
@@ -132,7 +138,10 @@ static double angle_between(v3 a, v3 b) { return atan2(norm(cross(a, b)), dot(a,
  * Reading: the largest angle between two directions joined by an edge of
  * the subdivided icosahedron's sub-triangles. */
 double orc_geodesic_alpha(int32_t N) {
+    static int32_t cached_N = 0;
+    static double cached = 0.0;
     if (N < 1) return -1.0;
+    if (N == cached_N) return cached;
     double V[12][3]; int E[30][2], Fc[20][3];
     ico_vertices(V); ico_topology(V, E, Fc);
     double best = 0.0;
@@ -150,6 +159,8 @@ double orc_geodesic_alpha(int32_t N) {
                 if (t3 > best) best = t3;
             }
     }
+    cached_N = N;
+    cached = best;
     return best;
 }
 
@@ -248,7 +259,8 @@ typedef struct {
     v3 tx;
     const double* rx; int32_t n_rx;
     int32_t N, K; double alpha, eps;
-    const double* dirs; /* all R directions */
+    const double* dirs; /* directions of rays [dir_base, ...) */
+    int64_t dir_base;
     int64_t r0, r1;
     orc_cand* buf; int64_t n, cap;
     uint8_t* flags; /* [r1 - r0], relative to the global ray_begin */
@@ -323,7 +335,7 @@ static int segment_flags(const scene_t* sc, v3 o, v3 d, int skip, int64_t best, 
 
 static void trace_ray(trace_job* j, int64_t ray) {
     const scene_t* sc = j->sc;
-    v3 o = j->tx, d = ld3(j->dirs + 3 * ray);
+    v3 o = j->tx, d = ld3(j->dirs + 3 * (ray - j->dir_base));
     double L = 0.0;
     int prev = -1, nb = 0;
     int32_t seq[ORC_KMAX];
@@ -397,9 +409,10 @@ int64_t orc_trace(const float* tri, const int32_t* surf, int64_t T, int32_t S,
     if (ray_end > R) return -1;
     scene_t sc;
     if (scene_init(&sc, tri, surf, T, S) != 0) { scene_free(&sc); return -2; }
-    double* dirs = malloc(sizeof(double) * 3 * R);
+    int64_t nr_all = ray_end - ray_begin;
+    double* dirs = malloc(sizeof(double) * 3 * (nr_all > 0 ? nr_all : 1));
     if (!dirs) { scene_free(&sc); return -3; }
-    orc_geodesic_dirs(N, dirs);
+    geodesic_range(N, ray_begin, ray_end, dirs);
     if (alpha <= 0) alpha = orc_geodesic_alpha(N);
     if (nthreads < 1) nthreads = 1;
     int64_t nr = ray_end - ray_begin;
@@ -409,7 +422,7 @@ int64_t orc_trace(const float* tri, const int32_t* surf, int64_t T, int32_t S,
     for (int i = 0; i < nthreads; ++i) {
         trace_job* j = &jobs[i];
         j->sc = &sc; j->tx = ld3(tx); j->rx = rx; j->n_rx = n_rx; j->N = N; j->K = K;
-        j->alpha = alpha; j->eps = eps; j->dirs = dirs;
+        j->alpha = alpha; j->eps = eps; j->dirs = dirs; j->dir_base = ray_begin;
         j->r0 = ray_begin + nr * i / nthreads; j->r1 = ray_begin + nr * (i + 1) / nthreads;
         j->flags = ray_flags; j->flag_base = ray_begin;
         pthread_create(&th[i], NULL, trace_worker, j);
@@ -448,11 +461,9 @@ int32_t orc_trace_one(const float* tri, const int32_t* surf, int64_t T, int32_t 
     if (N < 1 || K < 0 || K > ORC_KMAX || ray < 0 || ray >= orc_geodesic_count(N)) return -1;
     scene_t sc;
     if (scene_init(&sc, tri, surf, T, S) != 0) { scene_free(&sc); return -2; }
-    int64_t R = orc_geodesic_count(N);
-    double* dirs = malloc(sizeof(double) * 3 * R);
-    orc_geodesic_dirs(N, dirs);
-    v3 o = ld3(tx), d = ld3(dirs + 3 * ray);
-    free(dirs);
+    double dir[3];
+    geodesic_range(N, ray, ray + 1, dir);
+    v3 o = ld3(tx), d = ld3(dir);
     double L = 0; int prev = -1; int32_t ns = 0;
     for (int b = 0; b <= K; ++b) {
         double bt;

@@ -71,11 +71,11 @@ def version() -> str:
     return _L().sbr_version().decode()
 
 
-def launch_dirs(N: int, with_alpha: bool = True, stream=None):
+def launch_dirs(N: int, with_alpha: bool = True, with_dirs: bool = True, stream=None):
     """Geodesic launch directions [R, 3] (float64) and alpha (Sec. II-A.1)."""
     dev = _dev()
     R = 10 * N * N + 2
-    d = torch.empty((R, 3), dtype=torch.float64, device=dev)
+    d = torch.empty((R, 3), dtype=torch.float64, device=dev) if with_dirs else None
     a = torch.empty(1, dtype=torch.float64, device=dev) if with_alpha else None
     _check(_L().sbr_launch_dirs(N, _ptr(d), _ptr(a), _stream(stream)))
     return d, a
@@ -134,8 +134,9 @@ class TraceResult:
         if check:
             _check(st)
         return dict(rays=c.rays, ray_bounces=c.ray_bounces, candidates=c.candidates, keys=c.keys,
-                    fp64_segments=c.fp64_segments, queue=list(c.queue), alpha=c.alpha,
-                    status=c.status, table_log2=c.table_log2)
+                    fp64_segments=c.fp64_segments, fp64_tests=c.fp64_tests,
+                    queue=list(c.queue), alpha=c.alpha,
+                    status=c.status, table_log2=c.table_log2, bounce_ms=list(c.bounce_ms))
 
     def free(self):
         if self._h is not None:
@@ -150,7 +151,7 @@ class TraceResult:
 
 
 def trace(bvh: BVH, tx, rx: torch.Tensor, N: int, K: int, alpha: float = 0.0, table_log2: int = 0,
-          stream=None) -> TraceResult:
+          timing: bool = False, stream=None) -> TraceResult:
     """Shoot and bounce. tx: 3 floats; rx: float64 [n_rx, 3] CUDA."""
     p = _lib.TraceParams()
     for k in range(3):
@@ -164,6 +165,7 @@ def trace(bvh: BVH, tx, rx: torch.Tensor, N: int, K: int, alpha: float = 0.0, ta
     p.max_bounces = int(K)
     p.table_log2 = int(table_log2)
     p.alpha = float(alpha)
+    p.flags = _lib.TRACE_TIMING if timing else 0
     h = C.c_void_p()
     _check(_L().sbr_trace(bvh.handle, C.byref(p), C.byref(h), _stream(stream)))
     return TraceResult(h, p)

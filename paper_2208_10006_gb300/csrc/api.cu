@@ -225,9 +225,16 @@ sbr_status sbr_trace_stats(const sbr_trace_result* tr, sbr_trace_counters* out) 
     out->candidates = (int64_t)c.candidates;
     out->keys = (int64_t)c.keys;
     out->fp64_segments = (int64_t)c.fp64_segments;
+    out->fp64_tests = (int64_t)c.fp64_tests;
     for (int k = 0; k < SBR_KMAX + 2; ++k) out->queue[k] = (int64_t)c.queue[k];
     out->alpha = alpha;
     out->table_log2 = tr->table_log2;
+    if (tr->ev[0]) {
+        for (int k = 0; k <= tr->params.max_bounces; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, tr->ev[k], tr->ev[k + 1]) == cudaSuccess) out->bounce_ms[k] = ms;
+        }
+    }
     out->status = (int32_t)status_from_bits(c.status);
     return (sbr_status)out->status;
 }
@@ -237,6 +244,8 @@ void sbr_trace_free(sbr_trace_result* tr) {
     cudaStream_t s = tr->stream;
     dfree(tr->rx, s); dfree(tr->d_alpha, s); dfree(tr->ht_state, s); dfree(tr->ht_key, s);
     dfree(tr->ht_val, s); dfree(tr->cnt, s);
+    for (auto& e : tr->ev)
+        if (e) cudaEventDestroy(e);
     delete tr;
 }
 

@@ -1,6 +1,6 @@
 // Complex path gain g_n(f) (Eq. 1, 3, 6-10), one thread per (path, frequency).
 //
-// Per reflection k (FP32 complex, geometry from the FP64 refinement):
+// Per reflection k (FP64 complex):
 //   eta = eps_r - j sigma / (2 pi f eps0)                         (lossy dielectric)
 //   G_TE = (cos - sqrt(eta - sin^2)) / (cos + sqrt(eta - sin^2))
 //   G_TM = (eta cos - sqrt(eta - sin^2)) / (eta cos + sqrt(eta - sin^2))
@@ -9,6 +9,9 @@
 // real 2x2 change to the next reflection's basis; then the Rx projection, the
 // Friis amplitude c / (4 pi f L) (Eq. 3), absorption 10^(-gamma L / 20000)
 // (Eq. 9) and the dispersion phase -phi (pi/180) L / 1000 (Eq. 10).
+// FP64 because the co-polar projection of a multi-bounce field can cancel to
+// 1e-5 of the field, below which FP32 rounding alone exceeds a 1e-4 relative
+// error on the gain; the work is P x F, negligible next to the trace.
 #include <algorithm>
 
 #include "sbr_internal.cuh"
@@ -16,79 +19,81 @@
 namespace sbr {
 namespace {
 
-struct cf {
-    float re, im;
+struct cd {
+    double re, im;
 };
-__device__ __forceinline__ cf cmul(cf a, cf b) { return cf{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-__device__ __forceinline__ cf cadd(cf a, cf b) { return cf{a.re + b.re, a.im + b.im}; }
-__device__ __forceinline__ cf csub(cf a, cf b) { return cf{a.re - b.re, a.im - b.im}; }
-__device__ __forceinline__ cf cdiv(cf a, cf b) {
-    float s = fabsf(b.re) + fabsf(b.im);
-    float br = b.re / s, bi = b.im / s;
-    float d = br * br + bi * bi;
-    cf a2{a.re / s, a.im / s};
-    return cf{(a2.re * br + a2.im * bi) / d, (a2.im * br - a2.re * bi) / d};
+__device__ __forceinline__ cd cmul(cd a, cd b) { return cd{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ cd cadd(cd a, cd b) { return cd{a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cd csub(cd a, cd b) { return cd{a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cd cscale(cd a, double s) { return cd{a.re * s, a.im * s}; }
+__device__ __forceinline__ cd cdiv(cd a, cd b) {
+    double s = fabs(b.re) + fabs(b.im);
+    double br = b.re / s, bi = b.im / s;
+    double d = br * br + bi * bi;
+    double ar = a.re / s, ai = a.im / s;
+    return cd{(ar * br + ai * bi) / d, (ai * br - ar * bi) / d};
 }
 // principal square root
-__device__ __forceinline__ cf csqrt_(cf z) {
-    float r = hypotf(z.re, z.im);
-    float x = sqrtf(0.5f * (r + z.re));
-    float y = sqrtf(fmaxf(0.5f * (r - z.re), 0.f));
-    return cf{x, z.im < 0.f ? -y : y};
+__device__ __forceinline__ cd csqrt_(cd z) {
+    double r = hypot(z.re, z.im);
+    double x = sqrt(0.5 * (r + z.re));
+    double y = sqrt(fmax(0.5 * (r - z.re), 0.0));
+    return cd{x, z.im < 0.0 ? -y : y};
 }
-__device__ __forceinline__ cf cscale(cf a, float s) { return cf{a.re * s, a.im * s}; }
 
 __global__ void k_gains(int64_t P, int32_t F, const int32_t* __restrict__ nb,
                         const int32_t* __restrict__ surf, const double* __restrict__ L,
-                        const float* __restrict__ jones, const sbr_material* __restrict__ mats,
+                        const double* __restrict__ jones, const sbr_material* __restrict__ mats,
                         int32_t S, const double* __restrict__ freqs, const float* __restrict__ gamma,
-                        const float* __restrict__ disp, int pol, float2* __restrict__ g,
-                        unsigned int* __restrict__ status) {
+                        const float* __restrict__ disp, int pol, float2* __restrict__ g) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= P * F) return;
     int64_t p = t / F;
     int32_t fi = (int32_t)(t - p * F);
     const double f = freqs[fi];
-    const float* J = jones + p * kJones;
+    const double* J = jones + p * kJones;
     const int m = nb[p];
     const int pb = pol == SBR_POL_V ? 0 : 2;
-    cf b0{__ldg(J + pb), 0.f}, b1{__ldg(J + pb + 1), 0.f};
-    const float eps2_scale = (float)(1.0 / (2.0 * kPi * f * kEps0));
-    const float kr = (float)(4.0 * kPi * f / kC0);
+    cd b0{J[pb], 0.0}, b1{J[pb + 1], 0.0};
+    const double eps2_scale = 1.0 / (2.0 * kPi * f * kEps0);
+    const double kr = 4.0 * kPi * f / kC0;
     for (int k = 0; k < m; ++k) {
         int s = surf[p * kKmax + k];
-        if (s < 0 || s >= S) { atomicOr(status, (unsigned)ST_NUMERIC); return; }
+        if (s < 0 || s >= S) {  // not reachable: the host checks S covers every surface id
+            g[t] = make_float2(NAN, NAN);
+            return;
+        }
         const sbr_material mt = mats[s];
-        float c = __ldg(J + 36 + k);
-        float s2 = 1.f - c * c;
-        cf eta{(float)mt.eps_r, -(float)mt.sigma_s_per_m * eps2_scale};
-        cf root = csqrt_(cf{eta.re - s2, eta.im});
-        cf cc{c, 0.f};
-        cf te = cdiv(csub(cc, root), cadd(cc, root));
-        cf ec = cscale(eta, c);
-        cf tm = cdiv(csub(ec, root), cadd(ec, root));
-        float gk = kr * (float)mt.rough_m * c;
-        float rho = expf(-0.5f * gk * gk);
+        double c = J[36 + k];
+        double s2 = 1.0 - c * c;
+        cd eta{mt.eps_r, -mt.sigma_s_per_m * eps2_scale};
+        cd root = csqrt_(cd{eta.re - s2, eta.im});
+        cd cc{c, 0.0};
+        cd te = cdiv(csub(cc, root), cadd(cc, root));
+        cd ec = cscale(eta, c);
+        cd tm = cdiv(csub(ec, root), cadd(ec, root));
+        double gk = kr * mt.rough_m * c;
+        double rho = exp(-0.5 * gk * gk);
         b0 = cscale(cmul(te, b0), rho);
         b1 = cscale(cmul(tm, b1), rho);
         if (k + 1 < m) {
-            const float* M = J + 4 + 4 * k;
-            cf n0 = cadd(cscale(b0, M[0]), cscale(b1, M[1]));
-            cf n1 = cadd(cscale(b0, M[2]), cscale(b1, M[3]));
+            const double* M = J + 4 + 4 * k;
+            cd n0 = cadd(cscale(b0, M[0]), cscale(b1, M[1]));
+            cd n1 = cadd(cscale(b0, M[2]), cscale(b1, M[3]));
             b0 = n0;
             b1 = n1;
         }
     }
-    const float* cv = J + 32 + pb;
-    cf proj = cadd(cscale(b0, cv[0]), cscale(b1, cv[1]));
+    const double* cv = J + 32 + pb;
+    cd proj = cadd(cscale(b0, cv[0]), cscale(b1, cv[1]));
     const double Lp = L[p];
-    float amp = (float)(kC0 / (4.0 * kPi * f * Lp));
-    float att = gamma ? exp10f(-gamma[fi] * (float)Lp * (1.0f / 20000.0f)) : 1.f;
-    float ph = disp ? -disp[fi] * (float)(kPi / 180.0 * Lp / 1000.0) : 0.f;
-    float sn, cs;
-    sincosf(ph, &sn, &cs);
-    cf v = cmul(cscale(cf{cs, sn}, amp * att), proj);
-    g[t] = make_float2(v.re, v.im);
+    double amp = kC0 / (4.0 * kPi * f * Lp);
+    double att = gamma ? exp10(-(double)gamma[fi] * Lp / 20000.0) : 1.0;
+    double ph = disp ? -(double)disp[fi] * (kPi / 180.0) * Lp / 1000.0 : 0.0;
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    cd v = cmul(cscale(cd{cs, sn}, amp * att), proj);
+    g[t] = make_float2((float)v.re, (float)v.im);
 }
 
 }  // namespace
@@ -98,13 +103,9 @@ sbr_status gains_run(const sbr_path_list* pl, const sbr_material* mats, int32_t 
                      int32_t pol, float2* g, cudaStream_t s) {
     int64_t n = pl->P * (int64_t)F;
     if (n == 0) return SBR_OK;
-    unsigned int* status;
-    SBR_TRY(dalloc_n(&status, 1, s));
-    SBR_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
     k_gains<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pl->P, F, pl->nb, pl->surf, pl->L, pl->jones,
-                                                          mats, S, freqs, gamma, disp, pol, g, status);
+                                                          mats, S, freqs, gamma, disp, pol, g);
     SBR_TRY_CUDA(cudaGetLastError());
-    dfree(status, s);
     return SBR_OK;
 }
 

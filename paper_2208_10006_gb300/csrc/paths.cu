@@ -113,7 +113,7 @@ struct RefineArgs {
     double* aoa_o;
     uint32_t* ray_o;
     float* dist_o;
-    float* jones_o;
+    double* jones_o;
 };
 
 __global__ void k_refine(const __grid_constant__ RefineArgs a) {
@@ -180,10 +180,10 @@ __global__ void k_refine(const __grid_constant__ RefineArgs a) {
     a.ray_o[i] = (uint32_t)(v & 0xffffffffull);
     a.dist_o[i] = __uint_as_float((uint32_t)(v >> 32));
     // polarimetric transfer record (see kJones in sbr_internal.cuh)
-    float* J = a.jones_o + i * kJones;
-    for (int k = 0; k < kJones; ++k) J[k] = 0.f;
+    double* J = a.jones_o + i * kJones;
+    for (int k = 0; k < kJones; ++k) J[k] = 0.0;
     if (m == 0) {
-        J[0] = 1.f; J[2] = 1.f; J[32] = 1.f; J[34] = 1.f;
+        J[0] = 1.0; J[2] = 1.0; J[32] = 1.0; J[34] = 1.0;
         return;
     }
     d3 sv_prev{}, pout_prev{};
@@ -192,24 +192,24 @@ __global__ void k_refine(const __grid_constant__ RefineArgs a) {
         double c = fabs(dot(din, nn[k]));
         d3 sv = s_vector(din, nn[k]);
         d3 pin = cross(sv, din), pout = cross(sv, dout);
-        J[36 + k - 1] = (float)c;
+        J[36 + k - 1] = c;
         if (k == 1) {
             d3 d0 = din;
             d3 eV = pol_vec(d0, SBR_POL_V), eH = pol_vec(d0, SBR_POL_H);
-            J[0] = (float)dot(eV, sv); J[1] = (float)dot(eV, pin);
-            J[2] = (float)dot(eH, sv); J[3] = (float)dot(eH, pin);
+            J[0] = dot(eV, sv); J[1] = dot(eV, pin);
+            J[2] = dot(eH, sv); J[3] = dot(eH, pin);
         } else {
-            float* M = J + 4 + 4 * (k - 2);
-            M[0] = (float)dot(sv, sv_prev);  M[1] = (float)dot(sv, pout_prev);
-            M[2] = (float)dot(pin, sv_prev); M[3] = (float)dot(pin, pout_prev);
+            double* M = J + 4 + 4 * (k - 2);
+            M[0] = dot(sv, sv_prev);  M[1] = dot(sv, pout_prev);
+            M[2] = dot(pin, sv_prev); M[3] = dot(pin, pout_prev);
         }
         sv_prev = sv;
         pout_prev = pout;
     }
     d3 dl = unit(P[m + 1] - P[m]);
     d3 rV = pol_vec(dl, SBR_POL_V), rH = pol_vec(dl, SBR_POL_H);
-    J[32] = (float)dot(rV, sv_prev); J[33] = (float)dot(rV, pout_prev);
-    J[34] = (float)dot(rH, sv_prev); J[35] = (float)dot(rH, pout_prev);
+    J[32] = dot(rV, sv_prev); J[33] = dot(rV, pout_prev);
+    J[34] = dot(rH, sv_prev); J[35] = dot(rH, pout_prev);
 }
 
 template <class T>

@@ -121,6 +121,7 @@ struct TraceCountersDev {
     unsigned long long candidates;
     unsigned long long keys;
     unsigned long long fp64_segments;
+    unsigned long long fp64_tests;
     unsigned int status;
     unsigned int pad;
 };
@@ -137,6 +138,7 @@ struct sbr_trace_result {
     uint32_t* ht_key = nullptr;             // [cap * kKeyWords]
     unsigned long long* ht_val = nullptr;   // [cap]
     TraceCountersDev* cnt = nullptr;
+    cudaEvent_t ev[SBR_KMAX + 2] = {};     // bounce boundaries when timing is requested
     cudaStream_t stream = nullptr;
 };
 
@@ -156,14 +158,14 @@ struct sbr_path_list {
     double* aoa = nullptr;      // [P*2]
     uint32_t* ray = nullptr;    // [P]
     float* dist = nullptr;      // [P]
-    float* jones = nullptr;     // [P*kJones] polarimetric transfer data (gains)
+    double* jones = nullptr;    // [P*kJones] polarimetric transfer data (gains)
     int32_t* rx_off = nullptr;  // [n_rx+1] paths of receiver r: [rx_off[r], rx_off[r+1])
     int32_t* h_rx_off = nullptr;  // host copy
     cudaStream_t stream = nullptr;
 };
 
 namespace sbr {
-// per-path polarimetric record for the gains kernel (FP32, from FP64 geometry):
+// per-path polarimetric record for the gains kernel (FP64):
 //   [0..1]   a1 (V): Tx theta-hat in the (s_1, p_in_1) basis      (LoS: [1, 0])
 //   [2..3]   a1 (H): Tx phi-hat in the same basis                  (LoS: [1, 0])
 //   [4..31]  M_k (k=1..7): 2x2 basis change (s_k, p_out_k) -> (s_k+1, p_in_k+1), row-major

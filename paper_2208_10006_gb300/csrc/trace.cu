@@ -111,16 +111,34 @@ __device__ __forceinline__ bool box_hit(float lx, float ly, float lz, float hx, 
     return tmin <= tmx;
 }
 
+// Certification of the FP32 decisions. For every tested face the edge
+// functions U, V, W of the watertight test carry a rounding-error bound
+//   errE = 8 eps max(|Cx By| + |Cy Bx|, |Ax Cy| + |Ay Cx|, |Bx Ay| + |By Ax|)
+//        + 4 eps (|o|_inf + t_scale) (perimeter of the sheared triangle)
+// (eps = 2^-24): the first term covers the arithmetic of the test, the second
+// the rounding of the FP64 ray to FP32. A face is a certain miss if some edge
+// function is below -errE, a certain hit if all exceed +errE and t is clearly
+// positive. Everything in between, and hits of different surfaces whose t
+// agree within kTie, go to a short list that is re-decided in FP64 with the
+// exact rule; only a full list falls back to a complete FP64 traversal.
+constexpr int kUnc = 6;
+constexpr float kEps32 = 5.9604645e-8f;
+constexpr float kTie = 1e-5f;
+
 struct Trav {
-    float best_t;
+    float best_t, lim, omax;
     int32_t best_j, best_face, best_surf;
-    int best_small;      // barycentrics of the best hit below kCert
-    float second_t;      // hits of a surface other than the best at the time
-    float nm_t1;         // nearest near miss ...
-    int32_t nm_s1;       // ... and its surface
-    float nm_t2;         // nearest near miss of a surface other than nm_s1
-    bool unsure;
+    int nu;
+    bool overflow;
+    int32_t unc[kUnc];
 };
+
+__device__ __forceinline__ void push_unc(Trav& tv, int32_t j) {
+    for (int k = 0; k < tv.nu; ++k)
+        if (tv.unc[k] == j) return;
+    if (tv.nu < kUnc) tv.unc[tv.nu++] = j;
+    else tv.overflow = true;
+}
 
 __device__ __forceinline__ void tri_test32(const float4* __restrict__ tris, int32_t j, int prev,
                                            const Ray32& r, Trav& tv) {
@@ -137,72 +155,62 @@ __device__ __forceinline__ void tri_test32(const float4* __restrict__ tris, int3
     Bx = fmaf(-r.Sx, Bz, Bx); By = fmaf(-r.Sy, Bz, By);
     Cx = fmaf(-r.Sx, Cz, Cx); Cy = fmaf(-r.Sy, Cz, Cy);
     float U = Cx * By - Cy * Bx, V = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
-    if (U == 0.f || V == 0.f || W == 0.f) {  // exact edge: recompute in FP64 (Woop et al.)
-        U = (float)((double)Cx * By - (double)Cy * Bx);
-        V = (float)((double)Ax * Cy - (double)Ay * Cx);
-        W = (float)((double)Bx * Ay - (double)By * Ax);
-    }
     float det = U + V + W;
-    float asum = fabsf(U) + fabsf(V) + fabsf(W);
-    if (asum == 0.f) return;
-    if (!(fabsf(det) > kCert * asum)) {
-        // grazing or parallel: t is ill-conditioned; be unsure if the face could matter
-        tv.unsure = true;
+    float sg = det >= 0.f ? 1.f : -1.f;
+    float mn = fminf(fminf(sg * U, sg * V), sg * W);  // min of the orientation-adjusted values
+    float pU = fabsf(Cx * By) + fabsf(Cy * Bx), pV = fabsf(Ax * Cy) + fabsf(Ay * Cx),
+          pW = fabsf(Bx * Ay) + fabsf(By * Ax);
+    float per = fabsf(Bx - Cx) + fabsf(By - Cy) + fabsf(Cx - Ax) + fabsf(Cy - Ay) +
+                fabsf(Ax - Bx) + fabsf(Ay - By);
+    float zs = fmaxf(fabsf(Az), fmaxf(fabsf(Bz), fabsf(Cz)));
+    float errE = 8.f * kEps32 * fmaxf(pU, fmaxf(pV, pW)) + 4.f * kEps32 * (tv.omax + zs) * per;
+    if (mn < -errE) return;  // certainly outside one edge
+    float adet = fabsf(det);
+    if (!(adet > 3.f * errE)) {  // t is not reliable: let FP64 decide
+        push_unc(tv, j);
         return;
     }
     Az *= r.Sz; Bz *= r.Sz; Cz *= r.Sz;
-    float Tn = U * Az + V * Bz + W * Cz;
-    float inv = 1.0f / det;
-    float t = Tn * inv;
-    if (!(t > 0.f)) return;
-    float lim = tv.best_t * (1.0f + 4.0f * kCert);
-    if (!(t <= lim)) return;
-    float u = U * inv, v = V * inv, w = W * inv;
-    float m = fminf(u, fminf(v, w));
-    if (m >= 0.f) {
+    float t = (U * Az + V * Bz + W * Cz) / det;
+    float tiny = 1e-5f * (tv.omax + 1.f);
+    if (t < -tiny || t > tv.lim) return;
+    if (mn > errE && t > tiny) {
         int face = __float_as_int(b.w);
-        int small = (u < kCert) + (v < kCert) + (w < kCert);
+        float tol = kTie * fmaxf(t, tv.best_t) + 16.f * kEps32 * (tv.omax + fmaxf(t, tv.best_t));
+        if (tv.best_j >= 0 && surf != tv.best_surf && fabsf(t - tv.best_t) <= tol) {
+            push_unc(tv, j);
+            push_unc(tv, tv.best_j);
+        }
         if (t < tv.best_t || (t == tv.best_t && face < tv.best_face)) {
-            if (tv.best_j >= 0 && tv.best_surf != surf) tv.second_t = fminf(tv.second_t, tv.best_t);
             tv.best_t = t; tv.best_j = j; tv.best_face = face; tv.best_surf = surf;
-            tv.best_small = small;
-        } else if (surf != tv.best_surf) {
-            tv.second_t = fminf(tv.second_t, t);
+            tv.lim = t * (1.f + 4.f * kTie) + tiny;
         }
-    } else if (m > -kCert) {
-        if (t < tv.nm_t1) {
-            if (surf != tv.nm_s1) tv.nm_t2 = fminf(tv.nm_t2, tv.nm_t1);
-            tv.nm_t1 = t; tv.nm_s1 = surf;
-        } else if (surf != tv.nm_s1) {
-            tv.nm_t2 = fminf(tv.nm_t2, t);
-        }
+    } else {
+        push_unc(tv, j);
     }
 }
 
-// FP32 closest hit. Returns the sorted triangle index or -1; sets unsure when
-// an FP64 re-decision is needed.
-__device__ int32_t traverse32(const TraceArgs& a, const Ray32& r, int prev, float& t_out,
-                              bool& unsure, int* stack) {
-    Trav tv;
-    tv.best_t = INFINITY; tv.best_j = -1; tv.best_face = 0x7fffffff; tv.best_surf = -2;
-    tv.best_small = 0; tv.second_t = INFINITY; tv.nm_t1 = INFINITY; tv.nm_s1 = -3;
-    tv.nm_t2 = INFINITY; tv.unsure = false;
+// FP32 closest hit. Returns the sorted triangle index of the certain best
+// (or -1) and the list of faces that FP64 must re-decide.
+__device__ int32_t traverse32(const TraceArgs& a, const Ray32& r, int prev, Trav& tv, int* stack) {
+    tv.best_t = INFINITY; tv.lim = INFINITY; tv.best_j = -1; tv.best_face = 0x7fffffff;
+    tv.best_surf = -2; tv.nu = 0; tv.overflow = false;
+    tv.omax = fmaxf(fabsf(r.o.x), fmaxf(fabsf(r.o.y), fabsf(r.o.z)));
     int sp = 0;
     int32_t node = 0;
     for (;;) {
         const float4* nd = a.nodes + 4 * (int64_t)node;
         float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
         int32_t r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
-        float lim = tv.best_t * (1.0f + 4.0f * kCert);
         float tn0, tn1;
-        bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, lim, tn0);
-        bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, lim, tn1) && r1 != r0;
+        bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, tv.lim, tn0);
+        bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, tv.lim, tn1) && r1 != r0;
         if (h0 && r0 < 0) { tri_test32(a.tris, ~r0, prev, r, tv); h0 = false; }
         if (h1 && r1 < 0) { tri_test32(a.tris, ~r1, prev, r, tv); h1 = false; }
         if (h0 && h1) {
             int32_t nearn = tn0 <= tn1 ? r0 : r1, farn = tn0 <= tn1 ? r1 : r0;
             if (sp < kStack) stack[sp++] = farn;
-            else { atomicOr(&a.cnt->status, (unsigned)ST_STACK); unsure = true; t_out = tv.best_t; return tv.best_j; }
+            else { atomicOr(&a.cnt->status, (unsigned)ST_STACK); tv.overflow = true; break; }
             node = nearn;
         } else if (h0) {
             node = r0;
@@ -213,18 +221,6 @@ __device__ int32_t traverse32(const TraceArgs& a, const Ray32& r, int prev, floa
             node = stack[--sp];
         }
     }
-    float lim = tv.best_t * (1.0f + 4.0f * kCert);
-    bool u = tv.unsure;
-    if (tv.second_t <= lim) u = true;
-    if (tv.nm_t1 <= lim && tv.nm_s1 != tv.best_surf) u = true;
-    if (tv.nm_t2 <= lim) u = true;
-    if (tv.best_j >= 0) {
-        if (tv.best_small >= 2) u = true;
-        // near one edge: fine only if a coplanar face of the same surface lies across it
-        if (tv.best_small == 1 && !(tv.nm_s1 == tv.best_surf && tv.nm_t1 <= lim)) u = true;
-    }
-    unsure = u;
-    t_out = tv.best_t;
     return tv.best_j;
 }
 
@@ -459,12 +455,27 @@ k_trace_bounce(const __grid_constant__ TraceArgs a, const __grid_constant__ Ico 
             int32_t j = -1;
             double t64 = INFINITY;
             if (a.T > 0) {
-                float t32;
-                bool unsure;
-                j = traverse32(a, r, prev, t32, unsure, stack);
-                if (unsure) {
+                Trav tv;
+                j = traverse32(a, r, prev, tv, stack);
+                if (tv.overflow) {
                     j = traverse64(a, o, d, prev, t64, stack);
                     atomicAdd(&a.cnt->fp64_segments, 1ull);
+                } else if (tv.nu > 0) {
+                    // exact rule over the certain best and the uncertain faces
+                    int32_t bj = -1, bface = 0x7fffffff;
+                    double bt = INFINITY;
+                    for (int k = -1; k < tv.nu; ++k) {
+                        int32_t c = k < 0 ? tv.best_j : tv.unc[k];
+                        if (c < 0) continue;
+                        double tc;
+                        int face = __float_as_int(__ldg(a.tris + 3 * c + 1).w);
+                        if (mt64(a.tris, c, o, d, tc) && (tc < bt || (tc == bt && face < bface))) {
+                            bt = tc; bj = c; bface = face;
+                        }
+                    }
+                    j = bj;
+                    t64 = bt;
+                    atomicAdd(&a.cnt->fp64_tests, (unsigned long long)(tv.nu + (tv.best_j >= 0)));
                 } else if (j >= 0) {
                     d3 n = ld3(a.nrm + 3 * (int64_t)j);
                     float4 v0 = __ldg(a.tris + 3 * j);
@@ -581,6 +592,11 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     a.cnt = tr->cnt;
     Ico ico = make_ico();
     int grid = trace_grid();
+    const bool timing = (p.flags & SBR_TRACE_TIMING) != 0;
+    if (timing) {
+        for (int k = 0; k <= K + 1; ++k) SBR_TRY_CUDA(cudaEventCreate(&tr->ev[k]));
+        SBR_TRY_CUDA(cudaEventRecord(tr->ev[0], s));
+    }
     for (int bnc = 0; bnc <= K; ++bnc) {
         a.bounce = bnc;
         a.qin = (bnc & 1) ? q0 : q1;
@@ -590,6 +606,7 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
         a.work = &tr->cnt->work[bnc];
         k_trace_bounce<<<grid, kTraceThreads, 0, s>>>(a, ico);
         SBR_TRY_CUDA(cudaGetLastError());
+        if (timing) SBR_TRY_CUDA(cudaEventRecord(tr->ev[bnc + 1], s));
     }
     if (q0) dfree(q0, s);
     if (q1) dfree(q1, s);

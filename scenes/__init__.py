@@ -171,7 +171,7 @@ def config1(N: int = 100, K: int = 3):
 
 
 def config2(N: int = 1000, K: int = 6, nx: int = 8, ny: int = 5, sub: int = 11,
-            ground_sub: int = 40, rx_grid: int = 32, seed: int = 2):
+            ground_sub: int = 40, rx_grid: int = 32, seed: int = 2, crossing=None):
     """Urban grid at 300 GHz (seed 2).
 
     nx x ny cells on a 60 m pitch, cell (i, j) centred at (30+60i, 30+60j). Draw
@@ -185,7 +185,8 @@ def config2(N: int = 1000, K: int = 6, nx: int = 8, ny: int = 5, sub: int = 11,
     Tx at the street crossing (60*(nx//2), 60*(ny//2), 25), i.e. (240,120,25);
     rx_grid x rx_grid receivers on a 2 m pitch centred below it at z=1.5 (receivers inside a footprint get
     rx_valid False). F=1 at 300 GHz; gamma = 5 dB/km (synthetic stand-in for the
-    line-by-line value of Eq. 9)."""
+    line-by-line value of Eq. 9). `crossing` = (i, j) moves the Tx and the
+    receiver grid to the street crossing (60 i, 60 j); the buildings stay."""
     rng = np.random.default_rng(seed)
     xmax = -20 + 60 * nx + 40
     ymax = -20 + 60 * ny + 40
@@ -213,6 +214,8 @@ def config2(N: int = 1000, K: int = 6, nx: int = 8, ny: int = 5, sub: int = 11,
         mats[s, 2] = rng.uniform(0.05e-3, 0.3e-3)
     tri, sid = _assemble(groups)
     cx0, cy0 = 60.0 * (nx // 2), 60.0 * (ny // 2)   # (240, 120) for the 8 x 5 grid
+    if crossing is not None:
+        cx0, cy0 = 60.0 * crossing[0], 60.0 * crossing[1]
     tx = (cx0, cy0, 25.0)
     g = (np.arange(rx_grid) - (rx_grid - 1) / 2) * 2.0
     rx = np.array([(cx0 + gx, cy0 + gy, 1.5) for gx in g for gy in g])
