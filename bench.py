@@ -140,6 +140,7 @@ def oracle_sample(sc, n_rays: int, n_chunks: int = 16):
 def cpu_baseline(sc, budget_s: float = 15.0):
     import oracle
     oracle.build()
+    oracle.alpha(sc["N"])                               # one-off table, cached by the oracle
     segs, t, rays = oracle_sample(sc, 64, 16)          # calibration
     rate = segs / max(t, 1e-9)
     n = int(min(200000, max(256, 64 * budget_s / max(t, 1e-3))))
@@ -181,21 +182,6 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-def count_launches(fn):
-    """Kernels launched by one call of fn, from the CUDA profiler (kineto/CUPTI)."""
-    import torch
-    from torch.profiler import ProfilerActivity, profile
-    try:
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            fn()
-            torch.cuda.synchronize()
-        names = [e.name for e in prof.events() if e.device_type.name == "CUDA"]
-        ours = [n for n in names if "sbr" in n]
-        return len(ours), sorted(set(ours))
-    except Exception as e:  # profiler unavailable: no claim
-        return None, [repr(e)]
-
-
 def run_gpu(args):
     import torch
     import paper_2208_10006_gb300 as sbr
@@ -236,7 +222,10 @@ def run_gpu(args):
     for _ in range(args.warmup):
         step(d)
     torch.cuda.synchronize()
-    n_launch, kernel_names = count_launches(lambda: step(d))
+    c0 = sbr.launch_count()
+    step(d)
+    torch.cuda.synchronize()
+    n_launch = sbr.launch_count() - c0   # library kernels in one step (counted at each launch site)
 
     clocks = ClockSampler(torch.cuda.current_device())
     if world > 1:

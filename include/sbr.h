@@ -67,6 +67,10 @@ const char* sbr_last_error(void);
 /* Library version string. */
 const char* sbr_version(void);
 
+/* Number of CUDA kernels this library has launched in the calling process
+ * (all devices, all threads); for accounting, e.g. launches per pipeline step. */
+int64_t sbr_launch_count(void);
+
 typedef struct sbr_bvh sbr_bvh;
 typedef struct sbr_trace_result sbr_trace_result;
 typedef struct sbr_path_list sbr_path_list;

@@ -71,6 +71,11 @@ def version() -> str:
     return _L().sbr_version().decode()
 
 
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(_L().sbr_launch_count())
+
+
 def launch_dirs(N: int, with_alpha: bool = True, with_dirs: bool = True, stream=None):
     """Geodesic launch directions [R, 3] (float64) and alpha (Sec. II-A.1)."""
     dev = _dev()

@@ -17,7 +17,7 @@ POL_V, POL_H = 0, 1
 SYNTH_FP64, SYNTH_FP32, SYNTH_BF16X3 = 0, 1, 2
 TRACE_TIMING = 1
 
-EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_dirs", "sbr_build_bvh", "sbr_bvh_free",
+EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_count", "sbr_launch_dirs", "sbr_build_bvh", "sbr_bvh_free",
            "sbr_bvh_query", "sbr_trace", "sbr_trace_stats", "sbr_trace_free", "sbr_paths",
            "sbr_path_query", "sbr_path_export", "sbr_path_list_free", "sbr_path_gains",
            "sbr_synthesize_H", "sbr_pdp_angles", "sbr_capacity"]
@@ -67,6 +67,8 @@ def load() -> C.CDLL:
     L.sbr_last_error.argtypes = []
     L.sbr_version.restype = C.c_char_p
     L.sbr_version.argtypes = []
+    L.sbr_launch_count.restype = i64
+    L.sbr_launch_count.argtypes = []
     L.sbr_launch_dirs.restype = st
     L.sbr_launch_dirs.argtypes = [i32, p, p, p]
     L.sbr_build_bvh.restype = st

@@ -1,5 +1,6 @@
 // C ABI of libsbr (include/sbr.h): host-side validation, handle lifetime and
 // dispatch to the kernels of the other translation units.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -11,6 +12,9 @@
 namespace sbr {
 
 static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -55,13 +59,13 @@ __global__ void k_set_f64(double* dst, double v) { *dst = v; }
 }  // namespace
 
 sbr_status set_u64(unsigned long long* dst, unsigned long long v, cudaStream_t s) {
-    k_set_u64<<<1, 1, 0, s>>>(dst, v);
+    ::sbr::note_launch(), k_set_u64<<<1, 1, 0, s>>>(dst, v);
     SBR_TRY_CUDA(cudaGetLastError());
     return SBR_OK;
 }
 
 sbr_status set_f64(double* dst, double v, cudaStream_t s) {
-    k_set_f64<<<1, 1, 0, s>>>(dst, v);
+    ::sbr::note_launch(), k_set_f64<<<1, 1, 0, s>>>(dst, v);
     SBR_TRY_CUDA(cudaGetLastError());
     return SBR_OK;
 }
@@ -93,6 +97,8 @@ extern "C" {
 const char* sbr_last_error(void) { return g_err; }
 
 const char* sbr_version(void) { return "sbr-gb300 0.1 (sm_103a)"; }
+
+int64_t sbr_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
 sbr_status sbr_launch_dirs(int32_t N, double* dirs, double* alpha, void* stream) {
     clear_error();

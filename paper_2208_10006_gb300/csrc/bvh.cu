@@ -292,14 +292,14 @@ sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, BvhNodes*
     SBR_TRY(dalloc_n(&out->d_root, 6, s));
     SBR_TRY_CUDA(cudaMemsetAsync(flag, 0, nn * sizeof(int32_t), s));
     SBR_TRY_CUDA(cudaMemsetAsync(d_depth, 0, sizeof(int32_t), s));
-    k_bounds<<<1, 1024, 0, s>>>(prim_box, n, bnd);
-    k_morton<<<blocks_for(n), kThreads, 0, s>>>(prim_box, n, bnd, code, idx);
+    ::sbr::note_launch(), k_bounds<<<1, 1024, 0, s>>>(prim_box, n, bnd);
+    ::sbr::note_launch(), k_morton<<<blocks_for(n), kThreads, 0, s>>>(prim_box, n, bnd, code, idx);
     SBR_TRY_CUDA(cudaGetLastError());
     SBR_TRY(radix_sort_pairs(code, idx, n, 30, s));
-    if (n > 1) k_karras<<<blocks_for(n - 1), kThreads, 0, s>>>(code, n, left, right, pint, pleaf);
-    k_refit<<<blocks_for(n), kThreads, 0, s>>>(prim_box, (const int32_t*)idx, n, left, right, pint,
+    if (n > 1) ::sbr::note_launch(), k_karras<<<blocks_for(n - 1), kThreads, 0, s>>>(code, n, left, right, pint, pleaf);
+    ::sbr::note_launch(), k_refit<<<blocks_for(n), kThreads, 0, s>>>(prim_box, (const int32_t*)idx, n, left, right, pint,
                                                pleaf, flag, lbox, ibox, d_depth);
-    k_emit<<<blocks_for(nn), kThreads, 0, s>>>(n, left, right, lbox, ibox, pad_rel, out->nodes,
+    ::sbr::note_launch(), k_emit<<<blocks_for(nn), kThreads, 0, s>>>(n, left, right, lbox, ibox, pad_rel, out->nodes,
                                                out->d_root);
     SBR_TRY_CUDA(cudaGetLastError());
     out->order = reinterpret_cast<int32_t*>(idx);
@@ -340,23 +340,23 @@ sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S
     SBR_TRY_CUDA(cudaMemcpyAsync(b->surf, surf, sizeof(int32_t) * T, cudaMemcpyDeviceToDevice, s));
     float* box;
     SBR_TRY(dalloc_n(&box, 6 * T, s));
-    k_tri_boxes<<<blocks_for(T), kThreads, 0, s>>>(b->tri, T, box);
-    k_tri_normals<<<blocks_for(T), kThreads, 0, s>>>(b->tri, T, b->nrm, status);
+    ::sbr::note_launch(), k_tri_boxes<<<blocks_for(T), kThreads, 0, s>>>(b->tri, T, box);
+    ::sbr::note_launch(), k_tri_normals<<<blocks_for(T), kThreads, 0, s>>>(b->tri, T, b->nrm, status);
     SBR_TRY_CUDA(cudaGetLastError());
     // relative box padding: 2^-20 of (|x| + 1) covers FP32 ray/box rounding
     SBR_TRY(build_lbvh(box, T, 1.0f / (1 << 20), &b->tree, b->d_depth, s));
-    k_tri_pack<<<blocks_for(T), kThreads, 0, s>>>(b->tri, b->surf, b->nrm, b->tree.order, T,
+    ::sbr::note_launch(), k_tri_pack<<<blocks_for(T), kThreads, 0, s>>>(b->tri, b->surf, b->nrm, b->tree.order, T,
                                                   b->tri_sorted, b->nrm_sorted);
     // faces per surface, ascending face id (stable sort on the surface id)
     uint32_t *key, *val;
     SBR_TRY(dalloc_n(&key, T, s));
     val = reinterpret_cast<uint32_t*>(b->s_tri);
-    k_copy_surf<<<blocks_for(T), kThreads, 0, s>>>(b->surf, T, S, key, val, status);
+    ::sbr::note_launch(), k_copy_surf<<<blocks_for(T), kThreads, 0, s>>>(b->surf, T, S, key, val, status);
     SBR_TRY_CUDA(cudaGetLastError());
     int bits = 1;
     while (bits < 31 && ((int64_t)1 << bits) < (int64_t)S) ++bits;
     SBR_TRY(radix_sort_pairs(key, val, T, bits, s));
-    k_surface_offsets<<<blocks_for((int64_t)S + 1), kThreads, 0, s>>>(key, T, S, b->s_off);
+    ::sbr::note_launch(), k_surface_offsets<<<blocks_for((int64_t)S + 1), kThreads, 0, s>>>(key, T, S, b->s_off);
     SBR_TRY_CUDA(cudaGetLastError());
     uint32_t h_status = 0;
     SBR_TRY_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));

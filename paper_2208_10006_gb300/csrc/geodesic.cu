@@ -93,7 +93,7 @@ __global__ void k_alpha_store(const unsigned long long* best, double* alpha) {
 sbr_status launch_dirs(int32_t N, double* dirs, cudaStream_t s) {
     int64_t R = 10 * (int64_t)N * N + 2;
     Ico ico = make_ico();
-    k_dirs<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(ico, N, R, dirs);
+    ::sbr::note_launch(), k_dirs<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(ico, N, R, dirs);
     SBR_TRY_CUDA(cudaGetLastError());
     return SBR_OK;
 }
@@ -105,8 +105,8 @@ sbr_status launch_alpha(int32_t N, double* alpha, cudaStream_t s) {
     SBR_TRY(dalloc_n(&best, 1, s));
     SBR_TRY_CUDA(cudaMemsetAsync(best, 0, sizeof(unsigned long long), s));
     int64_t tot = 20 * per_face;
-    k_alpha<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ico, N, per_face, best);
-    k_alpha_store<<<1, 1, 0, s>>>(best, alpha);
+    ::sbr::note_launch(), k_alpha<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ico, N, per_face, best);
+    ::sbr::note_launch(), k_alpha_store<<<1, 1, 0, s>>>(best, alpha);
     SBR_TRY_CUDA(cudaGetLastError());
     dfree(best, s);
     return SBR_OK;

@@ -116,8 +116,11 @@ struct RefineArgs {
     double* jones_o;
 };
 
+// one warp per key: every lane runs the (cheap) image construction, the lanes
+// split the containment tests over the surface's faces, lane 0 writes
 __global__ void k_refine(const __grid_constant__ RefineArgs a) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= a.n) return;
     uint32_t slot = a.idx[a.perm[i]];
     const uint32_t* key = a.key + (size_t)slot * kKeyWords;
@@ -155,13 +158,20 @@ __global__ void k_refine(const __grid_constant__ RefineArgs a) {
     for (int k = 1; k <= m && ok; ++k) {
         int s = seq[k - 1];
         int32_t found = -1;
-        for (int32_t q = a.s_off[s]; q < a.s_off[s + 1]; ++q) {
-            int32_t t = a.s_tri[q];
-            if (point_in_tri(a.tri + 9 * (int64_t)t, P[k], 1e-9)) { found = t; break; }
+        const int32_t qa = a.s_off[s], qb = a.s_off[s + 1];
+        for (int32_t base = qa; base < qb; base += 32) {
+            int32_t q = base + lane;
+            bool in = q < qb && point_in_tri(a.tri + 9 * (int64_t)a.s_tri[q], P[k], 1e-9);
+            unsigned m32 = __ballot_sync(0xffffffffu, in);
+            if (m32) {  // faces are listed in ascending id: the lowest lane is the lowest id
+                found = a.s_tri[base + __ffs(m32) - 1];
+                break;
+            }
         }
         if (found < 0) { ok = false; break; }
         face[k - 1] = found;
     }
+    if (lane != 0) return;
     a.valid[i] = ok ? 1u : 0u;
     if (!ok) return;
     a.rx_o[i] = rx_id;
@@ -256,7 +266,7 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     SBR_TRY(dalloc_n(&count, 1, s));
     SBR_TRY(dalloc_n(&idx, cap, s));
     SBR_TRY_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned), s));
-    k_collect<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(tr->ht_state, cap, idx, count);
+    ::sbr::note_launch(), k_collect<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(tr->ht_state, cap, idx, count);
     SBR_TRY_CUDA(cudaGetLastError());
     unsigned h_count = 0;
     SBR_TRY_CUDA(cudaMemcpyAsync(&h_count, count, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -267,13 +277,13 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     uint32_t *perm, *word;
     SBR_TRY(dalloc_n(&perm, std::max<int64_t>(n, 1), s));
     SBR_TRY(dalloc_n(&word, std::max<int64_t>(n, 1), s));
-    k_iota<<<nblk(n), kThreads, 0, s>>>(perm, n);
+    ::sbr::note_launch(), k_iota<<<nblk(n), kThreads, 0, s>>>(perm, n);
     std::vector<std::pair<int, int>> words;  // (word index, bits)
     for (int k = K - 1; k >= 0; --k) words.push_back({2 + k, bits_for((int64_t)b->S)});
     words.push_back({1, bits_for(K)});
     words.push_back({0, bits_for(std::max(1, tr->n_rx - 1))});
     for (auto& w : words) {
-        k_key_word<<<nblk(n), kThreads, 0, s>>>(tr->ht_key, idx, perm, n, w.first, word);
+        ::sbr::note_launch(), k_key_word<<<nblk(n), kThreads, 0, s>>>(tr->ht_key, idx, perm, n, w.first, word);
         SBR_TRY_CUDA(cudaGetLastError());
         SBR_TRY(radix_sort_pairs(word, perm, n, w.second, s));
     }
@@ -309,7 +319,7 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     SBR_TRY(dalloc_n(&a.jones_o, nn * kJones, s));
     a.valid = valid;
     if (n > 0) {
-        k_refine<<<nblk(n), kThreads, 0, s>>>(a);
+        ::sbr::note_launch(), k_refine<<<nblk(32 * n), kThreads, 0, s>>>(a);
         SBR_TRY_CUDA(cudaGetLastError());
         SBR_TRY_CUDA(cudaMemcpyAsync(pos, valid, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
     }
@@ -335,7 +345,7 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     if (n > 0) {
         auto go = [&](auto* in, auto* out, int width) {
             using T = std::remove_pointer_t<decltype(out)>;
-            k_compact<T><<<nblk(n * width), kThreads, 0, s>>>(valid, pos, n, in, out, width);
+            ::sbr::note_launch(), k_compact<T><<<nblk(n * width), kThreads, 0, s>>>(valid, pos, n, in, out, width);
         };
         go(a.rx_o, pl->rx, 1);
         go(a.nb_o, pl->nb, 1);
@@ -350,7 +360,7 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
         go(a.jones_o, pl->jones, kJones);
         SBR_TRY_CUDA(cudaGetLastError());
     }
-    k_rx_offsets<<<nblk((int64_t)tr->n_rx + 1), kThreads, 0, s>>>(pl->rx, P, tr->n_rx, pl->rx_off);
+    ::sbr::note_launch(), k_rx_offsets<<<nblk((int64_t)tr->n_rx + 1), kThreads, 0, s>>>(pl->rx, P, tr->n_rx, pl->rx_off);
     SBR_TRY_CUDA(cudaGetLastError());
     pl->h_rx_off = new int32_t[tr->n_rx + 1];
     SBR_TRY_CUDA(cudaMemcpyAsync(pl->h_rx_off, pl->rx_off, sizeof(int32_t) * (tr->n_rx + 1),

@@ -199,7 +199,7 @@ sbr_status pdp_run(const sbr_path_list* pl, const float2* g, int32_t F, int32_t 
     size_t smem = sizeof(double) * (size_t)n_bins;
     if (smem > 48 * 1024)
         SBR_TRY_CUDA(cudaFuncSetAttribute(k_pdp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_pdp<<<pl->n_rx, kPdpThreads, smem, s>>>(pl->rx_off, pl->L, pl->aod, pl->aoa, g, F, f_index, fc,
+    ::sbr::note_launch(), k_pdp<<<pl->n_rx, kPdpThreads, smem, s>>>(pl->rx_off, pl->L, pl->aod, pl->aoa, g, F, f_index, fc,
                                                bin_s, n_bins, pdp, stats);
     SBR_TRY_CUDA(cudaGetLastError());
     return SBR_OK;
@@ -220,12 +220,12 @@ sbr_status capacity_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt, cons
     SBR_TRY(dalloc_n(&qbar, 1, s));
     SBR_TRY(dalloc_n(&ld, (size_t)F * n_snr, s));
     SBR_TRY_CUDA(cudaMemcpyAsync(d_lin, lin.data(), sizeof(double) * n_snr, cudaMemcpyHostToDevice, s));
-    k_frob<<<F, kCapThreads, 0, s>>>(H, (int64_t)Nr * Nt, qf);
-    k_qbar<<<1, 1, 0, s>>>(qf, F, qbar);
+    ::sbr::note_launch(), k_frob<<<F, kCapThreads, 0, s>>>(H, (int64_t)Nr * Nt, qf);
+    ::sbr::note_launch(), k_qbar<<<1, 1, 0, s>>>(qf, F, qbar);
     size_t smem = capacity_smem(Nr, Nt);
     SBR_TRY_CUDA(cudaFuncSetAttribute(k_capacity, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_capacity<<<F, kCapThreads, smem, s>>>(H, Nr, Nt, d_lin, n_snr, qbar, ld);
-    k_cap_reduce<<<1, 32, 0, s>>>(ld, F, n_snr, C);
+    ::sbr::note_launch(), k_capacity<<<F, kCapThreads, smem, s>>>(H, Nr, Nt, d_lin, n_snr, qbar, ld);
+    ::sbr::note_launch(), k_cap_reduce<<<1, 32, 0, s>>>(ld, F, n_snr, C);
     SBR_TRY_CUDA(cudaGetLastError());
     // the host SNR table must outlive the copy
     SBR_TRY_CUDA(cudaStreamSynchronize(s));

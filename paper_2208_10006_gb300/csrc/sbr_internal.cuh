@@ -60,6 +60,8 @@ sbr_status dalloc_n(T** p, size_t n, cudaStream_t s) {
     return dalloc(reinterpret_cast<void**>(p), n * sizeof(T) + (n == 0 ? 16 : 0), s);
 }
 int sm_count();
+// count of kernel launches made by the library in this process
+void note_launch();
 // enqueue a device-side store of a value (no host buffer outlives the call)
 sbr_status set_u64(unsigned long long* dst, unsigned long long v, cudaStream_t s);
 sbr_status set_f64(double* dst, double v, cudaStream_t s);

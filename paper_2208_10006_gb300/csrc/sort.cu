@@ -122,17 +122,17 @@ sbr_status scan_rec(uint32_t* data, int64_t n, cudaStream_t s) {
     if (n <= 0) return SBR_OK;
     int64_t nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 1) {
-        k_scan_blocks<<<1, kScanBlock, 0, s>>>(data, n, nullptr);
+        ::sbr::note_launch(), k_scan_blocks<<<1, kScanBlock, 0, s>>>(data, n, nullptr);
         SBR_TRY_CUDA(cudaGetLastError());
         return SBR_OK;
     }
     uint32_t* sums;
     SBR_TRY(dalloc_n(&sums, nb, s));
-    k_scan_blocks<<<(unsigned)nb, kScanBlock, 0, s>>>(data, n, sums);
+    ::sbr::note_launch(), k_scan_blocks<<<(unsigned)nb, kScanBlock, 0, s>>>(data, n, sums);
     SBR_TRY_CUDA(cudaGetLastError());
     sbr_status st = scan_rec(sums, nb, s);
     if (st == SBR_OK) {
-        k_add_offsets<<<(unsigned)nb, kScanBlock, 0, s>>>(data, n, sums);
+        ::sbr::note_launch(), k_add_offsets<<<(unsigned)nb, kScanBlock, 0, s>>>(data, n, sums);
         if (cudaGetLastError() != cudaSuccess) st = SBR_ERR_CUDA;
     }
     dfree(sums, s);
@@ -154,7 +154,7 @@ sbr_status exclusive_scan_u32(uint32_t* data, int64_t n, uint32_t* total, cudaSt
     }
     sbr_status st = scan_rec(data, n, s);
     if (st == SBR_OK && total) {
-        k_total<<<1, 1, 0, s>>>(data, last, n, total);
+        ::sbr::note_launch(), k_total<<<1, 1, 0, s>>>(data, last, n, total);
         if (cudaGetLastError() != cudaSuccess) st = SBR_ERR_CUDA;
     }
     if (last) dfree(last, s);
@@ -176,10 +176,10 @@ sbr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits,
     int passes = (bits + 7) / 8;
     sbr_status st = SBR_OK;
     for (int p = 0; p < passes && st == SBR_OK; ++p) {
-        k_hist<<<nblocks, kSortThreads, 0, s>>>(ka, n, 8 * p, hist, nblocks);
+        ::sbr::note_launch(), k_hist<<<nblocks, kSortThreads, 0, s>>>(ka, n, 8 * p, hist, nblocks);
         st = scan_rec(hist, (int64_t)256 * nblocks, s);
         if (st != SBR_OK) break;
-        k_scatter<<<nblocks, kSortThreads, 0, s>>>(ka, va, kb, vb, n, 8 * p, hist, nblocks);
+        ::sbr::note_launch(), k_scatter<<<nblocks, kSortThreads, 0, s>>>(ka, va, kb, vb, n, 8 * p, hist, nblocks);
         if (cudaGetLastError() != cudaSuccess) {
             set_error("radix scatter launch failed");
             st = SBR_ERR_CUDA;

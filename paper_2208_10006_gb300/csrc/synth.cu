@@ -157,12 +157,12 @@ sbr_status synth_prepare(const sbr_path_list* pl, const float2* g, const double*
     SBR_TRY(dalloc_n(&sp->dlos, (size_t)Nr * Nt, s));
     if (sp->Pr > 0) {
         int64_t ne = (int64_t)sp->Pr * (Nt + Nr);
-        k_prep_delays<<<nb256(ne), 256, 0, s>>>(sp->Pr, pl->nb + o0, pl->pts + (int64_t)o0 * kKmax * 3,
+        ::sbr::note_launch(), k_prep_delays<<<nb256(ne), 256, 0, s>>>(sp->Pr, pl->nb + o0, pl->pts + (int64_t)o0 * kKmax * 3,
                                                 T0, R0, tx_elem, Nt, rx_elem, Nr, sp->dt, sp->dr);
-        k_prep_w<<<nb256((int64_t)sp->Pr * F), 256, 0, s>>>(sp->Pr, F, g + (int64_t)o0 * F,
+        ::sbr::note_launch(), k_prep_w<<<nb256((int64_t)sp->Pr * F), 256, 0, s>>>(sp->Pr, F, g + (int64_t)o0 * F,
                                                             pl->L + o0, freqs, sp->w);
     }
-    k_prep_los<<<nb256((int64_t)Nr * Nt), 256, 0, s>>>(T0, R0, tx_elem, Nt, rx_elem, Nr, sp->dlos);
+    ::sbr::note_launch(), k_prep_los<<<nb256((int64_t)Nr * Nt), 256, 0, s>>>(T0, R0, tx_elem, Nt, rx_elem, Nr, sp->dlos);
     SBR_TRY_CUDA(cudaGetLastError());
     return SBR_OK;
 }
@@ -183,7 +183,7 @@ sbr_status synth_simt_run(const sbr_path_list* pl, const float2* g, const double
     dim3 grid((unsigned)((Nt + kSynthThreads - 1) / kSynthThreads), (unsigned)Nr, (unsigned)F);
     const int32_t Pr = std::max(sp.Pr, 1);
     if (fp64) {
-        k_synth<double><<<grid, kSynthThreads, 0, s>>>(F, Nr, Nt, sp.Pr, sp.los, freqs, sp.w, sp.dt,
+        ::sbr::note_launch(), k_synth<double><<<grid, kSynthThreads, 0, s>>>(F, Nr, Nt, sp.Pr, sp.los, freqs, sp.w, sp.dt,
                                                        sp.dr, sp.dlos, H);
         SBR_TRY_CUDA(cudaGetLastError());
     } else {
@@ -193,11 +193,11 @@ sbr_status synth_simt_run(const sbr_path_list* pl, const float2* g, const double
         SBR_TRY(dalloc_n(&dr, (size_t)Pr * Nr, s));
         SBR_TRY(dalloc_n(&dl, (size_t)Nr * Nt, s));
         SBR_TRY(dalloc_n(&w, (size_t)Pr * F, s));
-        k_convert<float><<<nb256((int64_t)Pr * Nt), 256, 0, s>>>(sp.dt, dt, (int64_t)Pr * Nt);
-        k_convert<float><<<nb256((int64_t)Pr * Nr), 256, 0, s>>>(sp.dr, dr, (int64_t)Pr * Nr);
-        k_convert<float><<<nb256((int64_t)Nr * Nt), 256, 0, s>>>(sp.dlos, dl, (int64_t)Nr * Nt);
-        k_convert2<float><<<nb256((int64_t)Pr * F), 256, 0, s>>>(sp.w, w, (int64_t)Pr * F);
-        k_synth<float><<<grid, kSynthThreads, 0, s>>>(F, Nr, Nt, sp.Pr, sp.los, freqs, w, dt, dr, dl, H);
+        ::sbr::note_launch(), k_convert<float><<<nb256((int64_t)Pr * Nt), 256, 0, s>>>(sp.dt, dt, (int64_t)Pr * Nt);
+        ::sbr::note_launch(), k_convert<float><<<nb256((int64_t)Pr * Nr), 256, 0, s>>>(sp.dr, dr, (int64_t)Pr * Nr);
+        ::sbr::note_launch(), k_convert<float><<<nb256((int64_t)Nr * Nt), 256, 0, s>>>(sp.dlos, dl, (int64_t)Nr * Nt);
+        ::sbr::note_launch(), k_convert2<float><<<nb256((int64_t)Pr * F), 256, 0, s>>>(sp.w, w, (int64_t)Pr * F);
+        ::sbr::note_launch(), k_synth<float><<<grid, kSynthThreads, 0, s>>>(F, Nr, Nt, sp.Pr, sp.los, freqs, w, dt, dr, dl, H);
         SBR_TRY_CUDA(cudaGetLastError());
         dfree(dt, s); dfree(dr, s); dfree(dl, s); dfree(w, s);
     }

@@ -1,13 +1,335 @@
-// H(f) synthesis on the tcgen05 tensor cores (BF16 hi/lo split).
+// H(f) synthesis on the 5th-generation tensor cores (tcgen05), Eq. 13-14.
+//
+// For one frequency and the reflected paths n of one receiver,
+//   H[q,p] = sum_n A[q,n] V[p,n],  A[q,n] = w_n exp(-j 2 pi f dr_qn / c),
+//   V[p,n] = exp(-j 2 pi f dt_pn / c),
+// is the complex contraction U diag(w) V^T. It runs as one real GEMM
+//   C (2Nr x Nt) = A' (2Nr x 2P) B' (2P x Nt)
+// with rows 2q / 2q+1 of C the real / imaginary part of H[q, :] and the
+// contraction index k = 2n + {0: real, 1: imaginary}:
+//   A'[2q,   2n] =  Re A,  A'[2q,   2n+1] = -Im A
+//   A'[2q+1, 2n] =  Im A,  A'[2q+1, 2n+1] =  Re A
+//   B'[2n, p]    =  Re V,  B'[2n+1, p]    =  Im V.
+// Each operand is split x = hi + lo into two BF16 values and the product is
+// taken as hi*hi + hi*lo + lo*hi (the lo*lo term, ~2^-18 relative, dropped),
+// accumulated in FP32 in tensor memory. The phasors are generated on chip
+// (FP32 phase from the FP64-prepared delays) straight into 128-byte-swizzled
+// K-major shared-memory tiles; one thread issues tcgen05.mma (M=128, N=256,
+// K=16) and commits to an mbarrier; the epilogue reads TMEM with tcgen05.ld,
+// pairs the real/imaginary rows across neighbouring lanes, adds the exact
+// per-element LoS term and stores complex64.
+//
+// Every wait on the mbarrier is bounded; on expiry the CTA records
+// ST_TIMEOUT, releases its tensor memory and returns.
+#include <algorithm>
+#include <cuda_bf16.h>
+
 #include "sbr_internal.cuh"
 #include "synth_common.cuh"
 
 namespace sbr {
+namespace {
 
-sbr_status synth_tc_run(const sbr_path_list*, const float2*, const double*, int32_t, const double*,
-                        int32_t, const double*, int32_t, int32_t, float2*, cudaStream_t) {
-    set_error("tensor-core synthesis not built yet");
-    return SBR_ERR_UNSUPPORTED;
+constexpr int kTcThreads = 256;
+constexpr int kTileM = 128;      // 2 x 64 receive elements
+constexpr int kTileN = 256;      // transmit elements
+constexpr int kChunkP = 32;      // paths per K-chunk (K = 64 BF16 = one 128-byte row)
+constexpr int kTmemCols = 256;
+constexpr uint32_t kSpin = 1u << 26;
+
+constexpr int kABytes = kTileM * 128;  // 16 KB
+constexpr int kBBytes = kTileN * 128;  // 32 KB
+constexpr int kSmemTiles = 2 * kABytes + 2 * kBBytes;  // hi/lo of A and B
+constexpr int kSmemBytes = kSmemTiles + 1024 + 64;      // + alignment slack + barrier
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// byte offset of element (row r, k) in a [rows][64] BF16 tile, 128-byte swizzle
+__device__ __forceinline__ uint32_t sw128(int r, int k) {
+    uint32_t off = (uint32_t)r * 128u + (uint32_t)k * 2u;
+    return off ^ (((off >> 7) & 7u) << 4);
+}
+
+// tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle,
+// 8-row core-matrix groups 1024 bytes apart
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                      // leading byte offset (unused with swizzle)
+    d |= (uint64_t)(1024u >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)1 << 46;                      // descriptor version
+    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor: kind::f16, A/B BF16, D F32, both K-major, M=128, N=256
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
+                            ((uint32_t)(kTileM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+    for (uint32_t it = 0; it < kSpin; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// x = hi + lo, both BF16; returns the two as raw 16-bit patterns
+__device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) {
+    __nv_bfloat16 h = __float2bfloat16_rn(x);
+    __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(l);
+}
+
+struct TcArgs {
+    int32_t F, Nr, Nt;
+    int32_t n0, nrefl;         // reflected paths: local indices [n0, n0 + nrefl)
+    int32_t Pr;                // stride of w rows
+    int32_t los;               // local LoS index or -1
+    const double* freqs;
+    const float* dt;           // [Pr][Nt]
+    const float* dr;           // [Pr][Nr]
+    const float2* w;           // [F][Pr]
+    const float* dlos;         // [Nr][Nt]
+    float2* H;
+    unsigned int* status;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constant__ TcArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA_hi = smem;
+    unsigned char* sA_lo = smem + kABytes;
+    unsigned char* sB_hi = smem + 2 * kABytes;
+    unsigned char* sB_lo = smem + 2 * kABytes + kBBytes;
+    uint64_t* mbar = (uint64_t*)(smem + kSmemTiles);
+    uint32_t* tmem_slot = (uint32_t*)(smem + kSmemTiles + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t mbar_a = smem_u32(mbar);
+    uint32_t phase = 0;
+    bool failed = false;
+
+    const int mtiles = (a.Nr + 63) / 64, ntiles = (a.Nt + kTileN - 1) / kTileN;
+    const int64_t items = (int64_t)a.F * mtiles * ntiles;
+    const int nch = (a.nrefl + kChunkP - 1) / kChunkP;
+    for (int64_t it = blockIdx.x; it < items && !failed; it += gridDim.x) {
+        const int f = (int)(it / (mtiles * ntiles));
+        const int rem = (int)(it - (int64_t)f * mtiles * ntiles);
+        const int q0 = (rem / ntiles) * 64, p0 = (rem % ntiles) * kTileN;
+        const float foc = (float)(a.freqs[f] / kC0);
+        for (int c = 0; c < nch && !failed; ++c) {
+            const int nb = a.n0 + c * kChunkP;
+            const int cnt = min(kChunkP, a.n0 + a.nrefl - nb);
+            // A' tile: 64 receive elements x 32 paths, each a 2x2 real block
+            for (int e = tid; e < 64 * kChunkP; e += kTcThreads) {
+                int ql = e / kChunkP, nl = e % kChunkP;
+                int q = q0 + ql, n = nb + nl;
+                float ar = 0.f, ai = 0.f;
+                if (nl < cnt && q < a.Nr) {
+                    float2 ww = a.w[(int64_t)f * a.Pr + n];
+                    float s, co;
+                    sincospif(-2.0f * foc * a.dr[(int64_t)n * a.Nr + q], &s, &co);
+                    ar = ww.x * co - ww.y * s;
+                    ai = ww.x * s + ww.y * co;
+                }
+                uint16_t h0, l0, h1, l1, h2, l2;
+                split_bf16(ar, h0, l0);
+                split_bf16(-ai, h1, l1);
+                split_bf16(ai, h2, l2);
+                uint32_t o0 = sw128(2 * ql, 2 * nl), o1 = sw128(2 * ql + 1, 2 * nl);
+                *(uint32_t*)(sA_hi + o0) = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                *(uint32_t*)(sA_lo + o0) = (uint32_t)l0 | ((uint32_t)l1 << 16);
+                *(uint32_t*)(sA_hi + o1) = (uint32_t)h2 | ((uint32_t)h0 << 16);
+                *(uint32_t*)(sA_lo + o1) = (uint32_t)l2 | ((uint32_t)l0 << 16);
+            }
+            // B' tile (stored N x K): 256 transmit elements x 32 paths
+            for (int e = tid; e < kTileN * kChunkP; e += kTcThreads) {
+                int pl = e / kChunkP, nl = e % kChunkP;
+                int p = p0 + pl, n = nb + nl;
+                float vr = 0.f, vi = 0.f;
+                if (nl < cnt && p < a.Nt) sincospif(-2.0f * foc * a.dt[(int64_t)n * a.Nt + p], &vi, &vr);
+                uint16_t h0, l0, h1, l1;
+                split_bf16(vr, h0, l0);
+                split_bf16(vi, h1, l1);
+                uint32_t o = sw128(pl, 2 * nl);
+                *(uint32_t*)(sB_hi + o) = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                *(uint32_t*)(sB_lo + o) = (uint32_t)l0 | ((uint32_t)l1 << 16);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                uint64_t dAh = make_desc(smem_u32(sA_hi)), dAl = make_desc(smem_u32(sA_lo));
+                uint64_t dBh = make_desc(smem_u32(sB_hi)), dBl = make_desc(smem_u32(sB_lo));
+                for (int ks = 0; ks < 4; ++ks) {
+                    uint64_t off = (uint64_t)(ks * 32) >> 4;  // 16 BF16 along K
+                    mma_bf16(tmem, dAh + off, dBh + off, (c > 0 || ks > 0) ? 1u : 0u);
+                    mma_bf16(tmem, dAh + off, dBl + off, 1u);
+                    mma_bf16(tmem, dAl + off, dBh + off, 1u);
+                }
+                mma_commit(mbar_a);
+            }
+            if (!mbar_wait(mbar_a, phase)) failed = true;
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+        if (failed) break;
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns 128 (w / 4) .. +127
+        const int qw = warp & 3, chalf = warp >> 2;
+        const int row = 32 * qw + lane;            // row of C: 2 (q - q0) + part
+        const int q = q0 + (row >> 1);
+        const int part = row & 1;
+        float2 wl = make_float2(0.f, 0.f);
+        if (a.los >= 0) wl = a.w[(int64_t)f * a.Pr + a.los];
+        for (int j = 0; j < 4; ++j) {
+            const int col0 = 128 * chalf + 32 * j;
+            uint32_t v[32];
+            if (nch > 0) {
+                tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)col0, v);
+            } else {
+                for (int k = 0; k < 32; ++k) v[k] = 0u;
+            }
+            // even lane (real row) keeps columns [0,16), odd lane (imaginary row) [16,32)
+            float re[16], im[16];
+            for (int k = 0; k < 16; ++k) {
+                float mine_lo = __uint_as_float(v[k]), mine_hi = __uint_as_float(v[16 + k]);
+                float send = part == 0 ? mine_hi : mine_lo;
+                float got = __shfl_xor_sync(0xffffffffu, send, 1);
+                if (part == 0) { re[k] = mine_lo; im[k] = got; }
+                else { re[k] = got; im[k] = mine_hi; }
+            }
+            const int pb = p0 + col0 + 16 * part;
+            if (q < a.Nr) {
+                float2* dst = a.H + ((int64_t)f * a.Nr + q) * a.Nt;
+                for (int k = 0; k < 16; ++k) {
+                    int p = pb + k;
+                    if (p >= a.Nt) break;
+                    float hr = re[k], hi = im[k];
+                    if (a.los >= 0) {
+                        float s, co;
+                        sincospif(-2.0f * foc * a.dlos[(int64_t)q * a.Nt + p], &s, &co);
+                        hr += wl.x * co - wl.y * s;
+                        hi += wl.x * s + wl.y * co;
+                    }
+                    dst[p] = make_float2(hr, hi);
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (failed && tid == 0) atomicOr(a.status, (unsigned)ST_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+template <class T>
+__global__ void k_to_f32(const T* __restrict__ in, float* __restrict__ out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+__global__ void k_w_to_f32(const double2* __restrict__ in, float2* __restrict__ out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+inline unsigned nb256(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + 255) / 256); }
+
+}  // namespace
+
+sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* freqs, int32_t F,
+                        const double* tx_elem, int32_t Nt, const double* rx_elem, int32_t Nr,
+                        int32_t rx_index, float2* H, cudaStream_t s) {
+    SynthPrep sp;
+    SBR_TRY(synth_prepare(pl, g, freqs, F, tx_elem, Nt, rx_elem, Nr, rx_index, &sp, s));
+    const int32_t Pr = std::max(sp.Pr, 1);
+    float *dt, *dr, *dl;
+    float2* w;
+    unsigned int* status;
+    SBR_TRY(dalloc_n(&dt, (size_t)Pr * Nt, s));
+    SBR_TRY(dalloc_n(&dr, (size_t)Pr * Nr, s));
+    SBR_TRY(dalloc_n(&dl, (size_t)Nr * Nt, s));
+    SBR_TRY(dalloc_n(&w, (size_t)Pr * F, s));
+    SBR_TRY(dalloc_n(&status, 1, s));
+    SBR_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
+    ::sbr::note_launch(), k_to_f32<double><<<nb256((int64_t)Pr * Nt), 256, 0, s>>>(sp.dt, dt, (int64_t)Pr * Nt);
+    ::sbr::note_launch(), k_to_f32<double><<<nb256((int64_t)Pr * Nr), 256, 0, s>>>(sp.dr, dr, (int64_t)Pr * Nr);
+    ::sbr::note_launch(), k_to_f32<double><<<nb256((int64_t)Nr * Nt), 256, 0, s>>>(sp.dlos, dl, (int64_t)Nr * Nt);
+    ::sbr::note_launch(), k_w_to_f32<<<nb256((int64_t)Pr * F), 256, 0, s>>>(sp.w, w, (int64_t)Pr * F);
+    TcArgs a{};
+    a.F = F; a.Nr = Nr; a.Nt = Nt;
+    a.los = sp.los;
+    a.n0 = sp.los == 0 ? 1 : 0;
+    a.nrefl = sp.Pr - a.n0;
+    a.Pr = Pr;
+    a.freqs = freqs; a.dt = dt; a.dr = dr; a.w = w; a.dlos = dl; a.H = H; a.status = status;
+    SBR_TRY_CUDA(cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    int64_t items = (int64_t)F * ((Nr + 63) / 64) * ((Nt + kTileN - 1) / kTileN);
+    int grid = (int)std::min<int64_t>(items, (int64_t)sm_count());
+    ::sbr::note_launch(), k_synth_tc<<<grid, kTcThreads, kSmemBytes, s>>>(a);
+    SBR_TRY_CUDA(cudaGetLastError());
+    unsigned h_status = 0;
+    SBR_TRY_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    SBR_TRY_CUDA(cudaStreamSynchronize(s));
+    dfree(dt, s); dfree(dr, s); dfree(dl, s); dfree(w, s); dfree(status, s);
+    synth_release(&sp, s);
+    return status_from_bits(h_status);
 }
 
 }  // namespace sbr

@@ -548,7 +548,7 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     SBR_TRY(dalloc_n(&tr->ht_val, cap, s));
     SBR_TRY(dalloc_n(&tr->cnt, 1, s));
     SBR_TRY_CUDA(cudaMemsetAsync(tr->cnt, 0, sizeof(TraceCountersDev), s));
-    k_init_table<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(tr->ht_state, tr->ht_val, cap);
+    ::sbr::note_launch(), k_init_table<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(tr->ht_state, tr->ht_val, cap);
     SBR_TRY_CUDA(cudaGetLastError());
     SBR_TRY(set_u64(&tr->cnt->queue[0], (unsigned long long)R, s));
     // receiver BVH
@@ -558,7 +558,7 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     if (tr->n_rx > 0) {
         SBR_TRY(dalloc_n(&rxbox, 6 * (size_t)tr->n_rx, s));
         SBR_TRY(dalloc_n(&rx_depth, 1, s));
-        k_rx_boxes<<<(tr->n_rx + 255) / 256, 256, 0, s>>>(tr->rx, tr->n_rx, rxbox);
+        ::sbr::note_launch(), k_rx_boxes<<<(tr->n_rx + 255) / 256, 256, 0, s>>>(tr->rx, tr->n_rx, rxbox);
         SBR_TRY_CUDA(cudaGetLastError());
         SBR_TRY(build_lbvh(rxbox, tr->n_rx, 0.0f, &rxb, rx_depth, s));
     }
@@ -604,7 +604,7 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
         a.n_in = &tr->cnt->queue[bnc];
         a.n_out = &tr->cnt->queue[bnc + 1];
         a.work = &tr->cnt->work[bnc];
-        k_trace_bounce<<<grid, kTraceThreads, 0, s>>>(a, ico);
+        ::sbr::note_launch(), k_trace_bounce<<<grid, kTraceThreads, 0, s>>>(a, ico);
         SBR_TRY_CUDA(cudaGetLastError());
         if (timing) SBR_TRY_CUDA(cudaEventRecord(tr->ev[bnc + 1], s));
     }
