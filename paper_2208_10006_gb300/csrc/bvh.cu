@@ -9,6 +9,7 @@
 // that FP32 traversal never culls a box that the exact ray touches.
 #include <algorithm>
 
+#include "dfloat.cuh"
 #include "sbr_internal.cuh"
 
 namespace sbr {
@@ -229,7 +230,7 @@ __global__ void k_tri_normals(const float* __restrict__ tri, int64_t T, double* 
 
 __global__ void k_tri_pack(const float* __restrict__ tri, const int32_t* __restrict__ surf,
                            const double* __restrict__ nrm, const int32_t* __restrict__ order,
-                           int64_t T, float4* __restrict__ out, double* __restrict__ nrm_sorted) {
+                           int64_t T, float4* __restrict__ out, float4* __restrict__ plane) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= T) return;
     int64_t t = order[j];
@@ -237,7 +238,12 @@ __global__ void k_tri_pack(const float* __restrict__ tri, const int32_t* __restr
     out[3 * j + 0] = make_float4(v[0], v[1], v[2], __int_as_float(surf[t]));
     out[3 * j + 1] = make_float4(v[3], v[4], v[5], __int_as_float((int)t));
     out[3 * j + 2] = make_float4(v[6], v[7], v[8], 0.f);
-    for (int k = 0; k < 3; ++k) nrm_sorted[3 * j + k] = nrm[3 * t + k];
+    // plane n.x = c with the FP64 unit normal, stored as double-float pairs
+    double n0 = nrm[3 * t], n1 = nrm[3 * t + 1], n2 = nrm[3 * t + 2];
+    double c = n0 * (double)v[0] + n1 * (double)v[1] + n2 * (double)v[2];
+    df a = df_from_double(n0), bb = df_from_double(n1), cc = df_from_double(n2), dd = df_from_double(c);
+    plane[2 * j] = make_float4(a.hi, bb.hi, cc.hi, dd.hi);
+    plane[2 * j + 1] = make_float4(a.lo, bb.lo, cc.lo, dd.lo);
 }
 
 __global__ void k_copy_surf(const int32_t* __restrict__ surf, int64_t T, int32_t S,
@@ -334,7 +340,7 @@ sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S
     SBR_TRY(dalloc_n(&b->surf, T, s));
     SBR_TRY(dalloc_n(&b->nrm, 3 * T, s));
     SBR_TRY(dalloc_n(&b->tri_sorted, 3 * T, s));
-    SBR_TRY(dalloc_n(&b->nrm_sorted, 3 * T, s));
+    SBR_TRY(dalloc_n(&b->plane_sorted, 2 * T, s));
     SBR_TRY(dalloc_n(&b->s_tri, T, s));
     SBR_TRY_CUDA(cudaMemcpyAsync(b->tri, tri, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, s));
     SBR_TRY_CUDA(cudaMemcpyAsync(b->surf, surf, sizeof(int32_t) * T, cudaMemcpyDeviceToDevice, s));
@@ -346,7 +352,7 @@ sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S
     // relative box padding: 2^-20 of (|x| + 1) covers FP32 ray/box rounding
     SBR_TRY(build_lbvh(box, T, 1.0f / (1 << 20), &b->tree, b->d_depth, s));
     ::sbr::note_launch(), k_tri_pack<<<blocks_for(T), kThreads, 0, s>>>(b->tri, b->surf, b->nrm, b->tree.order, T,
-                                                  b->tri_sorted, b->nrm_sorted);
+                                                  b->tri_sorted, b->plane_sorted);
     // faces per surface, ascending face id (stable sort on the surface id)
     uint32_t *key, *val;
     SBR_TRY(dalloc_n(&key, T, s));

@@ -1,0 +1,88 @@
+// Double-FP32 ("double-float") arithmetic: a value is hi + lo with two floats,
+// |lo| <= ulp(hi)/2, about 48 significant bits. Used for the ray state of the
+// bounce kernel (origin, direction, unfolded length) and the reception test,
+// where FP32 is too coarse and FP64 is scarce on this GPU. Built from the
+// error-free transformations: Knuth's two-sum, Dekker's fast two-sum and the
+// FMA-based two-product; division and square root add one Newton correction.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace sbr {
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_make(float h, float l) { return df{h, l}; }
+
+// exact split of a double into hi + lo floats
+__host__ __device__ __forceinline__ df df_from_double(double x) {
+    float h = (float)x;
+    return df{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df{s, e};
+}
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return df{s, e};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    return df{p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    df t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+    df p = two_prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+    p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    df p = two_prod(a.hi, b);
+    p.lo = __fmaf_rn(a.lo, b, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df df_div(df a, df b) {
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    df r = df_sub(a, df_mul_f(b, q1));
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    r = df_sub(r, df_mul_f(b, q2));
+    float q3 = __fdiv_rn(r.hi, b.hi);
+    df q = fast_two_sum(q1, q2);
+    return df_add(q, df{q3, 0.f});
+}
+// a < b, a <= b on the represented values
+__device__ __forceinline__ bool df_lt(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool df_le(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+
+struct df3 {
+    df x, y, z;
+};
+__device__ __forceinline__ df3 df3_add(df3 a, df3 b) { return df3{df_add(a.x, b.x), df_add(a.y, b.y), df_add(a.z, b.z)}; }
+__device__ __forceinline__ df3 df3_sub(df3 a, df3 b) { return df3{df_sub(a.x, b.x), df_sub(a.y, b.y), df_sub(a.z, b.z)}; }
+__device__ __forceinline__ df3 df3_scale(df3 a, df s) { return df3{df_mul(a.x, s), df_mul(a.y, s), df_mul(a.z, s)}; }
+__device__ __forceinline__ df df3_dot(df3 a, df3 b) {
+    return df_add(df_add(df_mul(a.x, b.x), df_mul(a.y, b.y)), df_mul(a.z, b.z));
+}
+__device__ __forceinline__ float3 df3_hi(df3 a) { return make_float3(a.x.hi, a.y.hi, a.z.hi); }
+
+}  // namespace sbr

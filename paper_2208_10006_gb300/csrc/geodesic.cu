@@ -2,7 +2,9 @@
 // direction list, and alpha, the largest angle between directions joined by
 // a sub-triangle edge, which sizes the reception sphere (Sec. II-A.3).
 #include <cmath>
+#include <mutex>
 
+#include "dfloat.cuh"
 #include "geodesic.cuh"
 
 namespace sbr {
@@ -88,7 +90,64 @@ __global__ void k_alpha_store(const unsigned long long* best, double* alpha) {
     *alpha = __longlong_as_double((long long)*best);
 }
 
+__global__ void k_dir_table(const __grid_constant__ Ico ico, int N, int64_t R, float4* __restrict__ da,
+                            float2* __restrict__ db) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R) return;
+    d3 d = geodesic_dir(ico, N, (uint32_t)i);
+    df x = df_from_double(d.x), y = df_from_double(d.y), z = df_from_double(d.z);
+    da[i] = make_float4(x.hi, y.hi, z.hi, x.lo);
+    db[i] = make_float2(y.lo, z.lo);
+}
+
+struct DirCache {
+    std::mutex mu;
+    int device = -1, N = 0;
+    float4* a = nullptr;
+    float2* b = nullptr;
+};
+DirCache g_dirs;
+
 }  // namespace
+
+sbr_status dir_table(int32_t N, const float4** dir_a, const float2** dir_b, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_dirs.mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (g_dirs.a == nullptr || g_dirs.device != dev || g_dirs.N != N) {
+        if (g_dirs.a) {
+            // a table of another N or device: release it (cudaFree waits for its users)
+            int cur = dev;
+            cudaSetDevice(g_dirs.device);
+            cudaFree(g_dirs.a);
+            cudaFree(g_dirs.b);
+            cudaSetDevice(cur);
+            g_dirs.a = nullptr;
+            g_dirs.b = nullptr;
+        }
+        int64_t R = 10 * (int64_t)N * N + 2;
+        float4* a = nullptr;
+        float2* b = nullptr;
+        SBR_TRY_CUDA(cudaMalloc(&a, sizeof(float4) * R));
+        if (cudaMalloc(&b, sizeof(float2) * R) != cudaSuccess) {
+            cudaFree(a);
+            set_error("direction table allocation failed");
+            return SBR_ERR_ALLOC;
+        }
+        Ico ico = make_ico();
+        ::sbr::note_launch(), k_dir_table<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(ico, N, R, a, b);
+        SBR_TRY_CUDA(cudaGetLastError());
+        // other streams may use the table next: finish building it now
+        SBR_TRY_CUDA(cudaStreamSynchronize(s));
+        g_dirs.a = a;
+        g_dirs.b = b;
+        g_dirs.device = dev;
+        g_dirs.N = N;
+    }
+    *dir_a = g_dirs.a;
+    *dir_b = g_dirs.b;
+    return SBR_OK;
+}
 
 sbr_status launch_dirs(int32_t N, double* dirs, cudaStream_t s) {
     int64_t R = 10 * (int64_t)N * N + 2;

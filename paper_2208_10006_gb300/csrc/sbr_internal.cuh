@@ -62,6 +62,9 @@ sbr_status dalloc_n(T** p, size_t n, cudaStream_t s) {
 int sm_count();
 // count of kernel launches made by the library in this process
 void note_launch();
+// geodesic directions of subdivision N as double-float, built once per (device, N)
+// and kept for the process: dir_a[i] = (hi.x, hi.y, hi.z, lo.x), dir_b[i] = (lo.y, lo.z)
+sbr_status dir_table(int32_t N, const float4** dir_a, const float2** dir_b, cudaStream_t s);
 // enqueue a device-side store of a value (no host buffer outlives the call)
 sbr_status set_u64(unsigned long long* dst, unsigned long long v, cudaStream_t s);
 sbr_status set_f64(double* dst, double v, cudaStream_t s);
@@ -107,7 +110,8 @@ struct sbr_bvh {
     int32_t S = 0;
     sbr::BvhNodes tree;
     float4* tri_sorted = nullptr;   // [T*3]: v0 (w = surface id bits), v1 (w = face id bits), v2
-    double* nrm_sorted = nullptr;   // [T*3] unit normal (FP64), BVH order
+    float4* plane_sorted = nullptr; // [T*2] face plane as double-float, BVH order:
+                                    //   (n_hi.xyz, c_hi), (n_lo.xyz, c_lo) with n.x = c
     float* tri = nullptr;           // [T*9] face-id order copy
     int32_t* surf = nullptr;        // [T]
     double* nrm = nullptr;          // [T*3] unit normal (FP64), face order

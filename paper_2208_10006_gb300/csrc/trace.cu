@@ -21,26 +21,29 @@
 //     keeps min(dist, ray id) per key with a 64-bit atomicMin.
 //  5. specular bounce d' = d - 2 (d.n) n in FP64, unfolded length L += t,
 //     survivors appended to the next queue with one atomic per warp.
-// The ray state (origin, direction, L) is kept in FP64 so that the hit and
-// reception decisions agree with an FP64 evaluation of the same rule to
-// rounding; the FP32 traversal carries the per-triangle cost.
+// The ray state (origin, direction, unfolded length L) is kept in double-FP32
+// (about 48 significant bits), so that the hit and reception decisions agree
+// with an FP64 evaluation of the same rule to rounding while the arithmetic
+// stays on the FP32 pipes (FP64 throughput on this GPU is a small fraction of
+// FP32). FP64 is used only to re-decide uncertain faces exactly. The FP32
+// traversal runs on the high words and carries the per-triangle cost.
 #include <algorithm>
 #include <cmath>
 
+#include "dfloat.cuh"
 #include "geodesic.cuh"
 
 namespace sbr {
 namespace {
 
 constexpr int kStack = 64;
-constexpr float kCert = 1e-3f;         // relative margin below which FP32 is not trusted
 constexpr int kTraceThreads = 128;
 constexpr int kSpinLimit = 1 << 20;    // bounded wait for a dedup slot being published
 
 struct RayRec {
-    double o[3];
-    double d[3];
-    double L;
+    float oh[3], ol[3];  // origin, double-float
+    float dh[3], dl[3];  // direction, double-float
+    float Lh, Ll;        // unfolded length, double-float
     uint32_t ray;
     int32_t prev;
 };
@@ -49,17 +52,19 @@ static_assert(sizeof(RayRec) == 64, "ray record is one 64-byte line");
 struct TraceArgs {
     const float4* nodes;
     const float4* tris;
-    const double* nrm;
+    const float4* plane;     // [T*2] double-float face planes, BVH order
     int64_t T;
     const float4* rx_nodes;
     const int32_t* rx_order;
-    const double* rx;
+    const float4* rx_df;     // [n_rx*2] receiver positions, double-float
     const float* rx_root;
     int32_t n_rx;
-    const double* alpha;
+    const float4* alpha_df;  // (alpha hi, lo, alpha^2/3 hi, lo)
+    const float4* dir_a;     // launch directions, double-float
+    const float2* dir_b;
     int N, K, bounce;
     int64_t R;
-    double tx[3];
+    float tx_h[3], tx_l[3];
     const RayRec* qin;
     RayRec* qout;
     const unsigned long long* n_in;
@@ -82,10 +87,10 @@ struct Ray32 {
     float Sx, Sy, Sz;
 };
 
-__device__ __forceinline__ Ray32 make_ray32(d3 o, d3 d) {
+__device__ __forceinline__ Ray32 make_ray32(float3 o, float3 d) {
     Ray32 r;
-    r.o = make_float3((float)o.x, (float)o.y, (float)o.z);
-    r.d = make_float3((float)d.x, (float)d.y, (float)d.z);
+    r.o = o;
+    r.d = d;
     r.inv = make_float3(1.0f / r.d.x, 1.0f / r.d.y, 1.0f / r.d.z);
     float ax = fabsf(r.d.x), ay = fabsf(r.d.y), az = fabsf(r.d.z);
     r.kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
@@ -346,26 +351,30 @@ __device__ void ht_insert(const TraceArgs& a, const uint32_t* key, unsigned long
 }
 
 // ---------------------------------------------------------------- reception
-__device__ void receive(const TraceArgs& a, d3 o, d3 d, double L, double t_hit, bool hit,
+// Receivers near the segment come from a BVH over the receiver points whose
+// boxes are grown by the largest sphere radius on the segment (FP32,
+// conservative); each is then tested exactly in double-float:
+//   t* = (Rx - o).d in [0, t_hit],  |o + t* d - Rx|^2 <= alpha^2 (L + t*)^2 / 3.
+__device__ void receive(const TraceArgs& a, const df3& o, const df3& d, df L, df t_hit, bool hit,
                         const Ray32& r, uint32_t ray, int* stack) {
     if (a.n_rx <= 0) return;
-    const double alpha = *a.alpha;
-    const double inv_sqrt3 = 0.57735026918962576451;
-    double t_end = t_hit;
+    const float4 al = __ldg(a.alpha_df);
+    const df a2o3 = df_make(al.z, al.w);
+    float t_end = t_hit.hi;
     if (!hit) {
         // no receiver lies beyond the farthest corner of their bounding box
-        double far2 = 0;
+        float far2 = 0.f;
         for (int c = 0; c < 8; ++c) {
-            double x = a.rx_root[(c & 1) ? 3 : 0] - o.x;
-            double y = a.rx_root[(c & 2) ? 4 : 1] - o.y;
-            double z = a.rx_root[(c & 4) ? 5 : 2] - o.z;
-            far2 = fmax(far2, x * x + y * y + z * z);
+            float x = a.rx_root[(c & 1) ? 3 : 0] - r.o.x;
+            float y = a.rx_root[(c & 2) ? 4 : 1] - r.o.y;
+            float z = a.rx_root[(c & 4) ? 5 : 2] - r.o.z;
+            far2 = fmaxf(far2, x * x + y * y + z * z);
         }
-        t_end = sqrt(far2) * (1.0 + 1e-6) + 1e-3;
+        t_end = sqrtf(far2) * (1.f + 1e-5f) + 1e-3f;
     }
-    float rmax = (float)(alpha * (L + t_end) * inv_sqrt3 * (1.0 + 1e-5)) +
-                 1e-5f * (float)(fabs(o.x) + fabs(o.y) + fabs(o.z) + L + t_end);
-    float tmax = (float)(t_end * (1.0 + 1e-5)) + rmax;
+    float rmax = al.x * (L.hi + t_end) * 0.57735027f * (1.f + 1e-4f) +
+                 1e-5f * (fabsf(r.o.x) + fabsf(r.o.y) + fabsf(r.o.z) + L.hi + t_end);
+    float tmax = t_end * (1.f + 1e-5f) + rmax;
     int sp = 0;
     int32_t node = 0;
     for (;;) {
@@ -382,20 +391,23 @@ __device__ void receive(const TraceArgs& a, d3 o, d3 d, double L, double t_hit, 
             bool hh = c ? h1 : h0;
             if (hh && rr < 0) {
                 int32_t rx_id = __ldg(a.rx_order + (~rr));
-                d3 R = mk3(a.rx[3 * rx_id], a.rx[3 * rx_id + 1], a.rx[3 * rx_id + 2]);
-                double ts = dot(R - o, d);
-                if (ts >= 0.0 && ts <= t_hit) {
-                    d3 p = o + d * ts;
-                    double dist = norm(p - R);
-                    double rad = alpha * (L + ts) * inv_sqrt3;
-                    if (dist <= rad) {
+                float4 ph = __ldg(a.rx_df + 2 * rx_id), pl = __ldg(a.rx_df + 2 * rx_id + 1);
+                df3 R{df_make(ph.x, pl.x), df_make(ph.y, pl.y), df_make(ph.z, pl.z)};
+                df3 v = df3_sub(R, o);
+                df ts = df3_dot(v, d);
+                if (!(ts.hi < 0.f) && !(hit && df_lt(t_hit, ts))) {
+                    df3 w = df3_sub(df3_scale(d, ts), v);   // o + t* d - Rx
+                    df dist2 = df3_dot(w, w);
+                    df s = df_add(L, ts);
+                    df rad2 = df_mul(a2o3, df_mul(s, s));
+                    if (df_le(dist2, rad2) && !(ts.hi == 0.f && ts.lo < 0.f)) {
                         uint32_t key[kKeyWords];
                         key[0] = (uint32_t)rx_id;
                         key[1] = (uint32_t)a.bounce;
                         for (int k = 0; k < kKmax; ++k)
                             key[2 + k] = k < a.bounce ? (uint32_t)a.seq[(int64_t)k * a.R + ray] : 0xffffffffu;
-                        unsigned long long val =
-                            ((unsigned long long)__float_as_uint((float)dist) << 32) | ray;
+                        float dist = sqrtf(fmaxf(dist2.hi, 0.f));
+                        unsigned long long val = ((unsigned long long)__float_as_uint(dist) << 32) | ray;
                         ht_insert(a, key, val);
                         atomicAdd(&a.cnt->candidates, 1ull);
                     }
@@ -419,8 +431,14 @@ __device__ void receive(const TraceArgs& a, d3 o, d3 d, double L, double t_hit, 
 }
 
 // ---------------------------------------------------------------- bounce kernel
+__device__ __forceinline__ df3 ld_plane_n(const float4* plane, int32_t j, df& c) {
+    float4 h = __ldg(plane + 2 * j), l = __ldg(plane + 2 * j + 1);
+    c = df_make(h.w, l.w);
+    return df3{df_make(h.x, l.x), df_make(h.y, l.y), df_make(h.z, l.z)};
+}
+
 __global__ void __launch_bounds__(kTraceThreads)
-k_trace_bounce(const __grid_constant__ TraceArgs a, const __grid_constant__ Ico ico) {
+k_trace_bounce(const __grid_constant__ TraceArgs a) {
     int stack[kStack];
     const int lane = threadIdx.x & 31;
     const unsigned long long n_in = a.bounce == 0 ? (unsigned long long)a.R : *a.n_in;
@@ -433,64 +451,79 @@ k_trace_bounce(const __grid_constant__ TraceArgs a, const __grid_constant__ Ico 
         bool survive = false;
         RayRec out;
         if (i < n_in) {
-            d3 o, d;
-            double L;
+            df3 o, d;
+            df L;
             uint32_t ray;
             int prev;
             if (a.bounce == 0) {
                 ray = (uint32_t)i;
-                o = mk3(a.tx[0], a.tx[1], a.tx[2]);
-                d = geodesic_dir(ico, a.N, ray);
-                L = 0.0;
+                o = df3{df_make(a.tx_h[0], a.tx_l[0]), df_make(a.tx_h[1], a.tx_l[1]),
+                        df_make(a.tx_h[2], a.tx_l[2])};
+                float4 da = __ldg(a.dir_a + i);
+                float2 db = __ldg(a.dir_b + i);
+                d = df3{df_make(da.x, da.w), df_make(da.y, db.x), df_make(da.z, db.y)};
+                L = df_make(0.f, 0.f);
                 prev = -1;
             } else {
                 const RayRec* q = a.qin + i;
-                o = ld3(q->o);
-                d = ld3(q->d);
-                L = q->L;
-                ray = q->ray;
-                prev = q->prev;
+                const float4* q4 = reinterpret_cast<const float4*>(q);
+                float4 w0 = q4[0], w1 = q4[1], w2 = q4[2], w3 = q4[3];
+                o = df3{df_make(w0.x, w0.w), df_make(w0.y, w1.x), df_make(w0.z, w1.y)};
+                d = df3{df_make(w1.z, w2.y), df_make(w1.w, w2.z), df_make(w2.x, w2.w)};
+                L = df_make(w3.x, w3.y);
+                ray = __float_as_uint(w3.z);
+                prev = __float_as_int(w3.w);
             }
-            Ray32 r = make_ray32(o, d);
+            Ray32 r = make_ray32(df3_hi(o), df3_hi(d));
             int32_t j = -1;
-            double t64 = INFINITY;
+            df t = df_make(INFINITY, 0.f);
             if (a.T > 0) {
                 Trav tv;
                 j = traverse32(a, r, prev, tv, stack);
-                if (tv.overflow) {
-                    j = traverse64(a, o, d, prev, t64, stack);
-                    atomicAdd(&a.cnt->fp64_segments, 1ull);
-                } else if (tv.nu > 0) {
-                    // exact rule over the certain best and the uncertain faces
-                    int32_t bj = -1, bface = 0x7fffffff;
-                    double bt = INFINITY;
-                    for (int k = -1; k < tv.nu; ++k) {
-                        int32_t c = k < 0 ? tv.best_j : tv.unc[k];
-                        if (c < 0) continue;
-                        double tc;
-                        int face = __float_as_int(__ldg(a.tris + 3 * c + 1).w);
-                        if (mt64(a.tris, c, o, d, tc) && (tc < bt || (tc == bt && face < bface))) {
-                            bt = tc; bj = c; bface = face;
+                if (tv.overflow || tv.nu > 0) {
+                    d3 o64 = mk3(df_to_double(o.x), df_to_double(o.y), df_to_double(o.z));
+                    d3 d64 = mk3(df_to_double(d.x), df_to_double(d.y), df_to_double(d.z));
+                    double t64 = INFINITY;
+                    if (tv.overflow) {
+                        j = traverse64(a, o64, d64, prev, t64, stack);
+                        atomicAdd(&a.cnt->fp64_segments, 1ull);
+                    } else {
+                        // exact rule over the certain best and the uncertain faces
+                        int32_t bj = -1, bface = 0x7fffffff;
+                        for (int k = -1; k < tv.nu; ++k) {
+                            int32_t c = k < 0 ? tv.best_j : tv.unc[k];
+                            if (c < 0) continue;
+                            double tc;
+                            int face = __float_as_int(__ldg(a.tris + 3 * c + 1).w);
+                            if (mt64(a.tris, c, o64, d64, tc) && (tc < t64 || (tc == t64 && face < bface))) {
+                                t64 = tc; bj = c; bface = face;
+                            }
                         }
+                        j = bj;
+                        atomicAdd(&a.cnt->fp64_tests, (unsigned long long)(tv.nu + (tv.best_j >= 0)));
                     }
-                    j = bj;
-                    t64 = bt;
-                    atomicAdd(&a.cnt->fp64_tests, (unsigned long long)(tv.nu + (tv.best_j >= 0)));
+                    if (j >= 0) t = df_from_double(t64);
                 } else if (j >= 0) {
-                    d3 n = ld3(a.nrm + 3 * (int64_t)j);
-                    float4 v0 = __ldg(a.tris + 3 * j);
-                    t64 = dot(n, mk3(v0.x, v0.y, v0.z) - o) / dot(n, d);
+                    df c;
+                    df3 n = ld_plane_n(a.plane, j, c);
+                    t = df_div(df_sub(c, df3_dot(n, o)), df3_dot(n, d));
                 }
             }
-            receive(a, o, d, L, t64, j >= 0, r, ray, stack);
+            receive(a, o, d, L, t, j >= 0, r, ray, stack);
             if (j >= 0 && a.bounce < a.K) {
-                d3 n = ld3(a.nrm + 3 * (int64_t)j);
+                df c;
+                df3 n = ld_plane_n(a.plane, j, c);
                 int32_t surf = __float_as_int(__ldg(a.tris + 3 * j).w);
-                d3 o2 = o + d * t64;
-                d3 d2 = d - n * (2.0 * dot(d, n));
-                st3(out.o, o2);
-                st3(out.d, d2);
-                out.L = L + t64;
+                df3 o2 = df3_add(o, df3_scale(d, t));
+                df dn = df3_dot(d, n);
+                df3 d2 = df3_sub(d, df3_scale(n, df_make(2.f * dn.hi, 2.f * dn.lo)));
+                df L2 = df_add(L, t);
+                out.oh[0] = o2.x.hi; out.oh[1] = o2.y.hi; out.oh[2] = o2.z.hi;
+                out.ol[0] = o2.x.lo; out.ol[1] = o2.y.lo; out.ol[2] = o2.z.lo;
+                out.dh[0] = d2.x.hi; out.dh[1] = d2.y.hi; out.dh[2] = d2.z.hi;
+                out.dl[0] = d2.x.lo; out.dl[1] = d2.y.lo; out.dl[2] = d2.z.lo;
+                out.Lh = L2.hi;
+                out.Ll = L2.lo;
                 out.ray = ray;
                 out.prev = surf;
                 a.seq[(int64_t)a.bounce * a.R + ray] = surf;
@@ -504,10 +537,28 @@ k_trace_bounce(const __grid_constant__ TraceArgs a, const __grid_constant__ Ico 
             ob = __shfl_sync(0xffffffffu, ob, 0);
             if (survive) {
                 unsigned long long pos = ob + __popc(mask & ((1u << lane) - 1u));
-                a.qout[pos] = out;
+                float4* q4 = reinterpret_cast<float4*>(a.qout + pos);
+                q4[0] = make_float4(out.oh[0], out.oh[1], out.oh[2], out.ol[0]);
+                q4[1] = make_float4(out.ol[1], out.ol[2], out.dh[0], out.dh[1]);
+                q4[2] = make_float4(out.dh[2], out.dl[0], out.dl[1], out.dl[2]);
+                q4[3] = make_float4(out.Lh, out.Ll, __uint_as_float(out.ray), __int_as_float(out.prev));
             }
         }
     }
+}
+
+__global__ void k_rx_df(const double* __restrict__ rx, int32_t n, float4* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    df x = df_from_double(rx[3 * i]), y = df_from_double(rx[3 * i + 1]), z = df_from_double(rx[3 * i + 2]);
+    out[2 * i] = make_float4(x.hi, y.hi, z.hi, 0.f);
+    out[2 * i + 1] = make_float4(x.lo, y.lo, z.lo, 0.f);
+}
+
+__global__ void k_alpha_df(const double* __restrict__ alpha, float4* __restrict__ out) {
+    double al = *alpha;
+    df a1 = df_from_double(al), a2 = df_from_double(al * al / 3.0);
+    *out = make_float4(a1.hi, a1.lo, a2.hi, a2.lo);
 }
 
 __global__ void k_rx_boxes(const double* __restrict__ rx, int32_t n, float* __restrict__ box) {
@@ -562,6 +613,18 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
         SBR_TRY_CUDA(cudaGetLastError());
         SBR_TRY(build_lbvh(rxbox, tr->n_rx, 0.0f, &rxb, rx_depth, s));
     }
+    float4* rx_df = nullptr;
+    float4* alpha_df = nullptr;
+    SBR_TRY(dalloc_n(&alpha_df, 1, s));
+    ::sbr::note_launch(), k_alpha_df<<<1, 1, 0, s>>>(tr->d_alpha, alpha_df);
+    if (tr->n_rx > 0) {
+        SBR_TRY(dalloc_n(&rx_df, 2 * (size_t)tr->n_rx, s));
+        ::sbr::note_launch(), k_rx_df<<<(tr->n_rx + 255) / 256, 256, 0, s>>>(tr->rx, tr->n_rx, rx_df);
+    }
+    SBR_TRY_CUDA(cudaGetLastError());
+    const float4* dir_a = nullptr;
+    const float2* dir_b = nullptr;
+    SBR_TRY(dir_table(p.subdiv_N, &dir_a, &dir_b, s));
     RayRec *q0 = nullptr, *q1 = nullptr;
     int32_t* seq = nullptr;
     if (K > 0) {
@@ -572,25 +635,30 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     TraceArgs a{};
     a.nodes = b->tree.nodes;
     a.tris = b->tri_sorted;
-    a.nrm = b->nrm_sorted;
+    a.plane = b->plane_sorted;
     a.T = b->T;
     a.rx_nodes = rxb.nodes;
     a.rx_order = rxb.order;
-    a.rx = tr->rx;
+    a.rx_df = rx_df;
     a.rx_root = rxb.d_root;
     a.n_rx = tr->n_rx;
-    a.alpha = tr->d_alpha;
+    a.alpha_df = alpha_df;
+    a.dir_a = dir_a;
+    a.dir_b = dir_b;
     a.N = p.subdiv_N;
     a.K = K;
     a.R = R;
-    for (int k = 0; k < 3; ++k) a.tx[k] = p.tx[k];
+    for (int k = 0; k < 3; ++k) {
+        df x = df_from_double(p.tx[k]);
+        a.tx_h[k] = x.hi;
+        a.tx_l[k] = x.lo;
+    }
     a.seq = seq;
     a.ht_state = tr->ht_state;
     a.ht_key = tr->ht_key;
     a.ht_val = tr->ht_val;
     a.ht_mask = (uint32_t)(cap - 1);
     a.cnt = tr->cnt;
-    Ico ico = make_ico();
     int grid = trace_grid();
     const bool timing = (p.flags & SBR_TRACE_TIMING) != 0;
     if (timing) {
@@ -604,7 +672,7 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
         a.n_in = &tr->cnt->queue[bnc];
         a.n_out = &tr->cnt->queue[bnc + 1];
         a.work = &tr->cnt->work[bnc];
-        ::sbr::note_launch(), k_trace_bounce<<<grid, kTraceThreads, 0, s>>>(a, ico);
+        ::sbr::note_launch(), k_trace_bounce<<<grid, kTraceThreads, 0, s>>>(a);
         SBR_TRY_CUDA(cudaGetLastError());
         if (timing) SBR_TRY_CUDA(cudaEventRecord(tr->ev[bnc + 1], s));
     }
@@ -615,7 +683,9 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
         free_lbvh(&rxb, s);
         dfree(rxbox, s);
         dfree(rx_depth, s);
+        dfree(rx_df, s);
     }
+    dfree(alpha_df, s);
     return SBR_OK;
 }
 
