@@ -63,6 +63,29 @@ __device__ __forceinline__ bool point_in_tri(const float* v, d3 p, double tol) {
     return l0 >= -tol && l1 >= -tol && l2 >= -tol;
 }
 
+// FP32 screen of the same barycentric test: +1 clearly inside, -1 clearly
+// outside, 0 near an edge (then the FP64 test decides). The margin is 1e-3 or,
+// for small or thin faces far from the origin, a bound on the FP32 error of
+// the barycentrics (rounding of p and of the products, ~ eps (|a| + |w|) / (size sin^2)).
+__device__ __forceinline__ int screen_in_tri(const float* v, float3 p) {
+    float3 a = make_float3(v[0], v[1], v[2]);
+    float3 e1 = make_float3(v[3] - a.x, v[4] - a.y, v[5] - a.z);
+    float3 e2 = make_float3(v[6] - a.x, v[7] - a.y, v[8] - a.z);
+    float3 w = make_float3(p.x - a.x, p.y - a.y, p.z - a.z);
+    float d00 = e1.x * e1.x + e1.y * e1.y + e1.z * e1.z, d01 = e1.x * e2.x + e1.y * e2.y + e1.z * e2.z;
+    float d11 = e2.x * e2.x + e2.y * e2.y + e2.z * e2.z;
+    float d20 = w.x * e1.x + w.y * e1.y + w.z * e1.z, d21 = w.x * e2.x + w.y * e2.y + w.z * e2.z;
+    float den = d00 * d11 - d01 * d01;
+    if (!(den > 0.f)) return 0;
+    float l1 = (d11 * d20 - d01 * d21) / den, l2 = (d00 * d21 - d01 * d20) / den;
+    float m = fminf(fminf(l1, l2), 1.f - l1 - l2);
+    float ext = fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fabsf(a.z)) +
+                fmaxf(fmaxf(fabsf(w.x), fabsf(w.y)), fabsf(w.z)) + 1.f;
+    float s2 = d00 + d11;
+    float margin = fmaxf(1e-3f, 16.f * 5.9604645e-8f * ext * s2 * sqrtf(s2) / den);
+    return m > margin ? 1 : (m < -margin ? -1 : 0);
+}
+
 __device__ __forceinline__ void angles_deg(d3 v, double* out) {
     out[0] = atan2(v.y, v.x) * (180.0 / kPi);
     out[1] = atan2(v.z, hypot(v.x, v.y)) * (180.0 / kPi);
@@ -161,7 +184,12 @@ __global__ void k_refine(const __grid_constant__ RefineArgs a) {
         const int32_t qa = a.s_off[s], qb = a.s_off[s + 1];
         for (int32_t base = qa; base < qb; base += 32) {
             int32_t q = base + lane;
-            bool in = q < qb && point_in_tri(a.tri + 9 * (int64_t)a.s_tri[q], P[k], 1e-9);
+            bool in = false;
+            if (q < qb) {
+                const float* v = a.tri + 9 * (int64_t)a.s_tri[q];
+                int sc = screen_in_tri(v, make_float3((float)P[k].x, (float)P[k].y, (float)P[k].z));
+                in = sc > 0 || (sc == 0 && point_in_tri(v, P[k], 1e-9));
+            }
             unsigned m32 = __ballot_sync(0xffffffffu, in);
             if (m32) {  // faces are listed in ascending id: the lowest lane is the lowest id
                 found = a.s_tri[base + __ffs(m32) - 1];

@@ -108,6 +108,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// exp(-j 2 pi c) for a phase of c cycles: reduce to [-1/2, 1/2] exactly, then
+// the hardware sine/cosine, whose absolute error on [-pi, pi] (below 1e-6) is
+// well under the 2^-16 resolution of the BF16 hi/lo operands
+__device__ __forceinline__ void phasor(float cycles, float& s, float& c) {
+    float r = cycles - rintf(cycles);
+    __sincosf(-6.283185307179586f * r, &s, &c);
+}
+
 // x = hi + lo, both BF16; returns the two as raw 16-bit patterns
 __device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) {
     __nv_bfloat16 h = __float2bfloat16_rn(x);
@@ -130,7 +138,7 @@ struct TcArgs {
     unsigned int* status;
 };
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constant__ TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constant__ TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA_hi = smem;
@@ -170,15 +178,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
         for (int c = 0; c < nch && !failed; ++c) {
             const int nb = a.n0 + c * kChunkP;
             const int cnt = min(kChunkP, a.n0 + a.nrefl - nb);
-            // A' tile: 64 receive elements x 32 paths, each a 2x2 real block
+            // A' tile: 64 receive elements x 32 paths, each a 2x2 real block;
+            // consecutive threads take consecutive receive elements (coalesced)
+#pragma unroll 4
             for (int e = tid; e < 64 * kChunkP; e += kTcThreads) {
-                int ql = e / kChunkP, nl = e % kChunkP;
+                int ql = e & 63, nl = e >> 6;
                 int q = q0 + ql, n = nb + nl;
                 float ar = 0.f, ai = 0.f;
                 if (nl < cnt && q < a.Nr) {
-                    float2 ww = a.w[(int64_t)f * a.Pr + n];
+                    float2 ww = __ldg(a.w + (int64_t)f * a.Pr + n);
                     float s, co;
-                    sincospif(-2.0f * foc * a.dr[(int64_t)n * a.Nr + q], &s, &co);
+                    phasor(foc * __ldg(a.dr + (int64_t)n * a.Nr + q), s, co);
                     ar = ww.x * co - ww.y * s;
                     ai = ww.x * s + ww.y * co;
                 }
@@ -192,12 +202,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
                 *(uint32_t*)(sA_hi + o1) = (uint32_t)h2 | ((uint32_t)h0 << 16);
                 *(uint32_t*)(sA_lo + o1) = (uint32_t)l2 | ((uint32_t)l0 << 16);
             }
-            // B' tile (stored N x K): 256 transmit elements x 32 paths
+            // B' tile (stored N x K): 256 transmit elements x 32 paths;
+            // consecutive threads take consecutive transmit elements (coalesced)
+#pragma unroll 8
             for (int e = tid; e < kTileN * kChunkP; e += kTcThreads) {
-                int pl = e / kChunkP, nl = e % kChunkP;
+                int pl = e & (kTileN - 1), nl = e / kTileN;
                 int p = p0 + pl, n = nb + nl;
                 float vr = 0.f, vi = 0.f;
-                if (nl < cnt && p < a.Nt) sincospif(-2.0f * foc * a.dt[(int64_t)n * a.Nt + p], &vi, &vr);
+                if (nl < cnt && p < a.Nt) phasor(foc * __ldg(a.dt + (int64_t)n * a.Nt + p), vi, vr);
                 uint16_t h0, l0, h1, l1;
                 split_bf16(vr, h0, l0);
                 split_bf16(vi, h1, l1);
@@ -252,17 +264,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
             const int pb = p0 + col0 + 16 * part;
             if (q < a.Nr) {
                 float2* dst = a.H + ((int64_t)f * a.Nr + q) * a.Nt;
-                for (int k = 0; k < 16; ++k) {
-                    int p = pb + k;
-                    if (p >= a.Nt) break;
-                    float hr = re[k], hi = im[k];
-                    if (a.los >= 0) {
-                        float s, co;
-                        sincospif(-2.0f * foc * a.dlos[(int64_t)q * a.Nt + p], &s, &co);
-                        hr += wl.x * co - wl.y * s;
-                        hi += wl.x * s + wl.y * co;
+                if (a.los >= 0) {
+                    float dl[16];
+                    const float* src = a.dlos + (int64_t)q * a.Nt + pb;
+                    if (pb + 16 <= a.Nt && ((((uintptr_t)src) & 15) == 0)) {
+                        for (int k = 0; k < 4; ++k) {
+                            float4 v4 = __ldg(reinterpret_cast<const float4*>(src) + k);
+                            dl[4 * k] = v4.x; dl[4 * k + 1] = v4.y; dl[4 * k + 2] = v4.z; dl[4 * k + 3] = v4.w;
+                        }
+                    } else {
+                        for (int k = 0; k < 16; ++k) dl[k] = pb + k < a.Nt ? __ldg(src + k) : 0.f;
                     }
-                    dst[p] = make_float2(hr, hi);
+                    for (int k = 0; k < 16; ++k) {
+                        float s, co;
+                        sincospif(-2.0f * foc * dl[k], &s, &co);
+                        re[k] += wl.x * co - wl.y * s;
+                        im[k] += wl.x * s + wl.y * co;
+                    }
+                }
+                if (pb + 16 <= a.Nt && ((((uintptr_t)(dst + pb)) & 15) == 0)) {
+                    float4* d4 = reinterpret_cast<float4*>(dst + pb);
+                    for (int k = 0; k < 8; ++k)
+                        d4[k] = make_float4(re[2 * k], im[2 * k], re[2 * k + 1], im[2 * k + 1]);
+                } else {
+                    for (int k = 0; k < 16 && pb + k < a.Nt; ++k) dst[pb + k] = make_float2(re[k], im[k]);
                 }
             }
         }
@@ -321,7 +346,9 @@ sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* 
     a.freqs = freqs; a.dt = dt; a.dr = dr; a.w = w; a.dlos = dl; a.H = H; a.status = status;
     SBR_TRY_CUDA(cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     int64_t items = (int64_t)F * ((Nr + 63) / 64) * ((Nt + kTileN - 1) / kTileN);
-    int grid = (int)std::min<int64_t>(items, (int64_t)sm_count());
+    // two CTAs per SM (97 KB shared memory and 256 TMEM columns each): one CTA's
+    // MMA and epilogue overlap the other's phasor generation
+    int grid = (int)std::min<int64_t>(items, 2 * (int64_t)sm_count());
     ::sbr::note_launch(), k_synth_tc<<<grid, kTcThreads, kSmemBytes, s>>>(a);
     SBR_TRY_CUDA(cudaGetLastError());
     unsigned h_status = 0;
