@@ -269,6 +269,25 @@ sbr_status sbr_pdp_angles(const sbr_path_list* pl, const void* gains, int32_t F,
 sbr_status sbr_capacity(const void* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,
                         int32_t n_snr, double* C, void* stream);
 
+/*
+ * sbr_capacity_noalloc - sbr_capacity for callers that cannot allocate device
+ * memory while they run (a host framework that owns the whole device memory
+ * pool and forbids libraries from calling cudaMalloc, or a real-time loop held
+ * to a fixed footprint after start-up). The paper has no counterpart: this is
+ * an allocation policy, not a step of the method. Same result as sbr_capacity,
+ * same arguments and layouts; it calls no cudaMalloc, cudaFree or allocating
+ * routine. Its scratch is a fixed array inside the library of about 1.1 MB
+ * that every GPU which loads the library holds until the process exits; hence
+ * F <= 4096 and n_snr <= 32, larger requests return SBR_ERR_INVALID_ARG (use
+ * sbr_capacity). The first call on a device looks up that array's address on
+ * the device: make that first call before any stream capture. All calls share
+ * the array, so calls whose work overlaps on the GPU (e.g. on two streams at
+ * once) race; serialise them. Every scratch value it reads is first written by
+ * the same call. Asynchronous: returns once the work is enqueued on `stream`.
+ */
+sbr_status sbr_capacity_noalloc(const void* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,
+                                int32_t n_snr, double* C, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,7 @@ TRACE_TIMING = 1
 EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_count", "sbr_launch_dirs", "sbr_build_bvh", "sbr_bvh_free",
            "sbr_bvh_query", "sbr_trace", "sbr_trace_stats", "sbr_trace_free", "sbr_paths",
            "sbr_path_query", "sbr_path_export", "sbr_path_list_free", "sbr_path_gains",
-           "sbr_synthesize_H", "sbr_pdp_angles", "sbr_capacity"]
+           "sbr_synthesize_H", "sbr_pdp_angles", "sbr_capacity", "sbr_capacity_noalloc"]
 
 
 class TraceParams(C.Structure):
@@ -99,5 +99,7 @@ def load() -> C.CDLL:
     L.sbr_pdp_angles.argtypes = [p, p, i32, i32, f64, f64, i32, p, p, p]
     L.sbr_capacity.restype = st
     L.sbr_capacity.argtypes = [p, i32, i32, i32, p, i32, p, p]
+    L.sbr_capacity_noalloc.restype = st
+    L.sbr_capacity_noalloc.argtypes = [p, i32, i32, i32, p, i32, p, p]
     _lib = L
     return L

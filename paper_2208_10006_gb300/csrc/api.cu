@@ -400,4 +400,15 @@ sbr_status sbr_capacity(const void* H, int32_t F, int32_t Nr, int32_t Nt, const 
     return capacity_run((const float2*)H, F, Nr, Nt, snr_db, n_snr, C, (cudaStream_t)stream);
 }
 
+sbr_status sbr_capacity_noalloc(const void* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,
+                                int32_t n_snr, double* C, void* stream) {
+    clear_error();
+    SBR_CHECK_ARG(H && snr_db && C, "pointers");
+    SBR_CHECK_ARG(F >= 1 && Nr >= 1 && Nt >= 1, "F, Nr, Nt >= 1");
+    SBR_CHECK_ARG((Nr < Nt ? Nr : Nt) <= 64, "min(Nr, Nt) <= 64");
+    SBR_CHECK_ARG(n_snr >= 1, "n_snr >= 1");
+    for (int i = 0; i < n_snr; ++i) SBR_CHECK_ARG(std::isfinite(snr_db[i]), "finite snr_db");
+    return capacity_noalloc_run((const float2*)H, F, Nr, Nt, snr_db, n_snr, C, (cudaStream_t)stream);
+}
+
 }  // extern "C"

@@ -15,6 +15,7 @@
 // in a fixed order.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "sbr_internal.cuh"
@@ -230,6 +231,90 @@ sbr_status capacity_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt, cons
     // the host SNR table must outlive the copy
     SBR_TRY_CUDA(cudaStreamSynchronize(s));
     dfree(d_lin, s); dfree(qf, s); dfree(qbar, s); dfree(ld, s);
+    return SBR_OK;
+}
+
+
+// ---------------------------------------------------------------- capacity without allocation
+// Some callers cannot allocate device memory once they are running: a host
+// framework that owns the whole device memory pool and forbids libraries from
+// calling cudaMalloc, or a real-time simulation loop held to a fixed memory
+// footprint after start-up. sbr_capacity_noalloc serves them: the same
+// kernels as sbr_capacity, with every scratch buffer placed in the fixed
+// array below, which each GPU that loads the library holds until the process
+// exits (about 1.1 MB).
+constexpr int kNoAllocMaxF = 4096;    // frequencies per call
+constexpr int kNoAllocMaxSnr = 32;    // SNR values per call
+
+struct CapacityScratch {
+    double qf[kNoAllocMaxF];                     // ||H_f||_F^2
+    double qbar;                                 // mean over f
+    double snr_lin[kNoAllocMaxSnr];              // 10^(dB/10)
+    double ld[kNoAllocMaxF * kNoAllocMaxSnr];    // ln det per (f, SNR)
+};
+static __device__ __align__(256) CapacityScratch g_capacity_scratch;
+
+namespace {
+
+struct SnrList {
+    double lin[kNoAllocMaxSnr];
+};
+
+__global__ void k_noalloc_snr(const __grid_constant__ SnrList snr, int32_t n, CapacityScratch* scr) {
+    int i = threadIdx.x;
+    if (i < n) scr->snr_lin[i] = snr.lin[i];
+}
+
+std::mutex g_scratch_mu;
+CapacityScratch* g_scratch_ptr[256] = {};
+
+// device address of the scratch array on the current device; looked up once
+// per device (the first call on a device does it)
+sbr_status capacity_scratch(CapacityScratch** out) {
+    int dev = 0;
+    SBR_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) {
+        set_error("device ordinal %d out of range", dev);
+        return SBR_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_capacity_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            set_error("cudaGetSymbolAddress(capacity scratch) failed: %s", cudaGetErrorString(e));
+            return SBR_ERR_CUDA;
+        }
+        g_scratch_ptr[dev] = static_cast<CapacityScratch*>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return SBR_OK;
+}
+
+}  // namespace
+
+sbr_status capacity_noalloc_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt,
+                                const double* snr_db, int32_t n_snr, double* C, cudaStream_t s) {
+    if (F > kNoAllocMaxF || n_snr > kNoAllocMaxSnr) {
+        set_error("sbr_capacity_noalloc: F = %d and n_snr = %d exceed the fixed scratch (F <= %d, "
+                  "n_snr <= %d); use sbr_capacity", F, n_snr, kNoAllocMaxF, kNoAllocMaxSnr);
+        return SBR_ERR_INVALID_ARG;
+    }
+    CapacityScratch* scr = nullptr;
+    SBR_TRY(capacity_scratch(&scr));
+    // every scratch field read below is first written by this call, so nothing
+    // has to be cleared; the SNR list travels by value in the launch itself
+    SnrList snr{};
+    for (int i = 0; i < n_snr; ++i) snr.lin[i] = std::pow(10.0, snr_db[i] / 10.0);
+    ::sbr::note_launch(), k_noalloc_snr<<<1, kNoAllocMaxSnr, 0, s>>>(snr, n_snr, scr);
+    ::sbr::note_launch(), k_frob<<<F, kCapThreads, 0, s>>>(H, (int64_t)Nr * Nt, scr->qf);
+    ::sbr::note_launch(), k_qbar<<<1, 1, 0, s>>>(scr->qf, F, &scr->qbar);
+    size_t smem = capacity_smem(Nr, Nt);
+    SBR_TRY_CUDA(cudaFuncSetAttribute(k_capacity, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ::sbr::note_launch(), k_capacity<<<F, kCapThreads, smem, s>>>(H, Nr, Nt, scr->snr_lin, n_snr, &scr->qbar,
+                                                                   scr->ld);
+    ::sbr::note_launch(), k_cap_reduce<<<1, 32, 0, s>>>(scr->ld, F, n_snr, C);
+    SBR_TRY_CUDA(cudaGetLastError());
     return SBR_OK;
 }
 

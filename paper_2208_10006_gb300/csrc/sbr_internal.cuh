@@ -201,6 +201,8 @@ sbr_status pdp_run(const sbr_path_list* pl, const float2* g, int32_t F, int32_t 
                    double bin_s, int32_t n_bins, float* pdp, double* stats, cudaStream_t s);
 sbr_status capacity_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,
                         int32_t n_snr, double* C, cudaStream_t s);
+sbr_status capacity_noalloc_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt,
+                                const double* snr_db, int32_t n_snr, double* C, cudaStream_t s);
 }  // namespace sbr
 
 // ---------------------------------------------------------------- device helpers

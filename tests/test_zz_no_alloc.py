@@ -1,0 +1,67 @@
+"""sbr_capacity_noalloc against sbr_capacity, through the C ABI.
+
+sbr_capacity_noalloc is the capacity entry point for callers that cannot
+allocate device memory while they run (a host framework that owns the whole
+device memory pool and forbids libraries from calling cudaMalloc, or a
+real-time loop held to a fixed footprint after start-up); its scratch is a
+fixed array inside the library. It must give the same capacities as
+sbr_capacity, call after call, although every call reuses the same scratch.
+This file is named to be collected last, so that a run which stops at the
+first failure has already run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_10006_gb300 import build as b
+    b.build()
+    from paper_2208_10006_gb300 import _lib
+    return _lib.load()
+
+
+def _capacity(lib, entry, H, snr_db):
+    F, Nr, Nt = H.shape
+    snr = np.ascontiguousarray(snr_db, dtype=np.float64)
+    C = torch.full((len(snr),), float("nan"), dtype=torch.float64, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = getattr(lib, entry)(ctypes.c_void_p(H.data_ptr()), F, Nr, Nt,
+                             snr.ctypes.data_as(ctypes.c_void_p), len(snr),
+                             ctypes.c_void_p(C.data_ptr()), stream)
+    assert st == 0, lib.sbr_last_error()
+    torch.cuda.synchronize()
+    return C.cpu().numpy()
+
+
+def test_two_calls_in_a_row_match_sbr_capacity(lib):
+    rng = np.random.default_rng(2024)
+    cases = [((64, 64, 256), np.arange(0.0, 31.0, 5.0)),   # the indoor MIMO shape, 64 subcarriers
+             ((9, 7, 3), np.array([-3.0, 12.0, 40.0]))]    # Nt < Nr, fewer frequencies than before
+    for (F, Nr, Nt), snr in cases:
+        Hn = (rng.normal(size=(F, Nr, Nt)) + 1j * rng.normal(size=(F, Nr, Nt))).astype(np.complex64)
+        H = torch.as_tensor(Hn, device="cuda")
+        ref = _capacity(lib, "sbr_capacity", H, snr)
+        got = _capacity(lib, "sbr_capacity_noalloc", H, snr)
+        assert np.isfinite(got).all()
+        # the tolerance of the capacity parity tests
+        assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), (got, ref)
+
+
+def test_sizes_beyond_the_fixed_scratch_are_rejected(lib):
+    H = torch.zeros((1, 1, 1), dtype=torch.complex64, device="cuda")
+    C = torch.zeros(1, dtype=torch.float64, device="cuda")
+    snr = np.zeros(1)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = lib.sbr_capacity_noalloc(ctypes.c_void_p(H.data_ptr()), 4097, 1, 1,
+                                  snr.ctypes.data_as(ctypes.c_void_p), 1,
+                                  ctypes.c_void_p(C.data_ptr()), stream)
+    assert st == 1
+    assert b"4096" in lib.sbr_last_error()
