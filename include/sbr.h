@@ -192,8 +192,14 @@ typedef struct {
     int64_t n_invalid;    /* dropped by refinement */
     int32_t n_rx;
     int32_t max_bounces;
+    int32_t status;       /* device-side failures of calls on this list so far */
+    int32_t reserved;
 } sbr_path_info;
 
+/* Synchronous: waits for the list's stream and also reports (in status and
+ * as the return value) any device-side failure recorded by earlier
+ * asynchronous calls on this list, e.g. a bounded wait that gave up in
+ * sbr_synthesize_H. */
 sbr_status sbr_path_query(const sbr_path_list* pl, sbr_path_info* out);
 
 /*

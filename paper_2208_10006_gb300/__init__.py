@@ -189,7 +189,7 @@ class PathList:
         i = _lib.PathInfo()
         _check(_L().sbr_path_query(self._h, C.byref(i)))
         return dict(n_paths=i.n_paths, n_keys=i.n_keys, n_invalid=i.n_invalid, n_rx=i.n_rx,
-                    max_bounces=i.max_bounces)
+                    max_bounces=i.max_bounces, status=i.status)
 
     def export(self, stream=None) -> dict:
         dev = _dev()

@@ -44,7 +44,8 @@ class BvhInfo(C.Structure):
 
 class PathInfo(C.Structure):
     _fields_ = [("n_paths", C.c_int64), ("n_keys", C.c_int64), ("n_invalid", C.c_int64),
-                ("n_rx", C.c_int32), ("max_bounces", C.c_int32)]
+                ("n_rx", C.c_int32), ("max_bounces", C.c_int32), ("status", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 assert C.sizeof(TraceParams) == 64

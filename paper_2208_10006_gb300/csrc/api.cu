@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "sbr_internal.cuh"
@@ -32,7 +33,26 @@ sbr_status status_from_bits(uint32_t bits) {
     return SBR_OK;
 }
 
+// The stream-ordered pool of each device keeps freed blocks instead of returning
+// them to the driver at every synchronisation (its default), so that the ray
+// queues of consecutive traces reuse the same memory.
+static void keep_pool_memory() {
+    static std::mutex mu;
+    static bool done[256] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+}
+
 sbr_status dalloc(void** p, size_t bytes, cudaStream_t s) {
+    keep_pool_memory();
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -289,12 +309,18 @@ sbr_status sbr_paths(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
 sbr_status sbr_path_query(const sbr_path_list* pl, sbr_path_info* out) {
     clear_error();
     SBR_CHECK_ARG(pl && out, "path list and out");
+    SBR_SAME_DEVICE(pl);
+    unsigned bits = 0;
+    SBR_TRY_CUDA(cudaMemcpyAsync(&bits, pl->d_status, sizeof bits, cudaMemcpyDeviceToHost, pl->stream));
+    SBR_TRY_CUDA(cudaStreamSynchronize(pl->stream));
     out->n_paths = pl->P;
     out->n_keys = pl->n_keys;
     out->n_invalid = pl->n_invalid;
     out->n_rx = pl->n_rx;
     out->max_bounces = pl->K;
-    return SBR_OK;
+    out->status = (int32_t)status_from_bits(bits);
+    out->reserved = 0;
+    return (sbr_status)out->status;
 }
 
 sbr_status sbr_path_export(const sbr_path_list* pl, int32_t* rx, int32_t* n_bounce, int32_t* surf_seq,
@@ -329,7 +355,7 @@ void sbr_path_list_free(sbr_path_list* pl) {
     cudaStream_t s = pl->stream;
     dfree(pl->rx_xyz, s); dfree(pl->rx, s); dfree(pl->nb, s); dfree(pl->surf, s); dfree(pl->face, s);
     dfree(pl->pts, s); dfree(pl->L, s); dfree(pl->aod, s); dfree(pl->aoa, s); dfree(pl->ray, s);
-    dfree(pl->dist, s); dfree(pl->jones, s); dfree(pl->rx_off, s);
+    dfree(pl->dist, s); dfree(pl->jones, s); dfree(pl->rx_off, s); dfree(pl->d_status, s);
     delete[] pl->h_rx_off;
     delete pl;
 }

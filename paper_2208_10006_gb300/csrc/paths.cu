@@ -370,6 +370,8 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     SBR_TRY(dalloc_n(&pl->dist, Pp, s));
     SBR_TRY(dalloc_n(&pl->jones, Pp * kJones, s));
     SBR_TRY(dalloc_n(&pl->rx_off, (size_t)tr->n_rx + 1, s));
+    SBR_TRY(dalloc_n(&pl->d_status, 1, s));
+    SBR_TRY_CUDA(cudaMemsetAsync(pl->d_status, 0, sizeof(unsigned), s));
     if (n > 0) {
         auto go = [&](auto* in, auto* out, int width) {
             using T = std::remove_pointer_t<decltype(out)>;

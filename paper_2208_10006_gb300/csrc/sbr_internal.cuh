@@ -167,6 +167,7 @@ struct sbr_path_list {
     double* jones = nullptr;    // [P*kJones] polarimetric transfer data (gains)
     int32_t* rx_off = nullptr;  // [n_rx+1] paths of receiver r: [rx_off[r], rx_off[r+1])
     int32_t* h_rx_off = nullptr;  // host copy
+    unsigned int* d_status = nullptr;  // device-side failures of later calls on this list
     cudaStream_t stream = nullptr;
 };
 

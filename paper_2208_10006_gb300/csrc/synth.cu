@@ -18,9 +18,10 @@ namespace sbr {
 namespace {
 
 __global__ void k_prep_delays(int32_t Pr, const int32_t* __restrict__ nb, const double* __restrict__ pts,
-                              d3 T0, d3 R0, const double* __restrict__ tx_elem, int32_t Nt,
-                              const double* __restrict__ rx_elem, int32_t Nr, double* __restrict__ dt,
-                              double* __restrict__ dr) {
+                              d3 T0, const double* __restrict__ R0p, const double* __restrict__ tx_elem,
+                              int32_t Nt, const double* __restrict__ rx_elem, int32_t Nr,
+                              double* __restrict__ dt, double* __restrict__ dr) {
+    const d3 R0 = ld3(R0p);
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t ne = (int64_t)Nt + Nr;
     if (t >= (int64_t)Pr * ne) return;
@@ -56,8 +57,10 @@ __global__ void k_prep_w(int32_t Pr, int32_t F, const float2* __restrict__ g,
     w[f * Pr + n] = make_double2(gg.x * c - gg.y * s, gg.x * s + gg.y * c);
 }
 
-__global__ void k_prep_los(d3 T0, d3 R0, const double* __restrict__ tx_elem, int32_t Nt,
-                           const double* __restrict__ rx_elem, int32_t Nr, double* __restrict__ dlos) {
+__global__ void k_prep_los(d3 T0, const double* __restrict__ R0p, const double* __restrict__ tx_elem,
+                           int32_t Nt, const double* __restrict__ rx_elem, int32_t Nr,
+                           double* __restrict__ dlos) {
+    const d3 R0 = ld3(R0p);
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)Nr * Nt) return;
     int64_t q = t / Nt, p = t - q * Nt;
@@ -91,7 +94,8 @@ constexpr int kSynthThreads = 128;
 
 template <class R>
 __global__ void __launch_bounds__(kSynthThreads)
-k_synth(int32_t F, int32_t Nr, int32_t Nt, int32_t Pr, int32_t los, const double* __restrict__ freqs,
+k_synth(int32_t F, int32_t Nr, int32_t Nt, int32_t Pr, const int32_t* __restrict__ nb0,
+        const double* __restrict__ freqs,
         const typename Cplx<R>::T* __restrict__ w, const R* __restrict__ dt, const R* __restrict__ dr,
         const R* __restrict__ dlos, float2* __restrict__ H) {
     using C2 = typename Cplx<R>::T;
@@ -101,6 +105,7 @@ k_synth(int32_t F, int32_t Nr, int32_t Nt, int32_t Pr, int32_t los, const double
     const int32_t q = blockIdx.y;
     const int32_t f = blockIdx.z;
     const R foc = (R)(freqs[f] / kC0);
+    const int32_t los = (Pr > 0 && *nb0 == 0) ? 0 : -1;
     const bool act = p < Nt;
     R acc_re = 0, acc_im = 0;
     for (int32_t n0 = 0; n0 < Pr; n0 += kSynthThreads) {
@@ -137,20 +142,12 @@ sbr_status synth_prepare(const sbr_path_list* pl, const float2* g, const double*
     const int32_t o0 = pl->h_rx_off[rx_index], o1 = pl->h_rx_off[rx_index + 1];
     sp->Pr = o1 - o0;
     sp->off = o0;
-    sp->los = -1;
-    // the LoS path (no reflection) sorts first among a receiver's paths
-    if (sp->Pr > 0) {
-        int32_t nb0 = 0;
-        SBR_TRY_CUDA(cudaMemcpyAsync(&nb0, pl->nb + o0, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        SBR_TRY_CUDA(cudaStreamSynchronize(s));
-        if (nb0 == 0) sp->los = 0;
-    }
+    // the LoS path (no reflection) sorts first among a receiver's paths; the
+    // kernels read its reflection count and the receiver reference on the device
+    sp->nb0 = pl->nb + o0;
     const int32_t Pr = std::max(sp->Pr, 1);
     d3 T0 = mk3(pl->tx[0], pl->tx[1], pl->tx[2]);
-    double R0h[3];
-    SBR_TRY_CUDA(cudaMemcpyAsync(R0h, pl->rx_xyz + 3 * rx_index, sizeof(R0h), cudaMemcpyDeviceToHost, s));
-    SBR_TRY_CUDA(cudaStreamSynchronize(s));
-    d3 R0 = mk3(R0h[0], R0h[1], R0h[2]);
+    const double* R0 = pl->rx_xyz + 3 * rx_index;
     SBR_TRY(dalloc_n(&sp->dt, (size_t)Pr * Nt, s));
     SBR_TRY(dalloc_n(&sp->dr, (size_t)Pr * Nr, s));
     SBR_TRY(dalloc_n(&sp->w, (size_t)Pr * F, s));
@@ -183,7 +180,7 @@ sbr_status synth_simt_run(const sbr_path_list* pl, const float2* g, const double
     dim3 grid((unsigned)((Nt + kSynthThreads - 1) / kSynthThreads), (unsigned)Nr, (unsigned)F);
     const int32_t Pr = std::max(sp.Pr, 1);
     if (fp64) {
-        ::sbr::note_launch(), k_synth<double><<<grid, kSynthThreads, 0, s>>>(F, Nr, Nt, sp.Pr, sp.los, freqs, sp.w, sp.dt,
+        ::sbr::note_launch(), k_synth<double><<<grid, kSynthThreads, 0, s>>>(F, Nr, Nt, sp.Pr, sp.nb0, freqs, sp.w, sp.dt,
                                                        sp.dr, sp.dlos, H);
         SBR_TRY_CUDA(cudaGetLastError());
     } else {
@@ -197,7 +194,7 @@ sbr_status synth_simt_run(const sbr_path_list* pl, const float2* g, const double
         ::sbr::note_launch(), k_convert<float><<<nb256((int64_t)Pr * Nr), 256, 0, s>>>(sp.dr, dr, (int64_t)Pr * Nr);
         ::sbr::note_launch(), k_convert<float><<<nb256((int64_t)Nr * Nt), 256, 0, s>>>(sp.dlos, dl, (int64_t)Nr * Nt);
         ::sbr::note_launch(), k_convert2<float><<<nb256((int64_t)Pr * F), 256, 0, s>>>(sp.w, w, (int64_t)Pr * F);
-        ::sbr::note_launch(), k_synth<float><<<grid, kSynthThreads, 0, s>>>(F, Nr, Nt, sp.Pr, sp.los, freqs, w, dt, dr, dl, H);
+        ::sbr::note_launch(), k_synth<float><<<grid, kSynthThreads, 0, s>>>(F, Nr, Nt, sp.Pr, sp.nb0, freqs, w, dt, dr, dl, H);
         SBR_TRY_CUDA(cudaGetLastError());
         dfree(dt, s); dfree(dr, s); dfree(dl, s); dfree(w, s);
     }

@@ -8,7 +8,8 @@ namespace sbr {
 struct SynthPrep {
     int32_t Pr = 0;           // paths of the receiver
     int32_t off = 0;          // first path index in the path list
-    int32_t los = -1;         // local index of the LoS path, or -1
+    const int32_t* nb0 = nullptr;  // device: reflections of the receiver's first path
+                                   // (0 = it is the LoS path, which sorts first)
     double* dt = nullptr;     // [Pr * Nt]  |T_p - P1| - |T_0 - P1|
     double* dr = nullptr;     // [Pr * Nr]  |R_q - Pm| - |R_0 - Pm|
     double2* w = nullptr;     // [F * Pr]   g_n(f) exp(-j 2 pi frac(f L_n / c))

@@ -126,9 +126,8 @@ __device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) 
 
 struct TcArgs {
     int32_t F, Nr, Nt;
-    int32_t n0, nrefl;         // reflected paths: local indices [n0, n0 + nrefl)
-    int32_t Pr;                // stride of w rows
-    int32_t los;               // local LoS index or -1
+    int32_t Pr;                // paths of the receiver (stride of w rows)
+    const int32_t* nb0;        // reflections of the first path: 0 = LoS at local index 0
     const double* freqs;
     const float* dt;           // [Pr][Nt]
     const float* dr;           // [Pr][Nr]
@@ -167,17 +166,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
     uint32_t phase = 0;
     bool failed = false;
 
+    // reflected paths are the local indices [n0, n0 + nrefl); the LoS path, when
+    // present, is local index 0 and is added exactly in the epilogue
+    const int los = (a.Pr > 0 && *a.nb0 == 0) ? 0 : -1;
+    const int n0 = los == 0 ? 1 : 0;
+    const int nrefl = a.Pr - n0;
     const int mtiles = (a.Nr + 63) / 64, ntiles = (a.Nt + kTileN - 1) / kTileN;
     const int64_t items = (int64_t)a.F * mtiles * ntiles;
-    const int nch = (a.nrefl + kChunkP - 1) / kChunkP;
+    const int nch = (nrefl + kChunkP - 1) / kChunkP;
     for (int64_t it = blockIdx.x; it < items && !failed; it += gridDim.x) {
         const int f = (int)(it / (mtiles * ntiles));
         const int rem = (int)(it - (int64_t)f * mtiles * ntiles);
         const int q0 = (rem / ntiles) * 64, p0 = (rem % ntiles) * kTileN;
         const float foc = (float)(a.freqs[f] / kC0);
         for (int c = 0; c < nch && !failed; ++c) {
-            const int nb = a.n0 + c * kChunkP;
-            const int cnt = min(kChunkP, a.n0 + a.nrefl - nb);
+            const int nb = n0 + c * kChunkP;
+            const int cnt = min(kChunkP, n0 + nrefl - nb);
             // A' tile: 64 receive elements x 32 paths, each a 2x2 real block;
             // consecutive threads take consecutive receive elements (coalesced)
 #pragma unroll 4
@@ -243,7 +247,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
         const int q = q0 + (row >> 1);
         const int part = row & 1;
         float2 wl = make_float2(0.f, 0.f);
-        if (a.los >= 0) wl = a.w[(int64_t)f * a.Pr + a.los];
+        if (los >= 0) wl = a.w[(int64_t)f * a.Pr + los];
         for (int j = 0; j < 4; ++j) {
             const int col0 = 128 * chalf + 32 * j;
             uint32_t v[32];
@@ -264,7 +268,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
             const int pb = p0 + col0 + 16 * part;
             if (q < a.Nr) {
                 float2* dst = a.H + ((int64_t)f * a.Nr + q) * a.Nt;
-                if (a.los >= 0) {
+                if (los >= 0) {
                     float dl[16];
                     const float* src = a.dlos + (int64_t)q * a.Nt + pb;
                     if (pb + 16 <= a.Nt && ((((uintptr_t)src) & 15) == 0)) {
@@ -326,24 +330,20 @@ sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* 
     const int32_t Pr = std::max(sp.Pr, 1);
     float *dt, *dr, *dl;
     float2* w;
-    unsigned int* status;
     SBR_TRY(dalloc_n(&dt, (size_t)Pr * Nt, s));
     SBR_TRY(dalloc_n(&dr, (size_t)Pr * Nr, s));
     SBR_TRY(dalloc_n(&dl, (size_t)Nr * Nt, s));
     SBR_TRY(dalloc_n(&w, (size_t)Pr * F, s));
-    SBR_TRY(dalloc_n(&status, 1, s));
-    SBR_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
     ::sbr::note_launch(), k_to_f32<double><<<nb256((int64_t)Pr * Nt), 256, 0, s>>>(sp.dt, dt, (int64_t)Pr * Nt);
     ::sbr::note_launch(), k_to_f32<double><<<nb256((int64_t)Pr * Nr), 256, 0, s>>>(sp.dr, dr, (int64_t)Pr * Nr);
     ::sbr::note_launch(), k_to_f32<double><<<nb256((int64_t)Nr * Nt), 256, 0, s>>>(sp.dlos, dl, (int64_t)Nr * Nt);
     ::sbr::note_launch(), k_w_to_f32<<<nb256((int64_t)Pr * F), 256, 0, s>>>(sp.w, w, (int64_t)Pr * F);
     TcArgs a{};
     a.F = F; a.Nr = Nr; a.Nt = Nt;
-    a.los = sp.los;
-    a.n0 = sp.los == 0 ? 1 : 0;
-    a.nrefl = sp.Pr - a.n0;
-    a.Pr = Pr;
-    a.freqs = freqs; a.dt = dt; a.dr = dr; a.w = w; a.dlos = dl; a.H = H; a.status = status;
+    a.Pr = sp.Pr;
+    a.nb0 = sp.nb0;
+    a.freqs = freqs; a.dt = dt; a.dr = dr; a.w = w; a.dlos = dl; a.H = H;
+    a.status = pl->d_status;  // a bounded wait that gave up is reported by sbr_path_query
     SBR_TRY_CUDA(cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     int64_t items = (int64_t)F * ((Nr + 63) / 64) * ((Nt + kTileN - 1) / kTileN);
     // two CTAs per SM (97 KB shared memory and 256 TMEM columns each): one CTA's
@@ -351,12 +351,9 @@ sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* 
     int grid = (int)std::min<int64_t>(items, 2 * (int64_t)sm_count());
     ::sbr::note_launch(), k_synth_tc<<<grid, kTcThreads, kSmemBytes, s>>>(a);
     SBR_TRY_CUDA(cudaGetLastError());
-    unsigned h_status = 0;
-    SBR_TRY_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    SBR_TRY_CUDA(cudaStreamSynchronize(s));
-    dfree(dt, s); dfree(dr, s); dfree(dl, s); dfree(w, s); dfree(status, s);
+    dfree(dt, s); dfree(dr, s); dfree(dl, s); dfree(w, s);
     synth_release(&sp, s);
-    return status_from_bits(h_status);
+    return SBR_OK;
 }
 
 }  // namespace sbr

@@ -437,7 +437,7 @@ __device__ __forceinline__ df3 ld_plane_n(const float4* plane, int32_t j, df& c)
     return df3{df_make(h.x, l.x), df_make(h.y, l.y), df_make(h.z, l.z)};
 }
 
-__global__ void __launch_bounds__(kTraceThreads)
+__global__ void __launch_bounds__(kTraceThreads, 8)
 k_trace_bounce(const __grid_constant__ TraceArgs a) {
     int stack[kStack];
     const int lane = threadIdx.x & 31;
