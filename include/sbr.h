@@ -100,7 +100,7 @@ sbr_status sbr_launch_dirs(int32_t N, double* dirs, double* alpha, void* stream)
  * sbr_build_bvh - acceleration structure over the scene triangles (the paper
  * gives none; Sec. III-C only says the intersection search is parallelised).
  * tri_xyz: dev float [T*9], vertices v0,v1,v2 (x,y,z) per triangle, face id =
- * index. surface_id: dev int32 [T] in [0, S): coplanar faces that form one
+ * index, T < 2^28. surface_id: dev int32 [T] in [0, S): coplanar faces that form one
  * reflecting surface share an id. T may be 0 (an empty scene). The handle
  * keeps its own copies; the inputs may be freed once the stream has run.
  * *out receives the handle (library-owned; sbr_bvh_free).
@@ -149,7 +149,8 @@ typedef struct {
 } sbr_trace_params;
 
 /* sbr_trace_params.flags */
-#define SBR_TRACE_TIMING 1u  /* record CUDA events around each bounce launch (bounce_ms) */
+#define SBR_TRACE_TIMING 1u        /* record CUDA events around each bounce launch (bounce_ms) */
+#define SBR_TRACE_COUNT_VISITS 2u  /* instrumented kernel: count BVH node visits and triangle tests */
 
 typedef struct {
     int64_t rays;
@@ -158,6 +159,9 @@ typedef struct {
     int64_t keys;               /* distinct (rx, surface sequence) keys             */
     int64_t fp64_segments;      /* segments re-traversed entirely in FP64           */
     int64_t fp64_tests;         /* faces re-decided by an exact FP64 test           */
+    int64_t node_visits;        /* BVH nodes fetched (SBR_TRACE_COUNT_VISITS only)  */
+    int64_t tri_tests;          /* triangle tests (SBR_TRACE_COUNT_VISITS only)     */
+    int64_t rx_visits;          /* receiver-BVH nodes fetched (SBR_TRACE_COUNT_VISITS only) */
     int64_t queue[SBR_KMAX + 2];/* rays alive at the start of each bounce           */
     double alpha;
     int32_t status;             /* sbr_status of the device-side checks             */

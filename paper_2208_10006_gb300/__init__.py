@@ -140,6 +140,7 @@ class TraceResult:
             _check(st)
         return dict(rays=c.rays, ray_bounces=c.ray_bounces, candidates=c.candidates, keys=c.keys,
                     fp64_segments=c.fp64_segments, fp64_tests=c.fp64_tests,
+                    node_visits=c.node_visits, tri_tests=c.tri_tests, rx_visits=c.rx_visits,
                     queue=list(c.queue), alpha=c.alpha,
                     status=c.status, table_log2=c.table_log2, bounce_ms=list(c.bounce_ms))
 
@@ -156,7 +157,7 @@ class TraceResult:
 
 
 def trace(bvh: BVH, tx, rx: torch.Tensor, N: int, K: int, alpha: float = 0.0, table_log2: int = 0,
-          timing: bool = False, stream=None) -> TraceResult:
+          timing: bool = False, count_visits: bool = False, stream=None) -> TraceResult:
     """Shoot and bounce. tx: 3 floats; rx: float64 [n_rx, 3] CUDA."""
     p = _lib.TraceParams()
     for k in range(3):
@@ -170,7 +171,7 @@ def trace(bvh: BVH, tx, rx: torch.Tensor, N: int, K: int, alpha: float = 0.0, ta
     p.max_bounces = int(K)
     p.table_log2 = int(table_log2)
     p.alpha = float(alpha)
-    p.flags = _lib.TRACE_TIMING if timing else 0
+    p.flags = (_lib.TRACE_TIMING if timing else 0) | (_lib.TRACE_COUNT_VISITS if count_visits else 0)
     h = C.c_void_p()
     _check(_L().sbr_trace(bvh.handle, C.byref(p), C.byref(h), _stream(stream)))
     return TraceResult(h, p)

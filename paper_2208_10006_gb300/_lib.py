@@ -16,6 +16,7 @@ NSTATS = 7
 POL_V, POL_H = 0, 1
 SYNTH_FP64, SYNTH_FP32, SYNTH_BF16X3 = 0, 1, 2
 TRACE_TIMING = 1
+TRACE_COUNT_VISITS = 2
 
 EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_count", "sbr_launch_dirs", "sbr_build_bvh", "sbr_bvh_free",
            "sbr_bvh_query", "sbr_trace", "sbr_trace_stats", "sbr_trace_free", "sbr_paths",
@@ -32,6 +33,7 @@ class TraceParams(C.Structure):
 class TraceCounters(C.Structure):
     _fields_ = [("rays", C.c_int64), ("ray_bounces", C.c_int64), ("candidates", C.c_int64),
                 ("keys", C.c_int64), ("fp64_segments", C.c_int64), ("fp64_tests", C.c_int64),
+                ("node_visits", C.c_int64), ("tri_tests", C.c_int64), ("rx_visits", C.c_int64),
                 ("queue", C.c_int64 * (KMAX + 2)),
                 ("alpha", C.c_double), ("status", C.c_int32), ("table_log2", C.c_int32),
                 ("bounce_ms", C.c_float * (KMAX + 1)), ("reserved", C.c_int32)]

@@ -135,7 +135,7 @@ sbr_status sbr_build_bvh(const float* tri_xyz, const int32_t* surface_id, int64_
     clear_error();
     SBR_CHECK_ARG(out != nullptr, "out");
     *out = nullptr;
-    SBR_CHECK_ARG(T >= 0 && T < ((int64_t)1 << 30), "0 <= T < 2^30");
+    SBR_CHECK_ARG(T >= 0 && T < ((int64_t)1 << 28), "0 <= T < 2^28");
     SBR_CHECK_ARG(S >= 0 && (T == 0 || S >= 1), "S >= 1 when T > 0");
     SBR_CHECK_ARG(T == 0 || (tri_xyz && surface_id), "tri_xyz and surface_id");
     cudaStream_t s = (cudaStream_t)stream;
@@ -252,6 +252,9 @@ sbr_status sbr_trace_stats(const sbr_trace_result* tr, sbr_trace_counters* out) 
     out->keys = (int64_t)c.keys;
     out->fp64_segments = (int64_t)c.fp64_segments;
     out->fp64_tests = (int64_t)c.fp64_tests;
+    out->node_visits = (int64_t)c.node_visits;
+    out->tri_tests = (int64_t)c.tri_tests;
+    out->rx_visits = (int64_t)c.rx_visits;
     for (int k = 0; k < SBR_KMAX + 2; ++k) out->queue[k] = (int64_t)c.queue[k];
     out->alpha = alpha;
     out->table_log2 = tr->table_log2;

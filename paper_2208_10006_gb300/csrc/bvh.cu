@@ -8,6 +8,7 @@
 // node and tests two boxes. Boxes are padded outward by a relative margin so
 // that FP32 traversal never culls a box that the exact ray touches.
 #include <algorithm>
+#include <cstdlib>
 
 #include "dfloat.cuh"
 #include "sbr_internal.cuh"
@@ -91,7 +92,7 @@ __device__ __forceinline__ int delta(const uint32_t* __restrict__ code, int64_t 
 
 __global__ void k_karras(const uint32_t* __restrict__ code, int64_t n, int32_t* __restrict__ left,
                          int32_t* __restrict__ right, int32_t* __restrict__ parent_int,
-                         int32_t* __restrict__ parent_leaf) {
+                         int32_t* __restrict__ parent_leaf, int32_t* __restrict__ span) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     int d = (delta(code, n, i, i + 1) - delta(code, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -110,6 +111,8 @@ __global__ void k_karras(const uint32_t* __restrict__ code, int64_t n, int32_t* 
     } while (t > 1);
     int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
     int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    span[2 * i] = (int32_t)lo;       // the node covers sorted primitives [lo, hi]
+    span[2 * i + 1] = (int32_t)hi;
     if (lo == gamma) {
         left[i] = ~(int32_t)gamma;
         parent_leaf[gamma] = (int32_t)i;
@@ -171,7 +174,19 @@ __global__ void k_refit(const float* __restrict__ prim_box, const int32_t* __res
 __device__ __forceinline__ float pad_lo(float x, float pad) { return x - pad * (fabsf(x) + 1.f); }
 __device__ __forceinline__ float pad_hi(float x, float pad) { return x + pad * (fabsf(x) + 1.f); }
 
+// child reference: internal node index, or a leaf ~(first | (count - 1) << 28)
+// holding `count` consecutive sorted primitives; subtrees of at most leaf_max
+// primitives are emitted as one leaf (their primitives are consecutive in
+// Morton order), so traversal stops above them
+__device__ __forceinline__ int32_t child_ref(int32_t c, const int32_t* __restrict__ span, int leaf_max) {
+    if (c < 0) return c;  // single primitive ~p (count 1)
+    int32_t lo = span[2 * c], hi = span[2 * c + 1];
+    if (hi - lo + 1 <= leaf_max) return ~(lo | ((hi - lo) << 28));
+    return c;
+}
+
 __global__ void k_emit(int64_t n, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                       const int32_t* __restrict__ span, int leaf_max,
                        const float* __restrict__ lbox, const float* __restrict__ ibox, float pad,
                        float4* __restrict__ nodes, float* __restrict__ root) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -188,6 +203,8 @@ __global__ void k_emit(int64_t n, const int32_t* __restrict__ left, const int32_
         const float* p0 = r0 < 0 ? lbox + 6 * (int64_t)(~r0) : ibox + 6 * (int64_t)r0;
         const float* p1 = r1 < 0 ? lbox + 6 * (int64_t)(~r1) : ibox + 6 * (int64_t)r1;
         for (int k = 0; k < 6; ++k) { b0[k] = p0[k]; b1[k] = p1[k]; }
+        r0 = child_ref(r0, span, leaf_max);
+        r1 = child_ref(r1, span, leaf_max);
     }
     for (int k = 0; k < 3; ++k) {
         b0[k] = pad_lo(b0[k], pad); b0[3 + k] = pad_hi(b0[3 + k], pad);
@@ -271,7 +288,7 @@ __global__ void k_surface_offsets(const uint32_t* __restrict__ key, int64_t T, i
 
 }  // namespace
 
-sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, BvhNodes* out,
+sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, int leaf_max, BvhNodes* out,
                       int32_t* d_depth, cudaStream_t s) {
     *out = BvhNodes{};
     if (n <= 0) return SBR_OK;
@@ -282,7 +299,7 @@ sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, BvhNodes*
     int64_t nn = n > 1 ? n - 1 : 1;
     float* bnd;
     uint32_t *code, *idx;
-    int32_t *left, *right, *pint, *pleaf, *flag;
+    int32_t *left, *right, *pint, *pleaf, *flag, *span;
     float *lbox, *ibox;
     SBR_TRY(dalloc_n(&bnd, 12, s));
     SBR_TRY(dalloc_n(&code, n, s));
@@ -292,6 +309,7 @@ sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, BvhNodes*
     SBR_TRY(dalloc_n(&pint, nn, s));
     SBR_TRY(dalloc_n(&pleaf, n, s));
     SBR_TRY(dalloc_n(&flag, nn, s));
+    SBR_TRY(dalloc_n(&span, 2 * nn, s));
     SBR_TRY(dalloc_n(&lbox, 6 * n, s));
     SBR_TRY(dalloc_n(&ibox, 6 * nn, s));
     SBR_TRY(dalloc_n(&out->nodes, 4 * nn, s));
@@ -302,16 +320,16 @@ sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, BvhNodes*
     ::sbr::note_launch(), k_morton<<<blocks_for(n), kThreads, 0, s>>>(prim_box, n, bnd, code, idx);
     SBR_TRY_CUDA(cudaGetLastError());
     SBR_TRY(radix_sort_pairs(code, idx, n, 30, s));
-    if (n > 1) ::sbr::note_launch(), k_karras<<<blocks_for(n - 1), kThreads, 0, s>>>(code, n, left, right, pint, pleaf);
+    if (n > 1) ::sbr::note_launch(), k_karras<<<blocks_for(n - 1), kThreads, 0, s>>>(code, n, left, right, pint, pleaf, span);
     ::sbr::note_launch(), k_refit<<<blocks_for(n), kThreads, 0, s>>>(prim_box, (const int32_t*)idx, n, left, right, pint,
                                                pleaf, flag, lbox, ibox, d_depth);
-    ::sbr::note_launch(), k_emit<<<blocks_for(nn), kThreads, 0, s>>>(n, left, right, lbox, ibox, pad_rel, out->nodes,
+    ::sbr::note_launch(), k_emit<<<blocks_for(nn), kThreads, 0, s>>>(n, left, right, span, leaf_max, lbox, ibox, pad_rel, out->nodes,
                                                out->d_root);
     SBR_TRY_CUDA(cudaGetLastError());
     out->order = reinterpret_cast<int32_t*>(idx);
     out->n_nodes = (int32_t)nn;
     dfree(bnd, s); dfree(code, s); dfree(left, s); dfree(right, s); dfree(pint, s);
-    dfree(pleaf, s); dfree(flag, s); dfree(lbox, s); dfree(ibox, s);
+    dfree(pleaf, s); dfree(flag, s); dfree(span, s); dfree(lbox, s); dfree(ibox, s);
     return SBR_OK;
 }
 
@@ -320,6 +338,17 @@ void free_lbvh(BvhNodes* b, cudaStream_t s) {
     if (b->order) dfree(b->order, s);
     if (b->d_root) dfree(b->d_root, s);
     *b = BvhNodes{};
+}
+
+// triangles per leaf at most: kTriLeaf, or the SBR_BVH_LEAF environment
+// variable (1..16), a tuning knob for the traversal/leaf-test balance
+static int tri_leaf_size() {
+    const char* e = getenv("SBR_BVH_LEAF");
+    if (e) {
+        int v = atoi(e);
+        if (v >= 1 && v <= 16) return v;
+    }
+    return kTriLeaf;
 }
 
 sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S, sbr_bvh* b,
@@ -350,7 +379,7 @@ sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S
     ::sbr::note_launch(), k_tri_normals<<<blocks_for(T), kThreads, 0, s>>>(b->tri, T, b->nrm, status);
     SBR_TRY_CUDA(cudaGetLastError());
     // relative box padding: 2^-20 of (|x| + 1) covers FP32 ray/box rounding
-    SBR_TRY(build_lbvh(box, T, 1.0f / (1 << 20), &b->tree, b->d_depth, s));
+    SBR_TRY(build_lbvh(box, T, 1.0f / (1 << 20), tri_leaf_size(), &b->tree, b->d_depth, s));
     ::sbr::note_launch(), k_tri_pack<<<blocks_for(T), kThreads, 0, s>>>(b->tri, b->surf, b->nrm, b->tree.order, T,
                                                   b->tri_sorted, b->plane_sorted);
     // faces per surface, ascending face id (stable sort on the surface id)

@@ -250,13 +250,27 @@ __global__ void k_refine(const __grid_constant__ RefineArgs a) {
     J[34] = dot(rH, sv_prev); J[35] = dot(rH, pout_prev);
 }
 
-template <class T>
-__global__ void k_compact(const uint32_t* __restrict__ valid, const uint32_t* __restrict__ pos,
-                          int64_t n, const T* __restrict__ in, T* __restrict__ out, int width) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n * width) return;
-    int64_t r = i / width;
-    if (valid[r]) out[(int64_t)pos[r] * width + (i - r * width)] = in[i];
+// move valid refined keys to their compacted positions: one warp per key, the
+// lanes stride over the 32-bit words of all fields of the record
+struct CompactArgs {
+    const uint32_t* valid;
+    const uint32_t* pos;
+    int64_t n;
+    const void* src[11];
+    void* dst[11];
+    int words[11];   // 32-bit words per record of each field
+};
+
+__global__ void k_compact_all(const __grid_constant__ CompactArgs a) {
+    const int lane = threadIdx.x & 31;
+    int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= a.n || !a.valid[r]) return;
+    const int64_t q = a.pos[r];
+    for (int f = 0; f < 11; ++f) {
+        const uint32_t* s = static_cast<const uint32_t*>(a.src[f]) + r * a.words[f];
+        uint32_t* d = static_cast<uint32_t*>(a.dst[f]) + q * a.words[f];
+        for (int w = lane; w < a.words[f]; w += 32) d[w] = s[w];
+    }
 }
 
 __global__ void k_rx_offsets(const int32_t* __restrict__ rx, int64_t P, int32_t n_rx,
@@ -373,21 +387,17 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     SBR_TRY(dalloc_n(&pl->d_status, 1, s));
     SBR_TRY_CUDA(cudaMemsetAsync(pl->d_status, 0, sizeof(unsigned), s));
     if (n > 0) {
-        auto go = [&](auto* in, auto* out, int width) {
-            using T = std::remove_pointer_t<decltype(out)>;
-            ::sbr::note_launch(), k_compact<T><<<nblk(n * width), kThreads, 0, s>>>(valid, pos, n, in, out, width);
-        };
-        go(a.rx_o, pl->rx, 1);
-        go(a.nb_o, pl->nb, 1);
-        go(a.surf_o, pl->surf, kKmax);
-        go(a.face_o, pl->face, kKmax);
-        go(a.pts_o, pl->pts, kKmax * 3);
-        go(a.L_o, pl->L, 1);
-        go(a.aod_o, pl->aod, 2);
-        go(a.aoa_o, pl->aoa, 2);
-        go(a.ray_o, pl->ray, 1);
-        go(a.dist_o, pl->dist, 1);
-        go(a.jones_o, pl->jones, kJones);
+        CompactArgs c{};
+        c.valid = valid;
+        c.pos = pos;
+        c.n = n;
+        const void* src[11] = {a.rx_o, a.nb_o, a.surf_o, a.face_o, a.pts_o, a.L_o, a.aod_o, a.aoa_o,
+                               a.ray_o, a.dist_o, a.jones_o};
+        void* dst[11] = {pl->rx, pl->nb, pl->surf, pl->face, pl->pts, pl->L, pl->aod, pl->aoa, pl->ray,
+                         pl->dist, pl->jones};
+        const int words[11] = {1, 1, kKmax, kKmax, 2 * 3 * kKmax, 2, 4, 4, 1, 1, 2 * kJones};
+        for (int f = 0; f < 11; ++f) { c.src[f] = src[f]; c.dst[f] = dst[f]; c.words[f] = words[f]; }
+        ::sbr::note_launch(), k_compact_all<<<nblk(32 * n), kThreads, 0, s>>>(c);
         SBR_TRY_CUDA(cudaGetLastError());
     }
     ::sbr::note_launch(), k_rx_offsets<<<nblk((int64_t)tr->n_rx + 1), kThreads, 0, s>>>(pl->rx, P, tr->n_rx, pl->rx_off);

@@ -96,9 +96,14 @@ struct BvhNodes {
     float* d_root = nullptr;   // [6] root bounds on the device
 };
 // Build over n primitives given by boxes [n*6] (lo xyz, hi xyz) on the device.
-// pad: absolute padding added to every child box (covers FP32 rounding).
-sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, BvhNodes* out,
+// pad_rel: relative padding added to every child box (covers FP32 rounding).
+// Subtrees of at most leaf_max (<= 16) primitives become one leaf; a leaf
+// reference is ~(first | (count - 1) << 28).
+sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, int leaf_max, BvhNodes* out,
                       int32_t* d_depth, cudaStream_t s);
+constexpr int kTriLeaf = 2;  // triangles per BVH leaf at most (measured best of 1..6)
+__host__ __device__ __forceinline__ int32_t leaf_first(int32_t ref) { return (~ref) & 0x0FFFFFFF; }
+__host__ __device__ __forceinline__ int32_t leaf_count(int32_t ref) { return (int32_t)(((uint32_t)(~ref)) >> 28) + 1; }
 void free_lbvh(BvhNodes* b, cudaStream_t s);
 
 }  // namespace sbr
@@ -128,6 +133,9 @@ struct TraceCountersDev {
     unsigned long long keys;
     unsigned long long fp64_segments;
     unsigned long long fp64_tests;
+    unsigned long long node_visits;  // instrumented traces only
+    unsigned long long tri_tests;
+    unsigned long long rx_visits;
     unsigned int status;
     unsigned int pad;
 };

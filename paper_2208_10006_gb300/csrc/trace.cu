@@ -121,7 +121,8 @@ __device__ __forceinline__ bool box_hit(float lx, float ly, float lz, float hx, 
 //   errE = 8 eps max(|Cx By| + |Cy Bx|, |Ax Cy| + |Ay Cx|, |Bx Ay| + |By Ax|)
 //        + 4 eps (|o|_inf + t_scale) (perimeter of the sheared triangle)
 // (eps = 2^-24): the first term covers the arithmetic of the test, the second
-// the rounding of the FP64 ray to FP32. A face is a certain miss if some edge
+// the rounding of the double-float ray to FP32. It is evaluated through the
+// upper bound 8 eps (Sx Sy + (|o|_inf + t_scale)(Sx + Sy)). A face is a certain miss if some edge
 // function is below -errE, a certain hit if all exceed +errE and t is clearly
 // positive. Everything in between, and hits of different surfaces whose t
 // agree within kTie, go to a short list that is re-decided in FP64 with the
@@ -163,12 +164,11 @@ __device__ __forceinline__ void tri_test32(const float4* __restrict__ tris, int3
     float det = U + V + W;
     float sg = det >= 0.f ? 1.f : -1.f;
     float mn = fminf(fminf(sg * U, sg * V), sg * W);  // min of the orientation-adjusted values
-    float pU = fabsf(Cx * By) + fabsf(Cy * Bx), pV = fabsf(Ax * Cy) + fabsf(Ay * Cx),
-          pW = fabsf(Bx * Ay) + fabsf(By * Ax);
-    float per = fabsf(Bx - Cx) + fabsf(By - Cy) + fabsf(Cx - Ax) + fabsf(Cy - Ay) +
-                fabsf(Ax - Bx) + fabsf(Ay - By);
+    // bound of the rounding error of U, V, W (see above), in a cheaper looser form:
+    // each |Cx By| + |Cy Bx| <= Sx Sy and the sheared perimeter <= 2 (Sx + Sy)
+    float Sx = fabsf(Ax) + fabsf(Bx) + fabsf(Cx), Sy = fabsf(Ay) + fabsf(By) + fabsf(Cy);
     float zs = fmaxf(fabsf(Az), fmaxf(fabsf(Bz), fabsf(Cz)));
-    float errE = 8.f * kEps32 * fmaxf(pU, fmaxf(pV, pW)) + 4.f * kEps32 * (tv.omax + zs) * per;
+    float errE = 8.f * kEps32 * fmaf(Sx, Sy, (tv.omax + zs) * (Sx + Sy));
     if (mn < -errE) return;  // certainly outside one edge
     float adet = fabsf(det);
     if (!(adet > 3.f * errE)) {  // t is not reliable: let FP64 decide
@@ -196,35 +196,44 @@ __device__ __forceinline__ void tri_test32(const float4* __restrict__ tris, int3
 }
 
 // FP32 closest hit. Returns the sorted triangle index of the certain best
-// (or -1) and the list of faces that FP64 must re-decide.
-__device__ int32_t traverse32(const TraceArgs& a, const Ray32& r, int prev, Trav& tv, int* stack) {
+// (or -1) and the list of faces that FP64 must re-decide. kCount adds node
+// visits and triangle tests to *visits / *tests (instrumented traces).
+template <bool kCount>
+__device__ int32_t traverse32(const TraceArgs& a, const Ray32& r, int prev, Trav& tv, int* stack,
+                              unsigned* visits, unsigned* tests) {
     tv.best_t = INFINITY; tv.lim = INFINITY; tv.best_j = -1; tv.best_face = 0x7fffffff;
     tv.best_surf = -2; tv.nu = 0; tv.overflow = false;
     tv.omax = fmaxf(fabsf(r.o.x), fmaxf(fabsf(r.o.y), fabsf(r.o.z)));
+    // one loop over references: an internal node tests its two child boxes and
+    // continues with the nearer hit child (the farther one is stacked); a leaf
+    // reference tests its triangles; leaves and nodes share the stack
     int sp = 0;
-    int32_t node = 0;
+    int32_t ref = 0;
     for (;;) {
-        const float4* nd = a.nodes + 4 * (int64_t)node;
-        float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
-        int32_t r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
-        float tn0, tn1;
-        bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, tv.lim, tn0);
-        bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, tv.lim, tn1) && r1 != r0;
-        if (h0 && r0 < 0) { tri_test32(a.tris, ~r0, prev, r, tv); h0 = false; }
-        if (h1 && r1 < 0) { tri_test32(a.tris, ~r1, prev, r, tv); h1 = false; }
-        if (h0 && h1) {
-            int32_t nearn = tn0 <= tn1 ? r0 : r1, farn = tn0 <= tn1 ? r1 : r0;
-            if (sp < kStack) stack[sp++] = farn;
-            else { atomicOr(&a.cnt->status, (unsigned)ST_STACK); tv.overflow = true; break; }
-            node = nearn;
-        } else if (h0) {
-            node = r0;
-        } else if (h1) {
-            node = r1;
+        if (ref >= 0) {
+            const float4* nd = a.nodes + 4 * (int64_t)ref;
+            float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+            int32_t r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
+            if (kCount) ++*visits;
+            float tn0, tn1;
+            bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, tv.lim, tn0);
+            bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, tv.lim, tn1) && r1 != r0;
+            if (h0 && h1) {
+                bool first0 = tn0 <= tn1;
+                if (sp < kStack) stack[sp++] = first0 ? r1 : r0;
+                else { atomicOr(&a.cnt->status, (unsigned)ST_STACK); tv.overflow = true; break; }
+                ref = first0 ? r0 : r1;
+                continue;
+            }
+            if (h0) { ref = r0; continue; }
+            if (h1) { ref = r1; continue; }
         } else {
-            if (sp == 0) break;
-            node = stack[--sp];
+            const int32_t first = leaf_first(ref), cnt = leaf_count(ref);
+            for (int k = 0; k < cnt; ++k) tri_test32(a.tris, first + k, prev, r, tv);
+            if (kCount) *tests += cnt;
         }
+        if (sp == 0) break;
+        ref = stack[--sp];
     }
     return tv.best_j;
 }
@@ -276,9 +285,10 @@ __device__ __noinline__ int32_t traverse64(const TraceArgs& a, d3 o, d3 d, int p
             int32_t rr = c ? r1 : r0;
             bool hh = c ? h1 : h0;
             if (hh && rr < 0) {
-                int32_t j = ~rr;
-                float4 a0 = __ldg(a.tris + 3 * j), a1 = __ldg(a.tris + 3 * j + 1);
-                if (__float_as_int(a0.w) != prev) {
+                const int32_t first = leaf_first(rr), cnt = leaf_count(rr);
+                for (int32_t j = first; j < first + cnt; ++j) {
+                    float4 a0 = __ldg(a.tris + 3 * j), a1 = __ldg(a.tris + 3 * j + 1);
+                    if (__float_as_int(a0.w) == prev) continue;
                     double t;
                     int face = __float_as_int(a1.w);
                     if (mt64(a.tris, j, o, d, t) && (t < best_t || (t == best_t && face < best_face))) {
@@ -355,8 +365,9 @@ __device__ void ht_insert(const TraceArgs& a, const uint32_t* key, unsigned long
 // boxes are grown by the largest sphere radius on the segment (FP32,
 // conservative); each is then tested exactly in double-float:
 //   t* = (Rx - o).d in [0, t_hit],  |o + t* d - Rx|^2 <= alpha^2 (L + t*)^2 / 3.
+template <bool kCount>
 __device__ void receive(const TraceArgs& a, const df3& o, const df3& d, df L, df t_hit, bool hit,
-                        const Ray32& r, uint32_t ray, int* stack) {
+                        const Ray32& r, uint32_t ray, int* stack, unsigned* rx_visits) {
     if (a.n_rx <= 0) return;
     const float4 al = __ldg(a.alpha_df);
     const df a2o3 = df_make(al.z, al.w);
@@ -381,6 +392,7 @@ __device__ void receive(const TraceArgs& a, const df3& o, const df3& d, df L, df
         const float4* nd = a.rx_nodes + 4 * (int64_t)node;
         float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
         int32_t r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
+        if (kCount) ++*rx_visits;
         float tn0, tn1;
         bool h0 = box_hit(n0.x - rmax, n0.y - rmax, n0.z - rmax, n0.w + rmax, n1.x + rmax, n1.y + rmax,
                           r, tmax, tn0);
@@ -437,9 +449,11 @@ __device__ __forceinline__ df3 ld_plane_n(const float4* plane, int32_t j, df& c)
     return df3{df_make(h.x, l.x), df_make(h.y, l.y), df_make(h.z, l.z)};
 }
 
+template <bool kCount>
 __global__ void __launch_bounds__(kTraceThreads, 8)
 k_trace_bounce(const __grid_constant__ TraceArgs a) {
     int stack[kStack];
+    unsigned visits = 0, tests = 0, rx_visits = 0;
     const int lane = threadIdx.x & 31;
     const unsigned long long n_in = a.bounce == 0 ? (unsigned long long)a.R : *a.n_in;
     for (;;) {
@@ -479,7 +493,7 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
             df t = df_make(INFINITY, 0.f);
             if (a.T > 0) {
                 Trav tv;
-                j = traverse32(a, r, prev, tv, stack);
+                j = traverse32<kCount>(a, r, prev, tv, stack, &visits, &tests);
                 if (tv.overflow || tv.nu > 0) {
                     d3 o64 = mk3(df_to_double(o.x), df_to_double(o.y), df_to_double(o.z));
                     d3 d64 = mk3(df_to_double(d.x), df_to_double(d.y), df_to_double(d.z));
@@ -509,7 +523,7 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
                     t = df_div(df_sub(c, df3_dot(n, o)), df3_dot(n, d));
                 }
             }
-            receive(a, o, d, L, t, j >= 0, r, ray, stack);
+            receive<kCount>(a, o, d, L, t, j >= 0, r, ray, stack, &rx_visits);
             if (j >= 0 && a.bounce < a.K) {
                 df c;
                 df3 n = ld_plane_n(a.plane, j, c);
@@ -529,6 +543,20 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
                 a.seq[(int64_t)a.bounce * a.R + ray] = surf;
                 survive = true;
             }
+        }
+        if (kCount) {
+            unsigned long long v = visits, w = tests, x = rx_visits;
+            for (int o = 16; o; o >>= 1) {
+                v += __shfl_xor_sync(0xffffffffu, v, o);
+                w += __shfl_xor_sync(0xffffffffu, w, o);
+                x += __shfl_xor_sync(0xffffffffu, x, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&a.cnt->node_visits, v);
+                atomicAdd(&a.cnt->tri_tests, w);
+                atomicAdd(&a.cnt->rx_visits, x);
+            }
+            visits = tests = rx_visits = 0;
         }
         unsigned mask = __ballot_sync(0xffffffffu, survive);
         if (mask) {
@@ -577,14 +605,17 @@ __global__ void k_init_table(uint32_t* state, unsigned long long* val, size_t ca
     val[i] = ~0ull;
 }
 
-int trace_grid() {
-    static int grid = 0;
-    if (!grid) {
+int trace_grid(bool count) {
+    static int grid[2] = {0, 0};
+    if (!grid[count]) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_bounce, kTraceThreads, 0);
-        grid = std::max(1, per_sm) * sm_count();
+        if (count)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_bounce<true>, kTraceThreads, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_bounce<false>, kTraceThreads, 0);
+        grid[count] = std::max(1, per_sm) * sm_count();
     }
-    return grid;
+    return grid[count];
 }
 
 }  // namespace
@@ -611,7 +642,7 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
         SBR_TRY(dalloc_n(&rx_depth, 1, s));
         ::sbr::note_launch(), k_rx_boxes<<<(tr->n_rx + 255) / 256, 256, 0, s>>>(tr->rx, tr->n_rx, rxbox);
         SBR_TRY_CUDA(cudaGetLastError());
-        SBR_TRY(build_lbvh(rxbox, tr->n_rx, 0.0f, &rxb, rx_depth, s));
+        SBR_TRY(build_lbvh(rxbox, tr->n_rx, 0.0f, 1, &rxb, rx_depth, s));
     }
     float4* rx_df = nullptr;
     float4* alpha_df = nullptr;
@@ -659,7 +690,8 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     a.ht_val = tr->ht_val;
     a.ht_mask = (uint32_t)(cap - 1);
     a.cnt = tr->cnt;
-    int grid = trace_grid();
+    const bool count = (p.flags & SBR_TRACE_COUNT_VISITS) != 0;
+    int grid = trace_grid(count);
     const bool timing = (p.flags & SBR_TRACE_TIMING) != 0;
     if (timing) {
         for (int k = 0; k <= K + 1; ++k) SBR_TRY_CUDA(cudaEventCreate(&tr->ev[k]));
@@ -672,7 +704,10 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
         a.n_in = &tr->cnt->queue[bnc];
         a.n_out = &tr->cnt->queue[bnc + 1];
         a.work = &tr->cnt->work[bnc];
-        ::sbr::note_launch(), k_trace_bounce<<<grid, kTraceThreads, 0, s>>>(a);
+        if (count)
+            ::sbr::note_launch(), k_trace_bounce<true><<<grid, kTraceThreads, 0, s>>>(a);
+        else
+            ::sbr::note_launch(), k_trace_bounce<false><<<grid, kTraceThreads, 0, s>>>(a);
         SBR_TRY_CUDA(cudaGetLastError());
         if (timing) SBR_TRY_CUDA(cudaEventRecord(tr->ev[bnc + 1], s));
     }
