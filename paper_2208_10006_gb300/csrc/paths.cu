@@ -91,11 +91,16 @@ __device__ __forceinline__ void angles_deg(d3 v, double* out) {
     out[1] = atan2(v.z, hypot(v.x, v.y)) * (180.0 / kPi);
 }
 
-// theta-hat (V) or phi-hat (H) of propagation direction d
+// theta-hat (V) or phi-hat (H) of a unit propagation direction d, from
+// cos(theta) = z, sin(theta) = rho = |(x, y)|, cos(phi) = x / rho,
+// sin(phi) = y / rho; at the poles (rho = 0) phi = atan2(0, 0) = 0
 __device__ __forceinline__ d3 pol_vec(d3 d, int pol) {
-    double th = atan2(hypot(d.x, d.y), d.z), ph = atan2(d.y, d.x);
-    if (pol == SBR_POL_V) return mk3(cos(th) * cos(ph), cos(th) * sin(ph), -sin(th));
-    return mk3(-sin(ph), cos(ph), 0.0);
+    double rho = hypot(d.x, d.y);
+    double cp = 1.0, sp = 0.0;
+    if (rho > 0.0) { cp = d.x / rho; sp = d.y / rho; }
+    double ct = d.z / norm(d), st = rho / norm(d);
+    if (pol == SBR_POL_V) return mk3(ct * cp, ct * sp, -st);
+    return mk3(-sp, cp, 0.0);
 }
 
 // s = unit(d_in x n); when d_in is parallel to n, unit(n x e) with e the axis of

@@ -139,6 +139,73 @@ sbr_status scan_rec(uint32_t* data, int64_t n, cudaStream_t s) {
     return st;
 }
 
+// Whole sort of a small array in one block: keys and values live in shared
+// memory and every 8-bit pass runs in the same launch (same stable ranking as
+// the multi-block path: round, warp, lane order).
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallMax = 12288;  // 2 x 2 x 4 B x 12288 = 192 KB of shared memory
+
+__global__ void __launch_bounds__(kSmallThreads)
+k_sort_small(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int n, int passes) {
+    extern __shared__ uint32_t sm[];
+    uint32_t* ka = sm;
+    uint32_t* va = sm + kSmallMax;
+    uint32_t* kb = sm + 2 * kSmallMax;
+    uint32_t* vb = sm + 3 * kSmallMax;
+    __shared__ uint32_t s_hist[256];
+    __shared__ uint32_t s_warp[kSmallThreads / 32][256];
+    __shared__ uint32_t s_run[256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int i = tid; i < n; i += kSmallThreads) { ka[i] = keys[i]; va[i] = vals[i]; }
+    __syncthreads();
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        if (tid < 256) s_hist[tid] = 0;
+        __syncthreads();
+        for (int i = tid; i < n; i += kSmallThreads) atomicAdd(&s_hist[(ka[i] >> shift) & 255u], 1u);
+        __syncthreads();
+        if (tid == 0) {  // exclusive scan of 256 counts
+            uint32_t run = 0;
+            for (int d = 0; d < 256; ++d) { uint32_t c = s_hist[d]; s_run[d] = run; run += c; }
+        }
+        __syncthreads();
+        for (int base = 0; base < n; base += kSmallThreads) {
+            for (int w = 0; w < kSmallThreads / 32; ++w)
+                if (tid < 256) s_warp[w][tid] = 0;
+            __syncthreads();
+            int i = base + tid;
+            bool valid = i < n;
+            uint32_t k = valid ? ka[i] : 0u, v = valid ? va[i] : 0u;
+            uint32_t d = valid ? ((k >> shift) & 255u) : 256u;
+            unsigned peers = __match_any_sync(0xffffffffu, d);
+            int rank = __popc(peers & lt);
+            if (valid && rank == 0) s_warp[warp][d] = __popc(peers);
+            __syncthreads();
+            if (tid < 256) {
+                uint32_t run = s_run[tid];
+                for (int w = 0; w < kSmallThreads / 32; ++w) {
+                    uint32_t c = s_warp[w][tid];
+                    s_warp[w][tid] = run;
+                    run += c;
+                }
+                s_run[tid] = run;
+            }
+            __syncthreads();
+            if (valid) {
+                uint32_t pos = s_warp[warp][d] + rank;
+                kb[pos] = k;
+                vb[pos] = v;
+            }
+            __syncthreads();
+        }
+        uint32_t* t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += kSmallThreads) { keys[i] = ka[i]; vals[i] = va[i]; }
+}
+
 }  // namespace
 
 sbr_status exclusive_scan_u32(uint32_t* data, int64_t n, uint32_t* total, cudaStream_t s) {
@@ -166,6 +233,18 @@ sbr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits,
     if (n > 0x7fffffffLL) {
         set_error("radix_sort_pairs: n too large");
         return SBR_ERR_UNSUPPORTED;
+    }
+    if (n <= kSmallMax) {
+        const size_t smem = sizeof(uint32_t) * 4 * kSmallMax;
+        static bool attr = false;
+        if (!attr) {
+            SBR_TRY_CUDA(cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+            attr = true;
+        }
+        ::sbr::note_launch(), k_sort_small<<<1, kSmallThreads, smem, s>>>(keys, vals, (int)n, (bits + 7) / 8);
+        SBR_TRY_CUDA(cudaGetLastError());
+        return SBR_OK;
     }
     int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     uint32_t *k2, *v2, *hist;
