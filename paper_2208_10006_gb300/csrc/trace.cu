@@ -82,16 +82,24 @@ __device__ __forceinline__ float comp(float4 v, int k) { return k == 0 ? v.x : (
 __device__ __forceinline__ float comp3(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 
 struct Ray32 {
-    float3 o, d, inv;
+    float3 o, d, inv, oinv;  // oinv = o * inv, for the slab test fma(lo, inv, -oinv)
     int kx, ky, kz;
     float Sx, Sy, Sz;
 };
+
+// reciprocal of a direction component for the slab test; an exact zero becomes
+// +-2^-80 so that inv and o * inv stay finite
+__device__ __forceinline__ float safe_rcp(float x) {
+    const float tiny = 8.271806e-25f;  // 2^-80
+    return 1.0f / (fabsf(x) > tiny ? x : copysignf(tiny, x));
+}
 
 __device__ __forceinline__ Ray32 make_ray32(float3 o, float3 d) {
     Ray32 r;
     r.o = o;
     r.d = d;
-    r.inv = make_float3(1.0f / r.d.x, 1.0f / r.d.y, 1.0f / r.d.z);
+    r.inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    r.oinv = make_float3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
     float ax = fabsf(r.d.x), ay = fabsf(r.d.y), az = fabsf(r.d.z);
     r.kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
     r.kx = r.kz == 2 ? 0 : r.kz + 1;
@@ -104,12 +112,13 @@ __device__ __forceinline__ Ray32 make_ray32(float3 o, float3 d) {
     return r;
 }
 
-// slab test; NaN from 0 * inf is ignored by fminf/fmaxf, which keeps it conservative
+// slab test, t = lo / d - o / d as one fma per plane; its rounding (~eps |o|
+// in distance) is far inside the relative padding of the BVH boxes
 __device__ __forceinline__ bool box_hit(float lx, float ly, float lz, float hx, float hy, float hz,
                                         const Ray32& r, float tmax, float& tnear) {
-    float t0x = (lx - r.o.x) * r.inv.x, t1x = (hx - r.o.x) * r.inv.x;
-    float t0y = (ly - r.o.y) * r.inv.y, t1y = (hy - r.o.y) * r.inv.y;
-    float t0z = (lz - r.o.z) * r.inv.z, t1z = (hz - r.o.z) * r.inv.z;
+    float t0x = fmaf(lx, r.inv.x, -r.oinv.x), t1x = fmaf(hx, r.inv.x, -r.oinv.x);
+    float t0y = fmaf(ly, r.inv.y, -r.oinv.y), t1y = fmaf(hy, r.inv.y, -r.oinv.y);
+    float t0z = fmaf(lz, r.inv.z, -r.oinv.z), t1z = fmaf(hz, r.inv.z, -r.oinv.z);
     float tmin = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.f));
     float tmx = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), tmax));
     tnear = tmin;
@@ -373,15 +382,12 @@ __device__ void receive(const TraceArgs& a, const df3& o, const df3& d, df L, df
     const df a2o3 = df_make(al.z, al.w);
     float t_end = t_hit.hi;
     if (!hit) {
-        // no receiver lies beyond the farthest corner of their bounding box
-        float far2 = 0.f;
-        for (int c = 0; c < 8; ++c) {
-            float x = a.rx_root[(c & 1) ? 3 : 0] - r.o.x;
-            float y = a.rx_root[(c & 2) ? 4 : 1] - r.o.y;
-            float z = a.rx_root[(c & 4) ? 5 : 2] - r.o.z;
-            far2 = fmaxf(far2, x * x + y * y + z * z);
-        }
-        t_end = sqrtf(far2) * (1.f + 1e-5f) + 1e-3f;
+        // no receiver lies farther than the centre of their box plus its half diagonal
+        float cx = 0.5f * (a.rx_root[0] + a.rx_root[3]) - r.o.x;
+        float cy = 0.5f * (a.rx_root[1] + a.rx_root[4]) - r.o.y;
+        float cz = 0.5f * (a.rx_root[2] + a.rx_root[5]) - r.o.z;
+        float hx = a.rx_root[3] - a.rx_root[0], hy = a.rx_root[4] - a.rx_root[1], hz = a.rx_root[5] - a.rx_root[2];
+        t_end = (sqrtf(cx * cx + cy * cy + cz * cz) + 0.5f * sqrtf(hx * hx + hy * hy + hz * hz)) * (1.f + 1e-5f) + 1e-3f;
     }
     float rmax = al.x * (L.hi + t_end) * 0.57735027f * (1.f + 1e-4f) +
                  1e-5f * (fabsf(r.o.x) + fabsf(r.o.y) + fabsf(r.o.z) + L.hi + t_end);
