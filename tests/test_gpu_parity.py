@@ -199,7 +199,8 @@ def test_bvh_shape(sbr):
         d = sbr.scene_to_device(sc)
         info = sbr.build_bvh(d["tri"], d["surface_id"], d["S"]).info()
         T = len(sc["tri"])
-        assert info["T"] == T and info["n_nodes"] == T - 1
+        # 4-wide nodes: at most one per binary internal node, at least one
+        assert info["T"] == T and 1 <= info["n_nodes"] <= max(1, T - 1)
         assert 1 <= info["depth"] <= 64
 
 
