@@ -61,6 +61,25 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+# street crossings (i, j) of the urban grid; rank r traces an independent Tx at
+# crossings[r % 8] with its receiver grid below it (weak scaling)
+CROSSINGS = [(4, 2), (3, 2), (5, 2), (4, 1), (4, 3), (2, 2), (6, 2), (3, 1)]
+
+
+def reduce_over_ranks(t_total: float, work: float, device=None):
+    """Job time = the slowest rank's timed region; work = the sum over ranks.
+    Returns (t_max, work_sum); a no-op without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_total, work
+    t = torch.tensor([t_total], dtype=torch.float64, device=device)
+    w = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(w[0])
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -200,9 +219,8 @@ def run_gpu(args):
     sbr._lib.load()
     peaks, peak_src = load_peaks()
 
-    crossings = [(4, 2), (3, 2), (5, 2), (4, 1), (4, 3), (2, 2), (6, 2), (3, 1)]
     N_w = {"urban": 1000, "urban_n400": 400}[args.workload]
-    sc = scenes.config2(N=N_w, crossing=crossings[rank % len(crossings)])
+    sc = scenes.config2(N=N_w, crossing=CROSSINGS[rank % len(CROSSINGS)])
     d = sbr.scene_to_device(sc)
     N, K = sc["N"], sc["K"]
     _, a = sbr.launch_dirs(N, with_dirs=False)
@@ -253,14 +271,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     t_total = sum(times) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_total, float(rb)], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
-        t_total, rb_all = float(mx[0]), float(tt[1])
-    else:
-        rb_all = float(rb)
+    t_total, rb_all = reduce_over_ranks(t_total, float(rb), device=dev)
     value = rb_all / t_total / 1e6
 
     # e2e: the same step through the public API from pinned host buffers, with the

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -51,7 +52,25 @@ static void keep_pool_memory() {
     done[dev] = true;
 }
 
+// Host-driven fault injection for tests (SBR_FAULT environment variable, read
+// at each use): "alloc" makes every library allocation fail; "timeout" makes
+// the tensor-core synthesis wait on a barrier nothing arrives at, with a short
+// bound, so that it reports SBR_ERR_TIMEOUT. No injected fault touches the GPU
+// beyond a bounded wait.
+int fault_mode() {
+    const char* e = getenv("SBR_FAULT");
+    if (!e) return kFaultNone;
+    if (!strcmp(e, "alloc")) return kFaultAlloc;
+    if (!strcmp(e, "timeout")) return kFaultTimeout;
+    return kFaultNone;
+}
+
 sbr_status dalloc(void** p, size_t bytes, cudaStream_t s) {
+    if (fault_mode() == kFaultAlloc) {
+        *p = nullptr;
+        set_error("injected allocation failure (SBR_FAULT=alloc), %zu bytes", bytes);
+        return SBR_ERR_ALLOC;
+    }
     keep_pool_memory();
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {

@@ -62,6 +62,9 @@ sbr_status dalloc_n(T** p, size_t n, cudaStream_t s) {
 int sm_count();
 // count of kernel launches made by the library in this process
 void note_launch();
+// test-only fault injection (SBR_FAULT=alloc|timeout)
+enum { kFaultNone = 0, kFaultAlloc = 1, kFaultTimeout = 2 };
+int fault_mode();
 // geodesic directions of subdivision N as double-float, built once per (device, N)
 // and kept for the process: dir_a[i] = (hi.x, hi.y, hi.z, lo.x), dir_b[i] = (lo.y, lo.z)
 sbr_status dir_table(int32_t N, const float4** dir_a, const float2** dir_b, cudaStream_t s);

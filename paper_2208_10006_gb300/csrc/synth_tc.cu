@@ -80,8 +80,8 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-    for (uint32_t it = 0; it < kSpin; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, uint32_t limit = kSpin) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -135,6 +135,7 @@ struct TcArgs {
     const float* dlos;         // [Nr][Nt]
     float2* H;
     unsigned int* status;
+    int inject_timeout;        // test-only: wait on a barrier nothing arrives at
 };
 
 __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constant__ TcArgs a) {
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
     unsigned char* sB_hi = smem + 2 * kABytes;
     unsigned char* sB_lo = smem + 2 * kABytes + kBBytes;
     uint64_t* mbar = (uint64_t*)(smem + kSmemTiles);
+    uint64_t* never = (uint64_t*)(smem + kSmemTiles + 8);   // injected-fault barrier
     uint32_t* tmem_slot = (uint32_t*)(smem + kSmemTiles + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -156,6 +158,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(never)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -165,6 +168,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
     const uint32_t mbar_a = smem_u32(mbar);
     uint32_t phase = 0;
     bool failed = false;
+    // injected fault: the first phase of `never` never completes; the bounded
+    // wait gives up and the CTA takes the same exit as a real timeout
+    if (a.inject_timeout && !mbar_wait(smem_u32(never), 0u, 1u << 12)) failed = true;
 
     // reflected paths are the local indices [n0, n0 + nrefl); the LoS path, when
     // present, is local index 0 and is added exactly in the epilogue
@@ -344,6 +350,7 @@ sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* 
     a.nb0 = sp.nb0;
     a.freqs = freqs; a.dt = dt; a.dr = dr; a.w = w; a.dlos = dl; a.H = H;
     a.status = pl->d_status;  // a bounded wait that gave up is reported by sbr_path_query
+    a.inject_timeout = fault_mode() == kFaultTimeout ? 1 : 0;
     SBR_TRY_CUDA(cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     int64_t items = (int64_t)F * ((Nr + 63) / 64) * ((Nt + kTileN - 1) / kTileN);
     // two CTAs per SM (97 KB shared memory and 256 TMEM columns each): one CTA's
