@@ -150,7 +150,8 @@ typedef struct {
 
 /* sbr_trace_params.flags */
 #define SBR_TRACE_TIMING 1u        /* record CUDA events around each bounce launch (bounce_ms) */
-#define SBR_TRACE_COUNT_VISITS 2u  /* instrumented kernel: count BVH node visits and triangle tests */
+#define SBR_TRACE_COUNT_VISITS 2u  /* instrumented kernel: count BVH node visits, triangle tests
+                                      and near-edge closest hits */
 
 typedef struct {
     int64_t rays;
@@ -162,6 +163,9 @@ typedef struct {
     int64_t node_visits;        /* BVH nodes fetched (SBR_TRACE_COUNT_VISITS only)  */
     int64_t tri_tests;          /* triangle tests (SBR_TRACE_COUNT_VISITS only)     */
     int64_t rx_visits;          /* receiver-BVH nodes fetched (SBR_TRACE_COUNT_VISITS only) */
+    int64_t near_edge_hits;     /* closest hits whose smallest FP64 barycentric is <= 1e-6
+                                   (SBR_TRACE_COUNT_VISITS only): the GPU's own count of the
+                                   edge-ambiguous hits the parity rule exempts */
     int64_t queue[SBR_KMAX + 2];/* rays alive at the start of each bounce           */
     double alpha;
     int32_t status;             /* sbr_status of the device-side checks             */

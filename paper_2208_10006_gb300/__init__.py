@@ -141,6 +141,7 @@ class TraceResult:
         return dict(rays=c.rays, ray_bounces=c.ray_bounces, candidates=c.candidates, keys=c.keys,
                     fp64_segments=c.fp64_segments, fp64_tests=c.fp64_tests,
                     node_visits=c.node_visits, tri_tests=c.tri_tests, rx_visits=c.rx_visits,
+                    near_edge_hits=c.near_edge_hits,
                     queue=list(c.queue), alpha=c.alpha,
                     status=c.status, table_log2=c.table_log2, bounce_ms=list(c.bounce_ms))
 

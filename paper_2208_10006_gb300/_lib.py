@@ -34,6 +34,7 @@ class TraceCounters(C.Structure):
     _fields_ = [("rays", C.c_int64), ("ray_bounces", C.c_int64), ("candidates", C.c_int64),
                 ("keys", C.c_int64), ("fp64_segments", C.c_int64), ("fp64_tests", C.c_int64),
                 ("node_visits", C.c_int64), ("tri_tests", C.c_int64), ("rx_visits", C.c_int64),
+                ("near_edge_hits", C.c_int64),
                 ("queue", C.c_int64 * (KMAX + 2)),
                 ("alpha", C.c_double), ("status", C.c_int32), ("table_log2", C.c_int32),
                 ("bounce_ms", C.c_float * (KMAX + 1)), ("reserved", C.c_int32)]

@@ -274,6 +274,7 @@ sbr_status sbr_trace_stats(const sbr_trace_result* tr, sbr_trace_counters* out) 
     out->node_visits = (int64_t)c.node_visits;
     out->tri_tests = (int64_t)c.tri_tests;
     out->rx_visits = (int64_t)c.rx_visits;
+    out->near_edge_hits = (int64_t)c.near_edge_hits;
     for (int k = 0; k < SBR_KMAX + 2; ++k) out->queue[k] = (int64_t)c.queue[k];
     out->alpha = alpha;
     out->table_log2 = tr->table_log2;

@@ -139,6 +139,7 @@ struct TraceCountersDev {
     unsigned long long node_visits;  // instrumented traces only
     unsigned long long tri_tests;
     unsigned long long rx_visits;
+    unsigned long long near_edge_hits;
     unsigned int status;
     unsigned int pad;
 };

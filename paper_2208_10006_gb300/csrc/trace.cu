@@ -265,6 +265,22 @@ __device__ __forceinline__ bool mt64(const float4* __restrict__ tris, int32_t j,
     return u >= 0.0 && v >= 0.0 && (1.0 - u - v) >= 0.0 && t > 0.0;
 }
 
+// smallest FP64 barycentric of the segment's hit on face j (instrumented
+// traces: a hit at or below 1e-6 is edge-ambiguous in the parity rule)
+__device__ __forceinline__ double min_bary64(const float4* __restrict__ tris, int32_t j, d3 o, d3 d) {
+    float4 a = __ldg(tris + 3 * j), b = __ldg(tris + 3 * j + 1), c = __ldg(tris + 3 * j + 2);
+    d3 v0 = mk3(a.x, a.y, a.z), v1 = mk3(b.x, b.y, b.z), v2 = mk3(c.x, c.y, c.z);
+    d3 e1 = v1 - v0, e2 = v2 - v0;
+    d3 p = cross(d, e2);
+    double det = dot(e1, p);
+    if (det == 0.0) return 0.0;
+    double inv = 1.0 / det;
+    d3 s = o - v0;
+    double u = dot(s, p) * inv;
+    double v = dot(d, cross(s, e1)) * inv;
+    return fmin(fmin(u, v), 1.0 - u - v);
+}
+
 __device__ __forceinline__ bool box_hit64(const float* b, d3 o, d3 inv, double tmax) {
     double t0x = ((double)b[0] - o.x) * inv.x, t1x = ((double)b[3] - o.x) * inv.x;
     double t0y = ((double)b[1] - o.y) * inv.y, t1y = ((double)b[4] - o.y) * inv.y;
@@ -459,7 +475,7 @@ template <bool kCount>
 __global__ void __launch_bounds__(kTraceThreads, 8)
 k_trace_bounce(const __grid_constant__ TraceArgs a) {
     int stack[kStack];
-    unsigned visits = 0, tests = 0, rx_visits = 0;
+    unsigned visits = 0, tests = 0, rx_visits = 0, edge = 0;
     const int lane = threadIdx.x & 31;
     const unsigned long long n_in = a.bounce == 0 ? (unsigned long long)a.R : *a.n_in;
     for (;;) {
@@ -529,6 +545,11 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
                     t = df_div(df_sub(c, df3_dot(n, o)), df3_dot(n, d));
                 }
             }
+            if (kCount && j >= 0) {
+                d3 o64 = mk3(df_to_double(o.x), df_to_double(o.y), df_to_double(o.z));
+                d3 d64 = mk3(df_to_double(d.x), df_to_double(d.y), df_to_double(d.z));
+                edge += min_bary64(a.tris, j, o64, d64) <= 1e-6 ? 1u : 0u;
+            }
             receive<kCount>(a, o, d, L, t, j >= 0, r, ray, stack, &rx_visits);
             if (j >= 0 && a.bounce < a.K) {
                 df c;
@@ -551,18 +572,20 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
             }
         }
         if (kCount) {
-            unsigned long long v = visits, w = tests, x = rx_visits;
+            unsigned long long v = visits, w = tests, x = rx_visits, e = edge;
             for (int o = 16; o; o >>= 1) {
                 v += __shfl_xor_sync(0xffffffffu, v, o);
                 w += __shfl_xor_sync(0xffffffffu, w, o);
                 x += __shfl_xor_sync(0xffffffffu, x, o);
+                e += __shfl_xor_sync(0xffffffffu, e, o);
             }
             if (lane == 0) {
                 atomicAdd(&a.cnt->node_visits, v);
                 atomicAdd(&a.cnt->tri_tests, w);
                 atomicAdd(&a.cnt->rx_visits, x);
+                if (e) atomicAdd(&a.cnt->near_edge_hits, e);
             }
-            visits = tests = rx_visits = 0;
+            visits = tests = rx_visits = edge = 0;
         }
         unsigned mask = __ballot_sync(0xffffffffu, survive);
         if (mask) {

@@ -301,6 +301,21 @@ def two_ray(h_tx: float = 10.0, h_rx: float = 2.0, dist: float = 50.0, f: float 
                  [(dist, 0.0, h_rx)], [f], N, 1, pol=pol)
 
 
+def edge_ceiling(N: int = 20):
+    """A ceiling z=10 of two triangles that share the edge x=0 (y in
+    [-100,100]; third vertices (+-97.3, 3.1), off any symmetry of the launch
+    grid); Tx at the origin, one Rx below it at (30,20,-5), K=1. Every
+    launch direction with d_x == 0 exactly (the 4 icosahedron vertices with
+    x=0 and the subdivision points of the edge between two of them) that goes
+    up meets the ceiling on the shared edge: an edge-ambiguous closest hit by
+    construction."""
+    ceil = np.array([[[0, -100, 10], [0, 100, 10], [-97.3, 3.1, 10]],
+                     [[0, -100, 10], [97.3, 3.1, 10], [0, 100, 10]]], dtype=np.float64)
+    tri, sid = _assemble([ceil])
+    return _base("edge_ceiling", tri, sid, [[5.31, 0.48, 0.0]], (0.0, 0.0, 0.0),
+                 [(30.0, 20.0, -5.0)], [28e9], N, 1)
+
+
 def corner_reflector(N: int = 150, K: int = 2):
     """Two perpendicular planes: ground z=0 over [-50,20]x[-50,50] and a wall
     x=20 over y in [-50,50], z in [0,60]. Tx (0,0,5), Rx (10,8,3): both in

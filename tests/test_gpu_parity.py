@@ -199,9 +199,30 @@ def test_bvh_shape(sbr):
         d = sbr.scene_to_device(sc)
         info = sbr.build_bvh(d["tri"], d["surface_id"], d["S"]).info()
         T = len(sc["tri"])
-        # 4-wide nodes: at most one per binary internal node, at least one
+        # two-child nodes over leaves of up to two triangles: at most T-1 nodes
         assert info["T"] == T and 1 <= info["n_nodes"] <= max(1, T - 1)
         assert 1 <= info["depth"] <= 64
+
+
+@pytest.mark.parametrize("N", [20, 33])
+def test_near_edge_hits_are_counted(sbr, N):
+    # rays with d_x == 0 that go up hit the ceiling on its shared edge; the
+    # instrumented trace counts them, and so does the oracle's edge flag
+    sc = scenes.edge_ceiling(N=N)
+    dirs = oracle.geodesic_dirs(N)
+    up = dirs[:, 2] > 0
+    xh = 10.0 * dirs[:, 0] / np.where(up, dirs[:, 2], 1.0)
+    yh = 10.0 * dirs[:, 1] / np.where(up, dirs[:, 2], 1.0)
+    expect = int(np.sum(up & (np.abs(xh) <= 1e-4) & (np.abs(yh) < 99.0)))
+    assert expect >= N + 1
+    _, fl, _ = oracle.trace(sc)
+    assert int(np.sum((fl & oracle.FLAG_NEAR_EDGE) != 0)) == expect
+    d = sbr.scene_to_device(sc)
+    bvh = sbr.build_bvh(d["tri"], d["surface_id"], d["S"])
+    st = sbr.trace(bvh, d["tx"], d["rx"], N, 1, count_visits=True).stats()
+    assert st["near_edge_hits"] == expect
+    # the default (uninstrumented) kernel leaves the counter at zero
+    assert sbr.trace(bvh, d["tx"], d["rx"], N, 1).stats()["near_edge_hits"] == 0
 
 
 @pytest.mark.parametrize("ny,nz,nr,F", [(16, 16, 64, 16), (10, 10, 10, 5), (20, 15, 70, 3)])
