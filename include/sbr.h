@@ -57,6 +57,8 @@ typedef enum {
 #define SBR_SYNTH_FP64 0    /* FP64 CUDA-core summation                          */
 #define SBR_SYNTH_FP32 1    /* FP32 CUDA-core summation, FP64 delay phase        */
 #define SBR_SYNTH_BF16X3 2  /* tcgen05 BF16 hi/lo split (3 products), FP32 TMEM  */
+#define SBR_SYNTH_FP16X3 3  /* tcgen05 FP16 hi/lo split (3 products), weights scaled
+                               per frequency by a power of two, FP32 TMEM          */
 
 /* number of stats columns written by sbr_pdp_angles */
 #define SBR_NSTATS 7
@@ -250,8 +252,9 @@ sbr_status sbr_path_gains(const sbr_path_list* pl, const sbr_material* mats, int
  * T_0 = the trace's tx, R_0 = rx_xyz[rx_index]; a LoS path uses the exact
  * |T_p - R_q| in its phase. gains: dev complex64 [P*F] from sbr_path_gains.
  * tx_elem: dev double [Nt*3]; rx_elem: dev double [Nr*3].
- * precision: SBR_SYNTH_FP64 / FP32 (CUDA cores) or SBR_SYNTH_BF16X3
- * (tcgen05 tensor cores, U diag(w) V^T contraction, FP32 accumulation).
+ * precision: SBR_SYNTH_FP64 / FP32 (CUDA cores) or SBR_SYNTH_BF16X3 /
+ * SBR_SYNTH_FP16X3 (tcgen05 tensor cores, U diag(w) V^T contraction, FP32
+ * accumulation; FP16X3 keeps ~2^-22 of each operand where BF16X3 keeps ~2^-16).
  * H: dev complex64 [F*Nr*Nt], element (f, q, p) at (f*Nr + q)*Nt + p.
  */
 sbr_status sbr_synthesize_H(const sbr_path_list* pl, const void* gains, const double* freqs_hz,

@@ -22,12 +22,12 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (KMAX, NSTATS, POL_H, POL_V, SYNTH_BF16X3, SYNTH_FP32, SYNTH_FP64,
+from ._lib import (KMAX, NSTATS, POL_H, POL_V, SYNTH_BF16X3, SYNTH_FP16X3, SYNTH_FP32, SYNTH_FP64,
                    STATUS_NAMES)
 
 __all__ = ["SbrError", "BVH", "TraceResult", "PathList", "launch_dirs", "build_bvh", "trace",
            "paths", "path_gains", "synthesize_H", "pdp_angles", "capacity", "version",
-           "POL_V", "POL_H", "SYNTH_FP64", "SYNTH_FP32", "SYNTH_BF16X3", "KMAX", "NSTATS",
+           "POL_V", "POL_H", "SYNTH_FP64", "SYNTH_FP32", "SYNTH_BF16X3", "SYNTH_FP16X3", "KMAX", "NSTATS",
            "scene_to_device", "run_scene"]
 
 

@@ -14,7 +14,7 @@ STATUS_NAMES = {0: "SBR_OK", 1: "SBR_ERR_INVALID_ARG", 2: "SBR_ERR_CUDA", 3: "SB
 KMAX = 8
 NSTATS = 7
 POL_V, POL_H = 0, 1
-SYNTH_FP64, SYNTH_FP32, SYNTH_BF16X3 = 0, 1, 2
+SYNTH_FP64, SYNTH_FP32, SYNTH_BF16X3, SYNTH_FP16X3 = 0, 1, 2, 3
 TRACE_TIMING = 1
 TRACE_COUNT_VISITS = 2
 

@@ -415,8 +415,9 @@ sbr_status sbr_synthesize_H(const sbr_path_list* pl, const void* gains, const do
             return synth_simt_run(pl, (const float2*)gains, freqs_hz, F, tx_elem, Nt, rx_elem, Nr,
                                   rx_index, precision == SBR_SYNTH_FP64, (float2*)H, s);
         case SBR_SYNTH_BF16X3:
+        case SBR_SYNTH_FP16X3:
             return synth_tc_run(pl, (const float2*)gains, freqs_hz, F, tx_elem, Nt, rx_elem, Nr,
-                                rx_index, (float2*)H, s);
+                                rx_index, (float2*)H, precision == SBR_SYNTH_FP16X3, s);
         default:
             set_error("unknown precision %d", precision);
             return SBR_ERR_INVALID_ARG;

@@ -209,7 +209,7 @@ sbr_status synth_simt_run(const sbr_path_list* pl, const float2* g, const double
                           int32_t rx_index, bool fp64, float2* H, cudaStream_t s);
 sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* freqs, int32_t F,
                         const double* tx_elem, int32_t Nt, const double* rx_elem, int32_t Nr,
-                        int32_t rx_index, float2* H, cudaStream_t s);
+                        int32_t rx_index, float2* H, bool f16, cudaStream_t s);
 sbr_status pdp_run(const sbr_path_list* pl, const float2* g, int32_t F, int32_t f_index, double fc,
                    double bin_s, int32_t n_bins, float* pdp, double* stats, cudaStream_t s);
 sbr_status capacity_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,

@@ -10,9 +10,12 @@
 //   A'[2q,   2n] =  Re A,  A'[2q,   2n+1] = -Im A
 //   A'[2q+1, 2n] =  Im A,  A'[2q+1, 2n+1] =  Re A
 //   B'[2n, p]    =  Re V,  B'[2n+1, p]    =  Im V.
-// Each operand is split x = hi + lo into two BF16 values and the product is
-// taken as hi*hi + hi*lo + lo*hi (the lo*lo term, ~2^-18 relative, dropped),
-// accumulated in FP32 in tensor memory. The phasors are generated on chip
+// Each operand is split x = hi + lo into two 16-bit values and the product is
+// taken as hi*hi + hi*lo + lo*hi, accumulated in FP32 in tensor memory. Two
+// forms: BF16 (the lo*lo term, ~2^-16 relative, dropped) and FP16 (~2^-22
+// relative, with 5 exponent bits: A' is scaled per frequency by a power of two
+// that brings max_n |w_n| into [1/2, 1), and the accumulator is scaled back,
+// both exactly). The phasors are generated on chip
 // (FP32 phase from the FP64-prepared delays) straight into 128-byte-swizzled
 // K-major shared-memory tiles; one thread issues tcgen05.mma (M=128, N=256,
 // K=16) and commits to an mbarrier; the epilogue reads TMEM with tcgen05.ld,
@@ -23,6 +26,7 @@
 // ST_TIMEOUT, releases its tensor memory and returns.
 #include <algorithm>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "sbr_internal.cuh"
 #include "synth_common.cuh"
@@ -64,15 +68,20 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
     return d;
 }
 
-// instruction descriptor: kind::f16, A/B BF16, D F32, both K-major, M=128, N=256
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
-                            ((uint32_t)(kTileM >> 4) << 24);
+// instruction descriptor: kind::f16, D F32, both K-major, M=128, N=256; A and
+// B both BF16 (format 1) or both FP16 (format 0)
+template <bool kF16>
+constexpr uint32_t idesc() {
+    return (1u << 4) | (kF16 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(kTileN >> 3) << 17) |
+           ((uint32_t)(kTileM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+template <bool kF16>
+__device__ __forceinline__ void mma_16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+        "l"(a), "l"(b), "r"(idesc<kF16>()), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
@@ -116,12 +125,20 @@ __device__ __forceinline__ void phasor(float cycles, float& s, float& c) {
     __sincosf(-6.283185307179586f * r, &s, &c);
 }
 
-// x = hi + lo, both BF16; returns the two as raw 16-bit patterns
-__device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) {
-    __nv_bfloat16 h = __float2bfloat16_rn(x);
-    __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-    hi = __bfloat16_as_ushort(h);
-    lo = __bfloat16_as_ushort(l);
+// x = hi + lo, both BF16 or both FP16; returns the two as raw 16-bit patterns
+template <bool kF16>
+__device__ __forceinline__ void split16(float x, uint16_t& hi, uint16_t& lo) {
+    if (kF16) {
+        __half h = __float2half_rn(x);
+        __half l = __float2half_rn(x - __half2float(h));
+        hi = __half_as_ushort(h);
+        lo = __half_as_ushort(l);
+    } else {
+        __nv_bfloat16 h = __float2bfloat16_rn(x);
+        __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(l);
+    }
 }
 
 struct TcArgs {
@@ -138,8 +155,10 @@ struct TcArgs {
     int inject_timeout;        // test-only: wait on a barrier nothing arrives at
 };
 
+template <bool kF16>
 __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constant__ TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
+    __shared__ float s_red[kTcThreads / 32];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA_hi = smem;
     unsigned char* sA_lo = smem + kABytes;
@@ -170,7 +189,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
     bool failed = false;
     // injected fault: the first phase of `never` never completes; the bounded
     // wait gives up and the CTA takes the same exit as a real timeout
-    if (a.inject_timeout && !mbar_wait(smem_u32(never), 0u, 1u << 12)) failed = true;
+    if (a.inject_timeout) failed = __syncthreads_or(!mbar_wait(smem_u32(never), 0u, 1u << 12)) != 0;
 
     // reflected paths are the local indices [n0, n0 + nrefl); the LoS path, when
     // present, is local index 0 and is added exactly in the epilogue
@@ -185,6 +204,27 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
         const int rem = (int)(it - (int64_t)f * mtiles * ntiles);
         const int q0 = (rem / ntiles) * 64, p0 = (rem % ntiles) * kTileN;
         const float foc = (float)(a.freqs[f] / kC0);
+        // FP16 form: power-of-two scale of this frequency's weights (exact)
+        float sc = 1.f, isc = 1.f;
+        if (kF16) {
+            float m = 0.f;
+            for (int n = n0 + tid; n < n0 + nrefl; n += kTcThreads) {
+                float2 ww = __ldg(a.w + (int64_t)f * a.Pr + n);
+                m = fmaxf(m, fmaxf(fabsf(ww.x), fabsf(ww.y)));
+            }
+            for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) s_red[warp] = m;
+            __syncthreads();
+            m = s_red[0];
+            for (int k = 1; k < kTcThreads / 32; ++k) m = fmaxf(m, s_red[k]);
+            __syncthreads();  // s_red is rewritten for the next item
+            if (m > 0.f) {
+                int e;
+                frexpf(m, &e);
+                sc = ldexpf(1.f, -e);
+                isc = ldexpf(1.f, e);
+            }
+        }
         for (int c = 0; c < nch && !failed; ++c) {
             const int nb = n0 + c * kChunkP;
             const int cnt = min(kChunkP, n0 + nrefl - nb);
@@ -201,11 +241,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
                     phasor(foc * __ldg(a.dr + (int64_t)n * a.Nr + q), s, co);
                     ar = ww.x * co - ww.y * s;
                     ai = ww.x * s + ww.y * co;
+                    if (kF16) { ar *= sc; ai *= sc; }
                 }
                 uint16_t h0, l0, h1, l1, h2, l2;
-                split_bf16(ar, h0, l0);
-                split_bf16(-ai, h1, l1);
-                split_bf16(ai, h2, l2);
+                split16<kF16>(ar, h0, l0);
+                split16<kF16>(-ai, h1, l1);
+                split16<kF16>(ai, h2, l2);
                 uint32_t o0 = sw128(2 * ql, 2 * nl), o1 = sw128(2 * ql + 1, 2 * nl);
                 *(uint32_t*)(sA_hi + o0) = (uint32_t)h0 | ((uint32_t)h1 << 16);
                 *(uint32_t*)(sA_lo + o0) = (uint32_t)l0 | ((uint32_t)l1 << 16);
@@ -221,8 +262,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
                 float vr = 0.f, vi = 0.f;
                 if (nl < cnt && p < a.Nt) phasor(foc * __ldg(a.dt + (int64_t)n * a.Nt + p), vi, vr);
                 uint16_t h0, l0, h1, l1;
-                split_bf16(vr, h0, l0);
-                split_bf16(vi, h1, l1);
+                split16<kF16>(vr, h0, l0);
+                split16<kF16>(vi, h1, l1);
                 uint32_t o = sw128(pl, 2 * nl);
                 *(uint32_t*)(sB_hi + o) = (uint32_t)h0 | ((uint32_t)h1 << 16);
                 *(uint32_t*)(sB_lo + o) = (uint32_t)l0 | ((uint32_t)l1 << 16);
@@ -235,16 +276,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
                 uint64_t dBh = make_desc(smem_u32(sB_hi)), dBl = make_desc(smem_u32(sB_lo));
                 for (int ks = 0; ks < 4; ++ks) {
                     uint64_t off = (uint64_t)(ks * 32) >> 4;  // 16 BF16 along K
-                    mma_bf16(tmem, dAh + off, dBh + off, (c > 0 || ks > 0) ? 1u : 0u);
-                    mma_bf16(tmem, dAh + off, dBl + off, 1u);
-                    mma_bf16(tmem, dAl + off, dBh + off, 1u);
+                    mma_16<kF16>(tmem, dAh + off, dBh + off, (c > 0 || ks > 0) ? 1u : 0u);
+                    mma_16<kF16>(tmem, dAh + off, dBl + off, 1u);
+                    mma_16<kF16>(tmem, dAl + off, dBh + off, 1u);
                 }
                 mma_commit(mbar_a);
             }
-            if (!mbar_wait(mbar_a, phase)) failed = true;
+            const bool ok = mbar_wait(mbar_a, phase);
             phase ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            __syncthreads();
+            failed = __syncthreads_or(!ok) != 0;  // one decision for the whole CTA
         }
         if (failed) break;
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns 128 (w / 4) .. +127
@@ -270,6 +311,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
                 float got = __shfl_xor_sync(0xffffffffu, send, 1);
                 if (part == 0) { re[k] = mine_lo; im[k] = got; }
                 else { re[k] = got; im[k] = mine_hi; }
+                if (kF16) { re[k] *= isc; im[k] *= isc; }
             }
             const int pb = p0 + col0 + 16 * part;
             if (q < a.Nr) {
@@ -330,7 +372,7 @@ inline unsigned nb256(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + 25
 
 sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* freqs, int32_t F,
                         const double* tx_elem, int32_t Nt, const double* rx_elem, int32_t Nr,
-                        int32_t rx_index, float2* H, cudaStream_t s) {
+                        int32_t rx_index, float2* H, bool f16, cudaStream_t s) {
     SynthPrep sp;
     SBR_TRY(synth_prepare(pl, g, freqs, F, tx_elem, Nt, rx_elem, Nr, rx_index, &sp, s));
     const int32_t Pr = std::max(sp.Pr, 1);
@@ -351,12 +393,13 @@ sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* 
     a.freqs = freqs; a.dt = dt; a.dr = dr; a.w = w; a.dlos = dl; a.H = H;
     a.status = pl->d_status;  // a bounded wait that gave up is reported by sbr_path_query
     a.inject_timeout = fault_mode() == kFaultTimeout ? 1 : 0;
-    SBR_TRY_CUDA(cudaFuncSetAttribute(k_synth_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    auto kern = f16 ? k_synth_tc<true> : k_synth_tc<false>;
+    SBR_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     int64_t items = (int64_t)F * ((Nr + 63) / 64) * ((Nt + kTileN - 1) / kTileN);
     // two CTAs per SM (97 KB shared memory and 256 TMEM columns each): one CTA's
     // MMA and epilogue overlap the other's phasor generation
     int grid = (int)std::min<int64_t>(items, 2 * (int64_t)sm_count());
-    ::sbr::note_launch(), k_synth_tc<<<grid, kTcThreads, kSmemBytes, s>>>(a);
+    ::sbr::note_launch(), kern<<<grid, kTcThreads, kSmemBytes, s>>>(a);
     SBR_TRY_CUDA(cudaGetLastError());
     dfree(dt, s); dfree(dr, s); dfree(dl, s); dfree(w, s);
     synth_release(&sp, s);
