@@ -237,7 +237,7 @@ void sbr_path_list_free(sbr_path_list* pl);
  * Rx polarisation. The delay phasor exp(-j 2 pi f L / c) is not included.
  * mats: dev sbr_material [S] indexed by surface id. freqs_hz: dev double [F].
  * gamma_db_km, disp_deg_km: dev float [F] or NULL (zero). pol: SBR_POL_V/H.
- * gains: dev complex64 [P*F] (re, im interleaved), path-major.
+ * gains: dev complex64 [P*F] (re, im interleaved), path-major; may be NULL when P = 0.
  */
 sbr_status sbr_path_gains(const sbr_path_list* pl, const sbr_material* mats, int32_t S,
                           const double* freqs_hz, int32_t F, const float* gamma_db_km,
@@ -250,7 +250,7 @@ sbr_status sbr_path_gains(const sbr_path_list* pl, const sbr_material* mats, int
  *   H[f,q,p] = sum_n g_n(f) exp(-j 2 pi f (L_n + dt_pn + dr_qn) / c),
  *   dt_pn = |T_p - P1| - |T_0 - P1|,  dr_qn = |R_q - Pm| - |R_0 - Pm|,
  * T_0 = the trace's tx, R_0 = rx_xyz[rx_index]; a LoS path uses the exact
- * |T_p - R_q| in its phase. gains: dev complex64 [P*F] from sbr_path_gains.
+ * |T_p - R_q| in its phase. gains: dev complex64 [P*F] from sbr_path_gains (NULL when P = 0).
  * tx_elem: dev double [Nt*3]; rx_elem: dev double [Nr*3].
  * precision: SBR_SYNTH_FP64 / FP32 (CUDA cores) or SBR_SYNTH_BF16X3 /
  * SBR_SYNTH_FP16X3 (tcgen05 tensor cores, U diag(w) V^T contraction, FP32
@@ -304,6 +304,117 @@ sbr_status sbr_capacity(const void* H, int32_t F, int32_t Nr, int32_t Nt, const 
  */
 sbr_status sbr_capacity_noalloc(const void* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,
                                 int32_t n_snr, double* C, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched execution: many Tx-Rx jobs (each one Tx reference point, one Rx
+ * reference point, its own ray count, reflection depth, frequency grid and
+ * arrays) over several scenes, run as one CUDA-graph launch. Per job the
+ * result is that of sbr_trace + sbr_paths + sbr_path_gains +
+ * sbr_synthesize_H on the same inputs (the same arithmetic in batched
+ * kernels): Sec. II-A ray launching, tracing, reception and effective paths,
+ * Eq. 1, 3, 6-10 gains and Eq. 13-14 synthesis, per job. Jobs are grouped
+ * into waves whose rays fit the ray-queue capacity; each wave runs the
+ * bounces as persistent launches over all of its jobs' rays, then the path,
+ * gain and tensor-core synthesis kernels over all of its jobs.
+ */
+typedef struct sbr_batch sbr_batch;
+
+typedef struct {
+    int32_t scene;            /* index into the scenes given to sbr_batch_create           */
+    int32_t subdiv_N;         /* rays R = 10 N^2 + 2, 1 <= N <= 1295 (R < 2^24)             */
+    int32_t max_bounces;      /* K, 0..8                                                   */
+    int32_t pol;              /* SBR_POL_V or SBR_POL_H, both ends                         */
+    double tx[3];             /* Tx reference point (m)                                    */
+    double rx[3];             /* Rx reference point (m)                                    */
+    double alpha;             /* reception-sphere angle (rad); 0 = the launch grid's own   */
+    int32_t F;                /* frequencies                                               */
+    int32_t Nt;               /* transmit elements                                         */
+    int32_t Nr;               /* receive elements                                          */
+    int32_t reserved;
+    const double* freqs_hz;   /* dev [F]                                                   */
+    const float* gamma_db_km; /* dev [F] or NULL (Eq. 9)                                   */
+    const float* disp_deg_km; /* dev [F] or NULL (Eq. 10)                                  */
+    const double* tx_elem;    /* dev [Nt*3] element positions                              */
+    const double* rx_elem;    /* dev [Nr*3]                                                */
+    void* H;                  /* dev complex64 [F*Nr*Nt], written by sbr_batch_run          */
+} sbr_batch_job;
+
+typedef struct {
+    int64_t wave_rays;        /* ray-queue capacity of a wave (rays); 0 = 2^26               */
+    int32_t path_cap;         /* keys and paths kept per job; 0 = 512                       */
+    int32_t table_log2;       /* dedup table slots per wave; 0 = from jobs per wave x path_cap */
+    int32_t tile_n;           /* tensor-core tile width: 64, 128 or 256; 0 = 128             */
+    int32_t trace_blocks_per_sm; /* persistent bounce grid; 0 = occupancy limit              */
+    int32_t precision;        /* SBR_SYNTH_FP16X3 (0 = this) or SBR_SYNTH_BF16X3             */
+    int32_t use_graph;        /* 1 (default when the config pointer is NULL): capture the   */
+                              /* whole batch into one CUDA graph; 0: plain stream launches  */
+} sbr_batch_config;
+
+typedef struct {
+    int32_t n_jobs;
+    int32_t n_waves;
+    int32_t graph_kernels;    /* kernel nodes of one sbr_batch_run                          */
+    int32_t status;           /* worst sbr_status over the jobs of the last run             */
+    int32_t max_keys;         /* largest dedup key count of a job in the last run            */
+    int32_t reserved;
+    int64_t rays;             /* rays of all jobs                                           */
+    int64_t ray_bounces;      /* segments traced in the last run                            */
+    int64_t paths;            /* paths kept over all jobs in the last run                   */
+    sbr_batch_config config;  /* the configuration in force (defaults resolved)             */
+} sbr_batch_info;
+
+/*
+ * sbr_batch_create - validate the jobs, group them into waves, build the
+ * launch-direction tables and alpha of every distinct N, and allocate every
+ * buffer of the batch (no allocation happens in sbr_batch_run).
+ * scenes: n_scenes BVH handles; mats[s]: dev array of scenes[s]'s surfaces
+ * (at least its S entries). jobs: host array of n_jobs (copied). cfg may be
+ * NULL (defaults). The scene handles and the jobs' device arrays must outlive
+ * the batch. Synchronous. Errors: SBR_ERR_INVALID_ARG (a job or config field
+ * out of range; nothing allocated), SBR_ERR_ALLOC.
+ */
+sbr_status sbr_batch_create(const sbr_bvh* const* scenes, const sbr_material* const* mats,
+                            int32_t n_scenes, const sbr_batch_job* jobs, int32_t n_jobs,
+                            const sbr_batch_config* cfg, sbr_batch** out, void* stream);
+/*
+ * sbr_batch_run - run every job; writes each job's H. With use_graph the
+ * first call captures the batch into a CUDA graph on a stream of its own and
+ * every call launches that graph on `stream`. Asynchronous; per-job failures
+ * (a full dedup table or path store: SBR_ERR_CAPACITY, a bounded wait that
+ * gave up: SBR_ERR_TIMEOUT) are reported by sbr_batch_query.
+ */
+sbr_status sbr_batch_run(sbr_batch* b, void* stream);
+/*
+ * sbr_batch_query - synchronous: per job the number of paths (n_paths, host
+ * int32 [n_jobs], may be NULL) and its sbr_status (status, host int32
+ * [n_jobs], may be NULL) of the last run, and the batch summary (info, may be
+ * NULL). Returns the worst job status.
+ */
+sbr_status sbr_batch_query(const sbr_batch* b, int32_t* n_paths, int32_t* status, sbr_batch_info* info);
+/*
+ * sbr_batch_export - copy the first n paths of one job (n <= its n_paths) in
+ * the layouts of sbr_path_export (receiver index implied: 0) and, if gains is
+ * not NULL, its complex64 gains [n*F]. Device pointers may be NULL to skip a
+ * field. Asynchronous on `stream`.
+ */
+sbr_status sbr_batch_export(const sbr_batch* b, int32_t job, int32_t n, int32_t* n_bounce,
+                            int32_t* surf_seq, int32_t* face_seq, double* pts, double* length,
+                            double* aod, double* aoa, uint32_t* ray_id, float* dist, void* gains,
+                            void* stream);
+void sbr_batch_free(sbr_batch* b);
+
+/*
+ * sbr_batch_tune - autotuner: for the given jobs (typically a sample of a
+ * larger batch) time each candidate of tile_n x trace_blocks_per_sm x
+ * wave_rays (its own batches, two warm runs and the median of three timed
+ * ones), size path_cap to the largest path count seen (x 1.5, a power of two,
+ * at least 64) and return the fastest configuration in *cfg (fields left
+ * non-zero by the caller are kept fixed) and its time per run in *ms.
+ * Synchronous.
+ */
+sbr_status sbr_batch_tune(const sbr_bvh* const* scenes, const sbr_material* const* mats,
+                          int32_t n_scenes, const sbr_batch_job* jobs, int32_t n_jobs,
+                          sbr_batch_config* cfg, double* ms, void* stream);
 
 #ifdef __cplusplus
 }

@@ -28,7 +28,7 @@ from ._lib import (KMAX, NSTATS, POL_H, POL_V, SYNTH_BF16X3, SYNTH_FP16X3, SYNTH
 __all__ = ["SbrError", "BVH", "TraceResult", "PathList", "launch_dirs", "build_bvh", "trace",
            "paths", "path_gains", "synthesize_H", "pdp_angles", "capacity", "version",
            "POL_V", "POL_H", "SYNTH_FP64", "SYNTH_FP32", "SYNTH_BF16X3", "SYNTH_FP16X3", "KMAX", "NSTATS",
-           "scene_to_device", "run_scene"]
+           "scene_to_device", "run_scene", "Batch", "batch_create", "batch_tune"]
 
 
 class SbrError(RuntimeError):
@@ -318,3 +318,139 @@ def run_scene(sc: dict, alpha: float = 0.0, table_log2: int = 0, stream=None):
     pl = paths(tr, bvh, stream=stream)
     g = path_gains(pl, d["mats"], d["freqs"], d["gamma"], d["disp"], d["pol"], stream=stream)
     return dict(dev=d, bvh=bvh, trace=tr, stats=st, paths=pl, export=pl.export(stream=stream), g=g)
+
+
+# ---------------------------------------------------------------- batched jobs
+class Batch:
+    """Handle of sbr_batch_create: many Tx-Rx jobs over several scenes."""
+
+    def __init__(self, handle, jobs, keep):
+        self._h = handle
+        self.jobs = jobs
+        self._keep = keep   # device tensors the batch reads (scenes' materials, job inputs, H)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def run(self, stream=None):
+        _check(_L().sbr_batch_run(self._h, _stream(stream)))
+
+    def query(self):
+        """(paths per job, sbr_status per job, summary dict); synchronous."""
+        n = len(self.jobs)
+        np_ = np.zeros(n, np.int32)
+        st = np.zeros(n, np.int32)
+        info = _lib.BatchInfo()
+        _L().sbr_batch_query(self._h, np_.ctypes.data_as(C.c_void_p), st.ctypes.data_as(C.c_void_p),
+                             C.byref(info))
+        c = info.config
+        summary = dict(n_jobs=info.n_jobs, n_waves=info.n_waves, graph_kernels=info.graph_kernels,
+                       status=info.status, max_keys=info.max_keys, rays=info.rays,
+                       ray_bounces=info.ray_bounces, paths=info.paths,
+                       config=dict(wave_rays=c.wave_rays, path_cap=c.path_cap, table_log2=c.table_log2,
+                                   tile_n=c.tile_n, trace_blocks_per_sm=c.trace_blocks_per_sm,
+                                   precision=c.precision, use_graph=c.use_graph))
+        return np_, st, summary
+
+    def export(self, job: int, n: int, stream=None) -> dict:
+        """First n paths of a job (n <= its path count) and their gains [n, F]."""
+        dev = _dev()
+        K = KMAX
+        F = int(self.jobs[job]["F"])
+        out = dict(nb=torch.empty(n, dtype=torch.int32, device=dev),
+                   seq=torch.empty((n, K), dtype=torch.int32, device=dev),
+                   face=torch.empty((n, K), dtype=torch.int32, device=dev),
+                   pts=torch.empty((n, K, 3), dtype=torch.float64, device=dev),
+                   L=torch.empty(n, dtype=torch.float64, device=dev),
+                   aod=torch.empty((n, 2), dtype=torch.float64, device=dev),
+                   aoa=torch.empty((n, 2), dtype=torch.float64, device=dev),
+                   ray=torch.empty(n, dtype=torch.int32, device=dev),
+                   dist=torch.empty(n, dtype=torch.float32, device=dev),
+                   g=torch.empty((n, F), dtype=torch.complex64, device=dev))
+        _check(_L().sbr_batch_export(self._h, int(job), int(n), _ptr(out["nb"]), _ptr(out["seq"]),
+                                     _ptr(out["face"]), _ptr(out["pts"]), _ptr(out["L"]), _ptr(out["aod"]),
+                                     _ptr(out["aoa"]), _ptr(out["ray"]),
+                                     _ptr(out["dist"]), _ptr(out["g"]), _stream(stream)))
+        return out
+
+    def free(self):
+        if self._h:
+            _L().sbr_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _batch_args(scenes, jobs):
+    """ctypes arrays for a list of (BVH, materials tensor) scenes and job dicts.
+
+    Job keys: scene, N, K, tx, rx, freqs (float64 CUDA [F]), tx_elem / rx_elem
+    (float64 CUDA [n, 3]); optional: pol, alpha, gamma / disp (float32 CUDA [F]),
+    H (complex64 CUDA [F, Nr, Nt], allocated when absent)."""
+    dev = _dev()
+    ns = len(scenes)
+    sc_arr = (C.c_void_p * ns)(*[s[0].handle.value for s in scenes])
+    mat_arr = (C.c_void_p * ns)(*[s[1].data_ptr() for s in scenes])
+    keep = [s[1] for s in scenes]
+    jarr = (_lib.BatchJob * len(jobs))()
+    for i, j in enumerate(jobs):
+        F, Nt, Nr = int(j["freqs"].shape[0]), int(j["tx_elem"].shape[0]), int(j["rx_elem"].shape[0])
+        for key in ("freqs", "tx_elem", "rx_elem"):
+            assert j[key].is_cuda and j[key].dtype == torch.float64 and j[key].is_contiguous(), key
+        if j.get("H") is None:
+            j["H"] = torch.empty((F, Nr, Nt), dtype=torch.complex64, device=dev)
+        j["F"] = F
+        b = jarr[i]
+        b.scene = int(j["scene"])
+        b.subdiv_N = int(j["N"])
+        b.max_bounces = int(j["K"])
+        b.pol = POL_V if j.get("pol", "V") in ("V", POL_V) else POL_H
+        for k in range(3):
+            b.tx[k] = float(j["tx"][k])
+            b.rx[k] = float(j["rx"][k])
+        b.alpha = float(j.get("alpha", 0.0))
+        b.F, b.Nt, b.Nr = F, Nt, Nr
+        b.freqs_hz = j["freqs"].data_ptr()
+        b.gamma_db_km = j["gamma"].data_ptr() if j.get("gamma") is not None else None
+        b.disp_deg_km = j["disp"].data_ptr() if j.get("disp") is not None else None
+        b.tx_elem = j["tx_elem"].data_ptr()
+        b.rx_elem = j["rx_elem"].data_ptr()
+        b.H = j["H"].data_ptr()
+        keep += [j[k] for k in ("freqs", "tx_elem", "rx_elem", "H", "gamma", "disp") if j.get(k) is not None]
+    return sc_arr, mat_arr, jarr, keep
+
+
+def _batch_config(config):
+    c = _lib.BatchConfig()
+    c.use_graph = 1
+    for k, v in (config or {}).items():
+        setattr(c, k, int(v))
+    return c
+
+
+def batch_create(scenes, jobs, config=None, stream=None) -> Batch:
+    """sbr_batch_create. scenes: list of (BVH, materials float64 CUDA [S, 3])."""
+    sc_arr, mat_arr, jarr, keep = _batch_args(scenes, jobs)
+    c = _batch_config(config)
+    h = C.c_void_p()
+    _check(_L().sbr_batch_create(sc_arr, mat_arr, len(scenes), jarr, len(jobs), C.byref(c), C.byref(h),
+                                 _stream(stream)))
+    return Batch(h, jobs, keep + [s[0] for s in scenes])
+
+
+def batch_tune(scenes, jobs, config=None, stream=None):
+    """sbr_batch_tune on these jobs; returns (config dict, ms per run)."""
+    sc_arr, mat_arr, jarr, keep = _batch_args(scenes, jobs)
+    c = _batch_config(config)
+    ms = C.c_double()
+    _check(_L().sbr_batch_tune(sc_arr, mat_arr, len(scenes), jarr, len(jobs), C.byref(c), C.byref(ms),
+                               _stream(stream)))
+    del keep
+    return dict(wave_rays=c.wave_rays, path_cap=c.path_cap, table_log2=c.table_log2, tile_n=c.tile_n,
+                trace_blocks_per_sm=c.trace_blocks_per_sm, precision=c.precision,
+                use_graph=c.use_graph), ms.value

@@ -21,7 +21,9 @@ TRACE_COUNT_VISITS = 2
 EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_count", "sbr_launch_dirs", "sbr_build_bvh", "sbr_bvh_free",
            "sbr_bvh_query", "sbr_trace", "sbr_trace_stats", "sbr_trace_free", "sbr_paths",
            "sbr_path_query", "sbr_path_export", "sbr_path_list_free", "sbr_path_gains",
-           "sbr_synthesize_H", "sbr_pdp_angles", "sbr_capacity", "sbr_capacity_noalloc"]
+           "sbr_synthesize_H", "sbr_pdp_angles", "sbr_capacity", "sbr_capacity_noalloc",
+           "sbr_batch_create", "sbr_batch_run", "sbr_batch_query", "sbr_batch_export", "sbr_batch_free",
+           "sbr_batch_tune"]
 
 
 class TraceParams(C.Structure):
@@ -51,7 +53,31 @@ class PathInfo(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class BatchJob(C.Structure):
+    _fields_ = [("scene", C.c_int32), ("subdiv_N", C.c_int32), ("max_bounces", C.c_int32),
+                ("pol", C.c_int32), ("tx", C.c_double * 3), ("rx", C.c_double * 3), ("alpha", C.c_double),
+                ("F", C.c_int32), ("Nt", C.c_int32), ("Nr", C.c_int32), ("reserved", C.c_int32),
+                ("freqs_hz", C.c_void_p), ("gamma_db_km", C.c_void_p), ("disp_deg_km", C.c_void_p),
+                ("tx_elem", C.c_void_p), ("rx_elem", C.c_void_p), ("H", C.c_void_p)]
+
+
+class BatchConfig(C.Structure):
+    _fields_ = [("wave_rays", C.c_int64), ("path_cap", C.c_int32), ("table_log2", C.c_int32),
+                ("tile_n", C.c_int32), ("trace_blocks_per_sm", C.c_int32), ("precision", C.c_int32),
+                ("use_graph", C.c_int32)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("n_jobs", C.c_int32), ("n_waves", C.c_int32), ("graph_kernels", C.c_int32),
+                ("status", C.c_int32), ("max_keys", C.c_int32), ("reserved", C.c_int32),
+                ("rays", C.c_int64), ("ray_bounces", C.c_int64), ("paths", C.c_int64),
+                ("config", BatchConfig)]
+
+
 assert C.sizeof(TraceParams) == 64
+assert C.sizeof(BatchJob) == 136
+assert C.sizeof(BatchConfig) == 32
+assert C.sizeof(BatchInfo) == 80
 
 _lib = None
 
@@ -105,5 +131,18 @@ def load() -> C.CDLL:
     L.sbr_capacity.argtypes = [p, i32, i32, i32, p, i32, p, p]
     L.sbr_capacity_noalloc.restype = st
     L.sbr_capacity_noalloc.argtypes = [p, i32, i32, i32, p, i32, p, p]
+    L.sbr_batch_create.restype = st
+    L.sbr_batch_create.argtypes = [p, p, i32, C.POINTER(BatchJob), i32, C.POINTER(BatchConfig), pp, p]
+    L.sbr_batch_run.restype = st
+    L.sbr_batch_run.argtypes = [p, p]
+    L.sbr_batch_query.restype = st
+    L.sbr_batch_query.argtypes = [p, p, p, C.POINTER(BatchInfo)]
+    L.sbr_batch_export.restype = st
+    L.sbr_batch_export.argtypes = [p, i32, i32] + [p] * 10 + [p]
+    L.sbr_batch_free.restype = None
+    L.sbr_batch_free.argtypes = [p]
+    L.sbr_batch_tune.restype = st
+    L.sbr_batch_tune.argtypes = [p, p, i32, C.POINTER(BatchJob), i32, C.POINTER(BatchConfig),
+                                 C.POINTER(C.c_double), p]
     _lib = L
     return L

@@ -17,6 +17,7 @@ static thread_local char g_err[512] = "";
 static std::atomic<long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -390,7 +391,7 @@ sbr_status sbr_path_gains(const sbr_path_list* pl, const sbr_material* mats, int
     SBR_CHECK_ARG(pl != nullptr, "path list");
     SBR_SAME_DEVICE(pl);
     SBR_CHECK_ARG(F >= 1, "F >= 1");
-    SBR_CHECK_ARG(freqs_hz && gains, "freqs_hz and gains");
+    SBR_CHECK_ARG(freqs_hz && (gains || pl->P == 0), "freqs_hz and gains (gains may be NULL without paths)");
     SBR_CHECK_ARG(S >= pl->S, "materials for every surface id of the scene");
     SBR_CHECK_ARG(pl->P == 0 || pl->S == 0 || mats, "mats");
     SBR_CHECK_ARG(pol == SBR_POL_V || pol == SBR_POL_H, "pol");
@@ -406,7 +407,7 @@ sbr_status sbr_synthesize_H(const sbr_path_list* pl, const void* gains, const do
     SBR_SAME_DEVICE(pl);
     SBR_CHECK_ARG(F >= 1 && Nt >= 1 && Nr >= 1, "F, Nt, Nr >= 1");
     SBR_CHECK_ARG(F <= 65535 && Nr <= 65535, "F, Nr <= 65535");
-    SBR_CHECK_ARG(gains && freqs_hz && tx_elem && rx_elem && H, "pointers");
+    SBR_CHECK_ARG((gains || pl->P == 0) && freqs_hz && tx_elem && rx_elem && H, "pointers (gains may be NULL without paths)");
     SBR_CHECK_ARG(rx_index >= 0 && rx_index < pl->n_rx, "rx_index");
     cudaStream_t s = (cudaStream_t)stream;
     switch (precision) {

@@ -149,6 +149,30 @@ sbr_status dir_table(int32_t N, const float4** dir_a, const float2** dir_b, cuda
     return SBR_OK;
 }
 
+sbr_status dir_table_build(int32_t N, float4** dir_a, float2** dir_b, cudaStream_t s) {
+    int64_t R = 10 * (int64_t)N * N + 2;
+    float4* a = nullptr;
+    float2* b = nullptr;
+    SBR_TRY_CUDA(cudaMalloc(&a, sizeof(float4) * R));
+    if (cudaMalloc(&b, sizeof(float2) * R) != cudaSuccess) {
+        cudaFree(a);
+        set_error("direction table allocation failed");
+        return SBR_ERR_ALLOC;
+    }
+    Ico ico = make_ico();
+    ::sbr::note_launch(), k_dir_table<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(ico, N, R, a, b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaFree(a);
+        cudaFree(b);
+        set_error("direction table: %s", cudaGetErrorString(e));
+        return SBR_ERR_CUDA;
+    }
+    *dir_a = a;
+    *dir_b = b;
+    return SBR_OK;
+}
+
 sbr_status launch_dirs(int32_t N, double* dirs, cudaStream_t s) {
     int64_t R = 10 * (int64_t)N * N + 2;
     Ico ico = make_ico();

@@ -68,6 +68,11 @@ int fault_mode();
 // geodesic directions of subdivision N as double-float, built once per (device, N)
 // and kept for the process: dir_a[i] = (hi.x, hi.y, hi.z, lo.x), dir_b[i] = (lo.y, lo.z)
 sbr_status dir_table(int32_t N, const float4** dir_a, const float2** dir_b, cudaStream_t s);
+// a new direction table of subdivision N owned by the caller (cudaFree both)
+sbr_status dir_table_build(int32_t N, float4** dir_a, float2** dir_b, cudaStream_t s);
+// adds n to the launch count (kernel nodes of a CUDA graph launch; negative to
+// take back launches that were only captured)
+void note_launches(long long n);
 // enqueue a device-side store of a value (no host buffer outlives the call)
 sbr_status set_u64(unsigned long long* dst, unsigned long long v, cudaStream_t s);
 sbr_status set_f64(double* dst, double v, cudaStream_t s);

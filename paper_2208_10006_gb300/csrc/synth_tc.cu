@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "batch.cuh"
 #include "sbr_internal.cuh"
 #include "synth_common.cuh"
 
@@ -36,15 +37,19 @@ namespace {
 
 constexpr int kTcThreads = 256;
 constexpr int kTileM = 128;      // 2 x 64 receive elements
-constexpr int kTileN = 256;      // transmit elements
-constexpr int kChunkP = 32;      // paths per K-chunk (K = 64 BF16 = one 128-byte row)
-constexpr int kTmemCols = 256;
+constexpr int kChunkP = 32;      // paths per K-chunk (K = 64 16-bit values = one 128-byte row)
 constexpr uint32_t kSpin = 1u << 26;
-
 constexpr int kABytes = kTileM * 128;  // 16 KB
-constexpr int kBBytes = kTileN * 128;  // 32 KB
-constexpr int kSmemTiles = 2 * kABytes + 2 * kBBytes;  // hi/lo of A and B
-constexpr int kSmemBytes = kSmemTiles + 1024 + 64;      // + alignment slack + barrier
+
+// tile of N transmit elements (N = 64, 128 or 256): shared-memory and TMEM sizes
+template <int kTileN>
+struct TcShape {
+    static_assert(kTileN == 64 || kTileN == 128 || kTileN == 256, "tile N");
+    static constexpr int kBBytes = kTileN * 128;
+    static constexpr int kSmemTiles = 2 * kABytes + 2 * kBBytes;  // hi/lo of A and B
+    static constexpr int kSmemBytes = kSmemTiles + 1024 + 64;      // + alignment slack + barriers
+    static constexpr int kTmemCols = kTileN;                       // FP32 accumulator columns
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -68,20 +73,20 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
     return d;
 }
 
-// instruction descriptor: kind::f16, D F32, both K-major, M=128, N=256; A and
-// B both BF16 (format 1) or both FP16 (format 0)
-template <bool kF16>
+// instruction descriptor: kind::f16, D F32, both K-major, M=128, N=kTileN; A
+// and B both BF16 (format 1) or both FP16 (format 0)
+template <bool kF16, int kTileN>
 constexpr uint32_t idesc() {
     return (1u << 4) | (kF16 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(kTileN >> 3) << 17) |
            ((uint32_t)(kTileM >> 4) << 24);
 }
 
-template <bool kF16>
+template <bool kF16, int kTileN>
 __device__ __forceinline__ void mma_16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc<kF16>()), "r"(acc));
+        "l"(a), "l"(b), "r"(idesc<kF16, kTileN>()), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
@@ -142,6 +147,7 @@ __device__ __forceinline__ void split16(float x, uint16_t& hi, uint16_t& lo) {
 }
 
 struct TcArgs {
+    // single receiver of one path list
     int32_t F, Nr, Nt;
     int32_t Pr;                // paths of the receiver (stride of w rows)
     const int32_t* nb0;        // reflections of the first path: 0 = LoS at local index 0
@@ -153,26 +159,105 @@ struct TcArgs {
     float2* H;
     unsigned int* status;
     int inject_timeout;        // test-only: wait on a barrier nothing arrives at
+    // batched form: items of all jobs of a wave
+    const BatchJobDev* jobs;
+    const int64_t* item_off;   // [n_jobs + 1] first item of each job
+    int32_t n_jobs;
+    int64_t items;
+    const int32_t* np;         // [n_jobs] paths of each job
+    const int32_t* nb;         // reflections per path slot (batch path store)
+    int32_t path_cap;          // stride of a job's w rows
+    const float* dt_all;
+    const float* dr_all;
+    const float* dl_all;
+    const float2* w_all;
 };
 
-template <bool kF16>
+// one output tile: frequency f, receive elements [q0, q0 + 64), transmit
+// elements [p0, p0 + N); reflected paths are the local indices
+// [n0, n0 + nrefl); the LoS path, when present, is local index 0 and is added
+// exactly in the epilogue
+struct TcItem {
+    int f, q0, p0, Nr, Nt, los, n0, nrefl;
+    float foc;
+    const float* dt;
+    const float* dr;
+    const float2* wf;          // weights of frequency f
+    const float* dlos;
+    float2* Hf;                // H of frequency f
+};
+
+template <bool kBatch, int kTileN>
+__device__ __forceinline__ TcItem tc_item(const TcArgs& a, int64_t it) {
+    TcItem x;
+    int F, Pr;
+    const int32_t* nb0;
+    const double* freqs;
+    const float2* w;
+    float2* H;
+    int64_t wstride;
+    if (kBatch) {
+        int lo = 0, hi = a.n_jobs - 1;   // the last job whose first item is <= it
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (__ldg(a.item_off + mid) <= it) lo = mid; else hi = mid - 1;
+        }
+        const BatchJobDev* J = a.jobs + lo;
+        it -= __ldg(a.item_off + lo);
+        F = J->F; x.Nr = J->Nr; x.Nt = J->Nt;
+        Pr = __ldg(a.np + lo);
+        nb0 = a.nb + J->path_base;
+        freqs = J->freqs;
+        x.dt = a.dt_all + J->dt_base;
+        x.dr = a.dr_all + J->dr_base;
+        x.dlos = a.dl_all + J->dl_base;
+        w = a.w_all + J->w_base;
+        wstride = a.path_cap;
+        H = J->H;
+    } else {
+        F = a.F; x.Nr = a.Nr; x.Nt = a.Nt;
+        Pr = a.Pr;
+        nb0 = a.nb0;
+        freqs = a.freqs;
+        x.dt = a.dt; x.dr = a.dr; x.dlos = a.dlos;
+        w = a.w;
+        wstride = a.Pr;
+        H = a.H;
+    }
+    (void)F;
+    const int mtiles = (x.Nr + 63) / 64, ntiles = (x.Nt + kTileN - 1) / kTileN;
+    x.f = (int)(it / (mtiles * ntiles));
+    const int rem = (int)(it - (int64_t)x.f * mtiles * ntiles);
+    x.q0 = (rem / ntiles) * 64;
+    x.p0 = (rem % ntiles) * kTileN;
+    x.los = (Pr > 0 && *nb0 == 0) ? 0 : -1;
+    x.n0 = x.los == 0 ? 1 : 0;
+    x.nrefl = Pr - x.n0;
+    x.foc = (float)(freqs[x.f] / kC0);
+    x.wf = w + (int64_t)x.f * wstride;
+    x.Hf = H + (int64_t)x.f * x.Nr * x.Nt;
+    return x;
+}
+
+template <bool kF16, bool kBatch, int kTileN>
 __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constant__ TcArgs a) {
+    using Sh = TcShape<kTileN>;
     extern __shared__ unsigned char smem_raw[];
     __shared__ float s_red[kTcThreads / 32];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA_hi = smem;
     unsigned char* sA_lo = smem + kABytes;
     unsigned char* sB_hi = smem + 2 * kABytes;
-    unsigned char* sB_lo = smem + 2 * kABytes + kBBytes;
-    uint64_t* mbar = (uint64_t*)(smem + kSmemTiles);
-    uint64_t* never = (uint64_t*)(smem + kSmemTiles + 8);   // injected-fault barrier
-    uint32_t* tmem_slot = (uint32_t*)(smem + kSmemTiles + 16);
+    unsigned char* sB_lo = smem + 2 * kABytes + Sh::kBBytes;
+    uint64_t* mbar = (uint64_t*)(smem + Sh::kSmemTiles);
+    uint64_t* never = (uint64_t*)(smem + Sh::kSmemTiles + 8);   // injected-fault barrier
+    uint32_t* tmem_slot = (uint32_t*)(smem + Sh::kSmemTiles + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(kTmemCols));
+                     "r"(Sh::kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -191,25 +276,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
     // wait gives up and the CTA takes the same exit as a real timeout
     if (a.inject_timeout) failed = __syncthreads_or(!mbar_wait(smem_u32(never), 0u, 1u << 12)) != 0;
 
-    // reflected paths are the local indices [n0, n0 + nrefl); the LoS path, when
-    // present, is local index 0 and is added exactly in the epilogue
-    const int los = (a.Pr > 0 && *a.nb0 == 0) ? 0 : -1;
-    const int n0 = los == 0 ? 1 : 0;
-    const int nrefl = a.Pr - n0;
-    const int mtiles = (a.Nr + 63) / 64, ntiles = (a.Nt + kTileN - 1) / kTileN;
-    const int64_t items = (int64_t)a.F * mtiles * ntiles;
-    const int nch = (nrefl + kChunkP - 1) / kChunkP;
+    const int64_t items = kBatch ? a.items
+                                 : (int64_t)a.F * ((a.Nr + 63) / 64) * ((a.Nt + kTileN - 1) / kTileN);
     for (int64_t it = blockIdx.x; it < items && !failed; it += gridDim.x) {
-        const int f = (int)(it / (mtiles * ntiles));
-        const int rem = (int)(it - (int64_t)f * mtiles * ntiles);
-        const int q0 = (rem / ntiles) * 64, p0 = (rem % ntiles) * kTileN;
-        const float foc = (float)(a.freqs[f] / kC0);
+        const TcItem x = tc_item<kBatch, kTileN>(a, it);
+        const int nch = (x.nrefl + kChunkP - 1) / kChunkP;
         // FP16 form: power-of-two scale of this frequency's weights (exact)
         float sc = 1.f, isc = 1.f;
         if (kF16) {
             float m = 0.f;
-            for (int n = n0 + tid; n < n0 + nrefl; n += kTcThreads) {
-                float2 ww = __ldg(a.w + (int64_t)f * a.Pr + n);
+            for (int n = x.n0 + tid; n < x.n0 + x.nrefl; n += kTcThreads) {
+                float2 ww = __ldg(x.wf + n);
                 m = fmaxf(m, fmaxf(fabsf(ww.x), fabsf(ww.y)));
             }
             for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -226,19 +303,19 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
             }
         }
         for (int c = 0; c < nch && !failed; ++c) {
-            const int nb = n0 + c * kChunkP;
-            const int cnt = min(kChunkP, n0 + nrefl - nb);
+            const int nb = x.n0 + c * kChunkP;
+            const int cnt = min(kChunkP, x.n0 + x.nrefl - nb);
             // A' tile: 64 receive elements x 32 paths, each a 2x2 real block;
             // consecutive threads take consecutive receive elements (coalesced)
 #pragma unroll 4
             for (int e = tid; e < 64 * kChunkP; e += kTcThreads) {
                 int ql = e & 63, nl = e >> 6;
-                int q = q0 + ql, n = nb + nl;
+                int q = x.q0 + ql, n = nb + nl;
                 float ar = 0.f, ai = 0.f;
-                if (nl < cnt && q < a.Nr) {
-                    float2 ww = __ldg(a.w + (int64_t)f * a.Pr + n);
+                if (nl < cnt && q < x.Nr) {
+                    float2 ww = __ldg(x.wf + n);
                     float s, co;
-                    phasor(foc * __ldg(a.dr + (int64_t)n * a.Nr + q), s, co);
+                    phasor(x.foc * __ldg(x.dr + (int64_t)n * x.Nr + q), s, co);
                     ar = ww.x * co - ww.y * s;
                     ai = ww.x * s + ww.y * co;
                     if (kF16) { ar *= sc; ai *= sc; }
@@ -253,14 +330,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
                 *(uint32_t*)(sA_hi + o1) = (uint32_t)h2 | ((uint32_t)h0 << 16);
                 *(uint32_t*)(sA_lo + o1) = (uint32_t)l2 | ((uint32_t)l0 << 16);
             }
-            // B' tile (stored N x K): 256 transmit elements x 32 paths;
+            // B' tile (stored N x K): N transmit elements x 32 paths;
             // consecutive threads take consecutive transmit elements (coalesced)
 #pragma unroll 8
             for (int e = tid; e < kTileN * kChunkP; e += kTcThreads) {
                 int pl = e & (kTileN - 1), nl = e / kTileN;
-                int p = p0 + pl, n = nb + nl;
+                int p = x.p0 + pl, n = nb + nl;
                 float vr = 0.f, vi = 0.f;
-                if (nl < cnt && p < a.Nt) phasor(foc * __ldg(a.dt + (int64_t)n * a.Nt + p), vi, vr);
+                if (nl < cnt && p < x.Nt) phasor(x.foc * __ldg(x.dt + (int64_t)n * x.Nt + p), vi, vr);
                 uint16_t h0, l0, h1, l1;
                 split16<kF16>(vr, h0, l0);
                 split16<kF16>(vi, h1, l1);
@@ -275,10 +352,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
                 uint64_t dAh = make_desc(smem_u32(sA_hi)), dAl = make_desc(smem_u32(sA_lo));
                 uint64_t dBh = make_desc(smem_u32(sB_hi)), dBl = make_desc(smem_u32(sB_lo));
                 for (int ks = 0; ks < 4; ++ks) {
-                    uint64_t off = (uint64_t)(ks * 32) >> 4;  // 16 BF16 along K
-                    mma_16<kF16>(tmem, dAh + off, dBh + off, (c > 0 || ks > 0) ? 1u : 0u);
-                    mma_16<kF16>(tmem, dAh + off, dBl + off, 1u);
-                    mma_16<kF16>(tmem, dAl + off, dBh + off, 1u);
+                    uint64_t off = (uint64_t)(ks * 32) >> 4;  // 16 elements along K
+                    mma_16<kF16, kTileN>(tmem, dAh + off, dBh + off, (c > 0 || ks > 0) ? 1u : 0u);
+                    mma_16<kF16, kTileN>(tmem, dAh + off, dBl + off, 1u);
+                    mma_16<kF16, kTileN>(tmem, dAl + off, dBh + off, 1u);
                 }
                 mma_commit(mbar_a);
             }
@@ -288,15 +365,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
             failed = __syncthreads_or(!ok) != 0;  // one decision for the whole CTA
         }
         if (failed) break;
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns 128 (w / 4) .. +127
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 and half (w / 4) of the N columns
         const int qw = warp & 3, chalf = warp >> 2;
         const int row = 32 * qw + lane;            // row of C: 2 (q - q0) + part
-        const int q = q0 + (row >> 1);
+        const int q = x.q0 + (row >> 1);
         const int part = row & 1;
         float2 wl = make_float2(0.f, 0.f);
-        if (los >= 0) wl = a.w[(int64_t)f * a.Pr + los];
-        for (int j = 0; j < 4; ++j) {
-            const int col0 = 128 * chalf + 32 * j;
+        if (x.los >= 0) wl = x.wf[x.los];
+        for (int j = 0; j < kTileN / 64; ++j) {
+            const int col0 = (kTileN / 2) * chalf + 32 * j;
             uint32_t v[32];
             if (nch > 0) {
                 tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)col0, v);
@@ -313,33 +390,33 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
                 else { re[k] = got; im[k] = mine_hi; }
                 if (kF16) { re[k] *= isc; im[k] *= isc; }
             }
-            const int pb = p0 + col0 + 16 * part;
-            if (q < a.Nr) {
-                float2* dst = a.H + ((int64_t)f * a.Nr + q) * a.Nt;
-                if (los >= 0) {
+            const int pb = x.p0 + col0 + 16 * part;
+            if (q < x.Nr) {
+                float2* dst = x.Hf + (int64_t)q * x.Nt;
+                if (x.los >= 0) {
                     float dl[16];
-                    const float* src = a.dlos + (int64_t)q * a.Nt + pb;
-                    if (pb + 16 <= a.Nt && ((((uintptr_t)src) & 15) == 0)) {
+                    const float* src = x.dlos + (int64_t)q * x.Nt + pb;
+                    if (pb + 16 <= x.Nt && ((((uintptr_t)src) & 15) == 0)) {
                         for (int k = 0; k < 4; ++k) {
                             float4 v4 = __ldg(reinterpret_cast<const float4*>(src) + k);
                             dl[4 * k] = v4.x; dl[4 * k + 1] = v4.y; dl[4 * k + 2] = v4.z; dl[4 * k + 3] = v4.w;
                         }
                     } else {
-                        for (int k = 0; k < 16; ++k) dl[k] = pb + k < a.Nt ? __ldg(src + k) : 0.f;
+                        for (int k = 0; k < 16; ++k) dl[k] = pb + k < x.Nt ? __ldg(src + k) : 0.f;
                     }
                     for (int k = 0; k < 16; ++k) {
                         float s, co;
-                        sincospif(-2.0f * foc * dl[k], &s, &co);
+                        sincospif(-2.0f * x.foc * dl[k], &s, &co);
                         re[k] += wl.x * co - wl.y * s;
                         im[k] += wl.x * s + wl.y * co;
                     }
                 }
-                if (pb + 16 <= a.Nt && ((((uintptr_t)(dst + pb)) & 15) == 0)) {
+                if (pb + 16 <= x.Nt && ((((uintptr_t)(dst + pb)) & 15) == 0)) {
                     float4* d4 = reinterpret_cast<float4*>(dst + pb);
                     for (int k = 0; k < 8; ++k)
                         d4[k] = make_float4(re[2 * k], im[2 * k], re[2 * k + 1], im[2 * k + 1]);
                 } else {
-                    for (int k = 0; k < 16 && pb + k < a.Nt; ++k) dst[pb + k] = make_float2(re[k], im[k]);
+                    for (int k = 0; k < 16 && pb + k < x.Nt; ++k) dst[pb + k] = make_float2(re[k], im[k]);
                 }
             }
         }
@@ -351,7 +428,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Sh::kTmemCols));
     }
 }
 
@@ -393,9 +470,10 @@ sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* 
     a.freqs = freqs; a.dt = dt; a.dr = dr; a.w = w; a.dlos = dl; a.H = H;
     a.status = pl->d_status;  // a bounded wait that gave up is reported by sbr_path_query
     a.inject_timeout = fault_mode() == kFaultTimeout ? 1 : 0;
-    auto kern = f16 ? k_synth_tc<true> : k_synth_tc<false>;
+    auto kern = f16 ? k_synth_tc<true, false, 256> : k_synth_tc<false, false, 256>;
+    constexpr int kSmemBytes = TcShape<256>::kSmemBytes;
     SBR_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    int64_t items = (int64_t)F * ((Nr + 63) / 64) * ((Nt + kTileN - 1) / kTileN);
+    int64_t items = (int64_t)F * ((Nr + 63) / 64) * ((Nt + 255) / 256);
     // two CTAs per SM (97 KB shared memory and 256 TMEM columns each): one CTA's
     // MMA and epilogue overlap the other's phasor generation
     int grid = (int)std::min<int64_t>(items, 2 * (int64_t)sm_count());
@@ -404,6 +482,56 @@ sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* 
     dfree(dt, s); dfree(dr, s); dfree(dl, s); dfree(w, s);
     synth_release(&sp, s);
     return SBR_OK;
+}
+
+namespace {
+template <bool kF16, int kTileN>
+sbr_status batch_tc_launch(const BatchSynthWave& w, cudaStream_t s) {
+    TcArgs a{};
+    a.jobs = w.jobs;
+    a.item_off = w.item_off;
+    a.n_jobs = w.n_jobs;
+    a.items = w.items;
+    a.np = w.np;
+    a.nb = w.nb;
+    a.path_cap = w.path_cap;
+    a.dt_all = w.dt;
+    a.dr_all = w.dr;
+    a.dl_all = w.dl;
+    a.w_all = w.w;
+    a.status = w.status;
+    a.inject_timeout = fault_mode() == kFaultTimeout ? 1 : 0;
+    if (w.items <= 0) return SBR_OK;
+    int grid = (int)std::min<int64_t>(w.items, 2 * (int64_t)sm_count());
+    ::sbr::note_launch(), k_synth_tc<kF16, true, kTileN><<<grid, kTcThreads, TcShape<kTileN>::kSmemBytes, s>>>(a);
+    SBR_TRY_CUDA(cudaGetLastError());
+    return SBR_OK;
+}
+
+template <bool kF16, int kTileN>
+sbr_status batch_tc_attr() {
+    SBR_TRY_CUDA(cudaFuncSetAttribute(k_synth_tc<kF16, true, kTileN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      TcShape<kTileN>::kSmemBytes));
+    return SBR_OK;
+}
+}  // namespace
+
+sbr_status batch_synth_prepare(bool f16, int tile_n) {
+    switch (tile_n) {
+        case 64: return f16 ? batch_tc_attr<true, 64>() : batch_tc_attr<false, 64>();
+        case 128: return f16 ? batch_tc_attr<true, 128>() : batch_tc_attr<false, 128>();
+        case 256: return f16 ? batch_tc_attr<true, 256>() : batch_tc_attr<false, 256>();
+        default: set_error("tile_n %d not in {64, 128, 256}", tile_n); return SBR_ERR_INVALID_ARG;
+    }
+}
+
+sbr_status batch_synth_tc(const BatchSynthWave& w, bool f16, int tile_n, cudaStream_t s) {
+    switch (tile_n) {
+        case 64: return f16 ? batch_tc_launch<true, 64>(w, s) : batch_tc_launch<false, 64>(w, s);
+        case 128: return f16 ? batch_tc_launch<true, 128>(w, s) : batch_tc_launch<false, 128>(w, s);
+        case 256: return f16 ? batch_tc_launch<true, 256>(w, s) : batch_tc_launch<false, 256>(w, s);
+        default: set_error("tile_n %d not in {64, 128, 256}", tile_n); return SBR_ERR_INVALID_ARG;
+    }
 }
 
 }  // namespace sbr

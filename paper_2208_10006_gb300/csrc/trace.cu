@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "batch.cuh"
 #include "dfloat.cuh"
 #include "geodesic.cuh"
 
@@ -207,8 +208,10 @@ __device__ __forceinline__ void tri_test32(const float4* __restrict__ tris, int3
 // FP32 closest hit. Returns the sorted triangle index of the certain best
 // (or -1) and the list of faces that FP64 must re-decide. kCount adds node
 // visits and triangle tests to *visits / *tests (instrumented traces).
-template <bool kCount>
-__device__ int32_t traverse32(const TraceArgs& a, const Ray32& r, int prev, Trav& tv, int* stack,
+// A is the kernel's argument block (or a per-job view of it) with the scene
+// fields nodes, tris and the counters cnt.
+template <bool kCount, class A>
+__device__ int32_t traverse32(const A& a, const Ray32& r, int prev, Trav& tv, int* stack,
                               unsigned* visits, unsigned* tests) {
     tv.best_t = INFINITY; tv.lim = INFINITY; tv.best_j = -1; tv.best_face = 0x7fffffff;
     tv.best_surf = -2; tv.nu = 0; tv.overflow = false;
@@ -290,8 +293,8 @@ __device__ __forceinline__ bool box_hit64(const float* b, d3 o, d3 inv, double t
     return tmin <= tmx;
 }
 
-__device__ __noinline__ int32_t traverse64(const TraceArgs& a, d3 o, d3 d, int prev, double& t_out,
-                                           int* stack) {
+template <class A>
+__device__ __noinline__ int32_t traverse64(const A& a, d3 o, d3 d, int prev, double& t_out, int* stack) {
     d3 inv = mk3(1.0 / d.x, 1.0 / d.y, 1.0 / d.z);
     double best_t = INFINITY;
     int32_t best_j = -1, best_face = 0x7fffffff;
@@ -352,7 +355,8 @@ __device__ __forceinline__ uint32_t key_hash(const uint32_t* key) {
     return h;
 }
 
-__device__ void ht_insert(const TraceArgs& a, const uint32_t* key, unsigned long long val) {
+template <class A>
+__device__ void ht_insert(const A& a, const uint32_t* key, unsigned long long val) {
     uint32_t h = key_hash(key) & a.ht_mask;
     for (uint32_t probe = 0; probe <= a.ht_mask; ++probe) {
         uint32_t s = (h + probe) & a.ht_mask;
@@ -386,6 +390,22 @@ __device__ void ht_insert(const TraceArgs& a, const uint32_t* key, unsigned long
 }
 
 // ---------------------------------------------------------------- reception
+// exact double-float test of one receiver R against the segment [0, t_hit]
+// (or the open ray when there is no hit); dist = closest-approach distance
+__device__ __forceinline__ bool rx_accept(const df3& o, const df3& d, df L, df t_hit, bool hit,
+                                          const df3& R, df a2o3, float& dist) {
+    df3 v = df3_sub(R, o);
+    df ts = df3_dot(v, d);
+    if (ts.hi < 0.f || (hit && df_lt(t_hit, ts))) return false;
+    df3 w = df3_sub(df3_scale(d, ts), v);   // o + t* d - Rx
+    df dist2 = df3_dot(w, w);
+    df sl = df_add(L, ts);
+    df rad2 = df_mul(a2o3, df_mul(sl, sl));
+    if (!df_le(dist2, rad2) || (ts.hi == 0.f && ts.lo < 0.f)) return false;
+    dist = sqrtf(fmaxf(dist2.hi, 0.f));
+    return true;
+}
+
 // Receivers near the segment come from a BVH over the receiver points whose
 // boxes are grown by the largest sphere radius on the segment (FP32,
 // conservative); each is then tested exactly in double-float:
@@ -427,24 +447,16 @@ __device__ void receive(const TraceArgs& a, const df3& o, const df3& d, df L, df
                 int32_t rx_id = __ldg(a.rx_order + (~rr));
                 float4 ph = __ldg(a.rx_df + 2 * rx_id), pl = __ldg(a.rx_df + 2 * rx_id + 1);
                 df3 R{df_make(ph.x, pl.x), df_make(ph.y, pl.y), df_make(ph.z, pl.z)};
-                df3 v = df3_sub(R, o);
-                df ts = df3_dot(v, d);
-                if (!(ts.hi < 0.f) && !(hit && df_lt(t_hit, ts))) {
-                    df3 w = df3_sub(df3_scale(d, ts), v);   // o + t* d - Rx
-                    df dist2 = df3_dot(w, w);
-                    df s = df_add(L, ts);
-                    df rad2 = df_mul(a2o3, df_mul(s, s));
-                    if (df_le(dist2, rad2) && !(ts.hi == 0.f && ts.lo < 0.f)) {
-                        uint32_t key[kKeyWords];
-                        key[0] = (uint32_t)rx_id;
-                        key[1] = (uint32_t)a.bounce;
-                        for (int k = 0; k < kKmax; ++k)
-                            key[2 + k] = k < a.bounce ? (uint32_t)a.seq[(int64_t)k * a.R + ray] : 0xffffffffu;
-                        float dist = sqrtf(fmaxf(dist2.hi, 0.f));
-                        unsigned long long val = ((unsigned long long)__float_as_uint(dist) << 32) | ray;
-                        ht_insert(a, key, val);
-                        atomicAdd(&a.cnt->candidates, 1ull);
-                    }
+                float dist;
+                if (rx_accept(o, d, L, t_hit, hit, R, a2o3, dist)) {
+                    uint32_t key[kKeyWords];
+                    key[0] = (uint32_t)rx_id;
+                    key[1] = (uint32_t)a.bounce;
+                    for (int k = 0; k < kKmax; ++k)
+                        key[2 + k] = k < a.bounce ? (uint32_t)a.seq[(int64_t)k * a.R + ray] : 0xffffffffu;
+                    unsigned long long val = ((unsigned long long)__float_as_uint(dist) << 32) | ray;
+                    ht_insert(a, key, val);
+                    atomicAdd(&a.cnt->candidates, 1ull);
                 }
                 if (c) h1 = false; else h0 = false;
             }
@@ -469,6 +481,43 @@ __device__ __forceinline__ df3 ld_plane_n(const float4* plane, int32_t j, df& c)
     float4 h = __ldg(plane + 2 * j), l = __ldg(plane + 2 * j + 1);
     c = df_make(h.w, l.w);
     return df3{df_make(h.x, l.x), df_make(h.y, l.y), df_make(h.z, l.z)};
+}
+
+// Final decision of a segment's closest hit after the FP32 traversal: the exact
+// FP64 rule over the uncertain faces (or a full FP64 traversal when their list
+// overflowed), else the certain FP32 face with t from its double-float plane.
+template <class A>
+__device__ __forceinline__ int32_t settle_hit(const A& a, const df3& o, const df3& d, int prev, const Trav& tv,
+                                              int32_t j, int* stack, df& t) {
+    if (tv.overflow || tv.nu > 0) {
+        d3 o64 = mk3(df_to_double(o.x), df_to_double(o.y), df_to_double(o.z));
+        d3 d64 = mk3(df_to_double(d.x), df_to_double(d.y), df_to_double(d.z));
+        double t64 = INFINITY;
+        if (tv.overflow) {
+            j = traverse64(a, o64, d64, prev, t64, stack);
+            atomicAdd(&a.cnt->fp64_segments, 1ull);
+        } else {
+            // exact rule over the certain best and the uncertain faces
+            int32_t bj = -1, bface = 0x7fffffff;
+            for (int k = -1; k < tv.nu; ++k) {
+                int32_t c = k < 0 ? tv.best_j : tv.unc[k];
+                if (c < 0) continue;
+                double tc;
+                int face = __float_as_int(__ldg(a.tris + 3 * c + 1).w);
+                if (mt64(a.tris, c, o64, d64, tc) && (tc < t64 || (tc == t64 && face < bface))) {
+                    t64 = tc; bj = c; bface = face;
+                }
+            }
+            j = bj;
+            atomicAdd(&a.cnt->fp64_tests, (unsigned long long)(tv.nu + (tv.best_j >= 0)));
+        }
+        if (j >= 0) t = df_from_double(t64);
+    } else if (j >= 0) {
+        df c;
+        df3 n = ld_plane_n(a.plane, j, c);
+        t = df_div(df_sub(c, df3_dot(n, o)), df3_dot(n, d));
+    }
+    return j;
 }
 
 template <bool kCount>
@@ -516,34 +565,7 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
             if (a.T > 0) {
                 Trav tv;
                 j = traverse32<kCount>(a, r, prev, tv, stack, &visits, &tests);
-                if (tv.overflow || tv.nu > 0) {
-                    d3 o64 = mk3(df_to_double(o.x), df_to_double(o.y), df_to_double(o.z));
-                    d3 d64 = mk3(df_to_double(d.x), df_to_double(d.y), df_to_double(d.z));
-                    double t64 = INFINITY;
-                    if (tv.overflow) {
-                        j = traverse64(a, o64, d64, prev, t64, stack);
-                        atomicAdd(&a.cnt->fp64_segments, 1ull);
-                    } else {
-                        // exact rule over the certain best and the uncertain faces
-                        int32_t bj = -1, bface = 0x7fffffff;
-                        for (int k = -1; k < tv.nu; ++k) {
-                            int32_t c = k < 0 ? tv.best_j : tv.unc[k];
-                            if (c < 0) continue;
-                            double tc;
-                            int face = __float_as_int(__ldg(a.tris + 3 * c + 1).w);
-                            if (mt64(a.tris, c, o64, d64, tc) && (tc < t64 || (tc == t64 && face < bface))) {
-                                t64 = tc; bj = c; bface = face;
-                            }
-                        }
-                        j = bj;
-                        atomicAdd(&a.cnt->fp64_tests, (unsigned long long)(tv.nu + (tv.best_j >= 0)));
-                    }
-                    if (j >= 0) t = df_from_double(t64);
-                } else if (j >= 0) {
-                    df c;
-                    df3 n = ld_plane_n(a.plane, j, c);
-                    t = df_div(df_sub(c, df3_dot(n, o)), df3_dot(n, d));
-                }
+                j = settle_hit(a, o, d, prev, tv, j, stack, t);
             }
             if (kCount && j >= 0) {
                 d3 o64 = mk3(df_to_double(o.x), df_to_double(o.y), df_to_double(o.z));
@@ -586,6 +608,142 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
                 if (e) atomicAdd(&a.cnt->near_edge_hits, e);
             }
             visits = tests = rx_visits = edge = 0;
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, survive);
+        if (mask) {
+            unsigned long long ob = 0;
+            if (lane == 0) ob = atomicAdd(a.n_out, (unsigned long long)__popc(mask));
+            ob = __shfl_sync(0xffffffffu, ob, 0);
+            if (survive) {
+                unsigned long long pos = ob + __popc(mask & ((1u << lane) - 1u));
+                float4* q4 = reinterpret_cast<float4*>(a.qout + pos);
+                q4[0] = make_float4(out.oh[0], out.oh[1], out.oh[2], out.ol[0]);
+                q4[1] = make_float4(out.ol[1], out.ol[2], out.dh[0], out.dh[1]);
+                q4[2] = make_float4(out.dh[2], out.dl[0], out.dl[1], out.dl[2]);
+                q4[3] = make_float4(out.Lh, out.Ll, __uint_as_float(out.ray), __int_as_float(out.prev));
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- batched bounce kernel
+// The same segment step for a wave of jobs (Tx-Rx pairs over several scenes)
+// in one launch per bounce: a ray's job comes from a binary search over the
+// jobs' first rays at bounce 0 and from its queue record afterwards (12 bits
+// split over the record's ray id and last-surface words). Each job has one
+// receiver, tested exactly with the same double-float rule; the dedup key
+// carries the job's index in the wave in place of the receiver index.
+struct JobScene {
+    const float4* nodes;
+    const float4* tris;
+    const float4* plane;
+    TraceCountersDev* cnt;
+};
+
+struct BatchTraceArgs {
+    const BatchJobDev* jobs;
+    const int64_t* ray_off;
+    int32_t n_jobs;
+    int bounce;
+    int64_t R_total;
+    const RayRec* qin;
+    RayRec* qout;
+    const unsigned long long* n_in;
+    unsigned long long* n_out;
+    unsigned long long* work;
+    uint32_t* ht_state;
+    uint32_t* ht_key;
+    unsigned long long* ht_val;
+    uint32_t ht_mask;
+    TraceCountersDev* cnt;
+};
+
+__global__ void __launch_bounds__(kTraceThreads) k_trace_batch(const __grid_constant__ BatchTraceArgs a) {
+    int stack[kStack];
+    const int lane = threadIdx.x & 31;
+    const unsigned long long n_in = a.bounce == 0 ? (unsigned long long)a.R_total : *a.n_in;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(a.work, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n_in) break;
+        unsigned long long i = base + lane;
+        bool survive = false;
+        RayRec out;
+        if (i < n_in) {
+            df3 o, d;
+            df L;
+            uint32_t ray;
+            int prev, job;
+            if (a.bounce == 0) {
+                // the last job whose first ray is <= i
+                int lo = 0, hi = a.n_jobs - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (__ldg(a.ray_off + mid) <= (int64_t)i) lo = mid; else hi = mid - 1;
+                }
+                job = lo;
+                const BatchJobDev* J = a.jobs + job;
+                ray = (uint32_t)((int64_t)i - __ldg(a.ray_off + job));
+                o = df3{df_make(J->tx_h[0], J->tx_l[0]), df_make(J->tx_h[1], J->tx_l[1]),
+                        df_make(J->tx_h[2], J->tx_l[2])};
+                float4 da = __ldg(J->dir_a + ray);
+                float2 db = __ldg(J->dir_b + ray);
+                d = df3{df_make(da.x, da.w), df_make(da.y, db.x), df_make(da.z, db.y)};
+                L = df_make(0.f, 0.f);
+                prev = -1;
+            } else {
+                const float4* q4 = reinterpret_cast<const float4*>(a.qin + i);
+                float4 w0 = q4[0], w1 = q4[1], w2 = q4[2], w3 = q4[3];
+                o = df3{df_make(w0.x, w0.w), df_make(w0.y, w1.x), df_make(w0.z, w1.y)};
+                d = df3{df_make(w1.z, w2.y), df_make(w1.w, w2.z), df_make(w2.x, w2.w)};
+                L = df_make(w3.x, w3.y);
+                uint32_t rw = __float_as_uint(w3.z), pw = __float_as_uint(w3.w);
+                ray = rw & 0xffffffu;
+                prev = (int)(pw & 0x0fffffffu);
+                job = (int)((rw >> 24) | ((pw >> 28) << 8));
+            }
+            const BatchJobDev* J = a.jobs + job;
+            const JobScene sc{J->nodes, J->tris, J->plane, a.cnt};
+            Ray32 r = make_ray32(df3_hi(o), df3_hi(d));
+            df t = df_make(INFINITY, 0.f);
+            Trav tv;
+            int32_t j = traverse32<false>(sc, r, prev, tv, stack, nullptr, nullptr);
+            j = settle_hit(sc, o, d, prev, tv, j, stack, t);
+            {
+                const float4 rh = J->rx_h, rl = J->rx_l, al = J->alpha;
+                const df3 Rx{df_make(rh.x, rl.x), df_make(rh.y, rl.y), df_make(rh.z, rl.z)};
+                float dist;
+                if (rx_accept(o, d, L, t, j >= 0, Rx, df_make(al.z, al.w), dist)) {
+                    uint32_t key[kKeyWords];
+                    key[0] = (uint32_t)job;
+                    key[1] = (uint32_t)a.bounce;
+                    for (int k = 0; k < kKmax; ++k)
+                        key[2 + k] = k < a.bounce ? (uint32_t)J->seq[(int64_t)k * J->R + ray] : 0xffffffffu;
+                    unsigned long long val = ((unsigned long long)__float_as_uint(dist) << 32) | ray;
+                    ht_insert(a, key, val);
+                    atomicAdd(&a.cnt->candidates, 1ull);
+                }
+            }
+            if (j >= 0 && a.bounce < J->K) {
+                df c;
+                df3 n = ld_plane_n(J->plane, j, c);
+                int32_t surf = __float_as_int(__ldg(J->tris + 3 * j).w);
+                df3 o2 = df3_add(o, df3_scale(d, t));
+                df dn = df3_dot(d, n);
+                df3 d2 = df3_sub(d, df3_scale(n, df_make(2.f * dn.hi, 2.f * dn.lo)));
+                df L2 = df_add(L, t);
+                out.oh[0] = o2.x.hi; out.oh[1] = o2.y.hi; out.oh[2] = o2.z.hi;
+                out.ol[0] = o2.x.lo; out.ol[1] = o2.y.lo; out.ol[2] = o2.z.lo;
+                out.dh[0] = d2.x.hi; out.dh[1] = d2.y.hi; out.dh[2] = d2.z.hi;
+                out.dl[0] = d2.x.lo; out.dl[1] = d2.y.lo; out.dl[2] = d2.z.lo;
+                out.Lh = L2.hi;
+                out.Ll = L2.lo;
+                out.ray = ray | ((uint32_t)job << 24);
+                out.prev = (int32_t)((uint32_t)surf | ((uint32_t)(job >> 8) << 28));
+                J->seq[(int64_t)a.bounce * J->R + ray] = surf;
+                survive = true;
+            }
         }
         unsigned mask = __ballot_sync(0xffffffffu, survive);
         if (mask) {
@@ -648,6 +806,45 @@ int trace_grid(bool count) {
 }
 
 }  // namespace
+
+int batch_trace_kernels(int Kmax) { return Kmax + 3; }
+
+sbr_status batch_trace_wave(const BatchTraceWave& w, int blocks_per_sm, cudaStream_t s) {
+    const size_t cap = (size_t)w.ht_mask + 1;
+    SBR_TRY_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(TraceCountersDev), s));
+    ::sbr::note_launch(), k_init_table<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(w.ht_state, w.ht_val, cap);
+    SBR_TRY_CUDA(cudaGetLastError());
+    SBR_TRY(set_u64(&w.cnt->queue[0], (unsigned long long)w.R_total, s));
+    int per_sm = blocks_per_sm;
+    if (per_sm <= 0) {
+        SBR_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_batch, kTraceThreads, 0));
+        per_sm = std::max(1, per_sm);
+    }
+    const int grid = per_sm * sm_count();
+    BatchTraceArgs a{};
+    a.jobs = w.jobs;
+    a.ray_off = w.ray_off;
+    a.n_jobs = w.n_jobs;
+    a.R_total = w.R_total;
+    a.ht_state = w.ht_state;
+    a.ht_key = w.ht_key;
+    a.ht_val = w.ht_val;
+    a.ht_mask = w.ht_mask;
+    a.cnt = w.cnt;
+    RayRec* q0 = static_cast<RayRec*>(w.q0);
+    RayRec* q1 = static_cast<RayRec*>(w.q1);
+    for (int bnc = 0; bnc <= w.Kmax; ++bnc) {
+        a.bounce = bnc;
+        a.qin = (bnc & 1) ? q0 : q1;
+        a.qout = (bnc & 1) ? q1 : q0;
+        a.n_in = &w.cnt->queue[bnc];
+        a.n_out = &w.cnt->queue[bnc + 1];
+        a.work = &w.cnt->work[bnc];
+        ::sbr::note_launch(), k_trace_batch<<<grid, kTraceThreads, 0, s>>>(a);
+        SBR_TRY_CUDA(cudaGetLastError());
+    }
+    return SBR_OK;
+}
 
 sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     const sbr_trace_params& p = tr->params;

@@ -350,3 +350,74 @@ def scene_summary(sc) -> dict:
     return dict(name=sc["name"], T=int(len(sc["tri"])), S=int(len(sc["materials"])),
                 n_rx=int(len(sc["rx"])), F=int(len(sc["freqs"])), N=sc["N"], K=sc["K"],
                 R=10 * sc["N"] ** 2 + 2, Nt=int(len(sc["tx_elem"])), Nr=int(len(sc["rx_elem"])))
+
+
+# ----------------------------------------------------------------------------
+# batched uneven workload: many Tx-Rx pairs over several scenes
+# ----------------------------------------------------------------------------
+
+# subdivisions whose ray counts R = 10 N^2 + 2 are log-spaced over [1e5, 1e7]
+BATCH_N_VALUES = np.unique(np.round(np.geomspace(100, 1000, 64)).astype(int))
+
+
+def batch_scene(s: int, t_min: float = 1e3, t_max: float = 2e5):
+    """Scene s of the batched workload (seed 1000 + s): an urban grid of the
+    config-2 kind with nx in [2, 8] x ny in [2, 5] cells, a coarse ground
+    (8 x 8 quads) and facade subdivision chosen so that the triangle count is
+    close to a target drawn log-uniform in [t_min, t_max]."""
+    rng = np.random.default_rng(1000 + s)
+    target = float(np.exp(rng.uniform(np.log(t_min), np.log(t_max))))
+    nx = int(rng.integers(2, 9))
+    ny = int(rng.integers(2, 6))
+    sub = max(1, int(round(np.sqrt(max(target - 128.0, 10.0 * nx * ny) / (10.0 * nx * ny)))))
+    sc = config2(N=10, K=1, nx=nx, ny=ny, sub=sub, ground_sub=8, rx_grid=1, seed=1000 + s)
+    return dict(tri=sc["tri"], surface_id=sc["surface_id"], materials=sc["materials"], nx=nx, ny=ny,
+                seed=1000 + s)
+
+
+def batch_jobs(scene_list, n_jobs: int = 4096, seed: int = 4, n_values=None, k_range=(2, 8),
+               f_exp_range=(6, 10), max_elem_exp: int = 6):
+    """Jobs of the batched workload (seed `seed`), each a Tx-Rx pair:
+    scene uniform over scene_list; N uniform over n_values (default
+    BATCH_N_VALUES, so R is log-uniform over [1e5, 1e7]); K uniform in k_range;
+    F = 2^e with e uniform in f_exp_range (64 ... 1024 subcarriers) around a
+    carrier from {28, 60, 100, 140, 300} GHz over min(10 GHz, fc / 10); Tx a UPA
+    in the y-z plane of 2^a x 2^b elements (a, b in [0, 3]) at a street crossing
+    (60 i, 60 j) +- 5 m, height U(5, 30) m; Rx a ULA along y of 2^c elements
+    (c in [0, max_elem_exp]) in an x-street (60 i +- 8 m), height 1.5 m, so that
+    neither end is inside a building; element spacing half a carrier
+    wavelength; polarisation V or H; gamma = 5 dB/km x (f / 300 GHz)
+    (synthetic stand-in for Eq. 9)."""
+    rng = np.random.default_rng(seed)
+    n_values = BATCH_N_VALUES if n_values is None else np.asarray(n_values)
+    carriers = np.array([28e9, 60e9, 100e9, 140e9, 300e9])
+    jobs = []
+    for _ in range(n_jobs):
+        s = int(rng.integers(0, len(scene_list)))
+        sc = scene_list[s]
+        nx, ny = sc["nx"], sc["ny"]
+        N = int(rng.choice(n_values))
+        K = int(rng.integers(k_range[0], k_range[1] + 1))
+        F = int(2 ** rng.integers(f_exp_range[0], f_exp_range[1] + 1))
+        fc = float(rng.choice(carriers))
+        bw = min(10e9, fc / 10.0)
+        freqs = fc + (np.arange(F) - F // 2) * (bw / F)
+        lam = 299792458.0 / fc
+        tx = np.array([60.0 * rng.integers(1, nx) + rng.uniform(-5, 5),
+                       60.0 * rng.integers(1, ny) + rng.uniform(-5, 5), rng.uniform(5, 30)])
+        rx = np.array([60.0 * rng.integers(0, nx + 1) + rng.uniform(-8, 8),
+                       rng.uniform(-10.0, 60.0 * ny + 10.0), 1.5])
+        nty, ntz = int(2 ** rng.integers(0, 4)), int(2 ** rng.integers(0, 4))
+        nr = int(2 ** rng.integers(0, max_elem_exp + 1))
+        pol = "V" if rng.integers(0, 2) == 0 else "H"
+        jobs.append(dict(scene=s, N=N, K=K, tx=tx, rx=rx, freqs=freqs, pol=pol,
+                         gamma=(5.0 * freqs / 300e9).astype(np.float32),
+                         tx_elem=upa_yz(tx, nty, ntz, lam / 2), rx_elem=ula_y(rx, nr, lam / 2)))
+    return jobs
+
+
+def batch_job_scene(scene, job) -> dict:
+    """One job as a single-receiver scene dict (for the oracle and the per-pair API)."""
+    return _base("batch_job", scene["tri"], scene["surface_id"], scene["materials"], job["tx"],
+                 [job["rx"]], job["freqs"], job["N"], job["K"], pol=job["pol"], gamma=job["gamma"],
+                 tx_elem=job["tx_elem"], rx_elem=job["rx_elem"])

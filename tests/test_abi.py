@@ -52,3 +52,36 @@ def test_library_is_built_for_sm103a_only():
     from paper_2208_10006_gb300 import build as b
     assert b.ARCH == "-gencode=arch=compute_103a,code=sm_103a"
     assert all("-gencode" not in f or f == b.ARCH for f in b.flags())
+
+
+def test_ctypes_struct_layouts_match_the_header(tmp_path):
+    # sizes and field offsets of the binding's structs against a C compile of sbr.h
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_2208_10006_gb300 import _lib
+    checks = {"sbr_trace_params": (_lib.TraceParams, ["tx", "rx_xyz", "alpha", "flags"]),
+              "sbr_trace_counters": (_lib.TraceCounters, ["near_edge_hits", "queue", "alpha", "bounce_ms"]),
+              "sbr_path_info": (_lib.PathInfo, ["n_paths", "status"]),
+              "sbr_batch_job": (_lib.BatchJob, ["tx", "alpha", "F", "freqs_hz", "H"]),
+              "sbr_batch_config": (_lib.BatchConfig, ["path_cap", "use_graph"]),
+              "sbr_batch_info": (_lib.BatchInfo, ["max_keys", "rays", "config"])}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sbr.h"', "int main(void) {"]
+    for cname, (_, fields) in checks.items():
+        lines.append('printf("%%zu\\n", sizeof(%s));' % cname)
+        for f in fields:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    cuda_inc = "/usr/local/cuda/include"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-I", cuda_inc, str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = []
+    for cname, (cls, fields) in checks.items():
+        want.append(ctypes.sizeof(cls))
+        want += [getattr(cls, f).offset for f in fields]
+    assert got == want
