@@ -324,6 +324,9 @@ def run_gpu(args):
     synth = None
     if not args.no_synth and rank == 0:
         synth = bench_synthesis(sbr, torch, flush, peaks, peak_src, args)
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = bench_batched(sbr, torch, args)
 
     if rank != 0:
         torch.distributed.barrier()
@@ -379,6 +382,7 @@ def run_gpu(args):
         "launches_per_step": n_launch,
         "clocks": clk,
         "synthesis": synth,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -455,6 +459,92 @@ def bench_synthesis(sbr, torch, flush, peaks, peak_src, args):
     return out
 
 
+def bench_batched(sbr, torch, args):
+    """The batched uneven workload: 4096 Tx-Rx jobs over 32 scenes (0.9k-125k
+    triangles), rays 1e5-1e7 log-uniform, K 2-8, 64-1024 subcarriers, up to
+    8 x 8 transmit and 64 receive elements; the batch (tuned on its first 128
+    jobs, one CUDA-graph launch per run) against a per-pair loop of the
+    single-job calls, with the largest H difference between the two."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n_jobs = args.batch_jobs
+    scs = [scenes.batch_scene(s) for s in range(32)]
+    jobs = scenes.batch_jobs(scs, n_jobs=n_jobs, seed=4)
+    sdev = []
+    for sc in scs:
+        tri = torch.as_tensor(sc["tri"].reshape(-1, 9), dtype=torch.float32, device=dev)
+        sid = torch.as_tensor(sc["surface_id"], dtype=torch.int32, device=dev)
+        mats = torch.as_tensor(sc["materials"], dtype=torch.float64, device=dev)
+        sdev.append((sbr.build_bvh(tri, sid, len(sc["materials"])), mats))
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    jdev = [dict(scene=j["scene"], N=j["N"], K=j["K"], tx=j["tx"], rx=j["rx"], pol=j["pol"],
+                 freqs=t(j["freqs"], torch.float64), gamma=t(j["gamma"], torch.float32),
+                 tx_elem=t(j["tx_elem"], torch.float64), rx_elem=t(j["rx_elem"], torch.float64))
+            for j in jobs]
+    t0 = time.perf_counter()
+    sample = [dict(j) for j in jdev[:128]]
+    cfg, tune_ms = sbr.batch_tune(sdev, sample)
+    tune_s = time.perf_counter() - t0
+    del sample
+    cfg["path_cap"] = min(2048, 2 * cfg["path_cap"])   # margin over the sample's largest key count
+    b = sbr.batch_create(sdev, jdev, config=cfg)
+    b.run()                     # capture + first launch
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.run()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    n_paths, status, info = b.query()
+    t_b = min(ts) / 1e3
+    # per-pair loop: the single-job calls for every job, FP16x3 synthesis; alpha of
+    # each N computed once beforehand (the batch caches it too) and the launch
+    # direction tables already cached by the batch
+    alphas = {}
+    for j in jdev:
+        if j["N"] not in alphas:
+            alphas[j["N"]] = float(sbr.launch_dirs(j["N"], with_dirs=False)[1].cpu()[0])
+    Hs = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    e0.record()
+    rb_pp = 0
+    for j in jdev:
+        bvh, mats = sdev[j["scene"]]
+        rx = torch.as_tensor(np.asarray(j["rx"], dtype=np.float64).reshape(1, 3), device=dev)
+        tr = sbr.trace(bvh, j["tx"], rx, j["N"], j["K"], alpha=alphas[j["N"]])
+        pl = sbr.paths(tr, bvh)
+        g = sbr.path_gains(pl, mats, j["freqs"], j["gamma"], None,
+                           sbr.POL_V if j["pol"] == "V" else sbr.POL_H)
+        Hs.append(sbr.synthesize_H(pl, g, j["freqs"], j["tx_elem"], j["rx_elem"], 0, sbr.SYNTH_FP16X3))
+    e1.record()
+    e1.synchronize()
+    t_pp = e0.elapsed_time(e1) / 1e3
+    wall_pp = time.perf_counter() - w0
+    dmax = 0.0
+    for H, j, st in zip(Hs, jdev, status):
+        if st == 0:
+            m = float(H.abs().max())
+            if m > 0:
+                dmax = max(dmax, float((H - j["H"]).abs().max()) / m)
+    rbs = info["ray_bounces"]
+    out = {"metric": "Tx-Rx jobs/s", "workload": "batched_%djobs_32scenes_R1e5-1e7_K2-8_F64-1024" % n_jobs,
+           "jobs": n_jobs, "rays": info["rays"], "ray_bounces": rbs, "paths": info["paths"],
+           "failed_jobs": int((status != 0).sum()),
+           "batched": {"ms": t_b * 1e3, "jobs_per_s": n_jobs / t_b, "Mray_bounces_per_s": rbs / t_b / 1e6,
+                       "graph_kernels": info["graph_kernels"], "waves": info["n_waves"],
+                       "config": info["config"], "tune_s": tune_s, "tune_sample_ms": tune_ms},
+           "per_pair_loop": {"ms": t_pp * 1e3, "wall_s": wall_pp, "jobs_per_s": n_jobs / t_pp,
+                             "Mray_bounces_per_s": rbs / t_pp / 1e6},
+           "speedup": t_pp / t_b,
+           "max_abs_dH_over_max_H_batched_vs_per_pair": dmax}
+    b.free()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__,
                                  formatter_class=argparse.RawDescriptionHelpFormatter)
@@ -464,6 +554,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-synth", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-jobs", type=int, default=4096)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="urban", choices=["urban", "urban_n400"],

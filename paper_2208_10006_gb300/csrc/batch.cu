@@ -243,11 +243,11 @@ __global__ void k_batch_status(const TraceCountersDev* __restrict__ cnt, int32_t
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 // ---------------------------------------------------------------- per-N launch data
-// direction tables and alpha of every subdivision used by a batch, kept for the
-// process (batches of the same sizes, e.g. the autotuner's, share them)
+// direction table (the process-wide cache of the single-job trace) and alpha of
+// every subdivision used by a batch; alpha is kept for the process as well
 struct NData {
-    float4* dir_a = nullptr;
-    float2* dir_b = nullptr;
+    const float4* dir_a = nullptr;
+    const float2* dir_b = nullptr;
     double alpha = 0.0;
 };
 std::mutex g_nmu;
@@ -260,7 +260,7 @@ sbr_status ndata(int N, cudaStream_t s, NData* out) {
     auto it = g_ndata.find({dev, N});
     if (it == g_ndata.end()) {
         NData d;
-        SBR_TRY(dir_table_build(N, &d.dir_a, &d.dir_b, s));
+        SBR_TRY(dir_table(N, &d.dir_a, &d.dir_b, s));
         double* da = nullptr;
         sbr_status st = dalloc_n(&da, 1, s);
         if (st == SBR_OK) st = launch_alpha(N, da, s);
@@ -269,8 +269,6 @@ sbr_status ndata(int N, cudaStream_t s, NData* out) {
         if (st == SBR_OK && cudaStreamSynchronize(s) != cudaSuccess) st = SBR_ERR_CUDA;
         if (da) dfree(da, s);
         if (st != SBR_OK) {
-            cudaFree(d.dir_a);
-            cudaFree(d.dir_b);
             if (st == SBR_ERR_CUDA) set_error("alpha of N=%d failed", N);
             return st;
         }
@@ -499,6 +497,7 @@ sbr_status create(const sbr_bvh* const* scenes, const sbr_material* const* mats,
     SBR_CHECK_ARG(c.precision == SBR_SYNTH_FP16X3 || c.precision == SBR_SYNTH_BF16X3, "precision");
     SBR_CHECK_ARG(c.trace_blocks_per_sm >= 0 && c.trace_blocks_per_sm <= 16, "trace_blocks_per_sm");
     SBR_CHECK_ARG(c.table_log2 == 0 || (c.table_log2 >= 4 && c.table_log2 <= 26), "table_log2");
+    if (c.trace_blocks_per_sm == 0) c.trace_blocks_per_sm = batch_trace_occupancy();
     int64_t max_R = 0;
     for (int i = 0; i < n_jobs; ++i) max_R = std::max<int64_t>(max_R, 10 * (int64_t)jobs[i].subdiv_N * jobs[i].subdiv_N + 2);
     c.wave_rays = std::max<int64_t>(c.wave_rays, max_R);
@@ -821,7 +820,7 @@ sbr_status sbr_batch_tune(const sbr_bvh* const* scenes, const sbr_material* cons
     sbr_batch_config best = fixed;
     if (best.use_graph == 0) best.use_graph = 1;
     // one candidate: create, two warm runs, median of three timed runs
-    auto time_cfg = [&](sbr_batch_config c, double* t_ms, int* max_keys) -> sbr_status {
+    auto time_cfg = [&](sbr_batch_config c, double* t_ms, int* max_keys, sbr_batch_config* resolved) -> sbr_status {
         sbr_batch* b = nullptr;
         SBR_TRY(create(scenes, mats, n_scenes, jobs, n_jobs, &c, &b, s));
         sbr_status st = SBR_OK;
@@ -848,15 +847,17 @@ sbr_status sbr_batch_tune(const sbr_bvh* const* scenes, const sbr_material* cons
         std::sort(ts.begin(), ts.end());
         *t_ms = ts[ts.size() / 2];
         *max_keys = info.max_keys;
+        *resolved = info.config;   // defaults made explicit
         return SBR_OK;
     };
     double t = 0;
     int mk = 0;
+    sbr_batch_config res{};
     // path store: a first run at the given (or 1024) capacity sizes it to the keys seen
     if (fixed.path_cap == 0) {
         sbr_batch_config c = best;
         c.path_cap = 1024;
-        SBR_TRY(time_cfg(c, &t, &mk));
+        SBR_TRY(time_cfg(c, &t, &mk, &res));
         int cap = 64;
         while (cap < 2048 && cap < (int)std::ceil(1.5 * mk)) cap <<= 1;
         best.path_cap = cap;
@@ -867,8 +868,8 @@ sbr_status sbr_batch_tune(const sbr_bvh* const* scenes, const sbr_material* cons
     const int grids[3] = {2, 3, 4};
     const int64_t waves[3] = {(int64_t)1 << 25, (int64_t)1 << 26, (int64_t)1 << 27};
     auto consider = [&](sbr_batch_config c) -> sbr_status {
-        SBR_TRY(time_cfg(c, &t, &mk));
-        if (t < best_t) { best_t = t; best = c; }
+        SBR_TRY(time_cfg(c, &t, &mk, &res));
+        if (t < best_t) { best_t = t; best = res; }
         return SBR_OK;
     };
     if (fixed.tile_n == 0) {

@@ -2,6 +2,7 @@
 // direction list, and alpha, the largest angle between directions joined by
 // a sub-triangle edge, which sizes the reception sphere (Sec. II-A.3).
 #include <cmath>
+#include <map>
 #include <mutex>
 
 #include "dfloat.cuh"
@@ -100,52 +101,28 @@ __global__ void k_dir_table(const __grid_constant__ Ico ico, int N, int64_t R, f
     db[i] = make_float2(y.lo, z.lo);
 }
 
-struct DirCache {
-    std::mutex mu;
-    int device = -1, N = 0;
-    float4* a = nullptr;
-    float2* b = nullptr;
-};
-DirCache g_dirs;
+// direction tables by (device, N), kept for the process: repeated traces and
+// batches of the same subdivisions reuse them (24 B per ray each)
+std::mutex g_dir_mu;
+std::map<std::pair<int, int>, std::pair<float4*, float2*>> g_dir_tables;
 
 }  // namespace
 
 sbr_status dir_table(int32_t N, const float4** dir_a, const float2** dir_b, cudaStream_t s) {
-    std::lock_guard<std::mutex> lk(g_dirs.mu);
+    std::lock_guard<std::mutex> lk(g_dir_mu);
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (g_dirs.a == nullptr || g_dirs.device != dev || g_dirs.N != N) {
-        if (g_dirs.a) {
-            // a table of another N or device: release it (cudaFree waits for its users)
-            int cur = dev;
-            cudaSetDevice(g_dirs.device);
-            cudaFree(g_dirs.a);
-            cudaFree(g_dirs.b);
-            cudaSetDevice(cur);
-            g_dirs.a = nullptr;
-            g_dirs.b = nullptr;
-        }
-        int64_t R = 10 * (int64_t)N * N + 2;
+    SBR_TRY_CUDA(cudaGetDevice(&dev));
+    auto it = g_dir_tables.find({dev, N});
+    if (it == g_dir_tables.end()) {
         float4* a = nullptr;
         float2* b = nullptr;
-        SBR_TRY_CUDA(cudaMalloc(&a, sizeof(float4) * R));
-        if (cudaMalloc(&b, sizeof(float2) * R) != cudaSuccess) {
-            cudaFree(a);
-            set_error("direction table allocation failed");
-            return SBR_ERR_ALLOC;
-        }
-        Ico ico = make_ico();
-        ::sbr::note_launch(), k_dir_table<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(ico, N, R, a, b);
-        SBR_TRY_CUDA(cudaGetLastError());
+        SBR_TRY(dir_table_build(N, &a, &b, s));
         // other streams may use the table next: finish building it now
         SBR_TRY_CUDA(cudaStreamSynchronize(s));
-        g_dirs.a = a;
-        g_dirs.b = b;
-        g_dirs.device = dev;
-        g_dirs.N = N;
+        it = g_dir_tables.emplace(std::make_pair(dev, N), std::make_pair(a, b)).first;
     }
-    *dir_a = g_dirs.a;
-    *dir_b = g_dirs.b;
+    *dir_a = it->second.first;
+    *dir_b = it->second.second;
     return SBR_OK;
 }
 

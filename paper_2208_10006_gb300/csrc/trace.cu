@@ -809,6 +809,13 @@ int trace_grid(bool count) {
 
 int batch_trace_kernels(int Kmax) { return Kmax + 3; }
 
+int batch_trace_occupancy() {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_batch, kTraceThreads, 0) != cudaSuccess)
+        per_sm = 1;
+    return std::max(1, per_sm);
+}
+
 sbr_status batch_trace_wave(const BatchTraceWave& w, int blocks_per_sm, cudaStream_t s) {
     const size_t cap = (size_t)w.ht_mask + 1;
     SBR_TRY_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(TraceCountersDev), s));
