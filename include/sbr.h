@@ -416,6 +416,76 @@ sbr_status sbr_batch_tune(const sbr_bvh* const* scenes, const sbr_material* cons
                           int32_t n_scenes, const sbr_batch_job* jobs, int32_t n_jobs,
                           sbr_batch_config* cfg, double* ms, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate. The paper has no counterpart: a query-time stand-in for
+ * the method's per-receiver outputs (path loss, RMS delay spread and PDP of
+ * Eq. 2, 4, 5), learned from them, with full SBR as the fallback and judge.
+ */
+
+/*
+ * sbr_surrogate_targets - per receiver r and frequency f of a path list and
+ * its gains (sbr_path_gains, [P*F]): out[(r*F + f)*(2 + n_taps) + k] =
+ *   k = 0: incoherent path loss -10 log10 sum_n |g_n(f)|^2 (dB, Eq. 4 power sum)
+ *   k = 1: RMS delay spread of Eq. 5 with P_n = |g_n(f)|^2, tau_n = L_n / c (s)
+ *   k = 2 + i: PDP tap i, 10 log10 of the power with tau_n - tau_min in
+ *              [i tap_s, (i + 1) tap_s) over the total (dB), floor_db when
+ *              below it or empty.
+ * A receiver without paths gets NaN everywhere. FP64 arithmetic, FP32 out.
+ * n_taps in [1, 32]. Asynchronous.
+ */
+sbr_status sbr_surrogate_targets(const sbr_path_list* pl, const void* gains, int32_t F, int32_t n_taps,
+                                 double tap_s, double floor_db, float* out, void* stream);
+
+typedef struct sbr_mlp sbr_mlp;
+
+typedef struct {
+    int32_t n_out;          /* outputs used, <= 128                                         */
+    int32_t width;          /* hidden width: 128 or 256                                     */
+    int32_t depth;          /* hidden layers, 1..8                                          */
+    int32_t max_batch;      /* rows per call, <= 2^22                                       */
+    uint64_t seed;          /* initial weights (He-uniform from splitmix64)                 */
+    float x_lo[4];          /* input box of (x, y, z, f), mapped to [0, 1] for the features */
+    float x_hi[4];
+    float lr, beta1, beta2, eps;   /* Adam                                                */
+    int32_t err_channel;    /* output that learns |output err_of - its target|, or -1       */
+    int32_t err_of;         /* (stop-gradient on output err_of), or -1                      */
+} sbr_mlp_config;
+
+/*
+ * sbr_mlp_create - the MLP: 128 Fourier features of (x, y, z, f) (coordinate
+ * c, octave k = 0..15: sin and cos of pi 2^(9k/15) u_c, u = (x - x_lo) /
+ * (x_hi - x_lo)) -> depth ReLU layers of `width` -> 128 linear outputs, the
+ * first n_out used. BF16 operands on the tcgen05 tensor cores, FP32
+ * accumulation and FP32 master weights. loss_w: host [n_out] weights of the
+ * squared errors (NULL: all 1); y_shift, y_scale: host [n_out] target
+ * normalisation, the network learning (y - shift) / scale and predicting in
+ * target units (NULL: 0 and 1). Synchronous.
+ */
+sbr_status sbr_mlp_create(const sbr_mlp_config* cfg, const float* loss_w, const float* y_shift,
+                          const float* y_scale, sbr_mlp** out, void* stream);
+/*
+ * sbr_mlp_train_step - one Adam step on a batch: x dev [B*4], y dev [B*n_out]
+ * targets (NaN = no target). Loss (1/B) sum w_o (p - y')^2 over finite targets
+ * y' = (y - shift) / scale, plus, for the error head, (1/B) sum w_e
+ * (p_e - |p_c - y'_c|)^2 (the head predicts in the normalised units of c,
+ * times scale_e + shift_e when predicted). loss: dev
+ * float accumulated with atomicAdd (zero it first), or NULL. Asynchronous.
+ */
+sbr_status sbr_mlp_train_step(sbr_mlp* m, const float* x, const float* y, int32_t B, float* loss, void* stream);
+/* sbr_mlp_predict - y dev [B*n_out] = outputs for x dev [B*4]. Asynchronous. */
+sbr_status sbr_mlp_predict(const sbr_mlp* m, const float* x, int32_t B, float* y, void* stream);
+/* number of FP32 parameters (per layer: W [n_out][n_in] row-major, then b) */
+int64_t sbr_mlp_param_count(const sbr_mlp* m);
+/*
+ * sbr_mlp_params - mode 0: copy the FP32 parameters to params (dev); 1: load
+ * them from params (and refresh the BF16 copies); 2: copy the gradients of
+ * the last training step. Layout of sbr_mlp_param_count. Asynchronous.
+ */
+sbr_status sbr_mlp_params(sbr_mlp* m, float* params, int32_t mode, void* stream);
+/* synchronous: SBR_ERR_TIMEOUT if a bounded tensor-core wait gave up */
+sbr_status sbr_mlp_status(const sbr_mlp* m);
+void sbr_mlp_free(sbr_mlp* m);
+
 #ifdef __cplusplus
 }
 #endif

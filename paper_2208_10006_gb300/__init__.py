@@ -28,7 +28,7 @@ from ._lib import (KMAX, NSTATS, POL_H, POL_V, SYNTH_BF16X3, SYNTH_FP16X3, SYNTH
 __all__ = ["SbrError", "BVH", "TraceResult", "PathList", "launch_dirs", "build_bvh", "trace",
            "paths", "path_gains", "synthesize_H", "pdp_angles", "capacity", "version",
            "POL_V", "POL_H", "SYNTH_FP64", "SYNTH_FP32", "SYNTH_BF16X3", "SYNTH_FP16X3", "KMAX", "NSTATS",
-           "scene_to_device", "run_scene", "Batch", "batch_create", "batch_tune"]
+           "scene_to_device", "run_scene", "Batch", "batch_create", "batch_tune", "surrogate_targets", "MLP"]
 
 
 class SbrError(RuntimeError):
@@ -454,3 +454,67 @@ def batch_tune(scenes, jobs, config=None, stream=None):
     return dict(wave_rays=c.wave_rays, path_cap=c.path_cap, table_log2=c.table_log2, tile_n=c.tile_n,
                 trace_blocks_per_sm=c.trace_blocks_per_sm, precision=c.precision,
                 use_graph=c.use_graph), ms.value
+
+
+# ---------------------------------------------------------------- surrogate
+def surrogate_targets(pl: PathList, gains: torch.Tensor, F: int, n_taps: int = 16, tap_s: float = 5e-9,
+                      floor_db: float = -40.0, stream=None) -> torch.Tensor:
+    """[n_rx, F, 2 + n_taps] float32: path loss (dB), RMS delay spread (s), PDP taps (dB)."""
+    info = pl.info()
+    out = torch.empty((max(info["n_rx"], 1), F, 2 + n_taps), dtype=torch.float32, device=_dev())
+    _check(_L().sbr_surrogate_targets(pl.handle, _ptr(gains) if pl.n else None, int(F), int(n_taps),
+                                      float(tap_s), float(floor_db), _ptr(out), _stream(stream)))
+    return out[: info["n_rx"]]
+
+
+class MLP:
+    """Handle of sbr_mlp_create (BF16 MLP on Fourier features of (x, y, z, f))."""
+
+    def __init__(self, n_out: int, x_lo, x_hi, width: int = 256, depth: int = 4, max_batch: int = 8192,
+                 seed: int = 0, lr: float = 1e-3, betas=(0.9, 0.999), eps: float = 1e-8, err_channel: int = -1,
+                 err_of: int = -1, loss_w=None, y_shift=None, y_scale=None, stream=None):
+        c = _lib.MlpConfig()
+        c.n_out, c.width, c.depth, c.max_batch, c.seed = n_out, width, depth, max_batch, seed
+        for k in range(4):
+            c.x_lo[k] = float(x_lo[k])
+            c.x_hi[k] = float(x_hi[k])
+        c.lr, c.beta1, c.beta2, c.eps = lr, betas[0], betas[1], eps
+        c.err_channel, c.err_of = err_channel, err_of
+        self.n_out, self.max_batch = n_out, max_batch
+        arr = lambda v: None if v is None else np.ascontiguousarray(v, dtype=np.float32)
+        lw, sh, sc = arr(loss_w), arr(y_shift), arr(y_scale)
+        p = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)
+        h = C.c_void_p()
+        _check(_L().sbr_mlp_create(C.byref(c), p(lw), p(sh), p(sc), C.byref(h), _stream(stream)))
+        self._h = h
+
+    def train_step(self, x: torch.Tensor, y: torch.Tensor, loss: torch.Tensor = None, stream=None):
+        assert x.dtype == torch.float32 and y.dtype == torch.float32
+        _check(_L().sbr_mlp_train_step(self._h, _ptr(x), _ptr(y), int(x.shape[0]), _ptr(loss), _stream(stream)))
+
+    def predict(self, x: torch.Tensor, out: torch.Tensor = None, stream=None) -> torch.Tensor:
+        B = int(x.shape[0])
+        y = out if out is not None else torch.empty((B, self.n_out), dtype=torch.float32, device=_dev())
+        _check(_L().sbr_mlp_predict(self._h, _ptr(x), B, _ptr(y), _stream(stream)))
+        return y
+
+    def params(self, mode: int = 0, values: torch.Tensor = None, stream=None) -> torch.Tensor:
+        """mode 0: parameters, 2: last gradients (flat float32); mode 1 loads `values`."""
+        n = int(_L().sbr_mlp_param_count(self._h))
+        buf = values if mode == 1 else torch.empty(n, dtype=torch.float32, device=_dev())
+        _check(_L().sbr_mlp_params(self._h, _ptr(buf), int(mode), _stream(stream)))
+        return buf
+
+    def status(self):
+        _check(_L().sbr_mlp_status(self._h))
+
+    def free(self):
+        if self._h:
+            _L().sbr_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -23,7 +23,8 @@ EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_count", "sbr_launch_dirs
            "sbr_path_query", "sbr_path_export", "sbr_path_list_free", "sbr_path_gains",
            "sbr_synthesize_H", "sbr_pdp_angles", "sbr_capacity", "sbr_capacity_noalloc",
            "sbr_batch_create", "sbr_batch_run", "sbr_batch_query", "sbr_batch_export", "sbr_batch_free",
-           "sbr_batch_tune"]
+           "sbr_batch_tune", "sbr_surrogate_targets", "sbr_mlp_create", "sbr_mlp_train_step",
+           "sbr_mlp_predict", "sbr_mlp_param_count", "sbr_mlp_params", "sbr_mlp_status", "sbr_mlp_free"]
 
 
 class TraceParams(C.Structure):
@@ -72,6 +73,13 @@ class BatchInfo(C.Structure):
                 ("status", C.c_int32), ("max_keys", C.c_int32), ("reserved", C.c_int32),
                 ("rays", C.c_int64), ("ray_bounces", C.c_int64), ("paths", C.c_int64),
                 ("config", BatchConfig)]
+
+
+class MlpConfig(C.Structure):
+    _fields_ = [("n_out", C.c_int32), ("width", C.c_int32), ("depth", C.c_int32), ("max_batch", C.c_int32),
+                ("seed", C.c_uint64), ("x_lo", C.c_float * 4), ("x_hi", C.c_float * 4), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("err_channel", C.c_int32),
+                ("err_of", C.c_int32)]
 
 
 assert C.sizeof(TraceParams) == 64
@@ -144,5 +152,21 @@ def load() -> C.CDLL:
     L.sbr_batch_tune.restype = st
     L.sbr_batch_tune.argtypes = [p, p, i32, C.POINTER(BatchJob), i32, C.POINTER(BatchConfig),
                                  C.POINTER(C.c_double), p]
+    L.sbr_surrogate_targets.restype = st
+    L.sbr_surrogate_targets.argtypes = [p, p, i32, i32, f64, f64, p, p]
+    L.sbr_mlp_create.restype = st
+    L.sbr_mlp_create.argtypes = [C.POINTER(MlpConfig), p, p, p, pp, p]
+    L.sbr_mlp_train_step.restype = st
+    L.sbr_mlp_train_step.argtypes = [p, p, p, i32, p, p]
+    L.sbr_mlp_predict.restype = st
+    L.sbr_mlp_predict.argtypes = [p, p, i32, p, p]
+    L.sbr_mlp_param_count.restype = i64
+    L.sbr_mlp_param_count.argtypes = [p]
+    L.sbr_mlp_params.restype = st
+    L.sbr_mlp_params.argtypes = [p, p, i32, p]
+    L.sbr_mlp_status.restype = st
+    L.sbr_mlp_status.argtypes = [p]
+    L.sbr_mlp_free.restype = None
+    L.sbr_mlp_free.argtypes = [p]
     _lib = L
     return L

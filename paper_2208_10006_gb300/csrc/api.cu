@@ -440,6 +440,18 @@ sbr_status sbr_pdp_angles(const sbr_path_list* pl, const void* gains, int32_t F,
                    (cudaStream_t)stream);
 }
 
+sbr_status sbr_surrogate_targets(const sbr_path_list* pl, const void* gains, int32_t F, int32_t n_taps,
+                                 double tap_s, double floor_db, float* out, void* stream) {
+    clear_error();
+    SBR_CHECK_ARG(pl != nullptr, "path list");
+    SBR_SAME_DEVICE(pl);
+    SBR_CHECK_ARG(F >= 1 && n_taps >= 1 && n_taps <= 32, "F >= 1, n_taps in [1, 32]");
+    SBR_CHECK_ARG(tap_s > 0 && std::isfinite(tap_s) && std::isfinite(floor_db), "tap_s > 0, finite floor_db");
+    SBR_CHECK_ARG(pl->n_rx == 0 || out, "out");
+    SBR_CHECK_ARG(pl->P == 0 || gains, "gains");
+    return surrogate_targets_run(pl, (const float2*)gains, F, n_taps, tap_s, floor_db, out, (cudaStream_t)stream);
+}
+
 sbr_status sbr_capacity(const void* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,
                         int32_t n_snr, double* C, void* stream) {
     clear_error();

@@ -192,6 +192,58 @@ __global__ void k_cap_reduce(const double* __restrict__ ld, int32_t F, int32_t n
     C[si] = s / F / log(2.0);
 }
 
+// surrogate targets: one warp per (receiver, frequency); FP64 sums over the
+// receiver's paths of P_n = |g_n(f)|^2, tau_n = L_n / c, relative to the first
+// arrival for the delay spread and the taps
+__global__ void k_surrogate_targets(const int32_t* __restrict__ rx_off, int32_t n_rx, const float2* __restrict__ g,
+                                    const double* __restrict__ L, int32_t F, int32_t n_taps, double tap_s,
+                                    double floor_db, float* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= (int64_t)n_rx * F) return;
+    const int r = (int)(w / F), f = (int)(w - (int64_t)r * F);
+    const int p0 = rx_off[r], p1 = rx_off[r + 1];
+    const int stride = 2 + n_taps;
+    float* o = out + w * stride;
+    if (p1 == p0) {
+        for (int k = lane; k < stride; k += 32) o[k] = NAN;
+        return;
+    }
+    double tmin = INFINITY;
+    for (int p = p0 + lane; p < p1; p += 32) tmin = fmin(tmin, L[p] / kC0);
+    for (int s = 16; s; s >>= 1) tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, s));
+    double sp = 0.0, st = 0.0, st2 = 0.0;
+    double tap[32];
+    for (int k = 0; k < 32; ++k) tap[k] = 0.0;
+    for (int p = p0 + lane; p < p1; p += 32) {
+        float2 gg = g[(int64_t)p * F + f];
+        double pw = (double)gg.x * gg.x + (double)gg.y * gg.y;
+        double t = L[p] / kC0 - tmin;
+        sp += pw;
+        st += pw * t;
+        st2 += pw * t * t;
+        double b = floor(t / tap_s);
+        if (b >= 0.0 && b < n_taps) {
+            int bi = (int)b;
+            for (int k = 0; k < 32; ++k) tap[k] += k == bi ? pw : 0.0;
+        }
+    }
+    for (int s = 16; s; s >>= 1) {
+        sp += __shfl_xor_sync(0xffffffffu, sp, s);
+        st += __shfl_xor_sync(0xffffffffu, st, s);
+        st2 += __shfl_xor_sync(0xffffffffu, st2, s);
+        for (int k = 0; k < 32; ++k) tap[k] += __shfl_xor_sync(0xffffffffu, tap[k], s);
+    }
+    if (lane != 0) return;
+    o[0] = (float)(-10.0 * log10(sp));
+    double mean = st / sp;
+    o[1] = (float)sqrt(fmax(st2 / sp - mean * mean, 0.0));
+    for (int k = 0; k < n_taps; ++k) {
+        double db = tap[k] > 0.0 ? 10.0 * log10(tap[k] / sp) : floor_db;
+        o[2 + k] = (float)fmax(db, floor_db);
+    }
+}
+
 }  // namespace
 
 sbr_status pdp_run(const sbr_path_list* pl, const float2* g, int32_t F, int32_t f_index, double fc,
@@ -209,6 +261,16 @@ sbr_status pdp_run(const sbr_path_list* pl, const float2* g, int32_t F, int32_t 
 size_t capacity_smem(int32_t Nr, int32_t Nt) {
     int n = std::min(Nr, Nt);
     return sizeof(float2) * (size_t)((n * n + 1) & ~1) + sizeof(double2) * (size_t)n * n;
+}
+
+sbr_status surrogate_targets_run(const sbr_path_list* pl, const float2* g, int32_t F, int32_t n_taps,
+                                double tap_s, double floor_db, float* out, cudaStream_t s) {
+    if (pl->n_rx == 0) return SBR_OK;
+    int64_t threads = (int64_t)pl->n_rx * F * 32;
+    ::sbr::note_launch(), k_surrogate_targets<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        pl->rx_off, pl->n_rx, g, pl->L, F, n_taps, tap_s, floor_db, out);
+    SBR_TRY_CUDA(cudaGetLastError());
+    return SBR_OK;
 }
 
 sbr_status capacity_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,

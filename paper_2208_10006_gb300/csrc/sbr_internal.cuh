@@ -217,6 +217,8 @@ sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* 
                         int32_t rx_index, float2* H, bool f16, cudaStream_t s);
 sbr_status pdp_run(const sbr_path_list* pl, const float2* g, int32_t F, int32_t f_index, double fc,
                    double bin_s, int32_t n_bins, float* pdp, double* stats, cudaStream_t s);
+sbr_status surrogate_targets_run(const sbr_path_list* pl, const float2* g, int32_t F, int32_t n_taps,
+                                double tap_s, double floor_db, float* out, cudaStream_t s);
 sbr_status capacity_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,
                         int32_t n_snr, double* C, cudaStream_t s);
 sbr_status capacity_noalloc_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt,

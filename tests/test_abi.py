@@ -66,7 +66,8 @@ def test_ctypes_struct_layouts_match_the_header(tmp_path):
               "sbr_path_info": (_lib.PathInfo, ["n_paths", "status"]),
               "sbr_batch_job": (_lib.BatchJob, ["tx", "alpha", "F", "freqs_hz", "H"]),
               "sbr_batch_config": (_lib.BatchConfig, ["path_cap", "use_graph"]),
-              "sbr_batch_info": (_lib.BatchInfo, ["max_keys", "rays", "config"])}
+              "sbr_batch_info": (_lib.BatchInfo, ["max_keys", "rays", "config"]),
+              "sbr_mlp_config": (_lib.MlpConfig, ["seed", "x_lo", "lr", "err_channel", "err_of"])}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sbr.h"', "int main(void) {"]
     for cname, (_, fields) in checks.items():
         lines.append('printf("%%zu\\n", sizeof(%s));' % cname)
