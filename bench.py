@@ -327,6 +327,9 @@ def run_gpu(args):
     batched = None
     if not args.no_batched and rank == 0:
         batched = bench_batched(sbr, torch, args)
+    surrogate = None
+    if not args.no_surrogate and rank == 0:
+        surrogate = bench_surrogate(sbr, torch, args)
 
     if rank != 0:
         torch.distributed.barrier()
@@ -383,6 +386,7 @@ def run_gpu(args):
         "clocks": clk,
         "synthesis": synth,
         "batched": batched,
+        "surrogate": surrogate,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -456,6 +460,16 @@ def bench_synthesis(sbr, torch, flush, peaks, peak_src, args):
     out["unit"] = "H tensors/s"
     C = sbr.capacity(H, sc["snr_db"])
     out["capacity_bits_per_s_per_hz"] = [float(x) for x in C.cpu()]
+    # capacity against the Tx array size (16^2 ... 128^2 UPA, same paths and 64-ULA Rx)
+    lam = 299792458.0 / 100e9
+    trend = {}
+    del H
+    for n in (16, 32, 64, 128):
+        te = torch.as_tensor(scenes.upa_yz(sc["tx"], n, n, lam / 2), dtype=torch.float64, device="cuda")
+        Hn = sbr.synthesize_H(pl, g, d["freqs"], te, d["rx_elem"], 0, sbr.SYNTH_FP16X3)
+        trend["%dx%d" % (n, n)] = [float(x) for x in sbr.capacity(Hn, sc["snr_db"]).cpu()]
+        del Hn
+    out["capacity_vs_tx_array"] = {"snr_db": [float(s) for s in sc["snr_db"]], "bits_per_s_per_hz": trend}
     return out
 
 
@@ -545,6 +559,63 @@ def bench_batched(sbr, torch, args):
     return out
 
 
+def bench_surrogate(sbr, torch, args):
+    """The learned surrogate on the urban 300 GHz scene (51,600 triangles, Tx
+    (240,120,25), 10,000,002 rays, K = 6): targets of 131,072 receivers at 8
+    frequencies over 280-320 GHz (1,048,576 samples, seed 5) from full SBR,
+    training of the 4 x 256 BF16 MLP, evaluation on 1,250 held-out receivers
+    at 8 other in-band frequencies (10,000 queries, seed 6) against full SBR,
+    and inference throughput against full SBR's per-sample rate."""
+    from paper_2208_10006_gb300 import surrogate as S
+    sc = scenes.config2()
+    f_train = np.linspace(280e9, 320e9, 8)
+    f_test = np.sort(np.random.default_rng(6).uniform(280e9, 320e9, 8))
+    rx = S.sample_receivers(sc, args.surrogate_rx, seed=5)
+    rx_t = S.sample_receivers(sc, 1250, seed=6)
+    d = sbr.scene_to_device(sc)
+    bvh = sbr.build_bvh(d["tri"], d["surface_id"], d["S"])
+    alpha = float(sbr.launch_dirs(sc["N"], with_dirs=False)[1].cpu()[0])
+    S.sbr_targets(sc, rx[:16384], f_train, alpha=alpha, dev=d, bvh=bvh)      # warm-up
+    t, gen_s = S.sbr_targets(sc, rx, f_train, alpha=alpha, dev=d, bvh=bvh)
+    tt, _ = S.sbr_targets(sc, rx_t, f_test, alpha=alpha, dev=d, bvh=bvh)
+    X, Y = S.make_xy(rx, f_train, t)
+    Xt, Yt = S.make_xy(rx_t, f_test, tt)
+    lo, hi = S.x_box(sc, [280e9, 320e9])
+    m, hist, train_s = S.train(X, Y, lo, hi, epochs=args.surrogate_epochs)
+    ev = S.evaluate(m, Xt, Yt, threshold_db=3.0)
+    # inference: one call of 1,048,576 queries on a copy of the trained model
+    nq = X.shape[0]
+    mi = sbr.MLP(S.N_OUT, lo, hi, max_batch=nq, err_channel=S.CH_ERR, err_of=S.CH_PL, loss_w=S.LOSS_W,
+                 y_shift=S.SHIFT, y_scale=S.SCALE)
+    mi.params(1, m.params(0))
+    out = torch.empty((nq, S.N_OUT), dtype=torch.float32, device="cuda")
+    mi.predict(X, out=out)
+    ts = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mi.predict(X, out=out)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    t_q = min(ts)
+    ok = bool(torch.allclose(out[:8192], m.predict(X[:8192].contiguous())))
+    mi.status()
+    flops = 2.0 * nq * (128 * 256 + 3 * 256 * 256 + 256 * 128)
+    sbr_rate = X.shape[0] / gen_s
+    q = nq / t_q
+    for v in ev["fallback"].values():   # throughput with the fallback queries sent to full SBR
+        v["queries_per_s"] = 1.0 / ((1.0 - v["fraction"]) / q + v["fraction"] / sbr_rate)
+    return {"metric": "surrogate queries/s", "value": nq / t_q, "unit": "queries/s",
+            "workload": "urban_300GHz_51600tri_N1000_K6: 131072 rx x 8 f train, 1250 rx x 8 f held out",
+            "train_samples": int(X.shape[0]), "test_queries": int(Xt.shape[0]),
+            "sbr_data_s": gen_s, "sbr_samples_per_s": sbr_rate,
+            "train_s": train_s, "epochs": args.surrogate_epochs, "loss_first_last": [hist[0], hist[-1]],
+            "inference_ms_per_1M": t_q * 1e3 * 1048576 / nq, "inference_TFLOPs": flops / t_q / 1e12,
+            "speedup_vs_sbr_per_sample": (nq / t_q) / sbr_rate, "large_batch_matches_small": ok,
+            "eval": ev}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__,
                                  formatter_class=argparse.RawDescriptionHelpFormatter)
@@ -555,6 +626,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-synth", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-rx", type=int, default=131072)
+    ap.add_argument("--surrogate-epochs", type=int, default=60)
     ap.add_argument("--batch-jobs", type=int, default=4096)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")

@@ -482,6 +482,8 @@ int64_t sbr_mlp_param_count(const sbr_mlp* m);
  * the last training step. Layout of sbr_mlp_param_count. Asynchronous.
  */
 sbr_status sbr_mlp_params(sbr_mlp* m, float* params, int32_t mode, void* stream);
+/* learning rate of the following steps (a schedule is the caller's) */
+sbr_status sbr_mlp_set_lr(sbr_mlp* m, float lr);
 /* synchronous: SBR_ERR_TIMEOUT if a bounded tensor-core wait gave up */
 sbr_status sbr_mlp_status(const sbr_mlp* m);
 void sbr_mlp_free(sbr_mlp* m);

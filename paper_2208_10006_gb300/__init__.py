@@ -508,6 +508,9 @@ class MLP:
     def status(self):
         _check(_L().sbr_mlp_status(self._h))
 
+    def set_lr(self, lr: float):
+        _check(_L().sbr_mlp_set_lr(self._h, float(lr)))
+
     def free(self):
         if self._h:
             _L().sbr_mlp_free(self._h)

@@ -24,7 +24,8 @@ EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_count", "sbr_launch_dirs
            "sbr_synthesize_H", "sbr_pdp_angles", "sbr_capacity", "sbr_capacity_noalloc",
            "sbr_batch_create", "sbr_batch_run", "sbr_batch_query", "sbr_batch_export", "sbr_batch_free",
            "sbr_batch_tune", "sbr_surrogate_targets", "sbr_mlp_create", "sbr_mlp_train_step",
-           "sbr_mlp_predict", "sbr_mlp_param_count", "sbr_mlp_params", "sbr_mlp_status", "sbr_mlp_free"]
+           "sbr_mlp_predict", "sbr_mlp_param_count", "sbr_mlp_params", "sbr_mlp_status", "sbr_mlp_free",
+           "sbr_mlp_set_lr"]
 
 
 class TraceParams(C.Structure):
@@ -166,6 +167,8 @@ def load() -> C.CDLL:
     L.sbr_mlp_params.argtypes = [p, p, i32, p]
     L.sbr_mlp_status.restype = st
     L.sbr_mlp_status.argtypes = [p]
+    L.sbr_mlp_set_lr.restype = st
+    L.sbr_mlp_set_lr.argtypes = [p, C.c_float]
     L.sbr_mlp_free.restype = None
     L.sbr_mlp_free.argtypes = [p]
     _lib = L

@@ -635,6 +635,13 @@ sbr_status sbr_mlp_status(const sbr_mlp* m) {
     return status_from_bits(bits);
 }
 
+sbr_status sbr_mlp_set_lr(sbr_mlp* m, float lr) {
+    clear_error();
+    SBR_CHECK_ARG(m != nullptr && lr > 0.f && std::isfinite(lr), "mlp and lr > 0");
+    m->cfg.lr = lr;
+    return SBR_OK;
+}
+
 void sbr_mlp_free(sbr_mlp* m) { free_mlp(m); }
 
 }  // extern "C"

@@ -112,8 +112,9 @@ def x_box(sc: dict, freqs) -> tuple:
 
 
 def train(X: torch.Tensor, Y: torch.Tensor, lo, hi, epochs: int = 20, batch: int = 8192, lr: float = 2e-3,
-          seed: int = 5, width: int = 256, depth: int = 4):
-    """Adam on shuffled batches; returns (model, per-epoch mean loss, seconds)."""
+          seed: int = 5, width: int = 256, depth: int = 4, lr_min: float = 5e-5):
+    """Adam on shuffled batches, learning rate on a cosine from lr to lr_min
+    over the epochs; returns (model, per-epoch mean loss, seconds)."""
     m = MLP(N_OUT, lo, hi, width=width, depth=depth, max_batch=batch, seed=seed, lr=lr,
             err_channel=CH_ERR, err_of=CH_PL, loss_w=LOSS_W, y_shift=SHIFT, y_scale=SCALE)
     gen = torch.Generator(device="cuda")
@@ -124,6 +125,7 @@ def train(X: torch.Tensor, Y: torch.Tensor, lo, hi, epochs: int = 20, batch: int
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for ep in range(epochs):
+        m.set_lr(lr_min + 0.5 * (lr - lr_min) * (1.0 + np.cos(np.pi * ep / max(epochs, 1))))
         perm = torch.randperm(n, device="cuda", generator=gen)
         loss.zero_()
         steps = 0
@@ -144,24 +146,28 @@ def predict(m: MLP, X: torch.Tensor, batch: int = 8192) -> torch.Tensor:
     return out
 
 
-def evaluate(m: MLP, X: torch.Tensor, Y: torch.Tensor, threshold_db: float = 3.0) -> dict:
+def evaluate(m: MLP, X: torch.Tensor, Y: torch.Tensor, threshold_db: float = 3.0,
+             thresholds=(3.0, 6.0, 10.0)) -> dict:
     """Errors against full SBR on (X, Y), and the effect of the fallback rule:
-    a query goes to full SBR when the error head predicts more than
-    threshold_db of path-loss error or the coverage output is in (0.2, 0.8)."""
+    a query goes to full SBR when the error head predicts more than the
+    threshold of path-loss error or the coverage output is in (0.2, 0.8); per
+    threshold, the fraction of queries that fall back, the path-loss RMSE of
+    the served ones and the RMSE over all (fallback answers exact)."""
     P = predict(m, X)
     cov = Y[:, CH_COV] > 0.5
     pc = P[:, CH_COV]
-    fb = (P[:, CH_ERR] > threshold_db) | ((pc > 0.2) & (pc < 0.8))
     e_pl = (P[:, CH_PL] - Y[:, CH_PL])[cov]
     e_tau = (P[:, CH_TAU] - Y[:, CH_TAU])[cov]
     e_tap = (P[:, CH_TAP0:CH_TAP0 + N_TAPS] - Y[:, CH_TAP0:CH_TAP0 + N_TAPS])[cov]
-    kept = ~fb[cov]
     rms = lambda e: float(torch.sqrt((e.double() ** 2).mean())) if e.numel() else float("nan")
     cov_ok = ((pc > 0.5) == cov).float().mean()
-    return dict(n=int(X.shape[0]), covered=float(cov.float().mean()),
-                pl_rmse_db=rms(e_pl), tau_rmse_ns=rms(e_tau), taps_rmse_db=rms(e_tap),
-                coverage_accuracy=float(cov_ok), fallback_fraction=float(fb.float().mean()),
-                pl_rmse_db_served=rms(e_pl[kept]),
-                pl_rmse_db_with_fallback=float(torch.sqrt((torch.where(kept, e_pl, torch.zeros_like(e_pl)).double() ** 2)
-                                                          .mean())) if e_pl.numel() else float("nan"),
-                threshold_db=threshold_db)
+    out = dict(n=int(X.shape[0]), covered=float(cov.float().mean()),
+               pl_rmse_db=rms(e_pl), tau_rmse_ns=rms(e_tau), taps_rmse_db=rms(e_tap),
+               coverage_accuracy=float(cov_ok), fallback={})
+    for th in sorted(set(thresholds) | {threshold_db}):
+        fb = (P[:, CH_ERR] > th) | ((pc > 0.2) & (pc < 0.8))
+        kept = ~fb[cov]
+        out["fallback"]["%g_dB" % th] = dict(
+            fraction=float(fb.float().mean()), pl_rmse_db_served=rms(e_pl[kept]),
+            pl_rmse_db_with_fallback=rms(torch.where(kept, e_pl, torch.zeros_like(e_pl))))
+    return out

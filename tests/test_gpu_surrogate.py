@@ -43,5 +43,8 @@ def test_surrogate_workflow_learns_path_loss(sbr):
     pl = Yt[Yt[:, S.CH_COV] > 0.5, S.CH_PL]
     assert ev["pl_rmse_db"] < 0.6 * float(pl.std())
     assert ev["coverage_accuracy"] > 0.8
-    assert 0.0 <= ev["fallback_fraction"] <= 1.0
-    assert ev["pl_rmse_db_with_fallback"] <= ev["pl_rmse_db"]
+    fb = ev["fallback"]["3_dB"]
+    assert 0.0 <= fb["fraction"] <= 1.0
+    assert fb["pl_rmse_db_with_fallback"] <= ev["pl_rmse_db"]
+    # a looser threshold serves more queries
+    assert ev["fallback"]["10_dB"]["fraction"] <= fb["fraction"]
