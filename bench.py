@@ -586,7 +586,7 @@ def bench_surrogate(sbr, torch, args):
     # inference: one call of 1,048,576 queries on a copy of the trained model
     nq = X.shape[0]
     mi = sbr.MLP(S.N_OUT, lo, hi, max_batch=nq, err_channel=S.CH_ERR, err_of=S.CH_PL, loss_w=S.LOSS_W,
-                 y_shift=S.SHIFT, y_scale=S.SCALE)
+                 y_shift=S.SHIFT, y_scale=S.SCALE, feat_log2_max=2.0)
     mi.params(1, m.params(0))
     out = torch.empty((nq, S.N_OUT), dtype=torch.float32, device="cuda")
     mi.predict(X, out=out)
@@ -628,7 +628,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-rx", type=int, default=131072)
-    ap.add_argument("--surrogate-epochs", type=int, default=60)
+    ap.add_argument("--surrogate-epochs", type=int, default=40)
     ap.add_argument("--batch-jobs", type=int, default=4096)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")

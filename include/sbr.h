@@ -449,12 +449,14 @@ typedef struct {
     float lr, beta1, beta2, eps;   /* Adam                                                */
     int32_t err_channel;    /* output that learns |output err_of - its target|, or -1       */
     int32_t err_of;         /* (stop-gradient on output err_of), or -1                      */
+    float feat_log2_max;    /* highest feature frequency pi 2^feat_log2_max (0 = 9)         */
+    int32_t reserved;
 } sbr_mlp_config;
 
 /*
  * sbr_mlp_create - the MLP: 128 Fourier features of (x, y, z, f) (coordinate
- * c, octave k = 0..15: sin and cos of pi 2^(9k/15) u_c, u = (x - x_lo) /
- * (x_hi - x_lo)) -> depth ReLU layers of `width` -> 128 linear outputs, the
+ * c, octave k = 0..15: sin and cos of pi 2^(k m / 15) u_c, u = (x - x_lo) /
+ * (x_hi - x_lo), m = feat_log2_max) -> depth ReLU layers of `width` -> 128 linear outputs, the
  * first n_out used. BF16 operands on the tcgen05 tensor cores, FP32
  * accumulation and FP32 master weights. loss_w: host [n_out] weights of the
  * squared errors (NULL: all 1); y_shift, y_scale: host [n_out] target

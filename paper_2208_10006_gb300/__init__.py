@@ -472,7 +472,8 @@ class MLP:
 
     def __init__(self, n_out: int, x_lo, x_hi, width: int = 256, depth: int = 4, max_batch: int = 8192,
                  seed: int = 0, lr: float = 1e-3, betas=(0.9, 0.999), eps: float = 1e-8, err_channel: int = -1,
-                 err_of: int = -1, loss_w=None, y_shift=None, y_scale=None, stream=None):
+                 err_of: int = -1, loss_w=None, y_shift=None, y_scale=None, feat_log2_max: float = 9.0,
+                 stream=None):
         c = _lib.MlpConfig()
         c.n_out, c.width, c.depth, c.max_batch, c.seed = n_out, width, depth, max_batch, seed
         for k in range(4):
@@ -480,6 +481,7 @@ class MLP:
             c.x_hi[k] = float(x_hi[k])
         c.lr, c.beta1, c.beta2, c.eps = lr, betas[0], betas[1], eps
         c.err_channel, c.err_of = err_channel, err_of
+        c.feat_log2_max = feat_log2_max
         self.n_out, self.max_batch = n_out, max_batch
         arr = lambda v: None if v is None else np.ascontiguousarray(v, dtype=np.float32)
         lw, sh, sc = arr(loss_w), arr(y_shift), arr(y_scale)

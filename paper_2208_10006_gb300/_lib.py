@@ -80,7 +80,7 @@ class MlpConfig(C.Structure):
     _fields_ = [("n_out", C.c_int32), ("width", C.c_int32), ("depth", C.c_int32), ("max_batch", C.c_int32),
                 ("seed", C.c_uint64), ("x_lo", C.c_float * 4), ("x_hi", C.c_float * 4), ("lr", C.c_float),
                 ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("err_channel", C.c_int32),
-                ("err_of", C.c_int32)]
+                ("err_of", C.c_int32), ("feat_log2_max", C.c_float), ("reserved", C.c_int32)]
 
 
 assert C.sizeof(TraceParams) == 64

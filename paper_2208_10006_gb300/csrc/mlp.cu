@@ -151,8 +151,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm(const __grid_constant__ G
 }
 
 // Fourier features of x = (x, y, z, f) mapped to u in [0, 1]^4: for coordinate
-// c and octave k, sin and cos of pi 2^(9k/15) u_c; rows >= B are zero
-__global__ void k_features(const float* __restrict__ x, int B, int Mp, float4 lo, float4 inv,
+// c and octave k, sin and cos of pi 2^(k lmax / 15) u_c; rows >= B are zero
+__global__ void k_features(const float* __restrict__ x, int B, int Mp, float4 lo, float4 inv, float lmax,
                            bf16* __restrict__ feat) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= Mp * 4 * kOctaves) return;
@@ -164,7 +164,7 @@ __global__ void k_features(const float* __restrict__ x, int B, int Mp, float4 lo
         float lov = c == 0 ? lo.x : (c == 1 ? lo.y : (c == 2 ? lo.z : lo.w));
         float iv = c == 0 ? inv.x : (c == 1 ? inv.y : (c == 2 ? inv.z : inv.w));
         float u = (xv - lov) * iv;
-        float w = exp2f(9.0f * (float)k / 15.0f);
+        float w = exp2f(lmax * (float)k / 15.0f);
         sincospif(w * u, &s, &co);
     }
     feat[(size_t)b * kFeat + c * 2 * kOctaves + 2 * k] = __float2bfloat16_rn(s);
@@ -380,7 +380,8 @@ sbr_status forward(const sbr_mlp* m, const float* x, int B, cudaStream_t s) {
     float4 lo = make_float4(c.x_lo[0], c.x_lo[1], c.x_lo[2], c.x_lo[3]);
     float4 inv = make_float4(1.f / (c.x_hi[0] - c.x_lo[0]), 1.f / (c.x_hi[1] - c.x_lo[1]),
                              1.f / (c.x_hi[2] - c.x_lo[2]), 1.f / (c.x_hi[3] - c.x_lo[3]));
-    ::sbr::note_launch(), k_features<<<nblk((int64_t)Mp * 4 * kOctaves), 256, 0, s>>>(x, B, Mp, lo, inv, m->feat);
+    ::sbr::note_launch(), k_features<<<nblk((int64_t)Mp * 4 * kOctaves), 256, 0, s>>>(x, B, Mp, lo, inv,
+                                                                                      c.feat_log2_max, m->feat);
     SBR_TRY_CUDA(cudaGetLastError());
     const bf16* in = m->feat;
     for (size_t l = 0; l < m->L.size(); ++l) {
@@ -510,12 +511,14 @@ sbr_status sbr_mlp_create(const sbr_mlp_config* cfg, const float* loss_w, const 
                        c.err_of != c.err_channel),
                   "error head channels: both -1, or two different outputs");
     for (int k = 0; k < 4; ++k) SBR_CHECK_ARG(c.x_hi[k] > c.x_lo[k], "x_hi > x_lo");
+    SBR_CHECK_ARG(c.feat_log2_max >= 0.f && c.feat_log2_max <= 20.f, "feat_log2_max in [0, 20]");
     SBR_CHECK_ARG(c.lr > 0.f && c.beta1 >= 0.f && c.beta1 < 1.f && c.beta2 >= 0.f && c.beta2 < 1.f && c.eps > 0.f,
                   "Adam hyper-parameters");
     sbr_mlp* m = new (std::nothrow) sbr_mlp();
     if (!m) { set_error("host allocation"); return SBR_ERR_ALLOC; }
     SBR_TRY_CUDA(cudaGetDevice(&m->device));
     m->cfg = c;
+    if (m->cfg.feat_log2_max == 0.f) m->cfg.feat_log2_max = 9.f;
     m->Mp = ((c.max_batch + 127) / 128) * 128;
     m->loss_w.assign(c.n_out, 1.f);
     if (loss_w) for (int k = 0; k < c.n_out; ++k) m->loss_w[k] = loss_w[k];

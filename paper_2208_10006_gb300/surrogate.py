@@ -12,9 +12,13 @@ Outputs of the network (target units):
   1        RMS delay spread (ns)
   2 .. 17  PDP taps relative to the total power (dB, 5 ns taps from the first
            arrival, floor -40 dB)
-  18       coverage (1 when the receiver has at least one path, else 0)
+  18       coverage (1 when the receiver has a path loss of at most
+           PL_MAX_DB, else 0)
   19       error head: the expected |path-loss error| (dB)
-A receiver without paths has no path-loss, delay or tap target.
+A receiver out of coverage has no path-loss, delay or tap target. At 300 GHz
+the Kirchhoff factor of a rough facade removes tens of dB per reflection, so
+receivers reached only by high-order paths sit at 200-500 dB: far below any
+link budget, and read here as out of coverage.
 """
 from __future__ import annotations
 
@@ -28,6 +32,7 @@ from . import MLP, POL_H, POL_V, build_bvh, path_gains, paths, scene_to_device, 
 N_TAPS, TAP_S, FLOOR_DB = 16, 5e-9, -40.0
 CH_PL, CH_TAU, CH_TAP0, CH_COV, CH_ERR = 0, 1, 2, 18, 19
 N_OUT = 20
+PL_MAX_DB = 200.0
 SHIFT = np.array([120.0, 20.0] + [-20.0] * N_TAPS + [0.0, 0.0], np.float32)
 SCALE = np.array([20.0, 20.0] + [20.0] * N_TAPS + [1.0, 20.0], np.float32)
 LOSS_W = np.array([1.0, 0.5] + [0.25] * N_TAPS + [1.0, 0.5], np.float32)
@@ -89,16 +94,17 @@ def sbr_targets(sc: dict, rx: np.ndarray, freqs: np.ndarray, alpha: float = 0.0,
     return out, e0.elapsed_time(e1) / 1e3
 
 
-def make_xy(rx: np.ndarray, freqs: np.ndarray, t: torch.Tensor):
+def make_xy(rx: np.ndarray, freqs: np.ndarray, t: torch.Tensor, pl_max_db: float = PL_MAX_DB):
     """Inputs [n F, 4] (x, y, z, f) and targets [n F, N_OUT] from sbr_targets."""
     n, F = len(rx), len(freqs)
     X = np.empty((n, F, 4), np.float32)
     X[:, :, :3] = rx[:, None, :]
     X[:, :, 3] = np.asarray(freqs)[None, :]
+    cov = torch.isfinite(t[:, :, 0]) & (t[:, :, 0] <= pl_max_db)
     Y = torch.full((n, F, N_OUT), float("nan"), dtype=torch.float32, device="cuda")
-    Y[:, :, :2 + N_TAPS] = t
+    Y[:, :, :2 + N_TAPS] = torch.where(cov[:, :, None], t, torch.full_like(t, float("nan")))
     Y[:, :, CH_TAU] *= 1e9
-    Y[:, :, CH_COV] = torch.isfinite(t[:, :, 0]).float()
+    Y[:, :, CH_COV] = cov.float()
     return torch.as_tensor(X.reshape(-1, 4), device="cuda"), Y.reshape(-1, N_OUT)
 
 
@@ -112,11 +118,12 @@ def x_box(sc: dict, freqs) -> tuple:
 
 
 def train(X: torch.Tensor, Y: torch.Tensor, lo, hi, epochs: int = 20, batch: int = 8192, lr: float = 2e-3,
-          seed: int = 5, width: int = 256, depth: int = 4, lr_min: float = 5e-5):
+          seed: int = 5, width: int = 256, depth: int = 4, lr_min: float = 5e-5, feat_log2_max: float = 2.0):
     """Adam on shuffled batches, learning rate on a cosine from lr to lr_min
     over the epochs; returns (model, per-epoch mean loss, seconds)."""
     m = MLP(N_OUT, lo, hi, width=width, depth=depth, max_batch=batch, seed=seed, lr=lr,
-            err_channel=CH_ERR, err_of=CH_PL, loss_w=LOSS_W, y_shift=SHIFT, y_scale=SCALE)
+            err_channel=CH_ERR, err_of=CH_PL, loss_w=LOSS_W, y_shift=SHIFT, y_scale=SCALE,
+            feat_log2_max=feat_log2_max)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed)
     n = X.shape[0]

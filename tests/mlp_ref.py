@@ -20,8 +20,8 @@ def bf16(a):
     return (r & 0xFFFFFFFF).astype(np.uint32).view(np.float32)
 
 
-def features(x, lo, hi, rnd=True):
-    """[B, 4] -> [B, 128]: coordinate c, octave k: sin, cos of pi 2^(9k/15) u_c."""
+def features(x, lo, hi, rnd=True, lmax=9.0):
+    """[B, 4] -> [B, 128]: coordinate c, octave k: sin, cos of pi 2^(k lmax/15) u_c."""
     x = np.asarray(x, np.float32)
     lo = np.asarray(lo, np.float32)
     inv = (np.float32(1.0) / (np.asarray(hi, np.float32) - lo)).astype(np.float32)
@@ -30,7 +30,7 @@ def features(x, lo, hi, rnd=True):
     f = np.zeros((B, N_FEAT), np.float32)
     for c in range(4):
         for k in range(N_OCT):
-            w = np.exp2(np.float32(9.0 * k / 15.0)).astype(np.float32)
+            w = np.exp2(np.float32(np.float32(lmax) * np.float32(k) / np.float32(15.0))).astype(np.float32)
             arg = (w * u[:, c]).astype(np.float64)
             f[:, c * 2 * N_OCT + 2 * k] = np.sin(np.pi * arg)
             f[:, c * 2 * N_OCT + 2 * k + 1] = np.cos(np.pi * arg)
