@@ -616,6 +616,63 @@ def bench_surrogate(sbr, torch, args):
             "eval": ev}
 
 
+def profile_case(case: str) -> int:
+    """Small single-purpose runs for ncu captures (no timing, no JSON line):
+    synth: the indoor MIMO workload traced, then H synthesised in the FP16x3,
+           BF16x3 and FP16x3 tensor-core forms;
+    batch: 48 jobs of the batched workload (seed 4) over its first 4 scenes, one
+           run with plain stream launches;
+    mlp:   three surrogate training steps (batch 8192) and one prediction of
+           1,048,576 queries."""
+    import torch
+    import paper_2208_10006_gb300 as sbr
+    from paper_2208_10006_gb300 import build as b
+    b.build()
+    if case == "synth":
+        sc = scenes.config3()
+        r = sbr.run_scene(sc)
+        d = r["dev"]
+        for prec in (sbr.SYNTH_FP16X3, sbr.SYNTH_BF16X3, sbr.SYNTH_FP16X3):
+            H = sbr.synthesize_H(r["paths"], r["g"], d["freqs"], d["tx_elem"], d["rx_elem"], 0, prec)
+        torch.cuda.synchronize()
+        print("synth", r["paths"].n, float(H.abs().max()))
+    elif case == "batch":
+        scs = [scenes.batch_scene(s) for s in range(4)]
+        jobs = scenes.batch_jobs(scs, n_jobs=48, seed=4)
+        dev = torch.device("cuda")
+        sdev = []
+        for sc in scs:
+            tri = torch.as_tensor(sc["tri"].reshape(-1, 9), dtype=torch.float32, device=dev)
+            sid = torch.as_tensor(sc["surface_id"], dtype=torch.int32, device=dev)
+            mats = torch.as_tensor(sc["materials"], dtype=torch.float64, device=dev)
+            sdev.append((sbr.build_bvh(tri, sid, len(sc["materials"])), mats))
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        jdev = [dict(scene=j["scene"], N=j["N"], K=j["K"], tx=j["tx"], rx=j["rx"], pol=j["pol"],
+                     freqs=t(j["freqs"], torch.float64), gamma=t(j["gamma"], torch.float32),
+                     tx_elem=t(j["tx_elem"], torch.float64), rx_elem=t(j["rx_elem"], torch.float64))
+                for j in jobs]
+        bt = sbr.batch_create(sdev, jdev, config=dict(path_cap=256, tile_n=64, use_graph=0))
+        bt.run()
+        n, st, info = bt.query()
+        print("batch", info["rays"], info["ray_bounces"], int((st != 0).sum()))
+    elif case == "mlp":
+        from paper_2208_10006_gb300 import surrogate as S
+        rng = np.random.default_rng(0)
+        B = 8192
+        x = torch.tensor(np.column_stack([rng.uniform(0, 1, B) for _ in range(4)]).astype(np.float32), device="cuda")
+        y = torch.tensor(rng.normal(size=(B, S.N_OUT)).astype(np.float32), device="cuda")
+        m = sbr.MLP(S.N_OUT, [0] * 4, [1] * 4, max_batch=B, err_channel=S.CH_ERR, err_of=S.CH_PL)
+        for _ in range(3):
+            m.train_step(x, y)
+        big = torch.tensor(rng.uniform(0, 1, (1 << 20, 4)).astype(np.float32), device="cuda")
+        mi = sbr.MLP(S.N_OUT, [0] * 4, [1] * 4, max_batch=1 << 20)
+        mi.predict(big)
+        torch.cuda.synchronize()
+        m.status()
+        print("mlp ok")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__,
                                  formatter_class=argparse.RawDescriptionHelpFormatter)
@@ -627,6 +684,8 @@ def main():
     ap.add_argument("--no-synth", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--profile-case", choices=["synth", "batch", "mlp"], default=None,
+                    help="run one small workload for an ncu capture and exit")
     ap.add_argument("--surrogate-rx", type=int, default=131072)
     ap.add_argument("--surrogate-epochs", type=int, default=40)
     ap.add_argument("--batch-jobs", type=int, default=4096)
@@ -637,6 +696,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.profile_case:
+        return profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
