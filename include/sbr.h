@@ -474,8 +474,15 @@ sbr_status sbr_mlp_create(const sbr_mlp_config* cfg, const float* loss_w, const 
  * float accumulated with atomicAdd (zero it first), or NULL. Asynchronous.
  */
 sbr_status sbr_mlp_train_step(sbr_mlp* m, const float* x, const float* y, int32_t B, float* loss, void* stream);
-/* sbr_mlp_predict - y dev [B*n_out] = outputs for x dev [B*4]. Asynchronous. */
+/*
+ * sbr_mlp_predict - y dev [B*n_out] = outputs for x dev [B*4], in one fused
+ * launch (every layer of 128 rows per CTA with the activations kept in shared
+ * memory). sbr_mlp_predict_layered: the same outputs through the training
+ * path's per-layer GEMMs (activations through device memory), for checking.
+ * Asynchronous.
+ */
 sbr_status sbr_mlp_predict(const sbr_mlp* m, const float* x, int32_t B, float* y, void* stream);
+sbr_status sbr_mlp_predict_layered(const sbr_mlp* m, const float* x, int32_t B, float* y, void* stream);
 /* number of FP32 parameters (per layer: W [n_out][n_in] row-major, then b) */
 int64_t sbr_mlp_param_count(const sbr_mlp* m);
 /*

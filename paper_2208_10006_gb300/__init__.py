@@ -494,10 +494,13 @@ class MLP:
         assert x.dtype == torch.float32 and y.dtype == torch.float32
         _check(_L().sbr_mlp_train_step(self._h, _ptr(x), _ptr(y), int(x.shape[0]), _ptr(loss), _stream(stream)))
 
-    def predict(self, x: torch.Tensor, out: torch.Tensor = None, stream=None) -> torch.Tensor:
+    def predict(self, x: torch.Tensor, out: torch.Tensor = None, layered: bool = False,
+                stream=None) -> torch.Tensor:
+        """Outputs for x [B, 4]: one fused launch, or (layered) the per-layer GEMMs."""
         B = int(x.shape[0])
         y = out if out is not None else torch.empty((B, self.n_out), dtype=torch.float32, device=_dev())
-        _check(_L().sbr_mlp_predict(self._h, _ptr(x), B, _ptr(y), _stream(stream)))
+        fn = _L().sbr_mlp_predict_layered if layered else _L().sbr_mlp_predict
+        _check(fn(self._h, _ptr(x), B, _ptr(y), _stream(stream)))
         return y
 
     def params(self, mode: int = 0, values: torch.Tensor = None, stream=None) -> torch.Tensor:

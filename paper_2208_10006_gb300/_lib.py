@@ -25,7 +25,7 @@ EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_count", "sbr_launch_dirs
            "sbr_batch_create", "sbr_batch_run", "sbr_batch_query", "sbr_batch_export", "sbr_batch_free",
            "sbr_batch_tune", "sbr_surrogate_targets", "sbr_mlp_create", "sbr_mlp_train_step",
            "sbr_mlp_predict", "sbr_mlp_param_count", "sbr_mlp_params", "sbr_mlp_status", "sbr_mlp_free",
-           "sbr_mlp_set_lr"]
+           "sbr_mlp_set_lr", "sbr_mlp_predict_layered"]
 
 
 class TraceParams(C.Structure):
@@ -161,6 +161,8 @@ def load() -> C.CDLL:
     L.sbr_mlp_train_step.argtypes = [p, p, p, i32, p, p]
     L.sbr_mlp_predict.restype = st
     L.sbr_mlp_predict.argtypes = [p, p, i32, p, p]
+    L.sbr_mlp_predict_layered.restype = st
+    L.sbr_mlp_predict_layered.argtypes = [p, p, i32, p, p]
     L.sbr_mlp_param_count.restype = i64
     L.sbr_mlp_param_count.argtypes = [p]
     L.sbr_mlp_params.restype = st

@@ -50,11 +50,12 @@ struct GemmArgs {
 
 template <int kN>
 struct GemmShape {
-    static constexpr int kSmemTiles = 128 * 128 + kN * 128;   // A and B chunks of 64 BF16 per row
-    // request enough shared memory that at most 512 / kN CTAs share an SM, so
+    static constexpr int kStage = 128 * 128 + kN * 128;   // A and B chunks of 64 BF16 per row
+    static constexpr int kSmemTiles = 2 * kStage;          // two stages
+    // at least the tiles, and enough that at most 512 / kN CTAs share an SM, so
     // their tensor-memory allocations (kN columns each) always fit
-    static constexpr int kSmemReq = 228 * 1024 / (512 / kN + 1) + 1024;
-    static_assert(kSmemTiles + 1024 + 64 <= kSmemReq, "shared memory request");
+    static constexpr int kTmemReq = 228 * 1024 / (512 / kN + 1) + 1024;
+    static constexpr int kSmemReq = kSmemTiles + 1024 + 64 > kTmemReq ? kSmemTiles + 1024 + 64 : kTmemReq;
 };
 
 // C = A B^T (FP32 accumulation) with a fused epilogue
@@ -62,10 +63,9 @@ template <int kN, int kMode>
 __global__ void __launch_bounds__(kGThreads, 1) k_gemm(const __grid_constant__ GemmArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* sA = smem;
-    unsigned char* sB = smem + 128 * 128;
-    uint64_t* mbar = (uint64_t*)(smem + GemmShape<kN>::kSmemTiles);
-    uint32_t* tmem_slot = (uint32_t*)(smem + GemmShape<kN>::kSmemTiles + 16);
+    using Sh = GemmShape<kN>;
+    uint64_t* mbar = (uint64_t*)(smem + Sh::kSmemTiles);
+    uint32_t* tmem_slot = (uint32_t*)(smem + Sh::kSmemTiles + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm(const __grid_constant__ G
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+        for (int k = 0; k < 2; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar + k)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -82,37 +82,63 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm(const __grid_constant__ G
     const uint32_t tmem = *tmem_slot;
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * kN;
     const int k0 = blockIdx.z * a.k_split, k1 = min(a.K, k0 + a.k_split);
-    uint32_t phase = 0;
-    bool failed = false, any = false;
-    for (int kc = k0; kc < k1 && !failed; kc += 64) {
-        // 16-byte vectors of 8 BF16 into the swizzled K-major tiles
+    // 16-byte vectors of 8 BF16 of K-chunk kc into the swizzled K-major tiles of
+    // stage b, with cp.async: chunk kc + 1 is in flight while chunk kc's MMAs run
+    auto issue = [&](int kc, int b) {
+        unsigned char* sA = smem + b * Sh::kStage;
+        unsigned char* sB = sA + 128 * 128;
         for (int e = tid; e < 128 * 8; e += kGThreads) {
             int r = e >> 3, v = e & 7;
-            uint4 val = *reinterpret_cast<const uint4*>(a.A + (size_t)(m0 + r) * a.K + kc + 8 * v);
-            *reinterpret_cast<uint4*>(sA + r * 128 + ((v ^ (r & 7)) << 4)) = val;
+            cp_async16(smem_u32(sA + r * 128 + ((v ^ (r & 7)) << 4)), a.A + (size_t)(m0 + r) * a.K + kc + 8 * v);
         }
         for (int e = tid; e < kN * 8; e += kGThreads) {
             int r = e >> 3, v = e & 7;
-            uint4 val = *reinterpret_cast<const uint4*>(a.B + (size_t)(n0 + r) * a.K + kc + 8 * v);
-            *reinterpret_cast<uint4*>(sB + r * 128 + ((v ^ (r & 7)) << 4)) = val;
+            cp_async16(smem_u32(sB + r * 128 + ((v ^ (r & 7)) << 4)), a.B + (size_t)(n0 + r) * a.K + kc + 8 * v);
+        }
+        cp_async_commit();
+    };
+    uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    bool failed = false;
+    const int nchunks = k1 > k0 ? (k1 - k0 + 63) / 64 : 0;
+    if (nchunks > 0) issue(k0, 0);
+    for (int i = 0; i < nchunks && !failed; ++i) {
+        const int bi = i & 1;
+        if (i + 1 < nchunks) {
+            const int nb = bi ^ 1;
+            if (pending[nb]) {   // the MMAs of chunk i - 1 read stage nb
+                const bool ok = mbar_wait(smem_u32(mbar + nb), phase[nb]);
+                phase[nb] ^= 1u;
+                pending[nb] = false;
+                if (__syncthreads_or(!ok)) { failed = true; break; }
+            }
+            issue(k0 + 64 * (i + 1), nb);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint64_t dA = make_desc(smem_u32(sA)), dB = make_desc(smem_u32(sB));
+            unsigned char* sA = smem + bi * Sh::kStage;
+            uint64_t dA = make_desc(smem_u32(sA)), dB = make_desc(smem_u32(sA + 128 * 128));
             for (int ks = 0; ks < 4; ++ks) {
                 uint64_t off = (uint64_t)(ks * 32) >> 4;   // 16 BF16 along K
-                mma_16<false, kN>(tmem, dA + off, dB + off, (any || ks > 0) ? 1u : 0u);
+                mma_16<false, kN>(tmem, dA + off, dB + off, (i > 0 || ks > 0) ? 1u : 0u);
             }
-            mma_commit(smem_u32(mbar));
+            mma_commit(smem_u32(mbar + bi));
         }
-        const bool ok = mbar_wait(smem_u32(mbar), phase);
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        failed = __syncthreads_or(!ok) != 0;
-        any = true;
+        pending[bi] = true;
     }
+    cp_async_wait<0>();
+    for (int b = 0; b < 2 && !failed; ++b) {   // every MMA of the tile has completed after both
+        if (!pending[b]) continue;
+        const bool ok = mbar_wait(smem_u32(mbar + b), phase[b]);
+        if (__syncthreads_or(!ok)) failed = true;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const bool any = nchunks > 0;
     if (failed && tid == 0) atomicOr(a.status, (unsigned)ST_TIMEOUT);
     if (any && !failed) {
         const int qw = warp & 3, chalf = warp >> 2;
@@ -283,6 +309,188 @@ __global__ void k_take_outputs(const float* __restrict__ P, int B, int n_out, co
 }
 
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+// ---------------------------------------------------------------- fused inference
+// The whole network for 128 rows per tile in one CTA. The features are written
+// straight into a shared-memory activation tile; each layer's MMAs read it, and
+// its bias + ReLU epilogue (run after those MMAs have completed) overwrites it
+// in place with the next layer's BF16 activations, in the MMA's own swizzled
+// layout. The weight K-chunks (a fixed sequence per tile) stream from L2 through
+// a ring of kStages shared-memory stages with cp.async, kStages - 1 chunks
+// ahead of the MMAs and across layer and tile boundaries; the accumulator is in
+// TMEM. Only the inputs and the n_out outputs touch HBM.
+constexpr int kMaxLayers = 9;
+constexpr int kStages = 4;
+constexpr int kActBytes = 128 * 256 * 2;    // 128 rows x 256 BF16, four 16 KB K-chunk tiles
+constexpr int kBChunkBytes = 256 * 128;     // up to 256 weight rows x 64 BF16
+constexpr int kInferSmem = kActBytes + kStages * kBChunkBytes + 1024 + 128;
+
+struct InferArgs {
+    const float* x;
+    int B;
+    float4 lo, inv;
+    float lmax;
+    int n_layers;
+    const bf16* W[kMaxLayers];
+    const float* bias[kMaxLayers];
+    int n_in[kMaxLayers];
+    int n_out[kMaxLayers];
+    int n_used;
+    const float* shift;
+    const float* scale;
+    float* y;
+    unsigned int* status;
+};
+
+__device__ __forceinline__ uint32_t act_off(int r, int k) {   // byte offset in the activation tile
+    return (uint32_t)(k >> 6) * (128 * 128) + sw128(r, k & 63);
+}
+
+__global__ void __launch_bounds__(kGThreads, 1) k_mlp_infer(const __grid_constant__ InferArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* act = smem;
+    unsigned char* ring = smem + kActBytes;
+    uint64_t* mbar = (uint64_t*)(smem + kActBytes + kStages * kBChunkBytes);
+    uint32_t* tmem_slot = (uint32_t*)(mbar + kStages);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int k = 0; k < kStages; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar + k)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    // the per-tile chunk sequence: layer l has n_in[l] / 64 chunks
+    int per_tile = 0;
+    for (int l = 0; l < a.n_layers; ++l) per_tile += a.n_in[l] / 64;
+    const int ntiles = (a.B + 127) / 128;
+    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t total = (int64_t)my_tiles * per_tile;   // chunks this CTA consumes
+    // copy of chunk g (of this CTA's sequence) into its stage
+    auto issue = [&](int64_t g) {
+        if (g < total) {
+            int q = (int)(g % per_tile), l = 0;
+            while (q >= a.n_in[l] / 64) { q -= a.n_in[l] / 64; ++l; }
+            const int K = a.n_in[l], N = a.n_out[l];
+            const bf16* W = a.W[l];
+            unsigned char* st = ring + (int)(g % kStages) * kBChunkBytes;
+            for (int e = tid; e < N * 8; e += kGThreads) {
+                int r = e >> 3, v = e & 7;
+                cp_async16(smem_u32(st + r * 128 + ((v ^ (r & 7)) << 4)), W + (size_t)r * K + q * 64 + 8 * v);
+            }
+        }
+        cp_async_commit();   // one group per chunk, empty past the end, so the group count stays fixed
+    };
+    uint32_t phase_bits = 0u;   // parity to wait for, per stage
+    bool failed = false;
+    // consume the MMA commits of chunks up to c, each exactly once and in order
+    // (a stage's barrier completes once per chunk that used it)
+    int64_t waited = -1;
+    auto wait_chunk = [&](int64_t c) -> bool {
+        while (waited < c) {
+            ++waited;
+            const int sp = (int)(waited % kStages);
+            // at most 2^21 tries of up to 1 us: a wait that never ends gives up within seconds
+            const bool ok = mbar_wait_sleep(smem_u32(mbar + sp), (phase_bits >> sp) & 1u, 1000u, 1u << 21);
+            phase_bits ^= 1u << sp;
+            if (__syncthreads_or(!ok)) return false;
+        }
+        return true;
+    };
+    for (int64_t c = 0; c < kStages - 1; ++c) issue(c);
+    int64_t g = 0;              // next chunk to consume
+    const int qw = warp & 3, chalf = warp >> 2;
+    for (int t = 0; t < my_tiles && !failed; ++t) {
+        const int r0 = (blockIdx.x + t * gridDim.x) * 128;
+        // Fourier features of the tile's rows (the previous tile's MMAs have completed)
+        for (int e = tid; e < 128 * 4 * kOctaves; e += kGThreads) {
+            int r = e / (4 * kOctaves), q = e - r * 4 * kOctaves;
+            int c = q / kOctaves, k = q - c * kOctaves;
+            float s = 0.f, co = 0.f;
+            if (r0 + r < a.B) {
+                float xv = a.x[4 * (r0 + r) + c];
+                float lov = c == 0 ? a.lo.x : (c == 1 ? a.lo.y : (c == 2 ? a.lo.z : a.lo.w));
+                float iv = c == 0 ? a.inv.x : (c == 1 ? a.inv.y : (c == 2 ? a.inv.z : a.inv.w));
+                sincospif(exp2f(a.lmax * (float)k / 15.0f) * ((xv - lov) * iv), &s, &co);
+            }
+            const int f = c * 2 * kOctaves + 2 * k;
+            *reinterpret_cast<__nv_bfloat162*>(act + act_off(r, f)) = __floats2bfloat162_rn(s, co);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int l = 0; l < a.n_layers && !failed; ++l) {
+            const int N = a.n_out[l], nch = a.n_in[l] / 64;
+            for (int kc = 0; kc < nch; ++kc, ++g) {
+                // chunks up to g + kStages - 2 are issued: all but the newest
+                // kStages - 2 groups complete means chunk g has landed
+                cp_async_wait<kStages - 2>();
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                if (tid == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int sg = (int)(g % kStages);
+                    uint64_t dA = make_desc(smem_u32(act + kc * (128 * 128)));
+                    uint64_t dB = make_desc(smem_u32(ring + sg * kBChunkBytes));
+                    for (int ks = 0; ks < 4; ++ks) {
+                        uint64_t off = (uint64_t)(ks * 32) >> 4;
+                        uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                        if (N == 256) mma_16<false, 256>(tmem, dA + off, dB + off, acc);
+                        else mma_16<false, 128>(tmem, dA + off, dB + off, acc);
+                    }
+                    mma_commit(smem_u32(mbar + sg));
+                }
+                // with chunk g's MMAs queued, recycle the stage of chunk g - 1 (its
+                // MMAs precede g's) for chunk g + kStages - 1
+                if (!wait_chunk(g - 1)) { failed = true; break; }
+                issue(g + kStages - 1);
+            }
+            if (failed) break;
+            // every MMA of the layer has completed once its last chunk's commit has
+            if (!wait_chunk(g - 1)) { failed = true; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = 32 * qw + lane;
+            const bool last = l + 1 == a.n_layers;
+            for (int j = 0; j < N / 64; ++j) {
+                const int col0 = (N / 2) * chalf + 32 * j;
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)col0, v);
+                if (!last) {
+                    for (int k = 0; k < 32; k += 8) {
+                        __align__(16) __nv_bfloat162 o[4];
+                        for (int u = 0; u < 4; ++u) {
+                            float x0 = fmaxf(__uint_as_float(v[k + 2 * u]) + a.bias[l][col0 + k + 2 * u], 0.f);
+                            float x1 = fmaxf(__uint_as_float(v[k + 2 * u + 1]) + a.bias[l][col0 + k + 2 * u + 1], 0.f);
+                            o[u] = __floats2bfloat162_rn(x0, x1);
+                        }
+                        *reinterpret_cast<uint4*>(act + act_off(row, col0 + k)) = *reinterpret_cast<uint4*>(o);
+                    }
+                } else if (r0 + row < a.B) {
+                    for (int k = 0; k < 32; ++k) {
+                        const int o = col0 + k;
+                        if (o < a.n_used)
+                            a.y[(size_t)(r0 + row) * a.n_used + o] =
+                                (__uint_as_float(v[k]) + a.bias[l][o]) * a.scale[o] + a.shift[o];
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    cp_async_wait<0>();
+    if (failed && tid == 0) atomicOr(a.status, (unsigned)ST_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+}
 
 template <int kN, int kMode>
 sbr_status gemm_launch(const GemmArgs& a, int splits, cudaStream_t s) {
@@ -483,6 +691,39 @@ sbr_status sync_bf16(sbr_mlp* m, cudaStream_t s) {
     return SBR_OK;
 }
 
+sbr_status infer_fused(const sbr_mlp* m, const float* x, int B, float* y, cudaStream_t s) {
+    const sbr_mlp_config& c = m->cfg;
+    static bool attr = false;
+    if (!attr) {
+        SBR_TRY_CUDA(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kInferSmem));
+        attr = true;
+    }
+    InferArgs a{};
+    a.x = x;
+    a.B = B;
+    a.lo = make_float4(c.x_lo[0], c.x_lo[1], c.x_lo[2], c.x_lo[3]);
+    a.inv = make_float4(1.f / (c.x_hi[0] - c.x_lo[0]), 1.f / (c.x_hi[1] - c.x_lo[1]),
+                        1.f / (c.x_hi[2] - c.x_lo[2]), 1.f / (c.x_hi[3] - c.x_lo[3]));
+    a.lmax = c.feat_log2_max;
+    a.n_layers = (int)m->L.size();
+    for (int l = 0; l < a.n_layers; ++l) {
+        a.W[l] = m->L[l].Wb;
+        a.bias[l] = m->L[l].b;
+        a.n_in[l] = m->L[l].n_in;
+        a.n_out[l] = m->L[l].n_out;
+    }
+    a.n_used = c.n_out;
+    a.shift = m->d_shift;
+    a.scale = m->d_scale;
+    a.y = y;
+    a.status = m->status;
+    const int ntiles = (B + 127) / 128;
+    const int grid = std::min(ntiles, sm_count());
+    ::sbr::note_launch(), k_mlp_infer<<<grid, kGThreads, kInferSmem, s>>>(a);
+    SBR_TRY_CUDA(cudaGetLastError());
+    return SBR_OK;
+}
+
 int64_t n_params(const sbr_mlp* m) {
     int64_t n = 0;
     for (const Layer& ly : m->L) n += (int64_t)ly.n_out * ly.n_in + ly.n_out;
@@ -593,6 +834,14 @@ sbr_status sbr_mlp_train_step(sbr_mlp* m, const float* x, const float* y, int32_
 }
 
 sbr_status sbr_mlp_predict(const sbr_mlp* m, const float* x, int32_t B, float* y, void* stream) {
+    clear_error();
+    SBR_CHECK_ARG(m && x && y, "mlp, x, y");
+    SBR_CHECK_ARG(B >= 1 && B <= m->cfg.max_batch, "1 <= B <= max_batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    return infer_fused(m, x, B, y, s);
+}
+
+sbr_status sbr_mlp_predict_layered(const sbr_mlp* m, const float* x, int32_t B, float* y, void* stream) {
     clear_error();
     SBR_CHECK_ARG(m && x && y, "mlp, x, y");
     SBR_CHECK_ARG(B >= 1 && B <= m->cfg.max_batch, "1 <= B <= max_batch");

@@ -49,11 +49,12 @@ def test_forward_gradients_and_adam_match_reference(sbr, depth, width, B):
     layers = mlp_ref.unpack(p0, width, depth)
     feat = mlp_ref.features(x, LO, HI)
     hs, p = mlp_ref.forward(layers, feat)
-    # forward, in target units
+    # forward, in target units: the fused kernel, and the per-layer GEMMs bit for bit
     got = m.predict(xd).cpu().numpy()
     want = p[:, :n_out] * SCALE + SHIFT
     err = np.abs(got - want).max() / np.abs(want).max()
     assert err < 1e-2, err
+    assert np.array_equal(got, m.predict(xd, layered=True).cpu().numpy())
     # one training step: loss, gradients, Adam update
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     m.train_step(xd, yd, loss)
