@@ -45,6 +45,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 RAY_REC_BYTES = 64      # one queued ray record (origin, direction, L, id, last surface)
 SEQ_BYTES = 4           # surface id appended per reflection
+DIR_BYTES = 24          # launch direction of a ray, double-float
 
 
 def load_peaks():
@@ -251,9 +252,9 @@ def run_gpu(args):
     fc = float(sc["freqs"][0])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
-    def step(dd):
+    def step(dd, df_from=0):
         bvh = sbr.build_bvh(dd["tri"], dd["surface_id"], dd["S"])
-        tr = sbr.trace(bvh, dd["tx"], dd["rx"], N, K, alpha=alpha, timing=True)
+        tr = sbr.trace(bvh, dd["tx"], dd["rx"], N, K, alpha=alpha, timing=True, depth_first_from=df_from)
         pl = sbr.paths(tr, bvh)
         g = sbr.path_gains(pl, dd["mats"], dd["freqs"], dd["gamma"], dd["disp"], dd["pol"])
         pdp, st = sbr.pdp_angles(pl, g, 0, fc, 1e-9, 2048)
@@ -285,17 +286,30 @@ def run_gpu(args):
         stats = out[-1]
         rb += stats["ray_bounces"]
         q = stats["queue"]
-        for bb in range(K + 1):
-            bounce_ms += stats["bounce_ms"][bb]
-            reads = q[bb] * RAY_REC_BYTES if bb > 0 else 0
-            writes = q[bb + 1] * (RAY_REC_BYTES + SEQ_BYTES) if bb < K else 0
-            bounce_bytes += reads + writes
+        bounce_ms += sum(stats["bounce_ms"][:K + 1])
+        # depth first from bounce 0: each ray's launch direction is read once and
+        # each reflection appends its surface id; no ray record goes through memory
+        bounce_bytes += DIR_BYTES * q[0] + SEQ_BYTES * sum(q[1:K + 1])
         del out
     torch.cuda.synchronize()
     clk = clocks.stop()
     t_total = sum(times) / 1e3
     t_total, rb_all = reduce_over_ranks(t_total, float(rb), device=dev)
     value = rb_all / t_total / 1e6
+    # the same step with every bounce breadth first (one launch per bounce over
+    # compacted ray queues), for comparison
+    bf_times, bf_rb = [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = step(d, df_from=K + 1)
+        e1.record()
+        e1.synchronize()
+        bf_times.append(e0.elapsed_time(e1))
+        bf_rb += out[-1]["ray_bounces"]
+        del out
+    bf_value = bf_rb / (sum(bf_times) / 1e3) / 1e6
 
     # e2e: the same step through the public API from pinned host buffers, with the
     # inputs copied in and the path list, gains, PDP and statistics copied out
@@ -359,12 +373,12 @@ def run_gpu(args):
 
     achieved = bounce_bytes / (bounce_ms / 1e3) / 1e9
     hbm = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
-    roof = {"kernel": "k_trace_bounce", "bound": "hbm", "achieved": achieved, "peak": hbm,
+    roof = {"kernel": "k_trace_df", "bound": "hbm", "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
             "peak_source": peak_src,
-            "algorithmic_bytes": "64 B ray record read (bounces >= 1) + 68 B record and surface "
-                                 "id written per surviving ray, per launch",
-            "avg_launch_ms": bounce_ms / (args.steps * (K + 1)),
+            "schedule": "depth first from bounce 0 (one launch per trace)",
+            "algorithmic_bytes": "24 B launch direction per ray + 4 B surface id per reflection, per launch",
+            "avg_launch_ms": bounce_ms / args.steps,
             "kernel_share_of_step": bounce_ms / sum(times), "l2": l2}
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -384,6 +398,7 @@ def run_gpu(args):
         "gpu_launches": None if n_launch is None else n_launch * args.steps,
         "launches_per_step": n_launch,
         "clocks": clk,
+        "breadth_first": {"value": bf_value, "unit": METRIC, "ms_per_step": statistics.mean(bf_times)},
         "synthesis": synth,
         "batched": batched,
         "surrogate": surrogate,

@@ -137,6 +137,13 @@ sbr_status sbr_bvh_query(const sbr_bvh* bvh, sbr_bvh_info* out);
  * rx_xyz: dev double [n_rx*3] (copied; may be freed after the stream runs).
  * alpha: 0 = computed as in sbr_launch_dirs. table_log2: 0 = automatic.
  * max_bounces in [0, 8]; n_rx in [0, 2^20]; 10 N^2 + 2 < 2^32.
+ * depth_first_from: bounces before it run breadth first (one launch per
+ * bounce over a compacted queue of live rays, the "width first" order of
+ * Sec. I); from it on, each thread carries its ray through every remaining
+ * bounce and then takes the next ray (one launch, no queue). 0 (the
+ * default) traces everything depth first; max_bounces + 1 or more traces
+ * everything breadth first. The results are the same; only the schedule
+ * differs.
  */
 typedef struct {
     double tx[3];
@@ -147,7 +154,7 @@ typedef struct {
     int32_t table_log2;
     double alpha;
     uint32_t flags;
-    int32_t reserved;
+    int32_t depth_first_from;
 } sbr_trace_params;
 
 /* sbr_trace_params.flags */

@@ -158,8 +158,10 @@ class TraceResult:
 
 
 def trace(bvh: BVH, tx, rx: torch.Tensor, N: int, K: int, alpha: float = 0.0, table_log2: int = 0,
-          timing: bool = False, count_visits: bool = False, stream=None) -> TraceResult:
-    """Shoot and bounce. tx: 3 floats; rx: float64 [n_rx, 3] CUDA."""
+          timing: bool = False, count_visits: bool = False, depth_first_from: int = 0,
+          stream=None) -> TraceResult:
+    """Shoot and bounce. tx: 3 floats; rx: float64 [n_rx, 3] CUDA. Bounces from
+    depth_first_from on are traced depth first (K + 1: all breadth first)."""
     p = _lib.TraceParams()
     for k in range(3):
         p.tx[k] = float(tx[k])
@@ -173,6 +175,7 @@ def trace(bvh: BVH, tx, rx: torch.Tensor, N: int, K: int, alpha: float = 0.0, ta
     p.table_log2 = int(table_log2)
     p.alpha = float(alpha)
     p.flags = (_lib.TRACE_TIMING if timing else 0) | (_lib.TRACE_COUNT_VISITS if count_visits else 0)
+    p.depth_first_from = int(depth_first_from)
     h = C.c_void_p()
     _check(_L().sbr_trace(bvh.handle, C.byref(p), C.byref(h), _stream(stream)))
     return TraceResult(h, p)

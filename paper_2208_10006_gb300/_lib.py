@@ -31,7 +31,7 @@ EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_count", "sbr_launch_dirs
 class TraceParams(C.Structure):
     _fields_ = [("tx", C.c_double * 3), ("rx_xyz", C.c_void_p), ("n_rx", C.c_int32),
                 ("subdiv_N", C.c_int32), ("max_bounces", C.c_int32), ("table_log2", C.c_int32),
-                ("alpha", C.c_double), ("flags", C.c_uint32), ("reserved", C.c_int32)]
+                ("alpha", C.c_double), ("flags", C.c_uint32), ("depth_first_from", C.c_int32)]
 
 
 class TraceCounters(C.Structure):

@@ -210,6 +210,7 @@ sbr_status sbr_trace(const sbr_bvh* b, const sbr_trace_params* p, sbr_trace_resu
     SBR_CHECK_ARG(finite3(p->tx), "finite tx");
     SBR_CHECK_ARG(std::isfinite(p->alpha) && p->alpha >= 0.0, "alpha >= 0");
     SBR_CHECK_ARG(p->table_log2 == 0 || (p->table_log2 >= 4 && p->table_log2 <= 28), "table_log2");
+    SBR_CHECK_ARG(p->depth_first_from >= 0, "depth_first_from >= 0");
     int64_t R = 10 * (int64_t)p->subdiv_N * p->subdiv_N + 2;
     SBR_CHECK_ARG(R < ((int64_t)1 << 32), "10 N^2 + 2 < 2^32");
     cudaStream_t s = (cudaStream_t)stream;
@@ -220,6 +221,7 @@ sbr_status sbr_trace(const sbr_bvh* b, const sbr_trace_params* p, sbr_trace_resu
     tr->params = *p;
     tr->R = R;
     tr->n_rx = p->n_rx;
+    tr->df_from = p->depth_first_from;
     if (p->table_log2) {
         tr->table_log2 = p->table_log2;
     } else {

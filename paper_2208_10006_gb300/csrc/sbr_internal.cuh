@@ -157,6 +157,7 @@ struct sbr_trace_result {
     double* rx = nullptr;                   // [n_rx*3] own copy
     double* d_alpha = nullptr;              // [1]
     int32_t table_log2 = 0;
+    int32_t df_from = 0;                    // first bounce traced depth-first (K + 1: none)
     uint32_t* ht_state = nullptr;           // [cap]
     uint32_t* ht_key = nullptr;             // [cap * kKeyWords]
     unsigned long long* ht_val = nullptr;   // [cap]

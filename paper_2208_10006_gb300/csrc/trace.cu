@@ -411,7 +411,7 @@ __device__ __forceinline__ bool rx_accept(const df3& o, const df3& d, df L, df t
 // conservative); each is then tested exactly in double-float:
 //   t* = (Rx - o).d in [0, t_hit],  |o + t* d - Rx|^2 <= alpha^2 (L + t*)^2 / 3.
 template <bool kCount>
-__device__ void receive(const TraceArgs& a, const df3& o, const df3& d, df L, df t_hit, bool hit,
+__device__ void receive(const TraceArgs& a, int bounce, const df3& o, const df3& d, df L, df t_hit, bool hit,
                         const Ray32& r, uint32_t ray, int* stack, unsigned* rx_visits) {
     if (a.n_rx <= 0) return;
     const float4 al = __ldg(a.alpha_df);
@@ -451,9 +451,9 @@ __device__ void receive(const TraceArgs& a, const df3& o, const df3& d, df L, df
                 if (rx_accept(o, d, L, t_hit, hit, R, a2o3, dist)) {
                     uint32_t key[kKeyWords];
                     key[0] = (uint32_t)rx_id;
-                    key[1] = (uint32_t)a.bounce;
+                    key[1] = (uint32_t)bounce;
                     for (int k = 0; k < kKmax; ++k)
-                        key[2 + k] = k < a.bounce ? (uint32_t)a.seq[(int64_t)k * a.R + ray] : 0xffffffffu;
+                        key[2 + k] = k < bounce ? (uint32_t)a.seq[(int64_t)k * a.R + ray] : 0xffffffffu;
                     unsigned long long val = ((unsigned long long)__float_as_uint(dist) << 32) | ray;
                     ht_insert(a, key, val);
                     atomicAdd(&a.cnt->candidates, 1ull);
@@ -572,7 +572,7 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
                 d3 d64 = mk3(df_to_double(d.x), df_to_double(d.y), df_to_double(d.z));
                 edge += min_bary64(a.tris, j, o64, d64) <= 1e-6 ? 1u : 0u;
             }
-            receive<kCount>(a, o, d, L, t, j >= 0, r, ray, stack, &rx_visits);
+            receive<kCount>(a, a.bounce, o, d, L, t, j >= 0, r, ray, stack, &rx_visits);
             if (j >= 0 && a.bounce < a.K) {
                 df c;
                 df3 n = ld_plane_n(a.plane, j, c);
@@ -622,6 +622,116 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
                 q4[2] = make_float4(out.dh[2], out.dl[0], out.dl[1], out.dl[2]);
                 q4[3] = make_float4(out.Lh, out.Ll, __uint_as_float(out.ray), __int_as_float(out.prev));
             }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- depth-first tail
+// From bounce a.bounce on, each lane keeps its ray's state in registers and
+// traces it through every remaining bounce; a lane whose ray has ended takes the
+// next ray of the input (one warp-aggregated atomic per refill), so no lane
+// idles while the pool lasts and the tail needs neither queues nor launches
+// per bounce. The per-segment step is the breadth-first kernel's; survivors
+// are still counted per bounce (rays entering bounce b in queue[b]).
+template <bool kCount>
+__global__ void __launch_bounds__(kTraceThreads, 8)
+k_trace_df(const __grid_constant__ TraceArgs a) {
+    int stack[kStack];
+    unsigned visits = 0, tests = 0, rx_visits = 0, edge = 0;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long n_in = a.bounce == 0 ? (unsigned long long)a.R : *a.n_in;
+    df3 o{}, d{};
+    df L = df_make(0.f, 0.f);
+    uint32_t ray = 0;
+    int prev = -1, bounce = 0;
+    bool has = false, exhausted = false;
+    for (;;) {
+        const unsigned need = __ballot_sync(FULL, !has);
+        if (need && !exhausted) {
+            const int leader = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(need));
+            base = __shfl_sync(FULL, base, leader);
+            if (base + __popc(need) >= n_in) exhausted = true;
+            if (!has) {
+                const unsigned long long i = base + __popc(need & ((1u << lane) - 1u));
+                if (i < n_in) {
+                    if (a.bounce == 0) {
+                        ray = (uint32_t)i;
+                        o = df3{df_make(a.tx_h[0], a.tx_l[0]), df_make(a.tx_h[1], a.tx_l[1]),
+                                df_make(a.tx_h[2], a.tx_l[2])};
+                        float4 da = __ldg(a.dir_a + i);
+                        float2 db = __ldg(a.dir_b + i);
+                        d = df3{df_make(da.x, da.w), df_make(da.y, db.x), df_make(da.z, db.y)};
+                        L = df_make(0.f, 0.f);
+                        prev = -1;
+                    } else {
+                        const float4* q4 = reinterpret_cast<const float4*>(a.qin + i);
+                        float4 w0 = q4[0], w1 = q4[1], w2 = q4[2], w3 = q4[3];
+                        o = df3{df_make(w0.x, w0.w), df_make(w0.y, w1.x), df_make(w0.z, w1.y)};
+                        d = df3{df_make(w1.z, w2.y), df_make(w1.w, w2.z), df_make(w2.x, w2.w)};
+                        L = df_make(w3.x, w3.y);
+                        ray = __float_as_uint(w3.z);
+                        prev = __float_as_int(w3.w);
+                    }
+                    bounce = a.bounce;
+                    has = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, has)) break;
+        int entered = -1;   // bounce this lane's ray enters after this segment
+        if (has) {
+            Ray32 r = make_ray32(df3_hi(o), df3_hi(d));
+            int32_t j = -1;
+            df t = df_make(INFINITY, 0.f);
+            if (a.T > 0) {
+                Trav tv;
+                j = traverse32<kCount>(a, r, prev, tv, stack, &visits, &tests);
+                j = settle_hit(a, o, d, prev, tv, j, stack, t);
+            }
+            if (kCount && j >= 0) {
+                d3 o64 = mk3(df_to_double(o.x), df_to_double(o.y), df_to_double(o.z));
+                d3 d64 = mk3(df_to_double(d.x), df_to_double(d.y), df_to_double(d.z));
+                edge += min_bary64(a.tris, j, o64, d64) <= 1e-6 ? 1u : 0u;
+            }
+            receive<kCount>(a, bounce, o, d, L, t, j >= 0, r, ray, stack, &rx_visits);
+            if (j >= 0 && bounce < a.K) {
+                df c;
+                df3 n = ld_plane_n(a.plane, j, c);
+                int32_t surf = __float_as_int(__ldg(a.tris + 3 * j).w);
+                df3 o2 = df3_add(o, df3_scale(d, t));
+                df dn = df3_dot(d, n);
+                d = df3_sub(d, df3_scale(n, df_make(2.f * dn.hi, 2.f * dn.lo)));
+                o = o2;
+                L = df_add(L, t);
+                a.seq[(int64_t)bounce * a.R + ray] = surf;
+                prev = surf;
+                bounce += 1;
+                entered = bounce;
+            } else {
+                has = false;
+            }
+        }
+        // rays entering bounce b are counted in queue[b]: one atomic per distinct b in the warp
+        const unsigned grp = __match_any_sync(FULL, entered);
+        if (entered >= 0 && lane == __ffs(grp) - 1)
+            atomicAdd(&a.cnt->queue[entered], (unsigned long long)__popc(grp));
+    }
+    if (kCount) {
+        unsigned long long v = visits, w = tests, x = rx_visits, e = edge;
+        for (int s = 16; s; s >>= 1) {
+            v += __shfl_xor_sync(FULL, v, s);
+            w += __shfl_xor_sync(FULL, w, s);
+            x += __shfl_xor_sync(FULL, x, s);
+            e += __shfl_xor_sync(FULL, e, s);
+        }
+        if (lane == 0) {
+            atomicAdd(&a.cnt->node_visits, v);
+            atomicAdd(&a.cnt->tri_tests, w);
+            atomicAdd(&a.cnt->rx_visits, x);
+            if (e) atomicAdd(&a.cnt->near_edge_hits, e);
         }
     }
 }
@@ -930,6 +1040,9 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
         for (int k = 0; k <= K + 1; ++k) SBR_TRY_CUDA(cudaEventCreate(&tr->ev[k]));
         SBR_TRY_CUDA(cudaEventRecord(tr->ev[0], s));
     }
+    // breadth-first bounces (one launch each over a compacted queue) up to
+    // df_from, then one depth-first launch for the rest
+    const int df_from = std::min(K + 1, tr->df_from);
     for (int bnc = 0; bnc <= K; ++bnc) {
         a.bounce = bnc;
         a.qin = (bnc & 1) ? q0 : q1;
@@ -937,6 +1050,16 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
         a.n_in = &tr->cnt->queue[bnc];
         a.n_out = &tr->cnt->queue[bnc + 1];
         a.work = &tr->cnt->work[bnc];
+        if (bnc >= df_from) {
+            if (count)
+                ::sbr::note_launch(), k_trace_df<true><<<grid, kTraceThreads, 0, s>>>(a);
+            else
+                ::sbr::note_launch(), k_trace_df<false><<<grid, kTraceThreads, 0, s>>>(a);
+            SBR_TRY_CUDA(cudaGetLastError());
+            if (timing)
+                for (int k = bnc; k <= K; ++k) SBR_TRY_CUDA(cudaEventRecord(tr->ev[k + 1], s));
+            break;
+        }
         if (count)
             ::sbr::note_launch(), k_trace_bounce<true><<<grid, kTraceThreads, 0, s>>>(a);
         else

@@ -204,6 +204,25 @@ def test_bvh_shape(sbr):
         assert 1 <= info["depth"] <= 64
 
 
+@pytest.mark.parametrize("name", ["config1_N37_K3", "shoebox_K5", "urban_small"])
+def test_schedules_give_identical_paths(sbr, name):
+    # breadth first, depth first from a middle bounce and depth first throughout:
+    # the same segments are traced, so the path lists agree exactly
+    sc = SCENES[name]()
+    d = sbr.scene_to_device(sc)
+    bvh = sbr.build_bvh(d["tri"], d["surface_id"], d["S"])
+    outs = []
+    for df in (sc["K"] + 1, 2, 0):
+        tr = sbr.trace(bvh, d["tx"], d["rx"], sc["N"], sc["K"], depth_first_from=df)
+        st = tr.stats()
+        ex = to_numpy(sbr.paths(tr, bvh).export())
+        outs.append((st["ray_bounces"], st["candidates"], st["keys"], st["queue"], ex))
+    for o in outs[1:]:
+        assert o[:4] == outs[0][:4]
+        for k in ("rx", "nb", "seq", "face", "L", "pts", "ray", "dist"):
+            assert np.array_equal(o[4][k], outs[0][4][k]), k
+
+
 @pytest.mark.parametrize("N", [20, 33])
 def test_near_edge_hits_are_counted(sbr, N):
     # rays with d_x == 0 that go up hit the ceiling on its shared edge; the
