@@ -294,7 +294,7 @@ sbr_status sbr_trace_stats(const sbr_trace_result* tr, sbr_trace_counters* out) 
 void sbr_trace_free(sbr_trace_result* tr) {
     if (!tr) return;
     cudaStream_t s = tr->stream;
-    dfree(tr->rx, s); dfree(tr->d_alpha, s); dfree(tr->ht_state, s); dfree(tr->ht_key, s);
+    dfree(tr->seqf, s); dfree(tr->rx, s); dfree(tr->d_alpha, s); dfree(tr->ht_state, s); dfree(tr->ht_key, s);
     dfree(tr->ht_val, s); dfree(tr->cnt, s);
     for (auto& e : tr->ev)
         if (e) cudaEventDestroy(e);

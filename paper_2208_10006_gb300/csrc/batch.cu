@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch_paths(const __grid_constant
         const uint32_t* key = a.ht_key + (size_t)slot * kKeyWords;
         int32_t seq[kKmax];
         for (int k = 0; k < kKmax; ++k) seq[k] = (int32_t)key[2 + k];
-        bool ok = refine_key(lane, (int)key[1], seq, a.ht_val[slot], sc, Tx, Rx, a.raw, rb + r);
+        bool ok = refine_key<false>(lane, (int)key[1], seq, a.ht_val[slot], sc, Tx, Rx, a.raw, rb + r);
         if (lane == 0) valid[r] = ok ? 1 : 0;
     }
     __syncthreads();

@@ -35,15 +35,26 @@ __global__ void k_collect(const uint32_t* __restrict__ state, size_t cap, uint32
     if (ready) idx[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)s;
 }
 
-// sortable form of key word w of slot idx[perm[i]]: surface ids shifted by one
-// so that the -1 padding sorts first
-__global__ void k_key_word(const uint32_t* __restrict__ key, const uint32_t* __restrict__ idx,
-                           const uint32_t* __restrict__ perm, int64_t n, int w,
+// one 32-bit sort word of slot idx[perm[i]]: the key words w[0..nf) placed at
+// bit shifts sh[0..nf), surface ids shifted by one so that the -1 padding sorts
+// first (the fields of one word are consecutive in significance)
+struct PackWord {
+    int nf;
+    int w[kKeyWords];
+    int sh[kKeyWords];
+};
+__global__ void k_key_pack(const uint32_t* __restrict__ key, const uint32_t* __restrict__ idx,
+                           const uint32_t* __restrict__ perm, int64_t n, const __grid_constant__ PackWord pw,
                            uint32_t* __restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    uint32_t v = key[(size_t)idx[perm[i]] * kKeyWords + w];
-    out[i] = w >= 2 ? v + 1u : v;
+    const uint32_t* k = key + (size_t)idx[perm[i]] * kKeyWords;
+    uint32_t v = 0;
+    for (int f = 0; f < pw.nf; ++f) {
+        uint32_t x = k[pw.w[f]];
+        v |= (pw.w[f] >= 2 ? x + 1u : x) << pw.sh[f];
+    }
+    out[i] = v;
 }
 
 __global__ void k_iota(uint32_t* p, int64_t n) {
@@ -64,6 +75,8 @@ struct RefineArgs {
     int32_t S;
     double tx[3];
     const double* rx;
+    const int32_t* seqf;   // [K][R] faces hit by each ray (refinement hints), or null
+    int64_t R;
     // raw outputs, key order
     uint32_t* valid;
     int32_t* rx_o;
@@ -93,8 +106,36 @@ __global__ void k_refine(const __grid_constant__ RefineArgs a) {
     for (int k = 0; k < kKmax; ++k) seq[k] = (int32_t)key[2 + k];
     const RefineScene sc{a.tri, a.nrm, a.s_off, a.s_tri, a.S};
     const RefineOut o{a.nb_o, a.surf_o, a.face_o, a.pts_o, a.L_o, a.aod_o, a.aoa_o, a.ray_o, a.dist_o, a.jones_o};
-    bool ok = refine_key(lane, m, seq, v, sc, mk3(a.tx[0], a.tx[1], a.tx[2]), ld3(a.rx + 3 * rx_id), o, i);
+    bool ok = refine_key<false>(lane, m, seq, v, sc, mk3(a.tx[0], a.tx[1], a.tx[2]), ld3(a.rx + 3 * rx_id), o, i);
     if (lane != 0) return;
+    a.valid[i] = ok ? 1u : 0u;
+    if (ok) a.rx_o[i] = rx_id;
+}
+
+// one thread per key, with the faces the kept ray hit as hints (the trace's
+// per-bounce face record): the same results as k_refine
+__global__ void k_refine_solo(const __grid_constant__ RefineArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool have = i < a.n;   // keyless lanes still take part in the warp's scans
+    int rx_id = 0, m = -1;
+    unsigned long long v = 0;
+    int32_t seq[kKmax];
+    for (int k = 0; k < kKmax; ++k) seq[k] = -1;
+    if (have) {
+        uint32_t slot = a.idx[a.perm[i]];
+        const uint32_t* key = a.key + (size_t)slot * kKeyWords;
+        v = a.val[slot];
+        rx_id = (int)key[0];
+        m = (int)key[1];
+        for (int k = 0; k < kKmax; ++k) seq[k] = (int32_t)key[2 + k];
+    }
+    const RefineScene sc{a.tri, a.nrm, a.s_off, a.s_tri, a.S};
+    const RefineOut o{a.nb_o, a.surf_o, a.face_o, a.pts_o, a.L_o, a.aod_o, a.aoa_o, a.ray_o, a.dist_o, a.jones_o};
+    const int32_t* hint = a.seqf + (uint32_t)(v & 0xffffffffull);
+    const d3 Rx = have ? ld3(a.rx + 3 * rx_id) : mk3(0, 0, 0);
+    bool ok = refine_key<true>(lane, m, seq, v, sc, mk3(a.tx[0], a.tx[1], a.tx[2]), Rx, o, have ? i : 0, hint, a.R);
+    if (!have) return;
     a.valid[i] = ok ? 1u : 0u;
     if (ok) a.rx_o[i] = rx_id;
 }
@@ -169,14 +210,27 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     SBR_TRY(dalloc_n(&perm, std::max<int64_t>(n, 1), s));
     SBR_TRY(dalloc_n(&word, std::max<int64_t>(n, 1), s));
     ::sbr::note_launch(), k_iota<<<nblk(n), kThreads, 0, s>>>(perm, n);
-    std::vector<std::pair<int, int>> words;  // (word index, bits)
-    for (int k = K - 1; k >= 0; --k) words.push_back({2 + k, bits_for((int64_t)b->S)});
-    words.push_back({1, bits_for(K)});
-    words.push_back({0, bits_for(std::max(1, tr->n_rx - 1))});
-    for (auto& w : words) {
-        ::sbr::note_launch(), k_key_word<<<nblk(n), kThreads, 0, s>>>(tr->ht_key, idx, perm, n, w.first, word);
+    // key fields from the least significant (the last surface) to the most
+    // (the receiver), packed greedily into 32-bit sort words; a stable LSD pass
+    // per word, least significant word first, gives the lexicographic order
+    std::vector<std::pair<int, int>> fields;  // (key word, bits)
+    for (int k = K - 1; k >= 0; --k) fields.push_back({2 + k, bits_for((int64_t)b->S)});
+    fields.push_back({1, bits_for(K)});
+    fields.push_back({0, bits_for(std::max(1, tr->n_rx - 1))});
+    size_t f0 = 0;
+    while (f0 < fields.size()) {
+        PackWord pw{};
+        int bits = 0;
+        while (f0 < fields.size() && bits + fields[f0].second <= 32) {
+            pw.w[pw.nf] = fields[f0].first;
+            pw.sh[pw.nf] = bits;
+            bits += fields[f0].second;
+            ++pw.nf;
+            ++f0;
+        }
+        ::sbr::note_launch(), k_key_pack<<<nblk(n), kThreads, 0, s>>>(tr->ht_key, idx, perm, n, pw, word);
         SBR_TRY_CUDA(cudaGetLastError());
-        SBR_TRY(radix_sort_pairs(word, perm, n, w.second, s));
+        SBR_TRY(radix_sort_pairs(word, perm, n, bits, s));
     }
     // refine into raw (key-order) buffers
     RefineArgs a{};
@@ -192,6 +246,8 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     a.S = b->S;
     for (int k = 0; k < 3; ++k) a.tx[k] = tr->params.tx[k];
     a.rx = tr->rx;
+    a.seqf = tr->seqf;
+    a.R = tr->R;
     int64_t nn = std::max<int64_t>(n, 1);
     uint32_t* valid;
     uint32_t* pos;
@@ -210,7 +266,11 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     SBR_TRY(dalloc_n(&a.jones_o, nn * kJones, s));
     a.valid = valid;
     if (n > 0) {
-        ::sbr::note_launch(), k_refine<<<nblk(32 * n), kThreads, 0, s>>>(a);
+        if (a.seqf)
+            // one warp per block: the keys spread over every SM (latency-bound FP64 chains)
+            ::sbr::note_launch(), k_refine_solo<<<(unsigned)((n + 31) / 32), 32, 0, s>>>(a);
+        else
+            ::sbr::note_launch(), k_refine<<<nblk(32 * n), kThreads, 0, s>>>(a);
         SBR_TRY_CUDA(cudaGetLastError());
         SBR_TRY_CUDA(cudaMemcpyAsync(pos, valid, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
     }

@@ -25,6 +25,19 @@ __device__ __forceinline__ bool point_in_tri(const float* v, d3 p, double tol) {
     return l0 >= -tol && l1 >= -tol && l2 >= -tol;
 }
 
+// smallest FP64 barycentric of p in the face (the containment margin)
+__device__ __forceinline__ double bary_margin(const float* v, d3 p) {
+    d3 a = mk3(v[0], v[1], v[2]), b = mk3(v[3], v[4], v[5]), c = mk3(v[6], v[7], v[8]);
+    d3 e1 = b - a, e2 = c - a, w = p - a;
+    double d00 = dot(e1, e1), d01 = dot(e1, e2), d11 = dot(e2, e2);
+    double d20 = dot(w, e1), d21 = dot(w, e2);
+    double den = d00 * d11 - d01 * d01;
+    if (den == 0.0) return -1.0;
+    double l1 = (d11 * d20 - d01 * d21) / den;
+    double l2 = (d00 * d21 - d01 * d20) / den;
+    return fmin(fmin(l1, l2), 1.0 - l1 - l2);
+}
+
 // FP32 screen of the same barycentric test: +1 clearly inside, -1 clearly
 // outside, 0 near an edge (then the FP64 test decides). The margin is 1e-3 or,
 // for small or thin faces far from the origin, a bound on the FP32 error of
@@ -101,15 +114,26 @@ struct RefineOut {
     double* jones_o;
 };
 
-// One warp per key: every lane runs the (cheap) image construction, the lanes
-// split the containment tests over the surface's faces. m reflections with
-// surfaces seq[0..m), kept (dist, ray) value v. Returns the key's validity on
-// every lane.
+// One key, by one warp (kSolo false: lane 0 builds the images and points,
+// which the lanes share for a scan of the surface's faces 32 at a time) or by
+// one thread (kSolo true: 32 keys per warp; a reflection its hint does not
+// settle gets the whole warp's scan; must be called by all 32 lanes). m reflections with
+// surfaces seq[0..m), kept (dist, ray) value v. hint (or null): the faces the
+// kept ray hit, hint[k * hint_stride] for reflection k; a face of the surface
+// that contains the point by a barycentric margin of at least 1e-6 is its only
+// container (the faces of a surface do not overlap), so it is taken without
+// scanning; otherwise the lowest-id container is searched. Both arrangements
+// give the same result. Returns the key's validity (on every lane).
+template <bool kSolo>
 __device__ bool refine_key(int lane, int m, const int32_t* seq, unsigned long long v, const RefineScene& sc,
-                           d3 Tx, d3 Rx, const RefineOut& o, int64_t i) {
+                           d3 Tx, d3 Rx, const RefineOut& o, int64_t i, const int32_t* hint = nullptr,
+                           int64_t hint_stride = 0) {
     d3 nn[kKmax + 1], img[kKmax + 1], P[kKmax + 2];
     double cc[kKmax + 1];
     bool ok = m >= 0 && m <= kKmax;
+    // the image construction and back-trace (FP64, scarce on this GPU) run on
+    // lane 0 alone; the points are then broadcast for the containment scan
+    if (kSolo || lane == 0) {
     img[0] = Tx;
     for (int k = 1; k <= m && ok; ++k) {
         int s = seq[k - 1];
@@ -129,30 +153,97 @@ __device__ bool refine_key(int lane, int m, const int32_t* seq, unsigned long lo
         P[k] = img[k] + dv * u;
         target = P[k];
     }
-    int32_t face[kKmax];
-    for (int k = 0; k < kKmax; ++k) face[k] = -1;
-    for (int k = 1; k <= m && ok; ++k) {
-        int s = seq[k - 1];
-        int32_t found = -1;
-        const int32_t qa = sc.s_off[s], qb = sc.s_off[s + 1];
-        for (int32_t base = qa; base < qb; base += 32) {
-            int32_t q = base + lane;
-            bool in = false;
-            if (q < qb) {
-                const float* v = sc.tri + 9 * (int64_t)sc.s_tri[q];
-                int sc = screen_in_tri(v, make_float3((float)P[k].x, (float)P[k].y, (float)P[k].z));
-                in = sc > 0 || (sc == 0 && point_in_tri(v, P[k], 1e-9));
-            }
-            unsigned m32 = __ballot_sync(0xffffffffu, in);
-            if (m32) {  // faces are listed in ascending id: the lowest lane is the lowest id
-                found = sc.s_tri[base + __ffs(m32) - 1];
-                break;
+    }
+    if (!kSolo) {
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (ok) {
+            for (int k = 1; k <= m; ++k) {
+                P[k].x = __shfl_sync(0xffffffffu, P[k].x, 0);
+                P[k].y = __shfl_sync(0xffffffffu, P[k].y, 0);
+                P[k].z = __shfl_sync(0xffffffffu, P[k].z, 0);
             }
         }
-        if (found < 0) { ok = false; break; }
-        face[k - 1] = found;
     }
-    if (lane != 0 || !ok) return ok;
+    int32_t face[kKmax];
+    for (int k = 0; k < kKmax; ++k) face[k] = -1;
+    if (kSolo) {
+        // every lane holds its own key; lanes whose hint does not settle a
+        // reflection are served in turn by the whole warp's 32-wide scan (all
+        // 32 lanes run this loop, keyless lanes with ok false)
+        for (int k = 1; k <= kKmax; ++k) {
+            const bool act = ok && k <= m;
+            const int s = act ? seq[k - 1] : 0;
+            int32_t found = -1;
+            bool need = false;
+            if (act) {
+                const int32_t h = hint ? hint[(int64_t)(k - 1) * hint_stride] : -1;
+                if (h >= 0 && bary_margin(sc.tri + 9 * (int64_t)h, P[k]) >= 1e-6) found = h;
+                else need = true;
+            }
+            unsigned nm = __ballot_sync(0xffffffffu, need);
+            const double px = act ? P[k].x : 0.0, py = act ? P[k].y : 0.0, pz = act ? P[k].z : 0.0;
+            while (nm) {
+                const int L = __ffs(nm) - 1;
+                nm &= nm - 1;
+                const d3 PL = mk3(__shfl_sync(0xffffffffu, px, L), __shfl_sync(0xffffffffu, py, L),
+                                  __shfl_sync(0xffffffffu, pz, L));
+                const int sL = __shfl_sync(0xffffffffu, s, L);
+                const float3 pf = make_float3((float)PL.x, (float)PL.y, (float)PL.z);
+                const int32_t qa = sc.s_off[sL], qb = sc.s_off[sL + 1];
+                int32_t fL = -1;
+                for (int32_t base = qa; base < qb; base += 32) {
+                    int32_t q = base + lane;
+                    bool in = false;
+                    if (q < qb) {
+                        const float* v = sc.tri + 9 * (int64_t)sc.s_tri[q];
+                        int scr = screen_in_tri(v, pf);
+                        in = scr > 0 || (scr == 0 && point_in_tri(v, PL, 1e-9));
+                    }
+                    unsigned m32 = __ballot_sync(0xffffffffu, in);
+                    if (m32) {  // faces in ascending id: the lowest lane is the lowest id
+                        fL = sc.s_tri[base + __ffs(m32) - 1];
+                        break;
+                    }
+                }
+                if (lane == L) found = fL;
+            }
+            if (act) {
+                if (found < 0) ok = false;
+                else face[k - 1] = found;
+            }
+        }
+    } else {
+        for (int k = 1; k <= m && ok; ++k) {
+            int s = seq[k - 1];
+            int32_t found = -1;
+            if (hint) {
+                const int32_t h = hint[(int64_t)(k - 1) * hint_stride];
+                if (h >= 0 && bary_margin(sc.tri + 9 * (int64_t)h, P[k]) >= 1e-6) {
+                    face[k - 1] = h;
+                    continue;
+                }
+            }
+            const int32_t qa = sc.s_off[s], qb = sc.s_off[s + 1];
+            const float3 pf = make_float3((float)P[k].x, (float)P[k].y, (float)P[k].z);
+            for (int32_t base = qa; base < qb; base += 32) {
+                int32_t q = base + lane;
+                bool in = false;
+                if (q < qb) {
+                    const float* v = sc.tri + 9 * (int64_t)sc.s_tri[q];
+                    int scr = screen_in_tri(v, pf);
+                    in = scr > 0 || (scr == 0 && point_in_tri(v, P[k], 1e-9));
+                }
+                unsigned m32 = __ballot_sync(0xffffffffu, in);
+                if (m32) {  // faces are listed in ascending id: the lowest lane is the lowest id
+                    found = sc.s_tri[base + __ffs(m32) - 1];
+                    break;
+                }
+            }
+            if (found < 0) { ok = false; break; }
+            face[k - 1] = found;
+        }
+    }
+    if ((!kSolo && lane != 0) || !ok) return ok;
     o.nb_o[i] = m;
     for (int k = 0; k < kKmax; ++k) {
         o.surf_o[i * kKmax + k] = k < m ? seq[k] : -1;

@@ -158,6 +158,7 @@ struct sbr_trace_result {
     double* d_alpha = nullptr;              // [1]
     int32_t table_log2 = 0;
     int32_t df_from = 0;                    // first bounce traced depth-first (K + 1: none)
+    int32_t* seqf = nullptr;                // [K][R] face hit by each ray at each bounce
     uint32_t* ht_state = nullptr;           // [cap]
     uint32_t* ht_key = nullptr;             // [cap * kKeyWords]
     unsigned long long* ht_val = nullptr;   // [cap]

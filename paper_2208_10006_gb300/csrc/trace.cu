@@ -72,6 +72,7 @@ struct TraceArgs {
     unsigned long long* n_out;
     unsigned long long* work;
     int32_t* seq;
+    int32_t* seqf;           // [K][R] face hit at each bounce (refinement hints)
     uint32_t* ht_state;
     uint32_t* ht_key;
     unsigned long long* ht_val;
@@ -590,6 +591,7 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
                 out.ray = ray;
                 out.prev = surf;
                 a.seq[(int64_t)a.bounce * a.R + ray] = surf;
+                a.seqf[(int64_t)a.bounce * a.R + ray] = __float_as_int(__ldg(a.tris + 3 * j + 1).w);
                 survive = true;
             }
         }
@@ -707,6 +709,7 @@ k_trace_df(const __grid_constant__ TraceArgs a) {
                 o = o2;
                 L = df_add(L, t);
                 a.seq[(int64_t)bounce * a.R + ray] = surf;
+                a.seqf[(int64_t)bounce * a.R + ray] = __float_as_int(__ldg(a.tris + 3 * j + 1).w);
                 prev = surf;
                 bounce += 1;
                 entered = bounce;
@@ -1005,6 +1008,7 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
         SBR_TRY(dalloc_n(&q0, (size_t)R, s));
         SBR_TRY(dalloc_n(&q1, (size_t)R, s));
         SBR_TRY(dalloc_n(&seq, (size_t)R * K, s));
+        SBR_TRY(dalloc_n(&tr->seqf, (size_t)R * K, s));
     }
     TraceArgs a{};
     a.nodes = b->tree.nodes;
@@ -1028,6 +1032,7 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
         a.tx_l[k] = x.lo;
     }
     a.seq = seq;
+    a.seqf = tr->seqf;
     a.ht_state = tr->ht_state;
     a.ht_key = tr->ht_key;
     a.ht_val = tr->ht_val;
