@@ -23,20 +23,11 @@ inline unsigned blocks_for(int64_t n, int t = kThreads) {
 }
 
 // out[0..5] centroid lo/hi, out[6..11] box lo/hi (one block)
-__global__ void k_bounds(const float* __restrict__ box, int64_t n, float* __restrict__ out) {
-    __shared__ float red[12][1024 / 32];
-    float v[12];
-    for (int a = 0; a < 3; ++a) {
-        v[a] = INFINITY; v[3 + a] = -INFINITY; v[6 + a] = INFINITY; v[9 + a] = -INFINITY;
-    }
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        for (int a = 0; a < 3; ++a) {
-            float lo = box[6 * i + a], hi = box[6 * i + 3 + a];
-            float c = 0.5f * (lo + hi);
-            v[a] = fminf(v[a], c); v[3 + a] = fmaxf(v[3 + a], c);
-            v[6 + a] = fminf(v[6 + a], lo); v[9 + a] = fmaxf(v[9 + a], hi);
-        }
-    }
+// scene bounds of the box centres (for the Morton grid) and of the boxes:
+// out[0..2] centre min, [3..5] centre max, [6..8] box min, [9..11] box max.
+// Stage 1: per-block partial reductions (grid-stride); stage 2: one block
+// combines the partials.
+__device__ __forceinline__ void bounds_block_reduce(float* v, float (*red)[32], float* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k < 12; ++k) {
         float x = v[k];
@@ -57,6 +48,35 @@ __global__ void k_bounds(const float* __restrict__ box, int64_t n, float* __rest
     }
 }
 
+__global__ void k_bounds(const float* __restrict__ box, int64_t n, float* __restrict__ part) {
+    __shared__ float red[12][32];
+    float v[12];
+    for (int a = 0; a < 3; ++a) {
+        v[a] = INFINITY; v[3 + a] = -INFINITY; v[6 + a] = INFINITY; v[9 + a] = -INFINITY;
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int a = 0; a < 3; ++a) {
+            float lo = box[6 * i + a], hi = box[6 * i + 3 + a];
+            float c = 0.5f * (lo + hi);
+            v[a] = fminf(v[a], c); v[3 + a] = fmaxf(v[3 + a], c);
+            v[6 + a] = fminf(v[6 + a], lo); v[9 + a] = fmaxf(v[9 + a], hi);
+        }
+    }
+    bounds_block_reduce(v, red, part + 12 * blockIdx.x);
+}
+
+__global__ void k_bounds_final(const float* __restrict__ part, int nparts, float* __restrict__ out) {
+    __shared__ float red[12][32];
+    float v[12];
+    for (int a = 0; a < 3; ++a) {
+        v[a] = INFINITY; v[3 + a] = -INFINITY; v[6 + a] = INFINITY; v[9 + a] = -INFINITY;
+    }
+    for (int p = threadIdx.x; p < nparts; p += blockDim.x)
+        for (int k = 0; k < 12; ++k) v[k] = ((k / 3) & 1) ? fmaxf(v[k], part[12 * p + k]) : fminf(v[k], part[12 * p + k]);
+    bounds_block_reduce(v, red, out);
+}
+
+// 10-bit integer spread to every third bit (the Morton interleave)
 __device__ __forceinline__ uint32_t expand_bits(uint32_t x) {
     x = (x * 0x00010001u) & 0xFF0000FFu;
     x = (x * 0x00000101u) & 0x0F00F00Fu;
@@ -139,20 +159,16 @@ __global__ void k_refit(const float* __restrict__ prim_box, const int32_t* __res
                         int64_t n, const int32_t* __restrict__ left,
                         const int32_t* __restrict__ right, const int32_t* __restrict__ parent_int,
                         const int32_t* __restrict__ parent_leaf, int32_t* __restrict__ flag,
-                        float* lbox, float* ibox, int32_t* __restrict__ depth) {
+                        float* lbox, float* ibox, int32_t* hd, int32_t* __restrict__ depth) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const float* src = prim_box + 6 * (int64_t)order[j];
     for (int k = 0; k < 6; ++k) lbox[6 * j + k] = src[k];
-    // depth of this leaf
-    {
-        int dd = 1;
-        int32_t node = n > 1 ? parent_leaf[j] : -1;
-        while (node >= 0) { ++dd; node = parent_int[node]; }
-        atomicMax(depth, dd);
-    }
     __threadfence();
-    if (n < 2) return;
+    if (n < 2) {
+        *depth = 1;
+        return;
+    }
     int32_t node = parent_leaf[j];
     while (node >= 0) {
         if (atomicAdd(&flag[node], 1) == 0) return;  // the sibling subtree is not done yet
@@ -166,7 +182,13 @@ __global__ void k_refit(const float* __restrict__ prim_box, const int32_t* __res
             o[k] = fminf(a[k], b[k]);
             o[3 + k] = fmaxf(a[3 + k], b[3 + k]);
         }
+        // height: a leaf counts 1, a node one more than its higher child; the
+        // root's height is the tree depth (levels on the longest root-leaf path)
+        const int hl = l < 0 ? 1 : ((volatile int32_t*)hd)[l], hr = r < 0 ? 1 : ((volatile int32_t*)hd)[r];
+        const int h = 1 + (hl > hr ? hl : hr);
+        ((volatile int32_t*)hd)[node] = h;
         __threadfence();
+        if (parent_int[node] < 0) *depth = h;
         node = parent_int[node];
     }
 }
@@ -302,6 +324,10 @@ sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, int leaf_
     int32_t *left, *right, *pint, *pleaf, *flag, *span;
     float *lbox, *ibox;
     SBR_TRY(dalloc_n(&bnd, 12, s));
+    float* part;
+    SBR_TRY(dalloc_n(&part, 12 * 2 * (size_t)sm_count(), s));
+    int32_t* hd;
+    SBR_TRY(dalloc_n(&hd, nn, s));
     SBR_TRY(dalloc_n(&code, n, s));
     SBR_TRY(dalloc_n(&idx, n, s));
     SBR_TRY(dalloc_n(&left, nn, s));
@@ -316,19 +342,21 @@ sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, int leaf_
     SBR_TRY(dalloc_n(&out->d_root, 6, s));
     SBR_TRY_CUDA(cudaMemsetAsync(flag, 0, nn * sizeof(int32_t), s));
     SBR_TRY_CUDA(cudaMemsetAsync(d_depth, 0, sizeof(int32_t), s));
-    ::sbr::note_launch(), k_bounds<<<1, 1024, 0, s>>>(prim_box, n, bnd);
+    const int nparts = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 2 * (int64_t)sm_count());
+    ::sbr::note_launch(), k_bounds<<<nparts, 256, 0, s>>>(prim_box, n, part);
+    ::sbr::note_launch(), k_bounds_final<<<1, 256, 0, s>>>(part, nparts, bnd);
     ::sbr::note_launch(), k_morton<<<blocks_for(n), kThreads, 0, s>>>(prim_box, n, bnd, code, idx);
     SBR_TRY_CUDA(cudaGetLastError());
     SBR_TRY(radix_sort_pairs(code, idx, n, 30, s));
     if (n > 1) ::sbr::note_launch(), k_karras<<<blocks_for(n - 1), kThreads, 0, s>>>(code, n, left, right, pint, pleaf, span);
     ::sbr::note_launch(), k_refit<<<blocks_for(n), kThreads, 0, s>>>(prim_box, (const int32_t*)idx, n, left, right, pint,
-                                               pleaf, flag, lbox, ibox, d_depth);
+                                               pleaf, flag, lbox, ibox, hd, d_depth);
     ::sbr::note_launch(), k_emit<<<blocks_for(nn), kThreads, 0, s>>>(n, left, right, span, leaf_max, lbox, ibox, pad_rel, out->nodes,
                                                out->d_root);
     SBR_TRY_CUDA(cudaGetLastError());
     out->order = reinterpret_cast<int32_t*>(idx);
     out->n_nodes = (int32_t)nn;
-    dfree(bnd, s); dfree(code, s); dfree(left, s); dfree(right, s); dfree(pint, s);
+    dfree(bnd, s); dfree(part, s); dfree(hd, s); dfree(code, s); dfree(left, s); dfree(right, s); dfree(pint, s);
     dfree(pleaf, s); dfree(flag, s); dfree(span, s); dfree(lbox, s); dfree(ibox, s);
     return SBR_OK;
 }

@@ -30,7 +30,8 @@ sbr_status gains_run(const sbr_path_list* pl, const sbr_material* mats, int32_t 
                      int32_t pol, float2* g, cudaStream_t s) {
     int64_t n = pl->P * (int64_t)F;
     if (n == 0) return SBR_OK;
-    ::sbr::note_launch(), k_gains<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pl->P, F, pl->nb, pl->surf, pl->L, pl->jones,
+    // small blocks: the per-(path, frequency) FP64 chains are latency-bound, spread them over every SM
+    ::sbr::note_launch(), k_gains<<<(unsigned)((n + 63) / 64), 64, 0, s>>>(pl->P, F, pl->nb, pl->surf, pl->L, pl->jones,
                                                           mats, S, freqs, gamma, disp, pol, g);
     SBR_TRY_CUDA(cudaGetLastError());
     return SBR_OK;
