@@ -355,6 +355,10 @@ typedef struct {
     int32_t precision;        /* SBR_SYNTH_FP16X3 (0 = this) or SBR_SYNTH_BF16X3             */
     int32_t use_graph;        /* 1 (default when the config pointer is NULL): capture the   */
                               /* whole batch into one CUDA graph; 0: plain stream launches  */
+    int32_t breadth_first;    /* 0 (default): each ray traced depth first through all its   */
+                              /* bounces in one launch per wave; 1: one launch per bounce   */
+                              /* over compacted ray queues                                  */
+    int32_t reserved;
 } sbr_batch_config;
 
 typedef struct {

@@ -353,7 +353,8 @@ class Batch:
                        ray_bounces=info.ray_bounces, paths=info.paths,
                        config=dict(wave_rays=c.wave_rays, path_cap=c.path_cap, table_log2=c.table_log2,
                                    tile_n=c.tile_n, trace_blocks_per_sm=c.trace_blocks_per_sm,
-                                   precision=c.precision, use_graph=c.use_graph))
+                                   precision=c.precision, use_graph=c.use_graph,
+                                   breadth_first=c.breadth_first))
         return np_, st, summary
 
     def export(self, job: int, n: int, stream=None) -> dict:
@@ -456,7 +457,7 @@ def batch_tune(scenes, jobs, config=None, stream=None):
     del keep
     return dict(wave_rays=c.wave_rays, path_cap=c.path_cap, table_log2=c.table_log2, tile_n=c.tile_n,
                 trace_blocks_per_sm=c.trace_blocks_per_sm, precision=c.precision,
-                use_graph=c.use_graph), ms.value
+                use_graph=c.use_graph, breadth_first=c.breadth_first), ms.value
 
 
 # ---------------------------------------------------------------- surrogate

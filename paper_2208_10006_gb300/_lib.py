@@ -66,7 +66,7 @@ class BatchJob(C.Structure):
 class BatchConfig(C.Structure):
     _fields_ = [("wave_rays", C.c_int64), ("path_cap", C.c_int32), ("table_log2", C.c_int32),
                 ("tile_n", C.c_int32), ("trace_blocks_per_sm", C.c_int32), ("precision", C.c_int32),
-                ("use_graph", C.c_int32)]
+                ("use_graph", C.c_int32), ("breadth_first", C.c_int32), ("reserved", C.c_int32)]
 
 
 class BatchInfo(C.Structure):
@@ -85,8 +85,8 @@ class MlpConfig(C.Structure):
 
 assert C.sizeof(TraceParams) == 64
 assert C.sizeof(BatchJob) == 136
-assert C.sizeof(BatchConfig) == 32
-assert C.sizeof(BatchInfo) == 80
+assert C.sizeof(BatchConfig) == 40
+assert C.sizeof(BatchInfo) == 88
 
 _lib = None
 

@@ -403,6 +403,7 @@ sbr_status enqueue(sbr_batch* b, cudaStream_t s) {
         tw.R_total = wv.R_total;
         tw.q0 = b->q0;
         tw.q1 = b->q1;
+        tw.depth_first = c.breadth_first == 0;
         tw.ht_state = b->ht_state;
         tw.ht_key = b->ht_key;
         tw.ht_val = b->ht_val;
@@ -488,7 +489,7 @@ sbr_status create(const sbr_bvh* const* scenes, const sbr_material* const* mats,
     sbr_batch_config c{};
     if (cfg_in) c = *cfg_in;
     else c.use_graph = 1;
-    if (c.wave_rays == 0) c.wave_rays = (int64_t)1 << 26;
+    if (c.wave_rays == 0) c.wave_rays = (int64_t)1 << (c.breadth_first ? 26 : 28);
     if (c.path_cap == 0) c.path_cap = 512;
     if (c.tile_n == 0) c.tile_n = 128;
     if (c.precision == 0) c.precision = SBR_SYNTH_FP16X3;
@@ -547,8 +548,10 @@ sbr_status create(const sbr_bvh* const* scenes, const sbr_material* const* mats,
 
     // device buffers
     sbr_status st = SBR_OK;
-    if ((st = balloc(b, reinterpret_cast<unsigned char**>(&b->q0), (size_t)max_R_wave * 64)) != SBR_OK) return fail(st);
-    if ((st = balloc(b, reinterpret_cast<unsigned char**>(&b->q1), (size_t)max_R_wave * 64)) != SBR_OK) return fail(st);
+    if (c.breadth_first) {   // ray queues only for the breadth-first schedule
+        if ((st = balloc(b, reinterpret_cast<unsigned char**>(&b->q0), (size_t)max_R_wave * 64)) != SBR_OK) return fail(st);
+        if ((st = balloc(b, reinterpret_cast<unsigned char**>(&b->q1), (size_t)max_R_wave * 64)) != SBR_OK) return fail(st);
+    }
     if ((st = balloc(b, &b->seq, (size_t)std::max<int64_t>(max_seq, 1))) != SBR_OK) return fail(st);
     if ((st = balloc(b, &b->ht_state, cap)) != SBR_OK) return fail(st);
     if ((st = balloc(b, &b->ht_key, cap * kKeyWords)) != SBR_OK) return fail(st);
@@ -866,7 +869,8 @@ sbr_status sbr_batch_tune(const sbr_bvh* const* scenes, const sbr_material* cons
     // coordinate search: tile width, then bounce grid, then ray-queue capacity
     const int tiles[3] = {64, 128, 256};
     const int grids[3] = {2, 3, 4};
-    const int64_t waves[3] = {(int64_t)1 << 25, (int64_t)1 << 26, (int64_t)1 << 27};
+    const int sh = fixed.breadth_first ? 25 : 26;
+    const int64_t waves[3] = {(int64_t)1 << sh, (int64_t)1 << (sh + 1), (int64_t)1 << (sh + 2)};
     auto consider = [&](sbr_batch_config c) -> sbr_status {
         SBR_TRY(time_cfg(c, &t, &mk, &res));
         if (t < best_t) { best_t = t; best = res; }

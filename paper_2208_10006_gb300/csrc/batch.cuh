@@ -68,8 +68,9 @@ struct BatchTraceWave {
     int32_t n_jobs;
     int32_t Kmax;
     int64_t R_total;
-    void* q0;                    // ray queues, 64 B records, capacity R_total each
+    void* q0;                    // ray queues, 64 B records, capacity R_total each (breadth first)
     void* q1;
+    bool depth_first;            // one launch, each ray carried through its bounces (no queues)
     uint32_t* ht_state;
     uint32_t* ht_key;
     unsigned long long* ht_val;

@@ -875,6 +875,97 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_batch(const __grid_cons
     }
 }
 
+// the batched step, depth first: each lane carries its ray (and job) through
+// every bounce of its job, then takes the next ray of the wave
+__global__ void __launch_bounds__(kTraceThreads) k_trace_batch_df(const __grid_constant__ BatchTraceArgs a) {
+    int stack[kStack];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long n_in = (unsigned long long)a.R_total;
+    df3 o{}, d{};
+    df L = df_make(0.f, 0.f);
+    uint32_t ray = 0;
+    int prev = -1, bounce = 0, job = 0;
+    bool has = false, exhausted = false;
+    for (;;) {
+        const unsigned need = __ballot_sync(FULL, !has);
+        if (need && !exhausted) {
+            const int leader = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(need));
+            base = __shfl_sync(FULL, base, leader);
+            if (base + __popc(need) >= n_in) exhausted = true;
+            if (!has) {
+                const unsigned long long i = base + __popc(need & ((1u << lane) - 1u));
+                if (i < n_in) {
+                    int lo = 0, hi = a.n_jobs - 1;   // the last job whose first ray is <= i
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (__ldg(a.ray_off + mid) <= (int64_t)i) lo = mid; else hi = mid - 1;
+                    }
+                    job = lo;
+                    const BatchJobDev* J = a.jobs + job;
+                    ray = (uint32_t)((int64_t)i - __ldg(a.ray_off + job));
+                    o = df3{df_make(J->tx_h[0], J->tx_l[0]), df_make(J->tx_h[1], J->tx_l[1]),
+                            df_make(J->tx_h[2], J->tx_l[2])};
+                    float4 da = __ldg(J->dir_a + ray);
+                    float2 db = __ldg(J->dir_b + ray);
+                    d = df3{df_make(da.x, da.w), df_make(da.y, db.x), df_make(da.z, db.y)};
+                    L = df_make(0.f, 0.f);
+                    prev = -1;
+                    bounce = 0;
+                    has = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, has)) break;
+        int entered = -1;
+        if (has) {
+            const BatchJobDev* J = a.jobs + job;
+            const JobScene sc{J->nodes, J->tris, J->plane, a.cnt};
+            Ray32 r = make_ray32(df3_hi(o), df3_hi(d));
+            df t = df_make(INFINITY, 0.f);
+            Trav tv;
+            int32_t j = traverse32<false>(sc, r, prev, tv, stack, nullptr, nullptr);
+            j = settle_hit(sc, o, d, prev, tv, j, stack, t);
+            {
+                const float4 rh = J->rx_h, rl = J->rx_l, al = J->alpha;
+                const df3 Rx{df_make(rh.x, rl.x), df_make(rh.y, rl.y), df_make(rh.z, rl.z)};
+                float dist;
+                if (rx_accept(o, d, L, t, j >= 0, Rx, df_make(al.z, al.w), dist)) {
+                    uint32_t key[kKeyWords];
+                    key[0] = (uint32_t)job;
+                    key[1] = (uint32_t)bounce;
+                    for (int k = 0; k < kKmax; ++k)
+                        key[2 + k] = k < bounce ? (uint32_t)J->seq[(int64_t)k * J->R + ray] : 0xffffffffu;
+                    unsigned long long val = ((unsigned long long)__float_as_uint(dist) << 32) | ray;
+                    ht_insert(a, key, val);
+                    atomicAdd(&a.cnt->candidates, 1ull);
+                }
+            }
+            if (j >= 0 && bounce < J->K) {
+                df c;
+                df3 n = ld_plane_n(J->plane, j, c);
+                int32_t surf = __float_as_int(__ldg(J->tris + 3 * j).w);
+                df3 o2 = df3_add(o, df3_scale(d, t));
+                df dn = df3_dot(d, n);
+                d = df3_sub(d, df3_scale(n, df_make(2.f * dn.hi, 2.f * dn.lo)));
+                o = o2;
+                L = df_add(L, t);
+                J->seq[(int64_t)bounce * J->R + ray] = surf;
+                prev = surf;
+                bounce += 1;
+                entered = bounce;
+            } else {
+                has = false;
+            }
+        }
+        const unsigned grp = __match_any_sync(FULL, entered);
+        if (entered >= 0 && lane == __ffs(grp) - 1)
+            atomicAdd(&a.cnt->queue[entered], (unsigned long long)__popc(grp));
+    }
+}
+
 __global__ void k_rx_df(const double* __restrict__ rx, int32_t n, float4* __restrict__ out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -923,10 +1014,12 @@ int trace_grid(bool count) {
 int batch_trace_kernels(int Kmax) { return Kmax + 3; }
 
 int batch_trace_occupancy() {
-    int per_sm = 0;
+    int per_sm = 0, per_sm_df = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_batch, kTraceThreads, 0) != cudaSuccess)
         per_sm = 1;
-    return std::max(1, per_sm);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_df, k_trace_batch_df, kTraceThreads, 0) != cudaSuccess)
+        per_sm_df = 1;
+    return std::max(1, std::min(per_sm, per_sm_df));
 }
 
 sbr_status batch_trace_wave(const BatchTraceWave& w, int blocks_per_sm, cudaStream_t s) {
@@ -951,6 +1044,13 @@ sbr_status batch_trace_wave(const BatchTraceWave& w, int blocks_per_sm, cudaStre
     a.ht_val = w.ht_val;
     a.ht_mask = w.ht_mask;
     a.cnt = w.cnt;
+    if (w.depth_first) {
+        a.bounce = 0;
+        a.work = &w.cnt->work[0];
+        ::sbr::note_launch(), k_trace_batch_df<<<grid, kTraceThreads, 0, s>>>(a);
+        SBR_TRY_CUDA(cudaGetLastError());
+        return SBR_OK;
+    }
     RayRec* q0 = static_cast<RayRec*>(w.q0);
     RayRec* q1 = static_cast<RayRec*>(w.q1);
     for (int bnc = 0; bnc <= w.Kmax; ++bnc) {

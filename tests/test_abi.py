@@ -65,7 +65,7 @@ def test_ctypes_struct_layouts_match_the_header(tmp_path):
               "sbr_trace_counters": (_lib.TraceCounters, ["near_edge_hits", "queue", "alpha", "bounce_ms"]),
               "sbr_path_info": (_lib.PathInfo, ["n_paths", "status"]),
               "sbr_batch_job": (_lib.BatchJob, ["tx", "alpha", "F", "freqs_hz", "H"]),
-              "sbr_batch_config": (_lib.BatchConfig, ["path_cap", "use_graph"]),
+              "sbr_batch_config": (_lib.BatchConfig, ["path_cap", "use_graph", "breadth_first"]),
               "sbr_batch_info": (_lib.BatchInfo, ["max_keys", "rays", "config"]),
               "sbr_mlp_config": (_lib.MlpConfig, ["seed", "x_lo", "lr", "err_channel", "err_of"])}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sbr.h"', "int main(void) {"]

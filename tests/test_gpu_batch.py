@@ -58,7 +58,9 @@ def _per_pair(sbr, sdev, j, precision):
     return pl, to_numpy(pl.export()), g.cpu().numpy(), H.cpu().numpy()
 
 
-@pytest.mark.parametrize("cfg", [dict(tile_n=64, wave_rays=40000), dict(tile_n=128), dict(tile_n=256, use_graph=0)])
+@pytest.mark.parametrize("cfg", [dict(tile_n=64, wave_rays=40000), dict(tile_n=128),
+                                 dict(tile_n=256, use_graph=0, breadth_first=1),
+                                 dict(tile_n=64, wave_rays=40000, breadth_first=1)])
 def test_batch_equals_per_pair_calls(sbr, cfg):
     scs, jobs, sdev, jdev = _workload(sbr)
     b = sbr.batch_create(sdev, jdev, config=dict(path_cap=256, **cfg))
