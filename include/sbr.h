@@ -220,8 +220,8 @@ typedef struct {
 sbr_status sbr_path_query(const sbr_path_list* pl, sbr_path_info* out);
 
 /*
- * sbr_path_export - copy the path list into caller buffers (dev, any may be
- * NULL). Layouts for P paths: rx, n_bounce int32 [P]; surf_seq, face_seq
+ * sbr_path_export - copy the path list into caller buffers (device memory, or
+ * host memory: pinned for the copy to stay asynchronous; any may be NULL). Layouts for P paths: rx, n_bounce int32 [P]; surf_seq, face_seq
  * int32 [P*8] (-1 padded); pts double [P*8*3] interaction points; length
  * double [P] (m); aod, aoa double [P*2] (azimuth, elevation from the
  * horizontal, degrees; AoD towards the first interaction point, AoA towards

@@ -61,6 +61,15 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _ptr_or_pinned(t):
+    """A CUDA tensor or a pinned host tensor (copy destinations)."""
+    if t is not None and not t.is_cuda:
+        if not t.is_pinned() or not t.is_contiguous():
+            raise ValueError("expected a CUDA tensor or a contiguous pinned host tensor")
+        return C.c_void_p(t.data_ptr())
+    return _ptr(t)
+
+
 def _dev():
     if not torch.cuda.is_available():
         raise RuntimeError("no CUDA device: the SBR library has no CPU path")
@@ -196,9 +205,17 @@ class PathList:
         return dict(n_paths=i.n_paths, n_keys=i.n_keys, n_invalid=i.n_invalid, n_rx=i.n_rx,
                     max_bounces=i.max_bounces, status=i.status)
 
-    def export(self, stream=None) -> dict:
+    def export(self, stream=None, out: dict = None) -> dict:
+        """The path list as tensors; `out` may hold preallocated CUDA or pinned
+        host tensors of the same shapes (then the copies land there directly)."""
         dev = _dev()
         P = self.n
+        if out is not None:
+            o = out
+            _check(_L().sbr_path_export(self._h, *[_ptr_or_pinned(o[k]) for k in
+                                                   ("rx", "nb", "seq", "face", "pts", "L", "aod", "aoa", "ray",
+                                                    "dist")], _stream(stream)))
+            return out
         out = dict(
             rx=torch.empty(P, dtype=torch.int32, device=dev),
             nb=torch.empty(P, dtype=torch.int32, device=dev),

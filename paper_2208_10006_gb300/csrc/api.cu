@@ -360,7 +360,8 @@ sbr_status sbr_path_export(const sbr_path_list* pl, int32_t* rx, int32_t* n_boun
     if (P == 0) return SBR_OK;
     auto cp = [&](void* dst, const void* src, size_t bytes) -> sbr_status {
         if (!dst) return SBR_OK;
-        SBR_TRY_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+        // device or (pinned) host destination, resolved by unified addressing
+        SBR_TRY_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
         return SBR_OK;
     };
     SBR_TRY(cp(rx, pl->rx, P * sizeof(int32_t)));

@@ -281,3 +281,17 @@ def test_tensor_core_synthesis_los_only(sbr, form):
     Htc = sbr.synthesize_H(r["paths"], r["g"], d["freqs"], d["tx_elem"], d["rx_elem"], 0, form).cpu().numpy()
     # the LoS term is evaluated in the FP32 epilogue (phase ~1e-6 relative)
     assert np.abs(Htc - H64).max() < 1e-5 * np.abs(H64).max()
+
+
+def test_export_into_pinned_host_buffers(sbr):
+    # the path list copied straight into pinned host memory equals the device export
+    sc = SCENES["urban_small"]()
+    r = sbr.run_scene(sc)
+    ex = r["paths"].export()
+    pinned = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in ex.items()}
+    r["paths"].export(out=pinned)
+    torch.cuda.synchronize()
+    for k, v in ex.items():
+        assert torch.equal(pinned[k], v.cpu()), k
+    with pytest.raises(ValueError):
+        r["paths"].export(out={k: torch.empty(v.shape, dtype=v.dtype) for k, v in ex.items()})
