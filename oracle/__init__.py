@@ -79,6 +79,8 @@ def lib():
         L.orc_gains.argtypes = [p, p, i64, i32, p, p, p, i64, p, p, p, p, p, p, i32, p, p, i32, p]
         L.orc_synth_H.restype = i32
         L.orc_synth_H.argtypes = [i64, p, p, p, p, p, i32, p, p, p, i32, p, i32, i32, p]
+        L.orc_synth_H_elements.restype = i32
+        L.orc_synth_H_elements.argtypes = [i64, p, p, p, p, p, p, i32, p, p, i32, p, i32, p]
         L.orc_pdp_stats.restype = i32
         L.orc_pdp_stats.argtypes = [i64, p, p, p, p, f64, f64, i32, p, p]
         L.orc_capacity.restype = i32
@@ -243,6 +245,24 @@ def synth_H(paths: dict, g: np.ndarray, freqs, tx_ref, rx_ref, tx_elem, rx_elem,
                       _ptr(gg), _ptr(freqs), F, _ptr(_c(tx_ref, np.float64)),
                       _ptr(_c(rx_ref, np.float64)), _ptr(txe), len(txe), _ptr(rxe), len(rxe),
                       nthreads or nthreads_default(), _ptr(H))
+    return H
+
+
+def synth_H_elements(paths: dict, g: np.ndarray, freqs, tx_ref, tx_elem, rx_elem):
+    """Per-element reception: paths of every receive element (paths["rx"] is the
+    element index), H [F, Nr, Nt] complex128, each row from its element's own paths."""
+    freqs = _c(freqs, np.float64)
+    F = len(freqs)
+    txe = _c(tx_elem, np.float64).reshape(-1, 3)
+    rxe = _c(rx_elem, np.float64).reshape(-1, 3)
+    H = np.zeros((F, len(rxe), len(txe)), np.complex128)
+    P = len(paths["L"])
+    rc = lib().orc_synth_H_elements(P, _ptr(_c(paths["rx"], np.int32)), _ptr(_c(paths["nb"], np.int32)),
+                                    _ptr(_c(paths["pts"], np.float64)), _ptr(_c(paths["L"], np.float64)),
+                                    _ptr(_c(g, np.complex128)), _ptr(freqs), F, _ptr(_c(tx_ref, np.float64)),
+                                    _ptr(txe), len(txe), _ptr(rxe), len(rxe), _ptr(H))
+    if rc != 0:
+        raise ValueError("path receiver index out of range")
     return H
 
 

@@ -806,6 +806,51 @@ int32_t orc_synth_H(int64_t P, const int32_t* nb, const double* pts, const doubl
 }
 
 /* ------------------------------------------------------------------------ */
+/* Per-element reception (Sec. I near field, Eq. 13-14, Fig. 11): every       */
+/* receive element q is traced as a receiver of its own, and its H row sums   */
+/* its own paths. Paths n of element q (rx[n] == q) with unfolded length L_n: */
+/*   H[f,q,p] = sum_n g_n(f) exp(-j 2 pi f len_np / c),                       */
+/*   len_np = |T_p - R_q| for the LoS path,                                   */
+/*   len_np = L_n + |T_p - P1| - |T_0 - P1| otherwise (P1 the first point);   */
+/* the Rx side needs no correction because R_q is the traced receiver.        */
+/* ------------------------------------------------------------------------ */
+
+int32_t orc_synth_H_elements(int64_t P, const int32_t* rx, const int32_t* nb, const double* pts,
+                             const double* L, const double* g, const double* freqs, int32_t F,
+                             const double* tx_ref, const double* tx_elem, int32_t Nt,
+                             const double* rx_elem, int32_t Nr, double* H) {
+    v3 T0 = ld3(tx_ref);
+    for (int64_t i = 0; i < (int64_t)F * Nr * Nt * 2; ++i) H[i] = 0.0;
+    for (int64_t n = 0; n < P; ++n) {
+        int32_t q = rx[n];
+        if (q < 0 || q >= Nr) return -1;
+        v3 Rq = ld3(rx_elem + 3 * q);
+        int m = nb[n];
+        for (int32_t p = 0; p < Nt; ++p) {
+            v3 Tp = ld3(tx_elem + 3 * p);
+            double len;
+            if (m == 0) {
+                len = norm(sub(Tp, Rq));
+            } else {
+                v3 P1 = ld3(pts + (n * ORC_KMAX) * 3);
+                double dt = norm(sub(Tp, P1)) - norm(sub(T0, P1));
+                len = L[n] + dt;
+            }
+            for (int32_t fi = 0; fi < F; ++fi) {
+                double cyc = freqs[fi] * len / ORC_C0;
+                double ang = -2.0 * ORC_PI * (cyc - floor(cyc));
+                double gr = g[2 * (n * F + fi)], gi = g[2 * (n * F + fi) + 1];
+                double c = cos(ang), s = sin(ang);
+                int64_t o = 2 * ((fi * (int64_t)Nr + q) * Nt + p);
+                H[o] += gr * c - gi * s;
+                H[o + 1] += gr * s + gi * c;
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* O8: PDP and channel statistics of one receiver (Eq. 2, 4, 5; Table I).     */
 /* Reading: absolute delay tau = L / c, bins [k, k+1) * bin_s; tap = sum of   */
 /* |g_n(f_c)|^2 falling in the bin, in dB (empty bins -inf). PL_inc =         */

@@ -165,3 +165,46 @@ def test_capacity_matches_numpy_slogdet(nr, nt):
             sign, ld = np.linalg.slogdet(np.eye(W.shape[0]) + 10 ** (sd / 10) / nt * W)
             ref[s] += ld / np.log(2) / F
     assert np.allclose(C, ref, rtol=1e-12)
+
+
+def _free_space(f):
+    return dict(name="free", tri=np.zeros((0, 3, 3), np.float32), surface_id=np.zeros(0, np.int32),
+                materials=np.zeros((0, 3)), tx=np.array([0.0, 0.0, 1.0]), rx_valid=None, freqs=f,
+                gamma_db_km=np.zeros(len(f), np.float32), disp_deg_km=np.zeros(len(f), np.float32),
+                N=30, K=1, pol="V")
+
+
+def test_per_element_free_space_is_the_exact_spherical_wave():
+    # every receive element traced as a receiver of its own: in free space each row is
+    # the element's own Friis amplitude times the exact element-pair phasor
+    f = np.array([27e9, 28e9, 29e9])
+    sc = _free_space(f)
+    T = scenes.upa_yz(sc["tx"], 4, 4, 0.05)
+    R = scenes.ula_y([3.0, 0.5, 1.2], 6, 0.05)
+    sc["rx"] = R
+    sc["rx_valid"] = np.ones(len(R), bool)
+    r = oracle.run(sc)
+    p, g = r["paths"], r["g"]
+    assert sorted(p["rx"].tolist()) == list(range(len(R))) and (p["nb"] == 0).all()
+    H = oracle.synth_H_elements(p, g, f, sc["tx"], T, R)
+    d0 = np.linalg.norm(R - sc["tx"], axis=1)                                  # [Nr]
+    dist = np.linalg.norm(R[:, None, :] - T[None, :, :], axis=2)                # [Nr, Nt]
+    ref = (C0 / (4 * np.pi * f[:, None, None] * d0[None, :, None])) * \
+        np.exp(-2j * np.pi * f[:, None, None] * dist[None] / C0)
+    assert np.abs(H - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_per_element_with_one_element_at_the_reference_equals_reference_synthesis():
+    # a single receive element at the receiver reference point: the per-element form and
+    # the reference-point form (zero receive-side correction) coincide
+    sc = _small_mimo(nr=1)
+    sc["rx_elem"] = sc["rx"][:1].copy()
+    r = oracle.run(sc)
+    p, g = r["paths"], r["g"]
+    sel = p["rx"] == 0
+    assert sel.sum() >= 3
+    H_ref = oracle.synth_H(p, g, sc["freqs"], sc["tx"], sc["rx"][0], sc["tx_elem"], sc["rx_elem"])
+    sub = {k: v[sel] for k, v in p.items() if isinstance(v, np.ndarray) and len(v) == len(sel)}
+    H_el = oracle.synth_H_elements(sub, g[sel], sc["freqs"], sc["tx"], sc["tx_elem"], sc["rx_elem"])
+    # (phases of ~1e3-1e4 cycles: agreement to the rounding of the path length)
+    assert np.abs(H_el - H_ref).max() <= 1e-11 * np.abs(H_ref).max()
