@@ -269,6 +269,26 @@ sbr_status sbr_synthesize_H(const sbr_path_list* pl, const void* gains, const do
                             int32_t Nr, int32_t rx_index, int32_t precision, void* H, void* stream);
 
 /*
+ * sbr_synthesize_H_elements - MIMO channel matrix with per-element reception
+ * (Sec. I near field, Eq. 13-14; the spatial non-stationarity of Fig. 11).
+ * Each receive element is a receiver of the trace (rx_xyz of the path list,
+ * Nr = n_rx), so element q sees its own path set; its row sums those paths:
+ *   H[f,q,p] = sum_{n: rx_n = q} g_n(f) exp(-j 2 pi f len_np / c),
+ *   len_np = |T_p - R_q| for the LoS path, L_n + |T_p - P1| - |T_0 - P1|
+ *   otherwise (P1 the first interaction point, T_0 the trace's tx).
+ * Unlike sbr_synthesize_H no Rx-side correction is applied: the element is
+ * the traced point. gains: dev complex64 [P*F] (NULL when P = 0);
+ * freqs_hz: dev double [F]; tx_elem: dev double [Nt*3].
+ * precision: SBR_SYNTH_FP64 or SBR_SYNTH_FP32 (summation type; element
+ * delays and the reduced phase f L_n / c are always FP64).
+ * H: dev complex64 [F*n_rx*Nt], element (f, q, p) at (f*n_rx + q)*Nt + p.
+ * F, n_rx <= 65535. Device scratch: P*(Nt+F) doubles (plus the FP32 copies).
+ */
+sbr_status sbr_synthesize_H_elements(const sbr_path_list* pl, const void* gains, const double* freqs_hz,
+                                     int32_t F, const double* tx_elem, int32_t Nt, int32_t precision,
+                                     void* H, void* stream);
+
+/*
  * sbr_pdp_angles - PDP and channel statistics per receiver (Eq. 2, 4, 5).
  * Uses column f_index of gains (F columns) at frequency fc_hz. PDP: absolute
  * delay tau = L / c in bins [k, k+1) * bin_s, tap = sum |g|^2 in dB (empty

@@ -26,7 +26,7 @@ from ._lib import (KMAX, NSTATS, POL_H, POL_V, SYNTH_BF16X3, SYNTH_FP16X3, SYNTH
                    STATUS_NAMES)
 
 __all__ = ["SbrError", "BVH", "TraceResult", "PathList", "launch_dirs", "build_bvh", "trace",
-           "paths", "path_gains", "synthesize_H", "pdp_angles", "capacity", "version",
+           "paths", "path_gains", "synthesize_H", "synthesize_H_elements", "pdp_angles", "capacity", "version",
            "POL_V", "POL_H", "SYNTH_FP64", "SYNTH_FP32", "SYNTH_BF16X3", "SYNTH_FP16X3", "KMAX", "NSTATS",
            "scene_to_device", "run_scene", "Batch", "batch_create", "batch_tune", "surrogate_targets", "MLP"]
 
@@ -275,6 +275,18 @@ def synthesize_H(pl: PathList, gains: torch.Tensor, freqs: torch.Tensor, tx_elem
     _check(_L().sbr_synthesize_H(pl.handle, _ptr(g), _ptr(freqs), F, _ptr(tx_elem), Nt,
                                  _ptr(rx_elem), Nr, int(rx_index), int(precision), _ptr(H),
                                  _stream(stream)))
+    return H
+
+
+def synthesize_H_elements(pl: PathList, gains: torch.Tensor, freqs: torch.Tensor, tx_elem: torch.Tensor,
+                          precision: int = SYNTH_FP32, out=None, stream=None) -> torch.Tensor:
+    """H(f) [F, n_rx, Nt] complex64 with per-element reception: every receiver
+    of the trace is one receive element and its row sums its own paths."""
+    F, Nt, Nr = int(freqs.numel()), int(tx_elem.shape[0]), int(pl.info()["n_rx"])
+    H = out if out is not None else torch.empty((F, Nr, Nt), dtype=torch.complex64, device=_dev())
+    g = gains if gains.numel() else torch.empty(1, dtype=torch.complex64, device=_dev())
+    _check(_L().sbr_synthesize_H_elements(pl.handle, _ptr(g), _ptr(freqs), F, _ptr(tx_elem), Nt,
+                                          int(precision), _ptr(H), _stream(stream)))
     return H
 
 

@@ -21,7 +21,7 @@ TRACE_COUNT_VISITS = 2
 EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_count", "sbr_launch_dirs", "sbr_build_bvh", "sbr_bvh_free",
            "sbr_bvh_query", "sbr_trace", "sbr_trace_stats", "sbr_trace_free", "sbr_paths",
            "sbr_path_query", "sbr_path_export", "sbr_path_list_free", "sbr_path_gains",
-           "sbr_synthesize_H", "sbr_pdp_angles", "sbr_capacity", "sbr_capacity_noalloc",
+           "sbr_synthesize_H", "sbr_synthesize_H_elements", "sbr_pdp_angles", "sbr_capacity", "sbr_capacity_noalloc",
            "sbr_batch_create", "sbr_batch_run", "sbr_batch_query", "sbr_batch_export", "sbr_batch_free",
            "sbr_batch_tune", "sbr_surrogate_targets", "sbr_mlp_create", "sbr_mlp_train_step",
            "sbr_mlp_predict", "sbr_mlp_param_count", "sbr_mlp_params", "sbr_mlp_status", "sbr_mlp_free",
@@ -134,6 +134,8 @@ def load() -> C.CDLL:
     L.sbr_path_gains.argtypes = [p, p, i32, p, i32, p, p, i32, p, p]
     L.sbr_synthesize_H.restype = st
     L.sbr_synthesize_H.argtypes = [p, p, p, i32, p, i32, p, i32, i32, i32, p, p]
+    L.sbr_synthesize_H_elements.restype = st
+    L.sbr_synthesize_H_elements.argtypes = [p, p, p, i32, p, i32, i32, p, p]
     L.sbr_pdp_angles.restype = st
     L.sbr_pdp_angles.argtypes = [p, p, i32, i32, f64, f64, i32, p, p, p]
     L.sbr_capacity.restype = st

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -426,6 +427,21 @@ sbr_status sbr_synthesize_H(const sbr_path_list* pl, const void* gains, const do
             set_error("unknown precision %d", precision);
             return SBR_ERR_INVALID_ARG;
     }
+}
+
+sbr_status sbr_synthesize_H_elements(const sbr_path_list* pl, const void* gains, const double* freqs_hz,
+                                     int32_t F, const double* tx_elem, int32_t Nt, int32_t precision,
+                                     void* H, void* stream) {
+    clear_error();
+    SBR_CHECK_ARG(pl != nullptr, "path list");
+    SBR_SAME_DEVICE(pl);
+    SBR_CHECK_ARG(F >= 1 && Nt >= 1, "F, Nt >= 1");
+    SBR_CHECK_ARG(F <= 65535 && pl->n_rx >= 1 && pl->n_rx <= 65535, "F <= 65535, 1 <= n_rx <= 65535");
+    SBR_CHECK_ARG(pl->P <= INT32_MAX, "P < 2^31");
+    SBR_CHECK_ARG((gains || pl->P == 0) && freqs_hz && tx_elem && H, "pointers (gains may be NULL without paths)");
+    SBR_CHECK_ARG(precision == SBR_SYNTH_FP64 || precision == SBR_SYNTH_FP32, "precision FP64 or FP32");
+    return synth_elements_run(pl, (const float2*)gains, freqs_hz, F, tx_elem, Nt, precision == SBR_SYNTH_FP64,
+                              (float2*)H, (cudaStream_t)stream);
 }
 
 sbr_status sbr_pdp_angles(const sbr_path_list* pl, const void* gains, int32_t F, int32_t f_index,

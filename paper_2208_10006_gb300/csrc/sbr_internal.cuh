@@ -214,6 +214,8 @@ sbr_status gains_run(const sbr_path_list* pl, const sbr_material* mats, int32_t 
 sbr_status synth_simt_run(const sbr_path_list* pl, const float2* g, const double* freqs, int32_t F,
                           const double* tx_elem, int32_t Nt, const double* rx_elem, int32_t Nr,
                           int32_t rx_index, bool fp64, float2* H, cudaStream_t s);
+sbr_status synth_elements_run(const sbr_path_list* pl, const float2* g, const double* freqs, int32_t F,
+                              const double* tx_elem, int32_t Nt, bool fp64, float2* H, cudaStream_t s);
 sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* freqs, int32_t F,
                         const double* tx_elem, int32_t Nt, const double* rx_elem, int32_t Nr,
                         int32_t rx_index, float2* H, bool f16, cudaStream_t s);

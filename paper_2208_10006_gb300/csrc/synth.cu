@@ -134,7 +134,101 @@ k_synth(int32_t F, int32_t Nr, int32_t Nt, int32_t Pr, const int32_t* __restrict
 
 inline unsigned nb256(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + 255) / 256); }
 
+// per-element reception: element delays of every path (FP64),
+//   dt_np = |T_p - R_q| - L_n for the LoS path of element q (so that L_n + dt_np
+//   is the exact element-pair distance), |T_p - P1| - |T_0 - P1| otherwise
+__global__ void k_el_delays(int64_t P, const int32_t* __restrict__ rx, const int32_t* __restrict__ nb,
+                            const double* __restrict__ pts, const double* __restrict__ L, d3 T0,
+                            const double* __restrict__ rx_xyz, const double* __restrict__ tx_elem, int32_t Nt,
+                            double* __restrict__ dt) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P * Nt) return;
+    int64_t n = t / Nt;
+    int32_t p = (int32_t)(t - n * Nt);
+    d3 Tp = ld3(tx_elem + 3 * p);
+    double v;
+    if (nb[n] == 0) {
+        v = norm(Tp - ld3(rx_xyz + 3 * rx[n])) - L[n];
+    } else {
+        d3 P1 = ld3(pts + (n * kKmax) * 3);
+        v = norm(Tp - P1) - norm(T0 - P1);
+    }
+    dt[t] = v;
+}
+
+// H[f, q, :] = sum over element q's own paths n of w_n(f) exp(-j 2 pi f dt_np / c)
+template <class R>
+__global__ void __launch_bounds__(kSynthThreads)
+k_synth_el(int32_t F, int32_t Nq, int32_t Nt, int64_t P, const int32_t* __restrict__ rx_off,
+           const double* __restrict__ freqs, const typename Cplx<R>::T* __restrict__ w,
+           const R* __restrict__ dt, float2* __restrict__ H) {
+    using C2 = typename Cplx<R>::T;
+    __shared__ C2 s_w[kSynthThreads];
+    const int32_t p = blockIdx.x * kSynthThreads + threadIdx.x;
+    const int32_t q = blockIdx.y;
+    const int32_t f = blockIdx.z;
+    const R foc = (R)(freqs[f] / kC0);
+    const bool act = p < Nt;
+    const int32_t a0 = rx_off[q], a1 = rx_off[q + 1];
+    R acc_re = 0, acc_im = 0;
+    for (int32_t n0 = a0; n0 < a1; n0 += kSynthThreads) {
+        int32_t n = n0 + threadIdx.x;
+        if (n < a1) s_w[threadIdx.x] = w[(int64_t)f * P + n];
+        __syncthreads();
+        int32_t cnt = min(kSynthThreads, a1 - n0);
+        if (act) {
+            for (int32_t k = 0; k < cnt; ++k) {
+                R s, c;
+                sincospi_((R)-2 * foc * dt[(int64_t)(n0 + k) * Nt + p], &s, &c);
+                C2 ww = s_w[k];
+                acc_re += ww.x * c - ww.y * s;
+                acc_im += ww.x * s + ww.y * c;
+            }
+        }
+        __syncthreads();
+    }
+    if (act) H[((int64_t)f * Nq + q) * Nt + p] = make_float2((float)acc_re, (float)acc_im);
+}
+
 }  // namespace
+
+sbr_status synth_elements_run(const sbr_path_list* pl, const float2* g, const double* freqs, int32_t F,
+                              const double* tx_elem, int32_t Nt, bool fp64, float2* H, cudaStream_t s) {
+    const int64_t P = pl->P;
+    const int32_t Nq = pl->n_rx;
+    const int64_t Pp = std::max<int64_t>(P, 1);
+    double* dt;
+    double2* w;
+    SBR_TRY(dalloc_n(&dt, (size_t)Pp * Nt, s));
+    SBR_TRY(dalloc_n(&w, (size_t)Pp * F, s));
+    if (P > 0) {
+        d3 T0 = mk3(pl->tx[0], pl->tx[1], pl->tx[2]);
+        ::sbr::note_launch(), k_el_delays<<<nb256(P * Nt), 256, 0, s>>>(P, pl->rx, pl->nb, pl->pts, pl->L, T0,
+                                                                       pl->rx_xyz, tx_elem, Nt, dt);
+        ::sbr::note_launch(), k_prep_w<<<nb256(P * F), 256, 0, s>>>((int32_t)P, F, g, pl->L, freqs, w);
+        SBR_TRY_CUDA(cudaGetLastError());
+    }
+    dim3 grid((unsigned)((Nt + kSynthThreads - 1) / kSynthThreads), (unsigned)Nq, (unsigned)F);
+    if (fp64) {
+        ::sbr::note_launch(), k_synth_el<double><<<grid, kSynthThreads, 0, s>>>(F, Nq, Nt, Pp, pl->rx_off, freqs, w,
+                                                                               dt, H);
+    } else {
+        float* dtf;
+        float2* wf;
+        SBR_TRY(dalloc_n(&dtf, (size_t)Pp * Nt, s));
+        SBR_TRY(dalloc_n(&wf, (size_t)Pp * F, s));
+        ::sbr::note_launch(), k_convert<float><<<nb256(Pp * Nt), 256, 0, s>>>(dt, dtf, Pp * Nt);
+        ::sbr::note_launch(), k_convert2<float><<<nb256(Pp * F), 256, 0, s>>>(w, wf, Pp * F);
+        ::sbr::note_launch(), k_synth_el<float><<<grid, kSynthThreads, 0, s>>>(F, Nq, Nt, Pp, pl->rx_off, freqs, wf,
+                                                                              dtf, H);
+        dfree(dtf, s);
+        dfree(wf, s);
+    }
+    SBR_TRY_CUDA(cudaGetLastError());
+    dfree(dt, s);
+    dfree(w, s);
+    return SBR_OK;
+}
 
 sbr_status synth_prepare(const sbr_path_list* pl, const float2* g, const double* freqs, int32_t F,
                          const double* tx_elem, int32_t Nt, const double* rx_elem, int32_t Nr,

@@ -295,3 +295,73 @@ def test_export_into_pinned_host_buffers(sbr):
         assert torch.equal(pinned[k], v.cpu()), k
     with pytest.raises(ValueError):
         r["paths"].export(out={k: torch.empty(v.shape, dtype=v.dtype) for k, v in ex.items()})
+
+
+def _wide_rx_array(sc, n, spacing, extra=()):
+    """Receivers = the elements of a wide ULA (traced one by one), plus extra points."""
+    el = scenes.ula_y([8.5, 4.0, 2.5], n, spacing)   # above every furniture box (heights <= 2 m)
+    if len(extra):
+        el = np.concatenate([el, np.asarray(extra, np.float64).reshape(-1, 3)])
+    sc = dict(sc, rx=el, rx_valid=np.ones(len(el), bool), rx_elem=el)
+    return sc
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 5e-6), (1, 2e-5)])
+def test_per_element_synthesis_matches_oracle(sbr, precision, tol):
+    # a 24-element ULA of 5.75 m aperture, and one point outside the room (no paths)
+    sc = _wide_rx_array(scenes.config3(N=40, K=3, F=8, ny_tx=3, nz_tx=2), 24, 0.25,
+                        extra=[[12.0, 4.0, 1.5]])
+    r = sbr.run_scene(sc)
+    ex = to_numpy(r["export"])
+    d = r["dev"]
+    H = sbr.synthesize_H_elements(r["paths"], r["g"], d["freqs"], d["tx_elem"], precision).cpu().numpy()
+    assert H.shape == (8, 25, 6)
+    paths = dict(rx=ex["rx"], nb=ex["nb"], pts=ex["pts"], L=ex["L"])
+    g_ref = oracle.gains(sc, dict(rx=ex["rx"], nb=ex["nb"], seq=ex["seq"], pts=ex["pts"], L=ex["L"]))
+    Ho = oracle.synth_H_elements(paths, g_ref, sc["freqs"], sc["tx"], sc["tx_elem"], sc["rx_elem"])
+    err = np.abs(H - Ho).max() / np.abs(Ho).max()
+    print("per-element synthesis precision", precision, "max|dH|/max|H| =", err)
+    assert err < tol
+    # the receiver outside the room has no path and a zero row
+    assert not np.any(ex["rx"] == 24) and np.all(H[:, 24, :] == 0)
+    # the array is non-stationary: its elements do not all see the same surface sequences
+    sets = [frozenset(tuple(s[:m]) for s, m in zip(ex["seq"][ex["rx"] == q], ex["nb"][ex["rx"] == q]))
+            for q in range(24)]
+    assert len(set(sets)) > 1
+
+
+def test_per_element_synthesis_free_space_is_the_spherical_wave(sbr):
+    tx = np.array([0.0, 0.0, 1.0])
+    rx_el = scenes.ula_y([6.0, 0.5, 1.2], 9, 0.75)       # 6 m aperture: distinct path loss per element
+    sc = dict(name="free", tri=np.zeros((0, 3, 3), np.float32), surface_id=np.zeros(0, np.int32),
+              materials=np.zeros((0, 3)), tx=tx, rx=rx_el, rx_valid=np.ones(len(rx_el), bool),
+              freqs=np.array([99e9, 100e9, 101e9]), gamma_db_km=np.zeros(3, np.float32),
+              disp_deg_km=np.zeros(3, np.float32), N=30, K=1, pol="V",
+              tx_elem=scenes.upa_yz(tx, 4, 4, 0.0015), rx_elem=rx_el)
+    r = sbr.run_scene(sc)
+    ex = to_numpy(r["export"])
+    assert ex["nb"].tolist() == [0] * len(rx_el)
+    d = r["dev"]
+    f = sc["freqs"]
+    d0 = np.linalg.norm(rx_el - tx, axis=1)
+    dist = np.linalg.norm(rx_el[:, None, :] - sc["tx_elem"][None, :, :], axis=2)
+    ref = (C0 / (4 * np.pi * f[:, None, None] * d0[None, :, None])) \
+        * np.exp(-2j * np.pi * f[:, None, None] * dist[None] / C0)
+    for prec, tol in ((0, 1e-6), (1, 1e-5)):
+        H = sbr.synthesize_H_elements(r["paths"], r["g"], d["freqs"], d["tx_elem"], prec).cpu().numpy()
+        assert np.abs(H - ref).max() < tol * np.abs(ref).max(), prec
+
+
+def test_per_element_synthesis_reduces_to_reference_point_form(sbr):
+    # one receive element at the traced receiver: both syntheses describe the same channel
+    sc = scenes.config3(N=40, K=3, F=6, ny_tx=4, nz_tx=2)
+    sc = dict(sc, rx_elem=sc["rx"][:1].copy())
+    r = sbr.run_scene(sc)
+    d = r["dev"]
+    He = sbr.synthesize_H_elements(r["paths"], r["g"], d["freqs"], d["tx_elem"], 0).cpu().numpy()
+    Hr = sbr.synthesize_H(r["paths"], r["g"], d["freqs"], d["tx_elem"], d["rx_elem"], 0, 0).cpu().numpy()
+    assert He.shape == Hr.shape == (6, 1, 8)
+    assert np.abs(He - Hr).max() <= 1e-6 * np.abs(Hr).max()
+    for bad in (dict(precision=2), dict(precision=3)):
+        with pytest.raises(sbr.SbrError):
+            sbr.synthesize_H_elements(r["paths"], r["g"], d["freqs"], d["tx_elem"], **bad)
