@@ -492,7 +492,85 @@ def bench_synthesis(sbr, torch, flush, peaks, peak_src, args):
         trend["%dx%d" % (n, n)] = [float(x) for x in sbr.capacity(Hn, sc["snr_db"]).cpu()]
         del Hn
     out["capacity_vs_tx_array"] = {"snr_db": [float(s) for s in sc["snr_db"]], "bits_per_s_per_hz": trend}
+    del pl, g, tr, bvh
+    out["per_element_reception"] = bench_per_element(sbr, torch, args)
     return out
+
+
+def bench_per_element(sbr, torch, args):
+    """Per-element reception on the indoor MIMO scene with a wide Rx array
+    (64-element ULA at 8 cm, 5 m aperture; Fig. 11): every element traced as a
+    receiver and its H row synthesised from its own paths, against the
+    reference-point form (one traced receiver, near-field element corrections)."""
+    sc = scenes.config3(rx_spacing=0.08)
+    d = sbr.scene_to_device(sc)
+    bvh = sbr.build_bvh(d["tri"], d["surface_id"], d["S"])
+    rx_el = torch.as_tensor(sc["rx_elem"], dtype=torch.float64, device="cuda")
+    F, Nr, Nt = len(sc["freqs"]), len(sc["rx_elem"]), len(sc["tx_elem"])
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return r, statistics.median(ts)
+
+    def chan(rx, lg=0):
+        for _ in range(4):
+            tr = sbr.trace(bvh, d["tx"], rx, sc["N"], sc["K"], table_log2=lg)
+            st = tr.stats(check=False)
+            if st["status"] != 3:
+                break
+            lg = st["table_log2"] + 1
+        pl = sbr.paths(tr, bvh)
+        return pl, sbr.path_gains(pl, d["mats"], d["freqs"], d["gamma"], d["disp"], d["pol"])
+
+    (pl_e, g_e), ms_chan_e = timed(lambda: chan(rx_el))
+    (pl_r, g_r), ms_chan_r = timed(lambda: chan(d["rx"]))
+    H_e, ms_syn_e = timed(lambda: sbr.synthesize_H_elements(pl_e, g_e, d["freqs"], d["tx_elem"], sbr.SYNTH_FP32))
+    H_r, ms_syn_r = timed(lambda: sbr.synthesize_H(pl_r, g_r, d["freqs"], d["tx_elem"], rx_el, 0,
+                                                    sbr.SYNTH_FP16X3))
+    # FP32 summation against FP64 on 64 of the subcarriers
+    sel = torch.arange(0, F, F // 64, device="cuda")
+    fr64 = d["freqs"][sel].contiguous()
+    g64 = g_e[:, sel].contiguous() if pl_e.n else g_e
+    H64 = sbr.synthesize_H_elements(pl_e, g64, fr64, d["tx_elem"], sbr.SYNTH_FP64)
+    H32 = sbr.synthesize_H_elements(pl_e, g64, fr64, d["tx_elem"], sbr.SYNTH_FP32)
+    err = float((H32 - H64).abs().max() / H64.abs().max())
+    ex = {k: v.cpu().numpy() for k, v in pl_e.export().items()}
+    nb, rxi, seq = ex["nb"], ex["rx"], ex["seq"]
+    n_paths = np.bincount(rxi, minlength=Nr)
+    los = np.zeros(Nr, bool)
+    los[rxi[nb == 0]] = True
+
+    def port_power_db(H):   # received power per Rx port, Tx ports combined with phase (mean over f)
+        return 10.0 * torch.log10((H.abs() ** 2).sum(2).mean(0)).cpu().numpy()
+
+    pe, pr = port_power_db(H_e), port_power_db(H_r)
+    C_e = [float(x) for x in sbr.capacity(H_e, sc["snr_db"]).cpu()]
+    C_r = [float(x) for x in sbr.capacity(H_r, sc["snr_db"]).cpu()]
+    terms = float(F) * Nt * pl_e.n
+    return {"workload": "indoor_100GHz_5736tri_N632_K4_UPA16x16_wideULA64_8cm_F1024",
+            "H_shape": [F, Nr, Nt], "paths_per_element": {"min": int(n_paths.min()), "max": int(n_paths.max()),
+                                                           "mean": float(n_paths.mean())},
+            "elements_with_los": int(los.sum()),
+            "distinct_path_sets": len({frozenset(tuple(s[:m]) for s, m in zip(seq[rxi == q], nb[rxi == q]))
+                                       for q in range(Nr)}),
+            "port_power_db": {"per_element": {"range": float(pe.max() - pe.min()), "std": float(pe.std())},
+                              "reference_point": {"range": float(pr.max() - pr.min()), "std": float(pr.std())},
+                              "per_element_profile": [round(float(x), 2) for x in pe]},
+            "capacity_bits_per_s_per_hz": {"snr_db": [float(s) for s in sc["snr_db"]],
+                                           "per_element": C_e, "reference_point": C_r},
+            "ms": {"trace_paths_gains_per_element": ms_chan_e, "trace_paths_gains_reference_point": ms_chan_r,
+                   "synth_per_element_fp32": ms_syn_e, "synth_reference_point_fp16x3": ms_syn_r},
+            "synth_per_element_Gterms_per_s": terms / (ms_syn_e * 1e-3) / 1e9,
+            "fp32_max_abs_err_vs_fp64_over_max": err}
 
 
 def bench_batched(sbr, torch, args):

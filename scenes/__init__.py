@@ -229,7 +229,7 @@ def config2(N: int = 1000, K: int = 6, nx: int = 8, ny: int = 5, sub: int = 11,
 
 def config3(N: int = 632, K: int = 4, n_furniture: int = 46, wall_sub: int = 8,
             box_sub: int = 3, F: int = 1024, ny_tx: int = 16, nz_tx: int = 16,
-            n_rx: int = 64, seed: int = 3):
+            n_rx: int = 64, seed: int = 3, rx_spacing: float = None):
     """Indoor massive MIMO at 100 GHz (seed 3).
 
     Room [0,10]x[0,8]x[0,3]: 6 surfaces (x-, x+, y-, y+, ceiling z+, floor z-),
@@ -241,7 +241,8 @@ def config3(N: int = 632, K: int = 4, n_furniture: int = 46, wall_sub: int = 8,
     Per surface (after the geometry): material type ~ integers(0,3) from the
     config-2 types, roughness U(0.05,0.3) mm. Tx: ny_tx x nz_tx UPA in the y-z
     plane centred at (0.5,4.0,2.0); Rx: n_rx ULA along y centred at
-    (8.5,3.0,1.2); spacing lambda/2 at 100 GHz. Frequencies
+    (8.5,3.0,1.2); spacing lambda/2 at 100 GHz (the Rx ULA takes rx_spacing
+    instead when given: a wide array whose elements see different paths). Frequencies
     f_k = 100 GHz + (k - F/2) * 10 GHz / F. gamma(f) = 0.5 + 0.1*(f-100 GHz)/5 GHz
     dB/km (synthetic stand-in). SNR 0:5:30 dB."""
     rng = np.random.default_rng(seed)
@@ -250,7 +251,7 @@ def config3(N: int = 632, K: int = 4, n_furniture: int = 46, wall_sub: int = 8,
     tx_c = np.array([0.5, 4.0, 2.0])
     rx_c = np.array([8.5, 3.0, 1.2])
     tx_elem = upa_yz(tx_c, ny_tx, nz_tx, d)
-    rx_elem = ula_y(rx_c, n_rx, d)
+    rx_elem = ula_y(rx_c, n_rx, d if rx_spacing is None else rx_spacing)
     groups = [g for _, g in _box_faces((0, 0, 0), (10, 8, 3), wall_sub,
                                        faces=("x-", "x+", "y-", "y+", "z+", "z-"))]
     elems = np.concatenate([tx_elem, rx_elem])

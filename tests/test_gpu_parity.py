@@ -39,6 +39,8 @@ SCENES = {
     "urban_small": lambda: scenes.config2(N=60, K=3, nx=2, ny=2, sub=3, ground_sub=6, rx_grid=6),
     "urban_med": lambda: scenes.config2(N=150, K=4, nx=3, ny=3, sub=4, ground_sub=8, rx_grid=8),
     "indoor_small": lambda: scenes.config3(N=40, K=3, F=8),
+    "indoor_small_dispersive": lambda: dict(scenes.config3(N=40, K=3, F=8),
+                                            disp_deg_km=np.linspace(-50.0, 80.0, 8).astype(np.float32)),
 }
 
 

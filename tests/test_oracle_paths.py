@@ -168,6 +168,22 @@ def test_friis_slope_and_absorption_linear_in_length():
     assert abs((vals[1] - vals[0]) + 20) < 1e-9 and abs((vals[2] - vals[1]) + 20) < 1e-9
 
 
+def test_dispersion_rotates_the_phase_by_phi_times_length():
+    # specific dispersion phi (deg/km) over the path length L: a phase of -phi L / 1000 degrees,
+    # magnitude unchanged; a quarter, half and full turn over the LoS length
+    sc = _empty_scene(250.0, 15.0)
+    r0 = oracle.run(sc)
+    L = r0["paths"]["L"][0]
+    g0 = r0["g"][0, 0]
+    for turn, factor in ((0.25, -1j), (0.5, -1.0), (1.0, 1.0)):
+        phi = 360.0 * turn / (L / 1000.0)
+        sc["disp_deg_km"] = np.array([phi], np.float32)
+        g = oracle.run(sc)["g"][0, 0]
+        # phi is stored in float32: allow its rounding (2^-24 relative) in the phase
+        assert abs(g - g0 * factor) <= abs(g0) * (1e-12 + 2 * np.pi * turn * 2.0 ** -23)
+        assert abs(abs(g) - abs(g0)) <= 1e-12 * abs(g0)
+
+
 @pytest.mark.parametrize("pol", ["V", "H"])
 @pytest.mark.parametrize("make", [scenes.config1, scenes.corner_reflector])
 def test_reciprocity(pol, make):
