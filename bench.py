@@ -11,7 +11,7 @@ ray-bounce is one closest-hit query plus the reception test of one segment.
 The same line carries the H(f) synthesis throughput (H tensors/s) of the
 indoor MIMO workload (16x16 UPA to 64-ULA, 1024 subcarriers, H [1024, 64,
 256]) in each precision form, the live roofline of the dominant kernel
-(the bounce kernel), the oracle's CPU throughput on a bounded sample, an
+(the depth-first trace kernel), the oracle's CPU throughput on a bounded sample, an
 end-to-end number through host buffers, clocks sampled during the timed
 region and the number of library kernels launched.
 
@@ -44,6 +44,13 @@ METRIC = "Mray-bounces/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 RAY_REC_BYTES = 64      # one queued ray record (origin, direction, L, id, last surface)
+# algorithmic HBM bytes of one ray-bounce of the trace: the ray state (a 64 B
+# record) read at the start of the segment and written for the next one
+ALG_BYTES_PER_RAY_BOUNCE = 2 * RAY_REC_BYTES
+# DRAM bytes of one k_trace_df launch on this workload, from one ncu capture of
+# the launch (dram__bytes_read.sum + dram__bytes_write.sum); None if not measured
+# for the kernel as it stands
+TRACE_DRAM_BYTES = None
 SEQ_BYTES = 4           # surface id appended per reflection
 DIR_BYTES = 24          # launch direction of a ray, double-float
 
@@ -378,13 +385,20 @@ def run_gpu(args):
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scenes.config2(), budget_s=args.cpu_budget)
 
-    achieved = bounce_bytes / (bounce_ms / 1e3) / 1e9
+    # the survey's algorithmic figure: 128 B of ray state per ray-bounce; the
+    # depth-first kernel keeps the ray state in registers, so what it moves
+    # through memory (streamed_bytes) is far below it
+    achieved = ALG_BYTES_PER_RAY_BOUNCE * rb / (bounce_ms / 1e3) / 1e9
     hbm = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
     roof = {"kernel": "k_trace_df", "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+            "unit": "GB/s", "frac": achieved / hbm, "traffic": TRACE_DRAM_BYTES,
             "peak_source": peak_src,
             "schedule": "depth first from bounce 0 (one launch per trace)",
-            "algorithmic_bytes": "24 B launch direction per ray + 4 B surface id per reflection, per launch",
+            "algorithmic_bytes": "128 B ray state (64 B read + 64 B written) per ray-bounce, "
+                                 "x ray-bounces per launch",
+            "algorithmic_bytes_per_launch": ALG_BYTES_PER_RAY_BOUNCE * rb / args.steps,
+            "streamed_bytes_per_launch": bounce_bytes / args.steps,
+            "streamed_bytes": "24 B launch direction per ray + 4 B surface id per reflection",
             "avg_launch_ms": bounce_ms / args.steps,
             "kernel_share_of_step": bounce_ms / sum(times), "l2": l2}
     line = {
@@ -396,7 +410,7 @@ def run_gpu(args):
                    "rays": 10 * N * N + 2, "max_bounces": K, "triangles": int(len(sc["tri"])),
                    "receivers": int(len(sc["rx"])), "ray_bounces_per_step": rb // args.steps,
                    "step": "build_bvh+trace+paths+gains+pdp", "l2": "flushed (256 MB write) "
-                   "between timed steps; ray queues (640 MB) exceed L2",
+                   "between timed steps",
                    "parallelism": "dp%d (independent Tx per rank)" % world},
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -244,27 +244,57 @@ __global__ void k_emit(int64_t n, const int32_t* __restrict__ left, const int32_
 }
 
 // ---------------------------------------------------------------- triangles
-__global__ void k_tri_boxes(const float* __restrict__ tri, int64_t T, float* __restrict__ box) {
+// per face: bounding box, FP64 unit normal, and the (surface id, face id)
+// pair of the faces-per-surface sort; degenerate faces and surface ids out of
+// range set the status word
+__global__ void k_tri_prep(const float* __restrict__ tri, const int32_t* __restrict__ surf, int64_t T,
+                           int32_t S, float* __restrict__ box, double* __restrict__ nrm,
+                           uint32_t* __restrict__ key, uint32_t* __restrict__ val,
+                           unsigned int* __restrict__ status) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
+    float v[9];
+    for (int k = 0; k < 9; ++k) v[k] = tri[9 * t + k];
     for (int a = 0; a < 3; ++a) {
-        float x0 = tri[9 * t + a], x1 = tri[9 * t + 3 + a], x2 = tri[9 * t + 6 + a];
-        box[6 * t + a] = fminf(x0, fminf(x1, x2));
-        box[6 * t + 3 + a] = fmaxf(x0, fmaxf(x1, x2));
+        box[6 * t + a] = fminf(v[a], fminf(v[3 + a], v[6 + a]));
+        box[6 * t + 3 + a] = fmaxf(v[a], fmaxf(v[3 + a], v[6 + a]));
     }
-}
-
-__global__ void k_tri_normals(const float* __restrict__ tri, int64_t T, double* __restrict__ nrm,
-                              unsigned int* __restrict__ status) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    d3 v0 = mk3(tri[9 * t], tri[9 * t + 1], tri[9 * t + 2]);
-    d3 v1 = mk3(tri[9 * t + 3], tri[9 * t + 4], tri[9 * t + 5]);
-    d3 v2 = mk3(tri[9 * t + 6], tri[9 * t + 7], tri[9 * t + 8]);
+    d3 v0 = mk3(v[0], v[1], v[2]), v1 = mk3(v[3], v[4], v[5]), v2 = mk3(v[6], v[7], v[8]);
     d3 c = cross(v1 - v0, v2 - v0);
     double l = norm(c);
-    if (!(l > 0.0) || !isfinite(l)) atomicOr(status, (unsigned)ST_NUMERIC);
+    bool bad = !(l > 0.0) || !isfinite(l);
     st3(nrm + 3 * t, c * (1.0 / l));
+    int32_t s = surf[t];
+    bad |= s < 0 || s >= S;
+    if (bad) atomicOr(status, (unsigned)ST_NUMERIC);
+    key[t] = (uint32_t)min(max(s, 0), S - 1);
+    val[t] = (uint32_t)t;
+}
+
+// A pinned host word and an event per thread and device: the result of the
+// input validation goes to the host while the rest of the build runs, and
+// the call waits for the validation kernel only.
+struct HostFlag {
+    unsigned* h = nullptr;
+    cudaEvent_t ev = nullptr;
+};
+
+sbr_status host_flag(HostFlag** out) {
+    constexpr int kMaxDev = 64;
+    thread_local HostFlag flags[kMaxDev];
+    int dev = 0;
+    SBR_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDev) {
+        set_error("device index %d out of range", dev);
+        return SBR_ERR_UNSUPPORTED;
+    }
+    HostFlag& f = flags[dev];
+    if (!f.h) {
+        SBR_TRY_CUDA(cudaMallocHost(&f.h, sizeof(unsigned)));
+        SBR_TRY_CUDA(cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming));
+    }
+    *out = &f;
+    return SBR_OK;
 }
 
 __global__ void k_tri_pack(const float* __restrict__ tri, const int32_t* __restrict__ surf,
@@ -283,17 +313,6 @@ __global__ void k_tri_pack(const float* __restrict__ tri, const int32_t* __restr
     df a = df_from_double(n0), bb = df_from_double(n1), cc = df_from_double(n2), dd = df_from_double(c);
     plane[2 * j] = make_float4(a.hi, bb.hi, cc.hi, dd.hi);
     plane[2 * j + 1] = make_float4(a.lo, bb.lo, cc.lo, dd.lo);
-}
-
-__global__ void k_copy_surf(const int32_t* __restrict__ surf, int64_t T, int32_t S,
-                            uint32_t* __restrict__ key, uint32_t* __restrict__ val,
-                            unsigned int* __restrict__ status) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    int32_t s = surf[t];
-    if (s < 0 || s >= S) atomicOr(status, (unsigned)ST_NUMERIC);
-    key[t] = (uint32_t)min(max(s, 0), S - 1);
-    val[t] = (uint32_t)t;
 }
 
 __global__ void k_surface_offsets(const uint32_t* __restrict__ key, int64_t T, int32_t S,
@@ -402,32 +421,30 @@ sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S
     SBR_TRY_CUDA(cudaMemcpyAsync(b->tri, tri, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, s));
     SBR_TRY_CUDA(cudaMemcpyAsync(b->surf, surf, sizeof(int32_t) * T, cudaMemcpyDeviceToDevice, s));
     float* box;
+    uint32_t *key, *val;
     SBR_TRY(dalloc_n(&box, 6 * T, s));
-    ::sbr::note_launch(), k_tri_boxes<<<blocks_for(T), kThreads, 0, s>>>(b->tri, T, box);
-    ::sbr::note_launch(), k_tri_normals<<<blocks_for(T), kThreads, 0, s>>>(b->tri, T, b->nrm, status);
+    SBR_TRY(dalloc_n(&key, T, s));
+    val = reinterpret_cast<uint32_t*>(b->s_tri);
+    ::sbr::note_launch(), k_tri_prep<<<blocks_for(T), kThreads, 0, s>>>(b->tri, b->surf, T, S, box, b->nrm, key, val,
+                                                                      status);
     SBR_TRY_CUDA(cudaGetLastError());
+    HostFlag* hf;
+    SBR_TRY(host_flag(&hf));
+    *hf->h = 0;
+    SBR_TRY_CUDA(cudaMemcpyAsync(hf->h, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    SBR_TRY_CUDA(cudaEventRecord(hf->ev, s));
     // relative box padding: 2^-20 of (|x| + 1) covers FP32 ray/box rounding
     SBR_TRY(build_lbvh(box, T, 1.0f / (1 << 20), tri_leaf_size(), &b->tree, b->d_depth, s));
     ::sbr::note_launch(), k_tri_pack<<<blocks_for(T), kThreads, 0, s>>>(b->tri, b->surf, b->nrm, b->tree.order, T,
                                                   b->tri_sorted, b->plane_sorted);
     // faces per surface, ascending face id (stable sort on the surface id)
-    uint32_t *key, *val;
-    SBR_TRY(dalloc_n(&key, T, s));
-    val = reinterpret_cast<uint32_t*>(b->s_tri);
-    ::sbr::note_launch(), k_copy_surf<<<blocks_for(T), kThreads, 0, s>>>(b->surf, T, S, key, val, status);
-    SBR_TRY_CUDA(cudaGetLastError());
     int bits = 1;
     while (bits < 31 && ((int64_t)1 << bits) < (int64_t)S) ++bits;
     SBR_TRY(radix_sort_pairs(key, val, T, bits, s));
     ::sbr::note_launch(), k_surface_offsets<<<blocks_for((int64_t)S + 1), kThreads, 0, s>>>(key, T, S, b->s_off);
     SBR_TRY_CUDA(cudaGetLastError());
-    uint32_t h_status = 0;
-    SBR_TRY_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    SBR_TRY_CUDA(cudaMemcpyAsync(b->tree.lo, b->tree.d_root, 3 * sizeof(float),
-                                 cudaMemcpyDeviceToHost, s));
-    SBR_TRY_CUDA(cudaMemcpyAsync(b->tree.hi, b->tree.d_root + 3, 3 * sizeof(float),
-                                 cudaMemcpyDeviceToHost, s));
-    SBR_TRY_CUDA(cudaStreamSynchronize(s));
+    SBR_TRY_CUDA(cudaEventSynchronize(hf->ev));
+    const unsigned h_status = *hf->h;
     dfree(box, s);
     dfree(key, s);
     dfree(status, s);

@@ -163,11 +163,11 @@ __global__ void k_compact_all(const __grid_constant__ CompactArgs a) {
     }
 }
 
-__global__ void k_rx_offsets(const int32_t* __restrict__ rx, int64_t P, int32_t n_rx,
+__global__ void k_rx_offsets(const int32_t* __restrict__ rx, const unsigned* __restrict__ P, int32_t n_rx,
                              int32_t* __restrict__ off) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r > n_rx) return;
-    int64_t lo = 0, hi = P;
+    int64_t lo = 0, hi = *P;
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
         if (rx[mid] < r) lo = mid + 1; else hi = mid;
@@ -275,12 +275,9 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
         SBR_TRY_CUDA(cudaMemcpyAsync(pos, valid, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
     }
     SBR_TRY(exclusive_scan_u32(pos, n, count, s));
-    SBR_TRY_CUDA(cudaMemcpyAsync(&h_count, count, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    SBR_TRY_CUDA(cudaStreamSynchronize(s));
-    const int64_t P = h_count;
-    pl->P = P;
-    pl->n_invalid = n - P;
-    int64_t Pp = std::max<int64_t>(P, 1);
+    // the list is sized for every key (P <= n), so compaction and the receiver
+    // offsets run before the host learns P: one wait for P and the offsets
+    const int64_t Pp = nn;
     SBR_TRY(dalloc_n(&pl->rx, Pp, s));
     SBR_TRY(dalloc_n(&pl->nb, Pp, s));
     SBR_TRY(dalloc_n(&pl->surf, Pp * kKmax, s));
@@ -309,12 +306,17 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
         ::sbr::note_launch(), k_compact_all<<<nblk(32 * n), kThreads, 0, s>>>(c);
         SBR_TRY_CUDA(cudaGetLastError());
     }
-    ::sbr::note_launch(), k_rx_offsets<<<nblk((int64_t)tr->n_rx + 1), kThreads, 0, s>>>(pl->rx, P, tr->n_rx, pl->rx_off);
+    ::sbr::note_launch(), k_rx_offsets<<<nblk((int64_t)tr->n_rx + 1), kThreads, 0, s>>>(pl->rx, count, tr->n_rx,
+                                                                                    pl->rx_off);
     SBR_TRY_CUDA(cudaGetLastError());
     pl->h_rx_off = new int32_t[tr->n_rx + 1];
+    SBR_TRY_CUDA(cudaMemcpyAsync(&h_count, count, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     SBR_TRY_CUDA(cudaMemcpyAsync(pl->h_rx_off, pl->rx_off, sizeof(int32_t) * (tr->n_rx + 1),
                                  cudaMemcpyDeviceToHost, s));
     SBR_TRY_CUDA(cudaStreamSynchronize(s));
+    const int64_t P = h_count;
+    pl->P = P;
+    pl->n_invalid = n - P;
     dfree(count, s); dfree(idx, s); dfree(perm, s); dfree(word, s); dfree(valid, s); dfree(pos, s);
     dfree(a.rx_o, s); dfree(a.nb_o, s); dfree(a.surf_o, s); dfree(a.face_o, s); dfree(a.pts_o, s);
     dfree(a.L_o, s); dfree(a.aod_o, s); dfree(a.aoa_o, s); dfree(a.ray_o, s); dfree(a.dist_o, s);

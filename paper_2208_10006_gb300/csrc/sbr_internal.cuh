@@ -100,7 +100,6 @@ struct BvhNodes {
     float4* nodes = nullptr;   // [n_nodes * 4]
     int32_t* order = nullptr;  // [n] sorted position -> primitive index
     int32_t n_nodes = 0;       // internal nodes (>= 1 when n >= 1)
-    float lo[3], hi[3];        // root bounds (host copy, valid after sync)
     float* d_root = nullptr;   // [6] root bounds on the device
 };
 // Build over n primitives given by boxes [n*6] (lo xyz, hi xyz) on the device.
