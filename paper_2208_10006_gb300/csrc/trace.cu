@@ -65,6 +65,11 @@ struct TraceArgs {
     const float2* dir_b;
     int N, K, bounce;
     int64_t R;
+    // launch order of the rays: the vertex and edge rays first, then the 20
+    // faces' interior rays face by face in the order face_order (their ids
+    // stay the geodesic ids)
+    int64_t pool_pre, pool_face;
+    uint8_t face_order[20];
     float tx_h[3], tx_l[3];
     const RayRec* qin;
     RayRec* qout;
@@ -79,6 +84,14 @@ struct TraceArgs {
     uint32_t ht_mask;
     TraceCountersDev* cnt;
 };
+
+// geodesic id of the i-th ray launched
+__device__ __forceinline__ uint32_t pool_ray(const TraceArgs& a, unsigned long long i) {
+    const int64_t r = (int64_t)i - a.pool_pre;
+    if (r < 0 || a.pool_face == 0) return (uint32_t)i;
+    const int64_t k = r / a.pool_face;
+    return (uint32_t)(a.pool_pre + (int64_t)a.face_order[k] * a.pool_face + (r - k * a.pool_face));
+}
 
 __device__ __forceinline__ float comp(float4 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 __device__ __forceinline__ float comp3(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
@@ -542,11 +555,11 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
             uint32_t ray;
             int prev;
             if (a.bounce == 0) {
-                ray = (uint32_t)i;
+                ray = pool_ray(a, i);
                 o = df3{df_make(a.tx_h[0], a.tx_l[0]), df_make(a.tx_h[1], a.tx_l[1]),
                         df_make(a.tx_h[2], a.tx_l[2])};
-                float4 da = __ldg(a.dir_a + i);
-                float2 db = __ldg(a.dir_b + i);
+                float4 da = __ldg(a.dir_a + ray);
+                float2 db = __ldg(a.dir_b + ray);
                 d = df3{df_make(da.x, da.w), df_make(da.y, db.x), df_make(da.z, db.y)};
                 L = df_make(0.f, 0.f);
                 prev = -1;
@@ -660,11 +673,11 @@ k_trace_df(const __grid_constant__ TraceArgs a) {
                 const unsigned long long i = base + __popc(need & ((1u << lane) - 1u));
                 if (i < n_in) {
                     if (a.bounce == 0) {
-                        ray = (uint32_t)i;
+                        ray = pool_ray(a, i);
                         o = df3{df_make(a.tx_h[0], a.tx_l[0]), df_make(a.tx_h[1], a.tx_l[1]),
                                 df_make(a.tx_h[2], a.tx_l[2])};
-                        float4 da = __ldg(a.dir_a + i);
-                        float2 db = __ldg(a.dir_b + i);
+                        float4 da = __ldg(a.dir_a + ray);
+                        float2 db = __ldg(a.dir_b + ray);
                         d = df3{df_make(da.x, da.w), df_make(da.y, db.x), df_make(da.z, db.y)};
                         L = df_make(0.f, 0.f);
                         prev = -1;
@@ -996,6 +1009,25 @@ __global__ void k_init_table(uint32_t* state, unsigned long long* val, size_t ca
     val[i] = ~0ull;
 }
 
+// Launch order of the face rays: by the height (z) of the face's centroid on
+// the icosahedron, lowest first. Rays toward the ground and the facades take
+// several reflections and rays toward the sky end after one segment; with the
+// sky last, the rays still in flight when the pool runs out are short, and
+// fewer SMs idle while the last warps drain.
+void set_pool_order(int N, TraceArgs* a) {
+    const Ico ico = make_ico();
+    a->pool_pre = 12 + 30 * (int64_t)(N - 1);
+    a->pool_face = (int64_t)(N - 1) * (N - 2) / 2;
+    int order[20];
+    double cz[20];
+    for (int f = 0; f < 20; ++f) {
+        order[f] = f;
+        cz[f] = ico.v[ico.f[f][0]][2] + ico.v[ico.f[f][1]][2] + ico.v[ico.f[f][2]][2];
+    }
+    std::stable_sort(order, order + 20, [&](int x, int y) { return cz[x] < cz[y]; });
+    for (int f = 0; f < 20; ++f) a->face_order[f] = (uint8_t)order[f];
+}
+
 int trace_grid(bool count) {
     static int grid[2] = {0, 0};
     if (!grid[count]) {
@@ -1105,8 +1137,10 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     RayRec *q0 = nullptr, *q1 = nullptr;
     int32_t* seq = nullptr;
     if (K > 0) {
-        SBR_TRY(dalloc_n(&q0, (size_t)R, s));
-        SBR_TRY(dalloc_n(&q1, (size_t)R, s));
+        if (tr->df_from > 0) {   // ray queues of the breadth-first bounces
+            SBR_TRY(dalloc_n(&q0, (size_t)R, s));
+            SBR_TRY(dalloc_n(&q1, (size_t)R, s));
+        }
         SBR_TRY(dalloc_n(&seq, (size_t)R * K, s));
         SBR_TRY(dalloc_n(&tr->seqf, (size_t)R * K, s));
     }
@@ -1126,6 +1160,7 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     a.N = p.subdiv_N;
     a.K = K;
     a.R = R;
+    set_pool_order(p.subdiv_N, &a);
     for (int k = 0; k < 3; ++k) {
         df x = df_from_double(p.tx[k]);
         a.tx_h[k] = x.hi;
