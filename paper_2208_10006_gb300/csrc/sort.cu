@@ -140,9 +140,13 @@ sbr_status scan_rec(uint32_t* data, int64_t n, cudaStream_t s) {
 }
 
 // Whole sort of a small array in one block: keys and values live in shared
-// memory and every 8-bit pass runs in the same launch (same stable ranking as
-// the multi-block path: round, warp, lane order).
+// memory and every 8-bit pass runs in the same launch. Warp w owns the
+// contiguous chunk [w c, (w+1) c) of the array, so a pass needs three block
+// barriers: per-warp digit counts, their scan (digit-major over warps, then
+// over digits), and the stable scatter, where each warp walks its chunk in
+// rounds of 32 and ranks equal digits of a round by lane.
 constexpr int kSmallThreads = 1024;
+constexpr int kSmallWarps = kSmallThreads / 32;
 constexpr int kSmallMax = 12288;  // 2 x 2 x 4 B x 12288 = 192 KB of shared memory
 
 __global__ void __launch_bounds__(kSmallThreads)
@@ -152,56 +156,66 @@ k_sort_small(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int n, in
     uint32_t* va = sm + kSmallMax;
     uint32_t* kb = sm + 2 * kSmallMax;
     uint32_t* vb = sm + 3 * kSmallMax;
-    __shared__ uint32_t s_hist[256];
-    __shared__ uint32_t s_warp[kSmallThreads / 32][256];
-    __shared__ uint32_t s_run[256];
+    __shared__ uint32_t s_cnt[kSmallWarps][256];   // per warp and digit: count, then output position
+    __shared__ uint32_t s_wsum[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    const int chunk = ((n + kSmallWarps - 1) / kSmallWarps + 31) & ~31;
+    const int c0 = min(n, warp * chunk), c1 = min(n, c0 + chunk);
     for (int i = tid; i < n; i += kSmallThreads) { ka[i] = keys[i]; va[i] = vals[i]; }
     __syncthreads();
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
-        if (tid < 256) s_hist[tid] = 0;
-        __syncthreads();
-        for (int i = tid; i < n; i += kSmallThreads) atomicAdd(&s_hist[(ka[i] >> shift) & 255u], 1u);
-        __syncthreads();
-        if (tid == 0) {  // exclusive scan of 256 counts
-            uint32_t run = 0;
-            for (int d = 0; d < 256; ++d) { uint32_t c = s_hist[d]; s_run[d] = run; run += c; }
+        for (int d = lane; d < 256; d += 32) s_cnt[warp][d] = 0;
+        __syncwarp();
+        for (int base = c0; base < c1; base += 32) {
+            const int i = base + lane;
+            const uint32_t d = i < c1 ? ((ka[i] >> shift) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (d < 256u && (peers & lt) == 0) s_cnt[warp][d] += __popc(peers);
+            __syncwarp();
         }
         __syncthreads();
-        for (int base = 0; base < n; base += kSmallThreads) {
-            for (int w = 0; w < kSmallThreads / 32; ++w)
-                if (tid < 256) s_warp[w][tid] = 0;
-            __syncthreads();
-            int i = base + tid;
-            bool valid = i < n;
-            uint32_t k = valid ? ka[i] : 0u, v = valid ? va[i] : 0u;
-            uint32_t d = valid ? ((k >> shift) & 255u) : 256u;
-            unsigned peers = __match_any_sync(0xffffffffu, d);
-            int rank = __popc(peers & lt);
-            if (valid && rank == 0) s_warp[warp][d] = __popc(peers);
-            __syncthreads();
-            if (tid < 256) {
-                uint32_t run = s_run[tid];
-                for (int w = 0; w < kSmallThreads / 32; ++w) {
-                    uint32_t c = s_warp[w][tid];
-                    s_warp[w][tid] = run;
-                    run += c;
-                }
-                s_run[tid] = run;
+        uint32_t run = 0, incl = 0;
+        if (tid < 256) {
+            for (int w = 0; w < kSmallWarps; ++w) {
+                const uint32_t c = s_cnt[w][tid];
+                s_cnt[w][tid] = run;
+                run += c;
             }
-            __syncthreads();
+            incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) s_wsum[warp] = incl;
+        }
+        __syncthreads();
+        if (tid < 256) {
+            uint32_t off = incl - run;
+            for (int k = 0; k < warp; ++k) off += s_wsum[k];
+            for (int w = 0; w < kSmallWarps; ++w) s_cnt[w][tid] += off;
+        }
+        __syncthreads();
+        for (int base = c0; base < c1; base += 32) {
+            const int i = base + lane;
+            const bool valid = i < c1;
+            const uint32_t k = valid ? ka[i] : 0u, v = valid ? va[i] : 0u;
+            const uint32_t d = valid ? ((k >> shift) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
             if (valid) {
-                uint32_t pos = s_warp[warp][d] + rank;
+                const uint32_t pos = s_cnt[warp][d] + __popc(peers & lt);
                 kb[pos] = k;
                 vb[pos] = v;
             }
-            __syncthreads();
+            __syncwarp();
+            if (valid && (peers & lt) == 0) s_cnt[warp][d] += __popc(peers);
+            __syncwarp();
         }
+        __syncthreads();
         uint32_t* t = ka; ka = kb; kb = t;
         t = va; va = vb; vb = t;
-        __syncthreads();
     }
     for (int i = tid; i < n; i += kSmallThreads) { keys[i] = ka[i]; vals[i] = va[i]; }
 }

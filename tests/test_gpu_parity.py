@@ -367,3 +367,14 @@ def test_per_element_synthesis_reduces_to_reference_point_form(sbr):
     for bad in (dict(precision=2), dict(precision=3)):
         with pytest.raises(sbr.SbrError):
             sbr.synthesize_H_elements(r["paths"], r["g"], d["freqs"], d["tx_elem"], **bad)
+
+
+@pytest.mark.parametrize("name", ["urban_small", "urban_med", "shoebox_K5", "indoor_small"])
+def test_path_list_is_in_key_order(sbr, name):
+    # paths come out sorted by (receiver, reflections, surface sequence), each key once;
+    # the per-receiver offsets follow that order
+    r = sbr.run_scene(SCENES[name]())
+    ex = to_numpy(r["export"])
+    keys = [(int(q), int(m)) + tuple(int(x) for x in s[:m]) for q, m, s in zip(ex["rx"], ex["nb"], ex["seq"])]
+    assert len(keys) > 10
+    assert all(a < b for a, b in zip(keys, keys[1:]))
