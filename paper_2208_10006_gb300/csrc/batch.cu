@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch_paths(const __grid_constant
         order[rank] = i;   // keys are distinct: ranks are a permutation
     }
     __syncthreads();
-    const RefineScene sc{J->tri, J->nrm, J->s_off, J->s_tri, J->S};
+    const RefineScene sc{J->tri, J->nrm, J->s_off, J->s_tri, J->S, J->nodes, J->tris};
     const d3 Tx = mk3(J->tx[0], J->tx[1], J->tx[2]);
     const d3 Rx = mk3(J->rx[0], J->rx[1], J->rx[2]);
     const int64_t rb = (int64_t)jl * a.path_cap;

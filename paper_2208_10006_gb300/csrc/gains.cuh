@@ -22,19 +22,23 @@ __device__ __forceinline__ cd cmul(cd a, cd b) { return cd{a.re * b.re - a.im * 
 __device__ __forceinline__ cd cadd(cd a, cd b) { return cd{a.re + b.re, a.im + b.im}; }
 __device__ __forceinline__ cd csub(cd a, cd b) { return cd{a.re - b.re, a.im - b.im}; }
 __device__ __forceinline__ cd cscale(cd a, double s) { return cd{a.re * s, a.im * s}; }
+// a / b as a conj(b) / |b|^2: one FP64 division (FP64 is a narrow pipe on this
+// GPU). The denominators here are cos + sqrt(eta - sin^2) and its TM form:
+// |b|^2 stays far inside the FP64 range for any physical permittivity,
+// conductivity and incidence angle.
 __device__ __forceinline__ cd cdiv(cd a, cd b) {
-    double s = fabs(b.re) + fabs(b.im);
-    double br = b.re / s, bi = b.im / s;
-    double d = br * br + bi * bi;
-    double ar = a.re / s, ai = a.im / s;
-    return cd{(ar * br + ai * bi) / d, (ai * br - ar * bi) / d};
+    const double inv = 1.0 / (b.re * b.re + b.im * b.im);
+    return cd{(a.re * b.re + a.im * b.im) * inv, (a.im * b.re - a.re * b.im) * inv};
 }
-// principal square root
+// principal square root; the larger part is sqrt((|z| + |re|) / 2) and the
+// other im / (2 that), so neither cancels
 __device__ __forceinline__ cd csqrt_(cd z) {
-    double r = hypot(z.re, z.im);
-    double x = sqrt(0.5 * (r + z.re));
-    double y = sqrt(fmax(0.5 * (r - z.re), 0.0));
-    return cd{x, z.im < 0.0 ? -y : y};
+    const double r = sqrt(z.re * z.re + z.im * z.im);
+    if (r == 0.0) return cd{0.0, 0.0};
+    const double u = sqrt(0.5 * (r + fabs(z.re)));
+    const double v = 0.5 * fabs(z.im) / u;
+    if (z.re >= 0.0) return cd{u, z.im < 0.0 ? -v : v};
+    return cd{v, z.im < 0.0 ? -u : u};
 }
 
 // m reflections off surfaces surf[0..m), unfolded length Lp, polarimetric

@@ -73,6 +73,8 @@ struct RefineArgs {
     const int32_t* s_off;
     const int32_t* s_tri;
     int32_t S;
+    const float4* nodes;   // scene BVH and its BVH-order faces (containment queries)
+    const float4* tris;
     double tx[3];
     const double* rx;
     const int32_t* seqf;   // [K][R] faces hit by each ray (refinement hints), or null
@@ -104,7 +106,7 @@ __global__ void k_refine(const __grid_constant__ RefineArgs a) {
     int m = (int)key[1];
     int32_t seq[kKmax];
     for (int k = 0; k < kKmax; ++k) seq[k] = (int32_t)key[2 + k];
-    const RefineScene sc{a.tri, a.nrm, a.s_off, a.s_tri, a.S};
+    const RefineScene sc{a.tri, a.nrm, a.s_off, a.s_tri, a.S, a.nodes, a.tris};
     const RefineOut o{a.nb_o, a.surf_o, a.face_o, a.pts_o, a.L_o, a.aod_o, a.aoa_o, a.ray_o, a.dist_o, a.jones_o};
     bool ok = refine_key<false>(lane, m, seq, v, sc, mk3(a.tx[0], a.tx[1], a.tx[2]), ld3(a.rx + 3 * rx_id), o, i);
     if (lane != 0) return;
@@ -130,7 +132,7 @@ __global__ void k_refine_solo(const __grid_constant__ RefineArgs a) {
         m = (int)key[1];
         for (int k = 0; k < kKmax; ++k) seq[k] = (int32_t)key[2 + k];
     }
-    const RefineScene sc{a.tri, a.nrm, a.s_off, a.s_tri, a.S};
+    const RefineScene sc{a.tri, a.nrm, a.s_off, a.s_tri, a.S, a.nodes, a.tris};
     const RefineOut o{a.nb_o, a.surf_o, a.face_o, a.pts_o, a.L_o, a.aod_o, a.aoa_o, a.ray_o, a.dist_o, a.jones_o};
     const int32_t* hint = a.seqf + (uint32_t)(v & 0xffffffffull);
     const d3 Rx = have ? ld3(a.rx + 3 * rx_id) : mk3(0, 0, 0);
@@ -244,6 +246,8 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     a.s_off = b->s_off;
     a.s_tri = b->s_tri;
     a.S = b->S;
+    a.nodes = b->T > 0 ? b->tree.nodes : nullptr;
+    a.tris = b->tri_sorted;
     for (int k = 0; k < 3; ++k) a.tx[k] = tr->params.tx[k];
     a.rx = tr->rx;
     a.seqf = tr->seqf;

@@ -71,8 +71,12 @@ k_pdp(const int32_t* __restrict__ rx_off, const double* __restrict__ L, const do
     cr = block_sum(cr, sh); ci = block_sum(ci, sh);
     a1 = block_sum(a1, sh); a2 = block_sum(a2, sh); a3 = block_sum(a3, sh); a4 = block_sum(a4, sh);
     __syncthreads();
-    for (int k = threadIdx.x; k < n_bins; k += blockDim.x)
-        pdp[(int64_t)r * n_bins + k] = acc[k] > 0.0 ? (float)(10.0 * log10(acc[k])) : -INFINITY;
+    // a bin holds a sum of powers (>= 0): its bit pattern is positive exactly when
+    // it is non-zero, which keeps the test of the (mostly empty) bins off the FP64 pipe
+    for (int k = threadIdx.x; k < n_bins; k += blockDim.x) {
+        const double v = acc[k];
+        pdp[(int64_t)r * n_bins + k] = __double_as_longlong(v) > 0 ? (float)(10.0 * log10(v)) : -INFINITY;
+    }
     if (threadIdx.x == 0) {
         double* o = stats + (int64_t)r * SBR_NSTATS;
         if (o1 == o0 || !(sp > 0.0)) {

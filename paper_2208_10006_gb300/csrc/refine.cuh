@@ -98,7 +98,59 @@ struct RefineScene {
     const int32_t* s_off;
     const int32_t* s_tri;
     int32_t S;
+    const float4* nodes;   // scene BVH (null: containers are found by scanning the surface)
+    const float4* tris;    // BVH-order faces: v0 (w = surface id bits), v1 (w = face id bits), v2
 };
+
+// Lowest-id face of surface s that contains p by the scan's rule (the FP32
+// screen, else the FP64 test with tolerance 1e-9), from a point query of the
+// scene BVH instead of a scan of the surface: a face that passes the rule holds
+// p within 1e-9 of its barycentrics, far inside the padding of its BVH box, so
+// the query meets every such face. -1: none; -2: the query's stack overflowed
+// (the caller then scans the surface).
+constexpr int kFindStack = 64;
+
+__device__ __forceinline__ bool in_box(float3 p, float lx, float ly, float lz, float hx, float hy, float hz) {
+    return p.x >= lx && p.x <= hx && p.y >= ly && p.y <= hy && p.z >= lz && p.z <= hz;
+}
+
+__device__ int32_t bvh_find_face(const RefineScene& sc, int s, d3 P) {
+    const float3 pf = make_float3((float)P.x, (float)P.y, (float)P.z);
+    int32_t best = 0x7fffffff;
+    int32_t stack[kFindStack];
+    int sp = 0;
+    int32_t ref = 0;
+    for (;;) {
+        if (ref >= 0) {
+            const float4* nd = sc.nodes + 4 * (int64_t)ref;
+            const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+            const int32_t r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
+            const bool h0 = in_box(pf, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y);
+            const bool h1 = in_box(pf, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w) && r1 != r0;
+            if (h0 && h1) {
+                if (sp == kFindStack) return -2;
+                stack[sp++] = r1;
+                ref = r0;
+                continue;
+            }
+            if (h0) { ref = r0; continue; }
+            if (h1) { ref = r1; continue; }
+        } else {
+            const int32_t first = leaf_first(ref), cnt = leaf_count(ref);
+            for (int32_t j = first; j < first + cnt; ++j) {
+                if (__float_as_int(__ldg(sc.tris + 3 * (int64_t)j).w) != s) continue;
+                const int32_t face = __float_as_int(__ldg(sc.tris + 3 * (int64_t)j + 1).w);
+                if (face >= best) continue;
+                const float* v = sc.tri + 9 * (int64_t)face;
+                const int scr = screen_in_tri(v, pf);
+                if (scr > 0 || (scr == 0 && point_in_tri(v, P, 1e-9))) best = face;
+            }
+        }
+        if (sp == 0) break;
+        ref = stack[--sp];
+    }
+    return best == 0x7fffffff ? -1 : best;
+}
 
 // outputs of one refined key, written at record i (lane 0, valid keys only)
 struct RefineOut {
@@ -177,8 +229,14 @@ __device__ bool refine_key(int lane, int m, const int32_t* seq, unsigned long lo
             bool need = false;
             if (act) {
                 const int32_t h = hint ? hint[(int64_t)(k - 1) * hint_stride] : -1;
-                if (h >= 0 && bary_margin(sc.tri + 9 * (int64_t)h, P[k]) >= 1e-6) found = h;
-                else need = true;
+                if (h >= 0 && bary_margin(sc.tri + 9 * (int64_t)h, P[k]) >= 1e-6) {
+                    found = h;
+                } else if (sc.nodes) {
+                    found = bvh_find_face(sc, s, P[k]);
+                    need = found == -2;
+                } else {
+                    need = true;
+                }
             }
             unsigned nm = __ballot_sync(0xffffffffu, need);
             const double px = act ? P[k].x : 0.0, py = act ? P[k].y : 0.0, pz = act ? P[k].z : 0.0;
@@ -220,6 +278,16 @@ __device__ bool refine_key(int lane, int m, const int32_t* seq, unsigned long lo
                 const int32_t h = hint[(int64_t)(k - 1) * hint_stride];
                 if (h >= 0 && bary_margin(sc.tri + 9 * (int64_t)h, P[k]) >= 1e-6) {
                     face[k - 1] = h;
+                    continue;
+                }
+            }
+            if (sc.nodes) {
+                int32_t f = 0;
+                if (lane == 0) f = bvh_find_face(sc, s, P[k]);
+                f = __shfl_sync(0xffffffffu, f, 0);
+                if (f != -2) {
+                    if (f < 0) { ok = false; break; }
+                    face[k - 1] = f;
                     continue;
                 }
             }
