@@ -3,8 +3,18 @@
 //
 // radix_sort_pairs: stable LSD radix sort, 8-bit digits. Each pass: a tile
 // histogram per block, an exclusive scan of the digit-major histogram, and a
-// stable scatter that ranks equal digits by (round, warp, lane) order.
+// stable scatter that ranks equal digits by (round, warp, lane) order. Up to
+// 12,288 keys the whole sort runs in one block in shared memory; up to 2^20
+// keys in one cooperative launch (grid-wide barriers between the phases);
+// beyond that as separate launches per phase.
+#include <algorithm>
+#include <atomic>
+
+#include <cooperative_groups.h>
+
 #include "sbr_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace sbr {
 namespace {
@@ -14,35 +24,49 @@ constexpr int kSortRounds = 8;
 constexpr int kSortTile = kSortThreads * kSortRounds;  // 2048 elements per block
 constexpr int kScanBlock = 1024;
 
-__global__ void k_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
-                       uint32_t* __restrict__ hist, int nblocks) {
+// loads of data that other blocks of the same launch wrote (kCG: at L2,
+// past this SM's L1 and the read-only path)
+template <bool kCG>
+__device__ __forceinline__ uint32_t ld_u32(const uint32_t* p) {
+    if (kCG) return __ldcg(p);
+    return *p;
+}
+
+// digit counts of tile t (kSortTile keys from t * kSortTile), digit-major:
+// hist[d * ntiles + t]
+template <bool kCG = false>
+__device__ __forceinline__ void tile_hist(const uint32_t* keys, int64_t n, int shift, uint32_t* hist, int ntiles,
+                                          int t) {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    int64_t base = (int64_t)t * kSortTile;
     for (int r = 0; r < kSortRounds; ++r) {
         int64_t i = base + r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+        if (i < n) atomicAdd(&h[(ld_u32<kCG>(keys + i) >> shift) & 255u], 1u);
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    hist[(int64_t)threadIdx.x * ntiles + t] = h[threadIdx.x];
+    __syncthreads();
 }
 
-__global__ void k_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
-                          int shift, const uint32_t* __restrict__ hist, int nblocks) {
+// stable scatter of tile t, its digits starting at the scanned hist[d * ntiles + t]
+template <bool kCG = false>
+__device__ __forceinline__ void tile_scatter(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
+                                             uint32_t* vout, int64_t n, int shift, const uint32_t* hist,
+                                             int ntiles, int t) {
     __shared__ uint32_t s_run[256];
     __shared__ uint32_t s_warp[kSortThreads / 32][256];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    s_run[tid] = hist[(int64_t)tid * nblocks + blockIdx.x];
-    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    s_run[tid] = ld_u32<kCG>(hist + (int64_t)tid * ntiles + t);
+    int64_t base = (int64_t)t * kSortTile;
     const unsigned lt = (1u << lane) - 1u;
     for (int r = 0; r < kSortRounds; ++r) {
         for (int w = 0; w < kSortThreads / 32; ++w) s_warp[w][tid] = 0;
         __syncthreads();
         int64_t i = base + r * kSortThreads + tid;
         bool valid = i < n;
-        uint32_t k = valid ? kin[i] : 0u, v = valid ? vin[i] : 0u;
+        uint32_t k = valid ? ld_u32<kCG>(kin + i) : 0u, v = valid ? ld_u32<kCG>(vin + i) : 0u;
         uint32_t d = valid ? ((k >> shift) & 255u) : 256u;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int rank = __popc(peers & lt);
@@ -65,6 +89,17 @@ __global__ void k_scatter(const uint32_t* __restrict__ kin, const uint32_t* __re
         }
         __syncthreads();
     }
+}
+
+__global__ void k_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                       uint32_t* __restrict__ hist, int nblocks) {
+    tile_hist(keys, n, shift, hist, nblocks, blockIdx.x);
+}
+
+__global__ void k_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                          int shift, const uint32_t* __restrict__ hist, int nblocks) {
+    tile_scatter(kin, vin, kout, vout, n, shift, hist, nblocks, blockIdx.x);
 }
 
 // block-level exclusive scan of up to kScanBlock values
@@ -116,6 +151,49 @@ __global__ void k_add_offsets(uint32_t* data, int64_t n, const uint32_t* offs) {
 __global__ void k_total(const uint32_t* scanned, const uint32_t* last_in, int64_t n,
                         uint32_t* total) {
     *total = n > 0 ? scanned[n - 1] + *last_in : 0u;
+}
+
+// The whole sort of a mid-sized array in one cooperative launch: per 8-bit
+// pass, tile counts, the digit-major scan (block 0) and the stable scatter,
+// separated by grid-wide barriers (every block is resident: the launch is
+// cooperative). Tiles are shared out over the blocks in a grid stride; the
+// result ends in (k0, v0).
+constexpr int kCoopMaxTiles = 512;   // n <= 512 tiles of kSortTile = 1,048,576 keys
+
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_coop(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int passes, uint32_t* hist) {
+    cg::grid_group grid = cg::this_grid();
+    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    uint32_t *ka = k0, *va = v0, *kb = k1, *vb = v1;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) tile_hist<true>(ka, n, shift, hist, ntiles, t);
+        grid.sync();
+        if (blockIdx.x == 0) {
+            const int total = 256 * ntiles;
+            const int c = (total + (int)blockDim.x - 1) / (int)blockDim.x;
+            const int i0 = min(total, (int)threadIdx.x * c), i1 = min(total, i0 + c);
+            uint32_t sum = 0;
+            for (int i = i0; i < i1; ++i) sum += __ldcg(hist + i);
+            uint32_t ex = block_exclusive_scan(sum, nullptr);
+            for (int i = i0; i < i1; ++i) {
+                const uint32_t x = __ldcg(hist + i);
+                hist[i] = ex;
+                ex += x;
+            }
+        }
+        grid.sync();
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
+            tile_scatter<true>(ka, va, kb, vb, n, shift, hist, ntiles, t);
+        grid.sync();
+        uint32_t* q = ka; ka = kb; kb = q;
+        q = va; va = vb; vb = q;
+    }
+    if (ka != k0)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            k0[i] = __ldcg(ka + i);
+            v0[i] = __ldcg(va + i);
+        }
 }
 
 sbr_status scan_rec(uint32_t* data, int64_t n, cudaStream_t s) {
@@ -242,6 +320,27 @@ sbr_status exclusive_scan_u32(uint32_t* data, int64_t n, uint32_t* total, cudaSt
     return st;
 }
 
+// blocks of k_sort_coop that fit on the current device at once (0: no
+// cooperative launch there)
+static sbr_status coop_blocks(int* out) {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];   // blocks + 1; 0 = not yet known
+    int dev = 0;
+    SBR_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDev) { *out = 0; return SBR_OK; }
+    int c = cache[dev].load();
+    if (c == 0) {
+        int coop = 0, sms = 0, per_sm = 0;
+        SBR_TRY_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        SBR_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        SBR_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_coop, kSortThreads, 0));
+        c = (coop ? sms * per_sm : 0) + 1;
+        cache[dev].store(c);
+    }
+    *out = c - 1;
+    return SBR_OK;
+}
+
 sbr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits, cudaStream_t s) {
     if (n <= 1 || bits <= 0) return SBR_OK;
     if (n > 0x7fffffffLL) {
@@ -265,8 +364,20 @@ sbr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits,
     SBR_TRY(dalloc_n(&k2, n, s));
     SBR_TRY(dalloc_n(&v2, n, s));
     SBR_TRY(dalloc_n(&hist, (size_t)256 * nblocks, s));
-    uint32_t *ka = keys, *va = vals, *kb = k2, *vb = v2;
     int passes = (bits + 7) / 8;
+    int coop = 0;
+    if (nblocks <= kCoopMaxTiles) SBR_TRY(coop_blocks(&coop));
+    if (coop > 0) {
+        int grid = std::min(nblocks, coop);
+        void* args[] = {&keys, &vals, &k2, &v2, &n, &passes, &hist};
+        ::sbr::note_launch();
+        SBR_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)k_sort_coop, dim3(grid), dim3(kSortThreads), args, 0, s));
+        dfree(k2, s);
+        dfree(v2, s);
+        dfree(hist, s);
+        return SBR_OK;
+    }
+    uint32_t *ka = keys, *va = vals, *kb = k2, *vb = v2;
     sbr_status st = SBR_OK;
     for (int p = 0; p < passes && st == SBR_OK; ++p) {
         ::sbr::note_launch(), k_hist<<<nblocks, kSortThreads, 0, s>>>(ka, n, 8 * p, hist, nblocks);
