@@ -47,11 +47,11 @@ RAY_REC_BYTES = 64      # one queued ray record (origin, direction, L, id, last 
 # algorithmic HBM bytes of one ray-bounce of the trace: the ray state (a 64 B
 # record) read at the start of the segment and written for the next one
 ALG_BYTES_PER_RAY_BOUNCE = 2 * RAY_REC_BYTES
-# DRAM bytes of one k_trace_df launch on this workload, from one ncu capture of
-# the launch (dram__bytes_read.sum + dram__bytes_write.sum); None if not measured
-# for the kernel as it stands
-TRACE_DRAM_BYTES = None
-SEQ_BYTES = 4           # surface id appended per reflection
+# DRAM bytes of one k_trace_df launch on the headline workload (N = 1000), from
+# one ncu capture of the launch (dram__bytes_read.sum + dram__bytes_write.sum,
+# profiles/k_trace_df_urban_N1000_dram.md); None once the kernel has changed
+TRACE_DRAM_BYTES = 263_167_744 + 117_104_128
+SEQ_BYTES = 8           # surface id and face id appended per reflection
 DIR_BYTES = 24          # launch direction of a ray, double-float
 
 
@@ -391,14 +391,14 @@ def run_gpu(args):
     achieved = ALG_BYTES_PER_RAY_BOUNCE * rb / (bounce_ms / 1e3) / 1e9
     hbm = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
     roof = {"kernel": "k_trace_df", "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm, "traffic": TRACE_DRAM_BYTES,
+            "unit": "GB/s", "frac": achieved / hbm, "traffic": TRACE_DRAM_BYTES if N == 1000 else None,
             "peak_source": peak_src,
             "schedule": "depth first from bounce 0 (one launch per trace)",
             "algorithmic_bytes": "128 B ray state (64 B read + 64 B written) per ray-bounce, "
                                  "x ray-bounces per launch",
             "algorithmic_bytes_per_launch": ALG_BYTES_PER_RAY_BOUNCE * rb / args.steps,
             "streamed_bytes_per_launch": bounce_bytes / args.steps,
-            "streamed_bytes": "24 B launch direction per ray + 4 B surface id per reflection",
+            "streamed_bytes": "24 B launch direction per ray + 8 B surface and face id per reflection",
             "avg_launch_ms": bounce_ms / args.steps,
             "kernel_share_of_step": bounce_ms / sum(times), "l2": l2}
     line = {
