@@ -191,9 +191,10 @@ def trace(bvh: BVH, tx, rx: torch.Tensor, N: int, K: int, alpha: float = 0.0, ta
 
 
 class PathList:
-    def __init__(self, handle, n):
+    def __init__(self, handle, n, n_rx):
         self._h = handle
-        self.n = n
+        self.n = n          # paths
+        self.n_rx = n_rx    # receivers of the trace (known without a query, which waits for the stream)
 
     @property
     def handle(self):
@@ -251,7 +252,7 @@ def paths(tr: TraceResult, bvh: BVH, stream=None) -> PathList:
     h = C.c_void_p()
     n = C.c_int64()
     _check(_L().sbr_paths(tr.handle, bvh.handle, C.byref(h), C.byref(n), _stream(stream)))
-    return PathList(h, int(n.value))
+    return PathList(h, int(n.value), int(tr.params.n_rx))
 
 
 def path_gains(pl: PathList, mats: torch.Tensor, freqs: torch.Tensor, gamma_db_km=None,
@@ -282,7 +283,7 @@ def synthesize_H_elements(pl: PathList, gains: torch.Tensor, freqs: torch.Tensor
                           precision: int = SYNTH_FP32, out=None, stream=None) -> torch.Tensor:
     """H(f) [F, n_rx, Nt] complex64 with per-element reception: every receiver
     of the trace is one receive element and its row sums its own paths."""
-    F, Nt, Nr = int(freqs.numel()), int(tx_elem.shape[0]), int(pl.info()["n_rx"])
+    F, Nt, Nr = int(freqs.numel()), int(tx_elem.shape[0]), pl.n_rx
     H = out if out is not None else torch.empty((F, Nr, Nt), dtype=torch.complex64, device=_dev())
     g = gains if gains.numel() else torch.empty(1, dtype=torch.complex64, device=_dev())
     _check(_L().sbr_synthesize_H_elements(pl.handle, _ptr(g), _ptr(freqs), F, _ptr(tx_elem), Nt,
@@ -293,8 +294,7 @@ def synthesize_H_elements(pl: PathList, gains: torch.Tensor, freqs: torch.Tensor
 def pdp_angles(pl: PathList, gains: torch.Tensor, f_index: int, fc_hz: float, bin_s: float = 1e-9,
                n_bins: int = 1024, stream=None):
     """PDP in dB [n_rx, n_bins] (float32) and stats [n_rx, 7] (float64)."""
-    info = pl.info()
-    n_rx = info["n_rx"]
+    n_rx = pl.n_rx
     F = int(gains.shape[1]) if gains.dim() == 2 else 1
     pdp = torch.empty((max(n_rx, 1), n_bins), dtype=torch.float32, device=_dev())
     stats = torch.empty((max(n_rx, 1), NSTATS), dtype=torch.float64, device=_dev())
@@ -493,11 +493,11 @@ def batch_tune(scenes, jobs, config=None, stream=None):
 def surrogate_targets(pl: PathList, gains: torch.Tensor, F: int, n_taps: int = 16, tap_s: float = 5e-9,
                       floor_db: float = -40.0, stream=None) -> torch.Tensor:
     """[n_rx, F, 2 + n_taps] float32: path loss (dB), RMS delay spread (s), PDP taps (dB)."""
-    info = pl.info()
-    out = torch.empty((max(info["n_rx"], 1), F, 2 + n_taps), dtype=torch.float32, device=_dev())
+    n_rx = pl.n_rx
+    out = torch.empty((max(n_rx, 1), F, 2 + n_taps), dtype=torch.float32, device=_dev())
     _check(_L().sbr_surrogate_targets(pl.handle, _ptr(gains) if pl.n else None, int(F), int(n_taps),
                                       float(tap_s), float(floor_db), _ptr(out), _stream(stream)))
-    return out[: info["n_rx"]]
+    return out[:n_rx]
 
 
 class MLP:
