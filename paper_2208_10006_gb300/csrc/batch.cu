@@ -498,7 +498,7 @@ sbr_status create(const sbr_bvh* const* scenes, const sbr_material* const* mats,
     SBR_CHECK_ARG(c.precision == SBR_SYNTH_FP16X3 || c.precision == SBR_SYNTH_BF16X3, "precision");
     SBR_CHECK_ARG(c.trace_blocks_per_sm >= 0 && c.trace_blocks_per_sm <= 16, "trace_blocks_per_sm");
     SBR_CHECK_ARG(c.table_log2 == 0 || (c.table_log2 >= 4 && c.table_log2 <= 26), "table_log2");
-    if (c.trace_blocks_per_sm == 0) c.trace_blocks_per_sm = batch_trace_occupancy();
+    if (c.trace_blocks_per_sm == 0) c.trace_blocks_per_sm = batch_trace_occupancy(!c.breadth_first);
     int64_t max_R = 0;
     for (int i = 0; i < n_jobs; ++i) max_R = std::max<int64_t>(max_R, 10 * (int64_t)jobs[i].subdiv_N * jobs[i].subdiv_N + 2);
     c.wave_rays = std::max<int64_t>(c.wave_rays, max_R);
@@ -868,7 +868,9 @@ sbr_status sbr_batch_tune(const sbr_bvh* const* scenes, const sbr_material* cons
     double best_t = 1e300;
     // coordinate search: tile width, then bounce grid, then ray-queue capacity
     const int tiles[3] = {64, 128, 256};
-    const int grids[3] = {2, 3, 4};
+    // resident blocks per SM of the trace kernel: all of them, three quarters, half
+    const int occ = batch_trace_occupancy(!fixed.breadth_first);
+    const int grids[3] = {occ, std::max(1, (3 * occ) / 4), std::max(1, occ / 2)};
     const int sh = fixed.breadth_first ? 25 : 26;
     const int64_t waves[3] = {(int64_t)1 << sh, (int64_t)1 << (sh + 1), (int64_t)1 << (sh + 2)};
     auto consider = [&](sbr_batch_config c) -> sbr_status {

@@ -82,7 +82,7 @@ struct BatchTraceWave {
 // synchronisation: capturable in a CUDA graph)
 sbr_status batch_trace_wave(const BatchTraceWave& w, int blocks_per_sm, cudaStream_t s);
 int batch_trace_kernels(int Kmax);   // launches batch_trace_wave makes
-int batch_trace_occupancy();         // resident blocks per SM of the batched bounce kernel
+int batch_trace_occupancy(bool depth_first);   // resident blocks per SM of the batched trace kernel
 
 }  // namespace sbr
 

@@ -890,7 +890,11 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_batch(const __grid_cons
 
 // the batched step, depth first: each lane carries its ray (and job) through
 // every bounce of its job, then takes the next ray of the wave
-__global__ void __launch_bounds__(kTraceThreads) k_trace_batch_df(const __grid_constant__ BatchTraceArgs a) {
+// eight 128-thread blocks per SM (64 registers), as the single-job depth-first
+// kernel: the walks are latency-bound and gain more from resident warps than
+// they lose to spills (4096-job batch: 2.07 s at 96 registers and 4 blocks,
+// 1.64 s here)
+__global__ void __launch_bounds__(kTraceThreads, 8) k_trace_batch_df(const __grid_constant__ BatchTraceArgs a) {
     int stack[kStack];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -1045,13 +1049,12 @@ int trace_grid(bool count) {
 
 int batch_trace_kernels(int Kmax) { return Kmax + 3; }
 
-int batch_trace_occupancy() {
-    int per_sm = 0, per_sm_df = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_batch, kTraceThreads, 0) != cudaSuccess)
-        per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_df, k_trace_batch_df, kTraceThreads, 0) != cudaSuccess)
-        per_sm_df = 1;
-    return std::max(1, std::min(per_sm, per_sm_df));
+int batch_trace_occupancy(bool depth_first) {
+    int per_sm = 0;
+    cudaError_t e = depth_first
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_batch_df, kTraceThreads, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_batch, kTraceThreads, 0);
+    return e == cudaSuccess ? std::max(1, per_sm) : 1;
 }
 
 sbr_status batch_trace_wave(const BatchTraceWave& w, int blocks_per_sm, cudaStream_t s) {
