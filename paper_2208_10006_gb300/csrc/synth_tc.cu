@@ -362,15 +362,67 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
     }
 }
 
-template <class T>
-__global__ void k_to_f32(const T* __restrict__ in, float* __restrict__ out, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (float)in[i];
-}
+// Operands of the tensor-core forms in one launch (the FP32 copies of the
+// FP64 prologue of the CUDA-core forms): for the Pr paths of one receiver,
+//   dt[n][p] = |T_p - P1| - |T_0 - P1|,  dr[n][q] = |R_q - Pm| - |R_0 - Pm|
+//   (0 for the LoS path), dlos[q][p] = |T_p - R_q| - |T_0 - R_0| (FP64, then
+//   rounded), and w[f][n] = g_n(f) exp(-j 2 pi frac(f L_n / c)) with the
+//   fraction taken in FP64 and the phasor in FP32.
+struct TcPrep {
+    int32_t Pr, Nt, Nr, F;
+    const int32_t* nb;       // [Pr] reflections of the receiver's paths
+    const double* pts;       // [Pr][kKmax][3]
+    const double* L;         // [Pr]
+    const float2* g;         // [Pr][F]
+    const double* freqs;
+    const double* tx_elem;
+    const double* rx_elem;
+    const double* R0;
+    d3 T0;
+    float* dt;
+    float* dr;
+    float* dlos;
+    float2* w;
+};
 
-__global__ void k_w_to_f32(const double2* __restrict__ in, float2* __restrict__ out, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+__global__ void k_tc_prep(const __grid_constant__ TcPrep a) {
+    const int64_t n_dt = (int64_t)a.Pr * a.Nt, n_dr = (int64_t)a.Pr * a.Nr, n_dl = (int64_t)a.Nr * a.Nt;
+    const int64_t total = n_dt + n_dr + n_dl + (int64_t)a.F * a.Pr;
+    const d3 R0 = ld3(a.R0);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < n_dt) {
+            const int64_t n = t / a.Nt;
+            const int p = (int)(t - n * a.Nt);
+            float v = 0.f;
+            if (a.nb[n] > 0) {
+                const d3 P1 = ld3(a.pts + n * kKmax * 3);
+                v = (float)(norm(ld3(a.tx_elem + 3 * p) - P1) - norm(a.T0 - P1));
+            }
+            a.dt[t] = v;
+        } else if (t < n_dt + n_dr) {
+            const int64_t u = t - n_dt, n = u / a.Nr;
+            const int q = (int)(u - n * a.Nr);
+            const int m = a.nb[n];
+            float v = 0.f;
+            if (m > 0) {
+                const d3 Pm = ld3(a.pts + (n * kKmax + m - 1) * 3);
+                v = (float)(norm(ld3(a.rx_elem + 3 * q) - Pm) - norm(R0 - Pm));
+            }
+            a.dr[u] = v;
+        } else if (t < n_dt + n_dr + n_dl) {
+            const int64_t u = t - n_dt - n_dr, q = u / a.Nt;
+            const int p = (int)(u - q * a.Nt);
+            a.dlos[u] = (float)(norm(ld3(a.tx_elem + 3 * p) - ld3(a.rx_elem + 3 * q)) - norm(a.T0 - R0));
+        } else {
+            const int64_t u = t - n_dt - n_dr - n_dl, f = u / a.Pr, n = u - f * a.Pr;
+            const double cyc = a.freqs[f] * a.L[n] / kC0;
+            float s, c;
+            sincospif(-2.0f * (float)(cyc - floor(cyc)), &s, &c);
+            const float2 gg = a.g[n * a.F + f];
+            a.w[u] = make_float2(gg.x * c - gg.y * s, gg.x * s + gg.y * c);
+        }
+    }
 }
 
 inline unsigned nb256(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + 255) / 256); }
@@ -380,23 +432,32 @@ inline unsigned nb256(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + 25
 sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* freqs, int32_t F,
                         const double* tx_elem, int32_t Nt, const double* rx_elem, int32_t Nr,
                         int32_t rx_index, float2* H, bool f16, cudaStream_t s) {
-    SynthPrep sp;
-    SBR_TRY(synth_prepare(pl, g, freqs, F, tx_elem, Nt, rx_elem, Nr, rx_index, &sp, s));
-    const int32_t Pr = std::max(sp.Pr, 1);
-    float *dt, *dr, *dl;
+    const int32_t o0 = pl->h_rx_off[rx_index], Pr_ = pl->h_rx_off[rx_index + 1] - o0;
+    const int32_t Pr = std::max(Pr_, 1);
+    // one buffer for the four operands: w (8-byte elements) first
+    const size_t n_w = (size_t)Pr * F, n_f = (size_t)Pr * Nt + (size_t)Pr * Nr + (size_t)Nr * Nt;
     float2* w;
-    SBR_TRY(dalloc_n(&dt, (size_t)Pr * Nt, s));
-    SBR_TRY(dalloc_n(&dr, (size_t)Pr * Nr, s));
-    SBR_TRY(dalloc_n(&dl, (size_t)Nr * Nt, s));
-    SBR_TRY(dalloc_n(&w, (size_t)Pr * F, s));
-    ::sbr::note_launch(), k_to_f32<double><<<nb256((int64_t)Pr * Nt), 256, 0, s>>>(sp.dt, dt, (int64_t)Pr * Nt);
-    ::sbr::note_launch(), k_to_f32<double><<<nb256((int64_t)Pr * Nr), 256, 0, s>>>(sp.dr, dr, (int64_t)Pr * Nr);
-    ::sbr::note_launch(), k_to_f32<double><<<nb256((int64_t)Nr * Nt), 256, 0, s>>>(sp.dlos, dl, (int64_t)Nr * Nt);
-    ::sbr::note_launch(), k_w_to_f32<<<nb256((int64_t)Pr * F), 256, 0, s>>>(sp.w, w, (int64_t)Pr * F);
+    SBR_TRY(dalloc_n(&w, n_w + (n_f + 1) / 2, s));
+    float* dt = reinterpret_cast<float*>(w + n_w);
+    float* dr = dt + (size_t)Pr * Nt;
+    float* dl = dr + (size_t)Pr * Nr;
+    TcPrep pp{};
+    pp.Pr = Pr_; pp.Nt = Nt; pp.Nr = Nr; pp.F = F;
+    pp.nb = pl->nb + o0;
+    pp.pts = pl->pts + (int64_t)o0 * kKmax * 3;
+    pp.L = pl->L + o0;
+    pp.g = g + (int64_t)o0 * F;
+    pp.freqs = freqs; pp.tx_elem = tx_elem; pp.rx_elem = rx_elem;
+    pp.R0 = pl->rx_xyz + 3 * rx_index;
+    pp.T0 = mk3(pl->tx[0], pl->tx[1], pl->tx[2]);
+    pp.dt = dt; pp.dr = dr; pp.dlos = dl; pp.w = w;
+    const int64_t n_all = (int64_t)Pr_ * (Nt + Nr) + (int64_t)Nr * Nt + (int64_t)Pr_ * F;
+    ::sbr::note_launch(), k_tc_prep<<<(unsigned)std::min<int64_t>(nb256(n_all), 8 * (int64_t)sm_count()), 256, 0, s>>>(pp);
+    SBR_TRY_CUDA(cudaGetLastError());
     TcArgs a{};
     a.F = F; a.Nr = Nr; a.Nt = Nt;
-    a.Pr = sp.Pr;
-    a.nb0 = sp.nb0;
+    a.Pr = Pr_;
+    a.nb0 = pl->nb + o0;
     a.freqs = freqs; a.dt = dt; a.dr = dr; a.w = w; a.dlos = dl; a.H = H;
     a.status = pl->d_status;  // a bounded wait that gave up is reported by sbr_path_query
     a.inject_timeout = fault_mode() == kFaultTimeout ? 1 : 0;
@@ -409,8 +470,7 @@ sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* 
     int grid = (int)std::min<int64_t>(items, 2 * (int64_t)sm_count());
     ::sbr::note_launch(), kern<<<grid, kTcThreads, kSmemBytes, s>>>(a);
     SBR_TRY_CUDA(cudaGetLastError());
-    dfree(dt, s); dfree(dr, s); dfree(dl, s); dfree(w, s);
-    synth_release(&sp, s);
+    dfree(w, s);
     return SBR_OK;
 }
 
