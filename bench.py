@@ -598,11 +598,11 @@ def bench_batched(sbr, torch, args):
     scs = [scenes.batch_scene(s) for s in range(32)]
     jobs = scenes.batch_jobs(scs, n_jobs=n_jobs, seed=4)
     sdev = []
-    for sc in scs:
+    for sc in scs:   # each scene is traced by ~128 jobs: the SAH top of its BVH pays for its build
         tri = torch.as_tensor(sc["tri"].reshape(-1, 9), dtype=torch.float32, device=dev)
         sid = torch.as_tensor(sc["surface_id"], dtype=torch.int32, device=dev)
         mats = torch.as_tensor(sc["materials"], dtype=torch.float64, device=dev)
-        sdev.append((sbr.build_bvh(tri, sid, len(sc["materials"])), mats))
+        sdev.append((sbr.build_bvh(tri, sid, len(sc["materials"]), sah_top=True), mats))
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
     jdev = [dict(scene=j["scene"], N=j["N"], K=j["K"], tx=j["tx"], rx=j["rx"], pol=j["pol"],
                  freqs=t(j["freqs"], torch.float64), gamma=t(j["gamma"], torch.float32),
@@ -759,7 +759,7 @@ def profile_case(case: str) -> int:
             tri = torch.as_tensor(sc["tri"].reshape(-1, 9), dtype=torch.float32, device=dev)
             sid = torch.as_tensor(sc["surface_id"], dtype=torch.int32, device=dev)
             mats = torch.as_tensor(sc["materials"], dtype=torch.float64, device=dev)
-            sdev.append((sbr.build_bvh(tri, sid, len(sc["materials"])), mats))
+            sdev.append((sbr.build_bvh(tri, sid, len(sc["materials"]), sah_top=True), mats))
         t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
         jdev = [dict(scene=j["scene"], N=j["N"], K=j["K"], tx=j["tx"], rx=j["rx"], pol=j["pol"],
                      freqs=t(j["freqs"], torch.float64), gamma=t(j["gamma"], torch.float32),

@@ -109,6 +109,21 @@ sbr_status sbr_launch_dirs(int32_t N, double* dirs, double* alpha, void* stream)
  */
 sbr_status sbr_build_bvh(const float* tri_xyz, const int32_t* surface_id, int64_t T, int32_t S,
                          sbr_bvh** out, void* stream);
+
+/* flags of sbr_build_bvh_ex */
+#define SBR_BVH_SAH_TOP 1   /* rebuild the top of the tree with the surface-area heuristic */
+
+/*
+ * sbr_build_bvh_ex - sbr_build_bvh with build options (same arguments,
+ * ownership and errors; flags 0 gives the same tree). SBR_BVH_SAH_TOP
+ * rebuilds the levels above the subtrees of at most max(8, T/800) triangles
+ * with a binned surface-area-heuristic build (about T/40 subtrees): on the
+ * 51,600-triangle urban scene 6.7% fewer node visits per segment for about
+ * 0.6 ms more build time, so it pays for scenes traced many times (batches,
+ * many transmitters), not for one trace per build. Unknown flags are rejected.
+ */
+sbr_status sbr_build_bvh_ex(const float* tri_xyz, const int32_t* surface_id, int64_t T, int32_t S,
+                            uint32_t flags, sbr_bvh** out, void* stream);
 void sbr_bvh_free(sbr_bvh* bvh);
 
 typedef struct {

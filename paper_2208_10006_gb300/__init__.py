@@ -121,15 +121,18 @@ class BVH:
             pass
 
 
-def build_bvh(tri: torch.Tensor, surface_id: torch.Tensor, S: int, stream=None) -> BVH:
-    """tri: float32 [T,3,3] (or [T,9]); surface_id: int32 [T]; both CUDA."""
+def build_bvh(tri: torch.Tensor, surface_id: torch.Tensor, S: int, sah_top: bool = False,
+              stream=None) -> BVH:
+    """tri: float32 [T,3,3] (or [T,9]); surface_id: int32 [T]; both CUDA.
+    sah_top: rebuild the top levels with the surface-area heuristic (slower
+    build, faster traversal: for scenes traced many times)."""
     T = int(surface_id.numel())
     tri = tri.reshape(T, 9) if T else tri
     if T:
         assert tri.dtype == torch.float32 and surface_id.dtype == torch.int32
     h = C.c_void_p()
-    _check(_L().sbr_build_bvh(_ptr(tri) if T else None, _ptr(surface_id) if T else None, T, int(S),
-                              C.byref(h), _stream(stream)))
+    _check(_L().sbr_build_bvh_ex(_ptr(tri) if T else None, _ptr(surface_id) if T else None, T, int(S),
+                                 _lib.BVH_SAH_TOP if sah_top else 0, C.byref(h), _stream(stream)))
     return BVH(h, T, int(S))
 
 

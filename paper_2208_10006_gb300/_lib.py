@@ -18,7 +18,9 @@ SYNTH_FP64, SYNTH_FP32, SYNTH_BF16X3, SYNTH_FP16X3 = 0, 1, 2, 3
 TRACE_TIMING = 1
 TRACE_COUNT_VISITS = 2
 
-EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_count", "sbr_launch_dirs", "sbr_build_bvh", "sbr_bvh_free",
+BVH_SAH_TOP = 1   # sbr_build_bvh_ex flag
+
+EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_count", "sbr_launch_dirs", "sbr_build_bvh", "sbr_build_bvh_ex", "sbr_bvh_free",
            "sbr_bvh_query", "sbr_trace", "sbr_trace_stats", "sbr_trace_free", "sbr_paths",
            "sbr_path_query", "sbr_path_export", "sbr_path_list_free", "sbr_path_gains",
            "sbr_synthesize_H", "sbr_synthesize_H_elements", "sbr_pdp_angles", "sbr_capacity", "sbr_capacity_noalloc",
@@ -112,6 +114,8 @@ def load() -> C.CDLL:
     L.sbr_launch_dirs.argtypes = [i32, p, p, p]
     L.sbr_build_bvh.restype = st
     L.sbr_build_bvh.argtypes = [p, p, i64, i32, pp, p]
+    L.sbr_build_bvh_ex.restype = st
+    L.sbr_build_bvh_ex.argtypes = [p, p, i64, i32, C.c_uint32, pp, p]
     L.sbr_bvh_free.restype = None
     L.sbr_bvh_free.argtypes = [p]
     L.sbr_bvh_query.restype = st

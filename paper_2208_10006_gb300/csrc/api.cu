@@ -153,8 +153,15 @@ sbr_status sbr_launch_dirs(int32_t N, double* dirs, double* alpha, void* stream)
 
 sbr_status sbr_build_bvh(const float* tri_xyz, const int32_t* surface_id, int64_t T, int32_t S,
                          sbr_bvh** out, void* stream) {
+    return sbr_build_bvh_ex(tri_xyz, surface_id, T, S, 0u, out, stream);
+}
+
+sbr_status sbr_build_bvh_ex(const float* tri_xyz, const int32_t* surface_id, int64_t T, int32_t S,
+                            uint32_t flags, sbr_bvh** out, void* stream) {
     clear_error();
     SBR_CHECK_ARG(out != nullptr, "out");
+    *out = nullptr;
+    SBR_CHECK_ARG((flags & ~(uint32_t)SBR_BVH_SAH_TOP) == 0, "flags: SBR_BVH_SAH_TOP only");
     *out = nullptr;
     SBR_CHECK_ARG(T >= 0 && T < ((int64_t)1 << 28), "0 <= T < 2^28");
     SBR_CHECK_ARG(S >= 0 && (T == 0 || S >= 1), "S >= 1 when T > 0");
@@ -164,7 +171,7 @@ sbr_status sbr_build_bvh(const float* tri_xyz, const int32_t* surface_id, int64_
     if (!b) { set_error("host allocation failed"); return SBR_ERR_ALLOC; }
     b->device = current_device();
     b->stream = s;
-    sbr_status st = bvh_build(tri_xyz, surface_id, T, S, b, s);
+    sbr_status st = bvh_build(tri_xyz, surface_id, T, S, b, s, (flags & SBR_BVH_SAH_TOP) != 0);
     if (st != SBR_OK) {
         sbr_bvh_free(b);
         return st;

@@ -106,8 +106,9 @@ struct BvhNodes {
 // pad_rel: relative padding added to every child box (covers FP32 rounding).
 // Subtrees of at most leaf_max (<= 16) primitives become one leaf; a leaf
 // reference is ~(first | (count - 1) << 28).
+// top_sah: rebuild the top of the tree with the surface-area heuristic
 sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, int leaf_max, BvhNodes* out,
-                      int32_t* d_depth, cudaStream_t s);
+                      int32_t* d_depth, cudaStream_t s, bool top_sah = false);
 constexpr int kTriLeaf = 2;  // triangles per BVH leaf at most (measured best of 1..6)
 __host__ __device__ __forceinline__ int32_t leaf_first(int32_t ref) { return (~ref) & 0x0FFFFFFF; }
 __host__ __device__ __forceinline__ int32_t leaf_count(int32_t ref) { return (int32_t)(((uint32_t)(~ref)) >> 28) + 1; }
@@ -202,8 +203,8 @@ constexpr int kJones = 48;
 // launchers implemented in the .cu files
 sbr_status launch_dirs(int32_t N, double* dirs, cudaStream_t s);
 sbr_status launch_alpha(int32_t N, double* alpha, cudaStream_t s);
-sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S, sbr_bvh* b,
-                     cudaStream_t s);
+sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S, sbr_bvh* b, cudaStream_t s,
+                     bool sah_top);
 sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s);
 sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list* pl,
                      cudaStream_t s);

@@ -366,8 +366,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
 // FP64 prologue of the CUDA-core forms): for the Pr paths of one receiver,
 //   dt[n][p] = |T_p - P1| - |T_0 - P1|,  dr[n][q] = |R_q - Pm| - |R_0 - Pm|
 //   (0 for the LoS path), dlos[q][p] = |T_p - R_q| - |T_0 - R_0| (FP64, then
-//   rounded), and w[f][n] = g_n(f) exp(-j 2 pi frac(f L_n / c)) with the
-//   fraction taken in FP64 and the phasor in FP32.
+//   rounded), and w[f][n] = g_n(f) exp(-j 2 pi frac(f L_n / c)) in FP64, then
+//   rounded.
 struct TcPrep {
     int32_t Pr, Nt, Nr, F;
     const int32_t* nb;       // [Pr] reflections of the receiver's paths
@@ -416,11 +416,14 @@ __global__ void k_tc_prep(const __grid_constant__ TcPrep a) {
             a.dlos[u] = (float)(norm(ld3(a.tx_elem + 3 * p) - ld3(a.rx_elem + 3 * q)) - norm(a.T0 - R0));
         } else {
             const int64_t u = t - n_dt - n_dr - n_dl, f = u / a.Pr, n = u - f * a.Pr;
+            // the batched form computes its weights with the same FP64 arithmetic,
+            // so both give bit-identical H for the same path list
             const double cyc = a.freqs[f] * a.L[n] / kC0;
-            float s, c;
-            sincospif(-2.0f * (float)(cyc - floor(cyc)), &s, &c);
+            const double frc = cyc - floor(cyc);
+            double s, c;
+            sincospi(-2.0 * frc, &s, &c);
             const float2 gg = a.g[n * a.F + f];
-            a.w[u] = make_float2(gg.x * c - gg.y * s, gg.x * s + gg.y * c);
+            a.w[u] = make_float2((float)(gg.x * c - gg.y * s), (float)(gg.x * s + gg.y * c));
         }
     }
 }

@@ -44,6 +44,8 @@ def test_host_validation_rejects_bad_arguments_before_any_launch(lib):
     assert b"N in" in lib.sbr_last_error()
     out = ctypes.c_void_p()
     assert lib.sbr_build_bvh(None, None, -1, 1, ctypes.byref(out), None) == 1
+    assert lib.sbr_build_bvh_ex(None, None, 0, 1, ctypes.c_uint32(2), ctypes.byref(out), None) == 1
+    assert b"flags" in lib.sbr_last_error()
     assert lib.sbr_trace(None, None, ctypes.byref(out), None) == 1
     assert lib.sbr_capacity(None, 1, 1, 1, None, 1, None, None) == 1
 

@@ -397,3 +397,22 @@ def test_large_path_list_is_in_key_order(sbr):
     st = st.cpu().numpy()
     assert np.all(np.isinf(st[counts == 0, 1]))
     assert np.mean(np.isfinite(st[counts > 0, 1])) > 0.9   # (gains below the FP32 range read as no power)
+
+
+@pytest.mark.parametrize("name", ["urban_small", "urban_med", "shoebox_K5", "indoor_small"])
+def test_sah_top_bvh_gives_the_same_paths(sbr, name):
+    # the SAH-rebuilt top changes the tree, not the closest hits: identical path lists
+    sc = SCENES[name]()
+    d = sbr.scene_to_device(sc)
+    out = []
+    for sah in (False, True):
+        bvh = sbr.build_bvh(d["tri"], d["surface_id"], d["S"], sah_top=sah)
+        info = bvh.info()
+        assert info["n_nodes"] == max(1, len(sc["tri"]) - 1) and 1 <= info["depth"] <= 64
+        tr = sbr.trace(bvh, d["tx"], d["rx"], sc["N"], sc["K"], table_log2=18)
+        st = tr.stats()
+        pl = sbr.paths(tr, bvh)
+        out.append((st["ray_bounces"], to_numpy(pl.export())))
+    assert out[0][0] == out[1][0]
+    for k in out[0][1]:
+        assert np.array_equal(out[0][1][k], out[1][1][k]), k
