@@ -35,7 +35,8 @@ def test_surrogate_workflow_learns_path_loss(sbr):
     cov = float((Y[:, S.CH_COV] > 0.5).float().mean())
     assert 0.2 < cov <= 1.0
     lo, hi = S.x_box(sc, freqs)
-    m, hist, _ = S.train(X, Y, lo, hi, epochs=30, batch=2048)
+    # a small training set: the coarser feature bandwidth of the 1M-sample sweeps
+    m, hist, _ = S.train(X, Y, lo, hi, epochs=30, batch=2048, feat_log2_max=2.0)
     assert hist[-1] < 0.5 * hist[0], hist
     ev = S.evaluate(m, Xt, Yt)
     print(ev)
