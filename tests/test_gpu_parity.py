@@ -416,3 +416,24 @@ def test_sah_top_bvh_gives_the_same_paths(sbr, name):
     assert out[0][0] == out[1][0]
     for k in out[0][1]:
         assert np.array_equal(out[0][1][k], out[1][1][k]), k
+
+
+def test_sah_top_bvh_with_duplicated_faces(sbr):
+    # every face three times (same surface): equal centroids exercise the SAH build's
+    # split by position, and tied hits go to the lowest face id in both trees
+    sc = scenes.shoebox(N=61, K=4, sub=3)
+    tri = np.concatenate([sc["tri"]] * 3)
+    sid = np.concatenate([sc["surface_id"]] * 3)
+    sc = dict(sc, tri=tri, surface_id=sid)
+    d = sbr.scene_to_device(sc)
+    out = []
+    for sah in (False, True):
+        bvh = sbr.build_bvh(d["tri"], d["surface_id"], d["S"], sah_top=sah)
+        tr = sbr.trace(bvh, d["tx"], d["rx"], sc["N"], sc["K"], table_log2=16)
+        st = tr.stats()
+        out.append((st["ray_bounces"], to_numpy(sbr.paths(tr, bvh).export())))
+    assert out[0][0] == out[1][0]
+    for k in out[0][1]:
+        assert np.array_equal(out[0][1][k], out[1][1][k]), k
+    # the faces reported are the lowest ids: the first copy
+    assert np.all(out[0][1]["face"][out[0][1]["face"] >= 0] < len(tri) // 3)
