@@ -116,10 +116,10 @@ sbr_status sbr_build_bvh(const float* tri_xyz, const int32_t* surface_id, int64_
 /*
  * sbr_build_bvh_ex - sbr_build_bvh with build options (same arguments,
  * ownership and errors; flags 0 gives the same tree). SBR_BVH_SAH_TOP
- * rebuilds the levels above the subtrees of at most max(8, T/800) triangles
- * with a binned surface-area-heuristic build (about T/40 subtrees): on the
- * 51,600-triangle urban scene 6.7% fewer node visits per segment for about
- * 0.6 ms more build time, so it pays for scenes traced many times (batches,
+ * rebuilds the levels above the subtrees of at most max(8, T/400) triangles
+ * (about 650 of them) with a binned surface-area-heuristic build: on the
+ * 51,600-triangle urban scene 7% fewer node visits per segment for about
+ * 0.45 ms more build time, so it pays for scenes traced many times (batches,
  * many transmitters), not for one trace per build. Unknown flags are rejected.
  */
 sbr_status sbr_build_bvh_ex(const float* tri_xyz, const int32_t* surface_id, int64_t T, int32_t S,

@@ -251,8 +251,11 @@ __global__ void k_emit(int64_t n, const int32_t* __restrict__ left, const int32_
 // per axis over the item centroids), which reuses the node slots of the old
 // top (a binary tree over C items has C - 1 nodes, and the root stays node 0).
 // The items' boxes are the padded child boxes of their old parents, so the new
-// boxes stay conservative. Urban scene, 51,600 triangles, cut of 1,283
-// subtrees: 6.7% fewer node visits per segment than the Morton top.
+// boxes stay conservative. The cut holds about 650 subtrees (lim = n / 400):
+// on the urban scene (51,600 triangles) a cut of 1,300 subtrees gives 6.7%
+// fewer node visits per segment than the Morton top, one of 300 gives 6%, a
+// full SAH build 11%. Each warp gathers its bins lane by lane over all of a
+// task's items, so the top levels are serial: the build takes 0.2-1.2 ms.
 struct TopElem {
     float b[6];
     int32_t ref;
@@ -261,7 +264,7 @@ struct TopElem {
 struct TopTask {
     int32_t begin, count, slot, depth;
 };
-constexpr int kTopCap = 4096;      // items at most (else the Morton top is kept)
+constexpr int kTopCap = 2048;      // items at most (held in shared memory; else the Morton top is kept)
 constexpr int kTopWarps = 16;
 constexpr int kTopBins = 32;
 constexpr int kTopForceMedian = 48;   // depth from which splits are by position (ends the build)
@@ -310,10 +313,28 @@ __device__ __forceinline__ float box_area(const float* b) {
     return 2.f * (dx * dy + dy * dz + dz * dx);
 }
 
-// one warp: split one task, write its node, queue its children
-__device__ void top_task(const TopTask tk, const TopElem* __restrict__ in, TopElem* __restrict__ out,
-                         float4* __restrict__ nodes, const int32_t* __restrict__ slots, TopTask* __restrict__ next,
-                         int* s_next, int* s_slot, int* s_depth, int* s_cnt, unsigned* s_box) {
+// warp scan of per-bin (count, box) over the 32 bins held one per lane:
+// inclusive from bin 0 up (up) or from bin 31 down (!up)
+__device__ __forceinline__ void bin_scan(int& c, float* b, bool up) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (int o = 1; o < 32; o <<= 1) {
+        const bool take = up ? lane >= o : lane + o < 32;
+        const int oc = up ? __shfl_up_sync(FULL, c, o) : __shfl_down_sync(FULL, c, o);
+        float ob[6];
+        for (int q = 0; q < 6; ++q) ob[q] = up ? __shfl_up_sync(FULL, b[q], o) : __shfl_down_sync(FULL, b[q], o);
+        if (take) {
+            c += oc;
+            for (int q = 0; q < 3; ++q) { b[q] = fminf(b[q], ob[q]); b[3 + q] = fmaxf(b[3 + q], ob[3 + q]); }
+        }
+    }
+}
+
+// one warp: split one task, write its node, queue its children. The items sit
+// in shared memory; lane b owns bin b of each axis and gathers it over all the
+// task's items (no atomics), then warp scans give every split's two sides.
+__device__ void top_task(const TopTask tk, const TopElem* in, TopElem* out, float4* __restrict__ nodes,
+                         const int32_t* __restrict__ slots, TopTask* next, int* s_next, int* s_slot, int* s_depth) {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     const int b0 = tk.begin, n = tk.count;
@@ -332,65 +353,60 @@ __device__ void top_task(const TopTask tk, const TopElem* __restrict__ in, TopEl
         }
     float sc[3];
     for (int a = 0; a < 3; ++a) sc[a] = hi[a] > lo[a] ? (float)kTopBins / (hi[a] - lo[a]) : 0.f;
-    // bins (per warp): count and box of the items whose centroid falls in each
-    for (int k = lane; k < 3 * kTopBins; k += 32) {
-        s_cnt[k] = 0;
-        for (int q = 0; q < 3; ++q) { s_box[6 * k + q] = f2o(INFINITY); s_box[6 * k + 3 + q] = f2o(-INFINITY); }
-    }
-    __syncwarp();
-    for (int i = lane; i < n; i += 32) {
-        const TopElem e = in[b0 + i];
+    // this lane's bin (number lane) of each axis
+    int cnt[3] = {0, 0, 0};
+    float bx[3][6];
+    for (int a = 0; a < 3; ++a)
+        for (int q = 0; q < 3; ++q) { bx[a][q] = INFINITY; bx[a][3 + q] = -INFINITY; }
+    for (int i = 0; i < n; ++i) {
+        const TopElem& e = in[b0 + i];
         for (int a = 0; a < 3; ++a) {
             if (sc[a] == 0.f) continue;
             const int bin = min(kTopBins - 1, (int)((0.5f * (e.b[a] + e.b[3 + a]) - lo[a]) * sc[a]));
-            const int k = a * kTopBins + bin;
-            atomicAdd(&s_cnt[k], 1);
-            for (int q = 0; q < 3; ++q) {
-                atomicMin(&s_box[6 * k + q], f2o(e.b[q]));
-                atomicMax(&s_box[6 * k + 3 + q], f2o(e.b[3 + q]));
-            }
+            if (bin != lane) continue;
+            ++cnt[a];
+            for (int q = 0; q < 3; ++q) { bx[a][q] = fminf(bx[a][q], e.b[q]); bx[a][3 + q] = fmaxf(bx[a][3 + q], e.b[3 + q]); }
         }
     }
-    __syncwarp();
-    // cost of "bins below s go left" for s = lane (1..31) on each axis
+    // split "bins below s go left" with s = lane (1..31): left = prefix through bin s-1, right =
+    // suffix from bin s; each lane keeps its best axis with the counts and boxes of both sides
     float best = INFINITY;
-    int bcode = 0x7fffffff;
-    if (lane >= 1 && tk.depth < kTopForceMedian) {
-        for (int a = 0; a < 3; ++a) {
-            if (sc[a] == 0.f) continue;
-            float L[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-            float R[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-            int nl = 0, nr = 0;
-            for (int k = 0; k < kTopBins; ++k) {
-                const int j = a * kTopBins + k;
-                const int c = s_cnt[j];
-                if (c == 0) continue;
-                float* D = k < lane ? L : R;
-                if (k < lane) nl += c; else nr += c;
-                for (int q = 0; q < 3; ++q) {
-                    D[q] = fminf(D[q], o2f(s_box[6 * j + q]));
-                    D[3 + q] = fmaxf(D[3 + q], o2f(s_box[6 * j + 3 + q]));
-                }
-            }
-            if (nl == 0 || nr == 0) continue;
-            const float cost = box_area(L) * nl + box_area(R) * nr;
-            const int code = a * kTopBins + lane;
-            if (cost < best || (cost == best && code < bcode)) { best = cost; bcode = code; }
+    int bcode = 0x7fffffff, bnl = 0;
+    float bl[6], br[6];
+    for (int a = 0; a < 3; ++a) {
+        int cp = cnt[a], cs = cnt[a];
+        float pb[6], sb6[6];
+        for (int q = 0; q < 6; ++q) { pb[q] = bx[a][q]; sb6[q] = bx[a][q]; }
+        bin_scan(cp, pb, true);
+        bin_scan(cs, sb6, false);
+        // the prefix through bin lane - 1 comes from the lane below
+        const int nl = __shfl_up_sync(FULL, cp, 1);
+        float L[6];
+        for (int q = 0; q < 6; ++q) L[q] = __shfl_up_sync(FULL, pb[q], 1);
+        if (lane == 0 || sc[a] == 0.f || tk.depth >= kTopForceMedian || nl == 0 || cs == 0) continue;
+        const float cost = box_area(L) * nl + box_area(sb6) * cs;
+        const int code = a * kTopBins + lane;
+        if (cost < best || (cost == best && code < bcode)) {
+            best = cost; bcode = code; bnl = nl;
+            for (int q = 0; q < 6; ++q) { bl[q] = L[q]; br[q] = sb6[q]; }
         }
     }
+    // the warp's best split (ties to the lowest axis, then the lowest s)
+    float wb = best;
+    int wc = bcode;
     for (int o = 16; o; o >>= 1) {
-        const float ob = __shfl_xor_sync(FULL, best, o);
-        const int oc = __shfl_xor_sync(FULL, bcode, o);
-        if (ob < best || (ob == best && oc < bcode)) { best = ob; bcode = oc; }
+        const float ob = __shfl_xor_sync(FULL, wb, o);
+        const int oc = __shfl_xor_sync(FULL, wc, o);
+        if (ob < wb || (ob == wb && oc < wc)) { wb = ob; wc = oc; }
     }
-    const bool by_pos = !(best < INFINITY);   // no split with both sides non-empty: split by position
-    const int ax = by_pos ? 0 : bcode / kTopBins, sb = by_pos ? 0 : bcode % kTopBins;
-    int nl = n / 2;
-    if (!by_pos) {
-        nl = 0;
-        for (int k = 0; k < sb; ++k) nl += s_cnt[ax * kTopBins + k];
+    const bool by_pos = !(wb < INFINITY);   // no split with both sides non-empty: split by position
+    const int ax = by_pos ? 0 : wc / kTopBins, sb = by_pos ? 0 : wc % kTopBins;
+    const int nl = by_pos ? n / 2 : __shfl_sync(FULL, bnl, sb);
+    float sl[6], sr[6];
+    for (int q = 0; q < 6; ++q) {
+        sl[q] = __shfl_sync(FULL, bl[q], by_pos ? 0 : sb);
+        sr[q] = __shfl_sync(FULL, br[q], by_pos ? 0 : sb);
     }
-    __syncwarp();   // the bins are free again after this point
     // stable partition into out[b0, b0 + n)
     int cl = 0, cr = 0;
     for (int base = 0; base < n; base += 32) {
@@ -413,21 +429,21 @@ __device__ void top_task(const TopTask tk, const TopElem* __restrict__ in, TopEl
         cr += __popc(mr);
     }
     __syncwarp();
-    // boxes of the two sides
-    float bl[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-    float br[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-    for (int i = lane; i < n; i += 32) {
-        float* D = i < nl ? bl : br;
-        const TopElem& e = out[b0 + i];
-        for (int q = 0; q < 3; ++q) { D[q] = fminf(D[q], e.b[q]); D[3 + q] = fmaxf(D[3 + q], e.b[3 + q]); }
-    }
-    for (int o = 16; o; o >>= 1)
-        for (int q = 0; q < 3; ++q) {
-            bl[q] = fminf(bl[q], __shfl_xor_sync(FULL, bl[q], o));
-            bl[3 + q] = fmaxf(bl[3 + q], __shfl_xor_sync(FULL, bl[3 + q], o));
-            br[q] = fminf(br[q], __shfl_xor_sync(FULL, br[q], o));
-            br[3 + q] = fmaxf(br[3 + q], __shfl_xor_sync(FULL, br[3 + q], o));
+    if (by_pos) {   // side boxes by reduction over the two halves
+        for (int q = 0; q < 3; ++q) { sl[q] = INFINITY; sl[3 + q] = -INFINITY; sr[q] = INFINITY; sr[3 + q] = -INFINITY; }
+        for (int i = lane; i < n; i += 32) {
+            float* D = i < nl ? sl : sr;
+            const TopElem& e = out[b0 + i];
+            for (int q = 0; q < 3; ++q) { D[q] = fminf(D[q], e.b[q]); D[3 + q] = fmaxf(D[3 + q], e.b[3 + q]); }
         }
+        for (int o = 16; o; o >>= 1)
+            for (int q = 0; q < 3; ++q) {
+                sl[q] = fminf(sl[q], __shfl_xor_sync(FULL, sl[q], o));
+                sl[3 + q] = fmaxf(sl[3 + q], __shfl_xor_sync(FULL, sl[3 + q], o));
+                sr[q] = fminf(sr[q], __shfl_xor_sync(FULL, sr[q], o));
+                sr[3 + q] = fmaxf(sr[3 + q], __shfl_xor_sync(FULL, sr[3 + q], o));
+            }
+    }
     if (lane == 0) {
         int32_t ref[2];
         const int cb[2] = {b0, b0 + nl}, cn[2] = {nl, n - nl};
@@ -441,38 +457,45 @@ __device__ void top_task(const TopTask tk, const TopElem* __restrict__ in, TopEl
             }
         }
         float4* o = nodes + 4 * (int64_t)tk.slot;
-        o[0] = make_float4(bl[0], bl[1], bl[2], bl[3]);
-        o[1] = make_float4(bl[4], bl[5], br[0], br[1]);
-        o[2] = make_float4(br[2], br[3], br[4], br[5]);
+        o[0] = make_float4(sl[0], sl[1], sl[2], sl[3]);
+        o[1] = make_float4(sl[4], sl[5], sr[0], sr[1]);
+        o[2] = make_float4(sr[2], sr[3], sr[4], sr[5]);
         o[3] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), 0.f, 0.f);
     }
     __syncwarp();
 }
 
-// one block: the top tree over the cut, level by level (every task of a level
-// is independent: disjoint item ranges, distinct node slots)
+// one block: the top tree over the cut, level by level (the tasks of a level
+// are independent: disjoint item ranges, distinct node slots); items and task
+// lists in shared memory
+constexpr int kTopSmem = 2 * kTopCap * (int)sizeof(TopElem) + 2 * (kTopCap / 2 + 1) * (int)sizeof(TopTask);
+
 __global__ void __launch_bounds__(32 * kTopWarps)
-k_top_sah(float4* __restrict__ nodes, TopElem* E0, TopElem* E1, TopTask* T0, TopTask* T1,
-          const int32_t* __restrict__ slots, const int* n_cut, const int* n_slot, int32_t* d_depth) {
-    __shared__ int s_cnt[kTopWarps][3 * kTopBins];
-    __shared__ unsigned s_box[kTopWarps][3 * kTopBins * 6];
+k_top_sah(float4* __restrict__ nodes, const TopElem* __restrict__ E, const int32_t* __restrict__ slots,
+          const int* n_cut, const int* n_slot, int32_t* d_depth) {
+    extern __shared__ unsigned char s_top[];
+    TopElem* S0 = reinterpret_cast<TopElem*>(s_top);
+    TopElem* S1 = S0 + kTopCap;
+    TopTask* Q0 = reinterpret_cast<TopTask*>(S1 + kTopCap);
+    TopTask* Q1 = Q0 + kTopCap / 2 + 1;
     __shared__ int s_nt, s_next, s_slot, s_depth;
     const int warp = threadIdx.x >> 5;
     const int C = *n_cut;
     // a cut of C items hangs below C - 1 old nodes: the root and C - 2 reusable slots
     if (C < 2 || C > kTopCap || *n_slot != C - 2) return;
+    for (int i = threadIdx.x; i < C; i += blockDim.x) S0[i] = E[i];
     if (threadIdx.x == 0) {
-        T0[0] = TopTask{0, C, 0, 1};
+        Q0[0] = TopTask{0, C, 0, 1};
         s_nt = 1; s_next = 0; s_slot = 0; s_depth = 0;
     }
     __syncthreads();
-    TopElem *in = E0, *out = E1;
-    TopTask *tin = T0, *tout = T1;
+    TopElem *in = S0, *out = S1;
+    TopTask *tin = Q0, *tout = Q1;
     for (int level = 0; level < kTopMaxLevels; ++level) {
         const int nt = s_nt;
         if (nt == 0) break;
         for (int t = warp; t < nt; t += kTopWarps)
-            top_task(tin[t], in, out, nodes, slots, tout, &s_next, &s_slot, &s_depth, s_cnt[warp], s_box[warp]);
+            top_task(tin[t], in, out, nodes, slots, tout, &s_next, &s_slot, &s_depth);
         __syncthreads();
         if (threadIdx.x == 0) { s_nt = s_next; s_next = 0; }
         __syncthreads();
@@ -612,27 +635,27 @@ sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, int leaf_
     ::sbr::note_launch(), k_emit<<<blocks_for(nn), kThreads, 0, s>>>(n, left, right, span, leaf_max, lbox, ibox, pad_rel, out->nodes,
                                                out->d_root);
     SBR_TRY_CUDA(cudaGetLastError());
-    // the cut: subtrees of at most lim primitives (about n / 40 of them); lim is
-    // at least the leaf size, so every collapsed leaf is an item of the cut
-    const int64_t lim = std::max<int64_t>(std::max(leaf_max, 8), n / 800);
+    // the cut: subtrees of at most lim primitives (about 650 of them at any n);
+    // lim is at least the leaf size, so every collapsed leaf is an item of the cut
+    const int64_t lim = std::max<int64_t>(std::max(leaf_max, 8), n / 400);
     if (top_sah && n > lim) {
-        TopElem *E0, *E1;
-        TopTask *T0, *T1;
+        static bool attr = false;
+        if (!attr) {
+            SBR_TRY_CUDA(cudaFuncSetAttribute(k_top_sah, cudaFuncAttributeMaxDynamicSharedMemorySize, kTopSmem));
+            attr = true;
+        }
+        TopElem* E;
         int32_t* slots;
         int* cnt;
-        SBR_TRY(dalloc_n(&E0, kTopCap, s));
-        SBR_TRY(dalloc_n(&E1, kTopCap, s));
-        SBR_TRY(dalloc_n(&T0, kTopCap, s));
-        SBR_TRY(dalloc_n(&T1, kTopCap, s));
+        SBR_TRY(dalloc_n(&E, kTopCap, s));
         SBR_TRY(dalloc_n(&slots, kTopCap, s));
         SBR_TRY(dalloc_n(&cnt, 2, s));
         SBR_TRY_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), s));
-        ::sbr::note_launch(), k_top_cut<<<blocks_for(nn), kThreads, 0, s>>>(nn, span, hd, out->nodes, (int)lim, E0, cnt,
+        ::sbr::note_launch(), k_top_cut<<<blocks_for(nn), kThreads, 0, s>>>(nn, span, hd, out->nodes, (int)lim, E, cnt,
                                                                           slots, cnt + 1);
-        ::sbr::note_launch(), k_top_sah<<<1, 32 * kTopWarps, 0, s>>>(out->nodes, E0, E1, T0, T1, slots, cnt, cnt + 1,
-                                                                     d_depth);
+        ::sbr::note_launch(), k_top_sah<<<1, 32 * kTopWarps, kTopSmem, s>>>(out->nodes, E, slots, cnt, cnt + 1, d_depth);
         SBR_TRY_CUDA(cudaGetLastError());
-        dfree(E0, s); dfree(E1, s); dfree(T0, s); dfree(T1, s); dfree(slots, s); dfree(cnt, s);
+        dfree(E, s); dfree(slots, s); dfree(cnt, s);
     }
     out->order = reinterpret_cast<int32_t*>(idx);
     out->n_nodes = (int32_t)nn;
