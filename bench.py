@@ -324,6 +324,7 @@ def run_gpu(args):
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     e2e_t, e2e_rb, d2h = 0.0, 0, 0
     pinned = None   # pinned host destinations of the step's results, sized by the first step
+    side = torch.cuda.Stream()   # the path list goes to the host on it while gains and PDP run
     for it in range(0 if args.no_e2e else max(1, args.steps // 2) + 1):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -331,15 +332,24 @@ def run_gpu(args):
         dd = dict(d)
         for k, v in host.items():
             dd[k] = v.to(dev, non_blocking=True)
-        bvh, tr, pl, g, pdp, st, stats = step(dd)
+        bvh = sbr.build_bvh(dd["tri"], dd["surface_id"], dd["S"])
+        tr = sbr.trace(bvh, dd["tx"], dd["rx"], N, K, alpha=alpha, timing=True)
+        pl = sbr.paths(tr, bvh)
         if pinned is None or pinned["rx"].shape[0] != pl.n:
             ex = pl.export()
             pinned = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in ex.items()}
-            for k, v in (("g", g), ("pdp", pdp), ("st", st)):
-                pinned[k] = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
-        pl.export(out=pinned)
+        ev_pl = torch.cuda.Event()
+        ev_pl.record()
+        side.wait_event(ev_pl)
+        pl.export(out=pinned, stream=side)
+        g = sbr.path_gains(pl, dd["mats"], dd["freqs"], dd["gamma"], dd["disp"], dd["pol"])
+        pdp, st = sbr.pdp_angles(pl, g, 0, fc, 1e-9, 2048)
         for k, v in (("g", g), ("pdp", pdp), ("st", st)):
+            if k not in pinned or pinned[k].shape != v.shape:
+                pinned[k] = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
             pinned[k].copy_(v, non_blocking=True)
+        stats = tr.stats()
+        torch.cuda.current_stream().wait_stream(side)
         e1.record()
         e1.synchronize()
         if it == 0:
