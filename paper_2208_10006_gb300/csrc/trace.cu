@@ -442,6 +442,15 @@ __device__ void receive(const TraceArgs& a, int bounce, const df3& o, const df3&
     float rmax = al.x * (L.hi + t_end) * 0.57735027f * (1.f + 1e-4f) +
                  1e-5f * (fabsf(r.o.x) + fabsf(r.o.y) + fabsf(r.o.z) + L.hi + t_end);
     float tmax = t_end * (1.f + 1e-5f) + rmax;
+    // the segment against the receivers' (padded) root box grown by rmax: it
+    // contains every grown child box, so a miss here is a miss of the whole
+    // tree, and most segments pass far from every receiver
+    {
+        float tn;
+        if (!box_hit(a.rx_root[0] - rmax, a.rx_root[1] - rmax, a.rx_root[2] - rmax, a.rx_root[3] + rmax,
+                     a.rx_root[4] + rmax, a.rx_root[5] + rmax, r, tmax, tn))
+            return;
+    }
     int sp = 0;
     int32_t node = 0;
     for (;;) {
