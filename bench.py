@@ -50,7 +50,7 @@ ALG_BYTES_PER_RAY_BOUNCE = 2 * RAY_REC_BYTES
 # DRAM bytes of one k_trace_df launch on the headline workload (N = 1000), from
 # one ncu capture of the launch (dram__bytes_read.sum + dram__bytes_write.sum,
 # profiles/k_trace_df_urban_N1000_dram.md); None once the kernel has changed
-TRACE_DRAM_BYTES = None
+TRACE_DRAM_BYTES = 264_006_144 + 117_032_704
 SEQ_BYTES = 8           # surface id and face id appended per reflection
 DIR_BYTES = 24          # launch direction of a ray, double-float
 
