@@ -639,11 +639,8 @@ sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, int leaf_
     // lim is at least the leaf size, so every collapsed leaf is an item of the cut
     const int64_t lim = std::max<int64_t>(std::max(leaf_max, 8), n / 400);
     if (top_sah && n > lim) {
-        static bool attr = false;
-        if (!attr) {
-            SBR_TRY_CUDA(cudaFuncSetAttribute(k_top_sah, cudaFuncAttributeMaxDynamicSharedMemorySize, kTopSmem));
-            attr = true;
-        }
+        static std::atomic<unsigned long long> attr{0};
+        SBR_TRY(set_smem_once((const void*)k_top_sah, kTopSmem, &attr));
         TopElem* E;
         int32_t* slots;
         int* cnt;

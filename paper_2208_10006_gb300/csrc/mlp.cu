@@ -494,12 +494,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_mlp_infer(const __grid_constan
 
 template <int kN, int kMode>
 sbr_status gemm_launch(const GemmArgs& a, int splits, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        SBR_TRY_CUDA(cudaFuncSetAttribute(k_gemm<kN, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          GemmShape<kN>::kSmemReq));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    SBR_TRY(set_smem_once((const void*)k_gemm<kN, kMode>, GemmShape<kN>::kSmemReq, &attr));
     dim3 grid(a.M / 128, a.N / kN, splits);
     ::sbr::note_launch(), k_gemm<kN, kMode><<<grid, kGThreads, GemmShape<kN>::kSmemReq, s>>>(a);
     SBR_TRY_CUDA(cudaGetLastError());
@@ -693,11 +689,8 @@ sbr_status sync_bf16(sbr_mlp* m, cudaStream_t s) {
 
 sbr_status infer_fused(const sbr_mlp* m, const float* x, int B, float* y, cudaStream_t s) {
     const sbr_mlp_config& c = m->cfg;
-    static bool attr = false;
-    if (!attr) {
-        SBR_TRY_CUDA(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kInferSmem));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    SBR_TRY(set_smem_once((const void*)k_mlp_infer, kInferSmem, &attr));
     InferArgs a{};
     a.x = x;
     a.B = B;

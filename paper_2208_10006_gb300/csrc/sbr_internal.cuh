@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libsbr.
 // Not part of the public ABI (include/sbr.h).
 #pragma once
+#include <atomic>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -60,6 +61,17 @@ sbr_status dalloc_n(T** p, size_t n, cudaStream_t s) {
     return dalloc(reinterpret_cast<void**>(p), n * sizeof(T) + (n == 0 ? 16 : 0), s);
 }
 int sm_count();
+// a kernel's dynamic shared-memory limit, set once per device (the attribute
+// belongs to the current device's context); devmask holds the devices done
+inline sbr_status set_smem_once(const void* func, int bytes, std::atomic<unsigned long long>* devmask) {
+    int dev = 0;
+    SBR_TRY_CUDA(cudaGetDevice(&dev));
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (devmask->load() & bit)) return SBR_OK;
+    SBR_TRY_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    if (bit) devmask->fetch_or(bit);
+    return SBR_OK;
+}
 // count of kernel launches made by the library in this process
 void note_launch();
 // test-only fault injection (SBR_FAULT=alloc|timeout)

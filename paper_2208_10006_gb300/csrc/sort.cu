@@ -349,12 +349,8 @@ sbr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits,
     }
     if (n <= kSmallMax) {
         const size_t smem = sizeof(uint32_t) * 4 * kSmallMax;
-        static bool attr = false;
-        if (!attr) {
-            SBR_TRY_CUDA(cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem));
-            attr = true;
-        }
+        static std::atomic<unsigned long long> attr{0};
+        SBR_TRY(set_smem_once((const void*)k_sort_small, (int)smem, &attr));
         ::sbr::note_launch(), k_sort_small<<<1, kSmallThreads, smem, s>>>(keys, vals, (int)n, (bits + 7) / 8);
         SBR_TRY_CUDA(cudaGetLastError());
         return SBR_OK;
