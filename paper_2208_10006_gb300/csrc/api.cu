@@ -37,8 +37,8 @@ sbr_status status_from_bits(uint32_t bits) {
 }
 
 // The stream-ordered pool of each device keeps freed blocks instead of returning
-// them to the driver at every synchronisation (its default), so that the ray
-// queues of consecutive traces reuse the same memory.
+// them to the CUDA driver at every synchronisation (its default), so that the
+// buffers of consecutive calls reuse the same memory.
 static void keep_pool_memory() {
     static std::mutex mu;
     static bool done[256] = {};
