@@ -8,6 +8,7 @@
 // node and tests two boxes. Boxes are padded outward by a relative margin so
 // that FP32 traversal never culls a box that the exact ray touches.
 #include <algorithm>
+#include <cuda/atomic>
 #include <cstdlib>
 
 #include "dfloat.cuh"
@@ -164,15 +165,15 @@ __global__ void k_refit(const float* __restrict__ prim_box, const int32_t* __res
     if (j >= n) return;
     const float* src = prim_box + 6 * (int64_t)order[j];
     for (int k = 0; k < 6; ++k) lbox[6 * j + k] = src[k];
-    __threadfence();
     if (n < 2) {
         *depth = 1;
         return;
     }
     int32_t node = parent_leaf[j];
     while (node >= 0) {
-        if (atomicAdd(&flag[node], 1) == 0) return;  // the sibling subtree is not done yet
-        __threadfence();
+        // release: this thread's boxes before the count; acquire: the sibling's after it
+        cuda::atomic_ref<int32_t, cuda::thread_scope_device> cnt(flag[node]);
+        if (cnt.fetch_add(1, cuda::memory_order_acq_rel) == 0) return;  // the sibling subtree is not done yet
         float a[6], b[6];
         int32_t l = left[node], r = right[node];
         ld_box(l < 0 ? lbox + 6 * (int64_t)(~l) : ibox + 6 * (int64_t)l, a);
@@ -187,7 +188,6 @@ __global__ void k_refit(const float* __restrict__ prim_box, const int32_t* __res
         const int hl = l < 0 ? 1 : ((volatile int32_t*)hd)[l], hr = r < 0 ? 1 : ((volatile int32_t*)hd)[r];
         const int h = 1 + (hl > hr ? hl : hr);
         ((volatile int32_t*)hd)[node] = h;
-        __threadfence();
         if (parent_int[node] < 0) *depth = h;
         node = parent_int[node];
     }
