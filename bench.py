@@ -102,21 +102,28 @@ class ClockSampler:
         self.lines = []
 
     def start(self):
+        """Start sampling every 10 ms and wait (up to 3 s) for the first sample,
+        so that the timed region that follows is covered."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_end = time.perf_counter() + 3.0
+            while not self.lines and time.perf_counter() < t_end:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self) -> dict:
+    def stop(self, window=None) -> dict:
+        """Summary of the samples taken in window = (t0, t1) (perf_counter
+        seconds; the last sample before t0 counts too), else of all."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -124,9 +131,13 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        lines = self.lines
+        if window is not None:
+            before = [x for x in lines if x[0] < window[0]]
+            lines = before[-1:] + [x for x in lines if window[0] <= x[0] <= window[1]]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for _, ln in lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -277,10 +288,11 @@ def run_gpu(args):
     n_launch = sbr.launch_count() - c0   # library kernels in one step (counted at each launch site)
 
     clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()   # sampling before the barrier: the timed region below is covered
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    t_clk0 = time.perf_counter()
     times, rb, bounce_ms, bounce_bytes = [], 0, 0.0, 0
     for _ in range(args.steps):
         flush.zero_()
@@ -295,11 +307,11 @@ def run_gpu(args):
         q = stats["queue"]
         bounce_ms += sum(stats["bounce_ms"][:K + 1])
         # depth first from bounce 0: each ray's launch direction is read once and
-        # each reflection appends its surface id; no ray record goes through memory
+        # each reflection appends its surface and face id; no ray record goes through memory
         bounce_bytes += DIR_BYTES * q[0] + SEQ_BYTES * sum(q[1:K + 1])
         del out
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    clk = clocks.stop(window=(t_clk0, time.perf_counter()))
     t_total = sum(times) / 1e3
     t_total, rb_all = reduce_over_ranks(t_total, float(rb), device=dev)
     value = rb_all / t_total / 1e6
@@ -802,7 +814,7 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__,
                                  formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
