@@ -51,8 +51,29 @@ ALG_BYTES_PER_RAY_BOUNCE = 2 * RAY_REC_BYTES
 # one ncu capture of the launch (dram__bytes_read.sum + dram__bytes_write.sum,
 # profiles/k_trace_df_urban_N1000_dram.md); None once the kernel has changed
 TRACE_DRAM_BYTES = 264_006_144 + 117_032_704
+# warp instructions issued by one k_trace_df launch on the same workload, from
+# one ncu capture (smsp__inst_executed.sum, profiles/k_trace_df_urban_N1000_issue.md);
+# None once the kernel has changed. The issue peak is one warp instruction per
+# clock on each of the 4 schedulers of the 152 SMs
+TRACE_WARP_INST = 2_752_797_180
+SM_COUNT = 152
+SCHEDULERS_PER_SM = 4
 SEQ_BYTES = 8           # surface id and face id appended per reflection
 DIR_BYTES = 24          # launch direction of a ray, double-float
+
+
+def issue_roofline(launch_ms, clk, N):
+    """Instruction-issue view of the trace kernel: warp instructions per launch
+    (counted once by ncu on the N = 1000 workload) over the live launch time,
+    against the issue peak at the median SM clock sampled in the timed region."""
+    mhz = clk.get("sm_mhz") if clk else None
+    if N != 1000 or not mhz:
+        return None
+    achieved = TRACE_WARP_INST / (launch_ms / 1e3) / 1e9
+    peak = SM_COUNT * SCHEDULERS_PER_SM * mhz / 1e3
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
+            "frac": achieved / peak, "warp_inst_per_launch": TRACE_WARP_INST,
+            "peak_from": "152 SMs x 4 schedulers x 1 warp instruction per clock x median SM clock"}
 
 
 def load_peaks():
@@ -422,7 +443,8 @@ def run_gpu(args):
             "streamed_bytes_per_launch": bounce_bytes / args.steps,
             "streamed_bytes": "24 B launch direction per ray + 8 B surface and face id per reflection",
             "avg_launch_ms": bounce_ms / args.steps,
-            "kernel_share_of_step": bounce_ms / sum(times), "l2": l2}
+            "kernel_share_of_step": bounce_ms / sum(times), "l2": l2,
+            "issue": issue_roofline(bounce_ms / args.steps, clk, N)}
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(times),
