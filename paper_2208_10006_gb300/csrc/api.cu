@@ -96,7 +96,6 @@ int sm_count() {
 
 namespace {
 __global__ void k_set_u64(unsigned long long* dst, unsigned long long v) { *dst = v; }
-__global__ void k_set_f64(double* dst, double v) { *dst = v; }
 }  // namespace
 
 sbr_status set_u64(unsigned long long* dst, unsigned long long v, cudaStream_t s) {
@@ -105,11 +104,6 @@ sbr_status set_u64(unsigned long long* dst, unsigned long long v, cudaStream_t s
     return SBR_OK;
 }
 
-sbr_status set_f64(double* dst, double v, cudaStream_t s) {
-    ::sbr::note_launch(), k_set_f64<<<1, 1, 0, s>>>(dst, v);
-    SBR_TRY_CUDA(cudaGetLastError());
-    return SBR_OK;
-}
 
 static int current_device() {
     int d = 0;
@@ -248,13 +242,9 @@ sbr_status sbr_trace(const sbr_bvh* b, const sbr_trace_params* p, sbr_trace_resu
         }
     }
     if (st == SBR_OK) st = dalloc_n(&tr->d_alpha, 1, s);
-    if (st == SBR_OK) {
-        if (p->alpha > 0.0) {
-            st = set_f64(tr->d_alpha, p->alpha, s);
-        } else {
-            st = launch_alpha(p->subdiv_N, tr->d_alpha, s);
-        }
-    }
+    // a given alpha is stored by the trace's set-up launch; the default one
+    // (alpha = 0) is computed from the launch grid first
+    if (st == SBR_OK && !(p->alpha > 0.0)) st = launch_alpha(p->subdiv_N, tr->d_alpha, s);
     if (st == SBR_OK) st = trace_run(b, tr, s);
     if (st != SBR_OK) {
         sbr_trace_free(tr);
@@ -318,8 +308,11 @@ sbr_status sbr_paths(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     SBR_SAME_DEVICE(tr);
     SBR_SAME_DEVICE(b);
     cudaStream_t s = (cudaStream_t)stream;
-    // the trace must have finished cleanly before its table is read
-    {
+    // the trace must have finished cleanly before its table is read. On the
+    // trace's own stream the path kernels are ordered after it and its status
+    // is read together with the key count (paths_run's first wait); on another
+    // stream the host waits for the trace here
+    if (tr->stream != s) {
         unsigned bits = 0;
         SBR_TRY_CUDA(cudaMemcpyAsync(&bits, &tr->cnt->status, sizeof bits, cudaMemcpyDeviceToHost, tr->stream));
         SBR_TRY_CUDA(cudaStreamSynchronize(tr->stream));

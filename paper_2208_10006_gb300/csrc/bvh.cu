@@ -217,7 +217,10 @@ __global__ void k_emit(int64_t n, const int32_t* __restrict__ left, const int32_
     float b0[6], b1[6];
     int32_t r0, r1;
     if (n == 1) {
-        // single primitive: both children name leaf 0; traversals skip r1 == r0
+        // single primitive: both children name leaf 0. The FP32 closest-hit
+        // traversal then tests that leaf twice, which changes nothing (a repeated
+        // face neither improves the best hit nor enters the uncertain list
+        // twice); the other traversals skip r1 == r0
         for (int k = 0; k < 6; ++k) b0[k] = b1[k] = lbox[k];
         r0 = ~0; r1 = ~0;
     } else {

@@ -202,9 +202,17 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     SBR_TRY_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned), s));
     ::sbr::note_launch(), k_collect<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(tr->ht_state, cap, idx, count);
     SBR_TRY_CUDA(cudaGetLastError());
-    unsigned h_count = 0;
+    unsigned h_count = 0, h_trace = 0;
     SBR_TRY_CUDA(cudaMemcpyAsync(&h_count, count, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    SBR_TRY_CUDA(cudaMemcpyAsync(&h_trace, &tr->cnt->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     SBR_TRY_CUDA(cudaStreamSynchronize(s));
+    // a trace that ended with an error (full dedup table, stack overflow, ...)
+    // yields no path list; the table was read only as plain memory
+    if (const sbr_status ts = status_from_bits(h_trace); ts != SBR_OK) {
+        dfree(count, s);
+        dfree(idx, s);
+        return ts;
+    }
     const int64_t n = h_count;
     pl->n_keys = n;
     // sort keys: least significant word first (stable LSD over words)

@@ -87,7 +87,6 @@ sbr_status dir_table_build(int32_t N, float4** dir_a, float2** dir_b, cudaStream
 void note_launches(long long n);
 // enqueue a device-side store of a value (no host buffer outlives the call)
 sbr_status set_u64(unsigned long long* dst, unsigned long long v, cudaStream_t s);
-sbr_status set_f64(double* dst, double v, cudaStream_t s);
 
 // ---------------------------------------------------------------- icosahedron
 struct Ico {

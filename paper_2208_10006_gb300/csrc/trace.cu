@@ -29,6 +29,7 @@
 // traversal runs on the high words and carries the per-triangle cost.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 
 #include "batch.cuh"
 #include "dfloat.cuh"
@@ -243,7 +244,7 @@ __device__ int32_t traverse32(const A& a, const Ray32& r, int prev, Trav& tv, in
             if (kCount) ++*visits;
             float tn0, tn1;
             bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, tv.lim, tn0);
-            bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, tv.lim, tn1) && r1 != r0;
+            bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, tv.lim, tn1);
             if (h0 && h1) {
                 bool first0 = tn0 <= tn1;
                 if (sp < kStack) stack[sp++] = first0 ? r1 : r0;
@@ -661,6 +662,11 @@ template <bool kCount>
 __global__ void __launch_bounds__(kTraceThreads, 8)
 k_trace_df(const __grid_constant__ TraceArgs a) {
     int stack[kStack];
+    // rays entering each bounce, counted per block in shared memory and added
+    // to the global counters once at the end
+    __shared__ unsigned s_queue[kKmax + 2];
+    if (threadIdx.x < kKmax + 2) s_queue[threadIdx.x] = 0u;
+    __syncthreads();
     unsigned visits = 0, tests = 0, rx_visits = 0, edge = 0;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -739,11 +745,15 @@ k_trace_df(const __grid_constant__ TraceArgs a) {
                 has = false;
             }
         }
-        // rays entering bounce b are counted in queue[b]: one atomic per distinct b in the warp
+        // rays entering bounce b are counted in queue[b]: one shared atomic per
+        // distinct b in the warp
         const unsigned grp = __match_any_sync(FULL, entered);
-        if (entered >= 0 && lane == __ffs(grp) - 1)
-            atomicAdd(&a.cnt->queue[entered], (unsigned long long)__popc(grp));
+        if (entered >= 0 && lane == __ffs(grp) - 1) atomicAdd(&s_queue[entered], (unsigned)__popc(grp));
     }
+    // every warp of the block leaves the loop above (no early return)
+    __syncthreads();
+    if (threadIdx.x < kKmax + 2 && s_queue[threadIdx.x])
+        atomicAdd(&a.cnt->queue[threadIdx.x], (unsigned long long)s_queue[threadIdx.x]);
     if (kCount) {
         unsigned long long v = visits, w = tests, x = rx_visits, e = edge;
         for (int s = 16; s; s >>= 1) {
@@ -992,26 +1002,40 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_batch_df(const __gri
     }
 }
 
-__global__ void k_rx_df(const double* __restrict__ rx, int32_t n, float4* __restrict__ out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    df x = df_from_double(rx[3 * i]), y = df_from_double(rx[3 * i + 1]), z = df_from_double(rx[3 * i + 2]);
-    out[2 * i] = make_float4(x.hi, y.hi, z.hi, 0.f);
-    out[2 * i + 1] = make_float4(x.lo, y.lo, z.lo, 0.f);
-}
+// Set-up of one trace in one launch: zeroed counters with queue[0] = R, an
+// empty dedup table, per receiver its point box (FP32, rounded outward) and its
+// double-float position, and the reception constants alpha and alpha^2 / 3 as
+// double-float (alpha_in > 0 is stored to *alpha first; otherwise *alpha was
+// computed on the device before this launch).
+static_assert(offsetof(TraceCountersDev, queue) == 0 && sizeof(TraceCountersDev) % 8 == 0,
+              "counters are 64-bit words, queue[0] first");
 
-__global__ void k_alpha_df(const double* __restrict__ alpha, float4* __restrict__ out) {
-    double al = *alpha;
-    df a1 = df_from_double(al), a2 = df_from_double(al * al / 3.0);
-    *out = make_float4(a1.hi, a1.lo, a2.hi, a2.lo);
-}
-
-__global__ void k_rx_boxes(const double* __restrict__ rx, int32_t n, float* __restrict__ box) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int k = 0; k < 3; ++k) {
-        box[6 * i + k] = __double2float_rd(rx[3 * i + k]);
-        box[6 * i + 3 + k] = __double2float_ru(rx[3 * i + k]);
+__global__ void k_trace_setup(TraceCountersDev* __restrict__ cnt, unsigned long long R,
+                              uint32_t* __restrict__ ht_state, unsigned long long* __restrict__ ht_val,
+                              size_t cap, const double* __restrict__ rx, int32_t n_rx,
+                              float* __restrict__ rx_box, float4* __restrict__ rx_df, double* alpha,
+                              double alpha_in, float4* __restrict__ alpha_df) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < sizeof(TraceCountersDev) / 8) reinterpret_cast<unsigned long long*>(cnt)[i] = i == 0 ? R : 0ull;
+    if (i < cap) {
+        ht_state[i] = 0u;
+        ht_val[i] = ~0ull;
+    }
+    if (i < (size_t)n_rx) {
+        for (int k = 0; k < 3; ++k) {
+            rx_box[6 * i + k] = __double2float_rd(rx[3 * i + k]);
+            rx_box[6 * i + 3 + k] = __double2float_ru(rx[3 * i + k]);
+        }
+        df x = df_from_double(rx[3 * i]), y = df_from_double(rx[3 * i + 1]), z = df_from_double(rx[3 * i + 2]);
+        rx_df[2 * i] = make_float4(x.hi, y.hi, z.hi, 0.f);
+        rx_df[2 * i + 1] = make_float4(x.lo, y.lo, z.lo, 0.f);
+    }
+    if (i == 0) {
+        double al = alpha_in;
+        if (al > 0.0) *alpha = al;
+        else al = *alpha;
+        df a1 = df_from_double(al), a2 = df_from_double(al * al / 3.0);
+        *alpha_df = make_float4(a1.hi, a1.lo, a2.hi, a2.lo);
     }
 }
 
@@ -1119,30 +1143,26 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     SBR_TRY(dalloc_n(&tr->ht_key, cap * kKeyWords, s));
     SBR_TRY(dalloc_n(&tr->ht_val, cap, s));
     SBR_TRY(dalloc_n(&tr->cnt, 1, s));
-    SBR_TRY_CUDA(cudaMemsetAsync(tr->cnt, 0, sizeof(TraceCountersDev), s));
-    ::sbr::note_launch(), k_init_table<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(tr->ht_state, tr->ht_val, cap);
-    SBR_TRY_CUDA(cudaGetLastError());
-    SBR_TRY(set_u64(&tr->cnt->queue[0], (unsigned long long)R, s));
-    // receiver BVH
     BvhNodes rxb;
     float* rxbox = nullptr;
     int32_t* rx_depth = nullptr;
-    if (tr->n_rx > 0) {
-        SBR_TRY(dalloc_n(&rxbox, 6 * (size_t)tr->n_rx, s));
-        SBR_TRY(dalloc_n(&rx_depth, 1, s));
-        ::sbr::note_launch(), k_rx_boxes<<<(tr->n_rx + 255) / 256, 256, 0, s>>>(tr->rx, tr->n_rx, rxbox);
-        SBR_TRY_CUDA(cudaGetLastError());
-        SBR_TRY(build_lbvh(rxbox, tr->n_rx, 0.0f, 1, &rxb, rx_depth, s));
-    }
     float4* rx_df = nullptr;
     float4* alpha_df = nullptr;
     SBR_TRY(dalloc_n(&alpha_df, 1, s));
-    ::sbr::note_launch(), k_alpha_df<<<1, 1, 0, s>>>(tr->d_alpha, alpha_df);
     if (tr->n_rx > 0) {
+        SBR_TRY(dalloc_n(&rxbox, 6 * (size_t)tr->n_rx, s));
+        SBR_TRY(dalloc_n(&rx_depth, 1, s));
         SBR_TRY(dalloc_n(&rx_df, 2 * (size_t)tr->n_rx, s));
-        ::sbr::note_launch(), k_rx_df<<<(tr->n_rx + 255) / 256, 256, 0, s>>>(tr->rx, tr->n_rx, rx_df);
     }
-    SBR_TRY_CUDA(cudaGetLastError());
+    {
+        const size_t n_set = std::max<size_t>(std::max<size_t>(cap, (size_t)tr->n_rx), sizeof(TraceCountersDev) / 8);
+        ::sbr::note_launch(), k_trace_setup<<<(unsigned)((n_set + 255) / 256), 256, 0, s>>>(
+            tr->cnt, (unsigned long long)R, tr->ht_state, tr->ht_val, cap, tr->rx, tr->n_rx, rxbox, rx_df,
+            tr->d_alpha, p.alpha, alpha_df);
+        SBR_TRY_CUDA(cudaGetLastError());
+    }
+    // receiver BVH
+    if (tr->n_rx > 0) SBR_TRY(build_lbvh(rxbox, tr->n_rx, 0.0f, 1, &rxb, rx_depth, s));
     const float4* dir_a = nullptr;
     const float2* dir_b = nullptr;
     SBR_TRY(dir_table(p.subdiv_N, &dir_a, &dir_b, s));
