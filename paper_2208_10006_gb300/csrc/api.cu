@@ -260,9 +260,14 @@ sbr_status sbr_trace_stats(const sbr_trace_result* tr, sbr_trace_counters* out) 
     SBR_SAME_DEVICE(tr);
     TraceCountersDev c;
     double alpha = 0;
-    SBR_TRY_CUDA(cudaMemcpyAsync(&c, tr->cnt, sizeof c, cudaMemcpyDeviceToHost, tr->stream));
-    SBR_TRY_CUDA(cudaMemcpyAsync(&alpha, tr->d_alpha, sizeof alpha, cudaMemcpyDeviceToHost, tr->stream));
-    SBR_TRY_CUDA(cudaStreamSynchronize(tr->stream));
+    if (tr->h_valid) {   // final counters already on the host (taken when the path list was built)
+        c = tr->h_cnt;
+        alpha = tr->h_alpha;
+    } else {
+        SBR_TRY_CUDA(cudaMemcpyAsync(&c, tr->cnt, sizeof c, cudaMemcpyDeviceToHost, tr->stream));
+        SBR_TRY_CUDA(cudaMemcpyAsync(&alpha, tr->d_alpha, sizeof alpha, cudaMemcpyDeviceToHost, tr->stream));
+        SBR_TRY_CUDA(cudaStreamSynchronize(tr->stream));
+    }
     memset(out, 0, sizeof *out);
     out->rays = tr->R;
     int64_t rb = 0;

@@ -86,10 +86,14 @@ __device__ __forceinline__ uint32_t expand_bits(uint32_t x) {
     return x;
 }
 
+// Also clears the refit's arrival flags (nn of them, nn <= n) and the depth.
 __global__ void k_morton(const float* __restrict__ box, int64_t n, const float* __restrict__ bnd,
-                         uint32_t* __restrict__ code, uint32_t* __restrict__ idx) {
+                         uint32_t* __restrict__ code, uint32_t* __restrict__ idx, int32_t* __restrict__ flag,
+                         int64_t nn, int32_t* __restrict__ depth) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (i < nn) flag[i] = 0;
+    if (i == 0) *depth = 0;
     uint32_t q[3];
     for (int a = 0; a < 3; ++a) {
         float c = 0.5f * (box[6 * i + a] + box[6 * i + 3 + a]);
@@ -512,14 +516,20 @@ k_top_sah(float4* __restrict__ nodes, const TopElem* __restrict__ E, const int32
 // per face: bounding box, FP64 unit normal, and the (surface id, face id)
 // pair of the faces-per-surface sort; degenerate faces and surface ids out of
 // range set the status word
-__global__ void k_tri_prep(const float* __restrict__ tri, const int32_t* __restrict__ surf, int64_t T,
-                           int32_t S, float* __restrict__ box, double* __restrict__ nrm,
-                           uint32_t* __restrict__ key, uint32_t* __restrict__ val,
-                           unsigned int* __restrict__ status) {
+// The BVH's own copies of the vertices and surface ids, and per face its box,
+// unit normal and surface sort key; a degenerate face or an out-of-range
+// surface id sets the host-mapped word h_status.
+__global__ void k_tri_prep(const float* __restrict__ tri_in, const int32_t* __restrict__ surf_in, int64_t T,
+                           int32_t S, float* __restrict__ tri, int32_t* __restrict__ surf,
+                           float* __restrict__ box, double* __restrict__ nrm, uint32_t* __restrict__ key,
+                           uint32_t* __restrict__ val, unsigned int* h_status) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     float v[9];
-    for (int k = 0; k < 9; ++k) v[k] = tri[9 * t + k];
+    for (int k = 0; k < 9; ++k) {
+        v[k] = tri_in[9 * t + k];
+        tri[9 * t + k] = v[k];
+    }
     for (int a = 0; a < 3; ++a) {
         box[6 * t + a] = fminf(v[a], fminf(v[3 + a], v[6 + a]));
         box[6 * t + 3 + a] = fmaxf(v[a], fmaxf(v[3 + a], v[6 + a]));
@@ -529,18 +539,20 @@ __global__ void k_tri_prep(const float* __restrict__ tri, const int32_t* __restr
     double l = norm(c);
     bool bad = !(l > 0.0) || !isfinite(l);
     st3(nrm + 3 * t, c * (1.0 / l));
-    int32_t s = surf[t];
+    int32_t s = surf_in[t];
+    surf[t] = s;
     bad |= s < 0 || s >= S;
-    if (bad) atomicOr(status, (unsigned)ST_NUMERIC);
+    if (bad) *(volatile unsigned int*)h_status = (unsigned)ST_NUMERIC;
     key[t] = (uint32_t)min(max(s, 0), S - 1);
     val[t] = (uint32_t)t;
 }
 
-// A pinned host word and an event per thread and device: the result of the
-// input validation goes to the host while the rest of the build runs, and
-// the call waits for the validation kernel only.
+// A pinned, device-mapped host word and an event per thread and device: the
+// validation kernel writes its verdict straight to the host while the rest of
+// the build runs, and the call waits for the validation kernel only.
 struct HostFlag {
     unsigned* h = nullptr;
+    unsigned* d = nullptr;   // the same word, device view
     cudaEvent_t ev = nullptr;
 };
 
@@ -555,8 +567,9 @@ sbr_status host_flag(HostFlag** out) {
     }
     HostFlag& f = flags[dev];
     if (!f.h) {
-        SBR_TRY_CUDA(cudaMallocHost(&f.h, sizeof(unsigned)));
         SBR_TRY_CUDA(cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming));
+        SBR_TRY_CUDA(cudaHostAlloc(&f.h, sizeof(unsigned), cudaHostAllocMapped));
+        SBR_TRY_CUDA(cudaHostGetDevicePointer(&f.d, f.h, 0));
     }
     *out = &f;
     return SBR_OK;
@@ -624,12 +637,10 @@ sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, int leaf_
     SBR_TRY(dalloc_n(&ibox, 6 * nn, s));
     SBR_TRY(dalloc_n(&out->nodes, 4 * nn, s));
     SBR_TRY(dalloc_n(&out->d_root, 6, s));
-    SBR_TRY_CUDA(cudaMemsetAsync(flag, 0, nn * sizeof(int32_t), s));
-    SBR_TRY_CUDA(cudaMemsetAsync(d_depth, 0, sizeof(int32_t), s));
     const int nparts = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 2 * (int64_t)sm_count());
     ::sbr::note_launch(), k_bounds<<<nparts, 256, 0, s>>>(prim_box, n, part);
     ::sbr::note_launch(), k_bounds_final<<<1, 256, 0, s>>>(part, nparts, bnd);
-    ::sbr::note_launch(), k_morton<<<blocks_for(n), kThreads, 0, s>>>(prim_box, n, bnd, code, idx);
+    ::sbr::note_launch(), k_morton<<<blocks_for(n), kThreads, 0, s>>>(prim_box, n, bnd, code, idx, flag, nn, d_depth);
     SBR_TRY_CUDA(cudaGetLastError());
     SBR_TRY(radix_sort_pairs(code, idx, n, 30, s));
     if (n > 1) ::sbr::note_launch(), k_karras<<<blocks_for(n - 1), kThreads, 0, s>>>(code, n, left, right, pint, pleaf, span);
@@ -687,35 +698,29 @@ sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S
     b->T = T;
     b->S = S;
     SBR_TRY(dalloc_n(&b->d_depth, 1, s));
-    SBR_TRY_CUDA(cudaMemsetAsync(b->d_depth, 0, sizeof(int32_t), s));
     SBR_TRY(dalloc_n(&b->s_off, (size_t)S + 1, s));
     if (T == 0) {
+        SBR_TRY_CUDA(cudaMemsetAsync(b->d_depth, 0, sizeof(int32_t), s));
         SBR_TRY_CUDA(cudaMemsetAsync(b->s_off, 0, sizeof(int32_t) * ((size_t)S + 1), s));
         return SBR_OK;
     }
-    unsigned int* status;
-    SBR_TRY(dalloc_n(&status, 1, s));
-    SBR_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
     SBR_TRY(dalloc_n(&b->tri, 9 * T, s));
     SBR_TRY(dalloc_n(&b->surf, T, s));
     SBR_TRY(dalloc_n(&b->nrm, 3 * T, s));
     SBR_TRY(dalloc_n(&b->tri_sorted, 3 * T, s));
     SBR_TRY(dalloc_n(&b->plane_sorted, 2 * T, s));
     SBR_TRY(dalloc_n(&b->s_tri, T, s));
-    SBR_TRY_CUDA(cudaMemcpyAsync(b->tri, tri, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, s));
-    SBR_TRY_CUDA(cudaMemcpyAsync(b->surf, surf, sizeof(int32_t) * T, cudaMemcpyDeviceToDevice, s));
     float* box;
     uint32_t *key, *val;
     SBR_TRY(dalloc_n(&box, 6 * T, s));
     SBR_TRY(dalloc_n(&key, T, s));
     val = reinterpret_cast<uint32_t*>(b->s_tri);
-    ::sbr::note_launch(), k_tri_prep<<<blocks_for(T), kThreads, 0, s>>>(b->tri, b->surf, T, S, box, b->nrm, key, val,
-                                                                      status);
-    SBR_TRY_CUDA(cudaGetLastError());
     HostFlag* hf;
     SBR_TRY(host_flag(&hf));
-    *hf->h = 0;
-    SBR_TRY_CUDA(cudaMemcpyAsync(hf->h, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    *(volatile unsigned*)hf->h = 0u;
+    ::sbr::note_launch(), k_tri_prep<<<blocks_for(T), kThreads, 0, s>>>(tri, surf, T, S, b->tri, b->surf, box, b->nrm,
+                                                                      key, val, hf->d);
+    SBR_TRY_CUDA(cudaGetLastError());
     SBR_TRY_CUDA(cudaEventRecord(hf->ev, s));
     // relative box padding: 2^-20 of (|x| + 1) covers FP32 ray/box rounding
     SBR_TRY(build_lbvh(box, T, 1.0f / (1 << 20), tri_leaf_size(), &b->tree, b->d_depth, s, sah_top));
@@ -728,10 +733,9 @@ sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S
     ::sbr::note_launch(), k_surface_offsets<<<blocks_for((int64_t)S + 1), kThreads, 0, s>>>(key, T, S, b->s_off);
     SBR_TRY_CUDA(cudaGetLastError());
     SBR_TRY_CUDA(cudaEventSynchronize(hf->ev));
-    const unsigned h_status = *hf->h;
+    const unsigned h_status = *(volatile unsigned*)hf->h;
     dfree(box, s);
     dfree(key, s);
-    dfree(status, s);
     if (h_status) {
         set_error("sbr_build_bvh: degenerate triangle or surface id out of range");
         return SBR_ERR_INVALID_ARG;

@@ -11,6 +11,7 @@
 // artefacts near edges) are dropped and counted; the rest keep key order.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "refine.cuh"
@@ -165,16 +166,82 @@ __global__ void k_compact_all(const __grid_constant__ CompactArgs a) {
     }
 }
 
+// first path of each receiver (and P at n_rx), on the device and in the
+// host-mapped buffer; thread 0 also stores P there
 __global__ void k_rx_offsets(const int32_t* __restrict__ rx, const unsigned* __restrict__ P, int32_t n_rx,
-                             int32_t* __restrict__ off) {
+                             int32_t* __restrict__ off, unsigned* h_P, int32_t* h_off) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r > n_rx) return;
     int64_t lo = 0, hi = *P;
+    if (r == 0) *(volatile unsigned*)h_P = (unsigned)hi;
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
         if (rx[mid] < r) lo = mid + 1; else hi = mid;
     }
     off[r] = (int32_t)lo;
+    *(volatile int32_t*)(h_off + r) = (int32_t)lo;
+}
+
+// Layout of the host-mapped words of one path-list build: the key count (later
+// P), the trace's alpha and final counters, then the receiver offsets.
+struct MappedHead {
+    unsigned count;
+    unsigned pad;
+    double alpha;
+    TraceCountersDev cnt;
+};
+static_assert(sizeof(MappedHead) % 8 == 0 && sizeof(TraceCountersDev) % 8 == 0, "64-bit words");
+
+// the key count, alpha and the trace's counters, stored to the host-mapped head
+__global__ void k_peek_counts(const unsigned* __restrict__ count, const double* __restrict__ alpha,
+                              const TraceCountersDev* __restrict__ cnt, MappedHead* h) {
+    const int i = threadIdx.x;
+    constexpr int kWords = (int)(sizeof(TraceCountersDev) / 8);
+    if (i < kWords)
+        reinterpret_cast<volatile unsigned long long*>(&h->cnt)[i] =
+            reinterpret_cast<const unsigned long long*>(cnt)[i];
+    if (i == 0) {
+        *(volatile unsigned*)&h->count = *count;
+        *(volatile double*)&h->alpha = *alpha;
+    }
+}
+
+// A pinned, device-mapped host buffer per thread and device. The small
+// results the host waits for (key count, trace status, path count, receiver
+// offsets) are stored there by kernels and read after the stream
+// synchronisation, without copy-engine round trips.
+struct Mapped {
+    char* h = nullptr;
+    char* d = nullptr;
+    size_t cap = 0;
+};
+
+sbr_status mapped_buf(size_t bytes, char** h, char** d) {
+    constexpr int kMaxDev = 64;
+    thread_local Mapped m[kMaxDev];
+    int dev = 0;
+    SBR_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDev) {
+        set_error("device index %d out of range", dev);
+        return SBR_ERR_UNSUPPORTED;
+    }
+    Mapped& x = m[dev];
+    if (x.cap < bytes) {
+        if (x.h) {
+            // every user waits for its kernels before returning; the device
+            // wait also covers one that returned early on an error
+            SBR_TRY_CUDA(cudaDeviceSynchronize());
+            SBR_TRY_CUDA(cudaFreeHost(x.h));
+            x = Mapped{};
+        }
+        const size_t cap = std::max<size_t>(bytes, 4096);
+        SBR_TRY_CUDA(cudaHostAlloc((void**)&x.h, cap, cudaHostAllocMapped));
+        SBR_TRY_CUDA(cudaHostGetDevicePointer((void**)&x.d, x.h, 0));
+        x.cap = cap;
+    }
+    *h = x.h;
+    *d = x.d;
+    return SBR_OK;
 }
 
 int bits_for(int64_t maxval) {
@@ -200,12 +267,21 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     SBR_TRY(dalloc_n(&count, 1, s));
     SBR_TRY(dalloc_n(&idx, cap, s));
     SBR_TRY_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned), s));
+    char *hm, *dm;
+    SBR_TRY(mapped_buf(sizeof(MappedHead) + sizeof(int32_t) * (1 + (size_t)tr->n_rx), &hm, &dm));
+    MappedHead* hh = reinterpret_cast<MappedHead*>(hm);
+    volatile unsigned* h_count = &hh->count;
+    int32_t* h_off = reinterpret_cast<int32_t*>(hm + sizeof(MappedHead));
     ::sbr::note_launch(), k_collect<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(tr->ht_state, cap, idx, count);
+    ::sbr::note_launch(), k_peek_counts<<<1, 32, 0, s>>>(count, tr->d_alpha, tr->cnt,
+                                                          reinterpret_cast<MappedHead*>(dm));
     SBR_TRY_CUDA(cudaGetLastError());
-    unsigned h_count = 0, h_trace = 0;
-    SBR_TRY_CUDA(cudaMemcpyAsync(&h_count, count, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    SBR_TRY_CUDA(cudaMemcpyAsync(&h_trace, &tr->cnt->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     SBR_TRY_CUDA(cudaStreamSynchronize(s));
+    // the trace has ended: its counters are final and are kept on the host
+    memcpy(&tr->h_cnt, &hh->cnt, sizeof(TraceCountersDev));
+    tr->h_alpha = hh->alpha;
+    tr->h_valid = true;
+    const unsigned h_trace = tr->h_cnt.status;
     // a trace that ended with an error (full dedup table, stack overflow, ...)
     // yields no path list; the table was read only as plain memory
     if (const sbr_status ts = status_from_bits(h_trace); ts != SBR_OK) {
@@ -213,7 +289,7 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
         dfree(idx, s);
         return ts;
     }
-    const int64_t n = h_count;
+    const int64_t n = *h_count;
     pl->n_keys = n;
     // sort keys: least significant word first (stable LSD over words)
     uint32_t *perm, *word;
@@ -318,15 +394,14 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
         ::sbr::note_launch(), k_compact_all<<<nblk(32 * n), kThreads, 0, s>>>(c);
         SBR_TRY_CUDA(cudaGetLastError());
     }
-    ::sbr::note_launch(), k_rx_offsets<<<nblk((int64_t)tr->n_rx + 1), kThreads, 0, s>>>(pl->rx, count, tr->n_rx,
-                                                                                    pl->rx_off);
+    ::sbr::note_launch(), k_rx_offsets<<<nblk((int64_t)tr->n_rx + 1), kThreads, 0, s>>>(
+        pl->rx, count, tr->n_rx, pl->rx_off, &reinterpret_cast<MappedHead*>(dm)->count,
+        reinterpret_cast<int32_t*>(dm + sizeof(MappedHead)));
     SBR_TRY_CUDA(cudaGetLastError());
     pl->h_rx_off = new int32_t[tr->n_rx + 1];
-    SBR_TRY_CUDA(cudaMemcpyAsync(&h_count, count, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    SBR_TRY_CUDA(cudaMemcpyAsync(pl->h_rx_off, pl->rx_off, sizeof(int32_t) * (tr->n_rx + 1),
-                                 cudaMemcpyDeviceToHost, s));
     SBR_TRY_CUDA(cudaStreamSynchronize(s));
-    const int64_t P = h_count;
+    memcpy(pl->h_rx_off, h_off, sizeof(int32_t) * (tr->n_rx + 1));
+    const int64_t P = *h_count;
     pl->P = P;
     pl->n_invalid = n - P;
     dfree(count, s); dfree(idx, s); dfree(perm, s); dfree(word, s); dfree(valid, s); dfree(pos, s);

@@ -176,6 +176,11 @@ struct sbr_trace_result {
     TraceCountersDev* cnt = nullptr;
     cudaEvent_t ev[SBR_KMAX + 2] = {};     // bounce boundaries when timing is requested
     cudaStream_t stream = nullptr;
+    // host copy of the final counters and alpha, taken by the path list's
+    // first wait (the counters do not change once the trace launch has ended)
+    mutable TraceCountersDev h_cnt{};
+    mutable double h_alpha = 0.0;
+    mutable bool h_valid = false;
 };
 
 struct sbr_path_list {
