@@ -1,12 +1,12 @@
 // Device sort and scan primitives used by the BVH build (Morton order,
 // surface CSR) and by path compaction (key order, valid-path compaction).
 //
-// radix_sort_pairs: stable LSD radix sort, 8-bit digits. Each pass: a tile
-// histogram per block, an exclusive scan of the digit-major histogram, and a
-// stable scatter that ranks equal digits by (round, warp, lane) order. Up to
-// 12,288 keys the whole sort runs in one block in shared memory; up to 2^20
-// keys in one cooperative launch (grid-wide barriers between the phases);
-// beyond that as separate launches per phase.
+// radix_sort_pairs: stable LSD radix sort, 8-bit digits. Each pass: digit
+// counts per tile, their exclusive scan (digit-major), and a stable scatter.
+// Up to 12,288 keys the whole sort runs in one block in shared memory; above
+// that in one cooperative launch (two grid-wide barriers per pass, every
+// block forming its own offsets from all tiles' counts); where a cooperative
+// launch is not available, as separate launches per phase.
 #include <algorithm>
 #include <atomic>
 
@@ -24,17 +24,8 @@ constexpr int kSortRounds = 8;
 constexpr int kSortTile = kSortThreads * kSortRounds;  // 2048 elements per block
 constexpr int kScanBlock = 1024;
 
-// loads of data that other blocks of the same launch wrote (kCG: at L2,
-// past this SM's L1 and the read-only path)
-template <bool kCG>
-__device__ __forceinline__ uint32_t ld_u32(const uint32_t* p) {
-    if (kCG) return __ldcg(p);
-    return *p;
-}
-
 // digit counts of tile t (kSortTile keys from t * kSortTile), digit-major:
 // hist[d * ntiles + t]
-template <bool kCG = false>
 __device__ __forceinline__ void tile_hist(const uint32_t* keys, int64_t n, int shift, uint32_t* hist, int ntiles,
                                           int t) {
     __shared__ uint32_t h[256];
@@ -43,7 +34,7 @@ __device__ __forceinline__ void tile_hist(const uint32_t* keys, int64_t n, int s
     int64_t base = (int64_t)t * kSortTile;
     for (int r = 0; r < kSortRounds; ++r) {
         int64_t i = base + r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(ld_u32<kCG>(keys + i) >> shift) & 255u], 1u);
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * ntiles + t] = h[threadIdx.x];
@@ -51,14 +42,13 @@ __device__ __forceinline__ void tile_hist(const uint32_t* keys, int64_t n, int s
 }
 
 // stable scatter of tile t, its digits starting at the scanned hist[d * ntiles + t]
-template <bool kCG = false>
 __device__ __forceinline__ void tile_scatter(const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
                                              uint32_t* vout, int64_t n, int shift, const uint32_t* hist,
                                              int ntiles, int t) {
     __shared__ uint32_t s_run[256];
     __shared__ uint32_t s_warp[kSortThreads / 32][256];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    s_run[tid] = ld_u32<kCG>(hist + (int64_t)tid * ntiles + t);
+    s_run[tid] = hist[(int64_t)tid * ntiles + t];
     int64_t base = (int64_t)t * kSortTile;
     const unsigned lt = (1u << lane) - 1u;
     for (int r = 0; r < kSortRounds; ++r) {
@@ -66,7 +56,7 @@ __device__ __forceinline__ void tile_scatter(const uint32_t* kin, const uint32_t
         __syncthreads();
         int64_t i = base + r * kSortThreads + tid;
         bool valid = i < n;
-        uint32_t k = valid ? ld_u32<kCG>(kin + i) : 0u, v = valid ? ld_u32<kCG>(vin + i) : 0u;
+        uint32_t k = valid ? kin[i] : 0u, v = valid ? vin[i] : 0u;
         uint32_t d = valid ? ((k >> shift) & 255u) : 256u;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int rank = __popc(peers & lt);
@@ -153,38 +143,89 @@ __global__ void k_total(const uint32_t* scanned, const uint32_t* last_in, int64_
     *total = n > 0 ? scanned[n - 1] + *last_in : 0u;
 }
 
-// The whole sort of a mid-sized array in one cooperative launch: per 8-bit
-// pass, tile counts, the digit-major scan (block 0) and the stable scatter,
-// separated by grid-wide barriers (every block is resident: the launch is
-// cooperative). Tiles are shared out over the blocks in a grid stride; the
-// result ends in (k0, v0).
-constexpr int kCoopMaxTiles = 512;   // n <= 512 tiles of kSortTile = 1,048,576 keys
+// The sort of a mid-sized array in one cooperative launch (every block is
+// resident), one tile of 256 x rounds keys per block and one chunk of
+// 32 x rounds keys per warp. Per 8-bit pass: each warp counts the digits of
+// its chunk into shared memory and the block publishes its tile's counts
+// (tile-major); after a grid-wide barrier every block forms its own offsets,
+// digit base (exclusive scan over digits of the counts of all tiles) + the
+// counts of the tiles before it + those of its warps before each warp; then
+// every warp scatters its chunk in rounds of 32, equal digits ranked by lane,
+// which keeps the pass stable; a second barrier ends the pass. Data written
+// by other blocks is read at L2 (__ldcg). The result ends in (k0, v0).
+constexpr int kCoopTileMin = 1024;   // keys per tile at least (fewer, larger tiles: fewer counts to add)
+constexpr int kCoopMaxRounds = 32;   // rounds of 32 keys per warp at most
 
 __global__ void __launch_bounds__(kSortThreads)
-k_sort_coop(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int passes, uint32_t* hist) {
+k_sort_coop(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int passes, int rounds,
+            uint32_t* hist) {
     cg::grid_group grid = cg::this_grid();
-    const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ uint32_t s_cnt[kWarps][256];   // per warp and digit: count, then output position
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int ntiles = (int)gridDim.x, t = (int)blockIdx.x;
+    const int64_t chunk = 32 * (int64_t)rounds;
+    const int64_t c0 = min(n, ((int64_t)t * kWarps + warp) * chunk), c1 = min(n, c0 + chunk);
     uint32_t *ka = k0, *va = v0, *kb = k1, *vb = v1;
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) tile_hist<true>(ka, n, shift, hist, ntiles, t);
-        grid.sync();
-        if (blockIdx.x == 0) {
-            const int total = 256 * ntiles;
-            const int c = (total + (int)blockDim.x - 1) / (int)blockDim.x;
-            const int i0 = min(total, (int)threadIdx.x * c), i1 = min(total, i0 + c);
-            uint32_t sum = 0;
-            for (int i = i0; i < i1; ++i) sum += __ldcg(hist + i);
-            uint32_t ex = block_exclusive_scan(sum, nullptr);
-            for (int i = i0; i < i1; ++i) {
-                const uint32_t x = __ldcg(hist + i);
-                hist[i] = ex;
-                ex += x;
-            }
+        for (int d = lane; d < 256; d += 32) s_cnt[warp][d] = 0;
+        __syncwarp();
+        for (int64_t b = c0; b < c1; b += 32) {
+            const int64_t i = b + lane;
+            const uint32_t d = i < c1 ? ((__ldcg(ka + i) >> shift) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (d < 256u && (peers & lt) == 0) s_cnt[warp][d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            uint32_t c = 0;
+            for (int w = 0; w < kWarps; ++w) c += s_cnt[w][tid];
+            hist[(int64_t)t * 256 + tid] = c;
         }
         grid.sync();
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
-            tile_scatter<true>(ka, va, kb, vb, n, shift, hist, ntiles, t);
+        {
+            // digit tid: its count over all tiles and over the tiles before t
+            uint32_t total = 0, before = 0;
+            int u = 0;
+            for (; u + 4 <= ntiles; u += 4) {
+                const uint32_t x0 = __ldcg(hist + (int64_t)u * 256 + tid);
+                const uint32_t x1 = __ldcg(hist + (int64_t)(u + 1) * 256 + tid);
+                const uint32_t x2 = __ldcg(hist + (int64_t)(u + 2) * 256 + tid);
+                const uint32_t x3 = __ldcg(hist + (int64_t)(u + 3) * 256 + tid);
+                total += x0 + x1 + x2 + x3;
+                before += (u < t ? x0 : 0u) + (u + 1 < t ? x1 : 0u) + (u + 2 < t ? x2 : 0u) + (u + 3 < t ? x3 : 0u);
+            }
+            for (; u < ntiles; ++u) {
+                const uint32_t x = __ldcg(hist + (int64_t)u * 256 + tid);
+                total += x;
+                before += u < t ? x : 0u;
+            }
+            uint32_t run = block_exclusive_scan(total, nullptr) + before;
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t c = s_cnt[w][tid];
+                s_cnt[w][tid] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+        for (int64_t b = c0; b < c1; b += 32) {
+            const int64_t i = b + lane;
+            const bool valid = i < c1;
+            const uint32_t k = valid ? __ldcg(ka + i) : 0u, v = valid ? __ldcg(va + i) : 0u;
+            const uint32_t d = valid ? ((k >> shift) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (valid) {
+                const uint32_t pos = s_cnt[warp][d] + __popc(peers & lt);
+                kb[pos] = k;
+                vb[pos] = v;
+            }
+            __syncwarp();
+            if (valid && (peers & lt) == 0) s_cnt[warp][d] += __popc(peers);
+            __syncwarp();
+        }
         grid.sync();
         uint32_t* q = ka; ka = kb; kb = q;
         q = va; va = vb; vb = q;
@@ -355,17 +396,19 @@ sbr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits,
         SBR_TRY_CUDA(cudaGetLastError());
         return SBR_OK;
     }
-    int nblocks = (int)((n + kSortTile - 1) / kSortTile);
-    uint32_t *k2, *v2, *hist;
-    SBR_TRY(dalloc_n(&k2, n, s));
-    SBR_TRY(dalloc_n(&v2, n, s));
-    SBR_TRY(dalloc_n(&hist, (size_t)256 * nblocks, s));
     int passes = (bits + 7) / 8;
     int coop = 0;
-    if (nblocks <= kCoopMaxTiles) SBR_TRY(coop_blocks(&coop));
-    if (coop > 0) {
-        int grid = std::min(nblocks, coop);
-        void* args[] = {&keys, &vals, &k2, &v2, &n, &passes, &hist};
+    SBR_TRY(coop_blocks(&coop));
+    // cooperative: one tile of 256 x rounds keys per block, every block resident
+    const int64_t coop_tiles = std::min<int64_t>(coop, (n + kCoopTileMin - 1) / kCoopTileMin);
+    const int64_t rounds = coop_tiles > 0 ? (n + 256 * coop_tiles - 1) / (256 * coop_tiles) : 0;
+    if (coop_tiles > 0 && rounds <= kCoopMaxRounds) {
+        int grid = (int)coop_tiles, r = (int)rounds;
+        uint32_t *k2, *v2, *hist;
+        SBR_TRY(dalloc_n(&k2, n, s));
+        SBR_TRY(dalloc_n(&v2, n, s));
+        SBR_TRY(dalloc_n(&hist, (size_t)256 * grid, s));
+        void* args[] = {&keys, &vals, &k2, &v2, &n, &passes, &r, &hist};
         ::sbr::note_launch();
         SBR_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)k_sort_coop, dim3(grid), dim3(kSortThreads), args, 0, s));
         dfree(k2, s);
@@ -373,6 +416,11 @@ sbr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits,
         dfree(hist, s);
         return SBR_OK;
     }
+    int nblocks = (int)((n + kSortTile - 1) / kSortTile);
+    uint32_t *k2, *v2, *hist;
+    SBR_TRY(dalloc_n(&k2, n, s));
+    SBR_TRY(dalloc_n(&v2, n, s));
+    SBR_TRY(dalloc_n(&hist, (size_t)256 * nblocks, s));
     uint32_t *ka = keys, *va = vals, *kb = k2, *vb = v2;
     sbr_status st = SBR_OK;
     for (int p = 0; p < passes && st == SBR_OK; ++p) {
