@@ -173,27 +173,37 @@ __global__ void k_refit(const float* __restrict__ prim_box, const int32_t* __res
         *depth = 1;
         return;
     }
+    // the climbing thread carries its subtree's box and height and reads only
+    // the sibling's; the node's children and parent (read-only here) are
+    // fetched before the arrival count, so each level costs the count and one
+    // dependent load
+    float a[6];
+    for (int k = 0; k < 6; ++k) a[k] = src[k];
+    int32_t me = ~(int32_t)j, h = 1;
     int32_t node = parent_leaf[j];
     while (node >= 0) {
+        const int32_t l = left[node], r = right[node], up = parent_int[node];
         // release: this thread's boxes before the count; acquire: the sibling's after it
         cuda::atomic_ref<int32_t, cuda::thread_scope_device> cnt(flag[node]);
         if (cnt.fetch_add(1, cuda::memory_order_acq_rel) == 0) return;  // the sibling subtree is not done yet
-        float a[6], b[6];
-        int32_t l = left[node], r = right[node];
-        ld_box(l < 0 ? lbox + 6 * (int64_t)(~l) : ibox + 6 * (int64_t)l, a);
-        ld_box(r < 0 ? lbox + 6 * (int64_t)(~r) : ibox + 6 * (int64_t)r, b);
-        volatile float* o = ibox + 6 * (int64_t)node;
-        for (int k = 0; k < 3; ++k) {
-            o[k] = fminf(a[k], b[k]);
-            o[3 + k] = fmaxf(a[3 + k], b[3 + k]);
-        }
+        const int32_t sib = l == me ? r : l;
+        float b[6];
+        ld_box(sib < 0 ? lbox + 6 * (int64_t)(~sib) : ibox + 6 * (int64_t)sib, b);
         // height: a leaf counts 1, a node one more than its higher child; the
         // root's height is the tree depth (levels on the longest root-leaf path)
-        const int hl = l < 0 ? 1 : ((volatile int32_t*)hd)[l], hr = r < 0 ? 1 : ((volatile int32_t*)hd)[r];
-        const int h = 1 + (hl > hr ? hl : hr);
+        const int hs = sib < 0 ? 1 : ((volatile int32_t*)hd)[sib];
+        volatile float* o = ibox + 6 * (int64_t)node;
+        for (int k = 0; k < 3; ++k) {
+            a[k] = fminf(a[k], b[k]);
+            a[3 + k] = fmaxf(a[3 + k], b[3 + k]);
+            o[k] = a[k];
+            o[3 + k] = a[3 + k];
+        }
+        h = 1 + (h > hs ? h : hs);
         ((volatile int32_t*)hd)[node] = h;
-        if (parent_int[node] < 0) *depth = h;
-        node = parent_int[node];
+        if (up < 0) *depth = h;
+        me = node;
+        node = up;
     }
 }
 
