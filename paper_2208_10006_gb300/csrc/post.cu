@@ -45,7 +45,6 @@ k_pdp(const int32_t* __restrict__ rx_off, const double* __restrict__ L, const do
       const double* __restrict__ aoa, const float2* __restrict__ g, int32_t F, int32_t f_index,
       double fc, double bin_s, int32_t n_bins, float* __restrict__ pdp, double* __restrict__ stats) {
     extern __shared__ double acc[];  // [n_bins]
-    __shared__ double sh[33];
     const int r = blockIdx.x;
     const int32_t o0 = rx_off[r], o1 = rx_off[r + 1];
     for (int k = threadIdx.x; k < n_bins; k += blockDim.x) acc[k] = 0.0;
@@ -67,10 +66,29 @@ k_pdp(const int32_t* __restrict__ rx_off, const double* __restrict__ L, const do
         a1 += pw * aod[2 * n]; a2 += pw * aod[2 * n + 1];
         a3 += pw * aoa[2 * n]; a4 += pw * aoa[2 * n + 1];
     }
-    sp = block_sum(sp, sh); st = block_sum(st, sh); st2 = block_sum(st2, sh);
-    cr = block_sum(cr, sh); ci = block_sum(ci, sh);
-    a1 = block_sum(a1, sh); a2 = block_sum(a2, sh); a3 = block_sum(a3, sh); a4 = block_sum(a4, sh);
-    __syncthreads();
+    {
+        // the nine block sums at once, each in the order of block_sum (butterfly
+        // within each warp, then the warps in order): two barriers instead of 27
+        __shared__ double part[kPdpThreads / 32][9];
+        __shared__ double tot[9];
+        double v[9] = {sp, st, st2, cr, ci, a1, a2, a3, a4};
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            for (int o = 16; o; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 9; ++q) part[warp][q] = v[q];
+        __syncthreads();
+        if (threadIdx.x < 9) {
+            double t = 0.0;
+            for (int w = 0; w < kPdpThreads / 32; ++w) t += part[w][threadIdx.x];
+            tot[threadIdx.x] = t;
+        }
+        __syncthreads();
+        sp = tot[0]; st = tot[1]; st2 = tot[2]; cr = tot[3]; ci = tot[4];
+        a1 = tot[5]; a2 = tot[6]; a3 = tot[7]; a4 = tot[8];
+    }
     // a bin holds a sum of powers (>= 0): its bit pattern is positive exactly when
     // it is non-zero, which keeps the test of the (mostly empty) bins off the FP64 pipe
     for (int k = threadIdx.x; k < n_bins; k += blockDim.x) {
