@@ -200,7 +200,10 @@ typedef struct {
 
 sbr_status sbr_trace(const sbr_bvh* bvh, const sbr_trace_params* params, sbr_trace_result** out,
                      void* stream);
-/* Synchronous: waits for the trace and returns its counters and status. */
+/* Synchronous: waits for the trace and returns its counters and status. After
+ * sbr_paths on the same result the final counters are already on the host
+ * (read by that call's first wait, when the trace had ended) and are returned
+ * without a device round trip. */
 sbr_status sbr_trace_stats(const sbr_trace_result* tr, sbr_trace_counters* out);
 void sbr_trace_free(sbr_trace_result* tr);
 
