@@ -9,6 +9,7 @@
 // launch is not available, as separate launches per phase.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 
 #include <cooperative_groups.h>
 
@@ -398,7 +399,10 @@ sbr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits,
     }
     int passes = (bits + 7) / 8;
     int coop = 0;
-    SBR_TRY(coop_blocks(&coop));
+    // SBR_SORT_PHASES=1 (read at each call) keeps to the per-phase launches: a
+    // test hook for the path taken where no cooperative launch is available
+    const char* force = getenv("SBR_SORT_PHASES");
+    if (!(force && force[0] == '1')) SBR_TRY(coop_blocks(&coop));
     // cooperative: one tile of 256 x rounds keys per block, every block resident
     const int64_t coop_tiles = std::min<int64_t>(coop, (n + kCoopTileMin - 1) / kCoopTileMin);
     const int64_t rounds = coop_tiles > 0 ? (n + 256 * coop_tiles - 1) / (256 * coop_tiles) : 0;

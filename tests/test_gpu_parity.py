@@ -399,6 +399,24 @@ def test_large_path_list_is_in_key_order(sbr):
     assert np.mean(np.isfinite(st[counts > 0, 1])) > 0.9   # (gains below the FP32 range read as no power)
 
 
+def test_sort_without_cooperative_launch_gives_the_same_paths(sbr, monkeypatch):
+    # SBR_SORT_PHASES=1 keeps the radix sorts above the single-block size to their
+    # per-phase launches (the path taken where no cooperative launch exists): the
+    # BVH's Morton order and the key order, hence the whole path list, are identical
+    sc = scenes.config2(N=150, K=4, rx_grid=64)
+    assert len(sc["tri"]) > 12288
+    ref = sbr.run_scene(sc)
+    monkeypatch.setenv("SBR_SORT_PHASES", "1")
+    alt = sbr.run_scene(sc)
+    monkeypatch.delenv("SBR_SORT_PHASES")
+    assert ref["paths"].info()["n_keys"] > 12288
+    a, b = to_numpy(ref["export"]), to_numpy(alt["export"])
+    assert a.keys() == b.keys()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(ref["g"].cpu().numpy(), alt["g"].cpu().numpy())
+
+
 @pytest.mark.parametrize("name", ["urban_small", "urban_med", "shoebox_K5", "indoor_small"])
 def test_sah_top_bvh_gives_the_same_paths(sbr, name):
     # the SAH-rebuilt top changes the tree, not the closest hits: identical path lists
