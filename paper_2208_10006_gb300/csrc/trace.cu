@@ -98,7 +98,8 @@ __device__ __forceinline__ float comp(float4 v, int k) { return k == 0 ? v.x : (
 __device__ __forceinline__ float comp3(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 
 struct Ray32 {
-    float3 o, d, inv, oinv;  // oinv = o * inv, for the slab test fma(lo, inv, -oinv)
+    float3 ok;         // origin in the shear frame's axis order (kx, ky, kz)
+    float3 inv, oinv;  // oinv = o * inv, for the slab test fma(lo, inv, -oinv)
     int kx, ky, kz;
     float Sx, Sy, Sz;
 };
@@ -112,18 +113,17 @@ __device__ __forceinline__ float safe_rcp(float x) {
 
 __device__ __forceinline__ Ray32 make_ray32(float3 o, float3 d) {
     Ray32 r;
-    r.o = o;
-    r.d = d;
     r.inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     r.oinv = make_float3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
-    float ax = fabsf(r.d.x), ay = fabsf(r.d.y), az = fabsf(r.d.z);
+    float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
     r.kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
     r.kx = r.kz == 2 ? 0 : r.kz + 1;
     r.ky = r.kx == 2 ? 0 : r.kx + 1;
-    float dz = comp3(r.d, r.kz);
+    float dz = comp3(d, r.kz);
     if (dz < 0.f) { int t = r.kx; r.kx = r.ky; r.ky = t; }
-    r.Sx = comp3(r.d, r.kx) / dz;
-    r.Sy = comp3(r.d, r.ky) / dz;
+    r.Sx = comp3(d, r.kx) / dz;
+    r.Sy = comp3(d, r.ky) / dz;
+    r.ok = make_float3(comp3(o, r.kx), comp3(o, r.ky), comp3(o, r.kz));
     r.Sz = 1.0f / dz;
     return r;
 }
@@ -176,12 +176,9 @@ __device__ __forceinline__ void tri_test32(const float4* __restrict__ tris, int3
     float4 a = __ldg(tris + 3 * j), b = __ldg(tris + 3 * j + 1), c = __ldg(tris + 3 * j + 2);
     int32_t surf = __float_as_int(a.w);
     if (surf == prev) return;
-    float Ax = comp(a, r.kx) - comp3(r.o, r.kx), Ay = comp(a, r.ky) - comp3(r.o, r.ky),
-          Az = comp(a, r.kz) - comp3(r.o, r.kz);
-    float Bx = comp(b, r.kx) - comp3(r.o, r.kx), By = comp(b, r.ky) - comp3(r.o, r.ky),
-          Bz = comp(b, r.kz) - comp3(r.o, r.kz);
-    float Cx = comp(c, r.kx) - comp3(r.o, r.kx), Cy = comp(c, r.ky) - comp3(r.o, r.ky),
-          Cz = comp(c, r.kz) - comp3(r.o, r.kz);
+    float Ax = comp(a, r.kx) - r.ok.x, Ay = comp(a, r.ky) - r.ok.y, Az = comp(a, r.kz) - r.ok.z;
+    float Bx = comp(b, r.kx) - r.ok.x, By = comp(b, r.ky) - r.ok.y, Bz = comp(b, r.kz) - r.ok.z;
+    float Cx = comp(c, r.kx) - r.ok.x, Cy = comp(c, r.ky) - r.ok.y, Cz = comp(c, r.kz) - r.ok.z;
     Ax = fmaf(-r.Sx, Az, Ax); Ay = fmaf(-r.Sy, Az, Ay);
     Bx = fmaf(-r.Sx, Bz, Bx); By = fmaf(-r.Sy, Bz, By);
     Cx = fmaf(-r.Sx, Cz, Cx); Cy = fmaf(-r.Sy, Cz, Cy);
@@ -230,7 +227,7 @@ __device__ int32_t traverse32(const A& a, const Ray32& r, int prev, Trav& tv, in
                               unsigned* visits, unsigned* tests) {
     tv.best_t = INFINITY; tv.lim = INFINITY; tv.best_j = -1; tv.best_face = 0x7fffffff;
     tv.best_surf = -2; tv.nu = 0; tv.overflow = false;
-    tv.omax = fmaxf(fabsf(r.o.x), fmaxf(fabsf(r.o.y), fabsf(r.o.z)));
+    tv.omax = fmaxf(fabsf(r.ok.x), fmaxf(fabsf(r.ok.y), fabsf(r.ok.z)));
     // one loop over references: an internal node tests its two child boxes and
     // continues with the nearer hit child (the farther one is stacked); a leaf
     // reference tests its triangles; leaves and nodes share the stack
@@ -434,14 +431,14 @@ __device__ void receive(const TraceArgs& a, int bounce, const df3& o, const df3&
     float t_end = t_hit.hi;
     if (!hit) {
         // no receiver lies farther than the centre of their box plus its half diagonal
-        float cx = 0.5f * (a.rx_root[0] + a.rx_root[3]) - r.o.x;
-        float cy = 0.5f * (a.rx_root[1] + a.rx_root[4]) - r.o.y;
-        float cz = 0.5f * (a.rx_root[2] + a.rx_root[5]) - r.o.z;
+        float cx = 0.5f * (a.rx_root[0] + a.rx_root[3]) - o.x.hi;
+        float cy = 0.5f * (a.rx_root[1] + a.rx_root[4]) - o.y.hi;
+        float cz = 0.5f * (a.rx_root[2] + a.rx_root[5]) - o.z.hi;
         float hx = a.rx_root[3] - a.rx_root[0], hy = a.rx_root[4] - a.rx_root[1], hz = a.rx_root[5] - a.rx_root[2];
         t_end = (sqrtf(cx * cx + cy * cy + cz * cz) + 0.5f * sqrtf(hx * hx + hy * hy + hz * hz)) * (1.f + 1e-5f) + 1e-3f;
     }
     float rmax = al.x * (L.hi + t_end) * 0.57735027f * (1.f + 1e-4f) +
-                 1e-5f * (fabsf(r.o.x) + fabsf(r.o.y) + fabsf(r.o.z) + L.hi + t_end);
+                 1e-5f * (fabsf(o.x.hi) + fabsf(o.y.hi) + fabsf(o.z.hi) + L.hi + t_end);
     float tmax = t_end * (1.f + 1e-5f) + rmax;
     // the segment against the receivers' (padded) root box grown by rmax: it
     // contains every grown child box, so a miss here is a miss of the whole
