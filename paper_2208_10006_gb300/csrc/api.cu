@@ -178,7 +178,7 @@ void sbr_bvh_free(sbr_bvh* b) {
     if (!b) return;
     cudaStream_t s = b->stream;
     free_lbvh(&b->tree, s);
-    dfree(b->tri_sorted, s); dfree(b->plane_sorted, s); dfree(b->tri, s); dfree(b->surf, s);
+    dfree(b->tri_rot, s); dfree(b->plane_sorted, s); dfree(b->tri, s); dfree(b->surf, s);
     dfree(b->nrm, s); dfree(b->s_off, s); dfree(b->s_tri, s); dfree(b->d_depth, s);
     delete b;
 }

@@ -586,6 +586,7 @@ sbr_status create(const sbr_bvh* const* scenes, const sbr_material* const* mats,
             J = BatchJobDev{};
             J.nodes = sc->tree.nodes;
             J.tris = sc->tri_sorted;
+            J.rot_stride = 3 * sc->T;
             J.plane = sc->plane_sorted;
             J.tri = sc->tri;
             J.nrm = sc->nrm;

@@ -15,6 +15,7 @@ struct BatchJobDev {
     const float4* nodes;
     const float4* tris;
     const float4* plane;
+    int64_t rot_stride;          // 3 T: float4s between the rotated copies of tris (tris is the last)
     // scene, face order (refinement) and materials (gains)
     const float* tri;
     const double* nrm;

@@ -585,16 +585,25 @@ sbr_status host_flag(HostFlag** out) {
     return SBR_OK;
 }
 
+// The faces in BVH order, three times: block kz holds each vertex with its
+// components rotated to (kz+1, kz+2, kz) mod 3, so that a ray whose dominant
+// direction axis is kz reads its shear frame's coordinates without selects;
+// block 2 is the plain order. w: surface id bits (v0), face id bits (v1).
 __global__ void k_tri_pack(const float* __restrict__ tri, const int32_t* __restrict__ surf,
                            const double* __restrict__ nrm, const int32_t* __restrict__ order,
-                           int64_t T, float4* __restrict__ out, float4* __restrict__ plane) {
+                           int64_t T, float4* __restrict__ rot, float4* __restrict__ plane) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= T) return;
     int64_t t = order[j];
     const float* v = tri + 9 * t;
-    out[3 * j + 0] = make_float4(v[0], v[1], v[2], __int_as_float(surf[t]));
-    out[3 * j + 1] = make_float4(v[3], v[4], v[5], __int_as_float((int)t));
-    out[3 * j + 2] = make_float4(v[6], v[7], v[8], 0.f);
+    const float ws = __int_as_float(surf[t]), wf = __int_as_float((int)t);
+    for (int kz = 0; kz < 3; ++kz) {
+        const int kx = kz == 2 ? 0 : kz + 1, ky = kx == 2 ? 0 : kx + 1;
+        float4* out = rot + 3 * T * kz;
+        out[3 * j + 0] = make_float4(v[kx], v[ky], v[kz], ws);
+        out[3 * j + 1] = make_float4(v[3 + kx], v[3 + ky], v[3 + kz], wf);
+        out[3 * j + 2] = make_float4(v[6 + kx], v[6 + ky], v[6 + kz], 0.f);
+    }
     // plane n.x = c with the FP64 unit normal, stored as double-float pairs
     double n0 = nrm[3 * t], n1 = nrm[3 * t + 1], n2 = nrm[3 * t + 2];
     double c = n0 * (double)v[0] + n1 * (double)v[1] + n2 * (double)v[2];
@@ -717,7 +726,8 @@ sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S
     SBR_TRY(dalloc_n(&b->tri, 9 * T, s));
     SBR_TRY(dalloc_n(&b->surf, T, s));
     SBR_TRY(dalloc_n(&b->nrm, 3 * T, s));
-    SBR_TRY(dalloc_n(&b->tri_sorted, 3 * T, s));
+    SBR_TRY(dalloc_n(&b->tri_rot, 9 * T, s));
+    b->tri_sorted = b->tri_rot + 6 * T;
     SBR_TRY(dalloc_n(&b->plane_sorted, 2 * T, s));
     SBR_TRY(dalloc_n(&b->s_tri, T, s));
     float* box;
@@ -735,7 +745,7 @@ sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S
     // relative box padding: 2^-20 of (|x| + 1) covers FP32 ray/box rounding
     SBR_TRY(build_lbvh(box, T, 1.0f / (1 << 20), tri_leaf_size(), &b->tree, b->d_depth, s, sah_top));
     ::sbr::note_launch(), k_tri_pack<<<blocks_for(T), kThreads, 0, s>>>(b->tri, b->surf, b->nrm, b->tree.order, T,
-                                                  b->tri_sorted, b->plane_sorted);
+                                                  b->tri_rot, b->plane_sorted);
     // faces per surface, ascending face id (stable sort on the surface id)
     int bits = 1;
     while (bits < 31 && ((int64_t)1 << bits) < (int64_t)S) ++bits;

@@ -133,7 +133,10 @@ struct sbr_bvh {
     int64_t T = 0;
     int32_t S = 0;
     sbr::BvhNodes tree;
-    float4* tri_sorted = nullptr;   // [T*3]: v0 (w = surface id bits), v1 (w = face id bits), v2
+    float4* tri_rot = nullptr;      // [3][T*3]: the faces below, vertex components rotated per
+                                    //   block kz to (kz+1, kz+2, kz) mod 3 (FP32 hit tests)
+    float4* tri_sorted = nullptr;   // [T*3] = block 2 of tri_rot: v0 (w = surface id bits),
+                                    //   v1 (w = face id bits), v2
     float4* plane_sorted = nullptr; // [T*2] face plane as double-float, BVH order:
                                     //   (n_hi.xyz, c_hi), (n_lo.xyz, c_lo) with n.x = c
     float* tri = nullptr;           // [T*9] face-id order copy

@@ -53,9 +53,10 @@ static_assert(sizeof(RayRec) == 64, "ray record is one 64-byte line");
 
 struct TraceArgs {
     const float4* nodes;
-    const float4* tris;
+    const float4* tris;      // [T*3] BVH-order faces, the last of three axis-rotated copies
     const float4* plane;     // [T*2] double-float face planes, BVH order
     int64_t T;
+    int64_t rot_stride;      // 3 T: float4s between the rotated copies
     const float4* rx_nodes;
     const int32_t* rx_order;
     const float4* rx_df;     // [n_rx*2] receiver positions, double-float
@@ -94,13 +95,17 @@ __device__ __forceinline__ uint32_t pool_ray(const TraceArgs& a, unsigned long l
     return (uint32_t)(a.pool_pre + (int64_t)a.face_order[k] * a.pool_face + (r - k * a.pool_face));
 }
 
-__device__ __forceinline__ float comp(float4 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 __device__ __forceinline__ float comp3(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 
+// The FP32 ray of the watertight test. kz is the dominant axis of the
+// direction, kx = kz + 1 and ky = kz + 2 (mod 3) follow it cyclically: the test
+// is two-sided (the sign of det absorbs the orientation), so the axes are not
+// swapped for a negative dz, and the faces are read from the copy whose vertex
+// components are stored in this (kx, ky, kz) order.
 struct Ray32 {
     float3 ok;         // origin in the shear frame's axis order (kx, ky, kz)
     float3 inv, oinv;  // oinv = o * inv, for the slab test fma(lo, inv, -oinv)
-    int kx, ky, kz;
+    int kz;
     float Sx, Sy, Sz;
 };
 
@@ -117,13 +122,11 @@ __device__ __forceinline__ Ray32 make_ray32(float3 o, float3 d) {
     r.oinv = make_float3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
     float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
     r.kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
-    r.kx = r.kz == 2 ? 0 : r.kz + 1;
-    r.ky = r.kx == 2 ? 0 : r.kx + 1;
+    const int kx = r.kz == 2 ? 0 : r.kz + 1, ky = kx == 2 ? 0 : kx + 1;
     float dz = comp3(d, r.kz);
-    if (dz < 0.f) { int t = r.kx; r.kx = r.ky; r.ky = t; }
-    r.Sx = comp3(d, r.kx) / dz;
-    r.Sy = comp3(d, r.ky) / dz;
-    r.ok = make_float3(comp3(o, r.kx), comp3(o, r.ky), comp3(o, r.kz));
+    r.Sx = comp3(d, kx) / dz;
+    r.Sy = comp3(d, ky) / dz;
+    r.ok = make_float3(comp3(o, kx), comp3(o, ky), comp3(o, r.kz));
     r.Sz = 1.0f / dz;
     return r;
 }
@@ -176,9 +179,9 @@ __device__ __forceinline__ void tri_test32(const float4* __restrict__ tris, int3
     float4 a = __ldg(tris + 3 * j), b = __ldg(tris + 3 * j + 1), c = __ldg(tris + 3 * j + 2);
     int32_t surf = __float_as_int(a.w);
     if (surf == prev) return;
-    float Ax = comp(a, r.kx) - r.ok.x, Ay = comp(a, r.ky) - r.ok.y, Az = comp(a, r.kz) - r.ok.z;
-    float Bx = comp(b, r.kx) - r.ok.x, By = comp(b, r.ky) - r.ok.y, Bz = comp(b, r.kz) - r.ok.z;
-    float Cx = comp(c, r.kx) - r.ok.x, Cy = comp(c, r.ky) - r.ok.y, Cz = comp(c, r.kz) - r.ok.z;
+    float Ax = a.x - r.ok.x, Ay = a.y - r.ok.y, Az = a.z - r.ok.z;
+    float Bx = b.x - r.ok.x, By = b.y - r.ok.y, Bz = b.z - r.ok.z;
+    float Cx = c.x - r.ok.x, Cy = c.y - r.ok.y, Cz = c.z - r.ok.z;
     Ax = fmaf(-r.Sx, Az, Ax); Ay = fmaf(-r.Sy, Az, Ay);
     Bx = fmaf(-r.Sx, Bz, Bx); By = fmaf(-r.Sy, Bz, By);
     Cx = fmaf(-r.Sx, Cz, Cx); Cy = fmaf(-r.Sy, Cz, Cy);
@@ -231,6 +234,9 @@ __device__ int32_t traverse32(const A& a, const Ray32& r, int prev, Trav& tv, in
     // one loop over references: an internal node tests its two child boxes and
     // continues with the nearer hit child (the farther one is stacked); a leaf
     // reference tests its triangles; leaves and nodes share the stack
+    // the faces with vertex components in this ray's (kx, ky, kz) order: block
+    // kz of the three rotated copies, of which a.tris is the last
+    const float4* tris_k = a.tris + (int64_t)(r.kz - 2) * a.rot_stride;
     int sp = 0;
     int32_t ref = 0;
     for (;;) {
@@ -253,7 +259,7 @@ __device__ int32_t traverse32(const A& a, const Ray32& r, int prev, Trav& tv, in
             if (h1) { ref = r1; continue; }
         } else {
             const int32_t first = leaf_first(ref), cnt = leaf_count(ref);
-            for (int k = 0; k < cnt; ++k) tri_test32(a.tris, first + k, prev, r, tv);
+            for (int k = 0; k < cnt; ++k) tri_test32(tris_k, first + k, prev, r, tv);
             if (kCount) *tests += cnt;
         }
         if (sp == 0) break;
@@ -780,6 +786,7 @@ struct JobScene {
     const float4* tris;
     const float4* plane;
     TraceCountersDev* cnt;
+    int64_t rot_stride;
 };
 
 struct BatchTraceArgs {
@@ -846,7 +853,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_batch(const __grid_cons
                 job = (int)((rw >> 24) | ((pw >> 28) << 8));
             }
             const BatchJobDev* J = a.jobs + job;
-            const JobScene sc{J->nodes, J->tris, J->plane, a.cnt};
+            const JobScene sc{J->nodes, J->tris, J->plane, a.cnt, J->rot_stride};
             Ray32 r = make_ray32(df3_hi(o), df3_hi(d));
             df t = df_make(INFINITY, 0.f);
             Trav tv;
@@ -955,7 +962,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_batch_df(const __gri
         int entered = -1;
         if (has) {
             const BatchJobDev* J = a.jobs + job;
-            const JobScene sc{J->nodes, J->tris, J->plane, a.cnt};
+            const JobScene sc{J->nodes, J->tris, J->plane, a.cnt, J->rot_stride};
             Ray32 r = make_ray32(df3_hi(o), df3_hi(d));
             df t = df_make(INFINITY, 0.f);
             Trav tv;
@@ -1178,6 +1185,7 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     a.tris = b->tri_sorted;
     a.plane = b->plane_sorted;
     a.T = b->T;
+    a.rot_stride = 3 * b->T;
     a.rx_nodes = rxb.nodes;
     a.rx_order = rxb.order;
     a.rx_df = rx_df;
