@@ -3,7 +3,9 @@
 // bounce kernel (origin, direction, unfolded length) and the reception test,
 // where FP32 is too coarse and FP64 is scarce on this GPU. Built from the
 // error-free transformations: Knuth's two-sum, Dekker's fast two-sum and the
-// FMA-based two-product; division and square root add one Newton correction.
+// FMA-based two-product; division takes two correction steps of the quotient,
+// the dot product gathers every lower-order term in one float (the compensated
+// dot product of Ogita, Rump and Oishi, 2005).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -61,12 +63,17 @@ __device__ __forceinline__ df df_mul_f(df a, float b) {
     p.lo = __fmaf_rn(a.lo, b, p.lo);
     return fast_two_sum(p.hi, p.lo);
 }
+// a / b: quotient terms from one reciprocal of b.hi, each correcting the
+// residual the previous ones left (computed in double-float); a term only
+// needs to be close to the residual's quotient, so the reciprocal's rounding
+// does not limit the result
 __device__ __forceinline__ df df_div(df a, df b) {
-    float q1 = __fdiv_rn(a.hi, b.hi);
+    const float ib = __frcp_rn(b.hi);
+    float q1 = a.hi * ib;
     df r = df_sub(a, df_mul_f(b, q1));
-    float q2 = __fdiv_rn(r.hi, b.hi);
+    float q2 = r.hi * ib;
     r = df_sub(r, df_mul_f(b, q2));
-    float q3 = __fdiv_rn(r.hi, b.hi);
+    float q3 = r.hi * ib;
     df q = fast_two_sum(q1, q2);
     return df_add(q, df{q3, 0.f});
 }
@@ -80,8 +87,22 @@ struct df3 {
 __device__ __forceinline__ df3 df3_add(df3 a, df3 b) { return df3{df_add(a.x, b.x), df_add(a.y, b.y), df_add(a.z, b.z)}; }
 __device__ __forceinline__ df3 df3_sub(df3 a, df3 b) { return df3{df_sub(a.x, b.x), df_sub(a.y, b.y), df_sub(a.z, b.z)}; }
 __device__ __forceinline__ df3 df3_scale(df3 a, df s) { return df3{df_mul(a.x, s), df_mul(a.y, s), df_mul(a.z, s)}; }
+// a.b: the three hi*hi products and their two partial sums by error-free
+// transformations; their errors, the cross terms hi*lo and lo*hi are summed in
+// one float and added once (not symmetric in a, b to the last bit: callers
+// keep one argument order per quantity)
 __device__ __forceinline__ df df3_dot(df3 a, df3 b) {
-    return df_add(df_add(df_mul(a.x, b.x), df_mul(a.y, b.y)), df_mul(a.z, b.z));
+    const df px = two_prod(a.x.hi, b.x.hi), py = two_prod(a.y.hi, b.y.hi), pz = two_prod(a.z.hi, b.z.hi);
+    const df s1 = two_sum(px.hi, py.hi);
+    const df s2 = two_sum(s1.hi, pz.hi);
+    float e = __fadd_rn(__fadd_rn(px.lo, py.lo), __fadd_rn(pz.lo, __fadd_rn(s1.lo, s2.lo)));
+    e = __fmaf_rn(a.x.hi, b.x.lo, e);
+    e = __fmaf_rn(a.x.lo, b.x.hi, e);
+    e = __fmaf_rn(a.y.hi, b.y.lo, e);
+    e = __fmaf_rn(a.y.lo, b.y.hi, e);
+    e = __fmaf_rn(a.z.hi, b.z.lo, e);
+    e = __fmaf_rn(a.z.lo, b.z.hi, e);
+    return two_sum(s2.hi, e);   // not fast_two_sum: under cancellation |e| may exceed |s2.hi|
 }
 __device__ __forceinline__ float3 df3_hi(df3 a) { return make_float3(a.x.hi, a.y.hi, a.z.hi); }
 

@@ -109,11 +109,15 @@ struct Ray32 {
     float Sx, Sy, Sz;
 };
 
-// reciprocal of a direction component for the slab test; an exact zero becomes
-// +-2^-80 so that inv and o * inv stay finite
+// reciprocal of a direction component for the slab tests; an exact zero
+// becomes +-2^-80 so that inv and o * inv stay finite. The fast division (a
+// few ulp for |x| in [2^-80, 1]) suffices: the slab tests only cull, and their
+// rounding stays far inside the boxes' relative padding (2^-20 of |x| + 1 in
+// the scene tree, the sphere radius and 1e-5 of the coordinates in the
+// receiver tree)
 __device__ __forceinline__ float safe_rcp(float x) {
     const float tiny = 8.271806e-25f;  // 2^-80
-    return 1.0f / (fabsf(x) > tiny ? x : copysignf(tiny, x));
+    return __fdividef(1.0f, fabsf(x) > tiny ? x : copysignf(tiny, x));
 }
 
 __device__ __forceinline__ Ray32 make_ray32(float3 o, float3 d) {
@@ -513,9 +517,11 @@ __device__ __forceinline__ df3 ld_plane_n(const float4* plane, int32_t j, df& c)
 // Final decision of a segment's closest hit after the FP32 traversal: the exact
 // FP64 rule over the uncertain faces (or a full FP64 traversal when their list
 // overflowed), else the certain FP32 face with t from its double-float plane.
+// For a hit, nd = n.d with the face's double-float normal (the reflection
+// reuses it).
 template <class A>
 __device__ __forceinline__ int32_t settle_hit(const A& a, const df3& o, const df3& d, int prev, const Trav& tv,
-                                              int32_t j, int* stack, df& t) {
+                                              int32_t j, int* stack, df& t, df& nd) {
     if (tv.overflow || tv.nu > 0) {
         d3 o64 = mk3(df_to_double(o.x), df_to_double(o.y), df_to_double(o.z));
         d3 d64 = mk3(df_to_double(d.x), df_to_double(d.y), df_to_double(d.z));
@@ -538,11 +544,16 @@ __device__ __forceinline__ int32_t settle_hit(const A& a, const df3& o, const df
             j = bj;
             atomicAdd(&a.cnt->fp64_tests, (unsigned long long)(tv.nu + (tv.best_j >= 0)));
         }
-        if (j >= 0) t = df_from_double(t64);
+        if (j >= 0) {
+            t = df_from_double(t64);
+            df c;
+            nd = df3_dot(ld_plane_n(a.plane, j, c), d);
+        }
     } else if (j >= 0) {
         df c;
         df3 n = ld_plane_n(a.plane, j, c);
-        t = df_div(df_sub(c, df3_dot(n, o)), df3_dot(n, d));
+        nd = df3_dot(n, d);
+        t = df_div(df_sub(c, df3_dot(n, o)), nd);
     }
     return j;
 }
@@ -588,11 +599,11 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
             }
             Ray32 r = make_ray32(df3_hi(o), df3_hi(d));
             int32_t j = -1;
-            df t = df_make(INFINITY, 0.f);
+            df t = df_make(INFINITY, 0.f), nd = df_make(0.f, 0.f);
             if (a.T > 0) {
                 Trav tv;
                 j = traverse32<kCount>(a, r, prev, tv, stack, &visits, &tests);
-                j = settle_hit(a, o, d, prev, tv, j, stack, t);
+                j = settle_hit(a, o, d, prev, tv, j, stack, t, nd);
             }
             if (kCount && j >= 0) {
                 d3 o64 = mk3(df_to_double(o.x), df_to_double(o.y), df_to_double(o.z));
@@ -605,7 +616,7 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
                 df3 n = ld_plane_n(a.plane, j, c);
                 int32_t surf = __float_as_int(__ldg(a.tris + 3 * j).w);
                 df3 o2 = df3_add(o, df3_scale(d, t));
-                df dn = df3_dot(d, n);
+                df dn = nd;
                 df3 d2 = df3_sub(d, df3_scale(n, df_make(2.f * dn.hi, 2.f * dn.lo)));
                 df L2 = df_add(L, t);
                 out.oh[0] = o2.x.hi; out.oh[1] = o2.y.hi; out.oh[2] = o2.z.hi;
@@ -718,11 +729,11 @@ k_trace_df(const __grid_constant__ TraceArgs a) {
         if (has) {
             Ray32 r = make_ray32(df3_hi(o), df3_hi(d));
             int32_t j = -1;
-            df t = df_make(INFINITY, 0.f);
+            df t = df_make(INFINITY, 0.f), nd = df_make(0.f, 0.f);
             if (a.T > 0) {
                 Trav tv;
                 j = traverse32<kCount>(a, r, prev, tv, stack, &visits, &tests);
-                j = settle_hit(a, o, d, prev, tv, j, stack, t);
+                j = settle_hit(a, o, d, prev, tv, j, stack, t, nd);
             }
             if (kCount && j >= 0) {
                 d3 o64 = mk3(df_to_double(o.x), df_to_double(o.y), df_to_double(o.z));
@@ -735,7 +746,7 @@ k_trace_df(const __grid_constant__ TraceArgs a) {
                 df3 n = ld_plane_n(a.plane, j, c);
                 int32_t surf = __float_as_int(__ldg(a.tris + 3 * j).w);
                 df3 o2 = df3_add(o, df3_scale(d, t));
-                df dn = df3_dot(d, n);
+                df dn = nd;
                 d = df3_sub(d, df3_scale(n, df_make(2.f * dn.hi, 2.f * dn.lo)));
                 o = o2;
                 L = df_add(L, t);
@@ -855,10 +866,10 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_batch(const __grid_cons
             const BatchJobDev* J = a.jobs + job;
             const JobScene sc{J->nodes, J->tris, J->plane, a.cnt, J->rot_stride};
             Ray32 r = make_ray32(df3_hi(o), df3_hi(d));
-            df t = df_make(INFINITY, 0.f);
+            df t = df_make(INFINITY, 0.f), nd = df_make(0.f, 0.f);
             Trav tv;
             int32_t j = traverse32<false>(sc, r, prev, tv, stack, nullptr, nullptr);
-            j = settle_hit(sc, o, d, prev, tv, j, stack, t);
+            j = settle_hit(sc, o, d, prev, tv, j, stack, t, nd);
             {
                 const float4 rh = J->rx_h, rl = J->rx_l, al = J->alpha;
                 const df3 Rx{df_make(rh.x, rl.x), df_make(rh.y, rl.y), df_make(rh.z, rl.z)};
@@ -879,7 +890,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_batch(const __grid_cons
                 df3 n = ld_plane_n(J->plane, j, c);
                 int32_t surf = __float_as_int(__ldg(J->tris + 3 * j).w);
                 df3 o2 = df3_add(o, df3_scale(d, t));
-                df dn = df3_dot(d, n);
+                df dn = nd;
                 df3 d2 = df3_sub(d, df3_scale(n, df_make(2.f * dn.hi, 2.f * dn.lo)));
                 df L2 = df_add(L, t);
                 out.oh[0] = o2.x.hi; out.oh[1] = o2.y.hi; out.oh[2] = o2.z.hi;
@@ -964,10 +975,10 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_batch_df(const __gri
             const BatchJobDev* J = a.jobs + job;
             const JobScene sc{J->nodes, J->tris, J->plane, a.cnt, J->rot_stride};
             Ray32 r = make_ray32(df3_hi(o), df3_hi(d));
-            df t = df_make(INFINITY, 0.f);
+            df t = df_make(INFINITY, 0.f), nd = df_make(0.f, 0.f);
             Trav tv;
             int32_t j = traverse32<false>(sc, r, prev, tv, stack, nullptr, nullptr);
-            j = settle_hit(sc, o, d, prev, tv, j, stack, t);
+            j = settle_hit(sc, o, d, prev, tv, j, stack, t, nd);
             {
                 const float4 rh = J->rx_h, rl = J->rx_l, al = J->alpha;
                 const df3 Rx{df_make(rh.x, rl.x), df_make(rh.y, rl.y), df_make(rh.z, rl.z)};
@@ -988,7 +999,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_batch_df(const __gri
                 df3 n = ld_plane_n(J->plane, j, c);
                 int32_t surf = __float_as_int(__ldg(J->tris + 3 * j).w);
                 df3 o2 = df3_add(o, df3_scale(d, t));
-                df dn = df3_dot(d, n);
+                df dn = nd;
                 d = df3_sub(d, df3_scale(n, df_make(2.f * dn.hi, 2.f * dn.lo)));
                 o = o2;
                 L = df_add(L, t);
