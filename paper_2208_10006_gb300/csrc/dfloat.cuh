@@ -41,12 +41,13 @@ __device__ __forceinline__ df two_prod(float a, float b) {
     return df{p, __fmaf_rn(a, b, -p)};
 }
 
+// a + b with one two-sum on the high words and the low words added in FP32:
+// the error is a few units of 2^-48 of the operands' magnitude (not of the
+// result's, under cancellation), the absolute accuracy the ray state, the face
+// planes and the receiver positions carry in any case
 __device__ __forceinline__ df df_add(df a, df b) {
     df s = two_sum(a.hi, b.hi);
-    df t = two_sum(a.lo, b.lo);
-    s.lo = __fadd_rn(s.lo, t.hi);
-    s = fast_two_sum(s.hi, s.lo);
-    s.lo = __fadd_rn(s.lo, t.lo);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
     return fast_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
