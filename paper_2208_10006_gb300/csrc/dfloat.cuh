@@ -105,6 +105,20 @@ __device__ __forceinline__ df df3_dot(df3 a, df3 b) {
     e = __fmaf_rn(a.z.lo, b.z.hi, e);
     return two_sum(s2.hi, e);   // not fast_two_sum: under cancellation |e| may exceed |s2.hi|
 }
+// a + b c in one pass: the product's high word error-free, its low terms and
+// a.lo gathered in FP32 (the accuracy of df_mul followed by df_add)
+__device__ __forceinline__ df df_fma(df a, df b, df c) {
+    df p = two_prod(b.hi, c.hi);
+    p.lo = __fmaf_rn(b.hi, c.lo, p.lo);
+    p.lo = __fmaf_rn(b.lo, c.hi, p.lo);
+    df s = two_sum(a.hi, p.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, p.lo));
+    return fast_two_sum(s.hi, s.lo);
+}
+// a + b s for vectors a, b and a scalar s
+__device__ __forceinline__ df3 df3_fma(df3 a, df3 b, df s) {
+    return df3{df_fma(a.x, b.x, s), df_fma(a.y, b.y, s), df_fma(a.z, b.z, s)};
+}
 __device__ __forceinline__ float3 df3_hi(df3 a) { return make_float3(a.x.hi, a.y.hi, a.z.hi); }
 
 }  // namespace sbr

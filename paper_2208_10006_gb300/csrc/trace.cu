@@ -419,7 +419,7 @@ __device__ __forceinline__ bool rx_accept(const df3& o, const df3& d, df L, df t
     df3 v = df3_sub(R, o);
     df ts = df3_dot(v, d);
     if (ts.hi < 0.f || (hit && df_lt(t_hit, ts))) return false;
-    df3 w = df3_sub(df3_scale(d, ts), v);   // o + t* d - Rx
+    df3 w = df3_fma(df3{df_neg(v.x), df_neg(v.y), df_neg(v.z)}, d, ts);   // o + t* d - Rx
     df dist2 = df3_dot(w, w);
     df sl = df_add(L, ts);
     df rad2 = df_mul(a2o3, df_mul(sl, sl));
@@ -615,9 +615,9 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
                 df c;
                 df3 n = ld_plane_n(a.plane, j, c);
                 int32_t surf = __float_as_int(__ldg(a.tris + 3 * j).w);
-                df3 o2 = df3_add(o, df3_scale(d, t));
+                df3 o2 = df3_fma(o, d, t);
                 df dn = nd;
-                df3 d2 = df3_sub(d, df3_scale(n, df_make(2.f * dn.hi, 2.f * dn.lo)));
+                df3 d2 = df3_fma(d, n, df_make(-2.f * dn.hi, -2.f * dn.lo));
                 df L2 = df_add(L, t);
                 out.oh[0] = o2.x.hi; out.oh[1] = o2.y.hi; out.oh[2] = o2.z.hi;
                 out.ol[0] = o2.x.lo; out.ol[1] = o2.y.lo; out.ol[2] = o2.z.lo;
@@ -745,9 +745,9 @@ k_trace_df(const __grid_constant__ TraceArgs a) {
                 df c;
                 df3 n = ld_plane_n(a.plane, j, c);
                 int32_t surf = __float_as_int(__ldg(a.tris + 3 * j).w);
-                df3 o2 = df3_add(o, df3_scale(d, t));
+                df3 o2 = df3_fma(o, d, t);
                 df dn = nd;
-                d = df3_sub(d, df3_scale(n, df_make(2.f * dn.hi, 2.f * dn.lo)));
+                d = df3_fma(d, n, df_make(-2.f * dn.hi, -2.f * dn.lo));
                 o = o2;
                 L = df_add(L, t);
                 a.seq[(int64_t)bounce * a.R + ray] = surf;
@@ -889,9 +889,9 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_batch(const __grid_cons
                 df c;
                 df3 n = ld_plane_n(J->plane, j, c);
                 int32_t surf = __float_as_int(__ldg(J->tris + 3 * j).w);
-                df3 o2 = df3_add(o, df3_scale(d, t));
+                df3 o2 = df3_fma(o, d, t);
                 df dn = nd;
-                df3 d2 = df3_sub(d, df3_scale(n, df_make(2.f * dn.hi, 2.f * dn.lo)));
+                df3 d2 = df3_fma(d, n, df_make(-2.f * dn.hi, -2.f * dn.lo));
                 df L2 = df_add(L, t);
                 out.oh[0] = o2.x.hi; out.oh[1] = o2.y.hi; out.oh[2] = o2.z.hi;
                 out.ol[0] = o2.x.lo; out.ol[1] = o2.y.lo; out.ol[2] = o2.z.lo;
@@ -998,9 +998,9 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_batch_df(const __gri
                 df c;
                 df3 n = ld_plane_n(J->plane, j, c);
                 int32_t surf = __float_as_int(__ldg(J->tris + 3 * j).w);
-                df3 o2 = df3_add(o, df3_scale(d, t));
+                df3 o2 = df3_fma(o, d, t);
                 df dn = nd;
-                d = df3_sub(d, df3_scale(n, df_make(2.f * dn.hi, 2.f * dn.lo)));
+                d = df3_fma(d, n, df_make(-2.f * dn.hi, -2.f * dn.lo));
                 o = o2;
                 L = df_add(L, t);
                 J->seq[(int64_t)bounce * J->R + ray] = surf;
