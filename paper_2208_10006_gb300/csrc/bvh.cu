@@ -318,13 +318,6 @@ __global__ void k_top_cut(int64_t nn, const int32_t* __restrict__ span, const in
     }
 }
 
-// float <-> unsigned with the same order (for atomicMin/Max on boxes)
-__device__ __forceinline__ unsigned f2o(float f) {
-    const unsigned u = __float_as_uint(f);
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float o2f(unsigned u) { return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u); }
-
 __device__ __forceinline__ float box_area(const float* b) {
     const float dx = b[3] - b[0], dy = b[4] - b[1], dz = b[5] - b[2];
     return 2.f * (dx * dy + dy * dz + dz * dx);
