@@ -314,7 +314,10 @@ sbr_status sbr_synthesize_H_elements(const sbr_path_list* pl, const void* gains,
  * PL_inc = -10 log10 sum |g|^2, tau_rms (Eq. 5, s), power-weighted mean AoD
  * azimuth/elevation and AoA azimuth/elevation (deg). A receiver without
  * paths gets +inf path loss and NaN for the rest.
- * pdp_db: dev float [n_rx*n_bins]; stats: dev double [n_rx*SBR_NSTATS].
+ * pdp_db: float [n_rx*n_bins]; stats: double [n_rx*SBR_NSTATS]; each in device
+ * memory or in pinned host memory (cudaHostAlloc / cudaMallocHost, which
+ * unified addressing makes device-accessible): the kernel writes the results
+ * in place, complete when the stream has passed the call.
  */
 sbr_status sbr_pdp_angles(const sbr_path_list* pl, const void* gains, int32_t F, int32_t f_index,
                           double fc_hz, double bin_s, int32_t n_bins, float* pdp_db,

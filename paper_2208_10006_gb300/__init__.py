@@ -295,15 +295,25 @@ def synthesize_H_elements(pl: PathList, gains: torch.Tensor, freqs: torch.Tensor
 
 
 def pdp_angles(pl: PathList, gains: torch.Tensor, f_index: int, fc_hz: float, bin_s: float = 1e-9,
-               n_bins: int = 1024, stream=None):
-    """PDP in dB [n_rx, n_bins] (float32) and stats [n_rx, 7] (float64)."""
+               n_bins: int = 1024, stream=None, out=None):
+    """PDP in dB [n_rx, n_bins] (float32) and stats [n_rx, 7] (float64). `out`
+    may be a (pdp, stats) pair of preallocated CUDA or pinned host tensors of
+    shapes [max(n_rx, 1), n_bins] and [max(n_rx, 1), 7]: the kernel then writes
+    them directly (pinned host memory is device-accessible under unified
+    addressing), complete once the stream has passed the call."""
     n_rx = pl.n_rx
     F = int(gains.shape[1]) if gains.dim() == 2 else 1
-    pdp = torch.empty((max(n_rx, 1), n_bins), dtype=torch.float32, device=_dev())
-    stats = torch.empty((max(n_rx, 1), NSTATS), dtype=torch.float64, device=_dev())
+    if out is None:
+        pdp = torch.empty((max(n_rx, 1), n_bins), dtype=torch.float32, device=_dev())
+        stats = torch.empty((max(n_rx, 1), NSTATS), dtype=torch.float64, device=_dev())
+    else:
+        pdp, stats = out
+        if (tuple(pdp.shape) != (max(n_rx, 1), n_bins) or pdp.dtype != torch.float32 or
+                tuple(stats.shape) != (max(n_rx, 1), NSTATS) or stats.dtype != torch.float64):
+            raise ValueError("out: float32 [max(n_rx, 1), n_bins] and float64 [max(n_rx, 1), %d]" % NSTATS)
     g = gains if gains.numel() else torch.empty(1, dtype=torch.complex64, device=_dev())
     _check(_L().sbr_pdp_angles(pl.handle, _ptr(g), F, int(f_index), float(fc_hz), float(bin_s),
-                               int(n_bins), _ptr(pdp), _ptr(stats), _stream(stream)))
+                               int(n_bins), _ptr_or_pinned(pdp), _ptr_or_pinned(stats), _stream(stream)))
     return pdp[:n_rx], stats[:n_rx]
 
 

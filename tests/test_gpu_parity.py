@@ -101,6 +101,24 @@ def test_pdp_and_stats_match_oracle(sbr, name):
     assert np.abs(st[has, 3:] - ost[has, 3:]).max(initial=0) < 1e-4          # degrees
 
 
+def test_pdp_into_pinned_host_memory_equals_device_output(sbr):
+    # the PDP kernel writes straight into pinned host tensors: bit-identical to
+    # its device output
+    sc = SCENES["urban_med"]()
+    r = sbr.run_scene(sc)
+    n_rx, n_bins = r["paths"].n_rx, 512
+    pdp_d, st_d = sbr.pdp_angles(r["paths"], r["g"], 0, float(sc["freqs"][0]), 1e-9, n_bins)
+    out = (torch.full((max(n_rx, 1), n_bins), 7.0, dtype=torch.float32, pin_memory=True),
+           torch.full((max(n_rx, 1), sbr.NSTATS), 7.0, dtype=torch.float64, pin_memory=True))
+    pdp_h, st_h = sbr.pdp_angles(r["paths"], r["g"], 0, float(sc["freqs"][0]), 1e-9, n_bins, out=out)
+    torch.cuda.synchronize()
+    assert not pdp_h.is_cuda and pdp_h.data_ptr() == out[0].data_ptr()
+    assert np.array_equal(pdp_h.numpy(), pdp_d.cpu().numpy())
+    assert np.array_equal(st_h.numpy(), st_d.cpu().numpy(), equal_nan=True)
+    with pytest.raises(ValueError):
+        sbr.pdp_angles(r["paths"], r["g"], 0, 1e9, 1e-9, n_bins + 1, out=out)
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 2e-5)])
 def test_synthesis_matches_oracle(sbr, precision, tol):
     sc = scenes.config3(N=40, K=3, F=12)
