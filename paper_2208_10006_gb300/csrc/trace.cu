@@ -235,16 +235,17 @@ __device__ int32_t traverse32(const A& a, const Ray32& r, int prev, Trav& tv, in
     tv.best_t = INFINITY; tv.lim = INFINITY; tv.best_j = -1; tv.best_face = 0x7fffffff;
     tv.best_surf = -2; tv.nu = 0; tv.overflow = false;
     tv.omax = fmaxf(fabsf(r.ok.x), fmaxf(fabsf(r.ok.y), fabsf(r.ok.z)));
-    // one loop over references: an internal node tests its two child boxes and
-    // continues with the nearer hit child (the farther one is stacked); a leaf
-    // reference tests its triangles; leaves and nodes share the stack
-    // the faces with vertex components in this ray's (kx, ky, kz) order: block
-    // kz of the three rotated copies, of which a.tris is the last
+    // while-while: the inner loop descends through internal nodes (each tests
+    // its two child boxes and continues with the nearer hit child, the farther
+    // one stacked) until it reaches a leaf reference, whose triangles the
+    // outer loop then tests; leaves and nodes share the stack. The faces are
+    // read with vertex components in this ray's (kx, ky, kz) order: block kz of
+    // the three rotated copies, of which a.tris is the last
     const float4* tris_k = a.tris + (int64_t)(r.kz - 2) * a.rot_stride;
     int sp = 0;
     int32_t ref = 0;
     for (;;) {
-        if (ref >= 0) {
+        while (ref >= 0) {
             const float4* nd = a.nodes + 4 * (int64_t)ref;
             float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
             int32_t r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
@@ -252,20 +253,18 @@ __device__ int32_t traverse32(const A& a, const Ray32& r, int prev, Trav& tv, in
             float tn0, tn1;
             bool h0 = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, r, tv.lim, tn0);
             bool h1 = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, r, tv.lim, tn1);
+            const bool first0 = h0 && (!h1 || tn0 <= tn1);
             if (h0 && h1) {
-                bool first0 = tn0 <= tn1;
-                if (sp < kStack) stack[sp++] = first0 ? r1 : r0;
-                else { atomicOr(&a.cnt->status, (unsigned)ST_STACK); tv.overflow = true; break; }
-                ref = first0 ? r0 : r1;
-                continue;
+                if (sp == kStack) { atomicOr(&a.cnt->status, (unsigned)ST_STACK); tv.overflow = true; return tv.best_j; }
+                stack[sp++] = first0 ? r1 : r0;
             }
-            if (h0) { ref = r0; continue; }
-            if (h1) { ref = r1; continue; }
-        } else {
-            const int32_t first = leaf_first(ref), cnt = leaf_count(ref);
-            for (int k = 0; k < cnt; ++k) tri_test32(tris_k, first + k, prev, r, tv);
-            if (kCount) *tests += cnt;
+            if (h0 || h1) ref = first0 ? r0 : r1;
+            else if (sp == 0) return tv.best_j;
+            else ref = stack[--sp];
         }
+        const int32_t first = leaf_first(ref), cnt = leaf_count(ref);
+        for (int k = 0; k < cnt; ++k) tri_test32(tris_k, first + k, prev, r, tv);
+        if (kCount) *tests += cnt;
         if (sp == 0) break;
         ref = stack[--sp];
     }
