@@ -101,6 +101,29 @@ def test_pdp_and_stats_match_oracle(sbr, name):
     assert np.abs(st[has, 3:] - ost[has, 3:]).max(initial=0) < 1e-4          # degrees
 
 
+def test_calls_on_user_streams_give_the_same_paths(sbr):
+    # build and trace on one user stream, the path list and gains on another (the
+    # path list call then waits on the host for the trace): the same path list
+    # and gains as on the current stream
+    sc = SCENES["urban_small"]()
+    ref = sbr.run_scene(sc)
+    d = sbr.scene_to_device(sc)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    s1.wait_stream(torch.cuda.current_stream())
+    bvh = sbr.build_bvh(d["tri"], d["surface_id"], d["S"], stream=s1)
+    tr = sbr.trace(bvh, d["tx"], d["rx"], sc["N"], sc["K"], stream=s1)
+    s2.wait_stream(torch.cuda.current_stream())
+    pl = sbr.paths(tr, bvh, stream=s2)
+    g = sbr.path_gains(pl, d["mats"], d["freqs"], d["gamma"], d["disp"], d["pol"], stream=s2)
+    ex = pl.export(stream=s2)
+    s2.synchronize()
+    assert tr.stats()["ray_bounces"] == ref["stats"]["ray_bounces"]
+    a, b = to_numpy(ref["export"]), to_numpy(ex)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(ref["g"].cpu().numpy(), g.cpu().numpy())
+
+
 def test_pdp_into_pinned_host_memory_equals_device_output(sbr):
     # the PDP kernel writes straight into pinned host tensors: bit-identical to
     # its device output
