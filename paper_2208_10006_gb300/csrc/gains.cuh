@@ -41,39 +41,46 @@ __device__ __forceinline__ cd csqrt_(cd z) {
     return cd{v, z.im < 0.0 ? -u : u};
 }
 
-// m reflections off surfaces surf[0..m), unfolded length Lp, polarimetric
-// record J (kJones doubles); gamma / disp may be null (no absorption / phase)
-__device__ __forceinline__ float2 path_gain(int m, const int32_t* __restrict__ surf, double Lp,
-                                            const double* __restrict__ J, const sbr_material* __restrict__ mats,
-                                            int32_t S, double f, const float* gamma, const float* disp, int pol) {
-    const int pb = pol == SBR_POL_V ? 0 : 2;
-    cd b0{J[pb], 0.0}, b1{J[pb + 1], 0.0};
+// Fresnel coefficients (TE, TM) of reflection k and its roughness factor rho
+// at frequency f; cosine of incidence c from the polarimetric record
+struct Refl {
+    cd te, tm;
+    double rho;
+};
+__device__ __forceinline__ Refl reflection(const sbr_material& mt, double c, double f) {
     const double eps2_scale = 1.0 / (2.0 * kPi * f * kEps0);
     const double kr = 4.0 * kPi * f / kC0;
-    for (int k = 0; k < m; ++k) {
-        int s = surf[k];
-        if (s < 0 || s >= S) return make_float2(NAN, NAN);  // not reachable: S is checked on the host
-        const sbr_material mt = mats[s];
-        double c = J[36 + k];
-        double s2 = 1.0 - c * c;
-        cd eta{mt.eps_r, -mt.sigma_s_per_m * eps2_scale};
-        cd root = csqrt_(cd{eta.re - s2, eta.im});
-        cd cc{c, 0.0};
-        cd te = cdiv(csub(cc, root), cadd(cc, root));
-        cd ec = cscale(eta, c);
-        cd tm = cdiv(csub(ec, root), cadd(ec, root));
-        double gk = kr * mt.rough_m * c;
-        double rho = exp(-0.5 * gk * gk);
-        b0 = cscale(cmul(te, b0), rho);
-        b1 = cscale(cmul(tm, b1), rho);
-        if (k + 1 < m) {
-            const double* M = J + 4 + 4 * k;
-            cd n0 = cadd(cscale(b0, M[0]), cscale(b1, M[1]));
-            cd n1 = cadd(cscale(b0, M[2]), cscale(b1, M[3]));
-            b0 = n0;
-            b1 = n1;
-        }
+    double s2 = 1.0 - c * c;
+    cd eta{mt.eps_r, -mt.sigma_s_per_m * eps2_scale};
+    cd root = csqrt_(cd{eta.re - s2, eta.im});
+    cd cc{c, 0.0};
+    Refl r;
+    r.te = cdiv(csub(cc, root), cadd(cc, root));
+    cd ec = cscale(eta, c);
+    r.tm = cdiv(csub(ec, root), cadd(ec, root));
+    double gk = kr * mt.rough_m * c;
+    r.rho = exp(-0.5 * gk * gk);
+    return r;
+}
+
+// the field (b0, b1) through reflection k (coefficients rf), then the change to
+// the next reflection's basis (k + 1 < m)
+__device__ __forceinline__ void reflect_field(cd& b0, cd& b1, const Refl& rf, const double* __restrict__ J,
+                                              int k, int m) {
+    b0 = cscale(cmul(rf.te, b0), rf.rho);
+    b1 = cscale(cmul(rf.tm, b1), rf.rho);
+    if (k + 1 < m) {
+        const double* M = J + 4 + 4 * k;
+        cd n0 = cadd(cscale(b0, M[0]), cscale(b1, M[1]));
+        cd n1 = cadd(cscale(b0, M[2]), cscale(b1, M[3]));
+        b0 = n0;
+        b1 = n1;
     }
+}
+
+// Rx projection, Friis amplitude, absorption and dispersion phase of the field
+__device__ __forceinline__ float2 finish_gain(cd b0, cd b1, const double* __restrict__ J, int pb, double Lp,
+                                              double f, const float* gamma, const float* disp) {
     const double* cv = J + 32 + pb;
     cd proj = cadd(cscale(b0, cv[0]), cscale(b1, cv[1]));
     double amp = kC0 / (4.0 * kPi * f * Lp);
@@ -83,6 +90,21 @@ __device__ __forceinline__ float2 path_gain(int m, const int32_t* __restrict__ s
     sincos(ph, &sn, &cs);
     cd v = cmul(cscale(cd{cs, sn}, amp * att), proj);
     return make_float2((float)v.re, (float)v.im);
+}
+
+// m reflections off surfaces surf[0..m), unfolded length Lp, polarimetric
+// record J (kJones doubles); gamma / disp may be null (no absorption / phase)
+__device__ __forceinline__ float2 path_gain(int m, const int32_t* __restrict__ surf, double Lp,
+                                            const double* __restrict__ J, const sbr_material* __restrict__ mats,
+                                            int32_t S, double f, const float* gamma, const float* disp, int pol) {
+    const int pb = pol == SBR_POL_V ? 0 : 2;
+    cd b0{J[pb], 0.0}, b1{J[pb + 1], 0.0};
+    for (int k = 0; k < m; ++k) {
+        int s = surf[k];
+        if (s < 0 || s >= S) return make_float2(NAN, NAN);  // not reachable: S is checked on the host
+        reflect_field(b0, b1, reflection(mats[s], J[36 + k], f), J, k, m);
+    }
+    return finish_gain(b0, b1, J, pb, Lp, f, gamma, disp);
 }
 
 }  // namespace

@@ -68,21 +68,28 @@ k_pdp(const int32_t* __restrict__ rx_off, const double* __restrict__ L, const do
     }
     {
         // the nine block sums at once, each in the order of block_sum (butterfly
-        // within each warp, then the warps in order): two barriers instead of 27
+        // within each warp, then the warps in order): two barriers instead of 27.
+        // A receiver with at most 32 paths has them all in warp 0, whose sums
+        // alone are added (the other warps' are exact zeros): the FP64 pipe,
+        // this kernel's bound, then carries one warp's butterflies, not eight
         __shared__ double part[kPdpThreads / 32][9];
         __shared__ double tot[9];
         double v[9] = {sp, st, st2, cr, ci, a1, a2, a3, a4};
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const bool one_warp = o1 - o0 <= 32;
+        if (!one_warp || warp == 0) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q)
-            for (int o = 16; o; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-        if (lane == 0)
+            for (int q = 0; q < 9; ++q)
+                for (int o = 16; o; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+            if (lane == 0)
 #pragma unroll
-            for (int q = 0; q < 9; ++q) part[warp][q] = v[q];
+                for (int q = 0; q < 9; ++q) part[warp][q] = v[q];
+        }
         __syncthreads();
         if (threadIdx.x < 9) {
             double t = 0.0;
-            for (int w = 0; w < kPdpThreads / 32; ++w) t += part[w][threadIdx.x];
+            const int nw = one_warp ? 1 : kPdpThreads / 32;
+            for (int w = 0; w < nw; ++w) t += part[w][threadIdx.x];
             tot[threadIdx.x] = t;
         }
         __syncthreads();
