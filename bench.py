@@ -50,12 +50,12 @@ ALG_BYTES_PER_RAY_BOUNCE = 2 * RAY_REC_BYTES
 # DRAM bytes of one k_trace_df launch on the headline workload (N = 1000), from
 # one ncu capture of the launch (dram__bytes_read.sum + dram__bytes_write.sum,
 # profiles/k_trace_df_urban_N1000_dram.md); None once the kernel has changed
-TRACE_DRAM_BYTES = 266_548_992 + 116_137_472
+TRACE_DRAM_BYTES = 260_538_112 + 85_420_800
 # warp instructions issued by one k_trace_df launch on the same workload, from
 # one ncu capture (smsp__inst_executed.sum, profiles/k_trace_df_urban_N1000_issue.md);
 # None once the kernel has changed. The issue peak is one warp instruction per
 # clock on each of the 4 schedulers of the 152 SMs
-TRACE_WARP_INST = 2_257_125_274
+TRACE_WARP_INST = 2_255_353_276
 SM_COUNT = 152
 SCHEDULERS_PER_SM = 4
 SEQ_BYTES = 8           # surface id and face id appended per reflection

@@ -704,8 +704,9 @@ k_trace_df(const __grid_constant__ TraceArgs a) {
                         ray = pool_ray(a, i);
                         o = df3{df_make(a.tx_h[0], a.tx_l[0]), df_make(a.tx_h[1], a.tx_l[1]),
                                 df_make(a.tx_h[2], a.tx_l[2])};
-                        float4 da = __ldg(a.dir_a + ray);
-                        float2 db = __ldg(a.dir_b + ray);
+                        // streamed once: evict-first, so that L1 keeps the BVH nodes
+                        float4 da = __ldcs(a.dir_a + ray);
+                        float2 db = __ldcs(a.dir_b + ray);
                         d = df3{df_make(da.x, da.w), df_make(da.y, db.x), df_make(da.z, db.y)};
                         L = df_make(0.f, 0.f);
                         prev = -1;
@@ -749,8 +750,9 @@ k_trace_df(const __grid_constant__ TraceArgs a) {
                 d = df3_fma(d, n, df_make(-2.f * dn.hi, -2.f * dn.lo));
                 o = o2;
                 L = df_add(L, t);
-                a.seq[(int64_t)bounce * a.R + ray] = surf;
-                a.seqf[(int64_t)bounce * a.R + ray] = __float_as_int(__ldg(a.tris + 3 * j + 1).w);
+                // per-bounce records, written once and read after the launch: streaming stores
+                __stcs(&a.seq[(int64_t)bounce * a.R + ray], surf);
+                __stcs(&a.seqf[(int64_t)bounce * a.R + ray], __float_as_int(__ldg(a.tris + 3 * j + 1).w));
                 prev = surf;
                 bounce += 1;
                 entered = bounce;
