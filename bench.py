@@ -450,7 +450,7 @@ def run_gpu(args):
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scenes.config2(), budget_s=args.cpu_budget)
 
-    # the survey's algorithmic figure: 128 B of ray state per ray-bounce; the
+    # the algorithmic figure: 128 B of ray state per ray-bounce; the
     # depth-first kernel keeps the ray state in registers, so what it moves
     # through memory (streamed_bytes) is far below it
     achieved = ALG_BYTES_PER_RAY_BOUNCE * rb / (bounce_ms / 1e3) / 1e9

@@ -45,7 +45,7 @@ typedef enum {
     SBR_ERR_STACK_OVERFLOW = 4, /* BVH deeper than the traversal stack          */
     SBR_ERR_TIMEOUT = 5,        /* a bounded device wait gave up                */
     SBR_ERR_NUMERIC = 6,        /* non-finite input or result                   */
-    SBR_ERR_UNSUPPORTED = 7,    /* valid request this build cannot serve        */
+    SBR_ERR_UNSUPPORTED = 7,    /* valid request the library cannot serve       */
     SBR_ERR_ALLOC = 8           /* device allocation failed                      */
 } sbr_status;
 
@@ -471,7 +471,7 @@ sbr_status sbr_batch_tune(const sbr_bvh* const* scenes, const sbr_material* cons
 /* ------------------------------------------------------------------------
  * Learned surrogate. The paper has no counterpart: a query-time stand-in for
  * the method's per-receiver outputs (path loss, RMS delay spread and PDP of
- * Eq. 2, 4, 5), learned from them, with full SBR as the fallback and judge.
+ * Eq. 2, 4, 5), learned from them, with full SBR as the fallback and arbiter.
  */
 
 /*

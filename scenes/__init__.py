@@ -21,7 +21,7 @@ A scene is a plain dict of numpy arrays:
     N, K                             geodesic subdivision frequency and max reflections
     pol                              'V' or 'H'
 
-The workloads follow the synthetic configurations of the hot-path survey:
+Three synthetic workloads:
 config 1 (SISO 28 GHz, ground + one box), config 2 (urban grid at 300 GHz,
 1024 receivers) and config 3 (indoor room with furniture, 16x16 UPA to 64-ULA
 at 100 GHz, 1024 subcarriers). Every random draw uses
