@@ -48,18 +48,46 @@ RAY_REC_BYTES = 64      # one queued ray record (origin, direction, L, id, last 
 # record) read at the start of the segment and written for the next one
 ALG_BYTES_PER_RAY_BOUNCE = 2 * RAY_REC_BYTES
 # DRAM bytes of one k_trace_df launch on the headline workload (N = 1000), from
-# one ncu capture of the launch (dram__bytes_read.sum + dram__bytes_write.sum,
-# profiles/k_trace_df_urban_N1000_dram.md); None once the kernel has changed
+# one ncu capture of the launch (dram__bytes_read.sum + dram__bytes_write.sum)
 TRACE_DRAM_BYTES = 260_538_112 + 85_420_800
 # warp instructions issued by one k_trace_df launch on the same workload, from
-# one ncu capture (smsp__inst_executed.sum, profiles/k_trace_df_urban_N1000_issue.md);
-# None once the kernel has changed. The issue peak is one warp instruction per
-# clock on each of the 4 schedulers of the 152 SMs
+# one ncu capture (smsp__inst_executed.sum). The issue peak is one warp
+# instruction per clock on each of the 4 schedulers of the 152 SMs
 TRACE_WARP_INST = 2_255_353_276
+# SHA-256 (first 16 hex digits) of the trace kernel's source and the local
+# headers it includes, as they were when the two counters above were captured.
+# Any later edit changes it, and the counters are then reported as null
+# (unmeasured) instead of describing a kernel that no longer exists.
+TRACE_COUNTERS_SRC = "5c26724f3077f218"
 SM_COUNT = 152
 SCHEDULERS_PER_SM = 4
 SEQ_BYTES = 8           # surface id and face id appended per reflection
 DIR_BYTES = 24          # launch direction of a ray, double-float
+
+
+def trace_source_hash() -> str:
+    """SHA-256 over csrc/trace.cu and every local header it includes (recursively)."""
+    import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_2208_10006_gb300", "csrc")
+    seen, order, todo = set(), [], ["trace.cu"]
+    while todo:
+        name = todo.pop(0)
+        if name in seen or not os.path.exists(os.path.join(csrc, name)):
+            continue
+        seen.add(name)
+        order.append(name)
+        src = open(os.path.join(csrc, name), "rb").read()
+        todo += [x.decode() for x in re.findall(rb'#include "([^"]+)"', src)]
+    h = hashlib.sha256()
+    for name in order:
+        h.update(name.encode() + b"\0" + open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def trace_counters_current() -> bool:
+    """True when the trace kernel's source is the one the ncu counters describe."""
+    return trace_source_hash() == TRACE_COUNTERS_SRC
 
 
 def issue_roofline(launch_ms, clk, N):
@@ -67,7 +95,7 @@ def issue_roofline(launch_ms, clk, N):
     (counted once by ncu on the N = 1000 workload) over the live launch time,
     against the issue peak at the median SM clock sampled in the timed region."""
     mhz = clk.get("sm_mhz") if clk else None
-    if N != 1000 or not mhz:
+    if N != 1000 or not mhz or not trace_counters_current():
         return None
     achieved = TRACE_WARP_INST / (launch_ms / 1e3) / 1e9
     peak = SM_COUNT * SCHEDULERS_PER_SM * mhz / 1e3
@@ -449,6 +477,10 @@ def run_gpu(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scenes.config2(), budget_s=args.cpu_budget)
+        if synth is not None:
+            synthesis_vs_oracle(synth)
+    if synth is not None:
+        synth.pop("_samples", None)
 
     # the algorithmic figure: 128 B of ray state per ray-bounce; the
     # depth-first kernel keeps the ray state in registers, so what it moves
@@ -456,7 +488,9 @@ def run_gpu(args):
     achieved = ALG_BYTES_PER_RAY_BOUNCE * rb / (bounce_ms / 1e3) / 1e9
     hbm = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
     roof = {"kernel": "k_trace_df", "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm, "traffic": TRACE_DRAM_BYTES if N == 1000 else None,
+            "unit": "GB/s", "frac": achieved / hbm, "traffic": TRACE_DRAM_BYTES if (N == 1000 and trace_counters_current()) else None,
+            "counters_source_sha": trace_source_hash(),
+            "counters_current": trace_counters_current(),
             "peak_source": peak_src,
             "schedule": "depth first from bounce 0 (one launch per trace)",
             "algorithmic_bytes": "128 B ray state (64 B read + 64 B written) per ray-bounce, "
@@ -517,6 +551,14 @@ def bench_synthesis(sbr, torch, flush, peaks, peak_src, args):
     names = {sbr.SYNTH_BF16X3: "bf16x3_tcgen05", sbr.SYNTH_FP16X3: "fp16x3_tcgen05",
              sbr.SYNTH_FP32: "fp32_simt", sbr.SYNTH_FP64: "fp64_simt"}
     Href = None
+    # sampled (f, q, p) entries of every form, compared with the oracle in the
+    # CPU-baseline leg (6 frequencies x 8 receive x 16 transmit elements)
+    rng = np.random.default_rng(3)
+    fi = np.sort(rng.choice(F, 6, replace=False))
+    qi = np.sort(rng.choice(Nr, 8, replace=False))
+    pi = np.sort(rng.choice(Nt, 16, replace=False))
+    ix = [torch.as_tensor(v, device=d["freqs"].device) for v in (fi, qi, pi)]
+    samples = {"f": fi, "q": qi, "p": pi, "forms": {}}
     for prec in (sbr.SYNTH_FP64, sbr.SYNTH_FP32, sbr.SYNTH_BF16X3, sbr.SYNTH_FP16X3):
         try:
             sbr.synthesize_H(pl, g, d["freqs"], d["tx_elem"], d["rx_elem"], 0, prec, out=H)
@@ -535,6 +577,7 @@ def bench_synthesis(sbr, torch, flush, peaks, peak_src, args):
             ts.append(e0.elapsed_time(e1) / 1e3)
         t = statistics.median(ts)
         Hc = H.clone()
+        samples["forms"][names[prec]] = Hc[ix[0]][:, ix[1]][:, :, ix[2]].cpu().numpy()
         if prec == sbr.SYNTH_FP64:
             Href = Hc
         err = med = None
@@ -548,8 +591,8 @@ def bench_synthesis(sbr, torch, flush, peaks, peak_src, args):
         flops = 8.0 * F * Nr * Nt * P
         entry = {"value": 1.0 / t, "unit": "H tensors/s", "ms": t * 1e3,
                  "achieved_GBps": bytes_ / t / 1e9, "achieved_TFLOPs": flops / t / 1e12,
-                 "max_abs_err_vs_fp64_over_max": err,
-                 "median_rel_err_vs_fp64_where_abs_gt_1e-3_max": med}
+                 "max_abs_err_vs_gpu_fp64_form_over_max": err,
+                 "median_rel_err_vs_gpu_fp64_form_where_abs_gt_1e-3_max": med}
         if prec in tc_forms:
             hbm = float(peaks.get("hbm_gbs", 6800.0))
             tc = float(peaks.get("bf16_tflops", 1900.0))
@@ -572,9 +615,44 @@ def bench_synthesis(sbr, torch, flush, peaks, peak_src, args):
         trend["%dx%d" % (n, n)] = [float(x) for x in sbr.capacity(Hn, sc["snr_db"]).cpu()]
         del Hn
     out["capacity_vs_tx_array"] = {"snr_db": [float(s) for s in sc["snr_db"]], "bits_per_s_per_hz": trend}
+    ex = {k: v.cpu().numpy() for k, v in pl.export().items()}
+    samples["paths"] = dict(rx=ex["rx"], nb=ex["nb"], seq=ex["seq"], pts=ex["pts"], L=ex["L"])
+    samples["scene"] = sc
     del pl, g, tr, bvh
     out["per_element_reception"] = bench_per_element(sbr, torch, args)
+    out["_samples"] = samples
     return out
+
+
+def synthesis_vs_oracle(synth):
+    """CPU-baseline leg for the synthesis: the oracle's direct FP64 sum of Eq.
+    13-14 (its own gains, the GPU's path list) on the sampled (f, q, p) entries,
+    timed, and each GPU form's per-output error against it."""
+    import oracle
+    oracle.build()
+    smp = synth.pop("_samples")
+    sc, paths = smp["scene"], smp["paths"]
+    fi, qi, pi = smp["f"], smp["q"], smp["p"]
+    t0 = time.perf_counter()
+    g_ref = oracle.gains(sc, paths, freqs=sc["freqs"][fi], gamma=sc["gamma_db_km"][fi],
+                         disp=sc["disp_deg_km"][fi])
+    Ho = oracle.synth_H(paths, g_ref, sc["freqs"][fi], sc["tx"], sc["rx"][0], sc["tx_elem"][pi],
+                        sc["rx_elem"][qi])
+    t_o = time.perf_counter() - t0
+    a = np.abs(Ho)
+    big = a > 1e-3 * a.max()
+    for name, Hs in smp["forms"].items():
+        dH = np.abs(Hs - Ho)
+        synth["forms"][name]["vs_oracle_sampled"] = {
+            "max_abs_err_over_max": float(dH.max() / a.max()),
+            "median_rel_err_where_abs_gt_1e-3_max": float(np.median(dH[big] / a[big]))}
+    n = len(fi) * len(qi) * len(pi)
+    full = len(sc["freqs"]) * len(sc["rx_elem"]) * len(sc["tx_elem"])
+    synth["cpu_baseline"] = {
+        "value": n / full / t_o, "unit": "H tensors/s", "cores": oracle.nthreads_default(),
+        "kind": "oracle",
+        "sample": "%d of the %d entries of H (%d f x %d q x %d p), gains + direct FP64 sum over "
+                  "%d paths (%.3f s)" % (n, full, len(fi), len(qi), len(pi), len(paths["rx"]), t_o)}
 
 
 def bench_per_element(sbr, torch, args):

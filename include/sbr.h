@@ -328,8 +328,11 @@ sbr_status sbr_pdp_angles(const sbr_path_list* pl, const void* gains, int32_t F,
  * read as a Frobenius normalisation: W_f = (Nr Nt / Qbar) H_f H_f^H
  * (H_f^H H_f when Nt < Nr), Qbar = mean over f of ||H_f||_F^2; SNR linear
  * 10^(dB/10); C = mean_f log2 det(I + SNR/Nt W_f) by an FP64 Cholesky.
- * H: dev complex64 [F*Nr*Nt]; snr_db: host double [n_snr];
- * C: dev double [n_snr] (bit/s/Hz). min(Nr, Nt) <= 128.
+ * H: dev complex64 [F*Nr*Nt]; snr_db: host double [n_snr], 1 <= n_snr <= 32
+ * (read before the call returns); C: dev double [n_snr] (bit/s/Hz).
+ * min(Nr, Nt) <= 64 (the n x n Cholesky of one frequency is held in shared
+ * memory); larger arrays return SBR_ERR_INVALID_ARG. Asynchronous: returns
+ * once the work is enqueued on `stream`.
  */
 sbr_status sbr_capacity(const void* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,
                         int32_t n_snr, double* C, void* stream);
@@ -345,7 +348,10 @@ sbr_status sbr_capacity(const void* H, int32_t F, int32_t Nr, int32_t Nt, const 
  * that every GPU which loads the library holds until the process exits; hence
  * F <= 4096 and n_snr <= 32, larger requests return SBR_ERR_INVALID_ARG (use
  * sbr_capacity). The first call on a device looks up that array's address on
- * the device: make that first call before any stream capture. All calls share
+ * the device: make that first call before any stream capture. The address is
+ * kept for the life of the process; after cudaDeviceReset the library's
+ * module is loaded again and the kept address is stale, so do not call this
+ * entry point after a device reset. All calls share
  * the array, so calls whose work overlaps on the GPU (e.g. on two streams at
  * once) race; serialise them. Every scratch value it reads is first written by
  * the same call. Asynchronous: returns once the work is enqueued on `stream`.

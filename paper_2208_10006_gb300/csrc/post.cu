@@ -119,6 +119,7 @@ k_pdp(const int32_t* __restrict__ rx_off, const double* __restrict__ L, const do
 
 // ---------------------------------------------------------------- capacity
 constexpr int kCapThreads = 256;
+constexpr int kMaxSnr = 32;        // SNR values per capacity call
 
 __global__ void k_frob(const float2* __restrict__ H, int64_t per_f, double* __restrict__ qf) {
     __shared__ double sh[33];
@@ -221,6 +222,16 @@ __global__ void k_cap_reduce(const double* __restrict__ ld, int32_t F, int32_t n
     C[si] = s / F / log(2.0);
 }
 
+// linear SNR values of one capacity call, passed by value in the launch
+struct SnrList {
+    double lin[kMaxSnr];
+};
+
+__global__ void k_snr_store(const __grid_constant__ SnrList snr, int32_t n, double* __restrict__ out) {
+    int i = threadIdx.x;
+    if (i < n) out[i] = snr.lin[i];
+}
+
 // surrogate targets: one warp per (receiver, frequency); FP64 sums over the
 // receiver's paths of P_n = |g_n(f)|^2, tau_n = L_n / c, relative to the first
 // arrival for the delay spread and the taps
@@ -304,14 +315,16 @@ sbr_status surrogate_targets_run(const sbr_path_list* pl, const float2* g, int32
 
 sbr_status capacity_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt, const double* snr_db,
                         int32_t n_snr, double* C, cudaStream_t s) {
-    std::vector<double> lin(n_snr);
-    for (int i = 0; i < n_snr; ++i) lin[i] = std::pow(10.0, snr_db[i] / 10.0);
+    // the linear SNR list travels by value in the first launch, so the call
+    // returns as soon as its work is enqueued (no host table has to outlive it)
+    SnrList snr{};
+    for (int i = 0; i < n_snr; ++i) snr.lin[i] = std::pow(10.0, snr_db[i] / 10.0);
     double *d_lin, *qf, *qbar, *ld;
     SBR_TRY(dalloc_n(&d_lin, n_snr, s));
     SBR_TRY(dalloc_n(&qf, F, s));
     SBR_TRY(dalloc_n(&qbar, 1, s));
     SBR_TRY(dalloc_n(&ld, (size_t)F * n_snr, s));
-    SBR_TRY_CUDA(cudaMemcpyAsync(d_lin, lin.data(), sizeof(double) * n_snr, cudaMemcpyHostToDevice, s));
+    ::sbr::note_launch(), k_snr_store<<<1, kMaxSnr, 0, s>>>(snr, n_snr, d_lin);
     ::sbr::note_launch(), k_frob<<<F, kCapThreads, 0, s>>>(H, (int64_t)Nr * Nt, qf);
     ::sbr::note_launch(), k_qbar<<<1, 1, 0, s>>>(qf, F, qbar);
     size_t smem = capacity_smem(Nr, Nt);
@@ -319,8 +332,6 @@ sbr_status capacity_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt, cons
     ::sbr::note_launch(), k_capacity<<<F, kCapThreads, smem, s>>>(H, Nr, Nt, d_lin, n_snr, qbar, ld);
     ::sbr::note_launch(), k_cap_reduce<<<1, 32, 0, s>>>(ld, F, n_snr, C);
     SBR_TRY_CUDA(cudaGetLastError());
-    // the host SNR table must outlive the copy
-    SBR_TRY_CUDA(cudaStreamSynchronize(s));
     dfree(d_lin, s); dfree(qf, s); dfree(qbar, s); dfree(ld, s);
     return SBR_OK;
 }
@@ -335,7 +346,7 @@ sbr_status capacity_run(const float2* H, int32_t F, int32_t Nr, int32_t Nt, cons
 // array below, which each GPU that loads the library holds until the process
 // exits (about 1.1 MB).
 constexpr int kNoAllocMaxF = 4096;    // frequencies per call
-constexpr int kNoAllocMaxSnr = 32;    // SNR values per call
+constexpr int kNoAllocMaxSnr = kMaxSnr;  // SNR values per call
 
 struct CapacityScratch {
     double qf[kNoAllocMaxF];                     // ||H_f||_F^2
@@ -346,15 +357,6 @@ struct CapacityScratch {
 static __device__ __align__(256) CapacityScratch g_capacity_scratch;
 
 namespace {
-
-struct SnrList {
-    double lin[kNoAllocMaxSnr];
-};
-
-__global__ void k_noalloc_snr(const __grid_constant__ SnrList snr, int32_t n, CapacityScratch* scr) {
-    int i = threadIdx.x;
-    if (i < n) scr->snr_lin[i] = snr.lin[i];
-}
 
 std::mutex g_scratch_mu;
 CapacityScratch* g_scratch_ptr[256] = {};
@@ -397,7 +399,7 @@ sbr_status capacity_noalloc_run(const float2* H, int32_t F, int32_t Nr, int32_t 
     // has to be cleared; the SNR list travels by value in the launch itself
     SnrList snr{};
     for (int i = 0; i < n_snr; ++i) snr.lin[i] = std::pow(10.0, snr_db[i] / 10.0);
-    ::sbr::note_launch(), k_noalloc_snr<<<1, kNoAllocMaxSnr, 0, s>>>(snr, n_snr, scr);
+    ::sbr::note_launch(), k_snr_store<<<1, kMaxSnr, 0, s>>>(snr, n_snr, scr->snr_lin);
     ::sbr::note_launch(), k_frob<<<F, kCapThreads, 0, s>>>(H, (int64_t)Nr * Nt, scr->qf);
     ::sbr::note_launch(), k_qbar<<<1, 1, 0, s>>>(scr->qf, F, &scr->qbar);
     size_t smem = capacity_smem(Nr, Nt);

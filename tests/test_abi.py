@@ -88,3 +88,19 @@ def test_ctypes_struct_layouts_match_the_header(tmp_path):
         want.append(ctypes.sizeof(cls))
         want += [getattr(cls, f).offset for f in fields]
     assert got == want
+
+
+@pytest.mark.parametrize("n", [65, 96, 128])
+def test_capacity_rejects_arrays_above_64_on_the_host(lib, n):
+    # the header's contract: min(Nr, Nt) <= 64 (the Cholesky of one frequency
+    # lives in shared memory); larger arrays are refused before any CUDA call,
+    # by both capacity entry points, with the limit named in the message
+    snr = (ctypes.c_double * 1)(0.0)
+    fake = ctypes.c_void_p(256)   # never dereferenced: the check comes first
+    for entry in (lib.sbr_capacity, lib.sbr_capacity_noalloc):
+        assert entry(fake, 1, n, n + 3, snr, 1, fake, None) == 1
+        assert b"64" in lib.sbr_last_error()
+    # n = 64 passes the array check and fails only on the SNR count (33 > 32)
+    snr33 = (ctypes.c_double * 33)()
+    assert lib.sbr_capacity(fake, 1, 64, 64, snr33, 33, fake, None) == 1
+    assert b"n_snr" in lib.sbr_last_error()

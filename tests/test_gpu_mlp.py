@@ -70,15 +70,25 @@ def test_forward_gradients_and_adam_match_reference(sbr, depth, width, B):
     ref = mlp_ref.backward(layers, hs, g)
     grads = m.params(2).cpu().numpy()
     o = 0
-    for dW, db in ref:
-        for r in (dW.ravel(), db):
+    worst = []
+    for li, (dW, db) in enumerate(ref):
+        for name, r in (("W", dW.ravel()), ("b", db)):
             gg = grads[o:o + r.size].astype(np.float64)
             o += r.size
             nrm = np.linalg.norm(r)
             if nrm == 0:
                 assert np.abs(gg).max() == 0
                 continue
-            assert np.linalg.norm(gg - r) <= 2e-2 * nrm, (np.linalg.norm(gg - r) / nrm)
+            # per tensor, element by element: every entry within 5% of the
+            # tensor's largest entry (BF16 operands carry 2^-9 relative each,
+            # and a ReLU whose input rounds across zero moves a whole row), and
+            # the tensor as a whole within 2% in norm
+            e_max = np.abs(gg - r).max() / np.abs(r).max()
+            e_nrm = np.linalg.norm(gg - r) / nrm
+            worst.append((li, name, e_max, e_nrm))
+            assert e_max <= 5e-2, (li, name, e_max)
+            assert e_nrm <= 2e-2, (li, name, e_nrm)
+    print("gradient errors per tensor (layer, W/b, max|dg|/max|g|, |dg|/|g|):", worst)
     assert o == len(grads)
     # Adam, first step: m = (1 - b1) g, v = (1 - b2) g^2, bias-corrected
     gg = grads.astype(np.float32)

@@ -83,14 +83,22 @@ def test_pdp_and_stats_match_oracle(sbr, name):
     orc = oracle.run(sc)
     rep = compare_paths(ex, r["g"].cpu().numpy(), orc)
     assert_parity(rep)
-    if rep["only_gpu"] or rep["only_orc"]:
-        pytest.skip("edge-ambiguous keys present; per-receiver sums differ by construction")
+    # a receiver that has an edge-ambiguous (exempted) key on one side only has
+    # different per-receiver sums by construction: the taps and statistics are
+    # compared on every other receiver, and those must be nearly all of them
+    n_rx = len(sc["rx"])
+    odd = {k[0] for k in rep["only_gpu"]} | {k[0] for k in rep["only_orc"]}
+    keep = np.array([q not in odd for q in range(n_rx)])
+    assert keep.sum() >= max(1, n_rx - max(1, n_rx // 20)), (keep.sum(), n_rx)
+    print(name, "PDP compared on", int(keep.sum()), "of", n_rx, "receivers")
     fc = float(sc["freqs"][len(sc["freqs"]) // 2])
     fi = len(sc["freqs"]) // 2
     n_bins = 2048
     pdp, st = sbr.pdp_angles(r["paths"], r["g"], fi, fc, 1e-9, n_bins)
-    pdp, st = pdp.cpu().numpy(), st.cpu().numpy()
-    opdp, ost = oracle.pdp_stats(orc["paths"], orc["g"], fi, fc, 1e-9, n_bins, len(sc["rx"]))
+    pdp, st = pdp.cpu().numpy()[keep], st.cpu().numpy()[keep]
+    opdp, ost = oracle.pdp_stats(orc["paths"], orc["g"], fi, fc, 1e-9, n_bins, n_rx)
+    opdp, ost = opdp[keep], ost[keep]
+    assert np.isfinite(ost[:, 1]).sum() >= 1
     empty = np.isneginf(opdp)
     assert np.array_equal(empty, np.isneginf(pdp))
     assert np.abs(pdp[~empty] - opdp[~empty]).max(initial=0) < 0.01
@@ -287,25 +295,92 @@ def test_near_edge_hits_are_counted(sbr, N):
     assert sbr.trace(bvh, d["tx"], d["rx"], N, 1).stats()["near_edge_hits"] == 0
 
 
-@pytest.mark.parametrize("form,tol", [(2, 5e-5), (3, 1e-5)])
+def _oracle_H_of(sc, ex, tx_elem=None, rx_elem=None, freqs=None, fsel=None):
+    """The oracle's direct FP64 sum of Eq. 13-14 over the GPU's own path list,
+    with the oracle's own gains (so the comparison isolates the synthesis)."""
+    paths = dict(rx=ex["rx"], nb=ex["nb"], seq=ex["seq"], pts=ex["pts"], L=ex["L"])
+    f = sc["freqs"] if fsel is None else sc["freqs"][fsel]
+    kw = {} if fsel is None else dict(freqs=f, gamma=sc["gamma_db_km"][fsel], disp=sc["disp_deg_km"][fsel])
+    g_ref = oracle.gains(sc, paths, **kw)
+    return oracle.synth_H(paths, g_ref, f, sc["tx"], sc["rx"][0],
+                          sc["tx_elem"] if tx_elem is None else tx_elem,
+                          sc["rx_elem"] if rx_elem is None else rx_elem)
+
+
+def _h_errors(H, Ho):
+    """Per-output error against the oracle: max |dH| / max |H|, and the median
+    of |dH| / |H| over the outputs with |H| > 1e-3 max |H|."""
+    a = np.abs(Ho)
+    big = a > 1e-3 * a.max()
+    return float(np.abs(H - Ho).max() / a.max()), float(np.median(np.abs(H - Ho)[big] / a[big]))
+
+
+# Error budget of the split-precision forms, per product of two operands x, y:
+# x = hi + lo with |x - hi| <= 2^-(s+1) |x| and lo itself rounded to s bits,
+# so hi*hi + hi*lo + lo*hi leaves ~3 * 2^-(2s+1) |x y| (BF16: s = 8 -> 1.1e-5;
+# FP16: s = 11 -> 1.8e-7); the on-chip phase adds the FP32 rounding of f*delay
+# (a few 1e-7 of a cycle for delays of a few cm at 100 GHz). Summed over the
+# paths, the maximum error stays within a few of those units of max |H| and
+# the median within one.
+TC_TOL = {2: (5e-5, 2e-5), 3: (1e-5, 5e-6)}   # form: (max |dH|/max|H|, median rel.)
+
+
+@pytest.mark.parametrize("form", [2, 3])
 @pytest.mark.parametrize("ny,nz,nr,F", [(16, 16, 64, 16), (10, 10, 10, 5), (20, 15, 70, 3)])
-def test_tensor_core_synthesis_matches_fp64_form(sbr, ny, nz, nr, F, form, tol):
-    # BF16 (form 2) or FP16 (form 3) hi/lo split on tcgen05 vs the FP64 CUDA-core
-    # form on the same path list; shapes cover one tile, ragged tiles (Nt=100,
-    # Nr=10) and two M and N tiles (Nr=70, Nt=300)
+def test_tensor_core_synthesis_matches_oracle(sbr, ny, nz, nr, F, form):
+    # BF16 (form 2) or FP16 (form 3) hi/lo split on tcgen05 against the FP64
+    # oracle's direct sum, element by element, on the GPU's path list; shapes
+    # cover one tile, ragged tiles (Nt=100, Nr=10) and two M and N tiles (Nr=70, Nt=300)
     sc = scenes.config3(N=60, K=3, F=F, ny_tx=ny, nz_tx=nz, n_rx=nr)
     r = sbr.run_scene(sc)
     d = r["dev"]
     assert r["paths"].n > 20
-    H64 = sbr.synthesize_H(r["paths"], r["g"], d["freqs"], d["tx_elem"], d["rx_elem"], 0, 0)
-    Htc = sbr.synthesize_H(r["paths"], r["g"], d["freqs"], d["tx_elem"], d["rx_elem"], 0, form)
-    H64, Htc = H64.cpu().numpy(), Htc.cpu().numpy()
-    err = np.abs(Htc - H64).max() / np.abs(H64).max()
-    print("tcgen05 form", form, "vs fp64: max|dH|/max|H| =", err)
-    assert err < tol
-    # per-frequency relative error stays small too (no frequency is dropped)
-    per_f = np.abs(Htc - H64).reshape(F, -1).max(1) / np.abs(H64).reshape(F, -1).max(1)
+    ex = to_numpy(r["export"])
+    Ho = _oracle_H_of(sc, ex)
+    Htc = sbr.synthesize_H(r["paths"], r["g"], d["freqs"], d["tx_elem"], d["rx_elem"], 0, form).cpu().numpy()
+    assert Htc.shape == Ho.shape == (F, nr, ny * nz)
+    e_max, e_med = _h_errors(Htc, Ho)
+    print("tcgen05 form", form, (ny * nz, nr, F), "vs oracle: max|dH|/max|H| =", e_max, "median rel =", e_med)
+    tol_max, tol_med = TC_TOL[form]
+    assert e_max < tol_max
+    assert e_med < tol_med
+    # every frequency on its own (none dropped or shifted)
+    per_f = np.abs(Htc - Ho).reshape(F, -1).max(1) / np.abs(Ho).reshape(F, -1).max(1)
     assert per_f.max() < 1e-4
+    # the CUDA-core FP64 form agrees with the oracle too (the tests above compare
+    # the tensor-core forms against the oracle itself, not against it)
+    H64 = sbr.synthesize_H(r["paths"], r["g"], d["freqs"], d["tx_elem"], d["rx_elem"], 0, 0).cpu().numpy()
+    assert _h_errors(H64, Ho)[0] < 5e-6
+
+
+def test_synthesis_and_capacity_at_128x128_tx(sbr):
+    # the largest Tx array of the capacity trend (128 x 128 UPA, Nt = 16384) on
+    # four subcarriers: every form against the oracle on sampled transmit
+    # elements (all receive elements and frequencies), and the capacity of the
+    # FP16x3 H against the oracle's log-det of that same H
+    sc = scenes.config3(N=60, K=3, F=4)
+    lam = 299792458.0 / 100e9
+    te = scenes.upa_yz(sc["tx"], 128, 128, lam / 2)
+    sc = dict(sc, tx_elem=te)
+    r = sbr.run_scene(sc)
+    ex = to_numpy(r["export"])
+    d = r["dev"]
+    rng = np.random.default_rng(128)
+    pi = np.unique(np.concatenate([[0, 127, 16383 - 127, 16383], rng.choice(16384, 60, replace=False)]))
+    Ho = _oracle_H_of(sc, ex, tx_elem=te[pi])
+    te_d = torch.as_tensor(te, dtype=torch.float64, device="cuda")
+    for form, (tol_max, tol_med) in ((0, (5e-6, 1e-6)), (1, (2e-5, 1e-5)), (2, TC_TOL[2]), (3, TC_TOL[3])):
+        H = sbr.synthesize_H(r["paths"], r["g"], d["freqs"], te_d, d["rx_elem"], 0, form)
+        assert tuple(H.shape) == (4, 64, 16384)
+        e_max, e_med = _h_errors(H.cpu().numpy()[:, :, pi], Ho)
+        print("128x128 Tx, form", form, "max", e_max, "median", e_med)
+        assert e_max < tol_max and e_med < tol_med, (form, e_max, e_med)
+        if form == 3:
+            snr = np.arange(0.0, 31.0, 5.0)
+            C = sbr.capacity(H, snr).cpu().numpy()
+            Co = oracle.capacity(H.cpu().numpy().astype(np.complex128), snr)
+            assert np.abs(C - Co).max() < 1e-5 * np.abs(Co).max(), (C, Co)
+            assert np.all(np.diff(C) > 0)
 
 
 @pytest.mark.parametrize("form", [2, 3])
