@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "synth_ops.cuh"
 #include "dfloat.cuh"
 #include "gains.cuh"
 #include "refine.cuh"
@@ -164,6 +165,10 @@ __global__ void __launch_bounds__(kBThreads) k_batch_paths(const __grid_constant
     if (tid == 0) a.np[jl] = P;
 }
 
+// row length of a job's synthesis operands (weights, transposed delays): the
+// path capacity rounded up to the 8-path K-steps the tensor-core form reads
+inline int32_t synth_stride(int32_t path_cap) { return (path_cap + 7) & ~7; }
+
 struct BatchGainArgs {
     const BatchJobDev* jobs;
     const int32_t* tile_job;     // wave-local job of each tile
@@ -172,16 +177,25 @@ struct BatchGainArgs {
     BatchPathsDev paths;
     float2* g;
     float2* w;
-    int32_t path_cap;
+    float2* wl;
+    float* sc;
+    int32_t path_cap;            // row length of w: synth_stride(the path capacity)
 };
 
-// the gain of sbr_path_gains and the weight of the synthesis prologue, per
-// (path, frequency) of a (job, 32-frequency) tile
+// the gain of sbr_path_gains and the synthesis weights (synth_ops.cuh, the
+// arithmetic of the single-receiver form), per (path, frequency) of a (job,
+// 32-frequency) tile: reflected-path weights w (padded slots up to the next
+// multiple of 8 zeroed), the LoS weight wl and the FP16 scale sc per frequency
 __global__ void __launch_bounds__(kBThreads) k_batch_gains(const __grid_constant__ BatchGainArgs a) {
+    __shared__ unsigned s_max[kGainTileF];
     const int jl = a.tile_job[blockIdx.x], f0 = a.tile_f0[blockIdx.x];
     const BatchJobDev* J = a.jobs + jl;
     const int P = a.np[jl], F = J->F;
     const int nf = min(kGainTileF, F - f0);
+    const int n0 = (P > 0 && a.paths.nb[J->path_base] == 0) ? 1 : 0;   // the LoS path sorts first
+    const int nrefl = P - n0, npad = (nrefl + 7) & ~7;
+    if (threadIdx.x < kGainTileF) s_max[threadIdx.x] = 0u;
+    __syncthreads();
     for (int it = threadIdx.x; it < P * nf; it += kBThreads) {
         const int p = it / nf, f = f0 + (it - p * nf);
         const int64_t slot = J->path_base + p;
@@ -191,46 +205,64 @@ __global__ void __launch_bounds__(kBThreads) k_batch_gains(const __grid_constant
                               J->mats, J->S, fr, J->gamma ? J->gamma + f : nullptr,
                               J->disp ? J->disp + f : nullptr, J->pol);
         a.g[J->g_base + (int64_t)p * F + f] = gg;
-        double cyc = fr * L / kC0;
-        double frc = cyc - floor(cyc);
-        double s, c;
-        sincospi(-2.0 * frc, &s, &c);
-        double wr = gg.x * c - gg.y * s, wi = gg.x * s + gg.y * c;
-        a.w[J->w_base + (int64_t)f * a.path_cap + p] = make_float2((float)wr, (float)wi);
+        const float2 ww = synth_weight(gg, fr, L);
+        if (p < n0) {
+            a.wl[J->wl_base + f] = ww;
+        } else {
+            a.w[J->w_base + (int64_t)f * a.path_cap + (p - n0)] = ww;
+            atomicMax(&s_max[f - f0], __float_as_uint(fmaxf(fabsf(ww.x), fabsf(ww.y))));
+        }
+    }
+    for (int it = threadIdx.x; it < (npad - nrefl) * nf; it += kBThreads) {
+        const int n = nrefl + it / nf, f = f0 + it % nf;
+        a.w[J->w_base + (int64_t)f * a.path_cap + n] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nf) {
+        const int f = f0 + threadIdx.x;
+        a.sc[J->wl_base + f] = synth_scale(__uint_as_float(s_max[threadIdx.x]));
+        if (n0 == 0) a.wl[J->wl_base + f] = make_float2(0.f, 0.f);
     }
 }
 
-// element delays of the synthesis (Eq. 13-14 near field), FP64 then FP32:
-//   dt = |T_p - P1| - |T_0 - P1|, dr = |R_q - Pm| - |R_0 - Pm|, 0 for LoS;
-//   dlos = |T_p - R_q| - |T_0 - R_0|
+// element delays of the synthesis (Eq. 13-14 near field; synth_ops.cuh), FP64
+// then FP32, transposed per element over the reflected paths (padded slots up
+// to the next multiple of 8 zeroed):
+//   dt[p][n] = |T_p - P1| - |T_0 - P1|, dr[q][n] = |R_q - Pm| - |R_0 - Pm|;
+//   dl[q][p] = |T_p - R_q| - |T_0 - R_0|
 __global__ void __launch_bounds__(kBThreads) k_batch_delays(const BatchJobDev* __restrict__ jobs,
                                                             const int32_t* __restrict__ np, BatchPathsDev paths,
-                                                            float* __restrict__ dt, float* __restrict__ dr,
-                                                            float* __restrict__ dl) {
+                                                            int32_t path_cap, float* __restrict__ dt,
+                                                            float* __restrict__ dr, float* __restrict__ dl) {
     const BatchJobDev* J = jobs + blockIdx.x;
     const int P = np[blockIdx.x], Nt = J->Nt, Nr = J->Nr;
     const d3 T0 = mk3(J->tx[0], J->tx[1], J->tx[2]), R0 = mk3(J->rx[0], J->rx[1], J->rx[2]);
+    const int n0 = (P > 0 && paths.nb[J->path_base] == 0) ? 1 : 0;
+    const int nrefl = P - n0, npad = (nrefl + 7) & ~7;
     const int ne = Nt + Nr;
-    for (int it = threadIdx.x; it < P * ne; it += kBThreads) {
-        const int n = it / ne, e = it - n * ne;
-        const int64_t slot = J->path_base + n;
-        const int m = paths.nb[slot];
-        double v = 0.0;
-        if (m > 0) {
-            if (e < Nt) {
-                d3 P1 = ld3(paths.pts + (slot * kKmax) * 3);
-                v = norm(ld3(J->tx_elem + 3 * e) - P1) - norm(T0 - P1);
-            } else {
-                d3 Pm = ld3(paths.pts + (slot * kKmax + m - 1) * 3);
-                v = norm(ld3(J->rx_elem + 3 * (e - Nt)) - Pm) - norm(R0 - Pm);
-            }
+    // one thread per (path, element side, run of up to 8 elements)
+    const int gt = (Nt + 7) / 8, gr = (Nr + 7) / 8;
+    for (int it = threadIdx.x; it < npad * (gt + gr); it += kBThreads) {
+        const int n = it % npad, g = it / npad;
+        const bool tx = g < gt;
+        const int e0 = (tx ? g : g - gt) * 8, e1 = min(tx ? Nt : Nr, e0 + 8);
+        float* dst = tx ? dt + J->dt_base : dr + J->dr_base;
+        if (n < nrefl) {
+            const int64_t slot = J->path_base + n + n0;
+            const int m = paths.nb[slot];
+            const d3 Pk = ld3(paths.pts + (slot * kKmax + (tx ? 0 : m - 1)) * 3);
+            const double ref = norm((tx ? T0 : R0) - Pk);
+            const double* el = tx ? J->tx_elem : J->rx_elem;
+            for (int e = e0; e < e1; ++e) dst[(int64_t)e * path_cap + n] = el_delay(el + 3 * e, Pk, ref);
+        } else {
+            for (int e = e0; e < e1; ++e) dst[(int64_t)e * path_cap + n] = 0.f;
         }
-        if (e < Nt) dt[J->dt_base + (int64_t)n * Nt + e] = (float)v;
-        else dr[J->dr_base + (int64_t)n * Nr + (e - Nt)] = (float)v;
     }
+    (void)ne;
+    const double ref = norm(T0 - R0);
     for (int it = threadIdx.x; it < Nr * Nt; it += kBThreads) {
         const int q = it / Nt, p = it - q * Nt;
-        dl[J->dl_base + it] = (float)(norm(ld3(J->tx_elem + 3 * p) - ld3(J->rx_elem + 3 * q)) - norm(T0 - R0));
+        dl[J->dl_base + it] = el_delay(J->tx_elem + 3 * p, ld3(J->rx_elem + 3 * q), ref);
     }
 }
 
@@ -340,6 +372,8 @@ struct sbr_batch {
     float* dr = nullptr;
     float* dl = nullptr;
     float2* w = nullptr;
+    float2* wl = nullptr;
+    float* sc = nullptr;
     // graph
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -440,10 +474,13 @@ sbr_status enqueue(sbr_batch* b, cudaStream_t s) {
         ga.paths = b->fin;
         ga.g = b->g;
         ga.w = b->w;
-        ga.path_cap = c.path_cap;
+        ga.wl = b->wl;
+        ga.sc = b->sc;
+        ga.path_cap = synth_stride(c.path_cap);
         ::sbr::note_launch(), k_batch_gains<<<wv.n_tiles, kBThreads, 0, s>>>(ga);
         SBR_TRY_CUDA(cudaGetLastError());
-        ::sbr::note_launch(), k_batch_delays<<<nj, kBThreads, 0, s>>>(jobs, b->np + wv.j0, b->fin, b->dt, b->dr, b->dl);
+        ::sbr::note_launch(), k_batch_delays<<<nj, kBThreads, 0, s>>>(jobs, b->np + wv.j0, b->fin, synth_stride(c.path_cap), b->dt, b->dr,
+                                                                       b->dl);
         SBR_TRY_CUDA(cudaGetLastError());
         BatchSynthWave sw{};
         sw.jobs = jobs;
@@ -452,11 +489,13 @@ sbr_status enqueue(sbr_batch* b, cudaStream_t s) {
         sw.items = wv.items;
         sw.np = b->np + wv.j0;
         sw.nb = b->fin.nb;
-        sw.path_cap = c.path_cap;
+        sw.path_cap = synth_stride(c.path_cap);
         sw.dt = b->dt;
         sw.dr = b->dr;
         sw.dl = b->dl;
         sw.w = b->w;
+        sw.wl = b->wl;
+        sw.sc = b->sc;
         sw.status = &wv.cnt->status;
         SBR_TRY(batch_synth_tc(sw, f16, c.tile_n, s));
         ::sbr::note_launch(), k_batch_status<<<nblk(nj), 256, 0, s>>>(wv.cnt, nj, b->status + wv.j0);
@@ -572,11 +611,11 @@ sbr_status create(const sbr_bvh* const* scenes, const sbr_material* const* mats,
 
     // job records, wave tables
     std::vector<BatchJobDev> hj(n_jobs);
-    int64_t max_dt = 0, max_dr = 0, max_dl = 0, max_w = 0;
+    int64_t max_dt = 0, max_dr = 0, max_dl = 0, max_w = 0, max_wl = 0;
     for (Wave& wv : b->waves) {
         std::vector<int64_t> ray_off, item_off;
         std::vector<int32_t> tile_job, tile_f0;
-        int64_t r0 = 0, it0 = 0, sq = 0, odt = 0, odr = 0, odl = 0, ow = 0;
+        int64_t r0 = 0, it0 = 0, sq = 0, odt = 0, odr = 0, odl = 0, ow = 0, owl = 0;
         for (int i = wv.j0; i < wv.j1; ++i) {
             const sbr_batch_job& jb = jobs[i];
             const sbr_bvh* sc = scenes[jb.scene];
@@ -629,11 +668,13 @@ sbr_status create(const sbr_bvh* const* scenes, const sbr_material* const* mats,
             J.path_base = (int64_t)i * c.path_cap;
             J.g_base = b->g_base[i];
             J.w_base = ow;
-            ow += (int64_t)jb.F * c.path_cap;
+            ow += (int64_t)jb.F * synth_stride(c.path_cap);
+            J.wl_base = owl;
+            owl += jb.F;
             J.dt_base = odt;
-            odt += (int64_t)c.path_cap * jb.Nt;
+            odt += (int64_t)synth_stride(c.path_cap) * jb.Nt;
             J.dr_base = odr;
-            odr += (int64_t)c.path_cap * jb.Nr;
+            odr += (int64_t)synth_stride(c.path_cap) * jb.Nr;
             J.dl_base = odl;
             odl += (int64_t)jb.Nr * jb.Nt;
             ray_off.push_back(r0);
@@ -652,6 +693,7 @@ sbr_status create(const sbr_bvh* const* scenes, const sbr_material* const* mats,
         wv.dt_words = odt; wv.dr_words = odr; wv.dl_words = odl; wv.w_words = ow;
         max_dt = std::max(max_dt, odt); max_dr = std::max(max_dr, odr);
         max_dl = std::max(max_dl, odl); max_w = std::max(max_w, ow);
+        max_wl = std::max(max_wl, owl);
         if ((st = balloc(b, &wv.d_ray_off, ray_off.size())) != SBR_OK) return fail(st);
         if ((st = balloc(b, &wv.d_item_off, item_off.size())) != SBR_OK) return fail(st);
         if ((st = balloc(b, &wv.d_tile_job, tile_job.size())) != SBR_OK) return fail(st);
@@ -671,6 +713,8 @@ sbr_status create(const sbr_bvh* const* scenes, const sbr_material* const* mats,
     if ((st = balloc(b, &b->dr, (size_t)max_dr)) != SBR_OK) return fail(st);
     if ((st = balloc(b, &b->dl, (size_t)max_dl)) != SBR_OK) return fail(st);
     if ((st = balloc(b, &b->w, (size_t)max_w)) != SBR_OK) return fail(st);
+    if ((st = balloc(b, &b->wl, (size_t)std::max<int64_t>(1, max_wl))) != SBR_OK) return fail(st);
+    if ((st = balloc(b, &b->sc, (size_t)std::max<int64_t>(1, max_wl))) != SBR_OK) return fail(st);
     if ((st = balloc(b, &b->d_jobs, (size_t)n_jobs)) != SBR_OK) return fail(st);
     if (cudaMemcpy(b->d_jobs, hj.data(), sizeof(BatchJobDev) * n_jobs, cudaMemcpyHostToDevice) != cudaSuccess) {
         set_error("job table upload failed");

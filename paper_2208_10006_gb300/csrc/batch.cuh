@@ -43,8 +43,10 @@ struct BatchJobDev {
     // per-job storage in the batch (capacity path_cap paths)
     int64_t path_base;           // first path slot of the job
     int64_t g_base;              // first gain, path-major [path_cap][F]
-    int64_t w_base;              // first synthesis weight, frequency-major [F][path_cap] (wave scratch)
-    int64_t dt_base, dr_base, dl_base;   // element delays (wave scratch)
+    // synthesis operands (wave scratch), rows of ps = the path capacity rounded up to 8
+    int64_t w_base;              // first reflected-path weight, frequency-major [F][ps]
+    int64_t wl_base;             // first LoS weight and FP16 scale, [F] each
+    int64_t dt_base, dr_base, dl_base;   // element delays, [Nt][ps], [Nr][ps], [Nr][Nt]
 };
 
 // Path records of the batch, SoA over path slots (job j owns slots
@@ -96,11 +98,13 @@ struct BatchSynthWave {
     int64_t items;
     const int32_t* np;           // [n_jobs] paths per job
     const int32_t* nb;           // reflections per path slot (batch path store)
-    int32_t path_cap;
+    int32_t path_cap;            // row length of w, dt, dr: the path capacity rounded up to 8
     const float* dt;
     const float* dr;
     const float* dl;
     const float2* w;
+    const float2* wl;
+    const float* sc;
     unsigned int* status;
 };
 // tiles of one job for a tile width (64 receive elements x tile_n transmit elements per frequency)

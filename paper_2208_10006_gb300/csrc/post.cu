@@ -152,23 +152,39 @@ k_capacity(const float2* __restrict__ H, int32_t Nr, int32_t Nt, const double* _
     const int f = blockIdx.x;
     const float2* h = H + (int64_t)f * Nr * Nt;
     // W[a][b] = sum_p H[a][p] conj(H[b][p])  (Nt >= Nr)  or  sum_q conj(H[q][a]) H[q][b]
+    // Blocked summation: FP32 partial sums over runs of kCapRun terms, added
+    // into FP64 totals, so the rounding error of an entry grows with the run
+    // length rather than with the array size (16,384 terms at a 128 x 128 UPA)
+    constexpr int kCapRun = 32;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         int a = e / n, b = e - a * n;
-        float re = 0.f, im = 0.f;
+        double sre = 0.0, sim = 0.0;
         if (Nt >= Nr) {
-            for (int p = 0; p < Nt; ++p) {
-                float2 x = h[(int64_t)a * Nt + p], y = h[(int64_t)b * Nt + p];
-                re += x.x * y.x + x.y * y.y;
-                im += x.y * y.x - x.x * y.y;
+            for (int p0 = 0; p0 < Nt; p0 += kCapRun) {
+                const int p1 = min(Nt, p0 + kCapRun);
+                float re = 0.f, im = 0.f;
+                for (int p = p0; p < p1; ++p) {
+                    float2 x = h[(int64_t)a * Nt + p], y = h[(int64_t)b * Nt + p];
+                    re += x.x * y.x + x.y * y.y;
+                    im += x.y * y.x - x.x * y.y;
+                }
+                sre += re;
+                sim += im;
             }
         } else {
-            for (int q = 0; q < Nr; ++q) {
-                float2 x = h[(int64_t)q * Nt + a], y = h[(int64_t)q * Nt + b];
-                re += x.x * y.x + x.y * y.y;
-                im += x.x * y.y - x.y * y.x;
+            for (int q0 = 0; q0 < Nr; q0 += kCapRun) {
+                const int q1 = min(Nr, q0 + kCapRun);
+                float re = 0.f, im = 0.f;
+                for (int q = q0; q < q1; ++q) {
+                    float2 x = h[(int64_t)q * Nt + a], y = h[(int64_t)q * Nt + b];
+                    re += x.x * y.x + x.y * y.y;
+                    im += x.x * y.y - x.y * y.x;
+                }
+                sre += re;
+                sim += im;
             }
         }
-        W[e] = make_float2(re, im);
+        W[e] = make_float2((float)sre, (float)sim);
     }
     __syncthreads();
     const double scale = (double)Nr * Nt / *qbar;

@@ -1,0 +1,55 @@
+// Operands of the tensor-core H(f) synthesis (Eq. 13-14), shared by the
+// single-receiver and the batched forms so that both compute them with the
+// same arithmetic (and therefore give bit-identical H for the same paths).
+//
+// Layout, for the Pr reflected paths of one receiver padded to Pp (a multiple
+// of 4; padded entries are zero):
+//   w   [F][Pp]  float2  g_n(f) exp(-j 2 pi f L_n / c), reflected paths only
+//   wl  [F]      float2  the same for the LoS path (zero when there is none)
+//   sc  [F]      float   FP16 form: the power of two that brings
+//                        max_n max(|Re w|, |Im w|) into [1/2, 1) (1 if all zero)
+//   dtT [Nt][Pp] float   |T_p - P1| - |T_0 - P1|   (P1 first interaction point)
+//   drT [Nr][Pp] float   |R_q - Pm| - |R_0 - Pm|   (Pm last interaction point)
+//   dl  [Nr][Nt] float   |T_p - R_q| - |T_0 - R_0|
+#pragma once
+#include "sbr_internal.cuh"
+
+namespace sbr {
+
+constexpr double kInvC0 = 1.0 / kC0;
+
+// g exp(-j 2 pi f L / c). The phase f L / c (up to ~1e6 cycles at THz) is
+// reduced exactly in FP64 to its fraction r in [0, 1); r = hi + lo with hi the
+// FP32 rounding of r and |lo| <= 2^-25; exp(-j 2 pi r) = exp(-j 2 pi hi)
+// (1 - j 2 pi lo) to second order in lo (< 1e-13), with the FP32 sine and
+// cosine of pi x (sincospif) for the hi part. FP64 is used for 7 operations
+// only: this GPU's FP64 rate is a small fraction of its FP32 rate.
+__device__ __forceinline__ float2 synth_weight(float2 g, double f, double L) {
+    const double cyc = f * L * kInvC0;
+    const double r = cyc - floor(cyc);
+    const float hi = (float)r;
+    const float lo = (float)(r - (double)hi);
+    float s, c;
+    sincospif(-2.0f * hi, &s, &c);
+    const float d = -6.283185307179586f * lo;   // exp(j d) ~ 1 + j d
+    const float cr = fmaf(-s, d, c), ci = fmaf(c, d, s);
+    return make_float2(g.x * cr - g.y * ci, g.x * ci + g.y * cr);
+}
+
+// the FP16 form's per-frequency scale from the largest weight component
+__device__ __forceinline__ float synth_scale(float m) {
+    if (!(m > 0.f)) return 1.f;
+    int e;
+    frexpf(m, &e);
+    return ldexpf(1.f, -e);
+}
+
+// element delay |E - P| - ref with ref = |E0 - P| computed once per path
+// (FP64, then rounded to FP32)
+__device__ __forceinline__ float el_delay(const double* elem, d3 P, double ref) {
+    return (float)(norm(ld3(elem) - P) - ref);
+}
+
+inline int64_t synth_pad4(int64_t n) { return (n + 3) & ~(int64_t)3; }
+
+}  // namespace sbr

@@ -32,24 +32,31 @@
 #include "tcgen05.cuh"
 #include "sbr_internal.cuh"
 #include "synth_common.cuh"
+#include "synth_ops.cuh"
 
 namespace sbr {
 namespace {
 
 using namespace tc;
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;  // 16 warps, one CTA per SM
+constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kChunkP = 32;      // paths per K-chunk (K = 64 16-bit values = one 128-byte row)
 constexpr int kABytes = kTileM * 128;  // 16 KB: 2 x 64 receive elements
+constexpr int kStageOut = 2048;  // per warp: 16 receive elements x 16 transmit elements, complex64
 
-// tile of N transmit elements (N = 64, 128 or 256): shared-memory and TMEM sizes
+// tile of N transmit elements (N = 64, 128 or 256): shared-memory and TMEM sizes.
+// Two operand stages (hi/lo of A' and B' each) and two FP32 accumulators, so
+// that the phasors of one K-chunk are generated while the tensor core works on
+// the previous one and a tile's epilogue runs while the next tile's MMAs do.
 template <int kTileN>
 struct TcShape {
     static_assert(kTileN == 64 || kTileN == 128 || kTileN == 256, "tile N");
     static constexpr int kBBytes = kTileN * 128;
-    static constexpr int kSmemTiles = 2 * kABytes + 2 * kBBytes;  // hi/lo of A and B
-    static constexpr int kSmemBytes = kSmemTiles + 1024 + 64;      // + alignment slack + barriers
-    static constexpr int kTmemCols = kTileN;                       // FP32 accumulator columns
+    static constexpr int kStage = 2 * kABytes + 2 * kBBytes;        // hi/lo of A and B
+    static constexpr int kOut = kTcWarps * kStageOut;               // epilogue staging
+    static constexpr int kSmemBytes = 2 * kStage + kOut + 1024 + 128;  // + alignment + barriers
+    static constexpr int kTmemCols = 2 * kTileN;                    // two accumulators
 };
 
 // exp(-j 2 pi c) for a phase of c cycles: reduce to [-1/2, 1/2] exactly, then
@@ -60,31 +67,22 @@ __device__ __forceinline__ void phasor(float cycles, float& s, float& c) {
     __sincosf(-6.283185307179586f * r, &s, &c);
 }
 
-// x = hi + lo, both BF16 or both FP16; returns the two as raw 16-bit patterns
-template <bool kF16>
-__device__ __forceinline__ void split16(float x, uint16_t& hi, uint16_t& lo) {
-    if (kF16) {
-        __half h = __float2half_rn(x);
-        __half l = __float2half_rn(x - __half2float(h));
-        hi = __half_as_ushort(h);
-        lo = __half_as_ushort(l);
-    } else {
-        __nv_bfloat16 h = __float2bfloat16_rn(x);
-        __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-        hi = __bfloat16_as_ushort(h);
-        lo = __bfloat16_as_ushort(l);
-    }
-}
-
+// Operands of the tensor-core forms (layouts in synth_ops.cuh): reflected
+// paths only, transposed and padded to Pp (a multiple of 8) paths per row, so
+// that four paths of one element are one 16-byte load; the LoS weight and the
+// FP16 scale per frequency come separately.
 struct TcArgs {
     // single receiver of one path list
     int32_t F, Nr, Nt;
-    int32_t Pr;                // paths of the receiver (stride of w rows)
-    const int32_t* nb0;        // reflections of the first path: 0 = LoS at local index 0
+    int32_t Pr;                // paths of the receiver (LoS included)
+    int32_t Pp;                // padded row length of dtT, drT and w
+    const int32_t* nb0;        // reflections of the first path: 0 = it is the LoS path
     const double* freqs;
-    const float* dt;           // [Pr][Nt]
-    const float* dr;           // [Pr][Nr]
-    const float2* w;           // [F][Pr]
+    const float* dtT;          // [Nt][Pp]
+    const float* drT;          // [Nr][Pp]
+    const float2* w;           // [F][Pp]
+    const float2* wl;          // [F]
+    const float* sc;           // [F]
     const float* dlos;         // [Nr][Nt]
     float2* H;
     unsigned int* status;
@@ -96,23 +94,26 @@ struct TcArgs {
     int64_t items;
     const int32_t* np;         // [n_jobs] paths of each job
     const int32_t* nb;         // reflections per path slot (batch path store)
-    int32_t path_cap;          // stride of a job's w rows
+    int32_t path_cap;          // padded row length of a job's operands
     const float* dt_all;
     const float* dr_all;
     const float* dl_all;
     const float2* w_all;
+    const float2* wl_all;
+    const float* sc_all;
 };
 
 // one output tile: frequency f, receive elements [q0, q0 + 64), transmit
-// elements [p0, p0 + N); reflected paths are the local indices
-// [n0, n0 + nrefl); the LoS path, when present, is local index 0 and is added
-// exactly in the epilogue
+// elements [p0, p0 + N); the reflected paths [0, nrefl) go through the tensor
+// cores, the LoS path (if any) is added exactly in the epilogue
 struct TcItem {
-    int f, q0, p0, Nr, Nt, los, n0, nrefl;
-    float foc;
-    const float* dt;
-    const float* dr;
-    const float2* wf;          // weights of frequency f
+    int f, q0, p0, Nr, Nt, nrefl, Pp;
+    bool los;
+    float foc, sc;
+    float2 wl;
+    const float* dtT;
+    const float* drT;
+    const float2* wf;          // reflected-path weights of frequency f
     const float* dlos;
     float2* Hf;                // H of frequency f
 };
@@ -120,12 +121,13 @@ struct TcItem {
 template <bool kBatch, int kTileN>
 __device__ __forceinline__ TcItem tc_item(const TcArgs& a, int64_t it) {
     TcItem x;
-    int F, Pr;
+    int Pr;
     const int32_t* nb0;
     const double* freqs;
     const float2* w;
+    const float2* wl;
+    const float* sc;
     float2* H;
-    int64_t wstride;
     if (kBatch) {
         int lo = 0, hi = a.n_jobs - 1;   // the last job whose first item is <= it
         while (lo < hi) {
@@ -134,54 +136,252 @@ __device__ __forceinline__ TcItem tc_item(const TcArgs& a, int64_t it) {
         }
         const BatchJobDev* J = a.jobs + lo;
         it -= __ldg(a.item_off + lo);
-        F = J->F; x.Nr = J->Nr; x.Nt = J->Nt;
+        x.Nr = J->Nr; x.Nt = J->Nt;
         Pr = __ldg(a.np + lo);
         nb0 = a.nb + J->path_base;
         freqs = J->freqs;
-        x.dt = a.dt_all + J->dt_base;
-        x.dr = a.dr_all + J->dr_base;
+        x.dtT = a.dt_all + J->dt_base;
+        x.drT = a.dr_all + J->dr_base;
         x.dlos = a.dl_all + J->dl_base;
         w = a.w_all + J->w_base;
-        wstride = a.path_cap;
+        wl = a.wl_all + J->wl_base;
+        sc = a.sc_all + J->wl_base;
+        x.Pp = a.path_cap;
         H = J->H;
     } else {
-        F = a.F; x.Nr = a.Nr; x.Nt = a.Nt;
+        x.Nr = a.Nr; x.Nt = a.Nt;
         Pr = a.Pr;
         nb0 = a.nb0;
         freqs = a.freqs;
-        x.dt = a.dt; x.dr = a.dr; x.dlos = a.dlos;
+        x.dtT = a.dtT; x.drT = a.drT; x.dlos = a.dlos;
         w = a.w;
-        wstride = a.Pr;
+        wl = a.wl;
+        sc = a.sc;
+        x.Pp = a.Pp;
         H = a.H;
     }
-    (void)F;
     const int mtiles = (x.Nr + 63) / 64, ntiles = (x.Nt + kTileN - 1) / kTileN;
     x.f = (int)(it / (mtiles * ntiles));
     const int rem = (int)(it - (int64_t)x.f * mtiles * ntiles);
     x.q0 = (rem / ntiles) * 64;
     x.p0 = (rem % ntiles) * kTileN;
-    x.los = (Pr > 0 && *nb0 == 0) ? 0 : -1;
-    x.n0 = x.los == 0 ? 1 : 0;
-    x.nrefl = Pr - x.n0;
+    x.los = Pr > 0 && *nb0 == 0;
+    x.nrefl = Pr - (x.los ? 1 : 0);
     x.foc = (float)(freqs[x.f] / kC0);
-    x.wf = w + (int64_t)x.f * wstride;
+    x.wf = w + (int64_t)x.f * x.Pp;
+    x.wl = wl[x.f];
+    x.sc = sc[x.f];
     x.Hf = H + (int64_t)x.f * x.Nr * x.Nt;
     return x;
 }
 
+// x = hi + lo for a pair of values, both BF16 or both FP16: the hi and lo
+// halves of two K positions packed as two 32-bit words (lower K index in the
+// low 16 bits)
+template <bool kF16>
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+    if (kF16) {
+        __half2 h = __floats2half2_rn(x0, x1);
+        float2 hf = __half22float2(h);
+        __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+        hi = *reinterpret_cast<uint32_t*>(&h);
+        lo = *reinterpret_cast<uint32_t*>(&l);
+    } else {
+        __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+        float2 hf = __bfloat1622float2(h);
+        __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+        hi = *reinterpret_cast<uint32_t*>(&h);
+        lo = *reinterpret_cast<uint32_t*>(&l);
+    }
+}
+
+// byte offset of the 16-byte chunk c (8 K values) of row r in a 128-byte
+// swizzled K-major tile (the layout the matrix descriptors describe)
+__device__ __forceinline__ uint32_t chunk_off(int r, int c) {
+    return (uint32_t)r * 128u + ((uint32_t)(c ^ (r & 7)) << 4);
+}
+
+// shared-memory store without a compiler memory barrier: global loads of later
+// work may be hoisted above it (the stores stay ordered among the volatile
+// statements, and the tensor core reads them only after a proxy fence and a
+// barrier)
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d));
+}
+
+// what the epilogue of a tile needs once its MMAs have been issued
+struct TcEpi {
+    int q0, p0, Nr, Nt, acc;
+    bool los;
+    bool full;                 // whole tile inside H, even Nt, aligned rows: no per-output checks
+    bool mma;                  // the tile has reflected paths (an accumulator to read)
+    uint32_t acc_parity;       // phase of acc_full[acc] that completes this tile
+    float foc, isc;
+    float2 wl;                 // LoS weight (unscaled)
+    const float* dlos;
+    float2* Hf;
+};
+
+// staging of one warp's 16 x 16 block: receive element r owns a 128-byte row,
+// its 16 real parts in logical 16-byte chunks 0-3 and its 16 imaginary parts
+// in chunks 4-7; chunk c is stored at c ^ t(r), t(r) = (r & 3) | (r & 1) << 2,
+// which keeps the writes (8 rows' halves per quarter warp) and the reads (two
+// rows' halves per half warp) free of bank conflicts
+__device__ __forceinline__ uint32_t stage_off(int r, int c) {
+    return (uint32_t)r * 128u + ((uint32_t)((c ^ ((r & 3) | ((r & 1) << 2))) & 7) << 4);
+}
+
+// Epilogue of one tile: each warp reads 32 TMEM lanes (rows 2q / 2q+1 of 16
+// receive elements) x 16 columns at a time, stages the raw rows in shared
+// memory, and reads back (real, imaginary) pairs of two transmit elements per
+// lane; it scales back (FP16 form), adds the exact per-element LoS term and
+// writes H with row-contiguous 128-byte segments (eight lanes per row).
+template <int kTileN>
+__device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t tmem, unsigned char* stage_out, int warp,
+                                            int lane) {
+    const int lg = warp & 3, cg = warp >> 2;   // TMEM lane quarter, column group
+    const int part = lane & 1;                 // 0: real row, 1: imaginary row
+    const int rw = lane >> 1;                  // row written: receive element within the warp's 16
+    const uint32_t sbase = smem_u32(stage_out + warp * kStageOut);
+    constexpr int kCols = kTileN / 4;          // columns of one warp
+    const int c = lane & 7;                    // pair of transmit elements read back
+    if (e.full) {
+        // every output of the tile exists: per lane, receive elements
+        // r0 + 4 i (i = 0..3) of the warp's 16, transmit elements p, p + 1; the
+        // staging offsets of those rows differ by 512 bytes (t(r) depends on r & 3)
+        const int r0 = lane >> 3;
+        const uint32_t s_re = sbase + stage_off(r0, c >> 1) + 8u * (uint32_t)(c & 1);
+        const uint32_t s_im = sbase + stage_off(r0, 4 + (c >> 1)) + 8u * (uint32_t)(c & 1);
+        const int64_t row0 = (int64_t)(e.q0 + 16 * lg + r0) * e.Nt;
+        const int64_t rstep = 4 * (int64_t)e.Nt;
+        // LoS delays of column block j + 1 are requested while block j is processed
+        float2 dl_next[4];
+        if (e.los) {
+            const int64_t o0 = row0 + e.p0 + cg * kCols + 2 * c;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dl_next[i] = __ldg(reinterpret_cast<const float2*>(e.dlos + o0 + i * rstep));
+        }
+#pragma unroll 1
+        for (int j = 0; j < kCols / 16; ++j) {
+            const int col0 = cg * kCols + 16 * j;
+            const int64_t o0 = row0 + e.p0 + col0 + 2 * c;
+            float2 dl[4];
+            if (e.los) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) dl[i] = dl_next[i];
+                if (j + 1 < kCols / 16) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        dl_next[i] = __ldg(reinterpret_cast<const float2*>(e.dlos + o0 + 16 + i * rstep));
+                }
+            }
+            uint32_t v[16];
+            if (e.mma) {
+                tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(e.acc * kTileN + col0), v);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) v[k] = 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                sts128(sbase + stage_off(rw, 4 * part + k), v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float2 re, im;
+                asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(re.x), "=f"(re.y) : "r"(s_re + 512u * i));
+                asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(im.x), "=f"(im.y) : "r"(s_im + 512u * i));
+                float4 o = make_float4(re.x * e.isc, im.x * e.isc, re.y * e.isc, im.y * e.isc);
+                if (e.los) {
+                    float sn, cs;
+                    phasor(e.foc * dl[i].x, sn, cs);
+                    o.x = fmaf(e.wl.x, cs, fmaf(-e.wl.y, sn, o.x));
+                    o.y = fmaf(e.wl.x, sn, fmaf(e.wl.y, cs, o.y));
+                    phasor(e.foc * dl[i].y, sn, cs);
+                    o.z = fmaf(e.wl.x, cs, fmaf(-e.wl.y, sn, o.z));
+                    o.w = fmaf(e.wl.x, sn, fmaf(e.wl.y, cs, o.w));
+                }
+                *reinterpret_cast<float4*>(e.Hf + o0 + i * rstep) = o;
+            }
+            __syncwarp();
+        }
+        return;
+    }
+#pragma unroll 1
+    for (int j = 0; j < kCols / 16; ++j) {
+        const int col0 = cg * kCols + 16 * j;
+        const int p = e.p0 + col0 + 2 * c;
+        // LoS delays of the four (receive element, pair) outputs of this lane,
+        // requested before the tensor-memory load so that their latency overlaps it
+        float2 dl[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int q = e.q0 + 16 * lg + 4 * i + (lane >> 3);
+            dl[i] = make_float2(0.f, 0.f);
+            if (e.los && q < e.Nr && p < e.Nt) {
+                const float* src = e.dlos + (int64_t)q * e.Nt + p;
+                if (p + 1 < e.Nt && ((((uintptr_t)src) & 7) == 0)) dl[i] = __ldg(reinterpret_cast<const float2*>(src));
+                else dl[i] = make_float2(__ldg(src), p + 1 < e.Nt ? __ldg(src + 1) : 0.f);
+            }
+        }
+        uint32_t v[16];
+        if (e.mma) {
+            tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(e.acc * kTileN + col0), v);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] = 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            sts128(sbase + stage_off(rw, 4 * part + k), v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = 4 * i + (lane >> 3);
+            const int q = e.q0 + 16 * lg + r;
+            float2 re, im;
+            asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                         : "=f"(re.x), "=f"(re.y)
+                         : "r"(sbase + stage_off(r, c >> 1) + 8u * (uint32_t)(c & 1)));
+            asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                         : "=f"(im.x), "=f"(im.y)
+                         : "r"(sbase + stage_off(r, 4 + (c >> 1)) + 8u * (uint32_t)(c & 1)));
+            float4 o = make_float4(re.x * e.isc, im.x * e.isc, re.y * e.isc, im.y * e.isc);
+            if (e.los) {
+                float sn, cs;
+                phasor(e.foc * dl[i].x, sn, cs);
+                o.x = fmaf(e.wl.x, cs, fmaf(-e.wl.y, sn, o.x));
+                o.y = fmaf(e.wl.x, sn, fmaf(e.wl.y, cs, o.y));
+                phasor(e.foc * dl[i].y, sn, cs);
+                o.z = fmaf(e.wl.x, cs, fmaf(-e.wl.y, sn, o.z));
+                o.w = fmaf(e.wl.x, sn, fmaf(e.wl.y, cs, o.w));
+            }
+            if (q < e.Nr && p < e.Nt) {
+                float2* dst = e.Hf + (int64_t)q * e.Nt + p;
+                if (p + 1 < e.Nt && ((((uintptr_t)dst) & 15) == 0)) {
+                    *reinterpret_cast<float4*>(dst) = o;
+                } else {
+                    dst[0] = make_float2(o.x, o.y);
+                    if (p + 1 < e.Nt) dst[1] = make_float2(o.z, o.w);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
 template <bool kF16, bool kBatch, int kTileN>
-__global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constant__ TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constant__ TcArgs a) {
     using Sh = TcShape<kTileN>;
     extern __shared__ unsigned char smem_raw[];
-    __shared__ float s_red[kTcThreads / 32];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* sA_hi = smem;
-    unsigned char* sA_lo = smem + kABytes;
-    unsigned char* sB_hi = smem + 2 * kABytes;
-    unsigned char* sB_lo = smem + 2 * kABytes + Sh::kBBytes;
-    uint64_t* mbar = (uint64_t*)(smem + Sh::kSmemTiles);
-    uint64_t* never = (uint64_t*)(smem + Sh::kSmemTiles + 8);   // injected-fault barrier
-    uint32_t* tmem_slot = (uint32_t*)(smem + Sh::kSmemTiles + 16);
+    unsigned char* stage_out = smem + 2 * Sh::kStage;
+    uint64_t* bars = (uint64_t*)(stage_out + Sh::kOut);
+    // bars: mma_done[0..1] (per operand stage), acc_full[0..1] (per accumulator),
+    // never (injected fault), drain (final wait before the tensor memory is freed)
+    const uint32_t bar0 = smem_u32(bars);
+    auto bar = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+    uint32_t* tmem_slot = (uint32_t*)(bars + 6);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) {
@@ -191,168 +391,177 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(never)), "r"(1));
+        for (int i = 0; i < 6; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(i)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t mbar_a = smem_u32(mbar);
-    uint32_t phase = 0;
     bool failed = false;
     // injected fault: the first phase of `never` never completes; the bounded
     // wait gives up and the CTA takes the same exit as a real timeout
-    if (a.inject_timeout) failed = __syncthreads_or(!mbar_wait(smem_u32(never), 0u, 1u << 12)) != 0;
+    if (a.inject_timeout) failed = __syncthreads_or(!mbar_wait(bar(4), 0u, 1u << 12)) != 0;
 
     const int64_t items = kBatch ? a.items
                                  : (int64_t)a.F * ((a.Nr + 63) / 64) * ((a.Nt + kTileN - 1) / kTileN);
-    for (int64_t it = blockIdx.x; it < items && !failed; it += gridDim.x) {
+    uint32_t stage_uses0 = 0u, stage_uses1 = 0u;   // chunks issued per operand stage
+    uint32_t acc_uses0 = 0u, acc_uses1 = 0u;       // tiles with MMAs per accumulator
+    uint32_t chunk_all = 0;
+    TcEpi prev{};
+    bool have_prev = false;
+    bool epi_ok = true;   // this thread's last epilogue wait succeeded (folded into the next barrier)
+    int local = 0;
+    for (int64_t it = blockIdx.x; it < items && !failed; it += gridDim.x, ++local) {
         const TcItem x = tc_item<kBatch, kTileN>(a, it);
+        const int acc = local & 1;
         const int nch = (x.nrefl + kChunkP - 1) / kChunkP;
-        // FP16 form: power-of-two scale of this frequency's weights (exact)
-        float sc = 1.f, isc = 1.f;
-        if (kF16) {
-            float m = 0.f;
-            for (int n = x.n0 + tid; n < x.n0 + x.nrefl; n += kTcThreads) {
-                float2 ww = __ldg(x.wf + n);
-                m = fmaxf(m, fmaxf(fabsf(ww.x), fabsf(ww.y)));
-            }
-            for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (lane == 0) s_red[warp] = m;
-            __syncthreads();
-            m = s_red[0];
-            for (int k = 1; k < kTcThreads / 32; ++k) m = fmaxf(m, s_red[k]);
-            __syncthreads();  // s_red is rewritten for the next item
-            if (m > 0.f) {
-                int e;
-                frexpf(m, &e);
-                sc = ldexpf(1.f, -e);
-                isc = ldexpf(1.f, e);
-            }
-        }
-        for (int c = 0; c < nch && !failed; ++c) {
-            const int nb = x.n0 + c * kChunkP;
-            const int cnt = min(kChunkP, x.n0 + x.nrefl - nb);
-            // A' tile: 64 receive elements x 32 paths, each a 2x2 real block;
-            // consecutive threads take consecutive receive elements (coalesced)
-#pragma unroll 4
-            for (int e = tid; e < 64 * kChunkP; e += kTcThreads) {
-                int ql = e & 63, nl = e >> 6;
-                int q = x.q0 + ql, n = nb + nl;
-                float ar = 0.f, ai = 0.f;
-                if (nl < cnt && q < x.Nr) {
-                    float2 ww = __ldg(x.wf + n);
-                    float s, co;
-                    phasor(x.foc * __ldg(x.dr + (int64_t)n * x.Nr + q), s, co);
-                    ar = ww.x * co - ww.y * s;
-                    ai = ww.x * s + ww.y * co;
-                    if (kF16) { ar *= sc; ai *= sc; }
+        // FP16 form: the power-of-two scale of this frequency's weights (exact)
+        const float sc = kF16 ? x.sc : 1.f;
+        for (int c = 0; c < nch; ++c) {
+            const int st = chunk_all & 1;
+            unsigned char* sA_hi = smem + st * Sh::kStage;
+            unsigned char* sA_lo = sA_hi + kABytes;
+            unsigned char* sB_hi = sA_hi + 2 * kABytes;
+            unsigned char* sB_lo = sB_hi + Sh::kBBytes;
+            bool ok = true;
+            // the stage is free once the MMAs of its previous chunk have completed
+            const uint32_t su = st ? stage_uses1 : stage_uses0;
+            if (su > 0) ok = mbar_wait(bar(st), (su - 1u) & 1u);
+            const int nb = c * kChunkP;
+            const int cnt = min(kChunkP, x.nrefl - nb);
+            const int nks = (cnt + 7) >> 3;        // MMA K-steps (8 paths each)
+            const int n16 = 2 * nks;               // 16-byte chunks per row (4 paths each)
+            const int unitsB = kTileN * n16, units = unitsB + 64 * n16;
+            if (ok) {
+#pragma unroll 2
+                for (int u = tid; u < units; u += kTcThreads) {
+                    if (u < unitsB) {
+                        // B' (stored N x K): transmit element p, paths nb + 4 c16 .. + 3
+                        // (padded paths have zero weight, so their phasors are harmless)
+                        const int pl = u % kTileN, c16 = u / kTileN;
+                        const int p = x.p0 + pl;
+                        float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (p < x.Nt) d4 = __ldg(reinterpret_cast<const float4*>(x.dtT + (int64_t)p * x.Pp + nb + 4 * c16));
+                        float vr[4], vi[4];
+                        phasor(x.foc * d4.x, vi[0], vr[0]);
+                        phasor(x.foc * d4.y, vi[1], vr[1]);
+                        phasor(x.foc * d4.z, vi[2], vr[2]);
+                        phasor(x.foc * d4.w, vi[3], vr[3]);
+                        uint32_t h[4], l[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) split2<kF16>(vr[k], vi[k], h[k], l[k]);
+                        const uint32_t o = chunk_off(pl, c16);
+                        sts128(smem_u32(sB_hi) + o, h[0], h[1], h[2], h[3]);
+                        sts128(smem_u32(sB_lo) + o, l[0], l[1], l[2], l[3]);
+                    } else {
+                        // A': receive element q, paths nb + 4 c16 .. + 3, as the two
+                        // rows 2q (Re A, -Im A) and 2q+1 (Im A, Re A)
+                        // lane pairs take neighbouring chunks of one receive element,
+                        // so that a quarter warp's 16-byte stores land in 8 distinct
+                        // bank groups of the swizzled rows 2q and 2q+1
+                        const int v = u - unitsB;
+                        const int ql = (v >> 1) & 63, c16 = (v & 1) + 2 * (v >> 7);
+                        const int q = x.q0 + ql;
+                        const int n = nb + 4 * c16;
+                        float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        float4 w01 = d4, w23 = d4;
+                        if (q < x.Nr) {
+                            d4 = __ldg(reinterpret_cast<const float4*>(x.drT + (int64_t)q * x.Pp + n));
+                            w01 = __ldg(reinterpret_cast<const float4*>(x.wf + n));
+                            w23 = __ldg(reinterpret_cast<const float4*>(x.wf + n + 2));
+                        }
+                        const float dd[4] = {d4.x, d4.y, d4.z, d4.w};
+                        const float wr[4] = {w01.x, w01.z, w23.x, w23.z};
+                        const float wi[4] = {w01.y, w01.w, w23.y, w23.w};
+                        uint32_t h0[4], l0[4], h1[4], l1[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            float sn, cs;
+                            phasor(x.foc * dd[k], sn, cs);
+                            const float ar = (wr[k] * cs - wi[k] * sn) * sc;
+                            const float ai = (wr[k] * sn + wi[k] * cs) * sc;
+                            split2<kF16>(ar, -ai, h0[k], l0[k]);
+                            // row 2q+1 holds (Im A, Re A): the same halves swapped, with
+                            // the sign of -Im A flipped (rounding to nearest is symmetric,
+                            // so these are the bits of a split of (ai, ar))
+                            h1[k] = __byte_perm(h0[k], 0u, 0x1032) ^ 0x8000u;
+                            l1[k] = __byte_perm(l0[k], 0u, 0x1032) ^ 0x8000u;
+                        }
+                        const uint32_t o0 = chunk_off(2 * ql, c16), o1 = chunk_off(2 * ql + 1, c16);
+                        sts128(smem_u32(sA_hi) + o0, h0[0], h0[1], h0[2], h0[3]);
+                        sts128(smem_u32(sA_lo) + o0, l0[0], l0[1], l0[2], l0[3]);
+                        sts128(smem_u32(sA_hi) + o1, h1[0], h1[1], h1[2], h1[3]);
+                        sts128(smem_u32(sA_lo) + o1, l1[0], l1[1], l1[2], l1[3]);
+                    }
                 }
-                uint16_t h0, l0, h1, l1, h2, l2;
-                split16<kF16>(ar, h0, l0);
-                split16<kF16>(-ai, h1, l1);
-                split16<kF16>(ai, h2, l2);
-                uint32_t o0 = sw128(2 * ql, 2 * nl), o1 = sw128(2 * ql + 1, 2 * nl);
-                *(uint32_t*)(sA_hi + o0) = (uint32_t)h0 | ((uint32_t)h1 << 16);
-                *(uint32_t*)(sA_lo + o0) = (uint32_t)l0 | ((uint32_t)l1 << 16);
-                *(uint32_t*)(sA_hi + o1) = (uint32_t)h2 | ((uint32_t)h0 << 16);
-                *(uint32_t*)(sA_lo + o1) = (uint32_t)l2 | ((uint32_t)l0 << 16);
-            }
-            // B' tile (stored N x K): N transmit elements x 32 paths;
-            // consecutive threads take consecutive transmit elements (coalesced)
-#pragma unroll 8
-            for (int e = tid; e < kTileN * kChunkP; e += kTcThreads) {
-                int pl = e & (kTileN - 1), nl = e / kTileN;
-                int p = x.p0 + pl, n = nb + nl;
-                float vr = 0.f, vi = 0.f;
-                if (nl < cnt && p < x.Nt) phasor(x.foc * __ldg(x.dt + (int64_t)n * x.Nt + p), vi, vr);
-                uint16_t h0, l0, h1, l1;
-                split16<kF16>(vr, h0, l0);
-                split16<kF16>(vi, h1, l1);
-                uint32_t o = sw128(pl, 2 * nl);
-                *(uint32_t*)(sB_hi + o) = (uint32_t)h0 | ((uint32_t)h1 << 16);
-                *(uint32_t*)(sB_lo + o) = (uint32_t)l0 | ((uint32_t)l1 << 16);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
+            // one decision for the whole CTA (this chunk's wait and the last epilogue's)
+            failed = __syncthreads_or(!(ok && epi_ok)) != 0;
+            if (failed) break;
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                uint64_t dAh = make_desc(smem_u32(sA_hi)), dAl = make_desc(smem_u32(sA_lo));
-                uint64_t dBh = make_desc(smem_u32(sB_hi)), dBl = make_desc(smem_u32(sB_lo));
-                for (int ks = 0; ks < 4; ++ks) {
-                    uint64_t off = (uint64_t)(ks * 32) >> 4;  // 16 elements along K
-                    mma_16<kF16, kTileN>(tmem, dAh + off, dBh + off, (c > 0 || ks > 0) ? 1u : 0u);
-                    mma_16<kF16, kTileN>(tmem, dAh + off, dBl + off, 1u);
-                    mma_16<kF16, kTileN>(tmem, dAl + off, dBh + off, 1u);
+                const uint64_t dAh = make_desc(smem_u32(sA_hi)), dAl = make_desc(smem_u32(sA_lo));
+                const uint64_t dBh = make_desc(smem_u32(sB_hi)), dBl = make_desc(smem_u32(sB_lo));
+                const uint32_t d = tmem + (uint32_t)(acc * kTileN);
+                for (int ks = 0; ks < nks; ++ks) {
+                    const uint64_t off = (uint64_t)(ks * 32) >> 4;  // 16 K values
+                    mma_16<kF16, kTileN>(d, dAh + off, dBh + off, (c > 0 || ks > 0) ? 1u : 0u);
+                    mma_16<kF16, kTileN>(d, dAh + off, dBl + off, 1u);
+                    mma_16<kF16, kTileN>(d, dAl + off, dBh + off, 1u);
                 }
-                mma_commit(mbar_a);
+                mma_commit(bar(st));
+                if (c == nch - 1) mma_commit(bar(2 + acc));
             }
-            const bool ok = mbar_wait(mbar_a, phase);
-            phase ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            failed = __syncthreads_or(!ok) != 0;  // one decision for the whole CTA
+            if (st) stage_uses1 += 1u; else stage_uses0 += 1u;
+            chunk_all += 1u;
         }
         if (failed) break;
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 and half (w / 4) of the N columns
-        const int qw = warp & 3, chalf = warp >> 2;
-        const int row = 32 * qw + lane;            // row of C: 2 (q - q0) + part
-        const int q = x.q0 + (row >> 1);
-        const int part = row & 1;
-        float2 wl = make_float2(0.f, 0.f);
-        if (x.los >= 0) wl = x.wf[x.los];
-        for (int j = 0; j < kTileN / 64; ++j) {
-            const int col0 = (kTileN / 2) * chalf + 32 * j;
-            uint32_t v[32];
-            if (nch > 0) {
-                tmem_ld32(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)col0, v);
-            } else {
-                for (int k = 0; k < 32; ++k) v[k] = 0u;
-            }
-            // even lane (real row) keeps columns [0,16), odd lane (imaginary row) [16,32)
-            float re[16], im[16];
-            for (int k = 0; k < 16; ++k) {
-                float mine_lo = __uint_as_float(v[k]), mine_hi = __uint_as_float(v[16 + k]);
-                float send = part == 0 ? mine_hi : mine_lo;
-                float got = __shfl_xor_sync(0xffffffffu, send, 1);
-                if (part == 0) { re[k] = mine_lo; im[k] = got; }
-                else { re[k] = got; im[k] = mine_hi; }
-                if (kF16) { re[k] *= isc; im[k] *= isc; }
-            }
-            const int pb = x.p0 + col0 + 16 * part;
-            if (q < x.Nr) {
-                float2* dst = x.Hf + (int64_t)q * x.Nt;
-                if (x.los >= 0) {
-                    float dl[16];
-                    const float* src = x.dlos + (int64_t)q * x.Nt + pb;
-                    if (pb + 16 <= x.Nt && ((((uintptr_t)src) & 15) == 0)) {
-                        for (int k = 0; k < 4; ++k) {
-                            float4 v4 = __ldg(reinterpret_cast<const float4*>(src) + k);
-                            dl[4 * k] = v4.x; dl[4 * k + 1] = v4.y; dl[4 * k + 2] = v4.z; dl[4 * k + 3] = v4.w;
-                        }
-                    } else {
-                        for (int k = 0; k < 16; ++k) dl[k] = pb + k < x.Nt ? __ldg(src + k) : 0.f;
-                    }
-                    for (int k = 0; k < 16; ++k) {
-                        float s, co;
-                        sincospif(-2.0f * x.foc * dl[k], &s, &co);
-                        re[k] += wl.x * co - wl.y * s;
-                        im[k] += wl.x * s + wl.y * co;
-                    }
-                }
-                if (pb + 16 <= x.Nt && ((((uintptr_t)(dst + pb)) & 15) == 0)) {
-                    float4* d4 = reinterpret_cast<float4*>(dst + pb);
-                    for (int k = 0; k < 8; ++k)
-                        d4[k] = make_float4(re[2 * k], im[2 * k], re[2 * k + 1], im[2 * k + 1]);
-                } else {
-                    for (int k = 0; k < 16 && pb + k < x.Nt; ++k) dst[pb + k] = make_float2(re[k], im[k]);
-                }
-            }
+        TcEpi cur;
+        cur.q0 = x.q0; cur.p0 = x.p0; cur.Nr = x.Nr; cur.Nt = x.Nt; cur.los = x.los; cur.acc = acc;
+        cur.mma = nch > 0;
+        cur.acc_parity = (acc ? acc_uses1 : acc_uses0) & 1u;
+        if (nch > 0) {
+            if (acc) acc_uses1 += 1u; else acc_uses0 += 1u;
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        cur.foc = x.foc;
+        cur.isc = kF16 ? 1.f / sc : 1.f;   // exact: sc is a power of two
+        cur.wl = x.wl;
+        cur.dlos = x.dlos; cur.Hf = x.Hf;
+        cur.full = x.q0 + 64 <= x.Nr && x.p0 + kTileN <= x.Nt && (x.Nt & 1) == 0 &&
+                   ((((uintptr_t)x.Hf) & 15) == 0) && (!x.los || ((((uintptr_t)x.dlos) & 7) == 0));
+        // the previous tile's epilogue runs while this tile's MMAs do; no
+        // barrier follows it: the next tile's first chunk barrier carries its
+        // status, and its accumulator is written again only after that barrier
+        if (have_prev) {
+            bool ok = true;
+            if (prev.mma) {
+                ok = __all_sync(0xffffffffu, mbar_wait(bar(2 + prev.acc), prev.acc_parity));
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            if (ok) tc_epilogue<kTileN>(prev, tmem, stage_out, warp, lane);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            epi_ok = epi_ok && ok;
+        }
+        prev = cur;
+        have_prev = true;
+    }
+    if (!failed && have_prev) {
+        bool ok = true;
+        if (prev.mma) {
+            ok = __all_sync(0xffffffffu, mbar_wait(bar(2 + prev.acc), prev.acc_parity));
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        if (ok) tc_epilogue<kTileN>(prev, tmem, stage_out, warp, lane);
+        epi_ok = epi_ok && ok;
+    }
+    failed = __syncthreads_or(failed || !epi_ok) != 0;
+    // every MMA this CTA issued has completed before its tensor memory is freed
+    // (bounded wait; on a normal exit the last epilogue has already seen them)
+    if (tid == 0) {
+        mma_commit(bar(5));
+        if (!mbar_wait(bar(5), 0u)) failed = true;
     }
     if (failed && tid == 0) atomicOr(a.status, (unsigned)ST_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -362,14 +571,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_synth_tc(const __grid_constan
     }
 }
 
-// Operands of the tensor-core forms in one launch (the FP32 copies of the
-// FP64 prologue of the CUDA-core forms): for the Pr paths of one receiver,
-//   dt[n][p] = |T_p - P1| - |T_0 - P1|,  dr[n][q] = |R_q - Pm| - |R_0 - Pm|
-//   (0 for the LoS path), dlos[q][p] = |T_p - R_q| - |T_0 - R_0| (FP64, then
-//   rounded), and w[f][n] = g_n(f) exp(-j 2 pi frac(f L_n / c)) in FP64, then
-//   rounded.
+// Operands of the tensor-core forms in one launch (layouts in synth_ops.cuh):
+// blocks [0, nbw) compute the weights, one warp per frequency (the FP16 scale
+// is that warp's maximum); the other blocks compute the element delays, one
+// thread per (path, 8 elements), the path's reference distance once.
 struct TcPrep {
-    int32_t Pr, Nt, Nr, F;
+    int32_t Pr, Pp, Nt, Nr, F, nbw;
     const int32_t* nb;       // [Pr] reflections of the receiver's paths
     const double* pts;       // [Pr][kKmax][3]
     const double* L;         // [Pr]
@@ -379,51 +586,57 @@ struct TcPrep {
     const double* rx_elem;
     const double* R0;
     d3 T0;
-    float* dt;
-    float* dr;
+    float* dtT;
+    float* drT;
     float* dlos;
     float2* w;
+    float2* wl;
+    float* sc;
 };
 
 __global__ void k_tc_prep(const __grid_constant__ TcPrep a) {
-    const int64_t n_dt = (int64_t)a.Pr * a.Nt, n_dr = (int64_t)a.Pr * a.Nr, n_dl = (int64_t)a.Nr * a.Nt;
-    const int64_t total = n_dt + n_dr + n_dl + (int64_t)a.F * a.Pr;
-    const d3 R0 = ld3(a.R0);
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        if (t < n_dt) {
-            const int64_t n = t / a.Nt;
-            const int p = (int)(t - n * a.Nt);
+    const int n0 = (a.Pr > 0 && a.nb[0] == 0) ? 1 : 0;   // the LoS path sorts first
+    const int nrefl = a.Pr - n0;
+    if ((int)blockIdx.x < a.nbw) {
+        const int f = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+        if (f >= a.F) return;
+        const double fr = a.freqs[f];
+        float m = 0.f;
+        for (int n = lane; n < a.Pp; n += 32) {
+            float2 ww = make_float2(0.f, 0.f);
+            if (n < nrefl) ww = synth_weight(a.g[(int64_t)(n + n0) * a.F + f], fr, a.L[n + n0]);
+            a.w[(int64_t)f * a.Pp + n] = ww;
+            m = fmaxf(m, fmaxf(fabsf(ww.x), fabsf(ww.y)));
+        }
+        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            a.sc[f] = synth_scale(m);
+            a.wl[f] = n0 ? synth_weight(a.g[f], fr, a.L[0]) : make_float2(0.f, 0.f);
+        }
+        return;
+    }
+    // delays: one element per thread over every SM (FP64 throughput per SM is
+    // the limit here), consecutive threads on consecutive paths of one element
+    const int64_t n_dt = (int64_t)a.Pp * a.Nt, n_dr = (int64_t)a.Pp * a.Nr, n_dl = (int64_t)a.Nr * a.Nt;
+    const int64_t total = n_dt + n_dr + n_dl;
+    const int64_t stride = (int64_t)(gridDim.x - a.nbw) * blockDim.x;
+    for (int64_t t = (int64_t)(blockIdx.x - a.nbw) * blockDim.x + threadIdx.x; t < total; t += stride) {
+        if (t < n_dr + n_dt) {
+            const bool tx = t < n_dt;
+            const int64_t u = tx ? t : t - n_dt;
+            const int n = (int)(u % a.Pp), e = (int)(u / a.Pp);
             float v = 0.f;
-            if (a.nb[n] > 0) {
-                const d3 P1 = ld3(a.pts + n * kKmax * 3);
-                v = (float)(norm(ld3(a.tx_elem + 3 * p) - P1) - norm(a.T0 - P1));
+            if (n < nrefl) {
+                const int i = n + n0, m = a.nb[i];
+                const d3 P = ld3(a.pts + ((int64_t)i * kKmax + (tx ? 0 : m - 1)) * 3);
+                const double ref = norm((tx ? a.T0 : ld3(a.R0)) - P);
+                v = el_delay((tx ? a.tx_elem : a.rx_elem) + 3 * e, P, ref);
             }
-            a.dt[t] = v;
-        } else if (t < n_dt + n_dr) {
-            const int64_t u = t - n_dt, n = u / a.Nr;
-            const int q = (int)(u - n * a.Nr);
-            const int m = a.nb[n];
-            float v = 0.f;
-            if (m > 0) {
-                const d3 Pm = ld3(a.pts + (n * kKmax + m - 1) * 3);
-                v = (float)(norm(ld3(a.rx_elem + 3 * q) - Pm) - norm(R0 - Pm));
-            }
-            a.dr[u] = v;
-        } else if (t < n_dt + n_dr + n_dl) {
-            const int64_t u = t - n_dt - n_dr, q = u / a.Nt;
-            const int p = (int)(u - q * a.Nt);
-            a.dlos[u] = (float)(norm(ld3(a.tx_elem + 3 * p) - ld3(a.rx_elem + 3 * q)) - norm(a.T0 - R0));
+            (tx ? a.dtT : a.drT)[u] = v;
         } else {
-            const int64_t u = t - n_dt - n_dr - n_dl, f = u / a.Pr, n = u - f * a.Pr;
-            // the batched form computes its weights with the same FP64 arithmetic,
-            // so both give bit-identical H for the same path list
-            const double cyc = a.freqs[f] * a.L[n] / kC0;
-            const double frc = cyc - floor(cyc);
-            double s, c;
-            sincospi(-2.0 * frc, &s, &c);
-            const float2 gg = a.g[n * a.F + f];
-            a.w[u] = make_float2((float)(gg.x * c - gg.y * s), (float)(gg.x * s + gg.y * c));
+            const int64_t u = t - n_dt - n_dr;
+            const int q = (int)(u / a.Nt), p = (int)(u - (int64_t)q * a.Nt);
+            a.dlos[u] = el_delay(a.tx_elem + 3 * p, ld3(a.rx_elem + 3 * q), norm(a.T0 - ld3(a.R0)));
         }
     }
 }
@@ -435,17 +648,22 @@ inline unsigned nb256(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + 25
 sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* freqs, int32_t F,
                         const double* tx_elem, int32_t Nt, const double* rx_elem, int32_t Nr,
                         int32_t rx_index, float2* H, bool f16, cudaStream_t s) {
-    const int32_t o0 = pl->h_rx_off[rx_index], Pr_ = pl->h_rx_off[rx_index + 1] - o0;
-    const int32_t Pr = std::max(Pr_, 1);
-    // one buffer for the four operands: w (8-byte elements) first
-    const size_t n_w = (size_t)Pr * F, n_f = (size_t)Pr * Nt + (size_t)Pr * Nr + (size_t)Nr * Nt;
+    const int32_t o0 = pl->h_rx_off[rx_index], Pr = pl->h_rx_off[rx_index + 1] - o0;
+    const int32_t Pp = (int32_t)std::max<int64_t>(8, (Pr + 7) & ~7);   // reflected paths, padded
+    // one buffer for every operand, 16-byte aligned parts: w, wl (8-byte
+    // elements) first, then sc, dtT, drT, dlos
+    const size_t n_w = (size_t)Pp * F, n_wl = ((size_t)F + 1) & ~(size_t)1;
+    const size_t n_sc = ((size_t)F + 3) & ~(size_t)3;
+    const size_t n_f = n_sc + (size_t)Pp * Nt + (size_t)Pp * Nr + (((size_t)Nr * Nt + 3) & ~(size_t)3);
     float2* w;
-    SBR_TRY(dalloc_n(&w, n_w + (n_f + 1) / 2, s));
-    float* dt = reinterpret_cast<float*>(w + n_w);
-    float* dr = dt + (size_t)Pr * Nt;
-    float* dl = dr + (size_t)Pr * Nr;
+    SBR_TRY(dalloc_n(&w, n_w + n_wl + (n_f + 1) / 2, s));
+    float2* wl = w + n_w;
+    float* sc = reinterpret_cast<float*>(wl + n_wl);
+    float* dtT = sc + n_sc;
+    float* drT = dtT + (size_t)Pp * Nt;
+    float* dl = drT + (size_t)Pp * Nr;
     TcPrep pp{};
-    pp.Pr = Pr_; pp.Nt = Nt; pp.Nr = Nr; pp.F = F;
+    pp.Pr = Pr; pp.Pp = Pp; pp.Nt = Nt; pp.Nr = Nr; pp.F = F;
     pp.nb = pl->nb + o0;
     pp.pts = pl->pts + (int64_t)o0 * kKmax * 3;
     pp.L = pl->L + o0;
@@ -453,24 +671,25 @@ sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* 
     pp.freqs = freqs; pp.tx_elem = tx_elem; pp.rx_elem = rx_elem;
     pp.R0 = pl->rx_xyz + 3 * rx_index;
     pp.T0 = mk3(pl->tx[0], pl->tx[1], pl->tx[2]);
-    pp.dt = dt; pp.dr = dr; pp.dlos = dl; pp.w = w;
-    const int64_t n_all = (int64_t)Pr_ * (Nt + Nr) + (int64_t)Nr * Nt + (int64_t)Pr_ * F;
-    ::sbr::note_launch(), k_tc_prep<<<(unsigned)std::min<int64_t>(nb256(n_all), 8 * (int64_t)sm_count()), 256, 0, s>>>(pp);
+    pp.dtT = dtT; pp.drT = drT; pp.dlos = dl; pp.w = w; pp.wl = wl; pp.sc = sc;
+    pp.nbw = (int)nb256((int64_t)F * 32);
+    const int64_t n_del = (int64_t)Pp * (Nt + Nr) + (int64_t)Nr * Nt;
+    const unsigned nbd = (unsigned)std::min<int64_t>(nb256(n_del), 8 * (int64_t)sm_count());
+    ::sbr::note_launch(), k_tc_prep<<<(unsigned)pp.nbw + nbd, 256, 0, s>>>(pp);
     SBR_TRY_CUDA(cudaGetLastError());
     TcArgs a{};
     a.F = F; a.Nr = Nr; a.Nt = Nt;
-    a.Pr = Pr_;
+    a.Pr = Pr; a.Pp = Pp;
     a.nb0 = pl->nb + o0;
-    a.freqs = freqs; a.dt = dt; a.dr = dr; a.w = w; a.dlos = dl; a.H = H;
+    a.freqs = freqs; a.dtT = dtT; a.drT = drT; a.w = w; a.wl = wl; a.sc = sc; a.dlos = dl; a.H = H;
     a.status = pl->d_status;  // a bounded wait that gave up is reported by sbr_path_query
     a.inject_timeout = fault_mode() == kFaultTimeout ? 1 : 0;
     auto kern = f16 ? k_synth_tc<true, false, 256> : k_synth_tc<false, false, 256>;
     constexpr int kSmemBytes = TcShape<256>::kSmemBytes;
     SBR_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     int64_t items = (int64_t)F * ((Nr + 63) / 64) * ((Nt + 255) / 256);
-    // two CTAs per SM (97 KB shared memory and 256 TMEM columns each): one CTA's
-    // MMA and epilogue overlap the other's phasor generation
-    int grid = (int)std::min<int64_t>(items, 2 * (int64_t)sm_count());
+    // one persistent CTA per SM (two operand stages and two accumulators each)
+    int grid = (int)std::min<int64_t>(items, (int64_t)sm_count());
     ::sbr::note_launch(), kern<<<grid, kTcThreads, kSmemBytes, s>>>(a);
     SBR_TRY_CUDA(cudaGetLastError());
     dfree(w, s);
@@ -492,10 +711,12 @@ sbr_status batch_tc_launch(const BatchSynthWave& w, cudaStream_t s) {
     a.dr_all = w.dr;
     a.dl_all = w.dl;
     a.w_all = w.w;
+    a.wl_all = w.wl;
+    a.sc_all = w.sc;
     a.status = w.status;
     a.inject_timeout = fault_mode() == kFaultTimeout ? 1 : 0;
     if (w.items <= 0) return SBR_OK;
-    int grid = (int)std::min<int64_t>(w.items, 2 * (int64_t)sm_count());
+    int grid = (int)std::min<int64_t>(w.items, (int64_t)sm_count());
     ::sbr::note_launch(), k_synth_tc<kF16, true, kTileN><<<grid, kTcThreads, TcShape<kTileN>::kSmemBytes, s>>>(a);
     SBR_TRY_CUDA(cudaGetLastError());
     return SBR_OK;

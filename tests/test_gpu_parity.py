@@ -322,7 +322,7 @@ def _h_errors(H, Ho):
 # (a few 1e-7 of a cycle for delays of a few cm at 100 GHz). Summed over the
 # paths, the maximum error stays within a few of those units of max |H| and
 # the median within one.
-TC_TOL = {2: (5e-5, 2e-5), 3: (1e-5, 5e-6)}   # form: (max |dH|/max|H|, median rel.)
+TC_TOL = {2: (3e-5, 1e-5), 3: (1e-5, 3e-6)}   # form: (max |dH|/max|H|, median rel.)
 
 
 @pytest.mark.parametrize("form", [2, 3])
