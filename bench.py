@@ -17,8 +17,10 @@ region and the number of library kernels launched.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-N > 1 runs under torchrun: every rank traces an independent Tx position of the
-same city (weak scaling, no collective on the data path); rank 0 prints.
+N > 1 runs under torchrun: the ranks split the one urban trace by geodesic ray
+id, all-gather their deduplicated reception records (the trace's single
+exchange step) and merge them with the trace's own min (dist, ray) rule before
+the paths are refined (strong scaling); rank 0 prints.
 --impl reference times the FP64 CPU oracle on bounded samples of the same
 workload and metric.
 """
@@ -118,9 +120,34 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-# street crossings (i, j) of the urban grid; rank r traces an independent Tx at
-# crossings[r % 8] with its receiver grid below it (weak scaling)
-CROSSINGS = [(4, 2), (3, 2), (5, 2), (4, 1), (4, 3), (2, 2), (6, 2), (3, 1)]
+def ray_range(R: int, rank: int, world: int):
+    """Rank's share of the launch grid's geodesic ids: contiguous, sizes within one."""
+    return R * rank // world, R * (rank + 1) // world
+
+
+def gather_records(keys, vals):
+    """The exchange step of a ray-range split trace: every rank's deduplicated
+    records (keys [n, 10] int32, vals [n] int64) all-gathered over the process
+    group (NCCL on GPUs, gloo on CPU); the identity without a group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return keys, vals
+    world = dist.get_world_size()
+    n = torch.tensor([keys.shape[0]], dtype=torch.int64, device=keys.device)
+    ns = [torch.zeros_like(n) for _ in range(world)]
+    dist.all_gather(ns, n)
+    counts = [int(x.item()) for x in ns]
+    m = max(1, max(counts))
+    kp = torch.zeros((m, keys.shape[1]), dtype=keys.dtype, device=keys.device)
+    vp = torch.zeros(m, dtype=vals.dtype, device=vals.device)
+    kp[:keys.shape[0]] = keys
+    vp[:vals.shape[0]] = vals
+    ks = [torch.empty_like(kp) for _ in range(world)]
+    vs = [torch.empty_like(vp) for _ in range(world)]
+    dist.all_gather(ks, kp)
+    dist.all_gather(vs, vp)
+    return (torch.cat([k[:c] for k, c in zip(ks, counts)]), torch.cat([v[:c] for v, c in zip(vs, counts)]))
 
 
 def reduce_over_ranks(t_total: float, work: float, device=None):
@@ -281,7 +308,7 @@ def run_reference(args):
     value = segs / t / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.nthreads_default(),
                              "kind": "oracle", "sample": cfg["sample_per_step"]},
@@ -311,7 +338,7 @@ def run_gpu(args):
     peaks, peak_src = load_peaks()
 
     N_w = {"urban": 1000, "urban_n400": 400}[args.workload]
-    sc = scenes.config2(N=N_w, crossing=CROSSINGS[rank % len(CROSSINGS)])
+    sc = scenes.config2(N=N_w)
     d = sbr.scene_to_device(sc)
     N, K = sc["N"], sc["K"]
     _, a = sbr.launch_dirs(N, with_dirs=False)
@@ -319,10 +346,22 @@ def run_gpu(args):
     fc = float(sc["freqs"][0])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
+    R = 10 * N * N + 2
+    rr = ray_range(R, rank, world)
+
     def step(dd, df_from=0):
         bvh = sbr.build_bvh(dd["tri"], dd["surface_id"], dd["S"])
-        tr = sbr.trace(bvh, dd["tx"], dd["rx"], N, K, alpha=alpha, timing=True, depth_first_from=df_from)
-        pl = sbr.paths(tr, bvh)
+        if world == 1:
+            tr = sbr.trace(bvh, dd["tx"], dd["rx"], N, K, alpha=alpha, timing=True, depth_first_from=df_from)
+            pl = sbr.paths(tr, bvh)
+        else:
+            # ray-range split (Sec. I: rays traced in parallel): this rank's ids,
+            # its deduplicated records all-gathered, merged with the trace's own
+            # min (dist, ray) rule, then the paths of the whole grid
+            tr = sbr.trace(bvh, dd["tx"], dd["rx"], N, K, alpha=alpha, timing=True, depth_first_from=df_from,
+                           ray_range=rr)
+            keys, vals = gather_records(*tr.entries())
+            pl = sbr.paths(sbr.trace_merge(dd["tx"], dd["rx"], N, K, keys, vals, alpha=alpha), bvh)
         g = sbr.path_gains(pl, dd["mats"], dd["freqs"], dd["gamma"], dd["disp"], dd["pol"])
         pdp, st = sbr.pdp_angles(pl, g, 0, fc, 1e-9, 2048)
         stats = tr.stats()
@@ -367,7 +406,7 @@ def run_gpu(args):
     # the same step with every bounce breadth first (one launch per bounce over
     # compacted ray queues), for comparison
     bf_times, bf_rb = [], 0
-    for _ in range(args.steps):
+    for _ in range(args.steps if world == 1 else 0):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -377,7 +416,7 @@ def run_gpu(args):
         bf_times.append(e0.elapsed_time(e1))
         bf_rb += out[-1]["ray_bounces"]
         del out
-    bf_value = bf_rb / (sum(bf_times) / 1e3) / 1e6
+    bf_value = bf_rb / (sum(bf_times) / 1e3) / 1e6 if bf_times else None
 
     # e2e: the same step through the public API from pinned host memory, with the
     # inputs copied in and the path list, gains, PDP and statistics copied out.
@@ -411,8 +450,13 @@ def run_gpu(args):
         dd = dict(d)
         dd.update(unpack(host_buf.to(dev, non_blocking=True)))
         bvh = sbr.build_bvh(dd["tri"], dd["surface_id"], dd["S"])
-        tr = sbr.trace(bvh, dd["tx"], dd["rx"], N, K, alpha=alpha, timing=True)
-        pl = sbr.paths(tr, bvh)
+        if world == 1:
+            tr = sbr.trace(bvh, dd["tx"], dd["rx"], N, K, alpha=alpha, timing=True)
+            pl = sbr.paths(tr, bvh)
+        else:
+            tr = sbr.trace(bvh, dd["tx"], dd["rx"], N, K, alpha=alpha, timing=True, ray_range=rr)
+            keys, vals = gather_records(*tr.entries())
+            pl = sbr.paths(sbr.trace_merge(dd["tx"], dd["rx"], N, K, keys, vals, alpha=alpha), bvh)
         ev_pl = torch.cuda.Event()
         ev_pl.record()
         # gains and PDP are enqueued first, so that the device has work while
@@ -440,7 +484,9 @@ def run_gpu(args):
         e2e_t += e0.elapsed_time(e1) / 1e3
         e2e_rb += stats["ray_bounces"]
         d2h = sum(v.numel() * v.element_size() for v in pinned.values())
-    e2e_value = e2e_rb / e2e_t / 1e6 * world if e2e_t > 0 else None
+    if e2e_t > 0:
+        e2e_t, e2e_rb = reduce_over_ranks(e2e_t, float(e2e_rb), device=dev)
+    e2e_value = e2e_rb / e2e_t / 1e6 if e2e_t > 0 else None
 
     synth = None
     if not args.no_synth and rank == 0:
@@ -504,14 +550,16 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(times),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": "urban_300GHz_8x5_51600tri_N%d_R%d_K6_1024rx" % (N, 10 * N * N + 2),
                    "rays": 10 * N * N + 2, "max_bounces": K, "triangles": int(len(sc["tri"])),
                    "receivers": int(len(sc["rx"])), "ray_bounces_per_step": rb // args.steps,
                    "step": "build_bvh+trace+paths+gains+pdp", "l2": "flushed (256 MB write) "
                    "between timed steps",
-                   "parallelism": "dp%d (independent Tx per rank)" % world},
+                   "parallelism": ("rays%d: the launch grid split into contiguous geodesic-id ranges, one "
+                                   "per rank; deduplicated records all-gathered and merged" % world
+                                   if world > 1 else "single GPU")},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": int(h2d),
@@ -519,7 +567,8 @@ def run_gpu(args):
         "gpu_launches": None if n_launch is None else n_launch * args.steps,
         "launches_per_step": n_launch,
         "clocks": clk,
-        "breadth_first": {"value": bf_value, "unit": METRIC, "ms_per_step": statistics.mean(bf_times)},
+        "breadth_first": ({"value": bf_value, "unit": METRIC, "ms_per_step": statistics.mean(bf_times)}
+                          if bf_times else None),
         "synthesis": synth,
         "batched": batched,
         "surrogate": surrogate,

@@ -152,6 +152,11 @@ sbr_status sbr_bvh_query(const sbr_bvh* bvh, sbr_bvh_info* out);
  * rx_xyz: dev double [n_rx*3] (copied; may be freed after the stream runs).
  * alpha: 0 = computed as in sbr_launch_dirs. table_log2: 0 = automatic.
  * max_bounces in [0, 8]; n_rx in [0, 2^20]; 10 N^2 + 2 < 2^32.
+ * ray_begin, ray_end: trace only the launch directions with geodesic ids in
+ * [ray_begin, ray_end) (ray_end = 0: up to R); rays are independent (Sec. I
+ * traces them in parallel), so traces of disjoint ranges, e.g. one per GPU,
+ * merged with sbr_trace_entries and sbr_trace_merge give the path list of
+ * the whole grid. 0 <= ray_begin < end <= R.
  * depth_first_from: bounces before it run breadth first (one launch per
  * bounce over a compacted queue of live rays, the "width first" order of
  * Sec. I); from it on, each thread carries its ray through every remaining
@@ -170,6 +175,8 @@ typedef struct {
     double alpha;
     uint32_t flags;
     int32_t depth_first_from;
+    int64_t ray_begin;       /* traced geodesic ids [ray_begin, ray_end); ray_end 0 = R */
+    int64_t ray_end;
 } sbr_trace_params;
 
 /* sbr_trace_params.flags */
@@ -206,6 +213,36 @@ sbr_status sbr_trace(const sbr_bvh* bvh, const sbr_trace_params* params, sbr_tra
  * without a device round trip. */
 sbr_status sbr_trace_stats(const sbr_trace_result* tr, sbr_trace_counters* out);
 void sbr_trace_free(sbr_trace_result* tr);
+
+/*
+ * sbr_trace_entries - the deduplicated receptions of a trace as plain records
+ * (Sec. II-A.2 "pick out effective paths"): one per (receiver, surface
+ * sequence), with the minimum reception distance and, on a tie, the lowest ray
+ * id. This is what the traces of disjoint ray ranges exchange before their
+ * paths are refined. Synchronous (waits for the trace). keys: dev uint32
+ * [cap*10] per record (receiver, reflections, 8 surface ids padded with
+ * 0xffffffff); vals: dev uint64 [cap] (bits of the FP32 distance << 32 | ray
+ * id). *n_out receives the record count; if it exceeds cap nothing is written
+ * and SBR_ERR_CAPACITY is returned. The record order is unspecified. A trace
+ * that failed on the device returns its status.
+ */
+sbr_status sbr_trace_entries(const sbr_trace_result* tr, uint32_t* keys, uint64_t* vals, int64_t cap,
+                             int64_t* n_out, void* stream);
+/*
+ * sbr_trace_merge - a trace result holding the union of records (from
+ * sbr_trace_entries of any number of traces of the same scene, launch grid,
+ * receivers and max_bounces, in any order): per key the minimum value, the rule
+ * of the trace's own deduplication, which is commutative and associative, so
+ * sbr_paths on the merged result gives the path list of one trace over the
+ * union of the ray ranges, bit for bit (its refinement takes no per-ray hints).
+ * params: as given to those traces (ray range, depth_first_from and flags
+ * ignored; table_log2 0 = sized from n). keys, vals: dev, layouts of
+ * sbr_trace_entries, n records (may be 0). sbr_trace_stats of the result
+ * reports the key count and zero ray counters. Asynchronous. A table too small
+ * for the keys reports SBR_ERR_CAPACITY through sbr_trace_stats / sbr_paths.
+ */
+sbr_status sbr_trace_merge(const sbr_trace_params* params, const uint32_t* keys, const uint64_t* vals, int64_t n,
+                           sbr_trace_result** out, void* stream);
 
 /*
  * sbr_paths - effective paths (Sec. II-A.2 "pick out effective paths",

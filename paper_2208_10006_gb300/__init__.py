@@ -157,6 +157,19 @@ class TraceResult:
                     queue=list(c.queue), alpha=c.alpha,
                     status=c.status, table_log2=c.table_log2, bounce_ms=list(c.bounce_ms))
 
+    def entries(self, stream=None):
+        """The deduplicated receptions as records (sbr_trace_entries): keys
+        int32 [n, 10] (receiver, reflections, 8 surface ids, -1 padded) and
+        vals int64 [n] (FP32 distance bits << 32 | ray id), CUDA tensors."""
+        n = C.c_int64(0)
+        st = _L().sbr_trace_entries(self._h, None, None, 0, C.byref(n), _stream(stream))
+        if st not in (0, 3):
+            _check(st)
+        keys = torch.empty((max(n.value, 1), 10), dtype=torch.int32, device=_dev())
+        vals = torch.empty(max(n.value, 1), dtype=torch.int64, device=_dev())
+        _check(_L().sbr_trace_entries(self._h, _ptr(keys), _ptr(vals), n.value, C.byref(n), _stream(stream)))
+        return keys[:n.value], vals[:n.value]
+
     def free(self):
         if self._h is not None:
             _L().sbr_trace_free(self._h)
@@ -169,11 +182,7 @@ class TraceResult:
             pass
 
 
-def trace(bvh: BVH, tx, rx: torch.Tensor, N: int, K: int, alpha: float = 0.0, table_log2: int = 0,
-          timing: bool = False, count_visits: bool = False, depth_first_from: int = 0,
-          stream=None) -> TraceResult:
-    """Shoot and bounce. tx: 3 floats; rx: float64 [n_rx, 3] CUDA. Bounces from
-    depth_first_from on are traced depth first (K + 1: all breadth first)."""
+def _trace_params(tx, rx, N, K, alpha, table_log2):
     p = _lib.TraceParams()
     for k in range(3):
         p.tx[k] = float(tx[k])
@@ -186,6 +195,32 @@ def trace(bvh: BVH, tx, rx: torch.Tensor, N: int, K: int, alpha: float = 0.0, ta
     p.max_bounces = int(K)
     p.table_log2 = int(table_log2)
     p.alpha = float(alpha)
+    return p
+
+
+def trace_merge(tx, rx: torch.Tensor, N: int, K: int, keys: torch.Tensor, vals: torch.Tensor, alpha: float = 0.0,
+                table_log2: int = 0, stream=None) -> TraceResult:
+    """A trace result from the records of traces of disjoint ray ranges
+    (sbr_trace_merge); sbr_paths on it gives the path list of the union."""
+    p = _trace_params(tx, rx, N, K, alpha, table_log2)
+    keys = keys.contiguous()
+    vals = vals.contiguous()
+    assert keys.dtype == torch.int32 and vals.dtype == torch.int64 and keys.shape[0] == vals.shape[0]
+    h = C.c_void_p()
+    _check(_L().sbr_trace_merge(C.byref(p), _ptr(keys), _ptr(vals), int(vals.shape[0]), C.byref(h),
+                                _stream(stream)))
+    return TraceResult(h, p)
+
+
+def trace(bvh: BVH, tx, rx: torch.Tensor, N: int, K: int, alpha: float = 0.0, table_log2: int = 0,
+          timing: bool = False, count_visits: bool = False, depth_first_from: int = 0,
+          ray_range=None, stream=None) -> TraceResult:
+    """Shoot and bounce. tx: 3 floats; rx: float64 [n_rx, 3] CUDA. Bounces from
+    depth_first_from on are traced depth first (K + 1: all breadth first).
+    ray_range = (begin, end): trace only those geodesic ids (end 0 = all)."""
+    p = _trace_params(tx, rx, N, K, alpha, table_log2)
+    if ray_range is not None:
+        p.ray_begin, p.ray_end = int(ray_range[0]), int(ray_range[1])
     p.flags = (_lib.TRACE_TIMING if timing else 0) | (_lib.TRACE_COUNT_VISITS if count_visits else 0)
     p.depth_first_from = int(depth_first_from)
     h = C.c_void_p()

@@ -21,7 +21,8 @@ TRACE_COUNT_VISITS = 2
 BVH_SAH_TOP = 1   # sbr_build_bvh_ex flag
 
 EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_count", "sbr_launch_dirs", "sbr_build_bvh", "sbr_build_bvh_ex", "sbr_bvh_free",
-           "sbr_bvh_query", "sbr_trace", "sbr_trace_stats", "sbr_trace_free", "sbr_paths",
+           "sbr_bvh_query", "sbr_trace", "sbr_trace_stats", "sbr_trace_free", "sbr_trace_entries",
+           "sbr_trace_merge", "sbr_paths",
            "sbr_path_query", "sbr_path_export", "sbr_path_list_free", "sbr_path_gains",
            "sbr_synthesize_H", "sbr_synthesize_H_elements", "sbr_pdp_angles", "sbr_capacity", "sbr_capacity_noalloc",
            "sbr_batch_create", "sbr_batch_run", "sbr_batch_query", "sbr_batch_export", "sbr_batch_free",
@@ -33,7 +34,8 @@ EXPORTS = ["sbr_last_error", "sbr_version", "sbr_launch_count", "sbr_launch_dirs
 class TraceParams(C.Structure):
     _fields_ = [("tx", C.c_double * 3), ("rx_xyz", C.c_void_p), ("n_rx", C.c_int32),
                 ("subdiv_N", C.c_int32), ("max_bounces", C.c_int32), ("table_log2", C.c_int32),
-                ("alpha", C.c_double), ("flags", C.c_uint32), ("depth_first_from", C.c_int32)]
+                ("alpha", C.c_double), ("flags", C.c_uint32), ("depth_first_from", C.c_int32),
+                ("ray_begin", C.c_int64), ("ray_end", C.c_int64)]
 
 
 class TraceCounters(C.Structure):
@@ -85,7 +87,7 @@ class MlpConfig(C.Structure):
                 ("err_of", C.c_int32), ("feat_log2_max", C.c_float), ("reserved", C.c_int32)]
 
 
-assert C.sizeof(TraceParams) == 64
+assert C.sizeof(TraceParams) == 80
 assert C.sizeof(BatchJob) == 136
 assert C.sizeof(BatchConfig) == 40
 assert C.sizeof(BatchInfo) == 88
@@ -126,6 +128,10 @@ def load() -> C.CDLL:
     L.sbr_trace_stats.argtypes = [p, C.POINTER(TraceCounters)]
     L.sbr_trace_free.restype = None
     L.sbr_trace_free.argtypes = [p]
+    L.sbr_trace_entries.restype = st
+    L.sbr_trace_entries.argtypes = [p, p, p, i64, C.POINTER(C.c_int64), p]
+    L.sbr_trace_merge.restype = st
+    L.sbr_trace_merge.argtypes = [C.POINTER(TraceParams), p, p, i64, pp, p]
     L.sbr_paths.restype = st
     L.sbr_paths.argtypes = [p, p, pp, C.POINTER(C.c_int64), p]
     L.sbr_path_query.restype = st

@@ -215,6 +215,9 @@ sbr_status sbr_trace(const sbr_bvh* b, const sbr_trace_params* p, sbr_trace_resu
     SBR_CHECK_ARG(p->depth_first_from >= 0, "depth_first_from >= 0");
     int64_t R = 10 * (int64_t)p->subdiv_N * p->subdiv_N + 2;
     SBR_CHECK_ARG(R < ((int64_t)1 << 32), "10 N^2 + 2 < 2^32");
+    const int64_t ray_end = p->ray_end ? p->ray_end : R;
+    SBR_CHECK_ARG(p->ray_begin >= 0 && p->ray_begin < ray_end && ray_end <= R,
+                  "0 <= ray_begin < ray_end <= 10 N^2 + 2");
     cudaStream_t s = (cudaStream_t)stream;
     sbr_trace_result* tr = new (std::nothrow) sbr_trace_result();
     if (!tr) { set_error("host allocation failed"); return SBR_ERR_ALLOC; }
@@ -222,6 +225,8 @@ sbr_status sbr_trace(const sbr_bvh* b, const sbr_trace_params* p, sbr_trace_resu
     tr->stream = s;
     tr->params = *p;
     tr->R = R;
+    tr->ray0 = p->ray_begin;
+    tr->Rr = ray_end - p->ray_begin;
     tr->n_rx = p->n_rx;
     tr->df_from = p->depth_first_from;
     if (p->table_log2) {
@@ -269,7 +274,7 @@ sbr_status sbr_trace_stats(const sbr_trace_result* tr, sbr_trace_counters* out) 
         SBR_TRY_CUDA(cudaStreamSynchronize(tr->stream));
     }
     memset(out, 0, sizeof *out);
-    out->rays = tr->R;
+    out->rays = tr->Rr;
     int64_t rb = 0;
     for (int k = 0; k <= tr->params.max_bounces; ++k) rb += (int64_t)c.queue[k];
     out->ray_bounces = rb;
@@ -292,6 +297,71 @@ sbr_status sbr_trace_stats(const sbr_trace_result* tr, sbr_trace_counters* out) 
     }
     out->status = (int32_t)status_from_bits(c.status);
     return (sbr_status)out->status;
+}
+
+sbr_status sbr_trace_entries(const sbr_trace_result* tr, uint32_t* keys, uint64_t* vals, int64_t cap,
+                             int64_t* n_out, void* stream) {
+    clear_error();
+    SBR_CHECK_ARG(tr && n_out, "trace result and n_out");
+    SBR_CHECK_ARG(cap >= 0 && (cap == 0 || (keys && vals)), "cap >= 0, keys and vals");
+    SBR_SAME_DEVICE(tr);
+    *n_out = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (tr->stream != s) SBR_TRY_CUDA(cudaStreamSynchronize(tr->stream));
+    return trace_entries_run(tr, keys, reinterpret_cast<unsigned long long*>(vals), cap, n_out, s);
+}
+
+sbr_status sbr_trace_merge(const sbr_trace_params* p, const uint32_t* keys, const uint64_t* vals, int64_t n,
+                           sbr_trace_result** out, void* stream) {
+    clear_error();
+    SBR_CHECK_ARG(out != nullptr, "out");
+    *out = nullptr;
+    SBR_CHECK_ARG(p != nullptr, "params");
+    SBR_CHECK_ARG(n >= 0 && (n == 0 || (keys && vals)), "n >= 0, keys and vals");
+    SBR_CHECK_ARG(p->subdiv_N >= 1 && p->subdiv_N <= 20000, "subdiv_N in [1, 20000]");
+    SBR_CHECK_ARG(p->max_bounces >= 0 && p->max_bounces <= SBR_KMAX, "max_bounces in [0, 8]");
+    SBR_CHECK_ARG(p->n_rx >= 0 && p->n_rx <= (1 << 20), "n_rx in [0, 2^20]");
+    SBR_CHECK_ARG(p->n_rx == 0 || p->rx_xyz, "rx_xyz");
+    SBR_CHECK_ARG(finite3(p->tx), "finite tx");
+    SBR_CHECK_ARG(std::isfinite(p->alpha) && p->alpha >= 0.0, "alpha >= 0");
+    SBR_CHECK_ARG(p->table_log2 == 0 || (p->table_log2 >= 4 && p->table_log2 <= 28), "table_log2");
+    cudaStream_t s = (cudaStream_t)stream;
+    sbr_trace_result* tr = new (std::nothrow) sbr_trace_result();
+    if (!tr) { set_error("host allocation failed"); return SBR_ERR_ALLOC; }
+    tr->device = current_device();
+    tr->stream = s;
+    tr->params = *p;
+    tr->R = 10 * (int64_t)p->subdiv_N * p->subdiv_N + 2;
+    tr->ray0 = 0;
+    tr->Rr = 0;   // no ray is traced by the merge itself
+    tr->n_rx = p->n_rx;
+    tr->df_from = 0;
+    if (p->table_log2) {
+        tr->table_log2 = p->table_log2;
+    } else {
+        int lg = 10;
+        while (lg < 28 && ((int64_t)1 << lg) < 2 * n) ++lg;   // load factor <= 1/2
+        tr->table_log2 = lg;
+    }
+    sbr_status st = SBR_OK;
+    if (tr->n_rx > 0) {
+        st = dalloc_n(&tr->rx, 3 * (size_t)tr->n_rx, s);
+        if (st == SBR_OK &&
+            cudaMemcpyAsync(tr->rx, p->rx_xyz, sizeof(double) * 3 * tr->n_rx, cudaMemcpyDeviceToDevice,
+                            s) != cudaSuccess) {
+            set_error("copy of rx_xyz failed");
+            st = SBR_ERR_CUDA;
+        }
+    }
+    if (st == SBR_OK) st = dalloc_n(&tr->d_alpha, 1, s);
+    if (st == SBR_OK && !(p->alpha > 0.0)) st = launch_alpha(p->subdiv_N, tr->d_alpha, s);
+    if (st == SBR_OK) st = trace_merge_run(tr, keys, reinterpret_cast<const unsigned long long*>(vals), n, s);
+    if (st != SBR_OK) {
+        sbr_trace_free(tr);
+        return st;
+    }
+    *out = tr;
+    return SBR_OK;
 }
 
 void sbr_trace_free(sbr_trace_result* tr) {

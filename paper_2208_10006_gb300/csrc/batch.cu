@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch_delays(const BatchJobDev* _
             const int64_t slot = J->path_base + n + n0;
             const int m = paths.nb[slot];
             const d3 Pk = ld3(paths.pts + (slot * kKmax + (tx ? 0 : m - 1)) * 3);
-            const double ref = norm((tx ? T0 : R0) - Pk);
+            const double ref = dist_rn(tx ? T0 : R0, Pk);
             const double* el = tx ? J->tx_elem : J->rx_elem;
             for (int e = e0; e < e1; ++e) dst[(int64_t)e * path_cap + n] = el_delay(el + 3 * e, Pk, ref);
         } else {
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch_delays(const BatchJobDev* _
         }
     }
     (void)ne;
-    const double ref = norm(T0 - R0);
+    const double ref = dist_rn(T0, R0);
     for (int it = threadIdx.x; it < Nr * Nt; it += kBThreads) {
         const int q = it / Nt, p = it - q * Nt;
         dl[J->dl_base + it] = el_delay(J->tx_elem + 3 * p, ld3(J->rx_elem + 3 * q), ref);
@@ -275,11 +275,8 @@ __global__ void k_batch_status(const TraceCountersDev* __restrict__ cnt, int32_t
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 // ---------------------------------------------------------------- per-N launch data
-// direction table (the process-wide cache of the single-job trace) and alpha of
-// every subdivision used by a batch; alpha is kept for the process as well
+// alpha of every subdivision used by a batch, kept for the process
 struct NData {
-    const float4* dir_a = nullptr;
-    const float2* dir_b = nullptr;
     double alpha = 0.0;
 };
 std::mutex g_nmu;
@@ -292,7 +289,6 @@ sbr_status ndata(int N, cudaStream_t s, NData* out) {
     auto it = g_ndata.find({dev, N});
     if (it == g_ndata.end()) {
         NData d;
-        SBR_TRY(dir_table(N, &d.dir_a, &d.dir_b, s));
         double* da = nullptr;
         sbr_status st = dalloc_n(&da, 1, s);
         if (st == SBR_OK) st = launch_alpha(N, da, s);
@@ -430,6 +426,7 @@ sbr_status enqueue(sbr_batch* b, cudaStream_t s) {
         const int nj = wv.j1 - wv.j0;
         const BatchJobDev* jobs = b->d_jobs + wv.j0;
         BatchTraceWave tw{};
+        tw.ico = make_ico_lattice();
         tw.jobs = jobs;
         tw.ray_off = wv.d_ray_off;
         tw.n_jobs = nj;
@@ -637,8 +634,7 @@ sbr_status create(const sbr_bvh* const* scenes, const sbr_material* const* mats,
             J.R = (int32_t)R;
             J.K = jb.max_bounces;
             J.wave_job = i - wv.j0;
-            J.dir_a = nd.dir_a;
-            J.dir_b = nd.dir_b;
+            J.geo = make_geo_n(jb.subdiv_N);
             J.seq = b->seq + sq;
             sq += R * jb.max_bounces;
             const double al = jb.alpha > 0.0 ? jb.alpha : nd.alpha;

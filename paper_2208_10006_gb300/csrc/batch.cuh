@@ -1,6 +1,7 @@
 // Batched execution of many Tx-Rx jobs over several scenes: the device-side
 // job records shared by the batched trace, path, gain and synthesis kernels.
 #pragma once
+#include "geodesic_df.cuh"
 #include "sbr_internal.cuh"
 
 namespace sbr {
@@ -25,8 +26,7 @@ struct BatchJobDev {
     int32_t S;
     // rays of the job
     int32_t R, K, wave_job;      // wave_job: index of the job within its wave
-    const float4* dir_a;         // double-float launch directions of the job's N
-    const float2* dir_b;
+    GeoN geo;                    // subdivision of the launch grid (directions decoded per ray)
     int32_t* seq;                // [K][R] surface sequence (wave scratch)
     float tx_h[3], tx_l[3];      // Tx reference point, double-float
     float4 alpha;                // alpha hi, lo, alpha^2/3 hi, lo
@@ -66,6 +66,7 @@ struct BatchPathsDev {
 
 // Device buffers of one wave of the batched trace.
 struct BatchTraceWave {
+    IcoLattice ico;              // launch grid decoded per ray
     const BatchJobDev* jobs;     // the wave's jobs
     const int64_t* ray_off;      // [n_jobs + 1] first global ray of each job in the wave
     int32_t n_jobs;

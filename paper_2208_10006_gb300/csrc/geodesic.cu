@@ -1,12 +1,15 @@
-// Geodesic ray launching (Sec. II-A.1, Fig. 1): icosahedron tables, the
-// direction list, and alpha, the largest angle between directions joined by
+// Geodesic ray launching (Sec. II-A.1, Fig. 1): icosahedron tables (FP64
+// and the exact integer lattice form the trace kernels decode), the direction
+// list, and alpha, the largest angle between directions joined by
 // a sub-triangle edge, which sizes the reception sphere (Sec. II-A.3).
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 
 #include "dfloat.cuh"
 #include "geodesic.cuh"
+#include "geodesic_df.cuh"
 
 namespace sbr {
 
@@ -91,69 +94,52 @@ __global__ void k_alpha_store(const unsigned long long* best, double* alpha) {
     *alpha = __longlong_as_double((long long)*best);
 }
 
-__global__ void k_dir_table(const __grid_constant__ Ico ico, int N, int64_t R, float4* __restrict__ da,
-                            float2* __restrict__ db) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= R) return;
-    d3 d = geodesic_dir(ico, N, (uint32_t)i);
-    df x = df_from_double(d.x), y = df_from_double(d.y), z = df_from_double(d.z);
-    da[i] = make_float4(x.hi, y.hi, z.hi, x.lo);
-    db[i] = make_float2(y.lo, z.lo);
-}
-
-// direction tables by (device, N), kept for the process: repeated traces and
-// batches of the same subdivisions reuse them (24 B per ray each)
-std::mutex g_dir_mu;
-std::map<std::pair<int, int>, std::pair<float4*, float2*>> g_dir_tables;
-
 }  // namespace
 
-sbr_status dir_table(int32_t N, const float4** dir_a, const float2** dir_b, cudaStream_t s) {
-    std::lock_guard<std::mutex> lk(g_dir_mu);
-    int dev = 0;
-    SBR_TRY_CUDA(cudaGetDevice(&dev));
-    auto it = g_dir_tables.find({dev, N});
-    if (it == g_dir_tables.end()) {
-        float4* a = nullptr;
-        float2* b = nullptr;
-        SBR_TRY(dir_table_build(N, &a, &b, s));
-        // other streams may use the table next: finish building it now
-        SBR_TRY_CUDA(cudaStreamSynchronize(s));
-        it = g_dir_tables.emplace(std::make_pair(dev, N), std::make_pair(a, b)).first;
-    }
-    *dir_a = it->second.first;
-    *dir_b = it->second.second;
-    return SBR_OK;
+IcoLattice make_ico_lattice() {
+    const Ico ico = make_ico();
+    const double ph = (1.0 + std::sqrt(5.0)) / 2.0;
+    IcoLattice t{};
+    for (int v = 0; v < 12; ++v)
+        for (int k = 0; k < 3; ++k) {
+            const double x = ico.v[v][k];
+            const bool is_phi = std::fabs(std::fabs(x) - ph) < 1e-9;
+            const int sg = x > 0 ? 1 : (x < 0 ? -1 : 0);
+            t.A[v][k] = (int8_t)(is_phi ? 0 : sg);
+            t.B[v][k] = (int8_t)(is_phi ? sg : 0);
+        }
+    for (int e = 0; e < 30; ++e)
+        for (int k = 0; k < 2; ++k) t.e[e][k] = ico.e[e][k];
+    for (int f = 0; f < 20; ++f)
+        for (int k = 0; k < 3; ++k) t.f[f][k] = ico.f[f][k];
+    const df p = df_from_double(ph);
+    t.phi_hi = p.hi;
+    t.phi_lo = p.lo;
+    return t;
 }
 
-sbr_status dir_table_build(int32_t N, float4** dir_a, float2** dir_b, cudaStream_t s) {
-    int64_t R = 10 * (int64_t)N * N + 2;
-    float4* a = nullptr;
-    float2* b = nullptr;
-    SBR_TRY_CUDA(cudaMalloc(&a, sizeof(float4) * R));
-    if (cudaMalloc(&b, sizeof(float2) * R) != cudaSuccess) {
-        cudaFree(a);
-        set_error("direction table allocation failed");
-        return SBR_ERR_ALLOC;
-    }
-    Ico ico = make_ico();
-    ::sbr::note_launch(), k_dir_table<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(ico, N, R, a, b);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        cudaFree(a);
-        cudaFree(b);
-        set_error("direction table: %s", cudaGetErrorString(e));
-        return SBR_ERR_CUDA;
-    }
-    *dir_a = a;
-    *dir_b = b;
-    return SBR_OK;
+namespace {
+// the double-float directions the trace kernels launch, widened to FP64
+__global__ void k_dirs_df(const __grid_constant__ IcoLattice t, GeoN g, int64_t R, double* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R) return;
+    const df3 d = geodesic_dir_df(t, g, (uint32_t)i);
+    out[3 * i] = df_to_double(d.x); out[3 * i + 1] = df_to_double(d.y); out[3 * i + 2] = df_to_double(d.z);
 }
+}  // namespace
 
 sbr_status launch_dirs(int32_t N, double* dirs, cudaStream_t s) {
     int64_t R = 10 * (int64_t)N * N + 2;
-    Ico ico = make_ico();
-    ::sbr::note_launch(), k_dirs<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(ico, N, R, dirs);
+    // test hook: SBR_DIRS_DF=1 returns the double-float directions the trace
+    // kernels compute where they launch a ray (instead of the FP64 form)
+    const char* e = getenv("SBR_DIRS_DF");
+    if (e && e[0] == '1') {
+        ::sbr::note_launch(), k_dirs_df<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(make_ico_lattice(), make_geo_n(N), R,
+                                                                                 dirs);
+    } else {
+        Ico ico = make_ico();
+        ::sbr::note_launch(), k_dirs<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(ico, N, R, dirs);
+    }
     SBR_TRY_CUDA(cudaGetLastError());
     return SBR_OK;
 }

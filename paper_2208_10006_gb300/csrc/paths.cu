@@ -78,8 +78,9 @@ struct RefineArgs {
     const float4* tris;
     double tx[3];
     const double* rx;
-    const int32_t* seqf;   // [K][R] faces hit by each ray (refinement hints), or null
-    int64_t R;
+    const int32_t* seqf;   // [K][R] faces hit by each traced ray (refinement hints), or null
+    int64_t R;             // rays of the trace (stride of seqf)
+    int64_t ray0;          // first ray id of the trace
     // raw outputs, key order
     uint32_t* valid;
     int32_t* rx_o;
@@ -135,7 +136,7 @@ __global__ void k_refine_solo(const __grid_constant__ RefineArgs a) {
     }
     const RefineScene sc{a.tri, a.nrm, a.s_off, a.s_tri, a.S, a.nodes, a.tris};
     const RefineOut o{a.nb_o, a.surf_o, a.face_o, a.pts_o, a.L_o, a.aod_o, a.aoa_o, a.ray_o, a.dist_o, a.jones_o};
-    const int32_t* hint = a.seqf + (uint32_t)(v & 0xffffffffull);
+    const int32_t* hint = a.seqf + ((int64_t)(uint32_t)(v & 0xffffffffull) - a.ray0);
     const d3 Rx = have ? ld3(a.rx + 3 * rx_id) : mk3(0, 0, 0);
     bool ok = refine_key<true>(lane, m, seq, v, sc, mk3(a.tx[0], a.tx[1], a.tx[2]), Rx, o, have ? i : 0, hint, a.R);
     if (!have) return;
@@ -335,7 +336,8 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     for (int k = 0; k < 3; ++k) a.tx[k] = tr->params.tx[k];
     a.rx = tr->rx;
     a.seqf = tr->seqf;
-    a.R = tr->R;
+    a.R = tr->Rr;
+    a.ray0 = tr->ray0;
     int64_t nn = std::max<int64_t>(n, 1);
     uint32_t* valid;
     uint32_t* pos;

@@ -77,11 +77,6 @@ void note_launch();
 // test-only fault injection (SBR_FAULT=alloc|timeout)
 enum { kFaultNone = 0, kFaultAlloc = 1, kFaultTimeout = 2 };
 int fault_mode();
-// geodesic directions of subdivision N as double-float, built once per (device, N)
-// and kept for the process: dir_a[i] = (hi.x, hi.y, hi.z, lo.x), dir_b[i] = (lo.y, lo.z)
-sbr_status dir_table(int32_t N, const float4** dir_a, const float2** dir_b, cudaStream_t s);
-// a new direction table of subdivision N owned by the caller (cudaFree both)
-sbr_status dir_table_build(int32_t N, float4** dir_a, float2** dir_b, cudaStream_t s);
 // adds n to the launch count (kernel nodes of a CUDA graph launch; negative to
 // take back launches that were only captured)
 void note_launches(long long n);
@@ -166,13 +161,14 @@ struct TraceCountersDev {
 struct sbr_trace_result {
     int device = 0;
     sbr_trace_params params{};
-    int64_t R = 0;
+    int64_t R = 0;                          // rays of the launch grid
+    int64_t ray0 = 0, Rr = 0;               // traced id range [ray0, ray0 + Rr)
     int32_t n_rx = 0;
     double* rx = nullptr;                   // [n_rx*3] own copy
     double* d_alpha = nullptr;              // [1]
     int32_t table_log2 = 0;
     int32_t df_from = 0;                    // first bounce traced depth-first (K + 1: none)
-    int32_t* seqf = nullptr;                // [K][R] face hit by each ray at each bounce
+    int32_t* seqf = nullptr;                // [K][Rr] face hit by each traced ray at each bounce
     uint32_t* ht_state = nullptr;           // [cap]
     uint32_t* ht_key = nullptr;             // [cap * kKeyWords]
     unsigned long long* ht_val = nullptr;   // [cap]
@@ -225,6 +221,12 @@ sbr_status launch_alpha(int32_t N, double* alpha, cudaStream_t s);
 sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S, sbr_bvh* b, cudaStream_t s,
                      bool sah_top);
 sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s);
+// the deduplicated records of a trace (sbr_trace_entries), synchronous
+sbr_status trace_entries_run(const sbr_trace_result* tr, uint32_t* keys, unsigned long long* vals, int64_t cap,
+                             int64_t* n_out, cudaStream_t s);
+// a trace result built from records (sbr_trace_merge)
+sbr_status trace_merge_run(sbr_trace_result* tr, const uint32_t* keys, const unsigned long long* vals, int64_t n,
+                           cudaStream_t s);
 sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list* pl,
                      cudaStream_t s);
 sbr_status gains_run(const sbr_path_list* pl, const sbr_material* mats, int32_t S,

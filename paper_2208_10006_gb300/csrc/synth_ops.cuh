@@ -24,16 +24,20 @@ constexpr double kInvC0 = 1.0 / kC0;
 // (1 - j 2 pi lo) to second order in lo (< 1e-13), with the FP32 sine and
 // cosine of pi x (sincospif) for the hi part. FP64 is used for 7 operations
 // only: this GPU's FP64 rate is a small fraction of its FP32 rate.
+//
+// Every operation is written with an explicit rounding intrinsic, so that the
+// compiler cannot contract a multiply and an add differently in the kernels
+// that share these functions (their results must agree bit for bit).
 __device__ __forceinline__ float2 synth_weight(float2 g, double f, double L) {
-    const double cyc = f * L * kInvC0;
-    const double r = cyc - floor(cyc);
-    const float hi = (float)r;
-    const float lo = (float)(r - (double)hi);
+    const double cyc = __dmul_rn(__dmul_rn(f, L), kInvC0);
+    const double r = __dsub_rn(cyc, floor(cyc));
+    const float hi = __double2float_rn(r);
+    const float lo = __double2float_rn(__dsub_rn(r, (double)hi));
     float s, c;
-    sincospif(-2.0f * hi, &s, &c);
-    const float d = -6.283185307179586f * lo;   // exp(j d) ~ 1 + j d
-    const float cr = fmaf(-s, d, c), ci = fmaf(c, d, s);
-    return make_float2(g.x * cr - g.y * ci, g.x * ci + g.y * cr);
+    sincospif(__fmul_rn(-2.0f, hi), &s, &c);
+    const float d = __fmul_rn(-6.283185307179586f, lo);   // exp(j d) ~ 1 + j d
+    const float cr = __fmaf_rn(-s, d, c), ci = __fmaf_rn(c, d, s);
+    return make_float2(__fmaf_rn(g.x, cr, __fmul_rn(-g.y, ci)), __fmaf_rn(g.x, ci, __fmul_rn(g.y, cr)));
 }
 
 // the FP16 form's per-frequency scale from the largest weight component
@@ -44,12 +48,16 @@ __device__ __forceinline__ float synth_scale(float m) {
     return ldexpf(1.f, -e);
 }
 
-// element delay |E - P| - ref with ref = |E0 - P| computed once per path
-// (FP64, then rounded to FP32)
-__device__ __forceinline__ float el_delay(const double* elem, d3 P, double ref) {
-    return (float)(norm(ld3(elem) - P) - ref);
+// |a - b| in FP64 with a fixed operation sequence
+__device__ __forceinline__ double dist_rn(d3 a, d3 b) {
+    const double x = __dsub_rn(a.x, b.x), y = __dsub_rn(a.y, b.y), z = __dsub_rn(a.z, b.z);
+    return __dsqrt_rn(__fma_rn(z, z, __fma_rn(y, y, __dmul_rn(x, x))));
 }
 
-inline int64_t synth_pad4(int64_t n) { return (n + 3) & ~(int64_t)3; }
+// element delay |E - P| - ref, ref = |E0 - P| = dist_rn(E0, P) computed once
+// per path (FP64, then rounded to FP32)
+__device__ __forceinline__ float el_delay(const double* elem, d3 P, double ref) {
+    return __double2float_rn(__dsub_rn(dist_rn(ld3(elem), P), ref));
+}
 
 }  // namespace sbr

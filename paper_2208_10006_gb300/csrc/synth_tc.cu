@@ -629,14 +629,14 @@ __global__ void k_tc_prep(const __grid_constant__ TcPrep a) {
             if (n < nrefl) {
                 const int i = n + n0, m = a.nb[i];
                 const d3 P = ld3(a.pts + ((int64_t)i * kKmax + (tx ? 0 : m - 1)) * 3);
-                const double ref = norm((tx ? a.T0 : ld3(a.R0)) - P);
+                const double ref = dist_rn(tx ? a.T0 : ld3(a.R0), P);
                 v = el_delay((tx ? a.tx_elem : a.rx_elem) + 3 * e, P, ref);
             }
             (tx ? a.dtT : a.drT)[u] = v;
         } else {
             const int64_t u = t - n_dt - n_dr;
             const int q = (int)(u / a.Nt), p = (int)(u - (int64_t)q * a.Nt);
-            a.dlos[u] = el_delay(a.tx_elem + 3 * p, ld3(a.rx_elem + 3 * q), norm(a.T0 - ld3(a.R0)));
+            a.dlos[u] = el_delay(a.tx_elem + 3 * p, ld3(a.rx_elem + 3 * q), dist_rn(a.T0, ld3(a.R0)));
         }
     }
 }

@@ -30,10 +30,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <cstring>
 
 #include "batch.cuh"
 #include "dfloat.cuh"
 #include "geodesic.cuh"
+#include "geodesic_df.cuh"
 
 namespace sbr {
 namespace {
@@ -63,10 +65,11 @@ struct TraceArgs {
     const float* rx_root;
     int32_t n_rx;
     const float4* alpha_df;  // (alpha hi, lo, alpha^2/3 hi, lo)
-    const float4* dir_a;     // launch directions, double-float
-    const float2* dir_b;
+    IcoLattice ico;          // launch grid: directions decoded per ray in double-float
+    GeoN geo;                // its subdivision constants
     int N, K, bounce;
-    int64_t R;
+    int64_t R;               // rays of the launch grid
+    int64_t ray0, Rr;        // the traced id range [ray0, ray0 + Rr) (the whole grid by default)
     // launch order of the rays: the vertex and edge rays first, then the 20
     // faces' interior rays face by face in the order face_order (their ids
     // stay the geodesic ids)
@@ -87,10 +90,10 @@ struct TraceArgs {
     TraceCountersDev* cnt;
 };
 
-// geodesic id of the i-th ray launched
+// geodesic id of the i-th ray launched (a range trace launches its ids in order)
 __device__ __forceinline__ uint32_t pool_ray(const TraceArgs& a, unsigned long long i) {
     const int64_t r = (int64_t)i - a.pool_pre;
-    if (r < 0 || a.pool_face == 0) return (uint32_t)i;
+    if (r < 0 || a.pool_face == 0) return (uint32_t)(a.ray0 + (int64_t)i);
     const int64_t k = r / a.pool_face;
     return (uint32_t)(a.pool_pre + (int64_t)a.face_order[k] * a.pool_face + (r - k * a.pool_face));
 }
@@ -483,7 +486,7 @@ __device__ void receive(const TraceArgs& a, int bounce, const df3& o, const df3&
                     key[0] = (uint32_t)rx_id;
                     key[1] = (uint32_t)bounce;
                     for (int k = 0; k < kKmax; ++k)
-                        key[2 + k] = k < bounce ? (uint32_t)a.seq[(int64_t)k * a.R + ray] : 0xffffffffu;
+                        key[2 + k] = k < bounce ? (uint32_t)a.seq[(int64_t)k * a.Rr + (ray - a.ray0)] : 0xffffffffu;
                     unsigned long long val = ((unsigned long long)__float_as_uint(dist) << 32) | ray;
                     ht_insert(a, key, val);
                     atomicAdd(&a.cnt->candidates, 1ull);
@@ -563,7 +566,7 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
     int stack[kStack];
     unsigned visits = 0, tests = 0, rx_visits = 0, edge = 0;
     const int lane = threadIdx.x & 31;
-    const unsigned long long n_in = a.bounce == 0 ? (unsigned long long)a.R : *a.n_in;
+    const unsigned long long n_in = a.bounce == 0 ? (unsigned long long)a.Rr : *a.n_in;
     for (;;) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(a.work, 32ull);
@@ -581,9 +584,7 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
                 ray = pool_ray(a, i);
                 o = df3{df_make(a.tx_h[0], a.tx_l[0]), df_make(a.tx_h[1], a.tx_l[1]),
                         df_make(a.tx_h[2], a.tx_l[2])};
-                float4 da = __ldg(a.dir_a + ray);
-                float2 db = __ldg(a.dir_b + ray);
-                d = df3{df_make(da.x, da.w), df_make(da.y, db.x), df_make(da.z, db.y)};
+                d = geodesic_dir_df(a.ico, a.geo, ray);
                 L = df_make(0.f, 0.f);
                 prev = -1;
             } else {
@@ -626,8 +627,8 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
                 out.Ll = L2.lo;
                 out.ray = ray;
                 out.prev = surf;
-                a.seq[(int64_t)a.bounce * a.R + ray] = surf;
-                a.seqf[(int64_t)a.bounce * a.R + ray] = __float_as_int(__ldg(a.tris + 3 * j + 1).w);
+                a.seq[(int64_t)a.bounce * a.Rr + (ray - a.ray0)] = surf;
+                a.seqf[(int64_t)a.bounce * a.Rr + (ray - a.ray0)] = __float_as_int(__ldg(a.tris + 3 * j + 1).w);
                 survive = true;
             }
         }
@@ -683,7 +684,7 @@ k_trace_df(const __grid_constant__ TraceArgs a) {
     unsigned visits = 0, tests = 0, rx_visits = 0, edge = 0;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const unsigned long long n_in = a.bounce == 0 ? (unsigned long long)a.R : *a.n_in;
+    const unsigned long long n_in = a.bounce == 0 ? (unsigned long long)a.Rr : *a.n_in;
     df3 o{}, d{};
     df L = df_make(0.f, 0.f);
     uint32_t ray = 0;
@@ -701,13 +702,11 @@ k_trace_df(const __grid_constant__ TraceArgs a) {
                 const unsigned long long i = base + __popc(need & ((1u << lane) - 1u));
                 if (i < n_in) {
                     if (a.bounce == 0) {
+                        // launch (Sec. II-A.1): the geodesic direction decoded from the id
                         ray = pool_ray(a, i);
                         o = df3{df_make(a.tx_h[0], a.tx_l[0]), df_make(a.tx_h[1], a.tx_l[1]),
                                 df_make(a.tx_h[2], a.tx_l[2])};
-                        // streamed once: evict-first, so that L1 keeps the BVH nodes
-                        float4 da = __ldcs(a.dir_a + ray);
-                        float2 db = __ldcs(a.dir_b + ray);
-                        d = df3{df_make(da.x, da.w), df_make(da.y, db.x), df_make(da.z, db.y)};
+                        d = geodesic_dir_df(a.ico, a.geo, ray);
                         L = df_make(0.f, 0.f);
                         prev = -1;
                     } else {
@@ -751,8 +750,8 @@ k_trace_df(const __grid_constant__ TraceArgs a) {
                 o = o2;
                 L = df_add(L, t);
                 // per-bounce records, written once and read after the launch: streaming stores
-                __stcs(&a.seq[(int64_t)bounce * a.R + ray], surf);
-                __stcs(&a.seqf[(int64_t)bounce * a.R + ray], __float_as_int(__ldg(a.tris + 3 * j + 1).w));
+                __stcs(&a.seq[(int64_t)bounce * a.Rr + (ray - a.ray0)], surf);
+                __stcs(&a.seqf[(int64_t)bounce * a.Rr + (ray - a.ray0)], __float_as_int(__ldg(a.tris + 3 * j + 1).w));
                 prev = surf;
                 bounce += 1;
                 entered = bounce;
@@ -802,6 +801,7 @@ struct JobScene {
 };
 
 struct BatchTraceArgs {
+    IcoLattice ico;
     const BatchJobDev* jobs;
     const int64_t* ray_off;
     int32_t n_jobs;
@@ -848,9 +848,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace_batch(const __grid_cons
                 ray = (uint32_t)((int64_t)i - __ldg(a.ray_off + job));
                 o = df3{df_make(J->tx_h[0], J->tx_l[0]), df_make(J->tx_h[1], J->tx_l[1]),
                         df_make(J->tx_h[2], J->tx_l[2])};
-                float4 da = __ldg(J->dir_a + ray);
-                float2 db = __ldg(J->dir_b + ray);
-                d = df3{df_make(da.x, da.w), df_make(da.y, db.x), df_make(da.z, db.y)};
+                d = geodesic_dir_df(a.ico, J->geo, ray);
                 L = df_make(0.f, 0.f);
                 prev = -1;
             } else {
@@ -960,9 +958,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8) k_trace_batch_df(const __gri
                     ray = (uint32_t)((int64_t)i - __ldg(a.ray_off + job));
                     o = df3{df_make(J->tx_h[0], J->tx_l[0]), df_make(J->tx_h[1], J->tx_l[1]),
                             df_make(J->tx_h[2], J->tx_l[2])};
-                    float4 da = __ldg(J->dir_a + ray);
-                    float2 db = __ldg(J->dir_b + ray);
-                    d = df3{df_make(da.x, da.w), df_make(da.y, db.x), df_make(da.z, db.y)};
+                    d = geodesic_dir_df(a.ico, J->geo, ray);
                     L = df_make(0.f, 0.f);
                     prev = -1;
                     bounce = 0;
@@ -1062,6 +1058,44 @@ __global__ void k_init_table(uint32_t* state, unsigned long long* val, size_t ca
     val[i] = ~0ull;
 }
 
+// ---------------------------------------------------------------- records of a trace
+// The deduplicated receptions as plain records (keys, packed (dist, ray)), and
+// a table rebuilt from records of several traces with the same insertion rule.
+__global__ void k_entries(const uint32_t* __restrict__ state, const uint32_t* __restrict__ key,
+                          const unsigned long long* __restrict__ val, size_t cap_t, uint32_t* __restrict__ out_k,
+                          unsigned long long* __restrict__ out_v, int64_t cap, unsigned long long* count) {
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool full = s < cap_t && state[s] == 2u;
+    const unsigned m = __ballot_sync(0xffffffffu, full);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!full) return;
+    const int64_t pos = (int64_t)(base + __popc(m & ((1u << lane) - 1u)));
+    if (pos >= cap) return;
+    for (int k = 0; k < kKeyWords; ++k) out_k[pos * kKeyWords + k] = key[s * kKeyWords + k];
+    out_v[pos] = val[s];
+}
+
+struct MergeArgs {
+    uint32_t* ht_state;
+    uint32_t* ht_key;
+    unsigned long long* ht_val;
+    uint32_t ht_mask;
+    TraceCountersDev* cnt;
+};
+
+__global__ void k_merge(const __grid_constant__ MergeArgs a, const uint32_t* __restrict__ keys,
+                        const unsigned long long* __restrict__ vals, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t key[kKeyWords];
+        for (int k = 0; k < kKeyWords; ++k) key[k] = keys[i * kKeyWords + k];
+        ht_insert(a, key, vals[i]);
+    }
+}
+
 // Launch order of the face rays: by the height (z) of the face's centroid on
 // the icosahedron, lowest first. Rays toward the ground and the facades take
 // several reflections and rays toward the sky end after one segment; with the
@@ -1119,6 +1153,7 @@ sbr_status batch_trace_wave(const BatchTraceWave& w, int blocks_per_sm, cudaStre
     }
     const int grid = per_sm * sm_count();
     BatchTraceArgs a{};
+    a.ico = w.ico;
     a.jobs = w.jobs;
     a.ray_off = w.ray_off;
     a.n_jobs = w.n_jobs;
@@ -1153,7 +1188,7 @@ sbr_status batch_trace_wave(const BatchTraceWave& w, int blocks_per_sm, cudaStre
 sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     const sbr_trace_params& p = tr->params;
     const int K = p.max_bounces;
-    const int64_t R = tr->R;
+    const int64_t R = tr->Rr;   // rays traced: the id range [ray0, ray0 + Rr)
     size_t cap = (size_t)1 << tr->table_log2;
     SBR_TRY(dalloc_n(&tr->ht_state, cap, s));
     SBR_TRY(dalloc_n(&tr->ht_key, cap * kKeyWords, s));
@@ -1179,9 +1214,6 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     }
     // receiver BVH
     if (tr->n_rx > 0) SBR_TRY(build_lbvh(rxbox, tr->n_rx, 0.0f, 1, &rxb, rx_depth, s));
-    const float4* dir_a = nullptr;
-    const float2* dir_b = nullptr;
-    SBR_TRY(dir_table(p.subdiv_N, &dir_a, &dir_b, s));
     RayRec *q0 = nullptr, *q1 = nullptr;
     int32_t* seq = nullptr;
     if (K > 0) {
@@ -1204,12 +1236,17 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     a.rx_root = rxb.d_root;
     a.n_rx = tr->n_rx;
     a.alpha_df = alpha_df;
-    a.dir_a = dir_a;
-    a.dir_b = dir_b;
+    a.ico = make_ico_lattice();
+    a.geo = make_geo_n(p.subdiv_N);
     a.N = p.subdiv_N;
     a.K = K;
-    a.R = R;
-    set_pool_order(p.subdiv_N, &a);
+    a.R = tr->R;
+    a.ray0 = tr->ray0;
+    a.Rr = R;
+    // the whole grid is launched face by face (sky-facing faces last); a range
+    // trace launches its ids in order
+    if (tr->ray0 == 0 && R == tr->R) set_pool_order(p.subdiv_N, &a);
+    else a.pool_pre = R, a.pool_face = 0;
     for (int k = 0; k < 3; ++k) {
         df x = df_from_double(p.tx[k]);
         a.tx_h[k] = x.hi;
@@ -1266,6 +1303,59 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
         dfree(rx_df, s);
     }
     dfree(alpha_df, s);
+    return SBR_OK;
+}
+
+}  // namespace sbr
+
+namespace sbr {
+
+sbr_status trace_entries_run(const sbr_trace_result* tr, uint32_t* keys, unsigned long long* vals, int64_t cap,
+                             int64_t* n_out, cudaStream_t s) {
+    const size_t cap_t = (size_t)1 << tr->table_log2;
+    unsigned long long* count = nullptr;
+    SBR_TRY(dalloc_n(&count, 1, s));
+    SBR_TRY_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s));
+    ::sbr::note_launch(), k_entries<<<(unsigned)((cap_t + 255) / 256), 256, 0, s>>>(
+        tr->ht_state, tr->ht_key, tr->ht_val, cap_t, keys, vals, cap, count);
+    SBR_TRY_CUDA(cudaGetLastError());
+    unsigned long long h_count = 0;
+    unsigned h_status = 0;
+    SBR_TRY_CUDA(cudaMemcpyAsync(&h_count, count, sizeof h_count, cudaMemcpyDeviceToHost, s));
+    SBR_TRY_CUDA(cudaMemcpyAsync(&h_status, &tr->cnt->status, sizeof h_status, cudaMemcpyDeviceToHost, s));
+    SBR_TRY_CUDA(cudaStreamSynchronize(s));
+    dfree(count, s);
+    SBR_TRY(status_from_bits(h_status));
+    *n_out = (int64_t)h_count;
+    if ((int64_t)h_count > cap) {
+        set_error("sbr_trace_entries: %lld records, buffers hold %lld", (long long)h_count, (long long)cap);
+        return SBR_ERR_CAPACITY;
+    }
+    return SBR_OK;
+}
+
+sbr_status trace_merge_run(sbr_trace_result* tr, const uint32_t* keys, const unsigned long long* vals, int64_t n,
+                           cudaStream_t s) {
+    const size_t cap = (size_t)1 << tr->table_log2;
+    SBR_TRY(dalloc_n(&tr->ht_state, cap, s));
+    SBR_TRY(dalloc_n(&tr->ht_key, cap * kKeyWords, s));
+    SBR_TRY(dalloc_n(&tr->ht_val, cap, s));
+    SBR_TRY(dalloc_n(&tr->cnt, 1, s));
+    SBR_TRY_CUDA(cudaMemsetAsync(tr->cnt, 0, sizeof(TraceCountersDev), s));
+    ::sbr::note_launch(), k_init_table<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(tr->ht_state, tr->ht_val, cap);
+    SBR_TRY_CUDA(cudaGetLastError());
+    if (tr->params.alpha > 0.0) {
+        unsigned long long bits;
+        const double al = tr->params.alpha;
+        memcpy(&bits, &al, sizeof bits);
+        SBR_TRY(set_u64(reinterpret_cast<unsigned long long*>(tr->d_alpha), bits, s));
+    }
+    if (n > 0) {
+        MergeArgs a{tr->ht_state, tr->ht_key, tr->ht_val, (uint32_t)(cap - 1), tr->cnt};
+        const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 8 * (int64_t)sm_count());
+        ::sbr::note_launch(), k_merge<<<grid, 256, 0, s>>>(a, keys, vals, n);
+        SBR_TRY_CUDA(cudaGetLastError());
+    }
     return SBR_OK;
 }
 

@@ -63,7 +63,7 @@ def test_ctypes_struct_layouts_match_the_header(tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("no C compiler")
     from paper_2208_10006_gb300 import _lib
-    checks = {"sbr_trace_params": (_lib.TraceParams, ["tx", "rx_xyz", "alpha", "flags"]),
+    checks = {"sbr_trace_params": (_lib.TraceParams, ["tx", "rx_xyz", "alpha", "flags", "ray_begin", "ray_end"]),
               "sbr_trace_counters": (_lib.TraceCounters, ["near_edge_hits", "queue", "alpha", "bounce_ms"]),
               "sbr_path_info": (_lib.PathInfo, ["n_paths", "status"]),
               "sbr_batch_job": (_lib.BatchJob, ["tx", "alpha", "F", "freqs_hz", "H"]),

@@ -54,6 +54,23 @@ def test_launch_dirs_and_alpha(sbr, N):
     assert abs(float(a.cpu()[0]) - oracle.alpha(N)) <= 1e-14 * oracle.alpha(N)
 
 
+@pytest.mark.parametrize("N", [1, 2, 3, 7, 50, 101, 1000])
+def test_directions_decoded_in_the_trace_kernels(sbr, N, monkeypatch):
+    # the double-float directions the trace kernels decode from the ray id
+    # (exact integer lattice point, normalised in double-float) against the
+    # oracle's FP64 directions, every ray: unit vectors within 1e-13 (the
+    # double-float ray state carries ~2^-48)
+    monkeypatch.setenv("SBR_DIRS_DF", "1")
+    d, _ = sbr.launch_dirs(N, with_alpha=False)
+    monkeypatch.delenv("SBR_DIRS_DF")
+    ref = oracle.geodesic_dirs(N)
+    dd = d.cpu().numpy()
+    assert dd.shape == ref.shape == (10 * N * N + 2, 3)
+    err = np.abs(dd - ref).max()
+    print("N", N, "double-float directions: max |d - d_oracle| =", err)
+    assert err < 1e-13
+
+
 @pytest.mark.parametrize("name", list(SCENES))
 def test_paths_and_gains_match_oracle(sbr, name):
     sc = SCENES[name]()
