@@ -51,20 +51,19 @@ RAY_REC_BYTES = 64      # one queued ray record (origin, direction, L, id, last 
 ALG_BYTES_PER_RAY_BOUNCE = 2 * RAY_REC_BYTES
 # DRAM bytes of one k_trace_df launch on the headline workload (N = 1000), from
 # one ncu capture of the launch (dram__bytes_read.sum + dram__bytes_write.sum)
-TRACE_DRAM_BYTES = 260_538_112 + 85_420_800
+TRACE_DRAM_BYTES = 21_302_016 + 82_188_288
 # warp instructions issued by one k_trace_df launch on the same workload, from
 # one ncu capture (smsp__inst_executed.sum). The issue peak is one warp
 # instruction per clock on each of the 4 schedulers of the 152 SMs
-TRACE_WARP_INST = 2_255_353_276
+TRACE_WARP_INST = 2_378_361_015
 # SHA-256 (first 16 hex digits) of the trace kernel's source and the local
 # headers it includes, as they were when the two counters above were captured.
 # Any later edit changes it, and the counters are then reported as null
 # (unmeasured) instead of describing a kernel that no longer exists.
-TRACE_COUNTERS_SRC = "5c26724f3077f218"
+TRACE_COUNTERS_SRC = "8bf637f26ab34fda"
 SM_COUNT = 152
 SCHEDULERS_PER_SM = 4
 SEQ_BYTES = 8           # surface id and face id appended per reflection
-DIR_BYTES = 24          # launch direction of a ray, double-float
 
 
 def trace_source_hash() -> str:
@@ -341,8 +340,9 @@ def run_gpu(args):
     sc = scenes.config2(N=N_w)
     d = sbr.scene_to_device(sc)
     N, K = sc["N"], sc["K"]
-    _, a = sbr.launch_dirs(N, with_dirs=False)
-    alpha = float(a.cpu()[0])
+    # alpha = 0: every trace computes the reception-sphere angle of its launch
+    # grid itself, inside the timed step (Sec. II-A.3)
+    alpha = 0.0
     fc = float(sc["freqs"][0])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
@@ -394,9 +394,10 @@ def run_gpu(args):
         rb += stats["ray_bounces"]
         q = stats["queue"]
         bounce_ms += sum(stats["bounce_ms"][:K + 1])
-        # depth first from bounce 0: each ray's launch direction is read once and
-        # each reflection appends its surface and face id; no ray record goes through memory
-        bounce_bytes += DIR_BYTES * q[0] + SEQ_BYTES * sum(q[1:K + 1])
+        # depth first from bounce 0: each ray's launch direction is decoded from
+        # its id and each reflection appends its surface and face id; no ray
+        # record goes through memory
+        bounce_bytes += SEQ_BYTES * sum(q[1:K + 1])
         del out
     torch.cuda.synchronize()
     clk = clocks.stop(window=(t_clk0, time.perf_counter()))
@@ -543,7 +544,8 @@ def run_gpu(args):
                                  "x ray-bounces per launch",
             "algorithmic_bytes_per_launch": ALG_BYTES_PER_RAY_BOUNCE * rb / args.steps,
             "streamed_bytes_per_launch": bounce_bytes / args.steps,
-            "streamed_bytes": "24 B launch direction per ray + 8 B surface and face id per reflection",
+            "streamed_bytes": "8 B surface and face id per reflection (launch directions are decoded "
+                              "from the ray id)",
             "avg_launch_ms": bounce_ms / args.steps,
             "kernel_share_of_step": bounce_ms / sum(times), "l2": l2,
             "issue": issue_roofline(bounce_ms / args.steps, clk, N)}
@@ -820,13 +822,9 @@ def bench_batched(sbr, torch, args):
         ts.append(e0.elapsed_time(e1))
     n_paths, status, info = b.query()
     t_b = min(ts) / 1e3
-    # per-pair loop: the single-job calls for every job, FP16x3 synthesis; alpha of
-    # each N computed once beforehand (the batch caches it too) and the launch
-    # direction tables already cached by the batch
-    alphas = {}
-    for j in jdev:
-        if j["N"] not in alphas:
-            alphas[j["N"]] = float(sbr.launch_dirs(j["N"], with_dirs=False)[1].cpu()[0])
+    # per-pair loop: the single-job calls for every job, FP16x3 synthesis; each
+    # trace computes the alpha of its launch grid (the batch computes one per
+    # distinct N when it is created)
     Hs = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -836,7 +834,7 @@ def bench_batched(sbr, torch, args):
     for j in jdev:
         bvh, mats = sdev[j["scene"]]
         rx = torch.as_tensor(np.asarray(j["rx"], dtype=np.float64).reshape(1, 3), device=dev)
-        tr = sbr.trace(bvh, j["tx"], rx, j["N"], j["K"], alpha=alphas[j["N"]])
+        tr = sbr.trace(bvh, j["tx"], rx, j["N"], j["K"])
         pl = sbr.paths(tr, bvh)
         g = sbr.path_gains(pl, mats, j["freqs"], j["gamma"], None,
                            sbr.POL_V if j["pol"] == "V" else sbr.POL_H)

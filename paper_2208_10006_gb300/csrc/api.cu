@@ -249,7 +249,7 @@ sbr_status sbr_trace(const sbr_bvh* b, const sbr_trace_params* p, sbr_trace_resu
     if (st == SBR_OK) st = dalloc_n(&tr->d_alpha, 1, s);
     // a given alpha is stored by the trace's set-up launch; the default one
     // (alpha = 0) is computed from the launch grid first
-    if (st == SBR_OK && !(p->alpha > 0.0)) st = launch_alpha(p->subdiv_N, tr->d_alpha, s);
+    if (st == SBR_OK && !(p->alpha > 0.0)) st = launch_alpha_fast(p->subdiv_N, tr->d_alpha, s);
     if (st == SBR_OK) st = trace_run(b, tr, s);
     if (st != SBR_OK) {
         sbr_trace_free(tr);
@@ -354,7 +354,7 @@ sbr_status sbr_trace_merge(const sbr_trace_params* p, const uint32_t* keys, cons
         }
     }
     if (st == SBR_OK) st = dalloc_n(&tr->d_alpha, 1, s);
-    if (st == SBR_OK && !(p->alpha > 0.0)) st = launch_alpha(p->subdiv_N, tr->d_alpha, s);
+    if (st == SBR_OK && !(p->alpha > 0.0)) st = launch_alpha_fast(p->subdiv_N, tr->d_alpha, s);
     if (st == SBR_OK) st = trace_merge_run(tr, keys, reinterpret_cast<const unsigned long long*>(vals), n, s);
     if (st != SBR_OK) {
         sbr_trace_free(tr);

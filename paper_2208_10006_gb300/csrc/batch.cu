@@ -291,7 +291,7 @@ sbr_status ndata(int N, cudaStream_t s, NData* out) {
         NData d;
         double* da = nullptr;
         sbr_status st = dalloc_n(&da, 1, s);
-        if (st == SBR_OK) st = launch_alpha(N, da, s);
+        if (st == SBR_OK) st = launch_alpha_fast(N, da, s);
         if (st == SBR_OK && cudaMemcpyAsync(&d.alpha, da, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             st = SBR_ERR_CUDA;
         if (st == SBR_OK && cudaStreamSynchronize(s) != cudaSuccess) st = SBR_ERR_CUDA;

@@ -128,6 +128,73 @@ __global__ void k_dirs_df(const __grid_constant__ IcoLattice t, GeoN g, int64_t 
 }
 }  // namespace
 
+namespace {
+// squared chord |u - v|^2 of two unit directions in double-float (no
+// cancellation: the differences of the components are formed first)
+__device__ __forceinline__ df chord2(const df3& u, const df3& v) {
+    const df x = df_sub(u.x, v.x), y = df_sub(u.y, v.y), z = df_sub(u.z, v.z);
+    return df_fma(df_fma(df_mul(x, x), y, y), z, z);
+}
+
+// the larger of two double-float values (their hi words first, then lo)
+__device__ __forceinline__ df df_max(df a, df b) { return (b.hi > a.hi || (b.hi == a.hi && b.lo > a.lo)) ? b : a; }
+
+// alpha over the sub-triangle edges of one face: every face is the image of
+// face 0 under a rotation of the icosahedron (an isometry that maps the
+// lattice of one face onto that of another), so the largest edge angle is the
+// same on all 20. One thread per upward sub-triangle (i, j) - (i+1, j) -
+// (i, j+1), i + j <= N-1, whose three edges cover every edge of the face; the
+// largest squared chord is reduced in double-float and stored as FP64 bits (a
+// monotone order for non-negative values), and alpha = 2 asin(chord / 2)
+// follows in FP64 once.
+__global__ void k_alpha_df(const __grid_constant__ IcoLattice t, int N, int64_t per_face,
+                           unsigned long long* __restrict__ best) {
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    df m{0.f, 0.f};
+    if (l < per_face) {
+        // row i holds N - i points (j = 0..N-1-i); rows before i hold i(2N+1-i)/2
+        auto before = [N](int64_t ii) { return ii * (2 * (int64_t)N + 1 - ii) / 2; };
+        const float b2 = 2.0f * (float)N + 1.0f;
+        int64_t i = (int64_t)floorf(0.5f * (b2 - sqrtf(fmaxf(b2 * b2 - 8.0f * (float)l, 0.f))));
+        i = i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
+        while (i > 0 && before(i) > l) --i;
+        while (i < N - 1 && before(i + 1) <= l) ++i;
+        const int j = (int)(l - before(i));
+        int PA[3], PB[3];
+        face_point(t, 0, N, (int)i, j, PA, PB);
+        const df3 p00 = lattice_unit_df(t, PA, PB);
+        face_point(t, 0, N, (int)i + 1, j, PA, PB);
+        const df3 p10 = lattice_unit_df(t, PA, PB);
+        face_point(t, 0, N, (int)i, j + 1, PA, PB);
+        const df3 p01 = lattice_unit_df(t, PA, PB);
+        m = df_max(chord2(p00, p10), df_max(chord2(p00, p01), chord2(p10, p01)));
+    }
+    for (int o = 16; o; o >>= 1) {
+        const df b{__shfl_xor_sync(0xffffffffu, m.hi, o), __shfl_xor_sync(0xffffffffu, m.lo, o)};
+        m = df_max(m, b);
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(best, (unsigned long long)__double_as_longlong(df_to_double(m)));
+}
+
+__global__ void k_alpha_df_store(const unsigned long long* best, double* alpha) {
+    const double c2 = __longlong_as_double((long long)*best);
+    *alpha = 2.0 * asin(0.5 * sqrt(c2));
+}
+}  // namespace
+
+sbr_status launch_alpha_fast(int32_t N, double* alpha, cudaStream_t s) {
+    const int64_t per_face = (int64_t)N * (N + 1) / 2;
+    unsigned long long* best;
+    SBR_TRY(dalloc_n(&best, 1, s));
+    SBR_TRY_CUDA(cudaMemsetAsync(best, 0, sizeof(unsigned long long), s));
+    ::sbr::note_launch(), k_alpha_df<<<(unsigned)((per_face + 255) / 256), 256, 0, s>>>(make_ico_lattice(), N,
+                                                                                          per_face, best);
+    ::sbr::note_launch(), k_alpha_df_store<<<1, 1, 0, s>>>(best, alpha);
+    SBR_TRY_CUDA(cudaGetLastError());
+    dfree(best, s);
+    return SBR_OK;
+}
+
 sbr_status launch_dirs(int32_t N, double* dirs, cudaStream_t s) {
     int64_t R = 10 * (int64_t)N * N + 2;
     // test hook: SBR_DIRS_DF=1 returns the double-float directions the trace

@@ -61,6 +61,43 @@ __device__ __forceinline__ df df_from_int(long long v) {
     return df{h, (float)(v - (long long)h)};
 }
 
+// unit direction of the lattice point with integer coordinates A + B phi
+__device__ __forceinline__ df3 lattice_unit_df(const IcoLattice& t, const int* PA, const int* PB) {
+    long long C = 0, D = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        C += (long long)PA[k] * PA[k] + (long long)PB[k] * PB[k];
+        D += 2LL * PA[k] * PB[k] + (long long)PB[k] * PB[k];
+    }
+    const df phi{t.phi_hi, t.phi_lo};
+    // |P|^2 = C + D phi, then 1 / |P| from rsqrt and one Newton step:
+    // y = y0 (1 + (1 - S y0^2) / 2)
+    const df S = df_fma(df_from_int(C), df_from_int(D), phi);
+    const float y0 = rsqrtf(S.hi);
+    const df e = df_sub(df{1.f, 0.f}, df_mul(S, two_prod(y0, y0)));
+    const df y = fast_two_sum(y0, __fmul_rn(__fmul_rn(y0, 0.5f), e.hi));
+    df c[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        // A + B phi, exact products of the integers with phi's two words
+        df x = two_prod((float)PB[k], t.phi_hi);
+        x.lo = __fmaf_rn((float)PB[k], t.phi_lo, x.lo);
+        x = df_add(df{(float)PA[k], 0.f}, x);
+        c[k] = df_mul(x, y);
+    }
+    return df3{c[0], c[1], c[2]};
+}
+
+// lattice point (N - i - j) V_a + i V_b + j V_c of face f, as A + B phi
+__device__ __forceinline__ void face_point(const IcoLattice& t, int f, int N, int i, int j, int* PA, int* PB) {
+    const int va = t.f[f][0], vb = t.f[f][1], vc = t.f[f][2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        PA[k] = (N - i - j) * t.A[va][k] + i * t.A[vb][k] + j * t.A[vc][k];
+        PB[k] = (N - i - j) * t.B[va][k] + i * t.B[vb][k] + j * t.B[vc][k];
+    }
+}
+
 __device__ __forceinline__ df3 geodesic_dir_df(const IcoLattice& t, const GeoN& g, uint32_t id) {
     const int N = g.N;
     int va, vb, vc, wa, wb, wc;
@@ -95,31 +132,12 @@ __device__ __forceinline__ df3 geodesic_dir_df(const IcoLattice& t, const GeoN& 
         }
     }
     int PA[3], PB[3];
-    long long C = 0, D = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         PA[k] = wa * t.A[va][k] + wb * t.A[vb][k] + wc * t.A[vc][k];
         PB[k] = wa * t.B[va][k] + wb * t.B[vb][k] + wc * t.B[vc][k];
-        C += (long long)PA[k] * PA[k] + (long long)PB[k] * PB[k];
-        D += 2LL * PA[k] * PB[k] + (long long)PB[k] * PB[k];
     }
-    const df phi{t.phi_hi, t.phi_lo};
-    // |P|^2 = C + D phi, then 1 / |P| from rsqrt and one Newton step:
-    // y = y0 (1 + (1 - S y0^2) / 2)
-    const df S = df_fma(df_from_int(C), df_from_int(D), phi);
-    const float y0 = rsqrtf(S.hi);
-    const df e = df_sub(df{1.f, 0.f}, df_mul(S, two_prod(y0, y0)));
-    const df y = fast_two_sum(y0, y0 * 0.5f * e.hi);
-    df c[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        // A + B phi, exact products of the integers with phi's two words
-        df x = two_prod((float)PB[k], t.phi_hi);
-        x.lo = __fmaf_rn((float)PB[k], t.phi_lo, x.lo);
-        x = df_add(df{(float)PA[k], 0.f}, x);
-        c[k] = df_mul(x, y);
-    }
-    return df3{c[0], c[1], c[2]};
+    return lattice_unit_df(t, PA, PB);
 }
 
 }  // namespace sbr

@@ -218,6 +218,9 @@ constexpr int kJones = 48;
 // launchers implemented in the .cu files
 sbr_status launch_dirs(int32_t N, double* dirs, cudaStream_t s);
 sbr_status launch_alpha(int32_t N, double* alpha, cudaStream_t s);
+// the same alpha from one face of the lattice in double-float (the form a trace
+// computes when it is given no alpha): ~1e-15 relative of the FP64 form
+sbr_status launch_alpha_fast(int32_t N, double* alpha, cudaStream_t s);
 sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S, sbr_bvh* b, cudaStream_t s,
                      bool sah_top);
 sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s);

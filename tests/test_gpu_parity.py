@@ -71,6 +71,19 @@ def test_directions_decoded_in_the_trace_kernels(sbr, N, monkeypatch):
     assert err < 1e-13
 
 
+@pytest.mark.parametrize("N", [1, 2, 5, 37, 100, 632, 1000])
+def test_trace_alpha_matches_oracle(sbr, N):
+    # the reception-sphere angle a trace computes when given none (one face of
+    # the lattice, double-float chords) against the oracle's FP64 maximum over
+    # all 20 faces
+    d = sbr.scene_to_device(scenes.config1(N=N, K=0))
+    bvh = sbr.build_bvh(d["tri"], d["surface_id"], d["S"])
+    a = sbr.trace(bvh, d["tx"], d["rx"], N, 0).stats()["alpha"]
+    ref = oracle.alpha(N)
+    print("N", N, "alpha", a, "oracle", ref, "rel", abs(a - ref) / ref)
+    assert abs(a - ref) <= 1e-13 * ref
+
+
 @pytest.mark.parametrize("name", list(SCENES))
 def test_paths_and_gains_match_oracle(sbr, name):
     sc = SCENES[name]()
