@@ -782,15 +782,38 @@ def bench_per_element(sbr, torch, args):
             "fp32_max_abs_err_vs_fp64_over_max": err}
 
 
+def job_ranges(scs, jobs):
+    """The ranges a batched workload actually spans."""
+    tri = [len(scs[j["scene"]]["tri"]) for j in jobs]
+    nt = [len(j["tx_elem"]) for j in jobs]
+    nr = [len(j["rx_elem"]) for j in jobs]
+    f = [len(j["freqs"]) for j in jobs]
+    r = [10 * j["N"] ** 2 + 2 for j in jobs]
+    k = [j["K"] for j in jobs]
+    upa = sorted({"%dx%d" % (int(round(np.ptp(j["tx_elem"][:, 1]) / max(1e-12, _spacing(j)))) + 1,
+                             int(round(np.ptp(j["tx_elem"][:, 2]) / max(1e-12, _spacing(j)))) + 1)
+                  for j in jobs}, key=lambda x: [int(v) for v in x.split("x")])
+    return {"triangles": [min(tri), max(tri)], "rays": [min(r), max(r)], "max_bounces": [min(k), max(k)],
+            "subcarriers": [min(f), max(f)], "tx_elements": [min(nt), max(nt)], "rx_elements": [min(nr), max(nr)],
+            "tx_upa": [upa[0], upa[-1]], "max_H_elements": int(max(a * b * c for a, b, c in zip(nt, nr, f)))}
+
+
+def _spacing(j):
+    """Element spacing of a job's arrays (half the carrier wavelength)."""
+    return 299792458.0 / float(np.mean(j["freqs"])) / 2.0
+
+
 def bench_batched(sbr, torch, args):
-    """The batched uneven workload: 4096 Tx-Rx jobs over 32 scenes (0.9k-125k
-    triangles), rays 1e5-1e7 log-uniform, K 2-8, 64-1024 subcarriers, up to
-    8 x 8 transmit and 64 receive elements; the batch (tuned on its first 128
-    jobs, one CUDA-graph launch per run) against a per-pair loop of the
-    single-job calls, with the largest H difference between the two."""
+    """The batched uneven workload: 4096 Tx-Rx jobs over 32 scenes (about 1k
+    to 200k triangles, log-spaced), rays 1e5-1e7 log-uniform, K 2-8, 64-1024
+    subcarriers, Tx UPAs up to 8 x 8 and Rx ULAs up to 64 elements (Nr x Nt up
+    to 64 x 64); the batch (tuned on its first 128 jobs, one CUDA-graph launch
+    per run) against a per-pair loop of the single-job calls, with the largest
+    H difference between the two. A second batch of 128 jobs reads the array
+    range as square Tx UPAs of 1 x 1 ... 64 x 64 elements (up to 4096)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     n_jobs = args.batch_jobs
-    scs = [scenes.batch_scene(s) for s in range(32)]
+    scs = [scenes.batch_scene(s, span=32) for s in range(32)]
     jobs = scenes.batch_jobs(scs, n_jobs=n_jobs, seed=4)
     sdev = []
     for sc in scs:   # each scene is traced by ~128 jobs: the SAH top of its BVH pays for its build
@@ -850,7 +873,11 @@ def bench_batched(sbr, torch, args):
             if m > 0:
                 dmax = max(dmax, float((H - j["H"]).abs().max()) / m)
     rbs = info["ray_bounces"]
+    b.free()
+    del Hs
+    upa = bench_batched_upa(sbr, torch, scs, sdev, cfg, args.batch_upa_jobs) if args.batch_upa_jobs > 0 else None
     out = {"metric": "Tx-Rx jobs/s", "workload": "batched_%djobs_32scenes_R1e5-1e7_K2-8_F64-1024" % n_jobs,
+           "ranges": job_ranges(scs, jobs), "upa_64x64": upa,
            "jobs": n_jobs, "rays": info["rays"], "ray_bounces": rbs, "paths": info["paths"],
            "failed_jobs": int((status != 0).sum()),
            "batched": {"ms": t_b * 1e3, "jobs_per_s": n_jobs / t_b, "Mray_bounces_per_s": rbs / t_b / 1e6,
@@ -860,6 +887,57 @@ def bench_batched(sbr, torch, args):
                              "Mray_bounces_per_s": rbs / t_pp / 1e6},
            "speedup": t_pp / t_b,
            "max_abs_dH_over_max_H_batched_vs_per_pair": dmax}
+    return out
+
+
+def bench_batched_upa(sbr, torch, scs, sdev, cfg, n_jobs):
+    """The array range read as Tx UPAs: n_jobs jobs (seed 5) over the same 32
+    scenes with square Tx UPAs of 2^a x 2^a elements, a uniform in [0, 6]
+    (1 x 1 ... 64 x 64, i.e. up to 4096 transmit elements), Rx ULAs up to 64,
+    64-1024 subcarriers; one batch run (the configuration tuned for the main
+    workload) against the per-pair loop, with the largest H difference."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    jobs = scenes.batch_jobs(scs, n_jobs=n_jobs, seed=5, tx_exp_range=(0, 6), square_tx=True)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    jdev = [dict(scene=j["scene"], N=j["N"], K=j["K"], tx=j["tx"], rx=j["rx"], pol=j["pol"],
+                 freqs=t(j["freqs"], torch.float64), gamma=t(j["gamma"], torch.float32),
+                 tx_elem=t(j["tx_elem"], torch.float64), rx_elem=t(j["rx_elem"], torch.float64))
+            for j in jobs]
+    b = sbr.batch_create(sdev, jdev, config=dict(cfg))
+    b.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.run()
+    e1.record()
+    e1.synchronize()
+    t_b = e0.elapsed_time(e1) / 1e3
+    n_paths, status, info = b.query()
+    torch.cuda.synchronize()
+    e0.record()
+    dmax = 0.0
+    for j, st in zip(jdev, status):
+        bvh, mats = sdev[j["scene"]]
+        rx = torch.as_tensor(np.asarray(j["rx"], dtype=np.float64).reshape(1, 3), device=dev)
+        tr = sbr.trace(bvh, j["tx"], rx, j["N"], j["K"])
+        pl = sbr.paths(tr, bvh)
+        g = sbr.path_gains(pl, mats, j["freqs"], j["gamma"], None, sbr.POL_V if j["pol"] == "V" else sbr.POL_H)
+        H = sbr.synthesize_H(pl, g, j["freqs"], j["tx_elem"], j["rx_elem"], 0, sbr.SYNTH_FP16X3)
+        if st == 0:
+            m = float(H.abs().max())
+            if m > 0:
+                dmax = max(dmax, float((H - j["H"]).abs().max()) / m)
+        del H
+    e1.record()
+    e1.synchronize()
+    t_pp = e0.elapsed_time(e1) / 1e3
+    h_bytes = sum(8 * len(j["freqs"]) * len(j["tx_elem"]) * len(j["rx_elem"]) for j in jobs)
+    out = {"workload": "batched_%djobs_32scenes_squareUPA1x1-64x64" % n_jobs, "ranges": job_ranges(scs, jobs),
+           "jobs_with_64x64_upa": int(sum(len(j["tx_elem"]) == 4096 for j in jobs)),
+           "H_bytes": h_bytes, "paths": info["paths"], "failed_jobs": int((status != 0).sum()),
+           "batched": {"ms": t_b * 1e3, "jobs_per_s": n_jobs / t_b, "H_GBps": h_bytes / t_b / 1e9},
+           "per_pair_loop": {"ms": t_pp * 1e3, "jobs_per_s": n_jobs / t_pp},
+           "speedup": t_pp / t_b, "max_abs_dH_over_max_H_batched_vs_per_pair": dmax}
     b.free()
     return out
 
@@ -943,7 +1021,7 @@ def profile_case(case: str) -> int:
         torch.cuda.synchronize()
         print("synth", r["paths"].n, float(H.abs().max()))
     elif case == "batch":
-        scs = [scenes.batch_scene(s) for s in range(4)]
+        scs = [scenes.batch_scene(s, span=32) for s in range(4)]
         jobs = scenes.batch_jobs(scs, n_jobs=48, seed=4)
         dev = torch.device("cuda")
         sdev = []
@@ -995,6 +1073,8 @@ def main():
     ap.add_argument("--surrogate-rx", type=int, default=1048576)
     ap.add_argument("--surrogate-epochs", type=int, default=40)
     ap.add_argument("--batch-jobs", type=int, default=4096)
+    ap.add_argument("--batch-upa-jobs", type=int, default=128,
+                    help="jobs of the square-UPA (up to 64 x 64) batch; 0 skips it")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="urban", choices=["urban", "urban_n400"],

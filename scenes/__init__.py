@@ -361,13 +361,19 @@ def scene_summary(sc) -> dict:
 BATCH_N_VALUES = np.unique(np.round(np.geomspace(100, 1000, 64)).astype(int))
 
 
-def batch_scene(s: int, t_min: float = 1e3, t_max: float = 2e5):
+def batch_scene(s: int, t_min: float = 1e3, t_max: float = 2e5, span: int = 0):
     """Scene s of the batched workload (seed 1000 + s): an urban grid of the
     config-2 kind with nx in [2, 8] x ny in [2, 5] cells, a coarse ground
     (8 x 8 quads) and facade subdivision chosen so that the triangle count is
-    close to a target drawn log-uniform in [t_min, t_max]."""
+    close to a target. The target is drawn log-uniform in [t_min, t_max]; with
+    span > 0 the targets of scenes 0 .. span-1 are instead the span
+    log-spaced values from t_min to t_max, in a seeded order, so that the set
+    reaches both ends of the range."""
     rng = np.random.default_rng(1000 + s)
     target = float(np.exp(rng.uniform(np.log(t_min), np.log(t_max))))
+    if span > 0:
+        order = np.random.default_rng(999).permutation(span)
+        target = float(np.geomspace(t_min, t_max, span)[order[s % span]])
     nx = int(rng.integers(2, 9))
     ny = int(rng.integers(2, 6))
     sub = max(1, int(round(np.sqrt(max(target - 128.0, 10.0 * nx * ny) / (10.0 * nx * ny)))))
@@ -377,13 +383,14 @@ def batch_scene(s: int, t_min: float = 1e3, t_max: float = 2e5):
 
 
 def batch_jobs(scene_list, n_jobs: int = 4096, seed: int = 4, n_values=None, k_range=(2, 8),
-               f_exp_range=(6, 10), max_elem_exp: int = 6):
+               f_exp_range=(6, 10), max_elem_exp: int = 6, tx_exp_range=(0, 3), square_tx: bool = False):
     """Jobs of the batched workload (seed `seed`), each a Tx-Rx pair:
     scene uniform over scene_list; N uniform over n_values (default
     BATCH_N_VALUES, so R is log-uniform over [1e5, 1e7]); K uniform in k_range;
     F = 2^e with e uniform in f_exp_range (64 ... 1024 subcarriers) around a
     carrier from {28, 60, 100, 140, 300} GHz over min(10 GHz, fc / 10); Tx a UPA
-    in the y-z plane of 2^a x 2^b elements (a, b in [0, 3]) at a street crossing
+    in the y-z plane of 2^a x 2^b elements (a, b uniform in tx_exp_range; b = a
+    with square_tx, so (0, 6) gives 1 x 1 ... 64 x 64 UPAs) at a street crossing
     (60 i, 60 j) +- 5 m, height U(5, 30) m; Rx a ULA along y of 2^c elements
     (c in [0, max_elem_exp]) in an x-street (60 i +- 8 m), height 1.5 m, so that
     neither end is inside a building; element spacing half a carrier
@@ -408,7 +415,10 @@ def batch_jobs(scene_list, n_jobs: int = 4096, seed: int = 4, n_values=None, k_r
                        60.0 * rng.integers(1, ny) + rng.uniform(-5, 5), rng.uniform(5, 30)])
         rx = np.array([60.0 * rng.integers(0, nx + 1) + rng.uniform(-8, 8),
                        rng.uniform(-10.0, 60.0 * ny + 10.0), 1.5])
-        nty, ntz = int(2 ** rng.integers(0, 4)), int(2 ** rng.integers(0, 4))
+        nty, ntz = int(2 ** rng.integers(tx_exp_range[0], tx_exp_range[1] + 1)), \
+            int(2 ** rng.integers(tx_exp_range[0], tx_exp_range[1] + 1))
+        if square_tx:
+            ntz = nty
         nr = int(2 ** rng.integers(0, max_elem_exp + 1))
         pol = "V" if rng.integers(0, 2) == 0 else "H"
         jobs.append(dict(scene=s, N=N, K=K, tx=tx, rx=rx, freqs=freqs, pol=pol,

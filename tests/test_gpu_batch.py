@@ -154,3 +154,36 @@ def test_autotuner_returns_a_working_config(sbr):
     b.run()
     _, status, _ = b.query()
     assert (status == 0).all()
+
+
+def test_batch_with_64x64_upa_matches_per_pair(sbr):
+    # the top of the array range read as a 64 x 64 Tx UPA (4096 elements): jobs
+    # with square UPAs up to 64 x 64 through the batch (tile width 64: 64 N tiles
+    # per frequency) give the per-pair H bit for bit
+    scs = [scenes.batch_scene(s, t_min=300, t_max=3000) for s in range(2)]
+    jobs = scenes.batch_jobs(scs, n_jobs=6, seed=11, n_values=[12, 17], k_range=(1, 3), f_exp_range=(2, 3),
+                             max_elem_exp=3, tx_exp_range=(4, 6), square_tx=True)
+    jobs[0]["tx_elem"] = scenes.upa_yz(jobs[0]["tx"], 64, 64, 299792458.0 / float(np.mean(jobs[0]["freqs"])) / 2)
+    dev = torch.device("cuda")
+    sdev = []
+    for sc in scs:
+        tri = torch.as_tensor(sc["tri"].reshape(-1, 9), dtype=torch.float32, device=dev)
+        sid = torch.as_tensor(sc["surface_id"], dtype=torch.int32, device=dev)
+        mats = torch.as_tensor(sc["materials"], dtype=torch.float64, device=dev)
+        sdev.append((sbr.build_bvh(tri, sid, len(sc["materials"])), mats))
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    jdev = [dict(scene=j["scene"], N=j["N"], K=j["K"], tx=j["tx"], rx=j["rx"], pol=j["pol"],
+                 freqs=t(j["freqs"], torch.float64), gamma=t(j["gamma"], torch.float32),
+                 tx_elem=t(j["tx_elem"], torch.float64), rx_elem=t(j["rx_elem"], torch.float64))
+            for j in jobs]
+    assert len(jobs[0]["tx_elem"]) == 4096 and all(len(j["tx_elem"]) >= 256 for j in jobs)
+    b = sbr.batch_create(sdev, jdev, config=dict(path_cap=256, tile_n=64))
+    b.run()
+    n_paths, status, info = b.query()
+    assert (status == 0).all()
+    for i, j in enumerate(jdev):
+        _, ex, g, H = _per_pair(sbr, sdev, j, sbr.SYNTH_FP16X3)
+        assert len(ex["rx"]) == n_paths[i]
+        Hb = j["H"].cpu().numpy()
+        assert Hb.shape == H.shape
+        assert np.array_equal(Hb, H), (i, np.abs(Hb - H).max())
