@@ -160,14 +160,19 @@ __device__ __forceinline__ TcItem tc_item(const TcArgs& a, int64_t it) {
         x.Pp = a.Pp;
         H = a.H;
     }
-    const int mtiles = (x.Nr + 63) / 64, ntiles = (x.Nt + kTileN - 1) / kTileN;
-    x.f = (int)(it / (mtiles * ntiles));
-    const int rem = (int)(it - (int64_t)x.f * mtiles * ntiles);
-    x.q0 = (rem / ntiles) * 64;
-    x.p0 = (rem % ntiles) * kTileN;
+    // 32-bit decode (a job has F * tiles < 2^31 items); every thread of the
+    // CTA repeats it, so it stays cheap
+    const uint32_t mtiles = (uint32_t)(x.Nr + 63) / 64u, ntiles = (uint32_t)(x.Nt + kTileN - 1) / (uint32_t)kTileN;
+    const uint32_t per_f = mtiles * ntiles, itu = (uint32_t)it;
+    const uint32_t fq = per_f == 1u ? itu : itu / per_f;
+    const uint32_t rem = itu - fq * per_f;
+    const uint32_t qt = ntiles == 1u ? rem : rem / ntiles;
+    x.f = (int)fq;
+    x.q0 = (int)qt * 64;
+    x.p0 = (int)(rem - qt * ntiles) * kTileN;
     x.los = Pr > 0 && *nb0 == 0;
     x.nrefl = Pr - (x.los ? 1 : 0);
-    x.foc = (float)(freqs[x.f] / kC0);
+    x.foc = (float)(freqs[x.f] * kInvC0);
     x.wf = w + (int64_t)x.f * x.Pp;
     x.wl = wl[x.f];
     x.sc = sc[x.f];
@@ -236,7 +241,7 @@ __device__ __forceinline__ uint32_t stage_off(int r, int c) {
 // memory, and reads back (real, imaginary) pairs of two transmit elements per
 // lane; it scales back (FP16 form), adds the exact per-element LoS term and
 // writes H with row-contiguous 128-byte segments (eight lanes per row).
-template <int kTileN>
+template <bool kF16, int kTileN>
 __device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t tmem, unsigned char* stage_out, int warp,
                                             int lane) {
     const int lg = warp & 3, cg = warp >> 2;   // TMEM lane quarter, column group
@@ -261,7 +266,7 @@ __device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t tmem, unsig
 #pragma unroll
             for (int i = 0; i < 4; ++i) dl_next[i] = __ldg(reinterpret_cast<const float2*>(e.dlos + o0 + i * rstep));
         }
-#pragma unroll 1
+#pragma unroll
         for (int j = 0; j < kCols / 16; ++j) {
             const int col0 = cg * kCols + 16 * j;
             const int64_t o0 = row0 + e.p0 + col0 + 2 * c;
@@ -291,7 +296,8 @@ __device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t tmem, unsig
                 float2 re, im;
                 asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(re.x), "=f"(re.y) : "r"(s_re + 512u * i));
                 asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(im.x), "=f"(im.y) : "r"(s_im + 512u * i));
-                float4 o = make_float4(re.x * e.isc, im.x * e.isc, re.y * e.isc, im.y * e.isc);
+                float4 o = kF16 ? make_float4(re.x * e.isc, im.x * e.isc, re.y * e.isc, im.y * e.isc)
+                                : make_float4(re.x, im.x, re.y, im.y);
                 if (e.los) {
                     float sn, cs;
                     phasor(e.foc * dl[i].x, sn, cs);
@@ -540,7 +546,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
                 ok = __all_sync(0xffffffffu, mbar_wait(bar(2 + prev.acc), prev.acc_parity));
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             }
-            if (ok) tc_epilogue<kTileN>(prev, tmem, stage_out, warp, lane);
+            if (ok) tc_epilogue<kF16, kTileN>(prev, tmem, stage_out, warp, lane);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             epi_ok = epi_ok && ok;
         }
@@ -553,7 +559,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
             ok = __all_sync(0xffffffffu, mbar_wait(bar(2 + prev.acc), prev.acc_parity));
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
-        if (ok) tc_epilogue<kTileN>(prev, tmem, stage_out, warp, lane);
+        if (ok) tc_epilogue<kF16, kTileN>(prev, tmem, stage_out, warp, lane);
         epi_ok = epi_ok && ok;
     }
     failed = __syncthreads_or(failed || !epi_ok) != 0;
