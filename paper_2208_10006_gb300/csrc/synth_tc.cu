@@ -404,6 +404,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    // launched as a programmatic dependent of the operand prologue, the
+    // prologue above overlaps its tail; its results are read only after this
+    // (a no-op for an ordinary launch)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     bool failed = false;
     // injected fault: the first phase of `never` never completes; the bounded
     // wait gives up and the CTA takes the same exit as a real timeout
@@ -580,7 +584,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
 // Operands of the tensor-core forms in one launch (layouts in synth_ops.cuh):
 // blocks [0, nbw) compute the weights, one warp per frequency (the FP16 scale
 // is that warp's maximum); the other blocks compute the element delays, one
-// thread per (path, 8 elements), the path's reference distance once.
+// thread per path and group of kPrepG elements (per transmit element and
+// group of kPrepG receive elements for the LoS delays), the reference
+// distance once per thread. Blocks of kPrepThreads threads spread the FP64
+// work (square roots above all) over every SM.
+constexpr int kPrepThreads = 128;
+constexpr int kPrepG = 2;
 struct TcPrep {
     int32_t Pr, Pp, Nt, Nr, F, nbw;
     const int32_t* nb;       // [Pr] reflections of the receiver's paths
@@ -601,6 +610,9 @@ struct TcPrep {
 };
 
 __global__ void k_tc_prep(const __grid_constant__ TcPrep a) {
+    // the synthesis kernel that follows may start its prologue now (it waits
+    // for this grid's results before it reads them)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int n0 = (a.Pr > 0 && a.nb[0] == 0) ? 1 : 0;   // the LoS path sorts first
     const int nrefl = a.Pr - n0;
     if ((int)blockIdx.x < a.nbw) {
@@ -621,33 +633,46 @@ __global__ void k_tc_prep(const __grid_constant__ TcPrep a) {
         }
         return;
     }
-    // delays: one element per thread over every SM (FP64 throughput per SM is
-    // the limit here), consecutive threads on consecutive paths of one element
-    const int64_t n_dt = (int64_t)a.Pp * a.Nt, n_dr = (int64_t)a.Pp * a.Nr, n_dl = (int64_t)a.Nr * a.Nt;
+    // delays; consecutive threads write consecutive words of a row
+    const int64_t gt = (a.Nt + kPrepG - 1) / kPrepG, gr = (a.Nr + kPrepG - 1) / kPrepG;
+    const int64_t n_dt = (int64_t)a.Pp * gt, n_dr = (int64_t)a.Pp * gr, n_dl = (int64_t)a.Nt * gr;
     const int64_t total = n_dt + n_dr + n_dl;
     const int64_t stride = (int64_t)(gridDim.x - a.nbw) * blockDim.x;
     for (int64_t t = (int64_t)(blockIdx.x - a.nbw) * blockDim.x + threadIdx.x; t < total; t += stride) {
         if (t < n_dr + n_dt) {
             const bool tx = t < n_dt;
             const int64_t u = tx ? t : t - n_dt;
-            const int n = (int)(u % a.Pp), e = (int)(u / a.Pp);
-            float v = 0.f;
+            const int n = (int)(u % a.Pp), e0 = (int)(u / a.Pp) * kPrepG;
+            const int ne = tx ? a.Nt : a.Nr;
+            const double* elem = tx ? a.tx_elem : a.rx_elem;
+            float* dst = (tx ? a.dtT : a.drT) + n;
             if (n < nrefl) {
                 const int i = n + n0, m = a.nb[i];
                 const d3 P = ld3(a.pts + ((int64_t)i * kKmax + (tx ? 0 : m - 1)) * 3);
                 const double ref = dist_rn(tx ? a.T0 : ld3(a.R0), P);
-                v = el_delay((tx ? a.tx_elem : a.rx_elem) + 3 * e, P, ref);
+#pragma unroll
+                for (int k = 0; k < kPrepG; ++k)
+                    if (e0 + k < ne) dst[(int64_t)(e0 + k) * a.Pp] = el_delay(elem + 3 * (e0 + k), P, ref);
+            } else {
+#pragma unroll
+                for (int k = 0; k < kPrepG; ++k)
+                    if (e0 + k < ne) dst[(int64_t)(e0 + k) * a.Pp] = 0.f;
             }
-            (tx ? a.dtT : a.drT)[u] = v;
         } else {
             const int64_t u = t - n_dt - n_dr;
-            const int q = (int)(u / a.Nt), p = (int)(u - (int64_t)q * a.Nt);
-            a.dlos[u] = el_delay(a.tx_elem + 3 * p, ld3(a.rx_elem + 3 * q), dist_rn(a.T0, ld3(a.R0)));
+            const int p = (int)(u % a.Nt), q0 = (int)(u / a.Nt) * kPrepG;
+            const double ref = dist_rn(a.T0, ld3(a.R0));
+#pragma unroll
+            for (int k = 0; k < kPrepG; ++k)
+                if (q0 + k < a.Nr)
+                    a.dlos[(int64_t)(q0 + k) * a.Nt + p] = el_delay(a.tx_elem + 3 * p, ld3(a.rx_elem + 3 * (q0 + k)), ref);
         }
     }
 }
 
-inline unsigned nb256(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + 255) / 256); }
+inline unsigned blocks_of(int64_t n, int threads) {
+    return (unsigned)std::max<int64_t>(1, (n + threads - 1) / threads);
+}
 
 }  // namespace
 
@@ -678,10 +703,11 @@ sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* 
     pp.R0 = pl->rx_xyz + 3 * rx_index;
     pp.T0 = mk3(pl->tx[0], pl->tx[1], pl->tx[2]);
     pp.dtT = dtT; pp.drT = drT; pp.dlos = dl; pp.w = w; pp.wl = wl; pp.sc = sc;
-    pp.nbw = (int)nb256((int64_t)F * 32);
-    const int64_t n_del = (int64_t)Pp * (Nt + Nr) + (int64_t)Nr * Nt;
-    const unsigned nbd = (unsigned)std::min<int64_t>(nb256(n_del), 8 * (int64_t)sm_count());
-    ::sbr::note_launch(), k_tc_prep<<<(unsigned)pp.nbw + nbd, 256, 0, s>>>(pp);
+    pp.nbw = (int)blocks_of((int64_t)F * 32, kPrepThreads);
+    const int64_t gt = (Nt + kPrepG - 1) / kPrepG, gr = (Nr + kPrepG - 1) / kPrepG;
+    const int64_t n_del = (int64_t)Pp * (gt + gr) + (int64_t)Nt * gr;
+    const unsigned nbd = (unsigned)std::min<int64_t>(blocks_of(n_del, kPrepThreads), 32 * (int64_t)sm_count());
+    ::sbr::note_launch(), k_tc_prep<<<(unsigned)pp.nbw + nbd, kPrepThreads, 0, s>>>(pp);
     SBR_TRY_CUDA(cudaGetLastError());
     TcArgs a{};
     a.F = F; a.Nr = Nr; a.Nt = Nt;
@@ -694,10 +720,21 @@ sbr_status synth_tc_run(const sbr_path_list* pl, const float2* g, const double* 
     constexpr int kSmemBytes = TcShape<256>::kSmemBytes;
     SBR_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     int64_t items = (int64_t)F * ((Nr + 63) / 64) * ((Nt + 255) / 256);
-    // one persistent CTA per SM (two operand stages and two accumulators each)
-    int grid = (int)std::min<int64_t>(items, (int64_t)sm_count());
-    ::sbr::note_launch(), kern<<<grid, kTcThreads, kSmemBytes, s>>>(a);
-    SBR_TRY_CUDA(cudaGetLastError());
+    // one persistent CTA per SM (two operand stages and two accumulators each),
+    // launched as a programmatic dependent of the prologue
+    const int grid = (int)std::min<int64_t>(items, (int64_t)sm_count());
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ::sbr::note_launch();
+    SBR_TRY_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
     dfree(w, s);
     return SBR_OK;
 }
