@@ -459,9 +459,10 @@ typedef struct {
 } sbr_batch_info;
 
 /*
- * sbr_batch_create - validate the jobs, group them into waves, build the
- * launch-direction tables and alpha of every distinct N, and allocate every
- * buffer of the batch (no allocation happens in sbr_batch_run).
+ * sbr_batch_create - validate the jobs, group them into waves, compute the
+ * reception-sphere angle alpha of every distinct N (launch directions are
+ * decoded from the ray id inside the trace, no table is built), and allocate
+ * every buffer of the batch (no allocation happens in sbr_batch_run).
  * scenes: n_scenes BVH handles; mats[s]: dev array of scenes[s]'s surfaces
  * (at least its S entries). jobs: host array of n_jobs (copied). cfg may be
  * NULL (defaults). The scene handles and the jobs' device arrays must outlive
