@@ -379,6 +379,7 @@ __device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t tmem, unsig
 template <bool kF16, bool kBatch, int kTileN>
 __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constant__ TcArgs a) {
     using Sh = TcShape<kTileN>;
+    static_assert(kTcThreads % kTileN == 0 && 64 * (kChunkP / 4) <= kTcThreads, "generation units");
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stage_out = smem + 2 * Sh::kStage;
@@ -442,17 +443,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
             const int cnt = min(kChunkP, x.nrefl - nb);
             const int nks = (cnt + 7) >> 3;        // MMA K-steps (8 paths each)
             const int n16 = 2 * nks;               // 16-byte chunks per row (4 paths each)
-            const int unitsB = kTileN * n16, units = unitsB + 64 * n16;
             if (ok) {
+                // B' (stored N x K): transmit element p, paths nb + 4 c16 .. + 3
+                // (padded paths have zero weight, so their phasors are harmless);
+                // kTcThreads is a multiple of N, so a thread keeps its element and
+                // steps through the chunks
+                {
+                    const int pl = tid % kTileN;
+                    const int p = x.p0 + pl;
+                    const float* src = x.dtT + (int64_t)(p < x.Nt ? p : 0) * x.Pp + nb;
+                    const uint32_t b_hi = smem_u32(sB_hi) + (uint32_t)pl * 128u;
+                    const uint32_t b_lo = smem_u32(sB_lo) + (uint32_t)pl * 128u;
 #pragma unroll 2
-                for (int u = tid; u < units; u += kTcThreads) {
-                    if (u < unitsB) {
-                        // B' (stored N x K): transmit element p, paths nb + 4 c16 .. + 3
-                        // (padded paths have zero weight, so their phasors are harmless)
-                        const int pl = u % kTileN, c16 = u / kTileN;
-                        const int p = x.p0 + pl;
+                    for (int c16 = tid / kTileN; c16 < n16; c16 += kTcThreads / kTileN) {
                         float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (p < x.Nt) d4 = __ldg(reinterpret_cast<const float4*>(x.dtT + (int64_t)p * x.Pp + nb + 4 * c16));
+                        if (p < x.Nt) d4 = __ldg(reinterpret_cast<const float4*>(src + 4 * c16));
                         float vr[4], vi[4];
                         phasor(x.foc * d4.x, vi[0], vr[0]);
                         phasor(x.foc * d4.y, vi[1], vr[1]);
@@ -461,49 +466,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
                         uint32_t h[4], l[4];
 #pragma unroll
                         for (int k = 0; k < 4; ++k) split2<kF16>(vr[k], vi[k], h[k], l[k]);
-                        const uint32_t o = chunk_off(pl, c16);
-                        sts128(smem_u32(sB_hi) + o, h[0], h[1], h[2], h[3]);
-                        sts128(smem_u32(sB_lo) + o, l[0], l[1], l[2], l[3]);
-                    } else {
-                        // A': receive element q, paths nb + 4 c16 .. + 3, as the two
-                        // rows 2q (Re A, -Im A) and 2q+1 (Im A, Re A)
-                        // lane pairs take neighbouring chunks of one receive element,
-                        // so that a quarter warp's 16-byte stores land in 8 distinct
-                        // bank groups of the swizzled rows 2q and 2q+1
-                        const int v = u - unitsB;
-                        const int ql = (v >> 1) & 63, c16 = (v & 1) + 2 * (v >> 7);
-                        const int q = x.q0 + ql;
-                        const int n = nb + 4 * c16;
-                        float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                        float4 w01 = d4, w23 = d4;
-                        if (q < x.Nr) {
-                            d4 = __ldg(reinterpret_cast<const float4*>(x.drT + (int64_t)q * x.Pp + n));
-                            w01 = __ldg(reinterpret_cast<const float4*>(x.wf + n));
-                            w23 = __ldg(reinterpret_cast<const float4*>(x.wf + n + 2));
-                        }
-                        const float dd[4] = {d4.x, d4.y, d4.z, d4.w};
-                        const float wr[4] = {w01.x, w01.z, w23.x, w23.z};
-                        const float wi[4] = {w01.y, w01.w, w23.y, w23.w};
-                        uint32_t h0[4], l0[4], h1[4], l1[4];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            float sn, cs;
-                            phasor(x.foc * dd[k], sn, cs);
-                            const float ar = (wr[k] * cs - wi[k] * sn) * sc;
-                            const float ai = (wr[k] * sn + wi[k] * cs) * sc;
-                            split2<kF16>(ar, -ai, h0[k], l0[k]);
-                            // row 2q+1 holds (Im A, Re A): the same halves swapped, with
-                            // the sign of -Im A flipped (rounding to nearest is symmetric,
-                            // so these are the bits of a split of (ai, ar))
-                            h1[k] = __byte_perm(h0[k], 0u, 0x1032) ^ 0x8000u;
-                            l1[k] = __byte_perm(l0[k], 0u, 0x1032) ^ 0x8000u;
-                        }
-                        const uint32_t o0 = chunk_off(2 * ql, c16), o1 = chunk_off(2 * ql + 1, c16);
-                        sts128(smem_u32(sA_hi) + o0, h0[0], h0[1], h0[2], h0[3]);
-                        sts128(smem_u32(sA_lo) + o0, l0[0], l0[1], l0[2], l0[3]);
-                        sts128(smem_u32(sA_hi) + o1, h1[0], h1[1], h1[2], h1[3]);
-                        sts128(smem_u32(sA_lo) + o1, l1[0], l1[1], l1[2], l1[3]);
+                        const uint32_t o = (uint32_t)(c16 ^ (pl & 7)) << 4;   // chunk_off(pl, c16) - pl * 128
+                        sts128(b_hi + o, h[0], h[1], h[2], h[3]);
+                        sts128(b_lo + o, l[0], l[1], l[2], l[3]);
                     }
+                }
+                // A': receive element q, paths nb + 4 c16 .. + 3, as the two rows
+                // 2q (Re A, -Im A) and 2q+1 (Im A, Re A); lane pairs take
+                // neighbouring chunks of one receive element, so that a quarter
+                // warp's 16-byte stores land in 8 distinct bank groups of the
+                // swizzled rows 2q and 2q+1 (at most 64 x 8 units: one per thread)
+                const int v = tid;
+                if (v < 64 * n16) {
+                    const int ql = (v >> 1) & 63, c16 = (v & 1) + 2 * (v >> 7);
+                    const int q = x.q0 + ql;
+                    const int n = nb + 4 * c16;
+                    float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 w01 = d4, w23 = d4;
+                    if (q < x.Nr) {
+                        d4 = __ldg(reinterpret_cast<const float4*>(x.drT + (int64_t)q * x.Pp + n));
+                        w01 = __ldg(reinterpret_cast<const float4*>(x.wf + n));
+                        w23 = __ldg(reinterpret_cast<const float4*>(x.wf + n + 2));
+                    }
+                    const float dd[4] = {d4.x, d4.y, d4.z, d4.w};
+                    const float wr[4] = {w01.x, w01.z, w23.x, w23.z};
+                    const float wi[4] = {w01.y, w01.w, w23.y, w23.w};
+                    uint32_t h0[4], l0[4], h1[4], l1[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float sn, cs;
+                        phasor(x.foc * dd[k], sn, cs);
+                        const float ar = (wr[k] * cs - wi[k] * sn) * sc;
+                        const float ai = (wr[k] * sn + wi[k] * cs) * sc;
+                        split2<kF16>(ar, -ai, h0[k], l0[k]);
+                        // row 2q+1 holds (Im A, Re A): the same halves swapped, with
+                        // the sign of -Im A flipped (rounding to nearest is symmetric,
+                        // so these are the bits of a split of (ai, ar))
+                        h1[k] = __byte_perm(h0[k], 0u, 0x1032) ^ 0x8000u;
+                        l1[k] = __byte_perm(l0[k], 0u, 0x1032) ^ 0x8000u;
+                    }
+                    const uint32_t o0 = chunk_off(2 * ql, c16), o1 = chunk_off(2 * ql + 1, c16);
+                    sts128(smem_u32(sA_hi) + o0, h0[0], h0[1], h0[2], h0[3]);
+                    sts128(smem_u32(sA_lo) + o0, l0[0], l0[1], l0[2], l0[3]);
+                    sts128(smem_u32(sA_hi) + o1, h1[0], h1[1], h1[2], h1[3]);
+                    sts128(smem_u32(sA_lo) + o1, l1[0], l1[1], l1[2], l1[3]);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
