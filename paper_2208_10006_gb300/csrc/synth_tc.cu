@@ -5,11 +5,13 @@
 //   V[p,n] = exp(-j 2 pi f dt_pn / c),
 // is the complex contraction U diag(w) V^T. It runs as one real GEMM
 //   C (2Nr x Nt) = A' (2Nr x 2P) B' (2P x Nt)
-// with rows 2q / 2q+1 of C the real / imaginary part of H[q, :] and the
+// with rows r(q) / i(q) of C the real / imaginary part of H[q, :] and the
 // contraction index k = 2n + {0: real, 1: imaginary}:
-//   A'[2q,   2n] =  Re A,  A'[2q,   2n+1] = -Im A
-//   A'[2q+1, 2n] =  Im A,  A'[2q+1, 2n+1] =  Re A
-//   B'[2n, p]    =  Re V,  B'[2n+1, p]    =  Im V.
+//   A'[r(q), 2n] =  Re A,  A'[r(q), 2n+1] = -Im A
+//   A'[i(q), 2n] =  Im A,  A'[i(q), 2n+1] =  Re A
+//   B'[2n, p]    =  Re V,  B'[2n+1, p]    =  Im V;
+// in a tile of 64 receive elements, r(q) = 16 (q / 8) + q % 8 and
+// i(q) = r(q) + 8 (acc_row).
 // Each operand is split x = hi + lo into two 16-bit values and the product is
 // taken as hi*hi + hi*lo + lo*hi, accumulated in FP32 in tensor memory. Two
 // forms: BF16 (the lo*lo term, ~2^-16 relative, dropped) and FP16 (~2^-22
@@ -18,9 +20,10 @@
 // both exactly). The phasors are generated on chip
 // (FP32 phase from the FP64-prepared delays) straight into 128-byte-swizzled
 // K-major shared-memory tiles; one thread issues tcgen05.mma (M=128, N=256,
-// K=16) and commits to an mbarrier; the epilogue reads TMEM with tcgen05.ld,
-// pairs the real/imaginary rows across neighbouring lanes, adds the exact
-// per-element LoS term and stores complex64.
+// K=16) and commits to an mbarrier; the epilogue reads TMEM with tcgen05.ld
+// in the 16-lane shape that gives each thread the real and the imaginary row
+// of one receive element, adds the exact per-element LoS term and stores
+// complex64.
 //
 // Every wait on the mbarrier is bounded; on expiry the CTA records
 // ST_TIMEOUT, releases its tensor memory and returns.
@@ -43,7 +46,6 @@ constexpr int kTcThreads = 512;  // 16 warps, one CTA per SM
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kChunkP = 32;      // paths per K-chunk (K = 64 16-bit values = one 128-byte row)
 constexpr int kABytes = kTileM * 128;  // 16 KB: 2 x 64 receive elements
-constexpr int kStageOut = 2048;  // per warp: 16 receive elements x 16 transmit elements, complex64
 
 // tile of N transmit elements (N = 64, 128 or 256): shared-memory and TMEM sizes.
 // Two operand stages (hi/lo of A' and B' each) and two FP32 accumulators, so
@@ -54,8 +56,7 @@ struct TcShape {
     static_assert(kTileN == 64 || kTileN == 128 || kTileN == 256, "tile N");
     static constexpr int kBBytes = kTileN * 128;
     static constexpr int kStage = 2 * kABytes + 2 * kBBytes;        // hi/lo of A and B
-    static constexpr int kOut = kTcWarps * kStageOut;               // epilogue staging
-    static constexpr int kSmemBytes = 2 * kStage + kOut + 1024 + 128;  // + alignment + barriers
+    static constexpr int kSmemBytes = 2 * kStage + 1024 + 128;      // + alignment + barriers
     static constexpr int kTmemCols = 2 * kTileN;                    // two accumulators
 };
 
@@ -227,138 +228,121 @@ struct TcEpi {
     float2* Hf;
 };
 
-// staging of one warp's 16 x 16 block: receive element r owns a 128-byte row,
-// its 16 real parts in logical 16-byte chunks 0-3 and its 16 imaginary parts
-// in chunks 4-7; chunk c is stored at c ^ t(r), t(r) = (r & 3) | (r & 1) << 2,
-// which keeps the writes (8 rows' halves per quarter warp) and the reads (two
-// rows' halves per half warp) free of bank conflicts
-__device__ __forceinline__ uint32_t stage_off(int r, int c) {
-    return (uint32_t)r * 128u + ((uint32_t)((c ^ ((r & 3) | ((r & 1) << 2))) & 7) << 4);
-}
+// Row of the M = 128 accumulator that holds the real (part 0) or imaginary
+// (part 1) part of receive element ql of the tile: receive elements come in
+// groups of 8, their real rows followed by their imaginary rows, so that one
+// 16-lane tensor-memory load hands each thread both parts of one output
+__device__ __forceinline__ int acc_row(int ql, int part) { return 16 * (ql >> 3) + 8 * part + (ql & 7); }
 
-// Epilogue of one tile: each warp reads 32 TMEM lanes (rows 2q / 2q+1 of 16
-// receive elements) x 16 columns at a time, stages the raw rows in shared
-// memory, and reads back (real, imaginary) pairs of two transmit elements per
-// lane; it scales back (FP16 form), adds the exact per-element LoS term and
-// writes H with row-contiguous 128-byte segments (eight lanes per row).
+// Epilogue of one tile: warp w reads TMEM lanes [32 (w % 4), + 32) (receive
+// elements [16 (w % 4), + 16) of the tile) over its N / 4 columns, 16 lanes
+// (8 receive elements) x 32 columns at a time; thread t receives, for 8
+// consecutive columns, (Re, Im) of receive element t / 4 at transmit elements
+// 2 (t % 4) and + 1. It scales back (FP16 form), adds the exact per-element
+// LoS term and writes them as one 16-byte store (four lanes write 64
+// contiguous bytes of a row of H).
 template <bool kF16, int kTileN>
-__device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t tmem, unsigned char* stage_out, int warp,
-                                            int lane) {
+__device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t tmem, int warp, int lane) {
     const int lg = warp & 3, cg = warp >> 2;   // TMEM lane quarter, column group
-    const int part = lane & 1;                 // 0: real row, 1: imaginary row
-    const int rw = lane >> 1;                  // row written: receive element within the warp's 16
-    const uint32_t sbase = smem_u32(stage_out + warp * kStageOut);
     constexpr int kCols = kTileN / 4;          // columns of one warp
-    const int c = lane & 7;                    // pair of transmit elements read back
+    constexpr int kRep = kCols >= 32 ? 4 : kCols / 8;   // 8-column repeats per load
+    constexpr int kBlkCols = 8 * kRep;
+    constexpr int kJ = kCols / kBlkCols;       // column blocks per 16-lane half
+    constexpr int kBlocks = 2 * kJ;
+    const int qa = lane >> 2, pc = 2 * (lane & 3);
+    const uint32_t tacc = tmem + (uint32_t)(e.acc * kTileN);
     if (e.full) {
-        // every output of the tile exists: per lane, receive elements
-        // r0 + 4 i (i = 0..3) of the warp's 16, transmit elements p, p + 1; the
-        // staging offsets of those rows differ by 512 bytes (t(r) depends on r & 3)
-        const int r0 = lane >> 3;
-        const uint32_t s_re = sbase + stage_off(r0, c >> 1) + 8u * (uint32_t)(c & 1);
-        const uint32_t s_im = sbase + stage_off(r0, 4 + (c >> 1)) + 8u * (uint32_t)(c & 1);
-        const int64_t row0 = (int64_t)(e.q0 + 16 * lg + r0) * e.Nt;
-        const int64_t rstep = 4 * (int64_t)e.Nt;
-        // LoS delays of column block j + 1 are requested while block j is processed
-        float2 dl_next[4];
+        // every output of the tile exists: no per-output checks. 32-bit element
+        // offsets within frequency f's H and LoS delays (Nr * Nt < 2^31 for a
+        // full tile); the LoS delays of block b + 1 are requested while block b
+        // is processed
+        auto offset = [&](int b, int k) {
+            const int h = b / kJ, jj = b % kJ;
+            const uint32_t q = (uint32_t)(e.q0 + 16 * lg + 8 * h + qa);
+            return q * (uint32_t)e.Nt + (uint32_t)(e.p0 + cg * kCols + kBlkCols * jj + 8 * k + pc);
+        };
+        float2 dl_next[kRep];
         if (e.los) {
-            const int64_t o0 = row0 + e.p0 + cg * kCols + 2 * c;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) dl_next[i] = __ldg(reinterpret_cast<const float2*>(e.dlos + o0 + i * rstep));
+            for (int k = 0; k < kRep; ++k) dl_next[k] = __ldg(reinterpret_cast<const float2*>(e.dlos + offset(0, k)));
         }
 #pragma unroll
-        for (int j = 0; j < kCols / 16; ++j) {
-            const int col0 = cg * kCols + 16 * j;
-            const int64_t o0 = row0 + e.p0 + col0 + 2 * c;
-            float2 dl[4];
+        for (int b = 0; b < kBlocks; ++b) {
+            const int h = b / kJ, jj = b % kJ;
+            float2 dl[kRep];
             if (e.los) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) dl[i] = dl_next[i];
-                if (j + 1 < kCols / 16) {
+                for (int k = 0; k < kRep; ++k) dl[k] = dl_next[k];
+                if (b + 1 < kBlocks) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        dl_next[i] = __ldg(reinterpret_cast<const float2*>(e.dlos + o0 + 16 + i * rstep));
+                    for (int k = 0; k < kRep; ++k)
+                        dl_next[k] = __ldg(reinterpret_cast<const float2*>(e.dlos + offset(b + 1, k)));
                 }
             }
-            uint32_t v[16];
+            uint32_t v[4 * kRep];
             if (e.mma) {
-                tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(e.acc * kTileN + col0), v);
+                tmem_ld_16x256b<kRep>(tacc + ((uint32_t)(32 * lg + 16 * h) << 16) + (uint32_t)(cg * kCols + kBlkCols * jj), v);
             } else {
 #pragma unroll
-                for (int k = 0; k < 16; ++k) v[k] = 0u;
+                for (int k = 0; k < 4 * kRep; ++k) v[k] = 0u;
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                sts128(sbase + stage_off(rw, 4 * part + k), v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-            __syncwarp();
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                float2 re, im;
-                asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(re.x), "=f"(re.y) : "r"(s_re + 512u * i));
-                asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(im.x), "=f"(im.y) : "r"(s_im + 512u * i));
-                float4 o = kF16 ? make_float4(re.x * e.isc, im.x * e.isc, re.y * e.isc, im.y * e.isc)
-                                : make_float4(re.x, im.x, re.y, im.y);
+            for (int k = 0; k < kRep; ++k) {
+                const float re0 = __uint_as_float(v[4 * k]), re1 = __uint_as_float(v[4 * k + 1]);
+                const float im0 = __uint_as_float(v[4 * k + 2]), im1 = __uint_as_float(v[4 * k + 3]);
+                float4 o = kF16 ? make_float4(re0 * e.isc, im0 * e.isc, re1 * e.isc, im1 * e.isc)
+                                : make_float4(re0, im0, re1, im1);
                 if (e.los) {
                     float sn, cs;
-                    phasor(e.foc * dl[i].x, sn, cs);
+                    phasor(e.foc * dl[k].x, sn, cs);
                     o.x = fmaf(e.wl.x, cs, fmaf(-e.wl.y, sn, o.x));
                     o.y = fmaf(e.wl.x, sn, fmaf(e.wl.y, cs, o.y));
-                    phasor(e.foc * dl[i].y, sn, cs);
+                    phasor(e.foc * dl[k].y, sn, cs);
                     o.z = fmaf(e.wl.x, cs, fmaf(-e.wl.y, sn, o.z));
                     o.w = fmaf(e.wl.x, sn, fmaf(e.wl.y, cs, o.w));
                 }
-                *reinterpret_cast<float4*>(e.Hf + o0 + i * rstep) = o;
+                *reinterpret_cast<float4*>(e.Hf + offset(b, k)) = o;
             }
-            __syncwarp();
         }
         return;
     }
 #pragma unroll 1
-    for (int j = 0; j < kCols / 16; ++j) {
-        const int col0 = cg * kCols + 16 * j;
-        const int p = e.p0 + col0 + 2 * c;
-        // LoS delays of the four (receive element, pair) outputs of this lane,
-        // requested before the tensor-memory load so that their latency overlaps it
-        float2 dl[4];
+    for (int b = 0; b < kBlocks; ++b) {
+        const int h = b / kJ, jj = b % kJ;
+        const int q = e.q0 + 16 * lg + 8 * h + qa;
+        const int pb = e.p0 + cg * kCols + kBlkCols * jj + pc;
+        // LoS delays of this lane's outputs, requested before the tensor-memory
+        // load so that their latency overlaps it
+        float2 dl[kRep];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int q = e.q0 + 16 * lg + 4 * i + (lane >> 3);
-            dl[i] = make_float2(0.f, 0.f);
+        for (int k = 0; k < kRep; ++k) {
+            const int p = pb + 8 * k;
+            dl[k] = make_float2(0.f, 0.f);
             if (e.los && q < e.Nr && p < e.Nt) {
                 const float* src = e.dlos + (int64_t)q * e.Nt + p;
-                if (p + 1 < e.Nt && ((((uintptr_t)src) & 7) == 0)) dl[i] = __ldg(reinterpret_cast<const float2*>(src));
-                else dl[i] = make_float2(__ldg(src), p + 1 < e.Nt ? __ldg(src + 1) : 0.f);
+                if (p + 1 < e.Nt && ((((uintptr_t)src) & 7) == 0)) dl[k] = __ldg(reinterpret_cast<const float2*>(src));
+                else dl[k] = make_float2(__ldg(src), p + 1 < e.Nt ? __ldg(src + 1) : 0.f);
             }
         }
-        uint32_t v[16];
+        uint32_t v[4 * kRep];
         if (e.mma) {
-            tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(e.acc * kTileN + col0), v);
+            tmem_ld_16x256b<kRep>(tacc + ((uint32_t)(32 * lg + 16 * h) << 16) + (uint32_t)(cg * kCols + kBlkCols * jj), v);
         } else {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] = 0u;
+            for (int k = 0; k < 4 * kRep; ++k) v[k] = 0u;
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            sts128(sbase + stage_off(rw, 4 * part + k), v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-        __syncwarp();
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = 4 * i + (lane >> 3);
-            const int q = e.q0 + 16 * lg + r;
-            float2 re, im;
-            asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
-                         : "=f"(re.x), "=f"(re.y)
-                         : "r"(sbase + stage_off(r, c >> 1) + 8u * (uint32_t)(c & 1)));
-            asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
-                         : "=f"(im.x), "=f"(im.y)
-                         : "r"(sbase + stage_off(r, 4 + (c >> 1)) + 8u * (uint32_t)(c & 1)));
-            float4 o = make_float4(re.x * e.isc, im.x * e.isc, re.y * e.isc, im.y * e.isc);
+        for (int k = 0; k < kRep; ++k) {
+            const int p = pb + 8 * k;
+            const float re0 = __uint_as_float(v[4 * k]), re1 = __uint_as_float(v[4 * k + 1]);
+            const float im0 = __uint_as_float(v[4 * k + 2]), im1 = __uint_as_float(v[4 * k + 3]);
+            float4 o = make_float4(re0 * e.isc, im0 * e.isc, re1 * e.isc, im1 * e.isc);
             if (e.los) {
                 float sn, cs;
-                phasor(e.foc * dl[i].x, sn, cs);
+                phasor(e.foc * dl[k].x, sn, cs);
                 o.x = fmaf(e.wl.x, cs, fmaf(-e.wl.y, sn, o.x));
                 o.y = fmaf(e.wl.x, sn, fmaf(e.wl.y, cs, o.y));
-                phasor(e.foc * dl[i].y, sn, cs);
+                phasor(e.foc * dl[k].y, sn, cs);
                 o.z = fmaf(e.wl.x, cs, fmaf(-e.wl.y, sn, o.z));
                 o.w = fmaf(e.wl.x, sn, fmaf(e.wl.y, cs, o.w));
             }
@@ -372,7 +356,6 @@ __device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t tmem, unsig
                 }
             }
         }
-        __syncwarp();
     }
 }
 
@@ -382,8 +365,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
     static_assert(kTcThreads % kTileN == 0 && 64 * (kChunkP / 4) <= kTcThreads, "generation units");
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* stage_out = smem + 2 * Sh::kStage;
-    uint64_t* bars = (uint64_t*)(stage_out + Sh::kOut);
+    uint64_t* bars = (uint64_t*)(smem + 2 * Sh::kStage);
     // bars: mma_done[0..1] (per operand stage), acc_full[0..1] (per accumulator),
     // never (injected fault), drain (final wait before the tensor memory is freed)
     const uint32_t bar0 = smem_u32(bars);
@@ -472,13 +454,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
                     }
                 }
                 // A': receive element q, paths nb + 4 c16 .. + 3, as the two rows
-                // 2q (Re A, -Im A) and 2q+1 (Im A, Re A); lane pairs take
-                // neighbouring chunks of one receive element, so that a quarter
-                // warp's 16-byte stores land in 8 distinct bank groups of the
-                // swizzled rows 2q and 2q+1 (at most 64 x 8 units: one per thread)
+                // r(q) (Re A, -Im A) and i(q) (Im A, Re A); consecutive lanes take
+                // consecutive receive elements (rows r(q) & 7 = q & 7), so that a
+                // quarter warp's 16-byte stores land in 8 distinct bank groups of
+                // the swizzled rows and a warp shares its weights (at most 64 x 8
+                // units: one per thread)
                 const int v = tid;
                 if (v < 64 * n16) {
-                    const int ql = (v >> 1) & 63, c16 = (v & 1) + 2 * (v >> 7);
+                    const int ql = v & 63, c16 = v >> 6;
                     const int q = x.q0 + ql;
                     const int n = nb + 4 * c16;
                     float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -499,13 +482,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
                         const float ar = (wr[k] * cs - wi[k] * sn) * sc;
                         const float ai = (wr[k] * sn + wi[k] * cs) * sc;
                         split2<kF16>(ar, -ai, h0[k], l0[k]);
-                        // row 2q+1 holds (Im A, Re A): the same halves swapped, with
+                        // row i(q) holds (Im A, Re A): the same halves swapped, with
                         // the sign of -Im A flipped (rounding to nearest is symmetric,
                         // so these are the bits of a split of (ai, ar))
                         h1[k] = __byte_perm(h0[k], 0u, 0x1032) ^ 0x8000u;
                         l1[k] = __byte_perm(l0[k], 0u, 0x1032) ^ 0x8000u;
                     }
-                    const uint32_t o0 = chunk_off(2 * ql, c16), o1 = chunk_off(2 * ql + 1, c16);
+                    const uint32_t o0 = chunk_off(acc_row(ql, 0), c16), o1 = chunk_off(acc_row(ql, 1), c16);
                     sts128(smem_u32(sA_hi) + o0, h0[0], h0[1], h0[2], h0[3]);
                     sts128(smem_u32(sA_lo) + o0, l0[0], l0[1], l0[2], l0[3]);
                     sts128(smem_u32(sA_hi) + o1, h1[0], h1[1], h1[2], h1[3]);
@@ -556,7 +539,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
                 ok = __all_sync(0xffffffffu, mbar_wait(bar(2 + prev.acc), prev.acc_parity));
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             }
-            if (ok) tc_epilogue<kF16, kTileN>(prev, tmem, stage_out, warp, lane);
+            if (ok) tc_epilogue<kF16, kTileN>(prev, tmem, warp, lane);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             epi_ok = epi_ok && ok;
         }
@@ -569,7 +552,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
             ok = __all_sync(0xffffffffu, mbar_wait(bar(2 + prev.acc), prev.acc_parity));
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
-        if (ok) tc_epilogue<kF16, kTileN>(prev, tmem, stage_out, warp, lane);
+        if (ok) tc_epilogue<kF16, kTileN>(prev, tmem, warp, lane);
         epi_ok = epi_ok && ok;
     }
     failed = __syncthreads_or(failed || !epi_ok) != 0;

@@ -111,6 +111,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 16 lanes x (8 kRep) columns of 32 bits starting at lane L of the address:
+// per 8-column repeat k, thread t receives r[4k], r[4k+1] = lane L + t/4,
+// columns 8k + 2(t%4) and + 1, and r[4k+2], r[4k+3] = the same columns of
+// lane L + 8 + t/4; then the wait
+template <int kRep>
+__device__ __forceinline__ void tmem_ld_16x256b(uint32_t taddr, uint32_t* r);
+template <>
+__device__ __forceinline__ void tmem_ld_16x256b<2>(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+template <>
+__device__ __forceinline__ void tmem_ld_16x256b<4>(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // 16-byte asynchronous global -> shared copy (cp.async, L2 only), its
 // commit group and the wait for all but the newest N groups
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr) {
