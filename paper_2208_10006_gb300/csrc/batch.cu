@@ -246,16 +246,17 @@ __global__ void __launch_bounds__(kBThreads) k_batch_delays(const BatchJobDev* _
         const int n = it % npad, g = it / npad;
         const bool tx = g < gt;
         const int e0 = (tx ? g : g - gt) * 8, e1 = min(tx ? Nt : Nr, e0 + 8);
-        float* dst = tx ? dt + J->dt_base : dr + J->dr_base;
+        // element e, path n at [n / 4][e][n % 4] (layout in synth_ops.cuh)
+        float* dst = (tx ? dt + J->dt_base : dr + J->dr_base) + (int64_t)(n >> 2) * (tx ? Nt : Nr) * 4 + (n & 3);
         if (n < nrefl) {
             const int64_t slot = J->path_base + n + n0;
             const int m = paths.nb[slot];
             const d3 Pk = ld3(paths.pts + (slot * kKmax + (tx ? 0 : m - 1)) * 3);
             const double ref = dist_rn(tx ? T0 : R0, Pk);
             const double* el = tx ? J->tx_elem : J->rx_elem;
-            for (int e = e0; e < e1; ++e) dst[(int64_t)e * path_cap + n] = el_delay(el + 3 * e, Pk, ref);
+            for (int e = e0; e < e1; ++e) dst[(int64_t)e * 4] = el_delay(el + 3 * e, Pk, ref);
         } else {
-            for (int e = e0; e < e1; ++e) dst[(int64_t)e * path_cap + n] = 0.f;
+            for (int e = e0; e < e1; ++e) dst[(int64_t)e * 4] = 0.f;
         }
     }
     (void)ne;

@@ -3,14 +3,17 @@
 // same arithmetic (and therefore give bit-identical H for the same paths).
 //
 // Layout, for the Pr reflected paths of one receiver padded to Pp (a multiple
-// of 4; padded entries are zero):
+// of 8; padded entries are zero):
 //   w   [F][Pp]  float2  g_n(f) exp(-j 2 pi f L_n / c), reflected paths only
 //   wl  [F]      float2  the same for the LoS path (zero when there is none)
 //   sc  [F]      float   FP16 form: the power of two that brings
 //                        max_n max(|Re w|, |Im w|) into [1/2, 1) (1 if all zero)
-//   dtT [Nt][Pp] float   |T_p - P1| - |T_0 - P1|   (P1 first interaction point)
-//   drT [Nr][Pp] float   |R_q - Pm| - |R_0 - Pm|   (Pm last interaction point)
+//   dtT [Pp/4][Nt][4] float   |T_p - P1| - |T_0 - P1|   (P1 first interaction point)
+//   drT [Pp/4][Nr][4] float   |R_q - Pm| - |R_0 - Pm|   (Pm last interaction point)
 //   dl  [Nr][Nt] float   |T_p - R_q| - |T_0 - R_0|
+// (the delay tables in groups of 4 paths, element-major within a group, so
+// that consecutive threads, on consecutive elements, read consecutive 16-byte
+// groups)
 #pragma once
 #include "sbr_internal.cuh"
 

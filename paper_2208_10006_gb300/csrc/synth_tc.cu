@@ -433,13 +433,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
                 {
                     const int pl = tid % kTileN;
                     const int p = x.p0 + pl;
-                    const float* src = x.dtT + (int64_t)(p < x.Nt ? p : 0) * x.Pp + nb;
+                    // [Pp / 4][Nt] groups of 4 paths: consecutive lanes read
+                    // consecutive 16-byte groups
+                    const float4* src = reinterpret_cast<const float4*>(x.dtT) + (int64_t)(nb >> 2) * x.Nt + (p < x.Nt ? p : 0);
                     const uint32_t b_hi = smem_u32(sB_hi) + (uint32_t)pl * 128u;
                     const uint32_t b_lo = smem_u32(sB_lo) + (uint32_t)pl * 128u;
 #pragma unroll 2
                     for (int c16 = tid / kTileN; c16 < n16; c16 += kTcThreads / kTileN) {
                         float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (p < x.Nt) d4 = __ldg(reinterpret_cast<const float4*>(src + 4 * c16));
+                        if (p < x.Nt) d4 = __ldg(src + (int64_t)c16 * x.Nt);
                         float vr[4], vi[4];
                         phasor(x.foc * d4.x, vi[0], vr[0]);
                         phasor(x.foc * d4.y, vi[1], vr[1]);
@@ -467,7 +469,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
                     float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
                     float4 w01 = d4, w23 = d4;
                     if (q < x.Nr) {
-                        d4 = __ldg(reinterpret_cast<const float4*>(x.drT + (int64_t)q * x.Pp + n));
+                        d4 = __ldg(reinterpret_cast<const float4*>(x.drT) + (int64_t)(n >> 2) * x.Nr + q);
                         w01 = __ldg(reinterpret_cast<const float4*>(x.wf + n));
                         w23 = __ldg(reinterpret_cast<const float4*>(x.wf + n + 2));
                     }
@@ -634,18 +636,19 @@ __global__ void k_tc_prep(const __grid_constant__ TcPrep a) {
             const int n = (int)(u % a.Pp), e0 = (int)(u / a.Pp) * kPrepG;
             const int ne = tx ? a.Nt : a.Nr;
             const double* elem = tx ? a.tx_elem : a.rx_elem;
-            float* dst = (tx ? a.dtT : a.drT) + n;
+            // element e, path n at [n / 4][e][n % 4]
+            float* dst = (tx ? a.dtT : a.drT) + (int64_t)(n >> 2) * ne * 4 + (n & 3);
             if (n < nrefl) {
                 const int i = n + n0, m = a.nb[i];
                 const d3 P = ld3(a.pts + ((int64_t)i * kKmax + (tx ? 0 : m - 1)) * 3);
                 const double ref = dist_rn(tx ? a.T0 : ld3(a.R0), P);
 #pragma unroll
                 for (int k = 0; k < kPrepG; ++k)
-                    if (e0 + k < ne) dst[(int64_t)(e0 + k) * a.Pp] = el_delay(elem + 3 * (e0 + k), P, ref);
+                    if (e0 + k < ne) dst[(int64_t)(e0 + k) * 4] = el_delay(elem + 3 * (e0 + k), P, ref);
             } else {
 #pragma unroll
                 for (int k = 0; k < kPrepG; ++k)
-                    if (e0 + k < ne) dst[(int64_t)(e0 + k) * a.Pp] = 0.f;
+                    if (e0 + k < ne) dst[(int64_t)(e0 + k) * 4] = 0.f;
             }
         } else {
             const int64_t u = t - n_dt - n_dr;
