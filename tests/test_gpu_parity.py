@@ -356,11 +356,13 @@ TC_TOL = {2: (3e-5, 1e-5), 3: (1e-5, 3e-6)}   # form: (max |dH|/max|H|, median r
 
 
 @pytest.mark.parametrize("form", [2, 3])
-@pytest.mark.parametrize("ny,nz,nr,F", [(16, 16, 64, 16), (10, 10, 10, 5), (20, 15, 70, 3)])
+@pytest.mark.parametrize("ny,nz,nr,F", [(16, 16, 64, 16), (10, 10, 10, 5), (20, 15, 70, 3), (9, 7, 13, 4)])
 def test_tensor_core_synthesis_matches_oracle(sbr, ny, nz, nr, F, form):
     # BF16 (form 2) or FP16 (form 3) hi/lo split on tcgen05 against the FP64
     # oracle's direct sum, element by element, on the GPU's path list; shapes
-    # cover one tile, ragged tiles (Nt=100, Nr=10) and two M and N tiles (Nr=70, Nt=300)
+    # cover one tile, ragged tiles (Nt=100, Nr=10), two M and N tiles (Nr=70,
+    # Nt=300) and an odd row length (Nt=63: rows of H start on odd elements,
+    # Nr=13: a partial group of 8 receive elements)
     sc = scenes.config3(N=60, K=3, F=F, ny_tx=ny, nz_tx=nz, n_rx=nr)
     r = sbr.run_scene(sc)
     d = r["dev"]
