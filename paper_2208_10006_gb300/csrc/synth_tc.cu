@@ -611,17 +611,20 @@ __global__ void k_tc_prep(const __grid_constant__ TcPrep a) {
         if (f >= a.F) return;
         const double fr = a.freqs[f];
         float m = 0.f;
-        for (int n = lane; n < a.Pp; n += 32) {
+        // index Pp is the LoS weight, taken by a lane of the last round (often
+        // an idle one) instead of after the reduction
+        for (int n = lane; n <= a.Pp; n += 32) {
+            if (n == a.Pp) {
+                a.wl[f] = n0 ? synth_weight(a.g[f], fr, a.L[0]) : make_float2(0.f, 0.f);
+                continue;
+            }
             float2 ww = make_float2(0.f, 0.f);
             if (n < nrefl) ww = synth_weight(a.g[(int64_t)(n + n0) * a.F + f], fr, a.L[n + n0]);
             a.w[(int64_t)f * a.Pp + n] = ww;
             m = fmaxf(m, fmaxf(fabsf(ww.x), fabsf(ww.y)));
         }
         for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) {
-            a.sc[f] = synth_scale(m);
-            a.wl[f] = n0 ? synth_weight(a.g[f], fr, a.L[0]) : make_float2(0.f, 0.f);
-        }
+        if (lane == 0) a.sc[f] = synth_scale(m);
         return;
     }
     // delays; consecutive threads write consecutive words of a row
