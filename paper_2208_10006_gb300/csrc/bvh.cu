@@ -50,6 +50,7 @@ __device__ __forceinline__ void bounds_block_reduce(float* v, float (*red)[32], 
 }
 
 __global__ void k_bounds(const float* __restrict__ box, int64_t n, float* __restrict__ part) {
+    ::sbr::pdl_wait();
     __shared__ float red[12][32];
     float v[12];
     for (int a = 0; a < 3; ++a) {
@@ -67,6 +68,7 @@ __global__ void k_bounds(const float* __restrict__ box, int64_t n, float* __rest
 }
 
 __global__ void k_bounds_final(const float* __restrict__ part, int nparts, float* __restrict__ out) {
+    ::sbr::pdl_wait();
     __shared__ float red[12][32];
     float v[12];
     for (int a = 0; a < 3; ++a) {
@@ -90,6 +92,7 @@ __device__ __forceinline__ uint32_t expand_bits(uint32_t x) {
 __global__ void k_morton(const float* __restrict__ box, int64_t n, const float* __restrict__ bnd,
                          uint32_t* __restrict__ code, uint32_t* __restrict__ idx, int32_t* __restrict__ flag,
                          int64_t nn, int32_t* __restrict__ depth) {
+    ::sbr::pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (i < nn) flag[i] = 0;
@@ -118,6 +121,7 @@ __device__ __forceinline__ int delta(const uint32_t* __restrict__ code, int64_t 
 __global__ void k_karras(const uint32_t* __restrict__ code, int64_t n, int32_t* __restrict__ left,
                          int32_t* __restrict__ right, int32_t* __restrict__ parent_int,
                          int32_t* __restrict__ parent_leaf, int32_t* __restrict__ span) {
+    ::sbr::pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     int d = (delta(code, n, i, i + 1) - delta(code, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -165,6 +169,7 @@ __global__ void k_refit(const float* __restrict__ prim_box, const int32_t* __res
                         const int32_t* __restrict__ right, const int32_t* __restrict__ parent_int,
                         const int32_t* __restrict__ parent_leaf, int32_t* __restrict__ flag,
                         float* lbox, float* ibox, int32_t* hd, int32_t* __restrict__ depth) {
+    ::sbr::pdl_wait();
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const float* src = prim_box + 6 * (int64_t)order[j];
@@ -225,6 +230,7 @@ __global__ void k_emit(int64_t n, const int32_t* __restrict__ left, const int32_
                        const int32_t* __restrict__ span, int leaf_max,
                        const float* __restrict__ lbox, const float* __restrict__ ibox, float pad,
                        float4* __restrict__ nodes, float* __restrict__ root) {
+    ::sbr::pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nn = n > 1 ? n - 1 : 1;
     if (i >= nn) return;
@@ -526,6 +532,7 @@ __global__ void k_tri_prep(const float* __restrict__ tri_in, const int32_t* __re
                            int32_t S, float* __restrict__ tri, int32_t* __restrict__ surf,
                            float* __restrict__ box, double* __restrict__ nrm, uint32_t* __restrict__ key,
                            uint32_t* __restrict__ val, unsigned int* h_status) {
+    ::sbr::pdl_wait();
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     float v[9];
@@ -585,6 +592,7 @@ sbr_status host_flag(HostFlag** out) {
 __global__ void k_tri_pack(const float* __restrict__ tri, const int32_t* __restrict__ surf,
                            const double* __restrict__ nrm, const int32_t* __restrict__ order,
                            int64_t T, float4* __restrict__ rot, float4* __restrict__ plane) {
+    ::sbr::pdl_wait();
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= T) return;
     int64_t t = order[j];
@@ -607,6 +615,7 @@ __global__ void k_tri_pack(const float* __restrict__ tri, const int32_t* __restr
 
 __global__ void k_surface_offsets(const uint32_t* __restrict__ key, int64_t T, int32_t S,
                                   int32_t* __restrict__ s_off) {
+    ::sbr::pdl_wait();
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s > S) return;
     int64_t lo = 0, hi = T;  // first position with key >= s
@@ -650,15 +659,15 @@ sbr_status build_lbvh(const float* prim_box, int64_t n, float pad_rel, int leaf_
     SBR_TRY(dalloc_n(&out->nodes, 4 * nn, s));
     SBR_TRY(dalloc_n(&out->d_root, 6, s));
     const int nparts = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 2 * (int64_t)sm_count());
-    ::sbr::note_launch(), k_bounds<<<nparts, 256, 0, s>>>(prim_box, n, part);
-    ::sbr::note_launch(), k_bounds_final<<<1, 256, 0, s>>>(part, nparts, bnd);
-    ::sbr::note_launch(), k_morton<<<blocks_for(n), kThreads, 0, s>>>(prim_box, n, bnd, code, idx, flag, nn, d_depth);
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_bounds, dim3(nparts), dim3(256), 0, s, prim_box, n, part);
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_bounds_final, dim3(1), dim3(256), 0, s, part, nparts, bnd);
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_morton, dim3(blocks_for(n)), dim3(kThreads), 0, s, prim_box, n, bnd, code, idx, flag, nn, d_depth);
     SBR_TRY_CUDA(cudaGetLastError());
     SBR_TRY(radix_sort_pairs(code, idx, n, 30, s));
-    if (n > 1) ::sbr::note_launch(), k_karras<<<blocks_for(n - 1), kThreads, 0, s>>>(code, n, left, right, pint, pleaf, span);
-    ::sbr::note_launch(), k_refit<<<blocks_for(n), kThreads, 0, s>>>(prim_box, (const int32_t*)idx, n, left, right, pint,
+    if (n > 1) ::sbr::note_launch(), (void)::sbr::launch_pdl(k_karras, dim3(blocks_for(n - 1)), dim3(kThreads), 0, s, code, n, left, right, pint, pleaf, span);
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_refit, dim3(blocks_for(n)), dim3(kThreads), 0, s, prim_box, (const int32_t*)idx, n, left, right, pint,
                                                pleaf, flag, lbox, ibox, hd, d_depth);
-    ::sbr::note_launch(), k_emit<<<blocks_for(nn), kThreads, 0, s>>>(n, left, right, span, leaf_max, lbox, ibox, pad_rel, out->nodes,
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_emit, dim3(blocks_for(nn)), dim3(kThreads), 0, s, n, left, right, span, leaf_max, lbox, ibox, pad_rel, out->nodes,
                                                out->d_root);
     SBR_TRY_CUDA(cudaGetLastError());
     // the cut: subtrees of at most lim primitives (about 650 of them at any n);
@@ -731,19 +740,19 @@ sbr_status bvh_build(const float* tri, const int32_t* surf, int64_t T, int32_t S
     HostFlag* hf;
     SBR_TRY(host_flag(&hf));
     *(volatile unsigned*)hf->h = 0u;
-    ::sbr::note_launch(), k_tri_prep<<<blocks_for(T), kThreads, 0, s>>>(tri, surf, T, S, b->tri, b->surf, box, b->nrm,
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_tri_prep, dim3(blocks_for(T)), dim3(kThreads), 0, s, tri, surf, T, S, b->tri, b->surf, box, b->nrm,
                                                                       key, val, hf->d);
     SBR_TRY_CUDA(cudaGetLastError());
     SBR_TRY_CUDA(cudaEventRecord(hf->ev, s));
     // relative box padding: 2^-20 of (|x| + 1) covers FP32 ray/box rounding
     SBR_TRY(build_lbvh(box, T, 1.0f / (1 << 20), tri_leaf_size(), &b->tree, b->d_depth, s, sah_top));
-    ::sbr::note_launch(), k_tri_pack<<<blocks_for(T), kThreads, 0, s>>>(b->tri, b->surf, b->nrm, b->tree.order, T,
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_tri_pack, dim3(blocks_for(T)), dim3(kThreads), 0, s, b->tri, b->surf, b->nrm, b->tree.order, T,
                                                   b->tri_rot, b->plane_sorted);
     // faces per surface, ascending face id (stable sort on the surface id)
     int bits = 1;
     while (bits < 31 && ((int64_t)1 << bits) < (int64_t)S) ++bits;
     SBR_TRY(radix_sort_pairs(key, val, T, bits, s));
-    ::sbr::note_launch(), k_surface_offsets<<<blocks_for((int64_t)S + 1), kThreads, 0, s>>>(key, T, S, b->s_off);
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_surface_offsets, dim3(blocks_for((int64_t)S + 1)), dim3(kThreads), 0, s, key, T, S, b->s_off);
     SBR_TRY_CUDA(cudaGetLastError());
     SBR_TRY_CUDA(cudaEventSynchronize(hf->ev));
     const unsigned h_status = *(volatile unsigned*)hf->h;

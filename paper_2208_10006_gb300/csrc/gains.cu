@@ -23,6 +23,7 @@ k_gains(int64_t P, int32_t F, const int32_t* __restrict__ nb, const int32_t* __r
         const double* __restrict__ L, const double* __restrict__ jones, const sbr_material* __restrict__ mats,
         int32_t S, const double* __restrict__ freqs, const float* __restrict__ gamma,
         const float* __restrict__ disp, int pol, float2* __restrict__ g) {
+    ::sbr::pdl_wait();
     __shared__ Refl s_rf[kGainThreads];
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t item = t / kGainLanes;
@@ -59,7 +60,7 @@ sbr_status gains_run(const sbr_path_list* pl, const sbr_material* mats, int32_t 
     // small blocks of eight lanes per (path, frequency): the FP64 chains are
     // latency-bound, so they are spread over every SM and split by reflection
     const int64_t threads = n * kGainLanes;
-    ::sbr::note_launch(), k_gains<<<(unsigned)((threads + kGainThreads - 1) / kGainThreads), kGainThreads, 0, s>>>(
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_gains, dim3((unsigned)((threads + kGainThreads - 1) / kGainThreads)), dim3(kGainThreads), 0, s,
         pl->P, F, pl->nb, pl->surf, pl->L, pl->jones, mats, S, freqs, gamma, disp, pol, g);
     SBR_TRY_CUDA(cudaGetLastError());
     return SBR_OK;

@@ -149,6 +149,7 @@ __device__ __forceinline__ df df_max(df a, df b) { return (b.hi > a.hi || (b.hi 
 // follows in FP64 once.
 __global__ void k_alpha_df(const __grid_constant__ IcoLattice t, int N, int64_t per_face,
                            unsigned long long* __restrict__ best) {
+    ::sbr::pdl_wait();
     const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     df m{0.f, 0.f};
     if (l < per_face) {
@@ -177,6 +178,7 @@ __global__ void k_alpha_df(const __grid_constant__ IcoLattice t, int N, int64_t 
 }
 
 __global__ void k_alpha_df_store(const unsigned long long* best, double* alpha) {
+    ::sbr::pdl_wait();
     const double c2 = __longlong_as_double((long long)*best);
     *alpha = 2.0 * asin(0.5 * sqrt(c2));
 }
@@ -187,9 +189,9 @@ sbr_status launch_alpha_fast(int32_t N, double* alpha, cudaStream_t s) {
     unsigned long long* best;
     SBR_TRY(dalloc_n(&best, 1, s));
     SBR_TRY_CUDA(cudaMemsetAsync(best, 0, sizeof(unsigned long long), s));
-    ::sbr::note_launch(), k_alpha_df<<<(unsigned)((per_face + 255) / 256), 256, 0, s>>>(make_ico_lattice(), N,
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_alpha_df, dim3((unsigned)((per_face + 255) / 256)), dim3(256), 0, s, make_ico_lattice(), N,
                                                                                           per_face, best);
-    ::sbr::note_launch(), k_alpha_df_store<<<1, 1, 0, s>>>(best, alpha);
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_alpha_df_store, dim3(1), dim3(1), 0, s, best, alpha);
     SBR_TRY_CUDA(cudaGetLastError());
     dfree(best, s);
     return SBR_OK;

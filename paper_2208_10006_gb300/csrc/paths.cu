@@ -25,6 +25,7 @@ inline unsigned nblk(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + kTh
 
 __global__ void k_collect(const uint32_t* __restrict__ state, size_t cap, uint32_t* __restrict__ idx,
                           unsigned int* __restrict__ count) {
+    ::sbr::pdl_wait();
     size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool ready = s < cap && state[s] == 2u;
     unsigned m = __ballot_sync(0xffffffffu, ready);
@@ -47,6 +48,7 @@ struct PackWord {
 __global__ void k_key_pack(const uint32_t* __restrict__ key, const uint32_t* __restrict__ idx,
                            const uint32_t* __restrict__ perm, int64_t n, const __grid_constant__ PackWord pw,
                            uint32_t* __restrict__ out) {
+    ::sbr::pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t* k = key + (size_t)idx[perm[i]] * kKeyWords;
@@ -59,6 +61,7 @@ __global__ void k_key_pack(const uint32_t* __restrict__ key, const uint32_t* __r
 }
 
 __global__ void k_iota(uint32_t* p, int64_t n) {
+    ::sbr::pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = (uint32_t)i;
 }
@@ -98,6 +101,7 @@ struct RefineArgs {
 
 // one warp per key (see refine_key); lane 0 writes the validity and receiver
 __global__ void k_refine(const __grid_constant__ RefineArgs a) {
+    ::sbr::pdl_wait();
     const int lane = threadIdx.x & 31;
     int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= a.n) return;
@@ -119,6 +123,7 @@ __global__ void k_refine(const __grid_constant__ RefineArgs a) {
 // one thread per key, with the faces the kept ray hit as hints (the trace's
 // per-bounce face record): the same results as k_refine
 __global__ void k_refine_solo(const __grid_constant__ RefineArgs a) {
+    ::sbr::pdl_wait();
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool have = i < a.n;   // keyless lanes still take part in the warp's scans
@@ -156,6 +161,7 @@ struct CompactArgs {
 };
 
 __global__ void k_compact_all(const __grid_constant__ CompactArgs a) {
+    ::sbr::pdl_wait();
     const int lane = threadIdx.x & 31;
     int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= a.n || !a.valid[r]) return;
@@ -171,6 +177,7 @@ __global__ void k_compact_all(const __grid_constant__ CompactArgs a) {
 // host-mapped buffer; thread 0 also stores P there
 __global__ void k_rx_offsets(const int32_t* __restrict__ rx, const unsigned* __restrict__ P, int32_t n_rx,
                              int32_t* __restrict__ off, unsigned* h_P, int32_t* h_off) {
+    ::sbr::pdl_wait();
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r > n_rx) return;
     int64_t lo = 0, hi = *P;
@@ -196,6 +203,7 @@ static_assert(sizeof(MappedHead) % 8 == 0 && sizeof(TraceCountersDev) % 8 == 0, 
 // the key count, alpha and the trace's counters, stored to the host-mapped head
 __global__ void k_peek_counts(const unsigned* __restrict__ count, const double* __restrict__ alpha,
                               const TraceCountersDev* __restrict__ cnt, MappedHead* h) {
+    ::sbr::pdl_wait();
     const int i = threadIdx.x;
     constexpr int kWords = (int)(sizeof(TraceCountersDev) / 8);
     if (i < kWords)
@@ -273,8 +281,8 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     MappedHead* hh = reinterpret_cast<MappedHead*>(hm);
     volatile unsigned* h_count = &hh->count;
     int32_t* h_off = reinterpret_cast<int32_t*>(hm + sizeof(MappedHead));
-    ::sbr::note_launch(), k_collect<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(tr->ht_state, cap, idx, count);
-    ::sbr::note_launch(), k_peek_counts<<<1, 32, 0, s>>>(count, tr->d_alpha, tr->cnt,
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_collect, dim3((unsigned)((cap + 255) / 256)), dim3(256), 0, s, tr->ht_state, cap, idx, count);
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_peek_counts, dim3(1), dim3(32), 0, s, count, tr->d_alpha, tr->cnt,
                                                           reinterpret_cast<MappedHead*>(dm));
     SBR_TRY_CUDA(cudaGetLastError());
     SBR_TRY_CUDA(cudaStreamSynchronize(s));
@@ -296,7 +304,7 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     uint32_t *perm, *word;
     SBR_TRY(dalloc_n(&perm, std::max<int64_t>(n, 1), s));
     SBR_TRY(dalloc_n(&word, std::max<int64_t>(n, 1), s));
-    ::sbr::note_launch(), k_iota<<<nblk(n), kThreads, 0, s>>>(perm, n);
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_iota, dim3(nblk(n)), dim3(kThreads), 0, s, perm, n);
     // key fields from the least significant (the last surface) to the most
     // (the receiver), packed greedily into 32-bit sort words; a stable LSD pass
     // per word, least significant word first, gives the lexicographic order
@@ -315,7 +323,7 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
             ++pw.nf;
             ++f0;
         }
-        ::sbr::note_launch(), k_key_pack<<<nblk(n), kThreads, 0, s>>>(tr->ht_key, idx, perm, n, pw, word);
+        ::sbr::note_launch(), (void)::sbr::launch_pdl(k_key_pack, dim3(nblk(n)), dim3(kThreads), 0, s, tr->ht_key, idx, perm, n, pw, word);
         SBR_TRY_CUDA(cudaGetLastError());
         SBR_TRY(radix_sort_pairs(word, perm, n, bits, s));
     }
@@ -358,9 +366,9 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
     if (n > 0) {
         if (a.seqf)
             // one warp per block: the keys spread over every SM (latency-bound FP64 chains)
-            ::sbr::note_launch(), k_refine_solo<<<(unsigned)((n + 31) / 32), 32, 0, s>>>(a);
+            ::sbr::note_launch(), (void)::sbr::launch_pdl(k_refine_solo, dim3((unsigned)((n + 31) / 32)), dim3(32), 0, s, a);
         else
-            ::sbr::note_launch(), k_refine<<<nblk(32 * n), kThreads, 0, s>>>(a);
+            ::sbr::note_launch(), (void)::sbr::launch_pdl(k_refine, dim3(nblk(32 * n)), dim3(kThreads), 0, s, a);
         SBR_TRY_CUDA(cudaGetLastError());
         SBR_TRY_CUDA(cudaMemcpyAsync(pos, valid, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
     }
@@ -393,10 +401,10 @@ sbr_status paths_run(const sbr_trace_result* tr, const sbr_bvh* b, sbr_path_list
                          pl->dist, pl->jones};
         const int words[11] = {1, 1, kKmax, kKmax, 2 * 3 * kKmax, 2, 4, 4, 1, 1, 2 * kJones};
         for (int f = 0; f < 11; ++f) { c.src[f] = src[f]; c.dst[f] = dst[f]; c.words[f] = words[f]; }
-        ::sbr::note_launch(), k_compact_all<<<nblk(32 * n), kThreads, 0, s>>>(c);
+        ::sbr::note_launch(), (void)::sbr::launch_pdl(k_compact_all, dim3(nblk(32 * n)), dim3(kThreads), 0, s, c);
         SBR_TRY_CUDA(cudaGetLastError());
     }
-    ::sbr::note_launch(), k_rx_offsets<<<nblk((int64_t)tr->n_rx + 1), kThreads, 0, s>>>(
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_rx_offsets, dim3(nblk((int64_t)tr->n_rx + 1)), dim3(kThreads), 0, s,
         pl->rx, count, tr->n_rx, pl->rx_off, &reinterpret_cast<MappedHead*>(dm)->count,
         reinterpret_cast<int32_t*>(dm + sizeof(MappedHead)));
     SBR_TRY_CUDA(cudaGetLastError());

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(kPdpThreads)
 k_pdp(const int32_t* __restrict__ rx_off, const double* __restrict__ L, const double* __restrict__ aod,
       const double* __restrict__ aoa, const float2* __restrict__ g, int32_t F, int32_t f_index,
       double fc, double bin_s, int32_t n_bins, float* __restrict__ pdp, double* __restrict__ stats) {
+    ::sbr::pdl_wait();
     extern __shared__ double acc[];  // [n_bins]
     const int r = blockIdx.x;
     const int32_t o0 = rx_off[r], o1 = rx_off[r + 1];
@@ -308,7 +309,7 @@ sbr_status pdp_run(const sbr_path_list* pl, const float2* g, int32_t F, int32_t 
     size_t smem = sizeof(double) * (size_t)n_bins;
     if (smem > 48 * 1024)
         SBR_TRY_CUDA(cudaFuncSetAttribute(k_pdp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ::sbr::note_launch(), k_pdp<<<pl->n_rx, kPdpThreads, smem, s>>>(pl->rx_off, pl->L, pl->aod, pl->aoa, g, F, f_index, fc,
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_pdp, dim3(pl->n_rx), dim3(kPdpThreads), smem, s, pl->rx_off, pl->L, pl->aod, pl->aoa, g, F, f_index, fc,
                                                bin_s, n_bins, pdp, stats);
     SBR_TRY_CUDA(cudaGetLastError());
     return SBR_OK;

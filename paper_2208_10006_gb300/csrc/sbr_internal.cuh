@@ -2,6 +2,7 @@
 // Not part of the public ABI (include/sbr.h).
 #pragma once
 #include <atomic>
+#include <utility>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -74,6 +75,28 @@ inline sbr_status set_smem_once(const void* func, int bytes, std::atomic<unsigne
 }
 // count of kernel launches made by the library in this process
 void note_launch();
+// Programmatic dependent launch: the kernel may be scheduled while its
+// predecessor on the stream finishes (its launch latency overlaps that tail);
+// every kernel launched this way calls pdl_wait() before its first memory
+// access, which returns once the predecessor has completed and its writes are
+// visible, so the stream order is kept (pdl_wait is a no-op for an ordinary
+// launch)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 // test-only fault injection (SBR_FAULT=alloc|timeout)
 enum { kFaultNone = 0, kFaultAlloc = 1, kFaultTimeout = 2 };
 int fault_mode();

@@ -84,12 +84,14 @@ __device__ __forceinline__ void tile_scatter(const uint32_t* kin, const uint32_t
 
 __global__ void k_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
                        uint32_t* __restrict__ hist, int nblocks) {
+    ::sbr::pdl_wait();
     tile_hist(keys, n, shift, hist, nblocks, blockIdx.x);
 }
 
 __global__ void k_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                           uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
                           int shift, const uint32_t* __restrict__ hist, int nblocks) {
+    ::sbr::pdl_wait();
     tile_scatter(kin, vin, kout, vout, n, shift, hist, nblocks, blockIdx.x);
 }
 
@@ -126,6 +128,7 @@ __device__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* total) {
 }
 
 __global__ void k_scan_blocks(uint32_t* data, int64_t n, uint32_t* block_sums) {
+    ::sbr::pdl_wait();
     int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     uint32_t x = i < n ? data[i] : 0u;
     uint32_t tot;
@@ -135,12 +138,14 @@ __global__ void k_scan_blocks(uint32_t* data, int64_t n, uint32_t* block_sums) {
 }
 
 __global__ void k_add_offsets(uint32_t* data, int64_t n, const uint32_t* offs) {
+    ::sbr::pdl_wait();
     int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     if (i < n) data[i] += offs[blockIdx.x];
 }
 
 __global__ void k_total(const uint32_t* scanned, const uint32_t* last_in, int64_t n,
                         uint32_t* total) {
+    ::sbr::pdl_wait();
     *total = n > 0 ? scanned[n - 1] + *last_in : 0u;
 }
 
@@ -242,17 +247,17 @@ sbr_status scan_rec(uint32_t* data, int64_t n, cudaStream_t s) {
     if (n <= 0) return SBR_OK;
     int64_t nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 1) {
-        ::sbr::note_launch(), k_scan_blocks<<<1, kScanBlock, 0, s>>>(data, n, nullptr);
+        ::sbr::note_launch(), (void)::sbr::launch_pdl(k_scan_blocks, dim3(1), dim3(kScanBlock), 0, s, data, n, nullptr);
         SBR_TRY_CUDA(cudaGetLastError());
         return SBR_OK;
     }
     uint32_t* sums;
     SBR_TRY(dalloc_n(&sums, nb, s));
-    ::sbr::note_launch(), k_scan_blocks<<<(unsigned)nb, kScanBlock, 0, s>>>(data, n, sums);
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_scan_blocks, dim3((unsigned)nb), dim3(kScanBlock), 0, s, data, n, sums);
     SBR_TRY_CUDA(cudaGetLastError());
     sbr_status st = scan_rec(sums, nb, s);
     if (st == SBR_OK) {
-        ::sbr::note_launch(), k_add_offsets<<<(unsigned)nb, kScanBlock, 0, s>>>(data, n, sums);
+        ::sbr::note_launch(), (void)::sbr::launch_pdl(k_add_offsets, dim3((unsigned)nb), dim3(kScanBlock), 0, s, data, n, sums);
         if (cudaGetLastError() != cudaSuccess) st = SBR_ERR_CUDA;
     }
     dfree(sums, s);
@@ -271,6 +276,7 @@ constexpr int kSmallMax = 12288;  // 2 x 2 x 4 B x 12288 = 192 KB of shared memo
 
 __global__ void __launch_bounds__(kSmallThreads)
 k_sort_small(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int n, int passes) {
+    ::sbr::pdl_wait();
     extern __shared__ uint32_t sm[];
     uint32_t* ka = sm;
     uint32_t* va = sm + kSmallMax;
@@ -355,7 +361,7 @@ sbr_status exclusive_scan_u32(uint32_t* data, int64_t n, uint32_t* total, cudaSt
     }
     sbr_status st = scan_rec(data, n, s);
     if (st == SBR_OK && total) {
-        ::sbr::note_launch(), k_total<<<1, 1, 0, s>>>(data, last, n, total);
+        ::sbr::note_launch(), (void)::sbr::launch_pdl(k_total, dim3(1), dim3(1), 0, s, data, last, n, total);
         if (cudaGetLastError() != cudaSuccess) st = SBR_ERR_CUDA;
     }
     if (last) dfree(last, s);
@@ -393,7 +399,7 @@ sbr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits,
         const size_t smem = sizeof(uint32_t) * 4 * kSmallMax;
         static std::atomic<unsigned long long> attr{0};
         SBR_TRY(set_smem_once((const void*)k_sort_small, (int)smem, &attr));
-        ::sbr::note_launch(), k_sort_small<<<1, kSmallThreads, smem, s>>>(keys, vals, (int)n, (bits + 7) / 8);
+        ::sbr::note_launch(), (void)::sbr::launch_pdl(k_sort_small, dim3(1), dim3(kSmallThreads), smem, s, keys, vals, (int)n, (bits + 7) / 8);
         SBR_TRY_CUDA(cudaGetLastError());
         return SBR_OK;
     }
@@ -428,10 +434,10 @@ sbr_status radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits,
     uint32_t *ka = keys, *va = vals, *kb = k2, *vb = v2;
     sbr_status st = SBR_OK;
     for (int p = 0; p < passes && st == SBR_OK; ++p) {
-        ::sbr::note_launch(), k_hist<<<nblocks, kSortThreads, 0, s>>>(ka, n, 8 * p, hist, nblocks);
+        ::sbr::note_launch(), (void)::sbr::launch_pdl(k_hist, dim3(nblocks), dim3(kSortThreads), 0, s, ka, n, 8 * p, hist, nblocks);
         st = scan_rec(hist, (int64_t)256 * nblocks, s);
         if (st != SBR_OK) break;
-        ::sbr::note_launch(), k_scatter<<<nblocks, kSortThreads, 0, s>>>(ka, va, kb, vb, n, 8 * p, hist, nblocks);
+        ::sbr::note_launch(), (void)::sbr::launch_pdl(k_scatter, dim3(nblocks), dim3(kSortThreads), 0, s, ka, va, kb, vb, n, 8 * p, hist, nblocks);
         if (cudaGetLastError() != cudaSuccess) {
             set_error("radix scatter launch failed");
             st = SBR_ERR_CUDA;

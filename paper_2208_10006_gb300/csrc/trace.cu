@@ -563,6 +563,7 @@ __device__ __forceinline__ int32_t settle_hit(const A& a, const df3& o, const df
 template <bool kCount>
 __global__ void __launch_bounds__(kTraceThreads, 8)
 k_trace_bounce(const __grid_constant__ TraceArgs a) {
+    ::sbr::pdl_wait();
     int stack[kStack];
     unsigned visits = 0, tests = 0, rx_visits = 0, edge = 0;
     const int lane = threadIdx.x & 31;
@@ -675,6 +676,7 @@ k_trace_bounce(const __grid_constant__ TraceArgs a) {
 template <bool kCount>
 __global__ void __launch_bounds__(kTraceThreads, 8)
 k_trace_df(const __grid_constant__ TraceArgs a) {
+    ::sbr::pdl_wait();
     int stack[kStack];
     // rays entering each bounce, counted per block in shared memory and added
     // to the global counters once at the end
@@ -1027,6 +1029,7 @@ __global__ void k_trace_setup(TraceCountersDev* __restrict__ cnt, unsigned long 
                               size_t cap, const double* __restrict__ rx, int32_t n_rx,
                               float* __restrict__ rx_box, float4* __restrict__ rx_df, double* alpha,
                               double alpha_in, float4* __restrict__ alpha_df) {
+    ::sbr::pdl_wait();
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < sizeof(TraceCountersDev) / 8) reinterpret_cast<unsigned long long*>(cnt)[i] = i == 0 ? R : 0ull;
     if (i < cap) {
@@ -1052,6 +1055,7 @@ __global__ void k_trace_setup(TraceCountersDev* __restrict__ cnt, unsigned long 
 }
 
 __global__ void k_init_table(uint32_t* state, unsigned long long* val, size_t cap) {
+    ::sbr::pdl_wait();
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cap) return;
     state[i] = 0u;
@@ -1064,6 +1068,7 @@ __global__ void k_init_table(uint32_t* state, unsigned long long* val, size_t ca
 __global__ void k_entries(const uint32_t* __restrict__ state, const uint32_t* __restrict__ key,
                           const unsigned long long* __restrict__ val, size_t cap_t, uint32_t* __restrict__ out_k,
                           unsigned long long* __restrict__ out_v, int64_t cap, unsigned long long* count) {
+    ::sbr::pdl_wait();
     const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool full = s < cap_t && state[s] == 2u;
     const unsigned m = __ballot_sync(0xffffffffu, full);
@@ -1089,6 +1094,7 @@ struct MergeArgs {
 
 __global__ void k_merge(const __grid_constant__ MergeArgs a, const uint32_t* __restrict__ keys,
                         const unsigned long long* __restrict__ vals, int64_t n) {
+    ::sbr::pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t key[kKeyWords];
         for (int k = 0; k < kKeyWords; ++k) key[k] = keys[i * kKeyWords + k];
@@ -1207,7 +1213,7 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
     }
     {
         const size_t n_set = std::max<size_t>(std::max<size_t>(cap, (size_t)tr->n_rx), sizeof(TraceCountersDev) / 8);
-        ::sbr::note_launch(), k_trace_setup<<<(unsigned)((n_set + 255) / 256), 256, 0, s>>>(
+        ::sbr::note_launch(), (void)::sbr::launch_pdl(k_trace_setup, dim3((unsigned)((n_set + 255) / 256)), dim3(256), 0, s,
             tr->cnt, (unsigned long long)R, tr->ht_state, tr->ht_val, cap, tr->rx, tr->n_rx, rxbox, rx_df,
             tr->d_alpha, p.alpha, alpha_df);
         SBR_TRY_CUDA(cudaGetLastError());
@@ -1278,18 +1284,18 @@ sbr_status trace_run(const sbr_bvh* b, sbr_trace_result* tr, cudaStream_t s) {
         a.work = &tr->cnt->work[bnc];
         if (bnc >= df_from) {
             if (count)
-                ::sbr::note_launch(), k_trace_df<true><<<grid, kTraceThreads, 0, s>>>(a);
+                ::sbr::note_launch(), (void)::sbr::launch_pdl(k_trace_df<true>, dim3(grid), dim3(kTraceThreads), 0, s, a);
             else
-                ::sbr::note_launch(), k_trace_df<false><<<grid, kTraceThreads, 0, s>>>(a);
+                ::sbr::note_launch(), (void)::sbr::launch_pdl(k_trace_df<false>, dim3(grid), dim3(kTraceThreads), 0, s, a);
             SBR_TRY_CUDA(cudaGetLastError());
             if (timing)
                 for (int k = bnc; k <= K; ++k) SBR_TRY_CUDA(cudaEventRecord(tr->ev[k + 1], s));
             break;
         }
         if (count)
-            ::sbr::note_launch(), k_trace_bounce<true><<<grid, kTraceThreads, 0, s>>>(a);
+            ::sbr::note_launch(), (void)::sbr::launch_pdl(k_trace_bounce<true>, dim3(grid), dim3(kTraceThreads), 0, s, a);
         else
-            ::sbr::note_launch(), k_trace_bounce<false><<<grid, kTraceThreads, 0, s>>>(a);
+            ::sbr::note_launch(), (void)::sbr::launch_pdl(k_trace_bounce<false>, dim3(grid), dim3(kTraceThreads), 0, s, a);
         SBR_TRY_CUDA(cudaGetLastError());
         if (timing) SBR_TRY_CUDA(cudaEventRecord(tr->ev[bnc + 1], s));
     }
@@ -1316,7 +1322,7 @@ sbr_status trace_entries_run(const sbr_trace_result* tr, uint32_t* keys, unsigne
     unsigned long long* count = nullptr;
     SBR_TRY(dalloc_n(&count, 1, s));
     SBR_TRY_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s));
-    ::sbr::note_launch(), k_entries<<<(unsigned)((cap_t + 255) / 256), 256, 0, s>>>(
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_entries, dim3((unsigned)((cap_t + 255) / 256)), dim3(256), 0, s,
         tr->ht_state, tr->ht_key, tr->ht_val, cap_t, keys, vals, cap, count);
     SBR_TRY_CUDA(cudaGetLastError());
     unsigned long long h_count = 0;
@@ -1342,7 +1348,7 @@ sbr_status trace_merge_run(sbr_trace_result* tr, const uint32_t* keys, const uns
     SBR_TRY(dalloc_n(&tr->ht_val, cap, s));
     SBR_TRY(dalloc_n(&tr->cnt, 1, s));
     SBR_TRY_CUDA(cudaMemsetAsync(tr->cnt, 0, sizeof(TraceCountersDev), s));
-    ::sbr::note_launch(), k_init_table<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(tr->ht_state, tr->ht_val, cap);
+    ::sbr::note_launch(), (void)::sbr::launch_pdl(k_init_table, dim3((unsigned)((cap + 255) / 256)), dim3(256), 0, s, tr->ht_state, tr->ht_val, cap);
     SBR_TRY_CUDA(cudaGetLastError());
     if (tr->params.alpha > 0.0) {
         unsigned long long bits;
@@ -1353,7 +1359,7 @@ sbr_status trace_merge_run(sbr_trace_result* tr, const uint32_t* keys, const uns
     if (n > 0) {
         MergeArgs a{tr->ht_state, tr->ht_key, tr->ht_val, (uint32_t)(cap - 1), tr->cnt};
         const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 8 * (int64_t)sm_count());
-        ::sbr::note_launch(), k_merge<<<grid, 256, 0, s>>>(a, keys, vals, n);
+        ::sbr::note_launch(), (void)::sbr::launch_pdl(k_merge, dim3(grid), dim3(256), 0, s, a, keys, vals, n);
         SBR_TRY_CUDA(cudaGetLastError());
     }
     return SBR_OK;
