@@ -51,16 +51,16 @@ RAY_REC_BYTES = 64      # one queued ray record (origin, direction, L, id, last 
 ALG_BYTES_PER_RAY_BOUNCE = 2 * RAY_REC_BYTES
 # DRAM bytes of one k_trace_df launch on the headline workload (N = 1000), from
 # one ncu capture of the launch (dram__bytes_read.sum + dram__bytes_write.sum)
-TRACE_DRAM_BYTES = 21_302_016 + 82_188_288
+TRACE_DRAM_BYTES = 21_319_680 + 82_202_880
 # warp instructions issued by one k_trace_df launch on the same workload, from
 # one ncu capture (smsp__inst_executed.sum). The issue peak is one warp
 # instruction per clock on each of the 4 schedulers of the 152 SMs
-TRACE_WARP_INST = 2_378_361_015
+TRACE_WARP_INST = 2_380_405_416
 # SHA-256 (first 16 hex digits) of the trace kernel's source and the local
 # headers it includes, as they were when the two counters above were captured.
 # Any later edit changes it, and the counters are then reported as null
 # (unmeasured) instead of describing a kernel that no longer exists.
-TRACE_COUNTERS_SRC = "8bf637f26ab34fda"
+TRACE_COUNTERS_SRC = "14f44f1765166e99"
 SM_COUNT = 152
 SCHEDULERS_PER_SM = 4
 SEQ_BYTES = 8           # surface id and face id appended per reflection
