@@ -334,8 +334,11 @@ __device__ bool refine_key(int lane, int m, const int32_t* seq, unsigned long lo
         return true;
     }
     d3 sv_prev{}, pout_prev{};
+    // unit segment directions, each computed once: the outgoing direction of
+    // reflection k is the incoming one of reflection k + 1
+    d3 din = unit(P[1] - P[0]);
     for (int k = 1; k <= m; ++k) {
-        d3 din = unit(P[k] - P[k - 1]), dout = unit(P[k + 1] - P[k]);
+        const d3 dout = unit(P[k + 1] - P[k]);
         double c = fabs(dot(din, nn[k]));
         d3 sv = s_vector(din, nn[k]);
         d3 pin = cross(sv, din), pout = cross(sv, dout);
@@ -352,8 +355,9 @@ __device__ bool refine_key(int lane, int m, const int32_t* seq, unsigned long lo
         }
         sv_prev = sv;
         pout_prev = pout;
+        din = dout;
     }
-    d3 dl = unit(P[m + 1] - P[m]);
+    const d3 dl = din;   // unit(P[m + 1] - P[m])
     d3 rV = pol_vec(dl, SBR_POL_V), rH = pol_vec(dl, SBR_POL_H);
     J[32] = dot(rV, sv_prev); J[33] = dot(rV, pout_prev);
     J[34] = dot(rH, sv_prev); J[35] = dot(rH, pout_prev);
