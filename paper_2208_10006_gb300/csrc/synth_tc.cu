@@ -79,8 +79,8 @@ struct TcArgs {
     int32_t Pp;                // padded row length of dtT, drT and w
     const int32_t* nb0;        // reflections of the first path: 0 = it is the LoS path
     const double* freqs;
-    const float* dtT;          // [Nt][Pp]
-    const float* drT;          // [Nr][Pp]
+    const float* dtT;          // [Pp/4][Nt][4]
+    const float* drT;          // [Pp/4][Nr][4]
     const float2* w;           // [F][Pp]
     const float2* wl;          // [F]
     const float* sc;           // [F]
@@ -592,8 +592,8 @@ struct TcPrep {
     const double* rx_elem;
     const double* R0;
     d3 T0;
-    float* dtT;
-    float* drT;
+    float* dtT;              // [Pp/4][Nt][4] (synth_ops.cuh)
+    float* drT;              // [Pp/4][Nr][4]
     float* dlos;
     float2* w;
     float2* wl;
