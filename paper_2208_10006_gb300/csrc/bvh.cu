@@ -346,11 +346,48 @@ __device__ __forceinline__ void bin_scan(int& c, float* b, bool up) {
     }
 }
 
+// lane 0 of a task's warp: the node with its two child boxes, and either the
+// item (a child of one item) or a new task per child
+__device__ void top_emit(const TopTask& tk, int nl, const float* sl, const float* sr, const TopElem* out,
+                         float4* __restrict__ nodes, const int32_t* __restrict__ slots, TopTask* next, int* s_next,
+                         int* s_slot, int* s_depth) {
+    const int b0 = tk.begin, n = tk.count;
+    int32_t ref[2];
+    const int cb[2] = {b0, b0 + nl}, cn[2] = {nl, n - nl};
+    for (int c = 0; c < 2; ++c) {
+        if (cn[c] == 1) {
+            ref[c] = out[cb[c]].ref;
+            atomicMax(s_depth, tk.depth + out[cb[c]].h);
+        } else {
+            ref[c] = slots[atomicAdd(s_slot, 1)];
+            next[atomicAdd(s_next, 1)] = TopTask{cb[c], cn[c], ref[c], tk.depth + 1};
+        }
+    }
+    float4* o = nodes + 4 * (int64_t)tk.slot;
+    o[0] = make_float4(sl[0], sl[1], sl[2], sl[3]);
+    o[1] = make_float4(sl[4], sl[5], sr[0], sr[1]);
+    o[2] = make_float4(sr[2], sr[3], sr[4], sr[5]);
+    o[3] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), 0.f, 0.f);
+}
+
+// float <-> int with the same order (for shared-memory atomicMin / atomicMax
+// on box bounds): the magnitude bits of a negative value are flipped
+__device__ __forceinline__ int ord_f(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float unord_f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+constexpr int kTopBinWords = 3 * kTopBins * 7;   // per warp: count and 6 bounds of every bin of each axis
+
 // one warp: split one task, write its node, queue its children. The items sit
-// in shared memory; lane b owns bin b of each axis and gathers it over all the
-// task's items (no atomics), then warp scans give every split's two sides.
+// in shared memory; the lanes bin the task's items in parallel into the warp's
+// shared-memory bins (counts by atomicAdd, bounds by atomicMin / atomicMax on
+// order-preserving integers: exact, so the split is independent of the
+// order), lane b then takes bin b of each axis, and warp scans give every
+// split's two sides.
 __device__ void top_task(const TopTask tk, const TopElem* in, TopElem* out, float4* __restrict__ nodes,
-                         const int32_t* __restrict__ slots, TopTask* next, int* s_next, int* s_slot, int* s_depth) {
+                         const int32_t* __restrict__ slots, TopTask* next, int* s_next, int* s_slot, int* s_depth,
+                         int* wbins) {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     const int b0 = tk.begin, n = tk.count;
@@ -369,21 +406,40 @@ __device__ void top_task(const TopTask tk, const TopElem* in, TopElem* out, floa
         }
     float sc[3];
     for (int a = 0; a < 3; ++a) sc[a] = hi[a] > lo[a] ? (float)kTopBins / (hi[a] - lo[a]) : 0.f;
-    // this lane's bin (number lane) of each axis
-    int cnt[3] = {0, 0, 0};
-    float bx[3][6];
-    for (int a = 0; a < 3; ++a)
-        for (int q = 0; q < 3; ++q) { bx[a][q] = INFINITY; bx[a][3 + q] = -INFINITY; }
-    for (int i = 0; i < n; ++i) {
+    // bin the items: wbins[a][b] = count, then [a][b][6] bounds
+    int* const bcnt = wbins;
+    int* const bbox = wbins + 3 * kTopBins;
+    for (int j = lane; j < 3 * kTopBins; j += 32) bcnt[j] = 0;
+    for (int j = lane; j < 3 * kTopBins * 6; j += 32) bbox[j] = ord_f(j % 6 < 3 ? INFINITY : -INFINITY);
+    __syncwarp();
+    // each lane takes a contiguous segment of the items: the items are in
+    // Morton order, so the 32 items of one round lie far apart and mostly
+    // update different bins
+    const int per = (n + 31) / 32;
+    for (int k = 0; k < per; ++k) {
+        const int i = lane * per + k;
+        if (i >= n) break;
         const TopElem& e = in[b0 + i];
         for (int a = 0; a < 3; ++a) {
             if (sc[a] == 0.f) continue;
             const int bin = min(kTopBins - 1, (int)((0.5f * (e.b[a] + e.b[3 + a]) - lo[a]) * sc[a]));
-            if (bin != lane) continue;
-            ++cnt[a];
-            for (int q = 0; q < 3; ++q) { bx[a][q] = fminf(bx[a][q], e.b[q]); bx[a][3 + q] = fmaxf(bx[a][3 + q], e.b[3 + q]); }
+            atomicAdd(&bcnt[a * kTopBins + bin], 1);
+            int* bb = bbox + (a * kTopBins + bin) * 6;
+            for (int q = 0; q < 3; ++q) {
+                atomicMin(&bb[q], ord_f(e.b[q]));
+                atomicMax(&bb[3 + q], ord_f(e.b[3 + q]));
+            }
         }
     }
+    __syncwarp();
+    // this lane's bin (number lane) of each axis
+    int cnt[3];
+    float bx[3][6];
+    for (int a = 0; a < 3; ++a) {
+        cnt[a] = bcnt[a * kTopBins + lane];
+        for (int q = 0; q < 6; ++q) bx[a][q] = unord_f(bbox[(a * kTopBins + lane) * 6 + q]);
+    }
+    __syncwarp();   // the bins are rewritten by this warp's next task
     // split "bins below s go left" with s = lane (1..31): left = prefix through bin s-1, right =
     // suffix from bin s; each lane keeps its best axis with the counts and boxes of both sides
     float best = INFINITY;
@@ -460,31 +516,15 @@ __device__ void top_task(const TopTask tk, const TopElem* in, TopElem* out, floa
                 sr[3 + q] = fmaxf(sr[3 + q], __shfl_xor_sync(FULL, sr[3 + q], o));
             }
     }
-    if (lane == 0) {
-        int32_t ref[2];
-        const int cb[2] = {b0, b0 + nl}, cn[2] = {nl, n - nl};
-        for (int c = 0; c < 2; ++c) {
-            if (cn[c] == 1) {
-                ref[c] = out[cb[c]].ref;
-                atomicMax(s_depth, tk.depth + out[cb[c]].h);
-            } else {
-                ref[c] = slots[atomicAdd(s_slot, 1)];
-                next[atomicAdd(s_next, 1)] = TopTask{cb[c], cn[c], ref[c], tk.depth + 1};
-            }
-        }
-        float4* o = nodes + 4 * (int64_t)tk.slot;
-        o[0] = make_float4(sl[0], sl[1], sl[2], sl[3]);
-        o[1] = make_float4(sl[4], sl[5], sr[0], sr[1]);
-        o[2] = make_float4(sr[2], sr[3], sr[4], sr[5]);
-        o[3] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), 0.f, 0.f);
-    }
+    if (lane == 0) top_emit(tk, nl, sl, sr, out, nodes, slots, next, s_next, s_slot, s_depth);
     __syncwarp();
 }
 
 // one block: the top tree over the cut, level by level (the tasks of a level
 // are independent: disjoint item ranges, distinct node slots); items and task
 // lists in shared memory
-constexpr int kTopSmem = 2 * kTopCap * (int)sizeof(TopElem) + 2 * (kTopCap / 2 + 1) * (int)sizeof(TopTask);
+constexpr int kTopSmem = 2 * kTopCap * (int)sizeof(TopElem) + 2 * (kTopCap / 2 + 1) * (int)sizeof(TopTask) +
+                         kTopWarps * kTopBinWords * (int)sizeof(int);
 
 __global__ void __launch_bounds__(32 * kTopWarps)
 k_top_sah(float4* __restrict__ nodes, const TopElem* __restrict__ E, const int32_t* __restrict__ slots,
@@ -494,6 +534,7 @@ k_top_sah(float4* __restrict__ nodes, const TopElem* __restrict__ E, const int32
     TopElem* S1 = S0 + kTopCap;
     TopTask* Q0 = reinterpret_cast<TopTask*>(S1 + kTopCap);
     TopTask* Q1 = Q0 + kTopCap / 2 + 1;
+    int* bins = reinterpret_cast<int*>(Q1 + kTopCap / 2 + 1);   // [kTopWarps][kTopBinWords]
     __shared__ int s_nt, s_next, s_slot, s_depth;
     const int warp = threadIdx.x >> 5;
     const int C = *n_cut;
@@ -511,7 +552,7 @@ k_top_sah(float4* __restrict__ nodes, const TopElem* __restrict__ E, const int32
         const int nt = s_nt;
         if (nt == 0) break;
         for (int t = warp; t < nt; t += kTopWarps)
-            top_task(tin[t], in, out, nodes, slots, tout, &s_next, &s_slot, &s_depth);
+            top_task(tin[t], in, out, nodes, slots, tout, &s_next, &s_slot, &s_depth, bins + warp * kTopBinWords);
         __syncthreads();
         if (threadIdx.x == 0) { s_nt = s_next; s_next = 0; }
         __syncthreads();
