@@ -162,6 +162,65 @@ def test_calls_on_user_streams_give_the_same_paths(sbr):
     assert np.array_equal(ref["g"].cpu().numpy(), g.cpu().numpy())
 
 
+def _capture(fn):
+    # one CUDA graph of fn's launches on a side stream (warmed up there first)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn()
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        fn()
+    return graph
+
+
+def test_gains_and_pdp_replay_in_a_cuda_graph(sbr):
+    # the asynchronous calls (kernels launched as programmatic dependents)
+    # captured into a CUDA graph and replayed: bit-identical to the eager calls
+    sc = SCENES["indoor_small"]()
+    r = sbr.run_scene(sc)
+    d, pl = r["dev"], r["paths"]
+    fc = float(sc["freqs"][0])
+    g_ref = sbr.path_gains(pl, d["mats"], d["freqs"], d["gamma"], d["disp"], d["pol"])
+    pdp_ref, st_ref = sbr.pdp_angles(pl, g_ref, 0, fc, 1e-9, 256)
+    torch.cuda.synchronize()
+    g, pdp, st = torch.empty_like(g_ref), torch.empty_like(pdp_ref), torch.empty_like(st_ref)
+
+    def fn():
+        sbr.path_gains(pl, d["mats"], d["freqs"], d["gamma"], d["disp"], d["pol"], out=g)
+        sbr.pdp_angles(pl, g, 0, fc, 1e-9, 256, out=(pdp, st))
+
+    graph = _capture(fn)
+    for t in (g, pdp, st):
+        t.zero_()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(g.cpu().numpy(), g_ref.cpu().numpy())
+    assert np.array_equal(pdp.cpu().numpy(), pdp_ref.cpu().numpy())
+    assert np.array_equal(st.cpu().numpy(), st_ref.cpu().numpy(), equal_nan=True)
+
+
+def test_synthesis_replays_in_a_cuda_graph(sbr):
+    # the tensor-core synthesis (operand prologue, then the kernel as its
+    # programmatic dependent, operands from the stream-ordered pool) captured
+    # into a CUDA graph and replayed: bit-identical to the eager call
+    sc = SCENES["indoor_small"]()
+    r = sbr.run_scene(sc)
+    d, pl = r["dev"], r["paths"]
+    H_ref = sbr.synthesize_H(pl, r["g"], d["freqs"], d["tx_elem"], d["rx_elem"], 0, sbr.SYNTH_FP16X3)
+    torch.cuda.synchronize()
+    H = torch.empty_like(H_ref)
+    graph = _capture(lambda: sbr.synthesize_H(pl, r["g"], d["freqs"], d["tx_elem"], d["rx_elem"], 0,
+                                              sbr.SYNTH_FP16X3, out=H))
+    H.zero_()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(H.cpu().numpy(), H_ref.cpu().numpy())
+
+
 def test_pdp_into_pinned_host_memory_equals_device_output(sbr):
     # the PDP kernel writes straight into pinned host tensors: bit-identical to
     # its device output
