@@ -444,6 +444,30 @@ def test_tensor_core_synthesis_matches_oracle(sbr, ny, nz, nr, F, form):
     assert _h_errors(H64, Ho)[0] < 5e-6
 
 
+@pytest.mark.parametrize("form", [2, 3])
+def test_tensor_core_synthesis_with_many_paths(sbr, form):
+    # a closed room at K = 5 gives one receiver well over a hundred reflected
+    # paths: many K-chunks of 32 paths, the two operand stages alternating
+    # within a tile and across tiles; element by element against the oracle
+    lam = C0 / 60e9
+    sc = scenes.shoebox(N=61, K=5, sub=3, n_rx=1)
+    sc = dict(sc, tx_elem=scenes.upa_yz(sc["tx"], 6, 5, lam / 2), rx_elem=scenes.ula_y(sc["rx"][0], 11, lam / 2),
+              freqs=np.array([59.5e9, 60e9, 60.5e9]), gamma_db_km=np.zeros(3, np.float32),
+              disp_deg_km=np.zeros(3, np.float32))
+    r = sbr.run_scene(sc)
+    ex = to_numpy(r["export"])
+    n_refl = int((ex["nb"] > 0).sum())
+    assert n_refl > 128, n_refl      # at least five chunks
+    Ho = _oracle_H_of(sc, ex)
+    d = r["dev"]
+    H = sbr.synthesize_H(r["paths"], r["g"], d["freqs"], d["tx_elem"], d["rx_elem"], 0, form).cpu().numpy()
+    assert H.shape == Ho.shape == (3, 11, 30)
+    e_max, e_med = _h_errors(H, Ho)
+    print("tcgen05 form", form, "with", n_refl, "reflected paths: max", e_max, "median", e_med)
+    tol_max, tol_med = TC_TOL[form]
+    assert e_max < tol_max and e_med < tol_med
+
+
 def test_synthesis_and_capacity_at_128x128_tx(sbr):
     # the largest Tx array of the capacity trend (128 x 128 UPA, Nt = 16384) on
     # four subcarriers: every form against the oracle on sampled transmit
