@@ -282,7 +282,8 @@ def test_synthesis_los_and_empty_receivers(sbr):
 
 def test_capacity_matches_oracle(sbr):
     rng = np.random.default_rng(0)
-    for (F, Nr, Nt) in ((5, 4, 7), (3, 9, 5), (4, 64, 256), (2, 64, 64)):
+    # both Gram orientations, square, the 64 limit, and single-antenna ends (SISO, SIMO, MISO)
+    for (F, Nr, Nt) in ((5, 4, 7), (3, 9, 5), (4, 64, 256), (2, 64, 64), (3, 1, 1), (2, 1, 16), (2, 16, 1)):
         H = (rng.normal(size=(F, Nr, Nt)) + 1j * rng.normal(size=(F, Nr, Nt))).astype(np.complex64)
         Ht = torch.as_tensor(H, device="cuda")
         snr = np.arange(0.0, 31.0, 5.0)
