@@ -42,7 +42,7 @@ __device__ __forceinline__ double bary_margin(const float* v, d3 p) {
 // outside, 0 near an edge (then the FP64 test decides). The margin is 1e-3 or,
 // for small or thin faces far from the origin, a bound on the FP32 error of
 // the barycentrics (rounding of p and of the products, ~ eps (|a| + |w|) / (size sin^2)).
-__device__ __forceinline__ int screen_in_tri(const float* v, float3 p) {
+__device__ __forceinline__ int screen_in_tri(const float* v, float3 p, float extra = 0.f) {
     float3 a = make_float3(v[0], v[1], v[2]);
     float3 e1 = make_float3(v[3] - a.x, v[4] - a.y, v[5] - a.z);
     float3 e2 = make_float3(v[6] - a.x, v[7] - a.y, v[8] - a.z);
@@ -58,7 +58,16 @@ __device__ __forceinline__ int screen_in_tri(const float* v, float3 p) {
                 fmaxf(fmaxf(fabsf(w.x), fabsf(w.y)), fabsf(w.z)) + 1.f;
     float s2 = d00 + d11;
     float margin = fmaxf(1e-3f, 16.f * 5.9604645e-8f * ext * s2 * sqrtf(s2) / den);
-    return m > margin ? 1 : (m < -margin ? -1 : 0);
+    return m > margin + extra ? 1 : (m < -margin ? -1 : 0);
+}
+
+// the kept ray's hit face holds the refined point by a barycentric margin of at
+// least 1e-6: the FP32 screen accepts it when its margin exceeds the screen's
+// error bound by 1e-6 (then the FP64 margin does too); otherwise the FP64
+// margin decides
+__device__ __forceinline__ bool hint_holds(const float* v, d3 p) {
+    if (screen_in_tri(v, make_float3((float)p.x, (float)p.y, (float)p.z), 1e-6f) > 0) return true;
+    return bary_margin(v, p) >= 1e-6;
 }
 
 __device__ __forceinline__ void angles_deg(d3 v, double* out) {
@@ -229,7 +238,7 @@ __device__ bool refine_key(int lane, int m, const int32_t* seq, unsigned long lo
             bool need = false;
             if (act) {
                 const int32_t h = hint ? hint[(int64_t)(k - 1) * hint_stride] : -1;
-                if (h >= 0 && bary_margin(sc.tri + 9 * (int64_t)h, P[k]) >= 1e-6) {
+                if (h >= 0 && hint_holds(sc.tri + 9 * (int64_t)h, P[k])) {
                     found = h;
                 } else if (sc.nodes) {
                     found = bvh_find_face(sc, s, P[k]);
@@ -276,7 +285,7 @@ __device__ bool refine_key(int lane, int m, const int32_t* seq, unsigned long lo
             int32_t found = -1;
             if (hint) {
                 const int32_t h = hint[(int64_t)(k - 1) * hint_stride];
-                if (h >= 0 && bary_margin(sc.tri + 9 * (int64_t)h, P[k]) >= 1e-6) {
+                if (h >= 0 && hint_holds(sc.tri + 9 * (int64_t)h, P[k])) {
                     face[k - 1] = h;
                     continue;
                 }
