@@ -531,6 +531,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_synth_tc(const __grid_constan
         cur.wl = x.wl;
         cur.dlos = x.dlos; cur.Hf = x.Hf;
         cur.full = x.q0 + 64 <= x.Nr && x.p0 + kTileN <= x.Nt && (x.Nt & 1) == 0 &&
+                   (int64_t)x.Nr * x.Nt < ((int64_t)1 << 31) &&   // 32-bit offsets in the fast epilogue
                    ((((uintptr_t)x.Hf) & 15) == 0) && (!x.los || ((((uintptr_t)x.dlos) & 7) == 0));
         // the previous tile's epilogue runs while this tile's MMAs do; no
         // barrier follows it: the next tile's first chunk barrier carries its
