@@ -221,6 +221,30 @@ def test_synthesis_replays_in_a_cuda_graph(sbr):
     assert np.array_equal(H.cpu().numpy(), H_ref.cpu().numpy())
 
 
+def test_foreign_kernels_between_calls_keep_stream_order(sbr):
+    # the library's kernels wait for their predecessor on the stream before
+    # their first memory access, whoever launched it: gains scaled in place by
+    # a torch kernel between path_gains and pdp_angles raise every PDP tap by
+    # exactly 20 log10(2) dB and leave the delay statistics unchanged
+    sc = SCENES["urban_med"]()
+    r = sbr.run_scene(sc)
+    pl, fc = r["paths"], float(sc["freqs"][0])
+    pdp0, st0 = sbr.pdp_angles(pl, r["g"], 0, fc, 1e-9, 512)
+    g = r["g"].clone()
+    for _ in range(3):
+        g.mul_(2.0)
+        pdp, st = sbr.pdp_angles(pl, g, 0, fc, 1e-9, 512)
+        g.mul_(0.5)
+    torch.cuda.synchronize()
+    a, b = pdp0.cpu().numpy(), pdp.cpu().numpy()
+    fin = np.isfinite(a)
+    assert fin.any() and np.array_equal(fin, np.isfinite(b))
+    assert np.abs(b[fin] - a[fin] - 20.0 * np.log10(2.0)).max() < 1e-4
+    s0, s1 = st0.cpu().numpy(), st.cpu().numpy()
+    ok = np.isfinite(s0[:, 2])
+    assert np.allclose(s1[ok, 2], s0[ok, 2], rtol=1e-12, atol=0.0)   # rms delay spread: scale-free
+
+
 def test_pdp_into_pinned_host_memory_equals_device_output(sbr):
     # the PDP kernel writes straight into pinned host tensors: bit-identical to
     # its device output
